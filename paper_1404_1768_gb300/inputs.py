@@ -1,0 +1,170 @@
+"""Seeded synthetic pencils -- the only module shared by the GPU path's tests
+and the oracle.  It holds input construction only: no quadrature, no
+factorisation, no projection.
+
+The paper's experiments use Matrix Market pencils that are not available
+here; these generators stand in for them with the same kind of structure:
+
+* ``prescribed_pencil``: dense complex A = P diag(lam) Q, B = P Q with
+  P, Q = I + 0.1 G / sqrt(n) (G complex Gaussian).  Then A x = lam B x has
+  exactly the eigenvalues ``lam`` (eigenvectors Q^{-1} e_i), which is the
+  canonical form of Theorem 2.1 with T = P^{-1}, S = Q^{-1}.
+* ``convection_diffusion``: -Lap u + (b1, b2) . grad u on the unit square,
+  Dirichlet, 5-point central differences on an nx x nx grid (B = I), in
+  compact band storage; its spectrum has a closed form.
+* ``ragged_batch``: many prescribed-spectrum pencils of uneven size.
+
+Random draws use ``numpy.random.default_rng(seed)`` (PCG64) in a fixed
+order: lam (u then v, then any re-draws), G_P, G_Q, Y.  With seed 0 and
+n = 200 this order puts 44 eigenvalues inside |z| < 1 (the dense n = 200
+workload is specified as having about 50 inside).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def complex_normal(rng: np.random.Generator, shape) -> np.ndarray:
+    """(N(0,1) + i N(0,1)) / sqrt(2), Fortran order."""
+    re = rng.standard_normal(shape)
+    im = rng.standard_normal(shape)
+    return np.asfortranarray((re + 1j * im) / math.sqrt(2.0))
+
+
+@dataclass
+class DensePencil:
+    A: np.ndarray          # n x n complex128, column-major
+    B: np.ndarray
+    Y: np.ndarray          # n x m0 start block
+    lam: np.ndarray        # prescribed eigenvalues (length n)
+    center: complex
+    radius: float
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+    def inside_count(self) -> int:
+        return int(np.sum(np.abs(self.lam - self.center) < self.radius))
+
+
+def draw_spectrum(rng: np.random.Generator, n: int, lam_radius: float, center: complex,
+                  radius: float, guard: float = 1e-3) -> np.ndarray:
+    """lam = lam_radius * sqrt(u) * exp(2 pi i v) (uniform in the disk), with
+    any eigenvalue within a relative distance ``guard`` of the contour
+    re-drawn so that the inside count is well posed."""
+    u = rng.random(n)
+    v = rng.random(n)
+    lam = lam_radius * np.sqrt(u) * np.exp(2j * np.pi * v)
+    for _ in range(1000):
+        bad = np.abs(np.abs(lam - center) / radius - 1.0) < guard
+        if not bad.any():
+            break
+        k = int(bad.sum())
+        u2 = rng.random(k)
+        v2 = rng.random(k)
+        lam[bad] = lam_radius * np.sqrt(u2) * np.exp(2j * np.pi * v2)
+    return lam
+
+
+def prescribed_pencil(n: int, m0: int, seed: int = 0, center: complex = 0j, radius: float = 1.0,
+                      lam_radius: float = 2.0, lam_center: complex = 0j) -> DensePencil:
+    rng = np.random.default_rng(seed)
+    lam = lam_center + draw_spectrum(rng, n, lam_radius, center - lam_center, radius)
+    gp = complex_normal(rng, (n, n))
+    gq = complex_normal(rng, (n, n))
+    Y = complex_normal(rng, (n, m0))
+    eye = np.eye(n, dtype=np.complex128)
+    P = eye + 0.1 * gp / math.sqrt(n)
+    Q = eye + 0.1 * gq / math.sqrt(n)
+    B = np.asfortranarray(P @ Q)
+    A = np.asfortranarray((P * lam[None, :]) @ Q)
+    return DensePencil(A=A, B=B, Y=Y, lam=lam, center=center, radius=radius)
+
+
+@dataclass
+class BandPencil:
+    A_band: np.ndarray     # (kl + ku + 1) x n compact band storage, row ku + i - j
+    n: int
+    kl: int
+    ku: int
+    Y: np.ndarray
+    nx: int
+    h: float
+    beta: tuple
+
+    def dense(self) -> np.ndarray:
+        A = np.zeros((self.n, self.n), np.complex128, order="F")
+        for j in range(self.n):
+            for i in range(max(0, j - self.ku), min(self.n, j + self.kl + 1)):
+                A[i, j] = self.A_band[self.ku + i - j, j]
+        return A
+
+
+def convection_diffusion(nx: int, m0: int, seed: int = 0, beta=(20.0, 10.0)) -> BandPencil:
+    """A = (1/h^2) [tridiag(-1 - b1 h/2, 4, -1 + b1 h/2) in x  (+)  the same
+    in y with b2], lexicographic order with x fastest, h = 1/(nx + 1).
+    Half-bandwidth nx; B = I."""
+    n = nx * nx
+    h = 1.0 / (nx + 1)
+    kl = ku = nx
+    ab = np.zeros((kl + ku + 1, n), np.complex128, order="F")
+    b1, b2 = beta
+    inv = 1.0 / (h * h)
+    for gy in range(nx):
+        for gx in range(nx):
+            i = gx + gy * nx
+            ab[ku, i] = 4.0 * inv
+            if gx > 0:       # (i, i-1): x-lower
+                ab[ku + 1, i - 1] = (-1.0 - b1 * h / 2) * inv
+            if gx < nx - 1:  # (i, i+1): x-upper
+                ab[ku - 1, i + 1] = (-1.0 + b1 * h / 2) * inv
+            if gy > 0:       # (i, i-nx): y-lower
+                ab[ku + nx, i - nx] = (-1.0 - b2 * h / 2) * inv
+            if gy < nx - 1:  # (i, i+nx): y-upper
+                ab[ku - nx, i + nx] = (-1.0 + b2 * h / 2) * inv
+    rng = np.random.default_rng(seed)
+    Y = complex_normal(rng, (n, m0))
+    return BandPencil(A_band=ab, n=n, kl=kl, ku=ku, Y=Y, nx=nx, h=h, beta=tuple(beta))
+
+
+@dataclass
+class RaggedBatch:
+    pencils: list          # list of DensePencil
+    m0: list               # per-pencil start-block width
+
+
+def ragged_batch(count: int, n_lo: int, n_hi: int, seed: int = 0, lam_radius: float = 2.0) -> RaggedBatch:
+    """count pencils, n ~ U[n_lo, n_hi], circle centre uniform in |z| <= 1,
+    radius U[0.5, 1]; m0 = max(8, ceil(1.5 s / 8) * 8) capped at n, where s is
+    the exact inside count."""
+    rng = np.random.default_rng(seed)
+    out, m0s = [], []
+    for _ in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        cr = math.sqrt(rng.random())
+        ca = 2 * math.pi * rng.random()
+        center = complex(cr * math.cos(ca), cr * math.sin(ca))
+        radius = 0.5 + 0.5 * rng.random()
+        sub_seed = int(rng.integers(0, 2**31 - 1))
+        # the start block width depends on the spectrum (drawn first)
+        lam = draw_spectrum(np.random.default_rng(sub_seed), n, lam_radius, center, radius)
+        s = int(np.sum(np.abs(lam - center) < radius))
+        m0 = min(n, max(8, int(math.ceil(1.5 * s / 8.0)) * 8))
+        p = prescribed_pencil(n, m0, seed=sub_seed, center=center, radius=radius,
+                              lam_radius=lam_radius)
+        out.append(p)
+        m0s.append(m0)
+    return RaggedBatch(pencils=out, m0=m0s)
+
+
+# The workloads of the benchmark and the tests, by name.
+WORKLOADS = {
+    # plain method, FP64 dense, n = 200, circle |z| < 1, 16 trapezoid nodes, m0 = 64
+    "dense_n200_m64_q16": dict(n=200, m0=64, q=16, rule=0, center=0j, radius=1.0, seed=0),
+    # precision form, dense n = 4096, m0 = 1280, 32 trapezoid nodes
+    "dense_n4096_m1280_q32": dict(n=4096, m0=1280, q=32, rule=0, center=0j, radius=1.0, seed=0),
+}
