@@ -1,0 +1,215 @@
+/*
+ * feast_gb300.h -- C ABI of the GB300 (sm_103a) oblique-projection FEAST
+ * solver for the generalized eigenproblem A x = lambda B x (Yin, Chan &
+ * Yeung, "A FEAST algorithm with oblique projection for generalized
+ * eigenvalue problems").
+ *
+ * The solver finds the eigenpairs whose eigenvalues lie strictly inside a
+ * closed contour Gamma.  Its hot path is the contour-integral subspace build
+ * of eq. 4.1 -- one shifted multi-right-hand-side solve (z_j B - A) X_j = B U1
+ * per quadrature node (eq. 4.2), summed as U = sum_j w_j X_j -- followed by
+ * the oblique (Petrov-Galerkin) projection onto the test space B K (eq. 3.9
+ * to 3.10): A~ = U2^H A U1, B~ = U2^H B U1 with U2 an orthonormal basis of
+ * B U1, a small QZ solve of (A~, B~), the residuals of eq. 5.1 and the three
+ * stopping tests of Algorithm GFEAST (Section 4.3).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major complex128 (interleaved re, im doubles)
+ *     unless stated otherwise, with an explicit leading dimension.
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device; "host" pointers are ordinary CPU memory.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream) except where a call says it
+ *     synchronises.
+ *   - The return value is FEAST_OK (0) or a negative FEAST_E* status.  The
+ *     paper's convergence flag (1 / 0 / -1) is a result, not an error.
+ *   - No entry point allocates device memory except feast_setup's host-side
+ *     context record; all device workspace is caller-provided.
+ */
+#ifndef FEAST_GB300_H
+#define FEAST_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status codes */
+#define FEAST_OK          0
+#define FEAST_EINVAL     -1   /* an argument is out of range or inconsistent      */
+#define FEAST_ENOMEM     -2   /* workspace too small or host allocation failed    */
+#define FEAST_ECUDA      -3   /* a CUDA runtime call or kernel launch failed      */
+#define FEAST_ESINGULAR  -4   /* a shifted matrix z_j B - A has an exact zero pivot */
+#define FEAST_ENONFINITE -5   /* NaN or Inf reached a residual                    */
+#define FEAST_ETIMEOUT   -6   /* a bounded device wait gave up                    */
+#define FEAST_ENOCONV    -7   /* the projected QZ iteration hit its iteration cap */
+#define FEAST_EDONE      -8   /* feast_iterate called after the algorithm stopped */
+
+/* ------------------------------------------------------------- problem types */
+typedef enum { FEAST_DENSE = 0, FEAST_BANDED = 1 } feast_kind;
+typedef enum { FEAST_CIRCLE = 0, FEAST_ELLIPSE = 1 } feast_contour_kind;
+typedef enum { FEAST_TRAPEZOID = 0, FEAST_GAUSS_LEGENDRE = 1 } feast_rule;
+typedef enum { FEAST_FP64 = 0, FEAST_C64_REFINE = 1 } feast_precision;
+
+/* The regular pencil z B - A of eq. 1.1 (Section 1: only regularity is
+ * required).
+ *   kind = FEAST_DENSE : A, B are device n x n complex128, leading dim ld.
+ *   kind = FEAST_BANDED: A, B are device complex128 in compact band storage,
+ *                        entry (i, j) at row ku + i - j of column j,
+ *                        ld >= kl + ku + 1.
+ *   b_is_identity != 0 : B = I and the B pointer is ignored (may be NULL).
+ * The matrices are read during feast_setup only (copied into the context). */
+typedef struct {
+    int kind;
+    int64_t n;
+    const void *A;
+    const void *B;
+    int64_t ld;
+    int64_t kl, ku;
+    int b_is_identity;
+} feast_pencil;
+
+/* The contour Gamma.  Circle: centre (center_re, center_im), radius a (b is
+ * ignored).  Ellipse: semi-axis a along the real axis, b along the
+ * imaginary axis.  q quadrature nodes, rule = trapezoid (theta_j =
+ * 2 pi (j - 1/2) / q) or Gauss-Legendre (theta_j = (1 + t_j) pi, eq. 4.1).
+ * "Inside" is strict (|lambda - centre| < a for the circle). */
+typedef struct {
+    int kind;
+    double center_re, center_im, a, b;
+    int q;
+    int rule;
+} feast_contour;
+
+/* Iteration controls (GFEAST inputs, Section 4.3).
+ *   m0        : subspace width t (>= the number of eigenvalues inside).
+ *   Y0        : device n x m0 complex128 start block (leading dim n); the
+ *               first subspace is U = Q Y0 by the quadrature (Algorithm
+ *               EIGENPAIRS, line 2).  Required (no internal RNG).
+ *   eps, eta  : accuracy and spurious-detection tolerances of lines 10, 13.
+ *   max_iter  : line 15.
+ *   prec      : FEAST_FP64 (every step in FP64) or FEAST_C64_REFINE.
+ *   max_refine, refine_tol : refinement controls of FEAST_C64_REFINE.
+ *   stream    : cudaStream_t for every launch of this context.
+ *   no_stop   : benchmark aid -- when non-zero, feast_iterate always performs
+ *               lines 16-17 and keeps iterating after a stop has fired (the
+ *               stopped result stays available through feast_eigs). */
+typedef struct {
+    int m0;
+    const void *Y0;
+    double eps, eta;
+    int max_iter;
+    int prec;
+    int max_refine;
+    double refine_tol;
+    void *stream;
+    int no_stop;
+} feast_options;
+
+/* Per-pass report.  flag: 2 = continue, 1 = converged (line 13), 0 = no
+ * further improvement, previous iterate returned (line 14), -1 = max_iter
+ * (line 15).  bad_node: 1-based node whose factor had a zero pivot. */
+typedef struct {
+    int k, count, flag;
+    double err;
+    double ms_lu, ms_solve, ms_refine, ms_qr, ms_proj, ms_qz;
+    int refine_sweeps_max;
+    int bad_node;
+} feast_iter_info;
+
+typedef struct feast_ctx feast_ctx;
+
+/* Device workspace (bytes, 256-byte aligned start required) that
+ * feast_setup needs for this problem.  Returns FEAST_EINVAL on bad sizes. */
+int feast_workspace_size(const feast_pencil *pencil, const feast_contour *contour,
+                         const feast_options *opts, size_t *bytes);
+
+/* GFEAST lines 1-3 with the start block Y0 in place of SEARCH: nodes and
+ * weights (eq. 4.1), z_j B - A for every node, their LU factors (factored
+ * once and reused every pass, end of Section 4.3), U = Q Y0 by quadrature,
+ * U = U1 R1, B U1 = U2 R2.  workspace: device, >= feast_workspace_size bytes,
+ * owned by the caller and used by the context until feast_destroy.
+ * Synchronises the stream once (to report singular pivots).  On success
+ * *out receives a context; info (may be NULL) receives ms_lu. */
+int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour *contour,
+                const feast_options *opts, void *workspace, size_t workspace_bytes,
+                feast_iter_info *info);
+
+/* One pass of GFEAST lines 5-17: projection A~, B~ (line 5), projected
+ * eigenpairs and Ritz vectors x_i = U1 y_i (line 6), residuals r_i of
+ * eq. 5.1 and the selection of line 10, c(k), e(k) and the stopping tests
+ * of lines 13-15 (evaluated on the device), then -- unless a test fired --
+ * U = Q U1 by quadrature (line 16, eq. 4.1-4.2) and U = U1 R1, B U1 = U2 R2
+ * (line 17).  Synchronises once to read c(k), e(k) and the flag.  Returns
+ * FEAST_EDONE if the algorithm has stopped and no_stop is 0. */
+int feast_iterate(feast_ctx *ctx, feast_iter_info *info);
+
+/* Output of lines 13-15 (the previous iterate's pairs when flag = 0).
+ *   count  : host, number of pairs returned.
+ *   lambda : host, 2 * m0 doubles (re, im) -- at least count pairs written.
+ *   X      : device, n x count complex128 (leading dim ldx) or NULL.
+ *   resid  : host, m0 doubles (eq. 5.1 residuals) or NULL.
+ *   err, flag : host.
+ * Synchronises the stream.  Returns FEAST_EINVAL if no stop has fired yet. */
+int feast_eigs(feast_ctx *ctx, int *count, double *lambda, void *X, int64_t ldx, double *resid,
+               double *err, int *flag);
+
+/* Diagnostic accessor for the test-suite: copies an internal array to the
+ * device buffer dst (asynchronous).  what: 0 U1 (n x m0), 1 U2 (n x m0),
+ * 2 R2 (m0 x m0), 3 A~ (m0 x m0), 4 B~ (m0 x m0), 5 Ritz vectors (n x m0),
+ * 6 Ritz values (m0), 7 A U1 (n x m0), 8 B U1 (n x m0), 9 nodes (q),
+ * 10 weights (q), 11 residuals r_i (m0 doubles), 12 selection flags
+ * (m0 int32).  All complex128 column-major with leading dim = rows. */
+int feast_get(const feast_ctx *ctx, int what, void *dst);
+
+/* The subspace build alone (GFEAST line 16, eq. 4.1-4.2) with the stored
+ * factors: U = sum_j w_j (z_j B - A)^{-1} B V.  V, U: device n x m0
+ * complex128, leading dim n.  Asynchronous. */
+int feast_filter(feast_ctx *ctx, const void *V, void *U);
+
+/* Replace U1 by the device n x m0 matrix U1 (assumed orthonormal) and
+ * recompute U2 R2 = B U1 -- lets a test start a pass from a chosen subspace. */
+int feast_set_subspace(feast_ctx *ctx, const void *U1);
+
+void feast_destroy(feast_ctx *ctx);
+const char *feast_strerror(int status);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (host-side counter; every launch site increments it). */
+unsigned long long feast_kernel_launches(void);
+
+/* ---------------------------------------------------- standalone kernels */
+
+/* Batched LU with partial pivoting (pivot = largest modulus), the direct
+ * solver of eq. 4.2 (Section 5 factors each shifted matrix once).
+ *   M    : device, batch blocks of n x n complex128 (leading dim ld, block
+ *          stride stride elements), factored in place (unit-lower L below
+ *          the diagonal, U on and above).
+ *   piv  : device int32, batch x n; piv[b*n + k] = row swapped with k.
+ *   info : device int32[1]: 0, or 1 + (first block with an exact zero pivot).
+ * Asynchronous. */
+int feast_zgetrf_batched(int64_t n, int batch, void *M, int64_t ld, int64_t stride, int *piv,
+                         int *info, void *stream);
+
+/* Solve with those factors: X_b = M_b^{-1} X_b (X: device, batch blocks of
+ * n x nrhs, leading dim ldx, block stride sx).  Asynchronous. */
+int feast_zgetrs_batched(int64_t n, int64_t nrhs, int batch, const void *M, int64_t ld,
+                         int64_t stride, const int *piv, void *X, int64_t ldx, int64_t sx,
+                         void *stream);
+
+/* Batched complex QZ for projected pencils (GFEAST line 6; the paper points
+ * to LAPACK xGGES / xGGEV).  A, B: device, batch blocks of m x m (B upper
+ * triangular -- its strictly lower part is ignored), overwritten by the
+ * generalized Schur form.  alpha, beta: device m per pencil; V: device
+ * m x m per pencil, unit-norm right eigenvectors (beta A v = alpha B v).
+ * work: device, batch * m * m complex128.  status: device int32[1], number
+ * of pencils whose iteration cap was hit.  Asynchronous. */
+int feast_zqz_batched(int m, int batch, void *A, void *B, void *alpha, void *beta, void *V,
+                      void *work, int *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEAST_GB300_H */

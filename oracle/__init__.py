@@ -61,6 +61,7 @@ def _load():
             lib.or_inside.argtypes = [I, D, D, D, D, D, D]
             lib.or_zgetrf.argtypes = [I, P, I, P]
             lib.or_zgetrs.argtypes = [I, I, P, I, P, P, I]
+            lib.or_zgetrs_cols.argtypes = [I, I, P, I, P, P, I]
             lib.or_zgbtrf.argtypes = [I, I, I, P, I, P]
             lib.or_zgbtrs.argtypes = [I, I, I, I, P, I, P, P, I]
             lib.or_zgemm.argtypes = [I, I, I, I, P, I, P, I, P, I]
@@ -133,6 +134,14 @@ def lu_solve(f, piv, b):
         x = x.reshape(-1, 1, order="F")
     n = f.shape[0]
     _load().or_zgetrs(n, x.shape[1], _p(f), n, _p(piv), _p(x), n)
+    return x
+
+
+def lu_solve_cols(f, piv, b):
+    """lu_solve with the columns solved in parallel (OpenMP)."""
+    x = _zf(b).copy(order="F")
+    n = f.shape[0]
+    _load().or_zgetrs_cols(n, x.shape[1], _p(f), n, _p(piv), _p(x), n)
     return x
 
 

@@ -172,6 +172,14 @@ void or_zgetrs(int n, int nrhs, const zc *lu, int lda, const int *piv, zc *b, in
     }
 }
 
+/* The same substitution for nrhs independent right-hand sides, in parallel
+ * over the columns (used by the CPU-baseline timing of the solve step). */
+void or_zgetrs_cols(int n, int nrhs, const zc *lu, int lda, const int *piv, zc *b, int ldb)
+{
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < nrhs; ++c) or_zgetrs(n, 1, lu, lda, piv, b + (size_t)c * ldb, ldb);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Banded LU with partial pivoting (LAPACK general-band storage):            */
 /* entry (i, j) of the matrix lives at ab[(kl + ku + i - j) + j * ldab] for   */

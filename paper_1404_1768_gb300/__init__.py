@@ -1,1 +1,338 @@
-"""GB300-native oblique-projection FEAST (placeholder; binding added below)."""
+"""GB300-native oblique-projection FEAST (Yin, Chan & Yeung) for A x = lambda B x.
+
+Thin Python binding over the C ABI in ``include/feast_gb300.h``: it only
+marshals arguments (torch device tensors -> raw pointers, structs, the
+current CUDA stream).  Every step of the method runs in the CUDA library
+``_build/libfeast_gb300.so`` (sm_103a); if that library is missing the
+binding raises -- there is no CPU fallback.
+
+Layout: matrices cross the boundary as column-major complex128 device
+buffers.  ``to_device_colmajor`` / ``from_device_colmajor`` convert numpy
+arrays of any order to and from that layout.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Feast", "load", "lib_path", "to_device_colmajor", "from_device_colmajor",
+           "zgetrf_batched", "zgetrs_batched", "zqz_batched", "FeastError"]
+
+FEAST_DENSE, FEAST_BANDED = 0, 1
+FEAST_CIRCLE, FEAST_ELLIPSE = 0, 1
+FEAST_TRAPEZOID, FEAST_GAUSS_LEGENDRE = 0, 1
+FEAST_FP64, FEAST_C64_REFINE = 0, 1
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESINGULAR", -5: "ENONFINITE",
+          -6: "ETIMEOUT", -7: "ENOCONV", -8: "EDONE"}
+
+
+class FeastError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({status})")
+
+
+class Pencil(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int64), ("A", C.c_void_p), ("B", C.c_void_p),
+                ("ld", C.c_int64), ("kl", C.c_int64), ("ku", C.c_int64),
+                ("b_is_identity", C.c_int)]
+
+
+class Contour(C.Structure):
+    _fields_ = [("kind", C.c_int), ("center_re", C.c_double), ("center_im", C.c_double),
+                ("a", C.c_double), ("b", C.c_double), ("q", C.c_int), ("rule", C.c_int)]
+
+
+class Options(C.Structure):
+    _fields_ = [("m0", C.c_int), ("Y0", C.c_void_p), ("eps", C.c_double), ("eta", C.c_double),
+                ("max_iter", C.c_int), ("prec", C.c_int), ("max_refine", C.c_int),
+                ("refine_tol", C.c_double), ("stream", C.c_void_p), ("no_stop", C.c_int)]
+
+
+class IterInfo(C.Structure):
+    _fields_ = [("k", C.c_int), ("count", C.c_int), ("flag", C.c_int), ("err", C.c_double),
+                ("ms_lu", C.c_double), ("ms_solve", C.c_double), ("ms_refine", C.c_double),
+                ("ms_qr", C.c_double), ("ms_proj", C.c_double), ("ms_qz", C.c_double),
+                ("refine_sweeps_max", C.c_int), ("bad_node", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+# every symbol declared in include/feast_gb300.h
+EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs", "feast_get",
+           "feast_filter", "feast_set_subspace", "feast_destroy", "feast_strerror",
+           "feast_zgetrf_batched", "feast_zgetrs_batched", "feast_zqz_batched",
+           "feast_kernel_launches"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if allowed and missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library not built: {path}")
+            _build.build()
+        lib = C.CDLL(path)
+        P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        lib.feast_workspace_size.argtypes = [C.POINTER(Pencil), C.POINTER(Contour), C.POINTER(Options),
+                                             C.POINTER(C.c_size_t)]
+        lib.feast_setup.argtypes = [C.POINTER(P), C.POINTER(Pencil), C.POINTER(Contour),
+                                    C.POINTER(Options), P, C.c_size_t, C.POINTER(IterInfo)]
+        lib.feast_iterate.argtypes = [P, C.POINTER(IterInfo)]
+        lib.feast_eigs.argtypes = [P, C.POINTER(I), P, P, I64, P, C.POINTER(D), C.POINTER(I)]
+        lib.feast_get.argtypes = [P, I, P]
+        lib.feast_filter.argtypes = [P, P, P]
+        lib.feast_set_subspace.argtypes = [P, P]
+        lib.feast_destroy.argtypes = [P]
+        lib.feast_destroy.restype = None
+        lib.feast_strerror.argtypes = [I]
+        lib.feast_strerror.restype = C.c_char_p
+        lib.feast_zgetrf_batched.argtypes = [I64, I, P, I64, I64, P, P, P]
+        lib.feast_zgetrs_batched.argtypes = [I64, I64, I, P, I64, I64, P, P, I64, I64, P]
+        lib.feast_zqz_batched.argtypes = [I, I, P, P, P, P, P, P, P, P]
+        lib.feast_kernel_launches.argtypes = []
+        lib.feast_kernel_launches.restype = C.c_ulonglong
+        _lib = lib
+        return lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the CUDA library in this process so far."""
+    return int(load().feast_kernel_launches())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def to_device_colmajor(x, device="cuda", dtype=None):
+    """numpy / torch (rows x cols) -> flat device tensor in column-major order."""
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        t = x.to(device)
+        if dtype is not None:
+            t = t.to(dtype)
+        if t.dim() == 1:
+            return t.contiguous()
+        return t.t().contiguous().reshape(-1)
+    a = np.asarray(x)
+    if dtype is None and np.iscomplexobj(a):
+        a = a.astype(np.complex128)
+    flat = np.ascontiguousarray(a.ravel(order="F")) if a.ndim == 2 else np.ascontiguousarray(a)
+    t = torch.from_numpy(flat).to(device)
+    if dtype is not None:
+        t = t.to(dtype)
+    return t
+
+
+def from_device_colmajor(t, rows: int, cols: int) -> np.ndarray:
+    """flat column-major device tensor -> numpy (rows x cols)."""
+    a = t.detach().reshape(-1)[: rows * cols].cpu().numpy()
+    return a.reshape(cols, rows).T
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise FeastError(st, where)
+
+
+class Feast:
+    """GFEAST on the GPU (lines 1-3 at construction, one pass of lines 5-17 per
+    ``iterate``).  A, B, Y: numpy arrays or torch tensors (rows x cols); they
+    are copied to column-major complex128 device buffers."""
+
+    def __init__(self, A, B, Y, *, contour_kind=0, rule=0, q=16, center=0j, a=1.0, b=0.0,
+                 eps=1e-12, eta=1e-3, max_iter=50, prec=FEAST_FP64, no_stop=False, kind=0, kl=0,
+                 ku=0, b_identity=False, device="cuda", stream=None, max_refine=5,
+                 refine_tol=1e-14):
+        torch = _torch()
+        self._lib = load()
+        self.device = torch.device(device)
+        self.stream = stream
+        self._A = to_device_colmajor(A, device)
+        self._B = to_device_colmajor(B, device) if (B is not None and not b_identity) else None
+        Yshape = (np.asarray(Y).shape if not isinstance(Y, torch.Tensor) else tuple(Y.shape))
+        self.n, self.m0 = int(Yshape[0]), int(Yshape[1])
+        self.q = int(q)
+        self._Y = to_device_colmajor(Y, device)
+        ld = self.n if kind == FEAST_DENSE else (kl + ku + 1)
+        self._pencil = Pencil(kind, self.n, self._A.data_ptr(),
+                              self._B.data_ptr() if self._B is not None else None,
+                              ld, kl, ku, int(bool(b_identity)))
+        self._contour = Contour(contour_kind, float(center.real), float(center.imag), float(a),
+                                float(b if contour_kind == FEAST_ELLIPSE else a), int(q), int(rule))
+        self._opts = Options(self.m0, self._Y.data_ptr(), float(eps), float(eta), int(max_iter),
+                             int(prec), int(max_refine), float(refine_tol),
+                             _stream_ptr(stream), int(bool(no_stop)))
+        nbytes = C.c_size_t(0)
+        _check(self._lib.feast_workspace_size(C.byref(self._pencil), C.byref(self._contour),
+                                              C.byref(self._opts), C.byref(nbytes)),
+               "feast_workspace_size")
+        self.workspace_bytes = int(nbytes.value)
+        self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+        self._ctx = C.c_void_p()
+        info = IterInfo()
+        st = self._lib.feast_setup(C.byref(self._ctx), C.byref(self._pencil), C.byref(self._contour),
+                                   C.byref(self._opts), self._ws.data_ptr(), self.workspace_bytes,
+                                   C.byref(info))
+        self.setup_info = info.as_dict()
+        _check(st, "feast_setup")
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self._lib.feast_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self) -> dict:
+        info = IterInfo()
+        _check(self._lib.feast_iterate(self._ctx, C.byref(info)), "feast_iterate")
+        return info.as_dict()
+
+    def run(self) -> list:
+        hist = []
+        while True:
+            it = self.iterate()
+            hist.append(it)
+            if it["flag"] != 2:
+                return hist
+
+    def eigs(self, want_vectors: bool = True) -> dict:
+        torch = _torch()
+        cnt, flag = C.c_int(), C.c_int()
+        err = C.c_double()
+        lam = np.zeros(2 * self.m0)
+        res = np.zeros(self.m0)
+        X = torch.zeros(self.n * self.m0, dtype=torch.complex128, device=self.device)
+        _check(self._lib.feast_eigs(self._ctx, C.byref(cnt), lam.ctypes.data,
+                                    X.data_ptr() if want_vectors else None, self.n,
+                                    res.ctypes.data, C.byref(err), C.byref(flag)), "feast_eigs")
+        c = cnt.value
+        out = dict(count=c, lam=(lam[0:2 * c:2] + 1j * lam[1:2 * c:2]), res=res[:c].copy(),
+                   err=err.value, flag=flag.value)
+        if want_vectors:
+            out["X"] = from_device_colmajor(X, self.n, self.m0)[:, :c]
+        return out
+
+    _GET = dict(U1=(0, "nm"), U2=(1, "nm"), R2=(2, "mm"), At=(3, "mm"), Bt=(4, "mm"),
+                X=(5, "nm"), lam=(6, "m"), AU1=(7, "nm"), BU1=(8, "nm"), z=(9, "q"),
+                w=(10, "q"), res=(11, "m_f64"), sel=(12, "m_i32"))
+
+    def get(self, what: str):
+        torch = _torch()
+        idx, shape = self._GET[what]
+        n, m, q = self.n, self.m0, self.q
+        if shape == "m_f64":
+            buf = torch.zeros(m, dtype=torch.float64, device=self.device)
+        elif shape == "m_i32":
+            buf = torch.zeros(m, dtype=torch.int32, device=self.device)
+        else:
+            cnt = dict(nm=n * m, mm=m * m, m=m, q=q)[shape]
+            buf = torch.zeros(cnt, dtype=torch.complex128, device=self.device)
+        _check(self._lib.feast_get(self._ctx, idx, buf.data_ptr()), "feast_get")
+        torch.cuda.current_stream().synchronize()
+        if shape == "nm":
+            return from_device_colmajor(buf, n, m)
+        if shape == "mm":
+            return from_device_colmajor(buf, m, m)
+        a = buf.cpu().numpy()
+        return a.astype(bool) if shape == "m_i32" else a
+
+    def filter(self, V) -> np.ndarray:
+        torch = _torch()
+        Vd = to_device_colmajor(V, self.device)
+        Ud = torch.zeros(self.n * self.m0, dtype=torch.complex128, device=self.device)
+        _check(self._lib.feast_filter(self._ctx, Vd.data_ptr(), Ud.data_ptr()), "feast_filter")
+        torch.cuda.current_stream().synchronize()
+        return from_device_colmajor(Ud, self.n, self.m0)
+
+    def set_subspace(self, U1):
+        Ud = to_device_colmajor(U1, self.device)
+        _check(self._lib.feast_set_subspace(self._ctx, Ud.data_ptr()), "feast_set_subspace")
+        _torch().cuda.current_stream().synchronize()
+
+
+# --------------------------------------------------------------- standalone kernels
+def zgetrf_batched(M_list, stream=None):
+    """LU of each n x n matrix in M_list.  Returns (factors list, pivots
+    (batch x n), info)."""
+    torch = _torch()
+    lib = load()
+    n = np.asarray(M_list[0]).shape[0]
+    batch = len(M_list)
+    buf = torch.cat([to_device_colmajor(M) for M in M_list])
+    piv = torch.zeros(batch * n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib.feast_zgetrf_batched(n, batch, buf.data_ptr(), n, n * n, piv.data_ptr(),
+                                    info.data_ptr(), _stream_ptr(stream)), "feast_zgetrf_batched")
+    torch.cuda.current_stream().synchronize()
+    facs = [from_device_colmajor(buf[b * n * n:(b + 1) * n * n], n, n) for b in range(batch)]
+    return facs, piv.cpu().numpy().reshape(batch, n), int(info.item())
+
+
+def zgetrs_batched(F_list, piv, R_list, stream=None):
+    torch = _torch()
+    lib = load()
+    n = np.asarray(F_list[0]).shape[0]
+    nrhs = np.asarray(R_list[0]).shape[1]
+    batch = len(F_list)
+    fb = torch.cat([to_device_colmajor(F) for F in F_list])
+    xb = torch.cat([to_device_colmajor(R) for R in R_list])
+    pv = torch.from_numpy(np.ascontiguousarray(piv, dtype=np.int32).ravel()).cuda()
+    _check(lib.feast_zgetrs_batched(n, nrhs, batch, fb.data_ptr(), n, n * n, pv.data_ptr(),
+                                    xb.data_ptr(), n, n * nrhs, _stream_ptr(stream)),
+           "feast_zgetrs_batched")
+    torch.cuda.current_stream().synchronize()
+    return [from_device_colmajor(xb[b * n * nrhs:(b + 1) * n * nrhs], n, nrhs) for b in range(batch)]
+
+
+def zqz_batched(A_list, B_list, stream=None):
+    """Generalized eigenpairs of each (A, B) (B upper triangular).  Returns
+    alpha (batch x m), beta, V list, fail count."""
+    torch = _torch()
+    lib = load()
+    m = np.asarray(A_list[0]).shape[0]
+    batch = len(A_list)
+    ab = torch.cat([to_device_colmajor(A) for A in A_list])
+    bb = torch.cat([to_device_colmajor(B) for B in B_list])
+    al = torch.zeros(batch * m, dtype=torch.complex128, device="cuda")
+    be = torch.zeros_like(al)
+    V = torch.zeros(batch * m * m, dtype=torch.complex128, device="cuda")
+    work = torch.zeros_like(V)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib.feast_zqz_batched(m, batch, ab.data_ptr(), bb.data_ptr(), al.data_ptr(),
+                                 be.data_ptr(), V.data_ptr(), work.data_ptr(), st.data_ptr(),
+                                 _stream_ptr(stream)), "feast_zqz_batched")
+    torch.cuda.current_stream().synchronize()
+    Vs = [from_device_colmajor(V[b * m * m:(b + 1) * m * m], m, m) for b in range(batch)]
+    return (al.cpu().numpy().reshape(batch, m), be.cpu().numpy().reshape(batch, m), Vs,
+            int(st.item()))

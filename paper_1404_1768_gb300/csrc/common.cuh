@@ -1,0 +1,154 @@
+// Internal helpers shared by the CUDA translation units of the GB300 FEAST
+// library (never by the oracle).  Complex numbers are double2 (re, im) in
+// FP64 and float2 in FP32; all matrices are column-major with an explicit
+// leading dimension.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/feast_gb300.h"
+
+namespace feast {
+
+// ---------------------------------------------------------------- complex FP64
+typedef double2 zd;
+
+__host__ __device__ __forceinline__ zd zmake(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ zd zadd(zd a, zd b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ zd zsub(zd a, zd b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ zd zmul(zd a, zd b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ zd zconj(zd a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ zd zscale(zd a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double zabs2(zd a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double zabs(zd a) { return hypot(a.x, a.y); }
+// c += a * b
+__host__ __device__ __forceinline__ void zfma(zd &c, zd a, zd b)
+{
+    c.x = fma(a.x, b.x, c.x);
+    c.x = fma(-a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y);
+    c.y = fma(a.y, b.x, c.y);
+}
+// c += conj(a) * b
+__host__ __device__ __forceinline__ void zfma_conj(zd &c, zd a, zd b)
+{
+    c.x = fma(a.x, b.x, c.x);
+    c.x = fma(a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y);
+    c.y = fma(-a.y, b.x, c.y);
+}
+// a / b  (Smith's algorithm, avoids overflow in |b|^2)
+__host__ __device__ __forceinline__ zd zdiv(zd a, zd b)
+{
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.x * r + b.y;
+        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+
+// ---------------------------------------------------------------- status
+// Per-context device-side status written by kernels (pivot failures,
+// non-finite values) and read by the host at the one sync point per pass.
+struct DevStatus {
+    int lu_info;        // first node (1-based) with an exactly zero pivot, else 0
+    int lu_row;         // its column (1-based)
+    int nonfinite;      // non-zero if a NaN/Inf reached a residual
+    int count;          // c(k)
+    double err;         // e(k)
+    int flag;           // 2 continue, 1 / 0 / -1 stopping criteria
+    int qz_fail;        // pencils whose QZ iteration hit its iteration cap
+    int pad[2];
+};
+
+#define FEAST_CUDA_TRY(expr)                                                         \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess) return FEAST_ECUDA;                                   \
+    } while (0)
+
+// Every kernel launch of the library is followed by this check, which also
+// counts the launch (feast_kernel_launches reports the total).
+void count_launch();
+#define FEAST_LAUNCH_CHECK()                                                         \
+    do {                                                                             \
+        ::feast::count_launch();                                                     \
+        cudaError_t _e = cudaGetLastError();                                         \
+        if (_e != cudaSuccess) return FEAST_ECUDA;                                   \
+    } while (0)
+
+static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------- kernels (FP64)
+// Batched complex GEMM:  C_b = alpha * op(A_b) * B_b + beta * C_b, b = 0..batch-1,
+// op(A) = A (conj_a = 0) or A^H (conj_a = 1).  op(A) is m x k, B k x n.
+// Strides are in elements between consecutive batch members.
+int zgemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, zd alpha,
+                  const zd *A, int64_t lda, int64_t sA, const zd *B, int64_t ldb, int64_t sB,
+                  zd beta, zd *C, int64_t ldc, int64_t sC, int batch);
+
+// M_j = z_j B - A for j = 0..q-1 into F (q blocks of ldf x n); B may be null
+// (identity).
+int zform_shifted(cudaStream_t s, int64_t n, int q, const zd *A, const zd *B, int64_t ld,
+                  const zd *z, zd *F, int64_t ldf, int64_t sF);
+
+// Batched LU with partial pivoting (modulus criterion) in place.
+// info (may be null): set to 1 + the first block with an exact zero pivot;
+// row (may be null): that pivot's column + 1.
+int zgetrf_batched(cudaStream_t s, int64_t n, int batch, zd *F, int64_t ldf, int64_t sF,
+                   int *piv, int *info, int *row);
+
+// Batched solve with the LU factors: X_b = F_b^{-1} X_b in place
+// (rows permuted by piv first).  X_b is n x nrhs.
+int zgetrs_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const zd *F,
+                   int64_t ldf, int64_t sF, const int *piv, zd *X, int64_t ldx, int64_t sX);
+
+// U = sum_j w_j X_j  (n x m, node order j = 0..q-1).
+int znode_sum(cudaStream_t s, int64_t n, int64_t m, int q, const zd *w, const zd *X,
+              int64_t ldx, int64_t sX, zd *U, int64_t ldu);
+
+// Thin QR by block classical Gram-Schmidt with re-orthogonalisation:
+// V (n x m, overwritten by Q), R (m x m upper, real positive diagonal).
+int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr,
+          zd *work);
+size_t zorth_work_elems(int64_t n, int64_t m);
+
+// Batched complex QZ (one pencil per CTA): A -> S, B -> P (B upper
+// triangular on entry), Zv -> right eigenvectors (unit 2-norm),
+// alpha / beta eigenvalue pairs.  work: 1 m x m block per pencil.
+int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA, zd *B,
+                int64_t ldb, int64_t sB, zd *alpha, zd *beta, zd *V, int64_t ldv, int64_t sV,
+                zd *work, int *fail);
+
+// Composition of the LU interchanges: perm[b*n + i] = original row at i.
+int zpiv_to_perm(cudaStream_t s, int64_t n, int batch, const int *piv, int *perm);
+// X_b[i, :] = R[perm_b[i], :]
+int zgather_rows(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const int *perm,
+                 const zd *R, int64_t ldr, zd *X, int64_t ldx, int64_t sX);
+// L then U solves of already-permuted right-hand sides (in place).
+int ztrsm_lu_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const zd *F,
+                     int64_t ldf, int64_t sF, zd *X, int64_t ldx, int64_t sX);
+
+// Residuals of eq. 5.1 for every Ritz pair.
+int ritz_residuals(cudaStream_t s, int64_t n, int m, const zd *AX, const zd *BX, int64_t ld,
+                   const zd *alpha, const zd *beta, zd *lam, double *res, DevStatus *st);
+// Selection and stopping tests of GFEAST lines 7-15 (device side).
+int stop_test(cudaStream_t s, int m, const feast_contour *c, const zd *lam, const double *res,
+              double eta, double eps, int k, int max_iter, int c_prev, double e_prev, int *sel,
+              int *idx, DevStatus *st);
+// Accepted pairs to the front of Xc / lamc / resc.
+int compact_pairs(cudaStream_t s, int64_t n, int m, const int *idx, const DevStatus *st,
+                  const zd *X, int64_t ldx, const zd *lam, const double *res, zd *Xc, zd *lamc,
+                  double *resc);
+
+// Contour nodes / weights on the device.
+int contour_nodes(cudaStream_t s, const feast_contour *c, zd *z, zd *w);
+
+}  // namespace feast

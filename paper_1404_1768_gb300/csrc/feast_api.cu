@@ -1,0 +1,477 @@
+// C ABI of the GB300 FEAST library: context set-up (GFEAST lines 1-3 with a
+// given start block), one pass of lines 5-17 per feast_iterate, the output
+// of lines 13-15, and the standalone batched LU / solve / QZ entry points.
+//
+// All device memory is carved from one caller-provided workspace; the
+// context record itself is the only host allocation.  Every step runs in
+// this library's kernels on the caller's stream; the host only sequences
+// launches and reads c(k), e(k) and the flag once per pass.
+#include <atomic>
+#include <stdlib.h>
+#include <string.h>
+
+#include "common.cuh"
+
+using namespace feast;
+
+namespace feast {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace feast
+
+struct feast_ctx {
+    // problem
+    int kind;
+    int64_t n, kl, ku;
+    int b_identity;
+    int q, m0;
+    feast_contour contour;
+    double eps, eta;
+    int max_iter, prec, no_stop;
+    cudaStream_t s;
+    // device arrays
+    zd *A, *B;          // n x n copies (B null when identity)
+    zd *z, *w;          // nodes, weights
+    zd *F;              // q x n x n factors
+    int *piv, *perm;    // q x n
+    zd *Xs;             // q x n x m0 per-node solutions
+    zd *U, *U1, *U2;    // n x m0
+    zd *W;              // n x 2 m0 : [A U1 | B U1]
+    zd *R1, *R2;        // m0 x m0
+    zd *P;              // m0 x 2 m0 : [A~ | B~]
+    zd *Q;              // m0 x 2 m0 : QZ working copy
+    zd *Yv;             // m0 x m0 projected eigenvectors
+    zd *alpha, *beta, *lam;
+    zd *Xr;             // n x m0 Ritz vectors
+    zd *AXBX;           // n x 2 m0 : [A X | B X]
+    double *res;
+    int *sel, *idx;
+    zd *Xc[2], *lamc[2];
+    double *resc[2];
+    zd *Xo, *lamo;
+    double *reso;
+    zd *tmp;            // n x m0
+    zd *orth_work, *qz_work;
+    DevStatus *st;
+    // host state
+    int k, c_prev, done, cur;
+    double e_prev;
+    int out_count, out_flag, out_k;
+    double out_err;
+    cudaEvent_t ev[8];
+};
+
+namespace {
+
+struct Carver {
+    char *base;
+    size_t off;
+    bool dry;
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = dry ? nullptr : reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int validate(const feast_pencil *p, const feast_contour *c, const feast_options *o)
+{
+    if (!p || !c || !o) return FEAST_EINVAL;
+    if (p->n < 1 || o->m0 < 1 || o->m0 > p->n || c->q < 1 || c->q > 4096) return FEAST_EINVAL;
+    if (p->kind != FEAST_DENSE) return FEAST_EINVAL;       // banded path: not in this build
+    if (o->prec != FEAST_FP64) return FEAST_EINVAL;        // precision form: not in this build
+    if (p->ld < p->n) return FEAST_EINVAL;
+    if (!(c->a > 0.0) || (c->kind == FEAST_ELLIPSE && !(c->b > 0.0))) return FEAST_EINVAL;
+    if (c->kind != FEAST_CIRCLE && c->kind != FEAST_ELLIPSE) return FEAST_EINVAL;
+    if (c->rule != FEAST_TRAPEZOID && c->rule != FEAST_GAUSS_LEGENDRE) return FEAST_EINVAL;
+    if (o->max_iter < 1 || !(o->eta > 0.0)) return FEAST_EINVAL;
+    if (!p->A || (!p->B && !p->b_is_identity) || !o->Y0) return FEAST_EINVAL;
+    return FEAST_OK;
+}
+
+void carve(feast_ctx *c, Carver &cv)
+{
+    const size_t n = (size_t)c->n, m = (size_t)c->m0, q = (size_t)c->q;
+    c->A = cv.take<zd>(n * n);
+    c->B = c->b_identity ? nullptr : cv.take<zd>(n * n);
+    c->z = cv.take<zd>(q);
+    c->w = cv.take<zd>(q);
+    c->F = cv.take<zd>(q * n * n);
+    c->piv = cv.take<int>(q * n);
+    c->perm = cv.take<int>(q * n);
+    c->Xs = cv.take<zd>(q * n * m);
+    c->U = cv.take<zd>(n * m);
+    c->U1 = cv.take<zd>(n * m);
+    c->U2 = cv.take<zd>(n * m);
+    c->W = cv.take<zd>(2 * n * m);
+    c->R1 = cv.take<zd>(m * m);
+    c->R2 = cv.take<zd>(m * m);
+    c->P = cv.take<zd>(2 * m * m);
+    c->Q = cv.take<zd>(2 * m * m);
+    c->Yv = cv.take<zd>(m * m);
+    c->alpha = cv.take<zd>(m);
+    c->beta = cv.take<zd>(m);
+    c->lam = cv.take<zd>(m);
+    c->Xr = cv.take<zd>(n * m);
+    c->AXBX = cv.take<zd>(2 * n * m);
+    c->res = cv.take<double>(m);
+    c->sel = cv.take<int>(m);
+    c->idx = cv.take<int>(m);
+    for (int i = 0; i < 2; ++i) {
+        c->Xc[i] = cv.take<zd>(n * m);
+        c->lamc[i] = cv.take<zd>(m);
+        c->resc[i] = cv.take<double>(m);
+    }
+    c->Xo = cv.take<zd>(n * m);
+    c->lamo = cv.take<zd>(m);
+    c->reso = cv.take<double>(m);
+    c->tmp = cv.take<zd>(n * m);
+    c->orth_work = cv.take<zd>(zorth_work_elems((int64_t)n, (int64_t)m));
+    c->qz_work = cv.take<zd>(m * m);
+    c->st = cv.take<DevStatus>(1);
+}
+
+void fill_ctx_params(feast_ctx *c, const feast_pencil *p, const feast_contour *ct,
+                     const feast_options *o)
+{
+    c->kind = p->kind;
+    c->n = p->n;
+    c->kl = p->kl;
+    c->ku = p->ku;
+    c->b_identity = p->b_is_identity ? 1 : 0;
+    c->q = ct->q;
+    c->m0 = o->m0;
+    c->contour = *ct;
+    if (c->contour.kind == FEAST_CIRCLE) c->contour.b = c->contour.a;
+    c->eps = o->eps;
+    c->eta = o->eta;
+    c->max_iter = o->max_iter;
+    c->prec = o->prec;
+    c->no_stop = o->no_stop;
+    c->s = (cudaStream_t)o->stream;
+}
+
+const zd kOne = {1.0, 0.0}, kZero = {0.0, 0.0}, kMone = {-1.0, 0.0};
+
+// Y = B X (copy when B = I).  X, Y: n x m, leading dim n.
+int apply_B(feast_ctx *c, const zd *X, zd *Y, int64_t m)
+{
+    const int64_t n = c->n;
+    if (c->b_identity) {
+        FEAST_CUDA_TRY(cudaMemcpyAsync(Y, X, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
+        return FEAST_OK;
+    }
+    return zgemm_batched(c->s, 0, n, m, n, kOne, c->B, n, 0, X, n, 0, kZero, Y, n, 0, 1);
+}
+
+// U = sum_j w_j (z_j B - A)^{-1} B V   (eq. 4.1 - 4.2)
+int filter(feast_ctx *c, const zd *V, zd *Uout)
+{
+    const int64_t n = c->n, m = c->m0;
+    int e;
+    if ((e = apply_B(c, V, c->tmp, m))) return e;
+    if ((e = zgather_rows(c->s, n, m, c->q, c->perm, c->tmp, n, c->Xs, n, n * m))) return e;
+    if ((e = ztrsm_lu_batched(c->s, n, m, c->q, c->F, n, n * n, c->Xs, n, n * m))) return e;
+    return znode_sum(c->s, n, m, c->q, c->w, c->Xs, n, n * m, Uout, n);
+}
+
+// U1 R1 = U ; W[:, m0:] = B U1 ; U2 R2 = B U1   (GFEAST lines 2, 17)
+int orthonormalise(feast_ctx *c, const zd *Usrc)
+{
+    const int64_t n = c->n, m = c->m0;
+    int e;
+    if (Usrc != c->U1)
+        FEAST_CUDA_TRY(cudaMemcpyAsync(c->U1, Usrc, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
+    if ((e = zorth(c->s, n, m, c->U1, n, c->R1, m, c->orth_work))) return e;
+    zd *BU1 = c->W + n * m;
+    if ((e = apply_B(c, c->U1, BU1, m))) return e;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
+    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work);
+}
+
+float ev_ms(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+    return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+int feast_workspace_size(const feast_pencil *pencil, const feast_contour *contour,
+                         const feast_options *opts, size_t *bytes)
+{
+    int e = validate(pencil, contour, opts);
+    if (e) return e;
+    if (!bytes) return FEAST_EINVAL;
+    feast_ctx c;
+    memset(&c, 0, sizeof(c));
+    fill_ctx_params(&c, pencil, contour, opts);
+    Carver cv{nullptr, 0, true};
+    carve(&c, cv);
+    *bytes = cv.off + 256;
+    return FEAST_OK;
+}
+
+int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour *contour,
+                const feast_options *opts, void *workspace, size_t workspace_bytes,
+                feast_iter_info *info)
+{
+    if (!out) return FEAST_EINVAL;
+    *out = nullptr;
+    int e = validate(pencil, contour, opts);
+    if (e) return e;
+    size_t need = 0;
+    feast_workspace_size(pencil, contour, opts, &need);
+    if (!workspace || workspace_bytes < need) return FEAST_ENOMEM;
+    if (((uintptr_t)workspace & 255u) != 0) return FEAST_EINVAL;
+    feast_ctx *c = (feast_ctx *)calloc(1, sizeof(feast_ctx));
+    if (!c) return FEAST_ENOMEM;
+    fill_ctx_params(c, pencil, contour, opts);
+    Carver cv{(char *)workspace, 0, false};
+    carve(c, cv);
+    for (int i = 0; i < 8; ++i)
+        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; }
+    const int64_t n = c->n, m = c->m0;
+    cudaStream_t s = c->s;
+#define TRY(x) do { int _r = (x); if (_r) { feast_destroy(c); return _r; } } while (0)
+#define CTRY(x) do { if ((x) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; } } while (0)
+    CTRY(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
+    CTRY(cudaMemcpy2DAsync(c->A, n * sizeof(zd), pencil->A, pencil->ld * sizeof(zd), n * sizeof(zd), n,
+                           cudaMemcpyDeviceToDevice, s));
+    if (!c->b_identity)
+        CTRY(cudaMemcpy2DAsync(c->B, n * sizeof(zd), pencil->B, pencil->ld * sizeof(zd), n * sizeof(zd), n,
+                               cudaMemcpyDeviceToDevice, s));
+    CTRY(cudaEventRecord(c->ev[0], s));
+    TRY(contour_nodes(s, &c->contour, c->z, c->w));
+    // z_j B - A and its LU factors (factored once, reused every pass)
+    TRY(zform_shifted(s, n, c->q, c->A, c->B, n, c->z, c->F, n, n * n));
+    TRY(zgetrf_batched(s, n, c->q, c->F, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row));
+    TRY(zpiv_to_perm(s, n, c->q, c->piv, c->perm));
+    CTRY(cudaEventRecord(c->ev[1], s));
+    // first subspace U = Q Y0, then U1, U2
+    TRY(filter(c, (const zd *)opts->Y0, c->U));
+    TRY(orthonormalise(c, c->U));
+    CTRY(cudaEventRecord(c->ev[2], s));
+    DevStatus hs;
+    CTRY(cudaMemcpyAsync(&hs, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CTRY(cudaStreamSynchronize(s));
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->ms_lu = ev_ms(c->ev[0], c->ev[1]);
+        info->ms_solve = ev_ms(c->ev[1], c->ev[2]);
+        info->flag = 2;
+        info->bad_node = hs.lu_info;
+    }
+    if (hs.lu_info) {
+        feast_destroy(c);
+        return FEAST_ESINGULAR;
+    }
+    c->k = 0;
+    c->c_prev = 0;
+    c->e_prev = 0.0;
+    c->done = 0;
+    c->cur = 0;
+    *out = c;
+    return FEAST_OK;
+#undef TRY
+#undef CTRY
+}
+
+int feast_iterate(feast_ctx *c, feast_iter_info *info)
+{
+    if (!c) return FEAST_EINVAL;
+    if (c->done && !c->no_stop) return FEAST_EDONE;
+    const int64_t n = c->n, m = c->m0;
+    cudaStream_t s = c->s;
+    int e;
+    c->k += 1;
+    FEAST_CUDA_TRY(cudaEventRecord(c->ev[0], s));
+    // line 5: [A~ | B~] = U2^H [A U1 | B U1]; B U1 is already in W[:, m0:]
+    if ((e = zgemm_batched(s, 0, n, m, n, kOne, c->A, n, 0, c->U1, n, 0, kZero, c->W, n, 0, 1))) return e;
+    if ((e = zgemm_batched(s, 1, m, 2 * m, n, kOne, c->U2, n, 0, c->W, n, 0, kZero, c->P, m, 0, 1))) return e;
+    FEAST_CUDA_TRY(cudaEventRecord(c->ev[1], s));
+    // line 6: projected eigenpairs, x_i = U1 y_i
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
+    if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
+                         c->qz_work, &c->st->qz_fail))) return e;
+    FEAST_CUDA_TRY(cudaEventRecord(c->ev[2], s));
+    if ((e = zgemm_batched(s, 0, n, m, m, kOne, c->U1, n, 0, c->Yv, m, 0, kZero, c->Xr, n, 0, 1))) return e;
+    // A x_i = (A U1) y_i, B x_i = (B U1) y_i
+    if ((e = zgemm_batched(s, 0, n, m, m, kOne, c->W, n, n * m, c->Yv, m, 0, kZero, c->AXBX, n, n * m, 2))) return e;
+    // lines 7-12: residuals (eq. 5.1), selection, c(k), e(k); lines 13-15
+    if ((e = ritz_residuals(s, n, (int)m, c->AXBX, c->AXBX + n * m, n, c->alpha, c->beta, c->lam, c->res, c->st))) return e;
+    if ((e = stop_test(s, (int)m, &c->contour, c->lam, c->res, c->eta, c->eps, c->k, c->max_iter, c->c_prev,
+                       c->e_prev, c->sel, c->idx, c->st))) return e;
+    if ((e = compact_pairs(s, n, (int)m, c->idx, c->st, c->Xr, n, c->lam, c->res, c->Xc[c->cur], c->lamc[c->cur],
+                           c->resc[c->cur]))) return e;
+    FEAST_CUDA_TRY(cudaEventRecord(c->ev[3], s));
+    // lines 16-17, issued before the flag is read back so that the whole pass
+    // is one stream-ordered sequence; when a stop fires the new subspace is
+    // simply not used (the stopped pairs were compacted above).
+    if ((e = filter(c, c->U1, c->U))) return e;
+    FEAST_CUDA_TRY(cudaEventRecord(c->ev[4], s));
+    if ((e = orthonormalise(c, c->U))) return e;
+    FEAST_CUDA_TRY(cudaEventRecord(c->ev[5], s));
+    DevStatus hs;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(&hs, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs.nonfinite) return FEAST_ENONFINITE;
+    if (hs.qz_fail) return FEAST_ENOCONV;
+    if (hs.flag != 2 && !c->done) {
+        c->done = 1;
+        c->out_flag = hs.flag;
+        // line 14 returns the previous iterate
+        const int src = (hs.flag == 0) ? (c->cur ^ 1) : c->cur;
+        c->out_count = (hs.flag == 0) ? c->c_prev : hs.count;
+        c->out_err = (hs.flag == 0) ? c->e_prev : hs.err;
+        c->out_k = (hs.flag == 0) ? c->k - 1 : c->k;
+        FEAST_CUDA_TRY(cudaMemcpyAsync(c->Xo, c->Xc[src], sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, s));
+        FEAST_CUDA_TRY(cudaMemcpyAsync(c->lamo, c->lamc[src], sizeof(zd) * m, cudaMemcpyDeviceToDevice, s));
+        FEAST_CUDA_TRY(cudaMemcpyAsync(c->reso, c->resc[src], sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    }
+    c->c_prev = hs.count;
+    c->e_prev = hs.err;
+    c->cur ^= 1;
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->k = c->k;
+        info->count = hs.count;
+        info->err = hs.err;
+        info->flag = hs.flag;
+        info->ms_proj = ev_ms(c->ev[0], c->ev[1]) + ev_ms(c->ev[2], c->ev[3]);
+        info->ms_qz = ev_ms(c->ev[1], c->ev[2]);
+        info->ms_solve = ev_ms(c->ev[3], c->ev[4]);
+        info->ms_qr = ev_ms(c->ev[4], c->ev[5]);
+    }
+    return FEAST_OK;
+}
+
+int feast_eigs(feast_ctx *c, int *count, double *lambda, void *X, int64_t ldx, double *resid,
+               double *err, int *flag)
+{
+    if (!c || !count || !lambda || !err || !flag) return FEAST_EINVAL;
+    if (!c->done) return FEAST_EINVAL;
+    const int64_t n = c->n;
+    cudaStream_t s = c->s;
+    const int cnt = c->out_count;
+    if (cnt > 0) {
+        FEAST_CUDA_TRY(cudaMemcpyAsync(lambda, c->lamo, sizeof(zd) * cnt, cudaMemcpyDeviceToHost, s));
+        if (resid) FEAST_CUDA_TRY(cudaMemcpyAsync(resid, c->reso, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+        if (X) {
+            if (ldx < n) return FEAST_EINVAL;
+            FEAST_CUDA_TRY(cudaMemcpy2DAsync(X, ldx * sizeof(zd), c->Xo, n * sizeof(zd), n * sizeof(zd), cnt,
+                                             cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    *count = cnt;
+    *err = c->out_err;
+    *flag = c->out_flag;
+    return FEAST_OK;
+}
+
+int feast_get(const feast_ctx *c, int what, void *dst)
+{
+    if (!c || !dst) return FEAST_EINVAL;
+    const size_t n = (size_t)c->n, m = (size_t)c->m0;
+    const void *src = nullptr;
+    size_t bytes = 0;
+    switch (what) {
+    case 0: src = c->U1; bytes = n * m * sizeof(zd); break;
+    case 1: src = c->U2; bytes = n * m * sizeof(zd); break;
+    case 2: src = c->R2; bytes = m * m * sizeof(zd); break;
+    case 3: src = c->P; bytes = m * m * sizeof(zd); break;
+    case 4: src = c->P + m * m; bytes = m * m * sizeof(zd); break;
+    case 5: src = c->Xr; bytes = n * m * sizeof(zd); break;
+    case 6: src = c->lam; bytes = m * sizeof(zd); break;
+    case 7: src = c->W; bytes = n * m * sizeof(zd); break;
+    case 8: src = c->W + n * m; bytes = n * m * sizeof(zd); break;
+    case 9: src = c->z; bytes = (size_t)c->q * sizeof(zd); break;
+    case 10: src = c->w; bytes = (size_t)c->q * sizeof(zd); break;
+    case 11: src = c->res; bytes = m * sizeof(double); break;
+    case 12: src = c->sel; bytes = m * sizeof(int); break;
+    default: return FEAST_EINVAL;
+    }
+    FEAST_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->s));
+    return FEAST_OK;
+}
+
+int feast_filter(feast_ctx *c, const void *V, void *U)
+{
+    if (!c || !V || !U) return FEAST_EINVAL;
+    return filter(c, (const zd *)V, (zd *)U);
+}
+
+int feast_set_subspace(feast_ctx *c, const void *U1)
+{
+    if (!c || !U1) return FEAST_EINVAL;
+    const int64_t n = c->n, m = c->m0;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->U1, U1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
+    zd *BU1 = c->W + n * m;
+    int e = apply_B(c, c->U1, BU1, m);
+    if (e) return e;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
+    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work);
+}
+
+void feast_destroy(feast_ctx *c)
+{
+    if (!c) return;
+    for (int i = 0; i < 8; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    free(c);
+}
+
+unsigned long long feast_kernel_launches(void) { return g_launches.load(); }
+
+const char *feast_strerror(int status)
+{
+    switch (status) {
+    case FEAST_OK: return "ok";
+    case FEAST_EINVAL: return "invalid argument";
+    case FEAST_ENOMEM: return "workspace too small or host allocation failed";
+    case FEAST_ECUDA: return "CUDA runtime error";
+    case FEAST_ESINGULAR: return "a shifted matrix has an exact zero pivot";
+    case FEAST_ENONFINITE: return "non-finite value in a residual";
+    case FEAST_ETIMEOUT: return "bounded device wait timed out";
+    case FEAST_ENOCONV: return "projected QZ did not converge";
+    case FEAST_EDONE: return "the iteration has already stopped";
+    default: return "unknown status";
+    }
+}
+
+int feast_zgetrf_batched(int64_t n, int batch, void *M, int64_t ld, int64_t stride, int *piv,
+                         int *info, void *stream)
+{
+    if (n < 0 || batch < 0 || ld < n || stride < ld * n || !M || !piv || !info) return FEAST_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    FEAST_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
+    return zgetrf_batched(s, n, batch, (zd *)M, ld, stride, piv, info, nullptr);
+}
+
+int feast_zgetrs_batched(int64_t n, int64_t nrhs, int batch, const void *M, int64_t ld,
+                         int64_t stride, const int *piv, void *X, int64_t ldx, int64_t sx,
+                         void *stream)
+{
+    if (n < 0 || nrhs < 0 || batch < 0 || ld < n || ldx < n || !M || !piv || !X) return FEAST_EINVAL;
+    return zgetrs_batched((cudaStream_t)stream, n, nrhs, batch, (const zd *)M, ld, stride, piv, (zd *)X,
+                          ldx, sx);
+}
+
+int feast_zqz_batched(int m, int batch, void *A, void *B, void *alpha, void *beta, void *V,
+                      void *work, int *status, void *stream)
+{
+    if (m < 0 || batch < 0 || !A || !B || !alpha || !beta || !V || !work || !status) return FEAST_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    FEAST_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    return zqz_batched(s, m, batch, (zd *)A, m, (int64_t)m * m, (zd *)B, m, (int64_t)m * m, (zd *)alpha,
+                       (zd *)beta, (zd *)V, m, (int64_t)m * m, (zd *)work, status);
+}
+
+}  // extern "C"

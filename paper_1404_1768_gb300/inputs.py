@@ -42,6 +42,8 @@ class DensePencil:
     lam: np.ndarray        # prescribed eigenvalues (length n)
     center: complex
     radius: float
+    P: np.ndarray = None   # A = P diag(lam) Q, B = P Q
+    Q: np.ndarray = None
 
     @property
     def n(self) -> int:
@@ -82,7 +84,7 @@ def prescribed_pencil(n: int, m0: int, seed: int = 0, center: complex = 0j, radi
     Q = eye + 0.1 * gq / math.sqrt(n)
     B = np.asfortranarray(P @ Q)
     A = np.asfortranarray((P * lam[None, :]) @ Q)
-    return DensePencil(A=A, B=B, Y=Y, lam=lam, center=center, radius=radius)
+    return DensePencil(A=A, B=B, Y=Y, lam=lam, center=center, radius=radius, P=P, Q=Q)
 
 
 @dataclass
