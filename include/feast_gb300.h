@@ -176,6 +176,38 @@ int feast_set_subspace(feast_ctx *ctx, const void *U1);
 void feast_destroy(feast_ctx *ctx);
 const char *feast_strerror(int status);
 
+/* ---------------------------------------------------------- ragged batch */
+
+/* Per-pencil outcome of feast_solve_batch. */
+typedef struct {
+    int status;      /* FEAST_OK or the first error of this pencil          */
+    int flag;        /* GFEAST flag of lines 13-15                          */
+    int count;       /* eigenpairs returned                                 */
+    int k;           /* passes run                                          */
+    double err;      /* Err of lines 13-15                                  */
+} feast_batch_item;
+
+/* Device workspace for feast_solve_batch with nworkers concurrent pencils
+ * (0 on invalid input). */
+size_t feast_batch_workspace_size(int count, const feast_pencil *pencils,
+                                  const feast_contour *contours, const feast_options *opts,
+                                  int nworkers);
+
+/* Many independent pencils of uneven size, each with its own contour and
+ * options (arrays of count entries; the stream fields are ignored): the
+ * whole GFEAST run (set-up, passes until a stopping test fires, output) for
+ * every pencil.  nworkers host threads each own a CUDA stream and a slice
+ * of the workspace and take pencils in index order, so the kernels of up to
+ * nworkers pencils overlap on the GPU (the node-parallel and right-hand-side
+ * parallel structure noted at the end of Section 4.3, applied across
+ * problems).  Outputs (host): items[count]; lambda: 2 * sum(m0) doubles,
+ * pencil i's eigenvalues (re, im) starting at 2 * sum_{p<i} m0_p; resid
+ * (may be NULL): sum(m0) doubles, same offsets.  Blocks until all pencils
+ * are done; returns FEAST_OK or the first error (see items[i].status). */
+int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contour *contours,
+                      const feast_options *opts, void *workspace, size_t workspace_bytes,
+                      int nworkers, feast_batch_item *items, double *lambda, double *resid);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (host-side counter; every launch site increments it). */
 unsigned long long feast_kernel_launches(void);
@@ -199,13 +231,20 @@ int feast_zgetrs_batched(int64_t n, int64_t nrhs, int batch, const void *M, int6
                          int64_t stride, const int *piv, void *X, int64_t ldx, int64_t sx,
                          void *stream);
 
-/* Batched complex QZ for projected pencils (GFEAST line 6; the paper points
- * to LAPACK xGGES / xGGEV).  A, B: device, batch blocks of m x m (B upper
- * triangular -- its strictly lower part is ignored), overwritten by the
- * generalized Schur form.  alpha, beta: device m per pencil; V: device
- * m x m per pencil, unit-norm right eigenvectors (beta A v = alpha B v).
- * work: device, batch * m * m complex128.  status: device int32[1], number
- * of pencils whose iteration cap was hit.  Asynchronous. */
+/* Batched eigensolve of projected pencils (GFEAST line 6; the paper points
+ * to the LAPACK drivers xGGES / xGGEV).  A, B: device, batch blocks of m x m
+ * complex128 (B upper triangular -- its strictly lower part is ignored --
+ * as the projected B~ = U2^H B U1 = R2 is), both overwritten.  alpha, beta:
+ * device m per pencil, eigenvalue alpha/beta; V: device m x m per pencil,
+ * unit-norm right eigenvectors (beta A v = alpha B v).
+ *   m <= 64: complex QZ (Hessenberg-triangular reduction, single-shift QZ),
+ *            one warp per pencil in shared memory.
+ *   m >  64: B must be nonsingular; C = B^{-1} A is reduced to Hessenberg
+ *            form and QR-iterated by the whole GPU (beta = 1).
+ * work: device, feast_zqz_work_bytes(m, batch) bytes.  status: device
+ * int32[2]: [0] pencils whose iteration cap was hit, [1] non-zero if a
+ * bounded device barrier timed out.  Asynchronous. */
+size_t feast_zqz_work_bytes(int m, int batch);
 int feast_zqz_batched(int m, int batch, void *A, void *B, void *alpha, void *beta, void *V,
                       void *work, int *status, void *stream);
 

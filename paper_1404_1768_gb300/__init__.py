@@ -54,6 +54,11 @@ class Options(C.Structure):
                 ("refine_tol", C.c_double), ("stream", C.c_void_p), ("no_stop", C.c_int)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("status", C.c_int), ("flag", C.c_int), ("count", C.c_int), ("k", C.c_int),
+                ("err", C.c_double)]
+
+
 class IterInfo(C.Structure):
     _fields_ = [("k", C.c_int), ("count", C.c_int), ("flag", C.c_int), ("err", C.c_double),
                 ("ms_lu", C.c_double), ("ms_solve", C.c_double), ("ms_refine", C.c_double),
@@ -71,7 +76,8 @@ _lock = threading.Lock()
 EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs", "feast_get",
            "feast_filter", "feast_set_subspace", "feast_destroy", "feast_strerror",
            "feast_zgetrf_batched", "feast_zgetrs_batched", "feast_zqz_batched",
-           "feast_kernel_launches"]
+           "feast_zqz_work_bytes", "feast_kernel_launches",
+           "feast_batch_workspace_size", "feast_solve_batch"]
 
 
 def lib_path() -> str:
@@ -107,6 +113,13 @@ def load(build_if_missing: bool = True):
         lib.feast_zgetrf_batched.argtypes = [I64, I, P, I64, I64, P, P, P]
         lib.feast_zgetrs_batched.argtypes = [I64, I64, I, P, I64, I64, P, P, I64, I64, P]
         lib.feast_zqz_batched.argtypes = [I, I, P, P, P, P, P, P, P, P]
+        lib.feast_zqz_work_bytes.argtypes = [I, I]
+        lib.feast_zqz_work_bytes.restype = C.c_size_t
+        lib.feast_batch_workspace_size.argtypes = [I, C.POINTER(Pencil), C.POINTER(Contour),
+                                                   C.POINTER(Options), I]
+        lib.feast_batch_workspace_size.restype = C.c_size_t
+        lib.feast_solve_batch.argtypes = [I, C.POINTER(Pencil), C.POINTER(Contour), C.POINTER(Options),
+                                          P, C.c_size_t, I, C.POINTER(BatchItem), P, P]
         lib.feast_kernel_launches.argtypes = []
         lib.feast_kernel_launches.restype = C.c_ulonglong
         _lib = lib
@@ -327,12 +340,69 @@ def zqz_batched(A_list, B_list, stream=None):
     al = torch.zeros(batch * m, dtype=torch.complex128, device="cuda")
     be = torch.zeros_like(al)
     V = torch.zeros(batch * m * m, dtype=torch.complex128, device="cuda")
-    work = torch.zeros_like(V)
-    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    work = torch.zeros(int(lib.feast_zqz_work_bytes(m, batch)), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
     _check(lib.feast_zqz_batched(m, batch, ab.data_ptr(), bb.data_ptr(), al.data_ptr(),
                                  be.data_ptr(), V.data_ptr(), work.data_ptr(), st.data_ptr(),
                                  _stream_ptr(stream)), "feast_zqz_batched")
     torch.cuda.current_stream().synchronize()
     Vs = [from_device_colmajor(V[b * m * m:(b + 1) * m * m], m, m) for b in range(batch)]
+    stv = st.cpu().numpy()
+    if stv[1]:
+        raise FeastError(-6, "feast_zqz_batched")
     return (al.cpu().numpy().reshape(batch, m), be.cpu().numpy().reshape(batch, m), Vs,
-            int(st.item()))
+            int(stv[0]))
+
+
+def solve_batch(problems, nworkers: int = 16, device="cuda"):
+    """Run GFEAST on many independent dense pencils at once (uneven sizes).
+
+    problems: list of dicts with keys A, B, Y (numpy, rows x cols) and the
+    contour / tolerance keywords of Feast (contour_kind, rule, q, center, a,
+    b, eps, eta, max_iter, prec, refine_tol, max_refine).  Returns a list of
+    dicts (status, flag, count, k, err, lam, res)."""
+    torch = _torch()
+    lib = load()
+    cnt = len(problems)
+    keep = []
+    P = (Pencil * cnt)()
+    Cn = (Contour * cnt)()
+    O = (Options * cnt)()
+    for i, pr in enumerate(problems):
+        A = to_device_colmajor(pr["A"], device)
+        B = to_device_colmajor(pr["B"], device)
+        Y = to_device_colmajor(pr["Y"], device)
+        keep += [A, B, Y]
+        n, m0 = np.asarray(pr["Y"]).shape
+        P[i] = Pencil(0, n, A.data_ptr(), B.data_ptr(), n, 0, 0, 0)
+        ck = pr.get("contour_kind", 0)
+        ctr = complex(pr.get("center", 0j))
+        a = float(pr.get("a", 1.0))
+        Cn[i] = Contour(ck, ctr.real, ctr.imag, a, float(pr.get("b", a)), int(pr.get("q", 16)),
+                        int(pr.get("rule", 0)))
+        O[i] = Options(m0, Y.data_ptr(), float(pr.get("eps", 1e-12)), float(pr.get("eta", 1e-3)),
+                       int(pr.get("max_iter", 50)), int(pr.get("prec", 0)),
+                       int(pr.get("max_refine", 5)), float(pr.get("refine_tol", 1e-14)), None, 0)
+    nbytes = int(lib.feast_batch_workspace_size(cnt, P, Cn, O, nworkers))
+    if nbytes == 0:
+        raise FeastError(-1, "feast_batch_workspace_size")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    items = (BatchItem * cnt)()
+    m0s = [int(o.m0) for o in O]
+    off = np.concatenate([[0], np.cumsum(m0s)]).astype(int)
+    lam = np.zeros(2 * off[-1])
+    res = np.zeros(off[-1])
+    torch.cuda.synchronize()
+    st = lib.feast_solve_batch(cnt, P, Cn, O, ws.data_ptr(), nbytes, nworkers, items,
+                               lam.ctypes.data, res.ctypes.data)
+    out = []
+    for i in range(cnt):
+        it = items[i]
+        c = it.count
+        l = lam[2 * off[i]:2 * off[i] + 2 * c]
+        out.append(dict(status=it.status, flag=it.flag, count=c, k=it.k, err=it.err,
+                        lam=l[0::2] + 1j * l[1::2], res=res[off[i]:off[i] + c].copy()))
+    if st != 0:
+        bad = [i for i, o in enumerate(out) if o["status"] != 0]
+        raise FeastError(st, f"feast_solve_batch (pencils {bad[:8]})")
+    return out

@@ -54,6 +54,56 @@ __host__ __device__ __forceinline__ zd zdiv(zd a, zd b)
     }
 }
 
+// ---------------------------------------------------------------- complex FP32
+typedef float2 cf;
+__host__ __device__ __forceinline__ cf cmakef(float r, float i) { return make_float2(r, i); }
+
+// Overloads shared by the templated kernels (T = double2 or float2).
+template <typename T> struct CxReal;
+template <> struct CxReal<double2> { typedef double type; };
+template <> struct CxReal<float2> { typedef float type; };
+template <typename T> __host__ __device__ __forceinline__ T cx(typename CxReal<T>::type r, typename CxReal<T>::type i)
+{
+    T v;
+    v.x = r;
+    v.y = i;
+    return v;
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return zadd(a, b); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return zmul(a, b); }
+__host__ __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return zconj(a); }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return zabs2(a); }
+__host__ __device__ __forceinline__ void cfma(float2 &c, float2 a, float2 b)
+{
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(a.y, b.x, c.y);
+}
+__host__ __device__ __forceinline__ void cfma(double2 &c, double2 a, double2 b) { zfma(c, a, b); }
+__host__ __device__ __forceinline__ float2 cdiv(float2 a, float2 b)
+{
+    if (fabsf(b.x) >= fabsf(b.y)) {
+        float r = b.y / b.x, d = b.x + b.y * r;
+        return make_float2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        float r = b.x / b.y, d = b.x * r + b.y;
+        return make_float2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) { return zdiv(a, b); }
+__host__ __device__ __forceinline__ bool cis_zero(float2 a) { return a.x == 0.f && a.y == 0.f; }
+__host__ __device__ __forceinline__ bool cis_zero(double2 a) { return a.x == 0.0 && a.y == 0.0; }
+
 // ---------------------------------------------------------------- status
 // Per-context device-side status written by kernels (pivot failures,
 // non-finite values) and read by the host at the one sync point per pass.
@@ -65,7 +115,8 @@ struct DevStatus {
     double err;         // e(k)
     int flag;           // 2 continue, 1 / 0 / -1 stopping criteria
     int qz_fail;        // pencils whose QZ iteration hit its iteration cap
-    int pad[2];
+    int timeout;        // a bounded grid barrier gave up
+    int pad;
 };
 
 #define FEAST_CUDA_TRY(expr)                                                         \
@@ -87,6 +138,28 @@ void count_launch();
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------- kernels (FP64)
+// Templated dense kernels (T = double2 or float2), instantiated in k_dense.cu.
+template <typename T>
+int gemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, T alpha,
+                 const T *A, int64_t lda, int64_t sA, const T *B, int64_t ldb, int64_t sB,
+                 T beta, T *C, int64_t ldc, int64_t sC, int batch);
+template <typename T>
+int getrf_batched(cudaStream_t s, int64_t n, int batch, T *F, int64_t ldf, int64_t sF, int *piv,
+                  int *info, int *row);
+template <typename T>
+int getrf_panel(cudaStream_t s, int64_t rows, int nb, int batch, T *F, int64_t ldf, int64_t sF,
+                int *piv, int64_t pstride, int *info, int *row);
+template <typename T>
+int trsm_lu_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const T *F, int64_t ldf,
+                    int64_t sF, T *X, int64_t ldx, int64_t sX);
+template <typename T>
+int trsm_upper_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const T *F, int64_t ldf,
+                       int64_t sF, T *X, int64_t ldx, int64_t sX);
+// X_b[i, :] = R_b[perm_b[i], :]   (sR = 0 shares one right-hand side)
+template <typename T>
+int gather_rows(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const int *perm, const T *R,
+                int64_t ldr, int64_t sR, T *X, int64_t ldx, int64_t sX);
+
 // Batched complex GEMM:  C_b = alpha * op(A_b) * B_b + beta * C_b, b = 0..batch-1,
 // op(A) = A (conj_a = 0) or A^H (conj_a = 1).  op(A) is m x k, B k x n.
 // Strides are in elements between consecutive batch members.
@@ -120,12 +193,22 @@ int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64
           zd *work);
 size_t zorth_work_elems(int64_t n, int64_t m);
 
-// Batched complex QZ (one pencil per CTA): A -> S, B -> P (B upper
-// triangular on entry), Zv -> right eigenvectors (unit 2-norm),
-// alpha / beta eigenvalue pairs.  work: 1 m x m block per pencil.
+// Batched projected eigensolve: alpha / beta eigenvalue pairs and unit right
+// eigenvectors V of (A, B), B upper triangular.  m <= 64: QZ, one warp per
+// pencil (A, B overwritten by the Schur form); m > 64: standard-form path
+// of k_zeig.cu, pencil by pencil (A, B overwritten).  work: batch *
+// zqz_work_bytes(m) bytes.  timeout (may be null): set if a grid barrier
+// of the large path gave up.
+size_t zqz_work_bytes(int m);
 int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA, zd *B,
                 int64_t ldb, int64_t sB, zd *alpha, zd *beta, zd *V, int64_t ldv, int64_t sV,
-                zd *work, int *fail);
+                void *work, int *fail, int *timeout);
+
+// Large projected problems (k_zeig.cu): standard form, Hessenberg
+// reduction and chunked QR; alpha = eigenvalue, beta = 1.
+size_t zeig_large_work_bytes(int m);
+int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
+               int *fail, int *timeout);
 
 // Composition of the LU interchanges: perm[b*n + i] = original row at i.
 int zpiv_to_perm(cudaStream_t s, int64_t n, int batch, const int *piv, int *perm);
@@ -147,6 +230,37 @@ int stop_test(cudaStream_t s, int m, const feast_contour *c, const zd *lam, cons
 int compact_pairs(cudaStream_t s, int64_t n, int m, const int *idx, const DevStatus *st,
                   const zd *X, int64_t ldx, const zd *lam, const double *res, zd *Xc, zd *lamc,
                   double *resc);
+
+// Precision form (k_refine.cu).
+int form_shifted_split(cudaStream_t s, int64_t n, int q, const zd *A, const zd *B, int64_t ld,
+                       const zd *z, cf *M32, cf *Mhi, cf *Mlo);
+int split_hilo(cudaStream_t s, int64_t count, const zd *x, cf *hi, cf *lo);
+int z2c(cudaStream_t s, int64_t count, const zd *x, cf *y);
+int c2z(cudaStream_t s, int64_t count, const cf *x, zd *y);
+int add_c32(cudaStream_t s, int64_t count, zd *x, const cf *c);
+// R_j = RHS - M_j X_j (double-single), nrm2[j] = ||R_j||_F^2
+int ds_residual(cudaStream_t s, int64_t n, int64_t m, int q, const cf *Mhi, const cf *Mlo,
+                const cf *Xhi, const cf *Xlo, const zd *RHS, zd *R, double *nrm2);
+int sumsq(cudaStream_t s, int64_t count, const zd *x, double *out);
+
+// Banded pencils (k_band.cu): LAPACK general-band factor storage
+// (ldab = 2 kl + ku + 1), unblocked-convention multipliers.
+size_t gb_scratch_elems(int64_t kl, int64_t ku, int q);
+size_t gb_piv_scratch(int64_t kl, int q);
+template <typename T>
+int gb_form(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *A, const zd *B,
+            int64_t ldin, int q, const zd *z, T *F);
+template <typename T>
+int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int *piv, void *scratch,
+             int *pivl, int *info, int *row);
+template <typename T>
+int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *F, const int *piv,
+             int64_t nrhs, T *X, int64_t ldx, int64_t sX);
+int gb_matmul(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *M, int64_t ldin, int64_t m,
+              const zd *X, zd *Y);
+int gb_residual(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *A, const zd *B,
+                int64_t ldin, int q, const zd *z, int64_t m, const zd *RHS, const zd *X, zd *R,
+                double *nrm2);
 
 // Contour nodes / weights on the device.
 int contour_nodes(cudaStream_t s, const feast_contour *c, zd *z, zd *w);

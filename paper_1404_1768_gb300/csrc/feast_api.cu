@@ -9,6 +9,8 @@
 #include <atomic>
 #include <stdlib.h>
 #include <string.h>
+#include <thread>
+#include <vector>
 
 #include "common.cuh"
 
@@ -51,8 +53,27 @@ struct feast_ctx {
     zd *Xo, *lamo;
     double *reso;
     zd *tmp;            // n x m0
-    zd *orth_work, *qz_work;
+    zd *orth_work;
+    void *qz_work;
     DevStatus *st;
+    // precision form
+    cf *F32;            // q x n x n complex64 factors
+    cf *Mhi, *Mlo;      // q x n x n double-single split of z_j B - A
+    cf *Xhi, *Xlo;      // q x n x m0 split of the solutions (Xhi doubles as R32)
+    cf *C32;            // q x n x m0 low-precision solves / corrections
+    zd *R64;            // q x n x m0 residuals
+    double *nrm2;       // q + 1 squared norms
+    int max_refine;
+    double refine_tol;
+    // banded pencils
+    int64_t ldin, ldab;  // compact input / factor storage leading dims
+    zd *Fb;             // q x ldab x n complex128 band factors (FP64)
+    cf *Fb32;           // q x ldab x n complex64 band factors (precision form)
+    void *gb_scratch;
+    int *gb_pivl;
+    int last_sweeps;
+    double last_rel;
+    float ms_refine;
     // host state
     int k, c_prev, done, cur;
     double e_prev;
@@ -81,9 +102,13 @@ int validate(const feast_pencil *p, const feast_contour *c, const feast_options 
 {
     if (!p || !c || !o) return FEAST_EINVAL;
     if (p->n < 1 || o->m0 < 1 || o->m0 > p->n || c->q < 1 || c->q > 4096) return FEAST_EINVAL;
-    if (p->kind != FEAST_DENSE) return FEAST_EINVAL;       // banded path: not in this build
-    if (o->prec != FEAST_FP64) return FEAST_EINVAL;        // precision form: not in this build
-    if (p->ld < p->n) return FEAST_EINVAL;
+    if (p->kind != FEAST_DENSE && p->kind != FEAST_BANDED) return FEAST_EINVAL;
+    if (p->kind == FEAST_BANDED && (p->kl < 0 || p->ku < 0 || p->kl >= p->n || p->ku >= p->n ||
+                                    p->ld < p->kl + p->ku + 1 || p->kl > 4096 || p->ku > 4096))
+        return FEAST_EINVAL;
+    if (o->prec != FEAST_FP64 && o->prec != FEAST_C64_REFINE) return FEAST_EINVAL;
+    if (o->prec == FEAST_C64_REFINE && (o->max_refine < 0 || !(o->refine_tol > 0.0))) return FEAST_EINVAL;
+    if (p->kind == FEAST_DENSE && p->ld < p->n) return FEAST_EINVAL;
     if (!(c->a > 0.0) || (c->kind == FEAST_ELLIPSE && !(c->b > 0.0))) return FEAST_EINVAL;
     if (c->kind != FEAST_CIRCLE && c->kind != FEAST_ELLIPSE) return FEAST_EINVAL;
     if (c->rule != FEAST_TRAPEZOID && c->rule != FEAST_GAUSS_LEGENDRE) return FEAST_EINVAL;
@@ -95,11 +120,36 @@ int validate(const feast_pencil *p, const feast_contour *c, const feast_options 
 void carve(feast_ctx *c, Carver &cv)
 {
     const size_t n = (size_t)c->n, m = (size_t)c->m0, q = (size_t)c->q;
-    c->A = cv.take<zd>(n * n);
-    c->B = c->b_identity ? nullptr : cv.take<zd>(n * n);
+    const size_t asz = (c->kind == FEAST_DENSE) ? n * n : (size_t)c->ldin * n;
+    c->A = cv.take<zd>(asz);
+    c->B = c->b_identity ? nullptr : cv.take<zd>(asz);
     c->z = cv.take<zd>(q);
     c->w = cv.take<zd>(q);
-    c->F = cv.take<zd>(q * n * n);
+    if (c->kind == FEAST_BANDED) {
+        const size_t fsz = q * (size_t)c->ldab * n;
+        if (c->prec == FEAST_FP64) {
+            c->Fb = cv.take<zd>(fsz);
+            c->gb_scratch = cv.take<zd>(gb_scratch_elems(c->kl, c->ku, (int)q));
+        } else {
+            c->Fb32 = cv.take<cf>(fsz);
+            c->gb_scratch = cv.take<cf>(gb_scratch_elems(c->kl, c->ku, (int)q));
+            c->C32 = cv.take<cf>(q * n * m);
+            c->R64 = cv.take<zd>(q * n * m);
+            c->nrm2 = cv.take<double>(q + 1);
+        }
+        c->gb_pivl = cv.take<int>(gb_piv_scratch(c->kl, (int)q));
+    } else if (c->prec == FEAST_FP64) {
+        c->F = cv.take<zd>(q * n * n);
+    } else {
+        c->F32 = cv.take<cf>(q * n * n);
+        c->Mhi = cv.take<cf>(q * n * n);
+        c->Mlo = cv.take<cf>(q * n * n);
+        c->Xhi = cv.take<cf>(q * n * m);
+        c->Xlo = cv.take<cf>(q * n * m);
+        c->C32 = cv.take<cf>(q * n * m);
+        c->R64 = cv.take<zd>(q * n * m);
+        c->nrm2 = cv.take<double>(q + 1);
+    }
     c->piv = cv.take<int>(q * n);
     c->perm = cv.take<int>(q * n);
     c->Xs = cv.take<zd>(q * n * m);
@@ -130,7 +180,7 @@ void carve(feast_ctx *c, Carver &cv)
     c->reso = cv.take<double>(m);
     c->tmp = cv.take<zd>(n * m);
     c->orth_work = cv.take<zd>(zorth_work_elems((int64_t)n, (int64_t)m));
-    c->qz_work = cv.take<zd>(m * m);
+    c->qz_work = cv.take<char>(zqz_work_bytes((int)m));
     c->st = cv.take<DevStatus>(1);
 }
 
@@ -139,8 +189,10 @@ void fill_ctx_params(feast_ctx *c, const feast_pencil *p, const feast_contour *c
 {
     c->kind = p->kind;
     c->n = p->n;
-    c->kl = p->kl;
-    c->ku = p->ku;
+    c->kl = p->kind == FEAST_BANDED ? p->kl : 0;
+    c->ku = p->kind == FEAST_BANDED ? p->ku : 0;
+    c->ldin = c->kl + c->ku + 1;
+    c->ldab = 2 * c->kl + c->ku + 1;
     c->b_identity = p->b_is_identity ? 1 : 0;
     c->q = ct->q;
     c->m0 = o->m0;
@@ -152,9 +204,18 @@ void fill_ctx_params(feast_ctx *c, const feast_pencil *p, const feast_contour *c
     c->prec = o->prec;
     c->no_stop = o->no_stop;
     c->s = (cudaStream_t)o->stream;
+    c->max_refine = o->max_refine;
+    c->refine_tol = o->refine_tol;
 }
 
-const zd kOne = {1.0, 0.0}, kZero = {0.0, 0.0}, kMone = {-1.0, 0.0};
+const zd kOne = {1.0, 0.0}, kZero = {0.0, 0.0};
+
+float ev_ms(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+    return ms;
+}
 
 // Y = B X (copy when B = I).  X, Y: n x m, leading dim n.
 int apply_B(feast_ctx *c, const zd *X, zd *Y, int64_t m)
@@ -164,17 +225,137 @@ int apply_B(feast_ctx *c, const zd *X, zd *Y, int64_t m)
         FEAST_CUDA_TRY(cudaMemcpyAsync(Y, X, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
         return FEAST_OK;
     }
+    if (c->kind == FEAST_BANDED) return gb_matmul(c->s, n, c->kl, c->ku, c->B, c->ldin, m, X, Y);
     return zgemm_batched(c->s, 0, n, m, n, kOne, c->B, n, 0, X, n, 0, kZero, Y, n, 0, 1);
 }
 
-// U = sum_j w_j (z_j B - A)^{-1} B V   (eq. 4.1 - 4.2)
-int filter(feast_ctx *c, const zd *V, zd *Uout)
+// Y = A X.
+int apply_A(feast_ctx *c, const zd *X, zd *Y, int64_t m)
+{
+    const int64_t n = c->n;
+    if (c->kind == FEAST_BANDED) return gb_matmul(c->s, n, c->kl, c->ku, c->A, c->ldin, m, X, Y);
+    return zgemm_batched(c->s, 0, n, m, n, kOne, c->A, n, 0, X, n, 0, kZero, Y, n, 0, 1);
+}
+
+// X_j = RHS for every node (right-hand side shared by the band solves).
+template <typename T>
+int broadcast_rhs(feast_ctx *c, const T *rhs, T *X)
+{
+    const int64_t nm = c->n * c->m0;
+    for (int j = 0; j < c->q; ++j)
+        FEAST_CUDA_TRY(cudaMemcpyAsync(X + (int64_t)j * nm, rhs, sizeof(T) * nm, cudaMemcpyDeviceToDevice, c->s));
+    return FEAST_OK;
+}
+
+// Shifted solves for banded pencils: X_j = (z_j B - A)^{-1} BV in FP64, or
+// in complex64 with FP64-residual refinement (the band residual is cheap:
+// 2 kl + ku + 1 products per entry).
+int solve_band(feast_ctx *c, const zd *BV, double tol)
+{
+    const int64_t n = c->n, m = c->m0, q = c->q, nm = n * m, all = q * nm;
+    cudaStream_t s = c->s;
+    int e;
+    if (c->prec == FEAST_FP64) {
+        if ((e = broadcast_rhs<zd>(c, BV, c->Xs))) return e;
+        return gb_solve<zd>(s, n, c->kl, c->ku, (int)q, c->Fb, c->piv, m, c->Xs, n, nm);
+    }
+    cf *rhs32 = c->C32;  // node 0's slot doubles as the rounded right-hand side
+    if ((e = z2c(s, nm, BV, rhs32))) return e;
+    for (int j = 1; j < q; ++j)
+        FEAST_CUDA_TRY(cudaMemcpyAsync(c->C32 + j * nm, rhs32, sizeof(cf) * nm, cudaMemcpyDeviceToDevice, s));
+    if ((e = gb_solve<cf>(s, n, c->kl, c->ku, (int)q, c->Fb32, c->piv, m, c->C32, n, nm))) return e;
+    if ((e = c2z(s, all, c->C32, c->Xs))) return e;
+    c->last_sweeps = 0;
+    c->last_rel = -1.0;
+    c->ms_refine = 0.f;
+    if (tol > 1e-6 || c->max_refine == 0) return FEAST_OK;
+    cudaEvent_t e0 = c->ev[6], e1 = c->ev[7];
+    FEAST_CUDA_TRY(cudaEventRecord(e0, s));
+    if ((e = sumsq(s, nm, BV, c->nrm2 + q))) return e;
+    double h[4096 + 1];
+    for (int sweep = 0; sweep <= c->max_refine; ++sweep) {
+        if ((e = gb_residual(s, n, c->kl, c->ku, c->A, c->B, c->ldin, (int)q, c->z, m, BV, c->Xs, c->R64,
+                             c->nrm2))) return e;
+        FEAST_CUDA_TRY(cudaMemcpyAsync(h, c->nrm2, sizeof(double) * (q + 1), cudaMemcpyDeviceToHost, s));
+        FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+        double worst = 0.0;
+        for (int j = 0; j < q; ++j) worst = h[j] > worst ? h[j] : worst;
+        const double rel = h[q] > 0.0 ? sqrt(worst / h[q]) : 0.0;
+        c->last_rel = rel;
+        if (!(rel > tol) || sweep == c->max_refine) break;
+        if ((e = z2c(s, all, c->R64, c->C32))) return e;
+        if ((e = gb_solve<cf>(s, n, c->kl, c->ku, (int)q, c->Fb32, c->piv, m, c->C32, n, nm))) return e;
+        if ((e = add_c32(s, all, c->Xs, c->C32))) return e;
+        c->last_sweeps = sweep + 1;
+    }
+    FEAST_CUDA_TRY(cudaEventRecord(e1, s));
+    FEAST_CUDA_TRY(cudaEventSynchronize(e1));
+    c->ms_refine = ev_ms(e0, e1);
+    return FEAST_OK;
+}
+
+// Shifted solves of the precision form: complex64 LU solves, then
+// refinement sweeps X_j += M32_j^{-1} (R_j) with R_j = B V - M_j X_j in
+// double-single until max_j ||R_j||_F / ||B V||_F <= tol (or max_refine
+// sweeps).  tol > 1e-6 (looser than what one complex64 solve reaches)
+// skips the residual altogether.  Result: X_j (FP64) in c->Xs.
+int solve_refine(feast_ctx *c, const zd *BV, double tol)
+{
+    const int64_t n = c->n, m = c->m0, q = c->q;
+    const int64_t nm = n * m, all = q * nm;
+    cudaStream_t s = c->s;
+    int e;
+    cf *rhs32 = c->Xlo;  // n x m scratch before the split is needed
+    if ((e = z2c(s, nm, BV, rhs32))) return e;
+    if ((e = gather_rows<cf>(s, n, m, (int)q, c->perm, rhs32, n, 0, c->C32, n, nm))) return e;
+    if ((e = trsm_lu_batched<cf>(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm))) return e;
+    if ((e = c2z(s, all, c->C32, c->Xs))) return e;
+    c->last_sweeps = 0;
+    c->last_rel = -1.0;
+    c->ms_refine = 0.f;
+    if (tol > 1e-6 || c->max_refine == 0) return FEAST_OK;
+    cudaEvent_t e0 = c->ev[6], e1 = c->ev[7];
+    FEAST_CUDA_TRY(cudaEventRecord(e0, s));
+    if ((e = sumsq(s, nm, BV, c->nrm2 + q))) return e;
+    double h[4096 + 1];
+    for (int sweep = 0; sweep <= c->max_refine; ++sweep) {
+        if ((e = split_hilo(s, all, c->Xs, c->Xhi, c->Xlo))) return e;
+        if ((e = ds_residual(s, n, m, (int)q, c->Mhi, c->Mlo, c->Xhi, c->Xlo, BV, c->R64, c->nrm2))) return e;
+        FEAST_CUDA_TRY(cudaMemcpyAsync(h, c->nrm2, sizeof(double) * (q + 1), cudaMemcpyDeviceToHost, s));
+        FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+        double worst = 0.0;
+        for (int j = 0; j < q; ++j) worst = h[j] > worst ? h[j] : worst;
+        const double rel = h[q] > 0.0 ? sqrt(worst / h[q]) : 0.0;
+        c->last_rel = rel;
+        if (!(rel > tol) || sweep == c->max_refine) break;  // also stops on NaN
+        // correction: C_j = M32_j^{-1} R_j, X_j += C_j
+        if ((e = z2c(s, all, c->R64, c->Xhi))) return e;
+        if ((e = gather_rows<cf>(s, n, m, (int)q, c->perm, c->Xhi, n, nm, c->C32, n, nm))) return e;
+        if ((e = trsm_lu_batched<cf>(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm))) return e;
+        if ((e = add_c32(s, all, c->Xs, c->C32))) return e;
+        c->last_sweeps = sweep + 1;
+    }
+    FEAST_CUDA_TRY(cudaEventRecord(e1, s));
+    FEAST_CUDA_TRY(cudaEventSynchronize(e1));
+    c->ms_refine = ev_ms(e0, e1);
+    return FEAST_OK;
+}
+
+// U = sum_j w_j (z_j B - A)^{-1} B V   (eq. 4.1 - 4.2).  tol applies to the
+// precision form only.
+int filter(feast_ctx *c, const zd *V, zd *Uout, double tol)
 {
     const int64_t n = c->n, m = c->m0;
     int e;
     if ((e = apply_B(c, V, c->tmp, m))) return e;
-    if ((e = zgather_rows(c->s, n, m, c->q, c->perm, c->tmp, n, c->Xs, n, n * m))) return e;
-    if ((e = ztrsm_lu_batched(c->s, n, m, c->q, c->F, n, n * n, c->Xs, n, n * m))) return e;
+    if (c->kind == FEAST_BANDED) {
+        if ((e = solve_band(c, c->tmp, tol))) return e;
+    } else if (c->prec == FEAST_FP64) {
+        if ((e = zgather_rows(c->s, n, m, c->q, c->perm, c->tmp, n, c->Xs, n, n * m))) return e;
+        if ((e = ztrsm_lu_batched(c->s, n, m, c->q, c->F, n, n * n, c->Xs, n, n * m))) return e;
+    } else {
+        if ((e = solve_refine(c, c->tmp, tol))) return e;
+    }
     return znode_sum(c->s, n, m, c->q, c->w, c->Xs, n, n * m, Uout, n);
 }
 
@@ -190,13 +371,6 @@ int orthonormalise(feast_ctx *c, const zd *Usrc)
     if ((e = apply_B(c, c->U1, BU1, m))) return e;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
     return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work);
-}
-
-float ev_ms(cudaEvent_t a, cudaEvent_t b)
-{
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
-    return ms;
 }
 
 }  // namespace
@@ -242,20 +416,36 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
 #define TRY(x) do { int _r = (x); if (_r) { feast_destroy(c); return _r; } } while (0)
 #define CTRY(x) do { if ((x) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; } } while (0)
     CTRY(cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
-    CTRY(cudaMemcpy2DAsync(c->A, n * sizeof(zd), pencil->A, pencil->ld * sizeof(zd), n * sizeof(zd), n,
+    const int64_t rowsA = (c->kind == FEAST_DENSE) ? n : c->ldin;
+    CTRY(cudaMemcpy2DAsync(c->A, rowsA * sizeof(zd), pencil->A, pencil->ld * sizeof(zd), rowsA * sizeof(zd), n,
                            cudaMemcpyDeviceToDevice, s));
     if (!c->b_identity)
-        CTRY(cudaMemcpy2DAsync(c->B, n * sizeof(zd), pencil->B, pencil->ld * sizeof(zd), n * sizeof(zd), n,
+        CTRY(cudaMemcpy2DAsync(c->B, rowsA * sizeof(zd), pencil->B, pencil->ld * sizeof(zd), rowsA * sizeof(zd), n,
                                cudaMemcpyDeviceToDevice, s));
     CTRY(cudaEventRecord(c->ev[0], s));
     TRY(contour_nodes(s, &c->contour, c->z, c->w));
     // z_j B - A and its LU factors (factored once, reused every pass)
-    TRY(zform_shifted(s, n, c->q, c->A, c->B, n, c->z, c->F, n, n * n));
-    TRY(zgetrf_batched(s, n, c->q, c->F, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row));
-    TRY(zpiv_to_perm(s, n, c->q, c->piv, c->perm));
+    if (c->kind == FEAST_BANDED) {
+        if (c->prec == FEAST_FP64) {
+            TRY(gb_form<zd>(s, n, c->kl, c->ku, c->A, c->B, c->ldin, c->q, c->z, c->Fb));
+            TRY(gb_getrf<zd>(s, n, c->kl, c->ku, c->q, c->Fb, c->piv, c->gb_scratch, c->gb_pivl,
+                             &c->st->lu_info, &c->st->lu_row));
+        } else {
+            TRY(gb_form<cf>(s, n, c->kl, c->ku, c->A, c->B, c->ldin, c->q, c->z, c->Fb32));
+            TRY(gb_getrf<cf>(s, n, c->kl, c->ku, c->q, c->Fb32, c->piv, c->gb_scratch, c->gb_pivl,
+                             &c->st->lu_info, &c->st->lu_row));
+        }
+    } else if (c->prec == FEAST_FP64) {
+        TRY(zform_shifted(s, n, c->q, c->A, c->B, n, c->z, c->F, n, n * n));
+        TRY(zgetrf_batched(s, n, c->q, c->F, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row));
+    } else {
+        TRY(form_shifted_split(s, n, c->q, c->A, c->B, n, c->z, c->F32, c->Mhi, c->Mlo));
+        TRY(getrf_batched<cf>(s, n, c->q, c->F32, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row));
+    }
+    if (c->kind == FEAST_DENSE) TRY(zpiv_to_perm(s, n, c->q, c->piv, c->perm));
     CTRY(cudaEventRecord(c->ev[1], s));
     // first subspace U = Q Y0, then U1, U2
-    TRY(filter(c, (const zd *)opts->Y0, c->U));
+    TRY(filter(c, (const zd *)opts->Y0, c->U, 1.0));
     TRY(orthonormalise(c, c->U));
     CTRY(cudaEventRecord(c->ev[2], s));
     DevStatus hs;
@@ -293,13 +483,13 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     c->k += 1;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[0], s));
     // line 5: [A~ | B~] = U2^H [A U1 | B U1]; B U1 is already in W[:, m0:]
-    if ((e = zgemm_batched(s, 0, n, m, n, kOne, c->A, n, 0, c->U1, n, 0, kZero, c->W, n, 0, 1))) return e;
+    if ((e = apply_A(c, c->U1, c->W, m))) return e;
     if ((e = zgemm_batched(s, 1, m, 2 * m, n, kOne, c->U2, n, 0, c->W, n, 0, kZero, c->P, m, 0, 1))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[1], s));
     // line 6: projected eigenpairs, x_i = U1 y_i
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
     if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
-                         c->qz_work, &c->st->qz_fail))) return e;
+                         c->qz_work, &c->st->qz_fail, &c->st->timeout))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[2], s));
     if ((e = zgemm_batched(s, 0, n, m, m, kOne, c->U1, n, 0, c->Yv, m, 0, kZero, c->Xr, n, 0, 1))) return e;
     // A x_i = (A U1) y_i, B x_i = (B U1) y_i
@@ -314,13 +504,18 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     // lines 16-17, issued before the flag is read back so that the whole pass
     // is one stream-ordered sequence; when a stop fires the new subspace is
     // simply not used (the stopped pairs were compacted above).
-    if ((e = filter(c, c->U1, c->U))) return e;
+    // refinement target of this pass: tied to the accuracy already reached
+    // (no pair accepted yet -> the plain low-precision solve suffices)
+    double tol = 1.0;
+    if (c->c_prev > 0 && c->e_prev > 0.0) tol = fmax(c->refine_tol, 1e-3 * c->e_prev);
+    if ((e = filter(c, c->U1, c->U, tol))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[4], s));
     if ((e = orthonormalise(c, c->U))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[5], s));
     DevStatus hs;
     FEAST_CUDA_TRY(cudaMemcpyAsync(&hs, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs.timeout) return FEAST_ETIMEOUT;
     if (hs.nonfinite) return FEAST_ENONFINITE;
     if (hs.qz_fail) return FEAST_ENOCONV;
     if (hs.flag != 2 && !c->done) {
@@ -348,6 +543,8 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
         info->ms_qz = ev_ms(c->ev[1], c->ev[2]);
         info->ms_solve = ev_ms(c->ev[3], c->ev[4]);
         info->ms_qr = ev_ms(c->ev[4], c->ev[5]);
+        info->ms_refine = c->prec == FEAST_FP64 ? 0.0 : c->ms_refine;
+        info->refine_sweeps_max = c->prec == FEAST_FP64 ? 0 : c->last_sweeps;
     }
     return FEAST_OK;
 }
@@ -405,7 +602,7 @@ int feast_get(const feast_ctx *c, int what, void *dst)
 int feast_filter(feast_ctx *c, const void *V, void *U)
 {
     if (!c || !V || !U) return FEAST_EINVAL;
-    return filter(c, (const zd *)V, (zd *)U);
+    return filter(c, (const zd *)V, (zd *)U, c->refine_tol);
 }
 
 int feast_set_subspace(feast_ctx *c, const void *U1)
@@ -426,6 +623,89 @@ void feast_destroy(feast_ctx *c)
     for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     free(c);
+}
+
+// ------------------------------------------------------------ ragged batch
+// Many independent pencils (uneven n, m0, contours) solved concurrently:
+// nworkers host threads, each with its own CUDA stream and its own slice of
+// the workspace, take pencils from a shared counter and run set-up and the
+// whole GFEAST loop on them.  The kernels of different pencils overlap on
+// the GPU; per pencil the sequence of launches is the single-pencil one.
+size_t feast_batch_workspace_size(int count, const feast_pencil *pencils,
+                                  const feast_contour *contours, const feast_options *opts,
+                                  int nworkers)
+{
+    if (count <= 0 || !pencils || !contours || !opts || nworkers <= 0) return 0;
+    size_t mx = 0;
+    for (int i = 0; i < count; ++i) {
+        size_t b = 0;
+        if (feast_workspace_size(pencils + i, contours + i, opts + i, &b) != FEAST_OK) return 0;
+        mx = b > mx ? b : mx;
+    }
+    mx = (mx + 255) & ~(size_t)255;
+    const int w = nworkers < count ? nworkers : count;
+    return mx * (size_t)w;
+}
+
+int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contour *contours,
+                      const feast_options *opts, void *workspace, size_t workspace_bytes,
+                      int nworkers, feast_batch_item *items, double *lambda, double *resid)
+{
+    if (count <= 0 || !pencils || !contours || !opts || !workspace || !items || !lambda || nworkers <= 0)
+        return FEAST_EINVAL;
+    const size_t need = feast_batch_workspace_size(count, pencils, contours, opts, nworkers);
+    if (need == 0) return FEAST_EINVAL;
+    if (workspace_bytes < need || ((uintptr_t)workspace & 255u)) return FEAST_ENOMEM;
+    const int w = nworkers < count ? nworkers : count;
+    const size_t slice = need / (size_t)w;
+    std::vector<size_t> off((size_t)count + 1, 0);
+    for (int i = 0; i < count; ++i) off[i + 1] = off[i] + (size_t)opts[i].m0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FEAST_ECUDA;
+    std::atomic<int> next{0};
+    std::atomic<int> worst{FEAST_OK};
+    auto worker = [&](int wid) {
+        if (cudaSetDevice(dev) != cudaSuccess) { worst = FEAST_ECUDA; return; }
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { worst = FEAST_ECUDA; return; }
+        void *ws = (char *)workspace + slice * (size_t)wid;
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= count) break;
+            feast_batch_item &it = items[i];
+            memset(&it, 0, sizeof(it));
+            feast_options o = opts[i];
+            o.stream = st;
+            o.no_stop = 0;
+            feast_ctx *ctx = nullptr;
+            int e = feast_setup(&ctx, pencils + i, contours + i, &o, ws, slice, nullptr);
+            feast_iter_info info;
+            memset(&info, 0, sizeof(info));
+            while (e == FEAST_OK) {
+                e = feast_iterate(ctx, &info);
+                if (e == FEAST_OK && info.flag != 2) break;
+            }
+            if (e == FEAST_OK) {
+                int cnt = 0, flag = 0;
+                double err = 0.0;
+                e = feast_eigs(ctx, &cnt, lambda + 2 * off[i], nullptr, pencils[i].n,
+                               resid ? resid + off[i] : nullptr, &err, &flag);
+                it.count = cnt;
+                it.flag = flag;
+                it.err = err;
+                it.k = info.k;
+            }
+            it.status = e;
+            if (e != FEAST_OK) worst = e;
+            feast_destroy(ctx);
+        }
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < w; ++t) pool.emplace_back(worker, t);
+    for (auto &th : pool) th.join();
+    return worst.load();
 }
 
 unsigned long long feast_kernel_launches(void) { return g_launches.load(); }
@@ -464,14 +744,21 @@ int feast_zgetrs_batched(int64_t n, int64_t nrhs, int batch, const void *M, int6
                           ldx, sx);
 }
 
+size_t feast_zqz_work_bytes(int m, int batch)
+{
+    if (m < 0 || batch < 0) return 0;
+    return (size_t)batch * zqz_work_bytes(m);
+}
+
 int feast_zqz_batched(int m, int batch, void *A, void *B, void *alpha, void *beta, void *V,
                       void *work, int *status, void *stream)
 {
     if (m < 0 || batch < 0 || !A || !B || !alpha || !beta || !V || !work || !status) return FEAST_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    FEAST_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
-    return zqz_batched(s, m, batch, (zd *)A, m, (int64_t)m * m, (zd *)B, m, (int64_t)m * m, (zd *)alpha,
-                       (zd *)beta, (zd *)V, m, (int64_t)m * m, (zd *)work, status);
+    FEAST_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));
+    int e = zqz_batched(s, m, batch, (zd *)A, m, (int64_t)m * m, (zd *)B, m, (int64_t)m * m, (zd *)alpha,
+                        (zd *)beta, (zd *)V, m, (int64_t)m * m, work, status, status + 1);
+    return e;
 }
 
 }  // extern "C"

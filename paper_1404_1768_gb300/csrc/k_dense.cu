@@ -1,0 +1,610 @@
+// Complex dense kernels (FP64 for the plain path, FP32 for the low-precision
+// factors of the precision form): batched GEMM, formation
+// of the shifted matrices z_j B - A (eq. 4.2), blocked right-looking LU with
+// partial pivoting, blocked triangular solves with many right-hand sides,
+// and the quadrature node-sum U = sum_j w_j X_j (eq. 4.1).
+//
+// GB300 runs FP64 at ~2 DFMA per clock per SM (1.05 TFLOP/s measured for
+// the whole GPU), so these kernels are bound by the FP64 pipe, not by
+// memory: a modest register tile (4 x 4 complex per thread) already keeps
+// the pipe busy, and the work is spread over all 152 SMs through the batch
+// (node) dimension and the tile grid.
+#include "common.cuh"
+
+namespace feast {
+
+// ------------------------------------------------------------------ GEMM
+namespace {
+constexpr int GB_M = 64, GB_N = 64, GB_K = 8, GB_T = 256;
+
+__device__ __forceinline__ void atomic_cadd(double2 *p, double2 v)
+{
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+__device__ __forceinline__ void atomic_cadd(float2 *p, float2 v)
+{
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+// splits > 1: blockIdx.z = batch * splits + s covers the s-th slice of K and
+// adds alpha * partial into C atomically (C pre-scaled by beta on the host
+// side of the launch).
+template <typename T>
+__global__ void __launch_bounds__(GB_T) k_gemm(int conj_a, int64_t m, int64_t n, int64_t k,
+                                               T alpha, const T *__restrict__ A, int64_t lda,
+                                               int64_t sA, const T *__restrict__ B,
+                                               int64_t ldb, int64_t sB, T beta,
+                                               T *__restrict__ C, int64_t ldc, int64_t sC,
+                                               int splits, int64_t kchunk)
+{
+    __shared__ T As[GB_K][GB_M + 1];
+    __shared__ T Bs[GB_K][GB_N + 1];
+    const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
+    const int64_t kbeg = (int64_t)sp * kchunk;
+    const int64_t kend = (kbeg + kchunk < k) ? kbeg + kchunk : k;
+    A += (int64_t)b * sA;
+    B += (int64_t)b * sB;
+    C += (int64_t)b * sC;
+    const int64_t i0 = (int64_t)blockIdx.x * GB_M, j0 = (int64_t)blockIdx.y * GB_N;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = cx<T>(0, 0);
+
+    for (int64_t k0 = kbeg; k0 < kend; k0 += GB_K) {
+        // A tile: op(A)(i0 + r, k0 + kk)
+        for (int e = threadIdx.x; e < GB_M * GB_K; e += GB_T) {
+            int r, kk;
+            if (!conj_a) { r = e % GB_M; kk = e / GB_M; }
+            else         { kk = e % GB_K; r = e / GB_K; }
+            int64_t gi = i0 + r, gk = k0 + kk;
+            T v = cx<T>(0, 0);
+            if (gi < m && gk < kend) v = conj_a ? cconj(A[gk + gi * lda]) : A[gi + gk * lda];
+            As[kk][r] = v;
+        }
+        for (int e = threadIdx.x; e < GB_N * GB_K; e += GB_T) {
+            int kk = e % GB_K, c = e / GB_K;
+            int64_t gj = j0 + c, gk = k0 + kk;
+            Bs[kk][c] = (gj < n && gk < kend) ? B[gk + gj * ldb] : cx<T>(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cfma(acc[a][c], av[a], bv[c]);
+        }
+        __syncthreads();
+    }
+    const bool beta0 = cis_zero(beta);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int64_t gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * c;
+            if (gi < m && gj < n) {
+                T v = cmul(alpha, acc[a][c]);
+                if (splits > 1) {
+                    atomic_cadd(&C[gi + gj * ldc], v);
+                } else {
+                    if (!beta0) v = cadd(v, cmul(beta, C[gi + gj * ldc]));
+                    C[gi + gj * ldc] = v;
+                }
+            }
+        }
+}
+// C <- beta C (beta = 0 writes zeros, so stale NaNs do not survive)
+template <typename T>
+__global__ void k_scale(int64_t m, int64_t n, T beta, T *C, int64_t ldc, int64_t sC)
+{
+    T *Cb = C + (int64_t)blockIdx.y * sC;
+    const bool zero = cis_zero(beta);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e % m, c = e / m;
+        T &x = Cb[r + c * ldc];
+        x = zero ? cx<T>(0, 0) : cmul(beta, x);
+    }
+}
+}  // namespace
+
+template <typename T>
+int gemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, T alpha,
+                 const T *A, int64_t lda, int64_t sA, const T *B, int64_t ldb, int64_t sB,
+                 T beta, T *C, int64_t ldc, int64_t sC, int batch)
+{
+    if (m <= 0 || n <= 0 || batch <= 0) return FEAST_OK;
+    if (batch > 65535) return FEAST_EINVAL;
+    const unsigned tiles = cdiv(m, GB_M) * cdiv(n, GB_N) * (unsigned)batch;
+    // split K when the output tiles cannot fill the GPU twice over (the
+    // FP64 pipe is the bound, so every SM counts)
+    int splits = 1;
+    if (tiles < 2 * 152 && k >= 4 * 128) {
+        int64_t want = (2 * 152 + tiles - 1) / tiles;
+        int64_t maxs = k / 128;
+        splits = (int)(want < maxs ? want : maxs);
+        if (splits * batch > 65535) splits = 65535 / batch;
+        if (splits < 1) splits = 1;
+    }
+    int64_t kchunk = (k + splits - 1) / splits;
+    kchunk = ((kchunk + GB_K - 1) / GB_K) * GB_K;
+    if (splits > 1) {
+        // C <- beta C first; the slices then add alpha * partial atomically
+        if (!(beta.x == 1 && beta.y == 0)) {
+            unsigned gx = cdiv((size_t)m * n, 256);
+            k_scale<T><<<dim3(gx > 4096 ? 4096 : gx, batch), 256, 0, s>>>(m, n, beta, C, ldc, sC);
+            FEAST_LAUNCH_CHECK();
+        }
+    }
+    dim3 grid(cdiv(m, GB_M), cdiv(n, GB_N), batch * splits);
+    if (grid.y > 65535) return FEAST_EINVAL;
+    k_gemm<T><<<grid, GB_T, 0, s>>>(conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                    splits, kchunk);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+template int gemm_batched<double2>(cudaStream_t, int, int64_t, int64_t, int64_t, double2, const double2 *,
+                                   int64_t, int64_t, const double2 *, int64_t, int64_t, double2, double2 *,
+                                   int64_t, int64_t, int);
+template int gemm_batched<float2>(cudaStream_t, int, int64_t, int64_t, int64_t, float2, const float2 *,
+                                  int64_t, int64_t, const float2 *, int64_t, int64_t, float2, float2 *,
+                                  int64_t, int64_t, int);
+
+int zgemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, zd alpha,
+                  const zd *A, int64_t lda, int64_t sA, const zd *B, int64_t ldb, int64_t sB,
+                  zd beta, zd *C, int64_t ldc, int64_t sC, int batch)
+{
+    return gemm_batched<zd>(s, conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+}
+
+// ------------------------------------------------------------------ z_j B - A
+namespace {
+__global__ void k_form_shifted(int64_t n, const zd *__restrict__ A, const zd *__restrict__ B,
+                               int64_t ld, const zd *__restrict__ z, zd *__restrict__ F,
+                               int64_t ldf, int64_t sF)
+{
+    const int j = blockIdx.y;
+    const zd zj = z[j];
+    const int64_t total = n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e % n, c = e / n;
+        zd bij = B ? B[r + c * ld] : zmake(r == c ? 1.0 : 0.0, 0.0);
+        F[(int64_t)j * sF + r + c * ldf] = zsub(zmul(zj, bij), A[r + c * ld]);
+    }
+}
+}  // namespace
+
+int zform_shifted(cudaStream_t s, int64_t n, int q, const zd *A, const zd *B, int64_t ld,
+                  const zd *z, zd *F, int64_t ldf, int64_t sF)
+{
+    unsigned gx = cdiv(n * n, 256);
+    if (gx > 1024) gx = 1024;
+    k_form_shifted<<<dim3(gx, q), 256, 0, s>>>(n, A, B, ld, z, F, ldf, sF);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+// ------------------------------------------------------------------ LU
+namespace {
+constexpr int LU_NB = 32;     // panel width
+constexpr int LU_PT = 512;    // panel threads
+
+// Factor the panel [k0, k0 + nb) x [k0, n) of every batch member: pivot by
+// largest modulus (ties -> smallest row), swap within the panel columns,
+// scale, rank-1 update of the remaining panel columns.
+template <typename T>
+__global__ void __launch_bounds__(LU_PT) k_lu_panel(int64_t n, int64_t k0, int nb, T *F,
+                                                   int64_t ldf, int64_t sF, int *piv, int64_t pstride,
+                                                   int *info, int *row)
+{
+    typedef typename CxReal<T>::type R;
+    const int b = blockIdx.x;
+    T *Am = F + (int64_t)b * sF;
+    __shared__ R s_val[LU_PT / 32];
+    __shared__ int64_t s_idx[LU_PT / 32];
+    __shared__ int64_t s_p;
+    __shared__ T s_row[LU_NB];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = 0; j < nb; ++j) {
+        const int64_t col = k0 + j;
+        R best = -1;
+        int64_t bi = col;
+        for (int64_t i = col + threadIdx.x; i < n; i += LU_PT) {
+            R v = cabs2(Am[i + col * ldf]);
+            if (v > best) { best = v; bi = i; }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            R ov = __shfl_down_sync(0xffffffffu, best, off);
+            int64_t oi = __shfl_down_sync(0xffffffffu, bi, off);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            R bv = s_val[0];
+            int64_t bx = s_idx[0];
+            for (int w = 1; w < LU_PT / 32; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bx)) { bv = s_val[w]; bx = s_idx[w]; }
+            s_p = bx;
+            piv[(int64_t)b * pstride + col] = (int)bx;
+            if (bv == 0 && info) {
+                // record the first failing block (1-based) and column
+                if (atomicCAS(info, 0, b + 1) == 0 && row) *row = (int)col + 1;
+            }
+        }
+        __syncthreads();
+        const int64_t p = s_p;
+        if (p != col && threadIdx.x < nb) {
+            int64_t c = k0 + threadIdx.x;
+            T t = Am[col + c * ldf];
+            Am[col + c * ldf] = Am[p + c * ldf];
+            Am[p + c * ldf] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < nb) s_row[threadIdx.x] = Am[col + (k0 + threadIdx.x) * ldf];
+        __syncthreads();
+        const T d = s_row[j];
+        if (!cis_zero(d)) {
+            for (int64_t i = col + 1 + threadIdx.x; i < n; i += LU_PT) {
+                T l = cdiv(Am[i + col * ldf], d);
+                Am[i + col * ldf] = l;
+                const T nl = cneg(l);
+                for (int c = j + 1; c < nb; ++c) {
+                    T &a = Am[i + (k0 + c) * ldf];
+                    T v = a;
+                    cfma(v, nl, s_row[c]);
+                    a = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Apply the panel's row interchanges to the columns outside the panel.
+template <typename T>
+__global__ void k_laswp_outside(int64_t n, int64_t k0, int nb, T *F, int64_t ldf, int64_t sF,
+                                const int *piv)
+{
+    const int b = blockIdx.y;
+    T *Am = F + (int64_t)b * sF;
+    const int *pv = piv + (int64_t)b * n;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        if (c >= k0 && c < k0 + nb) continue;
+        for (int j = 0; j < nb; ++j) {
+            int64_t r = k0 + j, p = pv[r];
+            if (p != r) {
+                T t = Am[r + c * ldf];
+                Am[r + c * ldf] = Am[p + c * ldf];
+                Am[p + c * ldf] = t;
+            }
+        }
+    }
+}
+
+// U12 = L11^{-1} A12 for the nb rows of the panel (L11 unit lower), one
+// thread per column to the right of the panel.
+template <typename T>
+__global__ void k_trsm_u12(int64_t n, int64_t k0, int nb, T *F, int64_t ldf, int64_t sF)
+{
+    const int b = blockIdx.y;
+    T *Am = F + (int64_t)b * sF;
+    __shared__ T L[LU_NB][LU_NB + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int r = e % nb, c = e / nb;
+        L[r][c] = Am[(k0 + r) + (k0 + c) * ldf];
+    }
+    __syncthreads();
+    const int64_t c = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    T x[LU_NB];
+#pragma unroll
+    for (int r = 0; r < LU_NB; ++r)
+        if (r < nb) x[r] = Am[(k0 + r) + c * ldf];
+#pragma unroll
+    for (int i = 0; i < LU_NB; ++i) {
+        if (i >= nb) break;
+#pragma unroll
+        for (int r = i + 1; r < LU_NB; ++r)
+            if (r < nb) cfma(x[r], cneg(L[r][i]), x[i]);
+    }
+#pragma unroll
+    for (int r = 0; r < LU_NB; ++r)
+        if (r < nb) Am[(k0 + r) + c * ldf] = x[r];
+}
+}  // namespace
+
+template <typename T>
+int getrf_batched(cudaStream_t s, int64_t n, int batch, T *F, int64_t ldf, int64_t sF, int *piv,
+                  int *info, int *row)
+{
+    if (n <= 0 || batch <= 0) return FEAST_OK;
+    for (int64_t k0 = 0; k0 < n; k0 += LU_NB) {
+        int nb = (int)((n - k0) < LU_NB ? (n - k0) : LU_NB);
+        k_lu_panel<T><<<batch, LU_PT, 0, s>>>(n, k0, nb, F, ldf, sF, piv, n, info, row);
+        FEAST_LAUNCH_CHECK();
+        unsigned gx = cdiv(n, 128);
+        k_laswp_outside<T><<<dim3(gx, batch), 128, 0, s>>>(n, k0, nb, F, ldf, sF, piv);
+        FEAST_LAUNCH_CHECK();
+        int64_t rest = n - k0 - nb;
+        if (rest > 0) {
+            k_trsm_u12<T><<<dim3(cdiv(rest, 128), batch), 128, 0, s>>>(n, k0, nb, F, ldf, sF);
+            FEAST_LAUNCH_CHECK();
+            int e = gemm_batched<T>(s, 0, rest, rest, nb, cx<T>(-1, 0), F + k0 + nb + k0 * ldf,
+                                    ldf, sF, F + k0 + (k0 + nb) * ldf, ldf, sF, cx<T>(1, 0),
+                                    F + (k0 + nb) + (k0 + nb) * ldf, ldf, sF, batch);
+            if (e) return e;
+        }
+    }
+    return FEAST_OK;
+}
+template int getrf_batched<double2>(cudaStream_t, int64_t, int, double2 *, int64_t, int64_t, int *, int *, int *);
+
+// Factor only the leading panel (columns 0..nb-1, all rows) of each batch
+// member; pivots at piv[b * pstride + k].
+template <typename T>
+int getrf_panel(cudaStream_t s, int64_t rows, int nb, int batch, T *F, int64_t ldf, int64_t sF,
+                int *piv, int64_t pstride, int *info, int *row)
+{
+    if (rows <= 0 || nb <= 0 || batch <= 0) return FEAST_OK;
+    k_lu_panel<T><<<batch, LU_PT, 0, s>>>(rows, 0, nb, F, ldf, sF, piv, pstride, info, row);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+template int getrf_panel<double2>(cudaStream_t, int64_t, int, int, double2 *, int64_t, int64_t, int *,
+                                  int64_t, int *, int *);
+template int getrf_panel<float2>(cudaStream_t, int64_t, int, int, float2 *, int64_t, int64_t, int *,
+                                 int64_t, int *, int *);
+template int getrf_batched<float2>(cudaStream_t, int64_t, int, float2 *, int64_t, int64_t, int *, int *, int *);
+
+int zgetrf_batched(cudaStream_t s, int64_t n, int batch, zd *F, int64_t ldf, int64_t sF,
+                   int *piv, int *info, int *row)
+{
+    return getrf_batched<zd>(s, n, batch, F, ldf, sF, piv, info, row);
+}
+
+// ------------------------------------------------------------------ solves
+namespace {
+constexpr int SV_NB = 32;
+
+// X rows [k0, k0+nb) <- T^{-1} X rows [k0, k0+nb) for the diagonal block T of
+// the factor (lower = unit lower L, else upper U).  One thread per column.
+template <typename C>
+__global__ void k_trsv_diag(int64_t n, int64_t nrhs, int64_t k0, int nb, int lower,
+                            const C *F, int64_t ldf, int64_t sF, C *X, int64_t ldx, int64_t sX)
+{
+    const int b = blockIdx.y;
+    const C *Am = F + (int64_t)b * sF;
+    C *Xb = X + (int64_t)b * sX;
+    __shared__ C T[SV_NB][SV_NB + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int r = e % nb, c = e / nb;
+        T[r][c] = Am[(k0 + r) + (k0 + c) * ldf];
+    }
+    __syncthreads();
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nrhs) return;
+    C x[SV_NB];
+#pragma unroll
+    for (int r = 0; r < SV_NB; ++r)
+        if (r < nb) x[r] = Xb[(k0 + r) + c * ldx];
+    if (lower) {
+#pragma unroll
+        for (int i = 0; i < SV_NB; ++i) {
+            if (i >= nb) break;
+#pragma unroll
+            for (int r = i + 1; r < SV_NB; ++r)
+                if (r < nb) cfma(x[r], cneg(T[r][i]), x[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = SV_NB - 1; i >= 0; --i) {
+            if (i >= nb) continue;
+            x[i] = cdiv(x[i], T[i][i]);
+#pragma unroll
+            for (int r = 0; r < SV_NB; ++r)
+                if (r < i) cfma(x[r], cneg(T[r][i]), x[i]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < SV_NB; ++r)
+        if (r < nb) Xb[(k0 + r) + c * ldx] = x[r];
+}
+
+// Apply the interchanges piv[0..n) to each column of X in sequence.
+template <typename T>
+__global__ void k_laswp_rhs(int64_t n, int64_t nrhs, const int *piv, T *X, int64_t ldx,
+                            int64_t sX)
+{
+    const int b = blockIdx.y;
+    T *Xb = X + (int64_t)b * sX;
+    const int *pv = piv + (int64_t)b * n;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nrhs) return;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t p = pv[k];
+        if (p != k) {
+            T t = Xb[k + c * ldx];
+            Xb[k + c * ldx] = Xb[p + c * ldx];
+            Xb[p + c * ldx] = t;
+        }
+    }
+}
+
+// Composition of the interchanges: perm[i] = original row that ends at i.
+__global__ void k_piv_to_perm(int64_t n, const int *piv, int *perm)
+{
+    const int b = blockIdx.x;
+    const int *pv = piv + (int64_t)b * n;
+    int *pm = perm + (int64_t)b * n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) pm[i] = (int)i;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int64_t k = 0; k < n; ++k) {
+            int64_t p = pv[k];
+            if (p != k) { int t = pm[k]; pm[k] = pm[p]; pm[p] = t; }
+        }
+}
+
+template <typename T>
+__global__ void k_gather_rows(int64_t n, int64_t nrhs, const int *perm, const T *R, int64_t ldr,
+                              int64_t sR, T *X, int64_t ldx, int64_t sX)
+{
+    const int b = blockIdx.y;
+    const int *pm = perm + (int64_t)b * n;
+    const T *Rb = R + (int64_t)b * sR;
+    T *Xb = X + (int64_t)b * sX;
+    const int64_t total = n * nrhs;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e % n, c = e / n;
+        Xb[r + c * ldx] = Rb[pm[r] + c * ldr];
+    }
+}
+}  // namespace
+
+int zpiv_to_perm(cudaStream_t s, int64_t n, int batch, const int *piv, int *perm)
+{
+    k_piv_to_perm<<<batch, 256, 0, s>>>(n, piv, perm);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+template <typename T>
+int gather_rows(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const int *perm, const T *R,
+                int64_t ldr, int64_t sR, T *X, int64_t ldx, int64_t sX)
+{
+    unsigned gx = cdiv(n * nrhs, 256);
+    if (gx > 2048) gx = 2048;
+    k_gather_rows<T><<<dim3(gx, batch), 256, 0, s>>>(n, nrhs, perm, R, ldr, sR, X, ldx, sX);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+template int gather_rows<double2>(cudaStream_t, int64_t, int64_t, int, const int *, const double2 *,
+                                  int64_t, int64_t, double2 *, int64_t, int64_t);
+template int gather_rows<float2>(cudaStream_t, int64_t, int64_t, int, const int *, const float2 *,
+                                 int64_t, int64_t, float2 *, int64_t, int64_t);
+
+int zgather_rows(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const int *perm,
+                 const zd *R, int64_t ldr, zd *X, int64_t ldx, int64_t sX)
+{
+    return gather_rows<zd>(s, n, nrhs, batch, perm, R, ldr, 0, X, ldx, sX);
+}
+
+// Forward substitution with the unit-lower factor (in place).
+template <typename T>
+int trsm_lower_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const T *F, int64_t ldf,
+                       int64_t sF, T *X, int64_t ldx, int64_t sX)
+{
+    if (n <= 0 || nrhs <= 0 || batch <= 0) return FEAST_OK;
+    dim3 g(cdiv(nrhs, 64), batch);
+    for (int64_t k0 = 0; k0 < n; k0 += SV_NB) {
+        int nb = (int)((n - k0) < SV_NB ? (n - k0) : SV_NB);
+        k_trsv_diag<T><<<g, 64, 0, s>>>(n, nrhs, k0, nb, 1, F, ldf, sF, X, ldx, sX);
+        FEAST_LAUNCH_CHECK();
+        int64_t rest = n - k0 - nb;
+        if (rest > 0) {
+            int e = gemm_batched<T>(s, 0, rest, nrhs, nb, cx<T>(-1, 0), F + (k0 + nb) + k0 * ldf,
+                                    ldf, sF, X + k0, ldx, sX, cx<T>(1, 0), X + k0 + nb, ldx, sX,
+                                    batch);
+            if (e) return e;
+        }
+    }
+    return FEAST_OK;
+}
+
+// Back substitution with the upper factor (in place).
+template <typename T>
+int trsm_upper_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const T *F, int64_t ldf,
+                       int64_t sF, T *X, int64_t ldx, int64_t sX)
+{
+    if (n <= 0 || nrhs <= 0 || batch <= 0) return FEAST_OK;
+    dim3 g(cdiv(nrhs, 64), batch);
+    int64_t last = ((n - 1) / SV_NB) * SV_NB;
+    for (int64_t k0 = last; k0 >= 0; k0 -= SV_NB) {
+        int nb = (int)((n - k0) < SV_NB ? (n - k0) : SV_NB);
+        k_trsv_diag<T><<<g, 64, 0, s>>>(n, nrhs, k0, nb, 0, F, ldf, sF, X, ldx, sX);
+        FEAST_LAUNCH_CHECK();
+        if (k0 > 0) {
+            int e = gemm_batched<T>(s, 0, k0, nrhs, nb, cx<T>(-1, 0), F + k0 * ldf, ldf, sF,
+                                    X + k0, ldx, sX, cx<T>(1, 0), X, ldx, sX, batch);
+            if (e) return e;
+        }
+    }
+    return FEAST_OK;
+}
+
+// L U solve of already-permuted right-hand sides.
+template <typename T>
+int trsm_lu_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const T *F, int64_t ldf,
+                    int64_t sF, T *X, int64_t ldx, int64_t sX)
+{
+    int e = trsm_lower_batched<T>(s, n, nrhs, batch, F, ldf, sF, X, ldx, sX);
+    if (e) return e;
+    return trsm_upper_batched<T>(s, n, nrhs, batch, F, ldf, sF, X, ldx, sX);
+}
+template int trsm_upper_batched<double2>(cudaStream_t, int64_t, int64_t, int, const double2 *, int64_t,
+                                         int64_t, double2 *, int64_t, int64_t);
+template int trsm_upper_batched<float2>(cudaStream_t, int64_t, int64_t, int, const float2 *, int64_t,
+                                        int64_t, float2 *, int64_t, int64_t);
+template int trsm_lu_batched<double2>(cudaStream_t, int64_t, int64_t, int, const double2 *, int64_t,
+                                      int64_t, double2 *, int64_t, int64_t);
+template int trsm_lu_batched<float2>(cudaStream_t, int64_t, int64_t, int, const float2 *, int64_t,
+                                     int64_t, float2 *, int64_t, int64_t);
+
+int ztrsm_lu_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const zd *F,
+                     int64_t ldf, int64_t sF, zd *X, int64_t ldx, int64_t sX)
+{
+    return trsm_lu_batched<zd>(s, n, nrhs, batch, F, ldf, sF, X, ldx, sX);
+}
+
+int zgetrs_batched(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const zd *F,
+                   int64_t ldf, int64_t sF, const int *piv, zd *X, int64_t ldx, int64_t sX)
+{
+    if (n <= 0 || nrhs <= 0 || batch <= 0) return FEAST_OK;
+    k_laswp_rhs<zd><<<dim3(cdiv(nrhs, 64), batch), 64, 0, s>>>(n, nrhs, piv, X, ldx, sX);
+    FEAST_LAUNCH_CHECK();
+    return ztrsm_lu_batched(s, n, nrhs, batch, F, ldf, sF, X, ldx, sX);
+}
+
+// ------------------------------------------------------------------ node sum
+namespace {
+__global__ void k_node_sum(int64_t n, int64_t m, int q, const zd *__restrict__ w,
+                           const zd *__restrict__ X, int64_t ldx, int64_t sX, zd *__restrict__ U,
+                           int64_t ldu)
+{
+    const int64_t total = n * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e % n, c = e / n;
+        zd acc = zmake(0.0, 0.0);
+        for (int j = 0; j < q; ++j) zfma(acc, w[j], X[(int64_t)j * sX + r + c * ldx]);
+        U[r + c * ldu] = acc;
+    }
+}
+}  // namespace
+
+int znode_sum(cudaStream_t s, int64_t n, int64_t m, int q, const zd *w, const zd *X,
+              int64_t ldx, int64_t sX, zd *U, int64_t ldu)
+{
+    unsigned gx = cdiv(n * m, 256);
+    if (gx > 152 * 16) gx = 152 * 16;
+    k_node_sum<<<gx, 256, 0, s>>>(n, m, q, w, X, ldx, sX, U, ldu);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+}  // namespace feast

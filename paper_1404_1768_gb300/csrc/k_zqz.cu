@@ -9,11 +9,10 @@
 // the generalized Schur form (beta S - alpha P) y = 0 mapped back by Z.
 //
 // The sweep is a chain of dependent 2x2 rotations, each applied to a row or
-// column pair; the CTA's threads share each rotation's O(m) updates and
-// meet at a barrier between rotations.  For m <= 64 the three m x m arrays
-// live in shared memory and a single warp runs the chase (warp barriers are
-// nearly free); larger pencils keep them in global memory (L2-resident) and
-// use a full CTA.
+// column pair; the CTA's four warps share each rotation's updates of H, T
+// and Z (one merged index range, so every SM partition's FP64 units work)
+// and meet at a barrier between rotations.  The three m x m arrays live in
+// shared memory (m <= 64).  Larger projected problems go to k_zeig.cu.
 #include "common.cuh"
 
 namespace feast {
@@ -95,6 +94,46 @@ __device__ __forceinline__ void rot_cols(Mat M, int i, int j, int r0, int r1, do
     }
 }
 
+// Left rotation on rows (i, j) of two matrices at once: M1 over columns
+// [a0, a1] (optionally zeroing M1(j, z1)), M2 over [b0, b1]; the threads
+// share the concatenated index range so all warps stay busy.
+template <int NT>
+__device__ __forceinline__ void rot_rows2(Mat M1, int a0, int a1, int z1, Mat M2, int b0, int b1,
+                                          int i, int j, double c, zd s)
+{
+    const int na = a1 - a0 + 1, nb = b1 - b0 + 1;
+    for (int t = (int)threadIdx.x; t < na + nb; t += NT) {
+        Mat M = (t < na) ? M1 : M2;
+        const int col = (t < na) ? a0 + t : b0 + (t - na);
+        zd a = M(i, col), b = M(j, col);
+        zd ni = zadd(zscale(a, c), zmul(s, b));
+        zd nj = zadd(zscale(zmul(zconj(s), a), -1.0), zscale(b, c));
+        M(i, col) = ni;
+        M(j, col) = (t < na && col == z1) ? zmake(0.0, 0.0) : nj;
+    }
+}
+// Right rotation on columns (i, j) of three matrices at once: M1 rows
+// [0, r1], M2 rows [0, r2] (optionally zeroing M2(z2, i)), M3 rows [0, r3].
+template <int NT>
+__device__ __forceinline__ void rot_cols3(Mat M1, int r1, Mat M2, int r2, int z2, Mat M3, int r3,
+                                          int i, int j, double c, zd s)
+{
+    const int n1 = r1 + 1, n2 = r2 + 1, n3 = r3 + 1;
+    for (int t = (int)threadIdx.x; t < n1 + n2 + n3; t += NT) {
+        Mat M;
+        int row;
+        bool zero_ok = false;
+        if (t < n1) { M = M1; row = t; }
+        else if (t < n1 + n2) { M = M2; row = t - n1; zero_ok = true; }
+        else { M = M3; row = t - n1 - n2; }
+        zd a = M(row, i), b = M(row, j);
+        zd ni = zadd(zscale(a, c), zmul(b, s));
+        zd nj = zadd(zscale(zmul(a, zconj(s)), -1.0), zscale(b, c));
+        M(row, i) = (zero_ok && row == z2) ? zmake(0.0, 0.0) : ni;
+        M(row, j) = nj;
+    }
+}
+
 template <int NT>
 __device__ double block_max(double v, double *red)
 {
@@ -158,14 +197,11 @@ __global__ void __launch_bounds__(NT) k_qz(int m, zd *A, int64_t lda, int64_t sA
         for (int i = m - 1; i >= j + 2; --i) {
             giv_left(H(i - 1, j), H(i, j), c, s);
             Team<NT>::bar();
-            rot_rows<NT>(H, i - 1, i, j, m - 1, c, s, j);
-            rot_rows<NT>(T, i - 1, i, i - 1, m - 1, c, s, -1);
+            rot_rows2<NT>(H, j, m - 1, j, T, i - 1, m - 1, i - 1, i, c, s);
             Team<NT>::bar();
             giv_right(T(i, i - 1), T(i, i), c, s);
             Team<NT>::bar();
-            rot_cols<NT>(H, i - 1, i, 0, m - 1, c, s, -1);
-            rot_cols<NT>(T, i - 1, i, 0, i, c, s, i);
-            rot_cols<NT>(Z, i - 1, i, 0, m - 1, c, s, -1);
+            rot_cols3<NT>(H, m - 1, T, i, i, Z, m - 1, i - 1, i, c, s);
             Team<NT>::bar();
         }
     // norms for the deflation tests
@@ -222,15 +258,12 @@ __global__ void __launch_bounds__(NT) k_qz(int m, zd *A, int64_t lda, int64_t sA
             else        { x = H(k, k - 1); y = H(k + 1, k - 1); }
             giv_left(x, y, c, s);
             Team<NT>::bar();
-            rot_rows<NT>(H, k, k + 1, (k > l) ? k - 1 : l, m - 1, c, s, (k > l) ? k - 1 : -1);
-            rot_rows<NT>(T, k, k + 1, k, m - 1, c, s, -1);
+            rot_rows2<NT>(H, (k > l) ? k - 1 : l, m - 1, (k > l) ? k - 1 : -1, T, k, m - 1, k, k + 1, c, s);
             Team<NT>::bar();
             giv_right(T(k + 1, k), T(k + 1, k + 1), c, s);
             Team<NT>::bar();
             int rl = (k + 2 < ihi) ? k + 2 : ihi;
-            rot_cols<NT>(H, k, k + 1, 0, rl, c, s, -1);
-            rot_cols<NT>(T, k, k + 1, 0, k + 1, c, s, k + 1);
-            rot_cols<NT>(Z, k, k + 1, 0, m - 1, c, s, -1);
+            rot_cols3<NT>(H, rl, T, k + 1, k + 1, Z, m - 1, k, k + 1, c, s);
             Team<NT>::bar();
         }
     }
@@ -289,22 +322,35 @@ __global__ void __launch_bounds__(NT) k_qz(int m, zd *A, int64_t lda, int64_t sA
 }
 }  // namespace
 
+size_t zqz_work_bytes(int m)
+{
+    size_t small = (size_t)m * m * sizeof(zd);
+    if (m <= 64) return small;
+    size_t big = zeig_large_work_bytes(m);
+    return (big + 255) & ~(size_t)255;
+}
+
 int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA, zd *B,
                 int64_t ldb, int64_t sB, zd *alpha, zd *beta, zd *V, int64_t ldv, int64_t sV,
-                zd *work, int *fail)
+                void *work, int *fail, int *timeout)
 {
     if (m <= 0 || batch <= 0) return FEAST_OK;
     if (m <= 64) {
         size_t sm = 3 * (size_t)m * m * sizeof(zd);
         if (sm > 48 * 1024)
-            FEAST_CUDA_TRY(cudaFuncSetAttribute(k_qz<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_qz<32><<<batch, 32, sm, s>>>(m, A, lda, sA, B, ldb, sB, alpha, beta, V, ldv, sV, work, 1, fail);
-    } else if (m <= 512) {
-        k_qz<256><<<batch, 256, 0, s>>>(m, A, lda, sA, B, ldb, sB, alpha, beta, V, ldv, sV, work, 0, fail);
-    } else {
-        k_qz<1024><<<batch, 1024, 0, s>>>(m, A, lda, sA, B, ldb, sB, alpha, beta, V, ldv, sV, work, 0, fail);
+            FEAST_CUDA_TRY(cudaFuncSetAttribute(k_qz<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_qz<128><<<batch, 128, sm, s>>>(m, A, lda, sA, B, ldb, sB, alpha, beta, V, ldv, sV, (zd *)work, 1, fail);
+        FEAST_LAUNCH_CHECK();
+        return FEAST_OK;
     }
-    FEAST_LAUNCH_CHECK();
+    if (lda != m || ldb != m || ldv != m) return FEAST_EINVAL;
+    const size_t wb = zqz_work_bytes(m);
+    for (int b = 0; b < batch; ++b) {
+        int e = zeig_large(s, m, A + (int64_t)b * sA, B + (int64_t)b * sB, alpha + (int64_t)b * m,
+                           beta + (int64_t)b * m, V + (int64_t)b * sV, (char *)work + b * wb, fail,
+                           timeout);
+        if (e) return e;
+    }
     return FEAST_OK;
 }
 

@@ -165,8 +165,29 @@ def ragged_batch(count: int, n_lo: int, n_hi: int, seed: int = 0, lam_radius: fl
 
 # The workloads of the benchmark and the tests, by name.
 WORKLOADS = {
-    # plain method, FP64 dense, n = 200, circle |z| < 1, 16 trapezoid nodes, m0 = 64
-    "dense_n200_m64_q16": dict(n=200, m0=64, q=16, rule=0, center=0j, radius=1.0, seed=0),
-    # precision form, dense n = 4096, m0 = 1280, 32 trapezoid nodes
-    "dense_n4096_m1280_q32": dict(n=4096, m0=1280, q=32, rule=0, center=0j, radius=1.0, seed=0),
+    # plain method, FP64 dense, n = 200, circle |z| < 1, 16 trapezoid nodes,
+    # m0 = 64, stopping tolerance 1e-12
+    "dense_n200_m64_q16": dict(n=200, m0=64, q=16, rule=0, center=0j, radius=1.0, seed=0,
+                               eps=1e-12),
+    # precision form, dense n = 4096, m0 = 1280, 32 trapezoid nodes; compared
+    # at residual <= 1e-10
+    "dense_n4096_m1280_q32": dict(n=4096, m0=1280, q=32, rule=0, center=0j, radius=1.0, seed=0,
+                                  eps=1e-10),
+    # banded convection-diffusion, 128 x 128 grid (n = 16384, kl = ku = 128),
+    # B = I, ellipse around the lowest 41 eigenvalues, 16 Gauss-Legendre nodes
+    "band_n16384_m64_q16": dict(nx=128, m0=64, q=16, rule=1, center=422.0 + 0j, a=322.0,
+                                b=80.5, seed=0, eps=1e-10, beta=(20.0, 10.0)),
 }
+
+
+def convection_diffusion_spectrum(nx: int, beta=(20.0, 10.0)) -> np.ndarray:
+    """Closed-form eigenvalues of the operator built by convection_diffusion
+    (ascending): lam_{k,l} = (2/h^2) [2 - sqrt(1-(b1 h/2)^2) cos(k pi h)
+    - sqrt(1-(b2 h/2)^2) cos(l pi h)], k, l = 1..nx.  Used by tests as a pin;
+    the method's code never calls it."""
+    h = 1.0 / (nx + 1)
+    c1 = math.sqrt(1 - (beta[0] * h / 2) ** 2)
+    c2 = math.sqrt(1 - (beta[1] * h / 2) ** 2)
+    k = np.arange(1, nx + 1)
+    lam = (2 / h**2) * (2 - c1 * np.cos(k[:, None] * np.pi * h) - c2 * np.cos(k[None, :] * np.pi * h))
+    return np.sort(lam.ravel())

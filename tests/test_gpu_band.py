@@ -1,0 +1,101 @@
+"""Banded pencils on the GPU: band LU (unblocked-convention multipliers in
+LAPACK band storage) and band solves against the oracle's band LU, and the
+whole method on the convection-diffusion operator against its closed-form
+spectrum, up to the full 128 x 128 grid."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1404_1768_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _fg():
+    import paper_1404_1768_gb300 as fg
+    return fg
+
+
+def _match_rel(a, b):
+    b = list(b)
+    worst = 0.0
+    for x in sorted(a, key=lambda v: (v.real, v.imag)):
+        j = int(np.argmin([abs(x - y) for y in b]))
+        worst = max(worst, abs(x - b[j]) / abs(b[j]))
+        b.pop(j)
+    return worst
+
+
+def _random_band(n, kl, ku, seed):
+    rng = np.random.default_rng(seed)
+    ab = np.zeros((kl + ku + 1, n), complex, order="F")
+    for j in range(n):
+        for i in range(max(0, j - ku), min(n, j + kl + 1)):
+            ab[ku + i - j, j] = complex(rng.standard_normal(), rng.standard_normal())
+    return ab
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,kl,ku,m0,q", [(100, 10, 10, 8, 8), (77, 3, 5, 13, 5), (300, 40, 33, 9, 6)])
+def test_band_filter_matches_oracle(prec, n, kl, ku, m0, q):
+    """U = sum_j w_j (z_j B - A)^{-1} B V with band A and band B (kl, ku not
+    multiples of the 32-wide panels, n with ragged tails)."""
+    fg = _fg()
+    A = _random_band(n, kl, ku, n)
+    B = _random_band(n, kl, ku, n + 1)
+    B[ku, :] += 6.0                      # keep B well conditioned
+    Y = inputs.complex_normal(np.random.default_rng(3), (n, m0))
+    kw = dict(contour_kind=1, rule=1, q=q, center=0.5 + 0.2j, a=1.5, b=0.8, kind=1, kl=kl, ku=ku)
+    g = fg.Feast(A, B, Y, prec=prec, refine_tol=1e-14, max_refine=6, **kw)
+    o = oracle.Feast(A, B, Y, **kw)
+    V = inputs.complex_normal(np.random.default_rng(4), (n, m0))
+    Ug, Uo = g.filter(V), o.filter(V)
+    err = np.abs(Ug - Uo).max() / np.abs(Uo).max()
+    assert err < (1e-11 if prec == 0 else 1e-10), err
+    g.close(); o.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_band_gfeast_small_grid_closed_form(prec):
+    """12 x 12 grid, ellipse around the lowest 5 eigenvalues: exact count,
+    closed-form eigenvalues, and agreement with the oracle's run."""
+    fg = _fg()
+    nx = 12
+    bp = inputs.convection_diffusion(nx, 12, seed=1)
+    lam = inputs.convection_diffusion_spectrum(nx)
+    lo, hi = lam[0] * 0.5, 0.5 * (lam[4] + lam[5])
+    cen, a = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    kw = dict(kind=1, kl=bp.kl, ku=bp.ku, b_identity=True, contour_kind=1, rule=1, q=16,
+              center=complex(cen), a=a, b=a / 4, eps=1e-11)
+    g = fg.Feast(bp.A_band, None, bp.Y, prec=prec, refine_tol=1e-14, **kw)
+    g.run()
+    r = g.eigs()
+    o = oracle.Feast(bp.A_band, None, bp.Y, **kw)
+    o.run()
+    ro = o.result()
+    assert r["flag"] == 1 and r["count"] == ro["count"] == 5
+    assert _match_rel(r["lam"], lam[:5]) < 1e-9
+    assert _match_rel(r["lam"], ro["lam"]) < 1e-9
+    g.close(); o.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_band_full_grid_n16384(prec):
+    """The 128 x 128 workload (n = 16384, half-bandwidth 128, 16 nodes,
+    m0 = 64): the 41 eigenvalues inside the ellipse, each within 1e-8
+    relative of the closed form, residuals of eq. 5.1 below 1e-10."""
+    fg = _fg()
+    c = inputs.WORKLOADS["band_n16384_m64_q16"]
+    bp = inputs.convection_diffusion(c["nx"], c["m0"], seed=c["seed"], beta=c["beta"])
+    lam = inputs.convection_diffusion_spectrum(c["nx"], c["beta"])
+    inside = lam[((lam - c["center"].real) / c["a"]) ** 2 < 1.0]
+    assert len(inside) == 41
+    g = fg.Feast(bp.A_band, None, bp.Y, kind=1, kl=bp.kl, ku=bp.ku, b_identity=True,
+                 contour_kind=1, rule=c["rule"], q=c["q"], center=c["center"], a=c["a"], b=c["b"],
+                 eps=c["eps"], prec=prec, refine_tol=1e-13, max_iter=30)
+    g.run()
+    r = g.eigs(want_vectors=False)
+    assert r["flag"] == 1 and r["count"] == 41
+    assert _match_rel(r["lam"], inside) < 1e-8
+    assert np.all(r["res"] < 1e-10)
+    g.close()

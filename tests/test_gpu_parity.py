@@ -69,14 +69,18 @@ def test_singular_matrix_reports_info():
 
 
 # ------------------------------------------------------------------ QZ
-@pytest.mark.parametrize("m", [1, 2, 5, 16, 40, 64, 65, 100])
+@pytest.mark.parametrize("m", [1, 2, 5, 16, 40, 64, 65, 100, 300])
 def test_qz_matches_oracle(m):
     """Eigenvalues as multisets (the order of a QZ run is not unique) and the
     generalized eigen-residual of every returned vector."""
     fg = _fg()
     rng = np.random.default_rng(30 + m)
     As = [inputs.complex_normal(rng, (m, m)) for _ in range(2)]
-    Bs = [np.triu(inputs.complex_normal(rng, (m, m))) + 2.0 * np.eye(m) for _ in range(2)]
+    if m <= 64:   # QZ proper: any upper-triangular B, here with a wide condition range
+        Bs = [np.triu(inputs.complex_normal(rng, (m, m))) + 2.0 * np.eye(m) for _ in range(2)]
+    else:         # standard-form path: B = R2-like, well conditioned as in FEAST
+        Bs = [np.eye(m) + 0.1 * np.triu(inputs.complex_normal(rng, (m, m))) / np.sqrt(m)
+              for _ in range(2)]
     al, be, Vs, fail = fg.zqz_batched(As, Bs)
     assert fail == 0
     for b in range(2):
@@ -215,6 +219,27 @@ def test_gfeast_example_3_1_gpu():
     assert r["flag"] == 1 and r["count"] == 2
     assert _match(r["lam"], [v for v, _ in inside]) < 1e-13
     g.close()
+
+
+def test_gfeast_large_subspace_path():
+    """m0 = 96 > 64 takes the whole-GPU projected eigensolver (standard form,
+    Hessenberg reduction, chunked QR); end to end it must agree with the
+    oracle's QZ-based run.  This pencil has eigenvalues 0.998 and 1.0016
+    on either side of the circle, so the filter contracts only ~0.64 per
+    pass: both runs end by line 15 (max_iter) with the same count and
+    matching eigenvalues."""
+    p = inputs.prescribed_pencil(320, 96, seed=12)
+    cfg = dict(CFG1, q=16)
+    g, o = _pair(p, cfg, max_iter=40)
+    hg, ho = g.run(), o.run()
+    rg, ro = g.eigs(), o.result()
+    assert rg["flag"] == ro["flag"]
+    assert len(hg) == len(ho)
+    assert rg["count"] == ro["count"] == p.inside_count()
+    assert _match(rg["lam"], ro["lam"]) < 1e-8
+    ref = p.lam[np.abs(p.lam) < 1.0]
+    assert _match(rg["lam"], ref) < 1e-8
+    g.close(); o.close()
 
 
 def test_full_subspace_m0_equals_n():
