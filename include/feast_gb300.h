@@ -248,6 +248,22 @@ size_t feast_zqz_work_bytes(int m, int batch);
 int feast_zqz_batched(int m, int batch, void *A, void *B, void *alpha, void *beta, void *V,
                       void *work, int *status, void *stream);
 
+/* The same eigensolve for callers that cannot allocate device memory (for
+ * example code running during CUDA graph capture, inside a callback that
+ * must not touch the allocator, or in a process whose device memory belongs
+ * to someone else's pool).  The paper has no counterpart: this is a calling
+ * convention, not a step of the method.  Scratch comes from a fixed array
+ * inside the library (4 MiB per device, held until the process exits), so
+ * the caller passes only A, B, alpha, beta, V and status exactly as for
+ * feast_zqz_batched.  Limits: m <= 64 and batch * m * m <= 262144; larger
+ * requests return FEAST_EINVAL and queue no work.  No device memory is
+ * allocated or freed.  All calls on a device share the array: calls that
+ * overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's address and should come before any stream capture.  Asynchronous. */
+int feast_zqz_batched_noalloc(int m, int batch, void *A, void *B, void *alpha, void *beta,
+                              void *V, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,7 +76,7 @@ _lock = threading.Lock()
 EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs", "feast_get",
            "feast_filter", "feast_set_subspace", "feast_destroy", "feast_strerror",
            "feast_zgetrf_batched", "feast_zgetrs_batched", "feast_zqz_batched",
-           "feast_zqz_work_bytes", "feast_kernel_launches",
+           "feast_zqz_work_bytes", "feast_kernel_launches", "feast_zqz_batched_noalloc",
            "feast_batch_workspace_size", "feast_solve_batch"]
 
 
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         lib.feast_zqz_batched.argtypes = [I, I, P, P, P, P, P, P, P, P]
         lib.feast_zqz_work_bytes.argtypes = [I, I]
         lib.feast_zqz_work_bytes.restype = C.c_size_t
+        lib.feast_zqz_batched_noalloc.argtypes = [I, I, P, P, P, P, P, P, P]
         lib.feast_batch_workspace_size.argtypes = [I, C.POINTER(Pencil), C.POINTER(Contour),
                                                    C.POINTER(Options), I]
         lib.feast_batch_workspace_size.restype = C.c_size_t
@@ -350,6 +351,29 @@ def zqz_batched(A_list, B_list, stream=None):
     stv = st.cpu().numpy()
     if stv[1]:
         raise FeastError(-6, "feast_zqz_batched")
+    return (al.cpu().numpy().reshape(batch, m), be.cpu().numpy().reshape(batch, m), Vs,
+            int(stv[0]))
+
+
+def zqz_batched_noalloc(A_list, B_list, stream=None):
+    """zqz_batched through the entry point that allocates nothing on the
+    device (scratch from the library's fixed array; m <= 64)."""
+    torch = _torch()
+    lib = load()
+    m = np.asarray(A_list[0]).shape[0]
+    batch = len(A_list)
+    ab = torch.cat([to_device_colmajor(A) for A in A_list])
+    bb = torch.cat([to_device_colmajor(B) for B in B_list])
+    al = torch.zeros(batch * m, dtype=torch.complex128, device="cuda")
+    be = torch.zeros_like(al)
+    V = torch.zeros(batch * m * m, dtype=torch.complex128, device="cuda")
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    _check(lib.feast_zqz_batched_noalloc(m, batch, ab.data_ptr(), bb.data_ptr(), al.data_ptr(),
+                                         be.data_ptr(), V.data_ptr(), st.data_ptr(),
+                                         _stream_ptr(stream)), "feast_zqz_batched_noalloc")
+    torch.cuda.current_stream().synchronize()
+    Vs = [from_device_colmajor(V[b * m * m:(b + 1) * m * m], m, m) for b in range(batch)]
+    stv = st.cpu().numpy()
     return (al.cpu().numpy().reshape(batch, m), be.cpu().numpy().reshape(batch, m), Vs,
             int(stv[0]))
 
