@@ -176,6 +176,20 @@ int feast_set_subspace(feast_ctx *ctx, const void *U1);
 void feast_destroy(feast_ctx *ctx);
 const char *feast_strerror(int status);
 
+/* Complex64 GEMM on the 5th-generation tensor cores (tcgen05, TF32 inputs
+ * with a head/tail split of each operand for ~FP32 accuracy, FP32
+ * accumulation in tensor memory): C_b = beta C_b + alpha A_b X_b for b <
+ * batch, column-major interleaved complex64, A m x k, X k x n.  This is the
+ * update product of the complex64 factorization and solves of eq. 4.2 in the
+ * precision form.  scratch: device, >= feast_cgemm_tc_scratch_bytes bytes
+ * (operand copies in the tensor-core layout).  err: device int32, set to 1
+ * if a bounded pipeline wait gave up.  Asynchronous. */
+size_t feast_cgemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int batch);
+int feast_cgemm_tc(int64_t m, int64_t n, int64_t k, float alpha_re, float alpha_im, const void *A,
+                   int64_t lda, int64_t sA, const void *X, int64_t ldx, int64_t sX, float beta_re,
+                   float beta_im, void *C, int64_t ldc, int64_t sC, int batch, void *scratch,
+                   size_t scratch_bytes, int *err, void *stream);
+
 /* ---------------------------------------------------------- ragged batch */
 
 /* Per-pencil outcome of feast_solve_batch. */

@@ -77,7 +77,8 @@ EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs",
            "feast_filter", "feast_set_subspace", "feast_destroy", "feast_strerror",
            "feast_zgetrf_batched", "feast_zgetrs_batched", "feast_zqz_batched",
            "feast_zqz_work_bytes", "feast_kernel_launches", "feast_zqz_batched_noalloc",
-           "feast_batch_workspace_size", "feast_solve_batch"]
+           "feast_batch_workspace_size", "feast_solve_batch", "feast_cgemm_tc_scratch_bytes",
+           "feast_cgemm_tc"]
 
 
 def lib_path() -> str:
@@ -121,6 +122,11 @@ def load(build_if_missing: bool = True):
         lib.feast_batch_workspace_size.restype = C.c_size_t
         lib.feast_solve_batch.argtypes = [I, C.POINTER(Pencil), C.POINTER(Contour), C.POINTER(Options),
                                           P, C.c_size_t, I, C.POINTER(BatchItem), P, P]
+        lib.feast_cgemm_tc_scratch_bytes.argtypes = [I64, I64, I64, I]
+        lib.feast_cgemm_tc_scratch_bytes.restype = C.c_size_t
+        F = C.c_float
+        lib.feast_cgemm_tc.argtypes = [I64, I64, I64, F, F, P, I64, I64, P, I64, I64, F, F, P, I64, I64,
+                                       I, P, C.c_size_t, P, P]
         lib.feast_kernel_launches.argtypes = []
         lib.feast_kernel_launches.restype = C.c_ulonglong
         _lib = lib
@@ -430,3 +436,30 @@ def solve_batch(problems, nworkers: int = 16, device="cuda"):
         bad = [i for i, o in enumerate(out) if o["status"] != 0]
         raise FeastError(st, f"feast_solve_batch (pencils {bad[:8]})")
     return out
+
+
+def cgemm_tc(A_list, X_list, C_list=None, alpha=1.0, beta=0.0, stream=None):
+    """complex64 C = beta C + alpha A X on tensor cores for each batch member."""
+    torch = _torch()
+    lib = load()
+    batch = len(A_list)
+    m, k = np.asarray(A_list[0]).shape
+    n = np.asarray(X_list[0]).shape[1]
+    c64 = torch.complex64
+    Ad = torch.cat([to_device_colmajor(np.asarray(A, np.complex64), dtype=c64) for A in A_list])
+    Xd = torch.cat([to_device_colmajor(np.asarray(X, np.complex64), dtype=c64) for X in X_list])
+    if C_list is None:
+        Cd = torch.zeros(batch * m * n, dtype=torch.complex64, device="cuda")
+    else:
+        Cd = torch.cat([to_device_colmajor(np.asarray(Cc, np.complex64), dtype=c64) for Cc in C_list])
+    nb = int(lib.feast_cgemm_tc_scratch_bytes(m, n, k, batch))
+    sc = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a, b = complex(alpha), complex(beta)
+    _check(lib.feast_cgemm_tc(m, n, k, a.real, a.imag, Ad.data_ptr(), m, m * k, Xd.data_ptr(), k, k * n,
+                              b.real, b.imag, Cd.data_ptr(), m, m * n, batch, sc.data_ptr(), nb,
+                              err.data_ptr(), _stream_ptr(stream)), "feast_cgemm_tc")
+    torch.cuda.current_stream().synchronize()
+    if int(err.item()):
+        raise FeastError(-6, "feast_cgemm_tc")
+    return [from_device_colmajor(Cd[b_ * m * n:(b_ + 1) * m * n], m, n) for b_ in range(batch)]

@@ -137,6 +137,46 @@ void count_launch();
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
+// ---------------------------------------------------------------- grid barrier
+constexpr long long SPIN_LIMIT = 1ll << 24;
+struct GridSync {
+    unsigned *count;
+    unsigned *gen;
+    int *err;
+};
+
+// Sense-counting grid barrier for a cooperative launch, with a bounded spin:
+// on timeout it raises *err and returns (every caller then bails out).
+__device__ __forceinline__ bool grid_barrier(const GridSync &g)
+{
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = g.gen;
+        const unsigned my = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(g.count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            *g.count = 0;
+            __threadfence();
+            atomicAdd(g.gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == my) {
+                if (++it > SPIN_LIMIT || *(volatile int *)g.err) { ok = 0; atomicExch(g.err, 1); break; }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();
+        s_ok = ok && !*(volatile int *)g.err;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+
+
 // ---------------------------------------------------------------- kernels (FP64)
 // Templated dense kernels (T = double2 or float2), instantiated in k_dense.cu.
 template <typename T>
@@ -189,8 +229,9 @@ int znode_sum(cudaStream_t s, int64_t n, int64_t m, int q, const zd *w, const zd
 
 // Thin QR by block classical Gram-Schmidt with re-orthogonalisation:
 // V (n x m, overwritten by Q), R (m x m upper, real positive diagonal).
+// timeout: flag raised if a grid barrier of the tall-panel form gives up
 int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr,
-          zd *work);
+          zd *work, int *timeout);
 size_t zorth_work_elems(int64_t n, int64_t m);
 
 // Batched projected eigensolve: alpha / beta eigenvalue pairs and unit right
@@ -261,6 +302,18 @@ int gb_matmul(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *M, in
 int gb_residual(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *A, const zd *B,
                 int64_t ldin, int q, const zd *z, int64_t m, const zd *RHS, const zd *X, zd *R,
                 double *nrm2);
+
+// Tensor-core complex64 GEMM (k_tc.cu): C_b = beta C_b + alpha A_b X_b on
+// tcgen05 (kind::tf32, 3-pass split); scratch of tc_scratch_floats floats.
+size_t tc_scratch_floats(int64_t m, int64_t k, int64_t n, int batch);
+int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf *A, int64_t lda,
+             int64_t sA, const cf *X, int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC,
+             int batch, float *scratch, int *err);
+// complex64 LU whose trailing updates run on tc_cgemm (pivots and factors as
+// getrf_batched<cf>); scratch of getrf_tc_scratch_floats floats.
+size_t getrf_tc_scratch_floats(int64_t n, int batch);
+int getrf_batched_tc(cudaStream_t s, int64_t n, int batch, cf *F, int64_t ldf, int64_t sF, int *piv,
+                     int *info, int *row, float *scratch, int *tc_err);
 
 // Contour nodes / weights on the device.
 int contour_nodes(cudaStream_t s, const feast_contour *c, zd *z, zd *w);

@@ -58,6 +58,7 @@ struct feast_ctx {
     DevStatus *st;
     // precision form
     cf *F32;            // q x n x n complex64 factors
+    float *tcs;         // tensor-core LU operand scratch (complex64 dense)
     cf *Mhi, *Mlo;      // q x n x n double-single split of z_j B - A
     cf *Xhi, *Xlo;      // q x n x m0 split of the solutions (Xhi doubles as R32)
     cf *C32;            // q x n x m0 low-precision solves / corrections
@@ -142,6 +143,7 @@ void carve(feast_ctx *c, Carver &cv)
         c->F = cv.take<zd>(q * n * n);
     } else {
         c->F32 = cv.take<cf>(q * n * n);
+        c->tcs = cv.take<float>(getrf_tc_scratch_floats((int64_t)n, (int)q));
         c->Mhi = cv.take<cf>(q * n * n);
         c->Mlo = cv.take<cf>(q * n * n);
         c->Xhi = cv.take<cf>(q * n * m);
@@ -366,11 +368,11 @@ int orthonormalise(feast_ctx *c, const zd *Usrc)
     int e;
     if (Usrc != c->U1)
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->U1, Usrc, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    if ((e = zorth(c->s, n, m, c->U1, n, c->R1, m, c->orth_work))) return e;
+    if ((e = zorth(c->s, n, m, c->U1, n, c->R1, m, c->orth_work, &c->st->timeout))) return e;
     zd *BU1 = c->W + n * m;
     if ((e = apply_B(c, c->U1, BU1, m))) return e;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work);
+    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work, &c->st->timeout);
 }
 
 }  // namespace
@@ -440,7 +442,8 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
         TRY(zgetrf_batched(s, n, c->q, c->F, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row));
     } else {
         TRY(form_shifted_split(s, n, c->q, c->A, c->B, n, c->z, c->F32, c->Mhi, c->Mlo));
-        TRY(getrf_batched<cf>(s, n, c->q, c->F32, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row));
+        TRY(getrf_batched_tc(s, n, c->q, c->F32, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row, c->tcs,
+                             &c->st->timeout));
     }
     if (c->kind == FEAST_DENSE) TRY(zpiv_to_perm(s, n, c->q, c->piv, c->perm));
     CTRY(cudaEventRecord(c->ev[1], s));
@@ -461,6 +464,10 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
     if (hs.lu_info) {
         feast_destroy(c);
         return FEAST_ESINGULAR;
+    }
+    if (hs.timeout) {
+        feast_destroy(c);
+        return FEAST_ETIMEOUT;
     }
     c->k = 0;
     c->c_prev = 0;
@@ -614,7 +621,7 @@ int feast_set_subspace(feast_ctx *c, const void *U1)
     int e = apply_B(c, c->U1, BU1, m);
     if (e) return e;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work);
+    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work, &c->st->timeout);
 }
 
 void feast_destroy(feast_ctx *c)
@@ -742,6 +749,27 @@ int feast_zgetrs_batched(int64_t n, int64_t nrhs, int batch, const void *M, int6
     if (n < 0 || nrhs < 0 || batch < 0 || ld < n || ldx < n || !M || !piv || !X) return FEAST_EINVAL;
     return zgetrs_batched((cudaStream_t)stream, n, nrhs, batch, (const zd *)M, ld, stride, piv, (zd *)X,
                           ldx, sx);
+}
+
+size_t feast_cgemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int batch)
+{
+    if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return 0;
+    return sizeof(float) * tc_scratch_floats(m, k, n, batch) + 256;
+}
+
+int feast_cgemm_tc(int64_t m, int64_t n, int64_t k, float alpha_re, float alpha_im, const void *A,
+                   int64_t lda, int64_t sA, const void *X, int64_t ldx, int64_t sX, float beta_re,
+                   float beta_im, void *C, int64_t ldc, int64_t sC, int batch, void *scratch,
+                   size_t scratch_bytes, int *err, void *stream)
+{
+    if (m < 0 || n < 0 || k < 0 || batch < 0 || !A || !X || !C || !scratch || !err) return FEAST_EINVAL;
+    if (lda < m || ldx < k || ldc < m) return FEAST_EINVAL;
+    if (scratch_bytes < feast_cgemm_tc_scratch_bytes(m, n, k, batch)) return FEAST_ENOMEM;
+    float *sc = (float *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+    cudaStream_t s = (cudaStream_t)stream;
+    FEAST_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    return tc_cgemm(s, m, n, k, make_float2(alpha_re, alpha_im), (const cf *)A, lda, sA, (const cf *)X, ldx, sX,
+                    make_float2(beta_re, beta_im), (cf *)C, ldc, sC, batch, sc, err);
 }
 
 size_t feast_zqz_work_bytes(int m, int batch)

@@ -199,6 +199,7 @@ int zform_shifted(cudaStream_t s, int64_t n, int q, const zd *A, const zd *B, in
 namespace {
 constexpr int LU_NB = 32;     // panel width
 constexpr int LU_PT = 512;    // panel threads
+constexpr int LU_NBO = 256;   // outer block of the tensor-core LU
 
 // Factor the panel [k0, k0 + nb) x [k0, n) of every batch member: pivot by
 // largest modulus (ties -> smallest row), swap within the panel columns,
@@ -296,9 +297,9 @@ __global__ void k_laswp_outside(int64_t n, int64_t k0, int nb, T *F, int64_t ldf
 }
 
 // U12 = L11^{-1} A12 for the nb rows of the panel (L11 unit lower), one
-// thread per column to the right of the panel.
+// thread per column in [cbeg, cend).
 template <typename T>
-__global__ void k_trsm_u12(int64_t n, int64_t k0, int nb, T *F, int64_t ldf, int64_t sF)
+__global__ void k_trsm_u12(int64_t cbeg, int64_t cend, int64_t k0, int nb, T *F, int64_t ldf, int64_t sF)
 {
     const int b = blockIdx.y;
     T *Am = F + (int64_t)b * sF;
@@ -308,8 +309,8 @@ __global__ void k_trsm_u12(int64_t n, int64_t k0, int nb, T *F, int64_t ldf, int
         L[r][c] = Am[(k0 + r) + (k0 + c) * ldf];
     }
     __syncthreads();
-    const int64_t c = k0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    const int64_t c = cbeg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cend) return;
     T x[LU_NB];
 #pragma unroll
     for (int r = 0; r < LU_NB; ++r)
@@ -341,7 +342,7 @@ int getrf_batched(cudaStream_t s, int64_t n, int batch, T *F, int64_t ldf, int64
         FEAST_LAUNCH_CHECK();
         int64_t rest = n - k0 - nb;
         if (rest > 0) {
-            k_trsm_u12<T><<<dim3(cdiv(rest, 128), batch), 128, 0, s>>>(n, k0, nb, F, ldf, sF);
+            k_trsm_u12<T><<<dim3(cdiv(rest, 128), batch), 128, 0, s>>>(k0 + nb, n, k0, nb, F, ldf, sF);
             FEAST_LAUNCH_CHECK();
             int e = gemm_batched<T>(s, 0, rest, rest, nb, cx<T>(-1, 0), F + k0 + nb + k0 * ldf,
                                     ldf, sF, F + k0 + (k0 + nb) * ldf, ldf, sF, cx<T>(1, 0),
@@ -352,6 +353,67 @@ int getrf_batched(cudaStream_t s, int64_t n, int batch, T *F, int64_t ldf, int64
     return FEAST_OK;
 }
 template int getrf_batched<double2>(cudaStream_t, int64_t, int, double2 *, int64_t, int64_t, int *, int *, int *);
+
+// complex64 LU with the bulk of its flops on the tensor cores.  Two-level
+// right-looking blocking: an outer block of LU_NBO columns is factored with
+// the LU_NB-wide panel kernel as above, except that each inner rank-LU_NB
+// update is confined to the outer block's columns (all rows below) and to
+// the outer block's rows (columns beyond it); the trailing matrix then takes
+// one rank-LU_NBO update A22 -= L21 U12 through the tcgen05 GEMM.  The
+// factors and pivots are those of the one-level routine up to rounding.
+size_t getrf_tc_scratch_floats(int64_t n, int batch)
+{
+    return tc_scratch_floats(n, LU_NBO, n, batch);
+}
+
+int getrf_batched_tc(cudaStream_t s, int64_t n, int batch, cf *F, int64_t ldf, int64_t sF, int *piv,
+                     int *info, int *row, float *scratch, int *tc_err)
+{
+    if (n <= 0 || batch <= 0) return FEAST_OK;
+    const cf mone = cx<cf>(-1, 0), one = cx<cf>(1, 0);
+    int e;
+    for (int64_t k0 = 0; k0 < n; k0 += LU_NBO) {
+        const int64_t nbo = (n - k0) < LU_NBO ? (n - k0) : LU_NBO;
+        const int64_t kend = k0 + nbo;                  // first column after the outer block
+        for (int64_t kk = k0; kk < kend; kk += LU_NB) {
+            const int nb = (int)((kend - kk) < LU_NB ? (kend - kk) : LU_NB);
+            k_lu_panel<cf><<<batch, LU_PT, 0, s>>>(n, kk, nb, F, ldf, sF, piv, n, info, row);
+            FEAST_LAUNCH_CHECK();
+            k_laswp_outside<cf><<<dim3(cdiv(n, 128), batch), 128, 0, s>>>(n, kk, nb, F, ldf, sF, piv);
+            FEAST_LAUNCH_CHECK();
+            const int64_t c1 = kk + nb;                 // first column right of the panel
+            if (kend > c1) {
+                // inside the outer block only: columns beyond it keep their
+                // original values (row swaps included) until the block is done
+                k_trsm_u12<cf><<<dim3(cdiv(kend - c1, 128), batch), 128, 0, s>>>(c1, kend, kk, nb, F, ldf, sF);
+                FEAST_LAUNCH_CHECK();
+                if ((e = gemm_batched<cf>(s, 0, n - c1, kend - c1, nb, mone, F + c1 + kk * ldf, ldf, sF,
+                                          F + kk + c1 * ldf, ldf, sF, one, F + c1 + c1 * ldf, ldf, sF, batch)))
+                    return e;
+            }
+        }
+        const int64_t rest = n - kend;
+        if (rest <= 0) break;
+        // U12 = L11^{-1} A12 for the columns beyond the block, LU_NB rows at a time
+        for (int64_t kk = k0; kk < kend; kk += LU_NB) {
+            const int nb = (int)((kend - kk) < LU_NB ? (kend - kk) : LU_NB);
+            k_trsm_u12<cf><<<dim3(cdiv(rest, 128), batch), 128, 0, s>>>(kend, n, kk, nb, F, ldf, sF);
+            FEAST_LAUNCH_CHECK();
+            const int64_t r1 = kk + nb;
+            if (r1 < kend) {
+                if ((e = gemm_batched<cf>(s, 0, kend - r1, rest, nb, mone, F + r1 + kk * ldf, ldf, sF,
+                                          F + kk + kend * ldf, ldf, sF, one, F + r1 + kend * ldf, ldf, sF,
+                                          batch)))
+                    return e;
+            }
+        }
+        // A22 -= L21 U12   (rest x rest, inner dimension nbo)
+        if ((e = tc_cgemm(s, rest, rest, nbo, mone, F + kend + k0 * ldf, ldf, sF, F + k0 + kend * ldf, ldf, sF,
+                          one, F + kend + kend * ldf, ldf, sF, batch, scratch, tc_err)))
+            return e;
+    }
+    return FEAST_OK;
+}
 
 // Factor only the leading panel (columns 0..nb-1, all rows) of each batch
 // member; pivots at piv[b * pstride + k].

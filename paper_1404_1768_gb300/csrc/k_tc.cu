@@ -1,0 +1,363 @@
+// Tensor-core (tcgen05, kind::tf32) complex64 GEMM for sm_103a.
+//
+//   C_b = beta C_b + alpha A_b X_b     (A: m x k, X: k x n, C: m x n complex64,
+//                                       column-major, interleaved re/im)
+//
+// Complex arithmetic as one real GEMM: every complex row i of A becomes two
+// real rows of A' (length 2k, K contiguous):
+//   A'(2i,   2p) =  Re A(i,p)   A'(2i,   2p+1) = -Im A(i,p)
+//   A'(2i+1, 2p) =  Im A(i,p)   A'(2i+1, 2p+1) =  Re A(i,p)
+// and X (column-major, interleaved) already is the real K-major operand
+// X'(2p + c, j).  Then D' = A' X' holds Re(AX)(i,j) in row 2i and Im in
+// row 2i+1, so one tcgen05 accumulator tile of 128 real rows covers 64
+// complex rows.  For ~FP32 accuracy each operand is split into a TF32 head
+// and a TF32 tail (3 products: hh + ht + th).
+//
+// Per CTA: one 128 x BN tile of D'.  Warp 0 (one lane) feeds a STAGES-deep
+// ring of 128B-swizzled shared-memory tiles with TMA (cp.async.bulk.tensor,
+// completion on an mbarrier); warp 1 (one lane) issues tcgen05.mma into a
+// TMEM accumulator and frees each stage with tcgen05.commit; all four warps
+// then read their 32 TMEM lanes (tcgen05.ld), pair re/im rows across
+// neighbouring lanes and write C.  Every mbarrier wait has an iteration cap;
+// on expiry the kernel raises an error word and finishes without hanging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace feast {
+
+namespace {
+
+constexpr int TC_BM = 128;          // real rows per tile (= 64 complex rows)
+constexpr int TC_BK = 32;           // fp32 per 128-byte swizzle row
+constexpr int TC_STAGES = 3;
+constexpr long long TC_SPIN = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < TC_SPIN; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                            int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// K-major operand tile, 128-byte swizzle, rows 128 bytes apart, 8-row groups
+// 1024 bytes apart (descriptor version 1, layout type 2 = SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sdesc(const void *p)
+{
+    const uint64_t a = (smem_u32(p) >> 4) & 0x3FFFull;
+    return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_tc_cgemm(const __grid_constant__ CUtensorMap tAh,
+                                                  const __grid_constant__ CUtensorMap tAt,
+                                                  const __grid_constant__ CUtensorMap tXh,
+                                                  const __grid_constant__ CUtensorMap tXt, int mr,
+                                                  int n, int kr, float2 *C, int64_t ldc, int64_t sC,
+                                                  float2 alpha, float2 beta, int *err)
+{
+    constexpr int A_BYTES = TC_BM * TC_BK * 4;          // 16 KiB
+    constexpr int B_BYTES = BN * TC_BK * 4;
+    constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bz = blockIdx.z;
+    const int row0 = blockIdx.x * TC_BM;                 // real row
+    const int col0 = blockIdx.y * BN;
+    const int kb_n = (kr + TC_BK - 1) / TC_BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        for (int kb = 0; kb < kb_n; ++kb) {
+            const int s = kb % TC_STAGES;
+            const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+            if (!mbar_wait(&empty[s], ph ^ 1u)) { s_fail = 1; break; }
+            unsigned char *st = base + s * STAGE;
+            mbar_expect_tx(&full[s], STAGE);
+            const int kx = kb * TC_BK;
+            tma_load_3d(st, &tAh, &full[s], kx, row0, bz);
+            tma_load_3d(st + A_BYTES, &tAt, &full[s], kx, row0, bz);
+            tma_load_3d(st + 2 * A_BYTES, &tXh, &full[s], kx, col0, bz);
+            tma_load_3d(st + 2 * A_BYTES + B_BYTES, &tXt, &full[s], kx, col0, bz);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: D = M=128 x N=BN, K=8 per instruction, 4 per stage
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                               ((uint32_t)(TC_BM >> 4) << 24);
+        bool ok = true;
+        for (int kb = 0; kb < kb_n && ok; ++kb) {
+            const int s = kb % TC_STAGES;
+            const uint32_t ph = (uint32_t)((kb / TC_STAGES) & 1);
+            if (!mbar_wait(&full[s], ph)) { s_fail = 1; ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            unsigned char *st = base + s * STAGE;
+            const uint64_t ah = sdesc(st), at = sdesc(st + A_BYTES);
+            const uint64_t xh = sdesc(st + 2 * A_BYTES), xt = sdesc(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 8; ++kk) {
+                const uint64_t adv = (uint64_t)((kk * 8 * 4) >> 4);   // 32 bytes per step
+                const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+                mma_tf32(tmem, ah + adv, xh + adv, idesc, acc0);
+                mma_tf32(tmem, ah + adv, xt + adv, idesc, 1u);
+                mma_tf32(tmem, at + adv, xh + adv, idesc, 1u);
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(&done);
+    }
+    __syncwarp();
+    // epilogue: all warps wait for the accumulator
+    bool good = mbar_wait(&done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!good || s_fail) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else {
+        const int r = row0 + warp * 32 + lane;            // real row of this lane
+        const int ci = r >> 1;                             // complex row
+        const bool im_row = (r & 1) != 0;
+        float2 *Cb = C + (int64_t)bz * sC;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                  "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                  "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // even lane (Re row) stores columns 0..15 of this chunk, odd lane
+            // (Im row) stores 16..31; each needs its partner's values
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float mine = __uint_as_float(v[j]);
+                const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                const int half = im_row ? 1 : 0;
+                if ((j >> 4) == half) {
+                    const int col = col0 + c0 + j;
+                    if (r < mr && col < n) {
+                        const float re = im_row ? other : mine;
+                        const float im = im_row ? mine : other;
+                        float2 *dst = Cb + ci + (int64_t)col * ldc;
+                        float2 o = *dst;
+                        float2 res;
+                        res.x = alpha.x * re - alpha.y * im + beta.x * o.x - beta.y * o.y;
+                        res.y = alpha.x * im + alpha.y * re + beta.x * o.y + beta.y * o.x;
+                        *dst = res;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+// A (m x k complex, column-major, ld) -> head / tail of A' (2m x 2k real,
+// row-major with leading dim ldr), batched.
+__global__ void k_realify_split(int m, int k, const float2 *A, int64_t lda, int64_t sA, float *head,
+                                float *tail, int64_t ldr, int64_t sR)
+{
+    const int b = blockIdx.y;
+    const float2 *Ab = A + (int64_t)b * sA;
+    float *H = head + (int64_t)b * sR, *Tt = tail + (int64_t)b * sR;
+    const int64_t total = (int64_t)m * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), p = (int)(e / m);
+        const float2 a = Ab[i + (int64_t)p * lda];
+        const float v[4] = {a.x, -a.y, a.y, a.x};   // (2i,2p) (2i,2p+1) (2i+1,2p) (2i+1,2p+1)
+        const int64_t o[4] = {(int64_t)(2 * i) * ldr + 2 * p, (int64_t)(2 * i) * ldr + 2 * p + 1,
+                              (int64_t)(2 * i + 1) * ldr + 2 * p, (int64_t)(2 * i + 1) * ldr + 2 * p + 1};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float h = __uint_as_float(__float_as_uint(v[t]) & 0xFFFFE000u);  // TF32 head (truncated)
+            H[o[t]] = h;
+            Tt[o[t]] = v[t] - h;
+        }
+    }
+}
+
+// X (k x n complex, column-major, ld) -> head / tail (same layout, as reals)
+__global__ void k_split_tf32(int64_t rows2, int n, const float *X, int64_t ldx2, int64_t sX, float *head,
+                             float *tail, int64_t ldh2, int64_t sH)
+{
+    const int b = blockIdx.y;
+    const float *Xb = X + (int64_t)b * sX;
+    float *H = head + (int64_t)b * sH, *Tt = tail + (int64_t)b * sH;
+    const int64_t total = rows2 * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e % rows2, c = e / rows2;
+        const float v = Xb[r + c * ldx2];
+        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        H[r + c * ldh2] = h;
+        Tt[r + c * ldh2] = v - h;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 3-D fp32 tensor map: dims {inner, rows, batch}, box {32, box_rows, 1},
+// 128-byte swizzle, zero fill out of bounds.
+int make_map(CUtensorMap *map, const float *base, int64_t inner, int64_t rows, int64_t batch,
+             int64_t ld_bytes, int64_t batch_bytes, int box_rows)
+{
+    auto enc = get_encode();
+    if (!enc) return FEAST_ECUDA;
+    if (((uintptr_t)base & 15) || (ld_bytes & 15) || (batch_bytes & 15)) return FEAST_EINVAL;
+    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)ld_bytes, (cuuint64_t)(batch_bytes > 0 ? batch_bytes : ld_bytes * rows)};
+    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FEAST_OK : FEAST_EINVAL;
+}
+}  // namespace
+
+constexpr int TC_BN = 128;
+
+size_t tc_scratch_floats(int64_t m, int64_t k, int64_t n, int batch)
+{
+    const int64_t kr = ((2 * k + TC_BK - 1) / TC_BK) * TC_BK;
+    const int64_t mr = 2 * m;
+    return (size_t)batch * (2 * (size_t)mr * kr + 2 * (size_t)kr * n);
+}
+
+// C_b = beta C_b + alpha A_b X_b on tensor cores (see the file comment).
+// scratch: tc_scratch_floats(m, k, n, batch) floats (16-byte aligned).
+int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf *A, int64_t lda,
+             int64_t sA, const cf *X, int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC,
+             int batch, float *scratch, int *err)
+{
+    if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return FEAST_OK;
+    const int64_t kr = ((2 * k + TC_BK - 1) / TC_BK) * TC_BK;   // padded real K
+    const int64_t mr = 2 * m;
+    float *Ah = scratch, *At = Ah + (size_t)batch * mr * kr;
+    float *Xh = At + (size_t)batch * mr * kr, *Xt = Xh + (size_t)batch * kr * n;
+    // operand preparation: A' head/tail (pad columns, if any, zeroed first),
+    // X head/tail as K-major real columns of length kr
+    if (kr != 2 * k) {
+        FEAST_CUDA_TRY(cudaMemsetAsync(Ah, 0, sizeof(float) * 2 * (size_t)batch * mr * kr, s));
+        FEAST_CUDA_TRY(cudaMemsetAsync(Xh, 0, sizeof(float) * 2 * (size_t)batch * kr * n, s));
+    }
+    {
+        unsigned g = cdiv((size_t)m * k, 256);
+        k_realify_split<<<dim3(g > 4096 ? 4096 : g, batch), 256, 0, s>>>((int)m, (int)k, A, lda, sA, Ah, At, kr,
+                                                                         mr * kr);
+        FEAST_LAUNCH_CHECK();
+        unsigned g2 = cdiv((size_t)2 * k * n, 256);
+        k_split_tf32<<<dim3(g2 > 4096 ? 4096 : g2, batch), 256, 0, s>>>(2 * k, (int)n, (const float *)X, 2 * ldx,
+                                                                        2 * sX, Xh, Xt, kr, kr * n);
+        FEAST_LAUNCH_CHECK();
+    }
+    CUtensorMap mAh, mAt, mXh, mXt;
+    int e;
+    if ((e = make_map(&mAh, Ah, kr, mr, batch, kr * 4, mr * kr * 4, TC_BM))) return e;
+    if ((e = make_map(&mAt, At, kr, mr, batch, kr * 4, mr * kr * 4, TC_BM))) return e;
+    if ((e = make_map(&mXh, Xh, kr, n, batch, kr * 4, kr * n * 4, TC_BN))) return e;
+    if ((e = make_map(&mXt, Xt, kr, n, batch, kr * 4, kr * n * 4, TC_BN))) return e;
+    const size_t smem = (size_t)TC_STAGES * (2 * TC_BM * TC_BK * 4 + 2 * TC_BN * TC_BK * 4) + 1024;
+    FEAST_CUDA_TRY(cudaFuncSetAttribute(k_tc_cgemm<TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(cdiv(mr, TC_BM), cdiv(n, TC_BN), batch);
+    k_tc_cgemm<TC_BN><<<grid, 128, smem, s>>>(mAh, mAt, mXh, mXt, (int)mr, (int)n, (int)kr, C, ldc, sC, alpha,
+                                              beta, err);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+}  // namespace feast

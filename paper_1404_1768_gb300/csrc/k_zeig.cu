@@ -7,13 +7,14 @@
 //   1. Hessenberg reduction C = Q H Q^H by Householder reflectors, one
 //      column per step, each step a handful of grid-wide kernels;
 //   2. single-shift complex QR sweeps on H with deflation, accumulating the
-//      Schur vectors into Q.  A sweep's rotations form a dependent chain,
-//      so they are generated in chunks of CH rotations by one warp on a small
-//      diagonal block held in shared memory, and the rest of each rotation
-//      (the long row / column / Schur-vector segments, which no later
-//      rotation of the chunk reads) is applied by the whole grid in one
-//      parallel pass.  The grid is a cooperative launch; its barriers spin
-//      with an iteration limit and report a timeout instead of hanging;
+//      Schur vectors into Q, in double-single arithmetic (~46 bits) on the
+//      FP32 pipe.  A sweep's rotations form a dependent chain, so they are
+//      generated in chunks of CH rotations by one warp on a small diagonal
+//      block held in shared memory, and the rest of each rotation (the long
+//      row / column / Schur-vector segments, which no later rotation of the
+//      chunk reads) is applied by the whole grid in one parallel pass.  The
+//      grid is a cooperative launch; its barriers spin with an iteration
+//      limit and report a timeout instead of hanging;
 //   3. right eigenvectors of the triangular Schur form by back-substitution
 //      (one warp per eigenvector), mapped back by Q (a GEMM), unit norm.
 // The small-pencil path (m0 <= 64, one warp, shared memory) is the QZ
@@ -29,7 +30,6 @@ namespace {
 constexpr int CH = 32;           // rotations per chunk
 constexpr int BLK = CH + 3;      // local block edge
 constexpr int QT = 256;          // threads per CTA of the QR kernel
-constexpr long long SPIN_LIMIT = 1ll << 24;
 
 // ------------------------------------------------------------- Householder
 // v = x - beta e1 with beta = -(x0/|x0|) ||x||, tau = 2 / ||v||^2, for
@@ -137,126 +137,195 @@ __global__ void k_eye(int m, zd *Q, int ld)
 }
 
 // ------------------------------------------------------------- QR sweeps
-struct GridSync {
-    unsigned *count;
-    unsigned *gen;
-    int *err;
+// ---------------------------------------------------------- double-single
+// The QR sweeps run in double-single arithmetic (a value is an unevaluated
+// sum h + l of two floats, ~46 significant bits) on the FP32 pipe: on
+// GB300 a warp-wide FP64 instruction issues about 64x slower than an FP32
+// one, and the chase is a chain of dependent rotations.  Error-free
+// transformations use explicit round-to-nearest intrinsics so that the
+// compiler cannot contract them into FMAs.
+struct ds {
+    float h, l;
+};
+struct cds {
+    ds re, im;
 };
 
-// Sense-counting grid barrier for a cooperative launch, with a bounded spin:
-// on timeout it raises *err and returns (every caller then bails out).
-__device__ bool grid_barrier(const GridSync &g)
+__device__ __forceinline__ ds ds_make(float h, float l) { ds r; r.h = h; r.l = l; return r; }
+__device__ __forceinline__ ds ds_qts(float a, float b)   // |a| >= |b|
 {
-    __syncthreads();
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        volatile unsigned *vgen = g.gen;
-        const unsigned my = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(g.count, 1u);
-        int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            *g.count = 0;
-            __threadfence();
-            atomicAdd(g.gen, 1u);
-        } else {
-            long long it = 0;
-            while (*vgen == my) {
-                if (++it > SPIN_LIMIT || *(volatile int *)g.err) { ok = 0; atomicExch(g.err, 1); break; }
-                __nanosleep(20);
-            }
-        }
-        __threadfence();
-        s_ok = ok && !*(volatile int *)g.err;
-    }
-    __syncthreads();
-    return s_ok != 0;
+    float s = __fadd_rn(a, b);
+    return ds_make(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
-
-struct Rot {
-    double c;
-    zd s;
-};
-
-__device__ __forceinline__ Rot make_rot(zd x, zd y)
+__device__ __forceinline__ ds ds_add(ds x, ds y)
 {
-    double ax = zabs(x), ay = zabs(y);
-    Rot r;
-    if (ay == 0.0) { r.c = 1.0; r.s = zmake(0.0, 0.0); return r; }
-    if (ax == 0.0) { r.c = 0.0; r.s = zmake(1.0, 0.0); return r; }
-    double h = hypot(ax, ay);
-    r.c = ax / h;
-    r.s = zscale(zmul(zscale(x, 1.0 / ax), zconj(y)), 1.0 / h);
+    float s = __fadd_rn(x.h, y.h);
+    float bb = __fsub_rn(s, x.h);
+    float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(y.h, bb));
+    e = __fadd_rn(e, __fadd_rn(x.l, y.l));
+    return ds_qts(s, e);
+}
+__device__ __forceinline__ ds ds_neg(ds x) { return ds_make(-x.h, -x.l); }
+__device__ __forceinline__ ds ds_sub(ds x, ds y) { return ds_add(x, ds_neg(y)); }
+__device__ __forceinline__ ds ds_mul(ds x, ds y)
+{
+    float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return ds_qts(p, e);
+}
+__device__ __forceinline__ ds ds_from(double d)
+{
+    float h = (float)d;
+    return ds_make(h, (float)(d - (double)h));
+}
+__device__ __forceinline__ float ds_approx(ds x) { return x.h; }
+// 1/sqrt(x), x > 0: float seed and one Newton step in double-single
+__device__ __forceinline__ ds ds_rsqrt(ds x)
+{
+    float y0 = rsqrtf(x.h);
+    ds y = ds_make(y0, 0.f);
+    ds t = ds_mul(x, ds_mul(y, y));                 // x y0^2 ~ 1
+    ds e = ds_sub(ds_make(1.f, 0.f), t);            // 1 - x y0^2
+    ds corr = ds_mul(ds_mul(y, e), ds_make(0.5f, 0.f));
+    return ds_add(y, corr);
+}
+__device__ __forceinline__ cds cds_add(cds a, cds b) { cds r; r.re = ds_add(a.re, b.re); r.im = ds_add(a.im, b.im); return r; }
+__device__ __forceinline__ cds cds_sub(cds a, cds b) { cds r; r.re = ds_sub(a.re, b.re); r.im = ds_sub(a.im, b.im); return r; }
+__device__ __forceinline__ cds cds_mul(cds a, cds b)
+{
+    cds r;
+    r.re = ds_sub(ds_mul(a.re, b.re), ds_mul(a.im, b.im));
+    r.im = ds_add(ds_mul(a.re, b.im), ds_mul(a.im, b.re));
     return r;
 }
-// left: [a; b] <- [c a + s b; -conj(s) a + c b]
-__device__ __forceinline__ void rot_left(const Rot &g, zd &a, zd &b)
+__device__ __forceinline__ cds cds_conj(cds a) { cds r; r.re = a.re; r.im = ds_neg(a.im); return r; }
+__device__ __forceinline__ cds cds_scale(cds a, ds s) { cds r; r.re = ds_mul(a.re, s); r.im = ds_mul(a.im, s); return r; }
+__device__ __forceinline__ ds cds_abs2(cds a) { return ds_add(ds_mul(a.re, a.re), ds_mul(a.im, a.im)); }
+__device__ __forceinline__ float cds_absf(cds a) { return hypotf(a.re.h, a.im.h); }
+__device__ __forceinline__ cds cds_zero() { cds r; r.re = ds_make(0.f, 0.f); r.im = r.re; return r; }
+
+// storage: float4 (re.h, re.l, im.h, im.l)
+__device__ __forceinline__ cds ld_cds(const float4 *p)
 {
-    zd na = zadd(zscale(a, g.c), zmul(g.s, b));
-    zd nb = zsub(zscale(b, g.c), zmul(zconj(g.s), a));
+    float4 v = __ldcg(p);
+    cds r;
+    r.re = ds_make(v.x, v.y);
+    r.im = ds_make(v.z, v.w);
+    return r;
+}
+__device__ __forceinline__ void st_cds(float4 *p, cds v) { __stcg(p, make_float4(v.re.h, v.re.l, v.im.h, v.im.l)); }
+
+struct RotDS {
+    ds c;   // real
+    cds s;
+};
+// G = [c s; -conj(s) c] with G [x; y] = [r; 0]
+__device__ __forceinline__ RotDS make_rot_ds(cds x, cds y)
+{
+    RotDS g;
+    ds ax2 = cds_abs2(x), ay2 = cds_abs2(y);
+    if (ay2.h == 0.f) { g.c = ds_make(1.f, 0.f); g.s = cds_zero(); return g; }
+    if (ax2.h == 0.f) { g.c = ds_make(0.f, 0.f); g.s = cds_zero(); g.s.re = ds_make(1.f, 0.f); return g; }
+    ds ia = ds_rsqrt(ax2), ir = ds_rsqrt(ds_add(ax2, ay2));
+    ds k = ds_mul(ia, ir);
+    g.c = ds_mul(ax2, k);                            // |x| / r
+    g.s = cds_scale(cds_mul(x, cds_conj(y)), k);     // (x/|x|) conj(y) / r
+    return g;
+}
+__device__ __forceinline__ void rot_left_ds(const RotDS &g, cds &a, cds &b)
+{
+    cds na = cds_add(cds_scale(a, g.c), cds_mul(g.s, b));
+    cds nb = cds_sub(cds_scale(b, g.c), cds_mul(cds_conj(g.s), a));
     a = na;
     b = nb;
 }
-// right by G^H: [a b] <- [a c + b conj(s), -a s + b c]
-__device__ __forceinline__ void rot_right(const Rot &g, zd &a, zd &b)
+__device__ __forceinline__ void rot_right_ds(const RotDS &g, cds &a, cds &b)
 {
-    zd na = zadd(zscale(a, g.c), zmul(b, zconj(g.s)));
-    zd nb = zsub(zscale(b, g.c), zmul(a, g.s));
+    cds na = cds_add(cds_scale(a, g.c), cds_mul(b, cds_conj(g.s)));
+    cds nb = cds_sub(cds_scale(b, g.c), cds_mul(a, g.s));
     a = na;
     b = nb;
 }
 
-__device__ __forceinline__ zd zsqrt_e(zd z)
+__global__ void k_to_ds(int64_t count, const zd *x, float4 *y)
 {
-    double r = hypot(z.x, z.y);
-    if (r == 0.0) return zmake(0.0, 0.0);
-    if (z.x >= 0.0) {
-        double t = sqrt(0.5 * (r + z.x));
-        return zmake(t, z.y / (2.0 * t));
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        zd v = x[e];
+        ds r = ds_from(v.x), i = ds_from(v.y);
+        y[e] = make_float4(r.h, r.l, i.h, i.l);
     }
-    double t = sqrt(0.5 * (r - z.x));
-    return zmake(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+__global__ void k_from_ds(int64_t count, const float4 *x, zd *y)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = x[e];
+        y[e] = zmake((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
 }
 
-// Whole QR phase: all CTAs run the same control flow (every decision is a
-// function of values read after a grid barrier), CTA 0 generates each chunk
-// of rotations, everybody applies the far parts.
-__global__ void __launch_bounds__(QT) k_hqr(int m, zd *H, zd *Z, int ld, Rot *rots, GridSync g,
-                                            int *fail, double hnorm)
+__device__ __forceinline__ cds csqrt_ds_approx(cds z)
 {
-    __shared__ zd blk[BLK][BLK + 1];
-    __shared__ Rot srot[CH];
-    const double eps = 2.220446049250313e-16;
-    const double htol = eps * fmax(hnorm, 1e-300);
+    // shift selection only needs a float-accurate square root
+    float zr = z.re.h, zi = z.im.h;
+    float r = hypotf(zr, zi);
+    cds o = cds_zero();
+    if (r == 0.f) return o;
+    if (zr >= 0.f) {
+        float t = sqrtf(0.5f * (r + zr));
+        o.re = ds_make(t, 0.f);
+        o.im = ds_make(zi / (2.f * t), 0.f);
+    } else {
+        float t = sqrtf(0.5f * (r - zr));
+        o.re = ds_make(fabsf(zi) / (2.f * t), 0.f);
+        o.im = ds_make(copysignf(t, zi), 0.f);
+    }
+    return o;
+}
+
+// Whole QR phase in double-single: all CTAs run the same control flow (every
+// decision is a function of values read after a grid barrier); CTA 0
+// generates each chunk of rotations in shared memory, everybody applies
+// the far parts.  H, Z: m x m double-single (float4), leading dim ld.
+__global__ void __launch_bounds__(QT) k_hqr(int m, float4 *H, float4 *Z, int ld, RotDS *rots, GridSync g,
+                                            int *fail, float tol_rel, float tol_abs)
+{
+    __shared__ cds blk[BLK][BLK + 1];
+    __shared__ RotDS srot[CH];
     const int gtid = blockIdx.x * QT + threadIdx.x, gthreads = gridDim.x * QT;
     int ihi = m - 1, iter = 0, total = 0;
     while (ihi > 0) {
-        // deflation scan (identical in every CTA)
         int l = ihi;
         while (l > 0) {
-            double sub = zabs(__ldcg(H + l + (int64_t)(l - 1) * ld));
-            double loc = zabs(__ldcg(H + (l - 1) + (int64_t)(l - 1) * ld)) + zabs(__ldcg(H + l + (int64_t)l * ld));
-            if (sub <= eps * loc || sub <= htol) break;
+            float sub = cds_absf(ld_cds(H + l + (int64_t)(l - 1) * ld));
+            float loc = cds_absf(ld_cds(H + (l - 1) + (int64_t)(l - 1) * ld)) +
+                        cds_absf(ld_cds(H + l + (int64_t)l * ld));
+            if (sub <= tol_rel * loc || sub <= tol_abs) break;
             --l;
         }
         if (l == ihi) { --ihi; iter = 0; continue; }
         if (++total > 40 * m) { if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(fail, 1); return; }
         ++iter;
-        // Wilkinson shift from the trailing 2 x 2 block (exceptional shift
-        // every 11th sweep without deflation)
-        zd sigma;
+        cds sigma;
         {
-            zd h00 = __ldcg(H + (ihi - 1) + (int64_t)(ihi - 1) * ld), h01 = __ldcg(H + (ihi - 1) + (int64_t)ihi * ld);
-            zd h10 = __ldcg(H + ihi + (int64_t)(ihi - 1) * ld), h11 = __ldcg(H + ihi + (int64_t)ihi * ld);
+            cds h00 = ld_cds(H + (ihi - 1) + (int64_t)(ihi - 1) * ld), h01 = ld_cds(H + (ihi - 1) + (int64_t)ihi * ld);
+            cds h10 = ld_cds(H + ihi + (int64_t)(ihi - 1) * ld), h11 = ld_cds(H + ihi + (int64_t)ihi * ld);
             if (iter % 11 == 10) {
-                double a = zabs(h10);
-                sigma = zadd(h11, zmake(a, 0.5 * a));
+                float a = cds_absf(h10);
+                sigma = h11;
+                sigma.re = ds_add(sigma.re, ds_make(a, 0.f));
+                sigma.im = ds_add(sigma.im, ds_make(0.5f * a, 0.f));
             } else {
-                zd tr = zadd(h00, h11), det = zsub(zmul(h00, h11), zmul(h01, h10));
-                zd disc = zsqrt_e(zsub(zscale(zmul(tr, tr), 0.25), det));
-                zd half = zscale(tr, 0.5);
-                zd r1 = zadd(half, disc), r2 = zsub(half, disc);
-                sigma = (zabs(zsub(r1, h11)) < zabs(zsub(r2, h11))) ? r1 : r2;
+                // Wilkinson shift: eigenvalue of the trailing 2 x 2 closest to h11
+                cds tr = cds_add(h00, h11);
+                cds half = cds_scale(tr, ds_make(0.5f, 0.f));
+                cds det = cds_sub(cds_mul(h00, h11), cds_mul(h01, h10));
+                cds disc = csqrt_ds_approx(cds_sub(cds_mul(half, half), det));
+                cds r1 = cds_add(half, disc), r2 = cds_sub(half, disc);
+                sigma = (cds_absf(cds_sub(r1, h11)) < cds_absf(cds_sub(r2, h11))) ? r1 : r2;
             }
         }
         // every CTA has read what it needs for l, ihi and sigma before CTA 0
@@ -270,29 +339,29 @@ __global__ void __launch_bounds__(QT) k_hqr(int m, zd *H, zd *Z, int ld, Rot *ro
             if (blockIdx.x == 0) {
                 for (int e = threadIdx.x; e < nb * nb; e += QT) {
                     int r = e % nb, c = e / nb;
-                    blk[r][c] = __ldcg(H + (b0 + r) + (int64_t)(b0 + c) * ld);
+                    blk[r][c] = ld_cds(H + (b0 + r) + (int64_t)(b0 + c) * ld);
                 }
                 __syncthreads();
                 if (threadIdx.x < 32) {
                     const int lane = threadIdx.x;
                     for (int k = k0; k < k1; ++k) {
                         const int kr = k - b0;
-                        zd x, y;
+                        cds x, y;
                         if (k == l) {
-                            x = zsub(blk[kr][kr], sigma);
+                            x = cds_sub(blk[kr][kr], sigma);
                             y = blk[kr + 1][kr];
                         } else {
                             x = blk[kr][kr - 1];
                             y = blk[kr + 1][kr - 1];
                         }
-                        Rot gr = make_rot(x, y);
+                        RotDS gr = make_rot_ds(x, y);
                         __syncwarp();
                         const int cs = (k == l) ? kr : kr - 1;
-                        for (int c = cs + lane; c < nb; c += 32) rot_left(gr, blk[kr][c], blk[kr + 1][c]);
+                        for (int c = cs + lane; c < nb; c += 32) rot_left_ds(gr, blk[kr][c], blk[kr + 1][c]);
                         __syncwarp();
-                        if (k > l && lane == 0) blk[kr + 1][kr - 1] = zmake(0.0, 0.0);
+                        if (k > l && lane == 0) blk[kr + 1][kr - 1] = cds_zero();
                         const int rl = ((k + 2 < ihi) ? k + 2 : ihi) - b0;
-                        for (int r = lane; r <= rl && r < nb; r += 32) rot_right(gr, blk[r][kr], blk[r][kr + 1]);
+                        for (int r = lane; r <= rl && r < nb; r += 32) rot_right_ds(gr, blk[r][kr], blk[r][kr + 1]);
                         __syncwarp();
                         if (lane == 0) srot[k - k0] = gr;
                     }
@@ -300,52 +369,48 @@ __global__ void __launch_bounds__(QT) k_hqr(int m, zd *H, zd *Z, int ld, Rot *ro
                 __syncthreads();
                 for (int e = threadIdx.x; e < nb * nb; e += QT) {
                     int r = e % nb, c = e / nb;
-                    __stcg(H + (b0 + r) + (int64_t)(b0 + c) * ld, blk[r][c]);
+                    st_cds(H + (b0 + r) + (int64_t)(b0 + c) * ld, blk[r][c]);
                 }
                 for (int e = threadIdx.x; e < k1 - k0; e += QT) {
-                    __stcg(&rots[e].c, srot[e].c);
-                    __stcg(&rots[e].s, srot[e].s);
+                    float *dst = (float *)(rots + e);
+                    const float *src = (const float *)(srot + e);
+                    for (int w = 0; w < (int)(sizeof(RotDS) / sizeof(float)); ++w) __stcg(dst + w, src[w]);
                 }
             }
             if (!grid_barrier(g)) return;
-            // far parts: left rotations on rows k0..k1 for columns > b1,
-            // right rotations on columns k0..k1 for rows < b0 of H and all
-            // rows of Z
             const int nrot = k1 - k0;
-            const int ncol = m - 1 - b1, nrowH = b0;
-            const int lines = ncol + nrowH + m;
             if (blockIdx.x != 0) {
-                for (int e = threadIdx.x; e < nrot; e += QT) {
-                    srot[e].c = __ldcg(&rots[e].c);
-                    srot[e].s = __ldcg(&rots[e].s);
-                }
+                for (int e = threadIdx.x; e < nrot * (int)(sizeof(RotDS) / sizeof(float)); e += QT)
+                    ((float *)srot)[e] = __ldcg(((const float *)rots) + e);
             }
             __syncthreads();
+            const int ncol = m - 1 - b1, nrowH = b0;
+            const int lines = ncol + nrowH + m;
             for (int t = gtid; t < lines; t += gthreads) {
-                zd seg[CH + 1];
+                cds seg[CH + 1];
                 if (t < ncol) {
-                    zd *col = H + (int64_t)(b1 + 1 + t) * ld + k0;
+                    float4 *col = H + (int64_t)(b1 + 1 + t) * ld + k0;
 #pragma unroll
                     for (int i = 0; i <= CH; ++i)
-                        if (i <= nrot) seg[i] = __ldcg(col + i);
+                        if (i <= nrot) seg[i] = ld_cds(col + i);
 #pragma unroll
                     for (int i = 0; i < CH; ++i)
-                        if (i < nrot) rot_left(srot[i], seg[i], seg[i + 1]);
+                        if (i < nrot) rot_left_ds(srot[i], seg[i], seg[i + 1]);
 #pragma unroll
                     for (int i = 0; i <= CH; ++i)
-                        if (i <= nrot) __stcg(col + i, seg[i]);
+                        if (i <= nrot) st_cds(col + i, seg[i]);
                 } else {
                     const int r = (t < ncol + nrowH) ? t - ncol : t - ncol - nrowH;
-                    zd *row = ((t < ncol + nrowH) ? H : Z) + r + (int64_t)k0 * ld;
+                    float4 *row = ((t < ncol + nrowH) ? H : Z) + r + (int64_t)k0 * ld;
 #pragma unroll
                     for (int i = 0; i <= CH; ++i)
-                        if (i <= nrot) seg[i] = __ldcg(row + (int64_t)i * ld);
+                        if (i <= nrot) seg[i] = ld_cds(row + (int64_t)i * ld);
 #pragma unroll
                     for (int i = 0; i < CH; ++i)
-                        if (i < nrot) rot_right(srot[i], seg[i], seg[i + 1]);
+                        if (i < nrot) rot_right_ds(srot[i], seg[i], seg[i + 1]);
 #pragma unroll
                     for (int i = 0; i <= CH; ++i)
-                        if (i <= nrot) __stcg(row + (int64_t)i * ld, seg[i]);
+                        if (i <= nrot) st_cds(row + (int64_t)i * ld, seg[i]);
                 }
             }
             if (!grid_barrier(g)) return;
@@ -430,8 +495,10 @@ __global__ void k_absmax(int64_t count, const zd *x, double *out)
 size_t zeig_large_work_bytes(int m)
 {
     // Q (m*m) + v (m) + w (m) + u (2m) complex, tau, absmax, rotations,
-    // barrier words
-    return sizeof(zd) * ((size_t)m * m + 4 * (size_t)m) + 64 + sizeof(Rot) * CH + 64;
+    // barrier words, then the double-single copies of H and Q (m*m float4
+    // each)
+    return sizeof(zd) * ((size_t)m * m + 4 * (size_t)m) + 64 + sizeof(RotDS) * CH + 64 + 256 +
+           2 * sizeof(float4) * (size_t)m * m;
 }
 
 // A (m x m, overwritten), Bt (m x m upper triangular, overwritten by the
@@ -447,8 +514,10 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     zd *u = wv + m;
     double *tau = (double *)(u + 2 * m);
     double *hmax = tau + 1;
-    Rot *rots = (Rot *)(hmax + 7);
+    RotDS *rots = (RotDS *)(hmax + 7);
     unsigned *bar = (unsigned *)(rots + CH);
+    float4 *Hds = (float4 *)(((uintptr_t)(bar + 16) + 255) & ~(uintptr_t)255);
+    float4 *Qds = Hds + (size_t)m * m;
     int e;
     // C = B~^{-1} A~  (upper-triangular solve with m right-hand sides)
     if ((e = trsm_upper_batched<zd>(s, m, m, 1, Bt, m, 0, A, m, 0))) return e;
@@ -494,10 +563,20 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     // are worth having even when there are fewer lines than threads)
     int grid = sms * (per < 1 ? 1 : 1);
     GridSync gs{bar, bar + 1, timeout};
-    double hnorm = hn;
+    // deflation thresholds at double-single resolution (2^-44 relative)
+    float tol_rel = 5.7e-14f, tol_abs = (float)(5.7e-14 * (hn > 0.0 ? hn : 1e-300));
     int mm = m, ldh = m;
-    void *args[] = {&mm, &C, &Q, &ldh, &rots, &gs, &fail, &hnorm};
+    const unsigned gcv = cdiv((size_t)m * m, 256) > 4096 ? 4096 : cdiv((size_t)m * m, 256);
+    k_to_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, C, Hds);
+    FEAST_LAUNCH_CHECK();
+    k_to_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, Q, Qds);
+    FEAST_LAUNCH_CHECK();
+    void *args[] = {&mm, &Hds, &Qds, &ldh, &rots, &gs, &fail, &tol_rel, &tol_abs};
     FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hqr, dim3(grid), dim3(QT), args, 0, s));
+    FEAST_LAUNCH_CHECK();
+    k_from_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, Hds, C);
+    FEAST_LAUNCH_CHECK();
+    k_from_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, Qds, Q);
     FEAST_LAUNCH_CHECK();
     // eigenvalues and eigenvectors
     k_diag_out<<<cdiv(m, 128), 128, 0, s>>>(m, C, m, alpha, beta);

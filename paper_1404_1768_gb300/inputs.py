@@ -173,6 +173,9 @@ WORKLOADS = {
     # at residual <= 1e-10
     "dense_n4096_m1280_q32": dict(n=4096, m0=1280, q=32, rule=0, center=0j, radius=1.0, seed=0,
                                   eps=1e-10),
+    # mid-size dense case for kernel profiles (same generator)
+    "dense_n1024_m256_q8": dict(n=1024, m0=256, q=8, rule=0, center=0j, radius=1.0, seed=0,
+                                eps=1e-10),
     # banded convection-diffusion, 128 x 128 grid (n = 16384, kl = ku = 128),
     # B = I, ellipse around the lowest 41 eigenvalues, 16 Gauss-Legendre nodes
     "band_n16384_m64_q16": dict(nx=128, m0=64, q=16, rule=1, center=422.0 + 0j, a=322.0,
