@@ -30,6 +30,9 @@ namespace {
 constexpr int CH = 32;           // rotations per chunk
 constexpr int BLK = CH + 3;      // local block edge
 constexpr int QT = 256;          // threads per CTA of the QR kernel
+constexpr int NSH = 16;          // most shifts (bulges) of a multishift sweep
+constexpr int DSEP = 2;          // phases between the entries of consecutive bulges
+constexpr int MS_MIN = 192;      // smallest active window that takes multishift sweeps
 
 // ------------------------------------------------------------- Householder
 // v = x - beta e1 with beta = -(x0/|x0|) ||x||, tau = 2 / ||v||^2, for
@@ -222,9 +225,28 @@ struct RotDS {
     cds s;
 };
 // G = [c s; -conj(s) c] with G [x; y] = [r; 0]
+__device__ __forceinline__ cds cds_ldexp(cds a, float f)
+{
+    // exact scaling by a power of two f
+    cds r;
+    r.re = ds_make(a.re.h * f, a.re.l * f);
+    r.im = ds_make(a.im.h * f, a.im.l * f);
+    return r;
+}
 __device__ __forceinline__ RotDS make_rot_ds(cds x, cds y)
 {
     RotDS g;
+    // the rotation depends only on the direction of (x, y): bring the
+    // larger entry near 1 first, so that |x|^2 and |y|^2 neither underflow
+    // nor overflow the float exponent range (a bulge running into an
+    // almost deflated stretch carries entries far below 1e-19)
+    const float mx = fmaxf(fmaxf(fabsf(x.re.h), fabsf(x.im.h)), fmaxf(fabsf(y.re.h), fabsf(y.im.h)));
+    if (mx == 0.f) { g.c = ds_make(1.f, 0.f); g.s = cds_zero(); return g; }
+    int ex;
+    frexpf(mx, &ex);
+    const float f = ldexpf(1.f, -ex);
+    x = cds_ldexp(x, f);
+    y = cds_ldexp(y, f);
     ds ax2 = cds_abs2(x), ay2 = cds_abs2(y);
     if (ay2.h == 0.f) { g.c = ds_make(1.f, 0.f); g.s = cds_zero(); return g; }
     if (ax2.h == 0.f) { g.c = ds_make(0.f, 0.f); g.s = cds_zero(); g.s.re = ds_make(1.f, 0.f); return g; }
@@ -286,15 +308,233 @@ __device__ __forceinline__ cds csqrt_ds_approx(cds z)
     return o;
 }
 
+// ------------------------------------------------------------ QR sweeps
+// Bulge bookkeeping for the multishift sweep: bulge b enters the active
+// window [l, ihi] DSEP phases after bulge b-1 and moves CH rows per phase,
+// so the diagonal blocks of concurrent bulges (CH + 3 wide, DSEP * CH
+// apart) never overlap.
+struct Bulge {
+    int k0, nrot, b0, b1;
+};
+__device__ __forceinline__ Bulge bulge_at(int t, int b, int l, int ihi, int m)
+{
+    Bulge g{0, 0, 0, 0};
+    const int c = t - DSEP * b;
+    if (c < 0) return g;
+    const int k0 = l + c * CH;
+    if (k0 >= ihi) return g;
+    const int k1 = (k0 + CH < ihi) ? k0 + CH : ihi;
+    g.k0 = k0;
+    g.nrot = k1 - k0;
+    g.b0 = (k0 - 1 > 0) ? k0 - 1 : 0;
+    g.b1 = (k1 + 1 < m - 1) ? k1 + 1 : m - 1;
+    return g;
+}
+
+// One chunk of a bulge chase (rotations k0 .. k0+nrot-1) on the diagonal
+// block [b0, b1] held in shared memory; warp 0 generates the dependent
+// chain.  A bulge enters at k == l with the first column of H - sigma I.
+// The rotations go to rots_g (global) for the far-part pass.
+__device__ __forceinline__ void chase_chunk(int m, float4 *H, int ld, int l, int ihi, const Bulge &bg, cds sigma,
+                            cds (*blk)[BLK + 1], RotDS *lrot, RotDS *rots_g)
+{
+    const int b0 = bg.b0, nb = bg.b1 - bg.b0 + 1, k0 = bg.k0, k1 = bg.k0 + bg.nrot;
+    for (int e = threadIdx.x; e < nb * nb; e += QT) {
+        int r = e % nb, c = e / nb;
+        blk[r][c] = ld_cds(H + (b0 + r) + (int64_t)(b0 + c) * ld);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int k = k0; k < k1; ++k) {
+            const int kr = k - b0;
+            cds x, y;
+            if (k == l) {
+                x = cds_sub(blk[kr][kr], sigma);
+                y = blk[kr + 1][kr];
+            } else {
+                x = blk[kr][kr - 1];
+                y = blk[kr + 1][kr - 1];
+            }
+            RotDS gr = make_rot_ds(x, y);
+            __syncwarp();
+            const int cs = (k == l) ? kr : kr - 1;
+            for (int c = cs + lane; c < nb; c += 32) rot_left_ds(gr, blk[kr][c], blk[kr + 1][c]);
+            __syncwarp();
+            if (k > l && lane == 0) blk[kr + 1][kr - 1] = cds_zero();
+            const int rl = ((k + 2 < ihi) ? k + 2 : ihi) - b0;
+            for (int r = lane; r <= rl && r < nb; r += 32) rot_right_ds(gr, blk[r][kr], blk[r][kr + 1]);
+            __syncwarp();
+            if (lane == 0) lrot[k - k0] = gr;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * nb; e += QT) {
+        int r = e % nb, c = e / nb;
+        st_cds(H + (b0 + r) + (int64_t)(b0 + c) * ld, blk[r][c]);
+    }
+    for (int e = threadIdx.x; e < bg.nrot * (int)(sizeof(RotDS) / sizeof(float)); e += QT)
+        __stcg(((float *)rots_g) + e, ((const float *)lrot)[e]);
+}
+
+// Left rotations of one chunk on the column segment col[0 .. nrot]: rotation
+// i mixes entries i and i+1, so entry i is final once rotation i is done and
+// only one entry is carried forward; loads go out FG entries at a time.
+constexpr int FG = 8;
+__device__ __forceinline__ void far_left(float4 *col, int nrot, const RotDS *rot)
+{
+    cds carry = ld_cds(col);
+    for (int g0 = 0; g0 < nrot; g0 += FG) {
+        cds buf[FG];
+#pragma unroll
+        for (int j = 0; j < FG; ++j)
+            if (g0 + j < nrot) buf[j] = ld_cds(col + g0 + j + 1);
+#pragma unroll
+        for (int j = 0; j < FG; ++j) {
+            if (g0 + j < nrot) {
+                rot_left_ds(rot[g0 + j], carry, buf[j]);
+                st_cds(col + g0 + j, carry);
+                carry = buf[j];
+            }
+        }
+    }
+    st_cds(col + nrot, carry);
+}
+// Right rotations of one chunk on the row segment row[0], row[ld], ...
+__device__ __forceinline__ void far_right(float4 *row, int ld, int nrot, const RotDS *rot)
+{
+    cds carry = ld_cds(row);
+    for (int g0 = 0; g0 < nrot; g0 += FG) {
+        cds buf[FG];
+#pragma unroll
+        for (int j = 0; j < FG; ++j)
+            if (g0 + j < nrot) buf[j] = ld_cds(row + (int64_t)(g0 + j + 1) * ld);
+#pragma unroll
+        for (int j = 0; j < FG; ++j) {
+            if (g0 + j < nrot) {
+                rot_right_ds(rot[g0 + j], carry, buf[j]);
+                st_cds(row + (int64_t)(g0 + j) * ld, carry);
+                carry = buf[j];
+            }
+        }
+    }
+    st_cds(row + (int64_t)nrot * ld, carry);
+}
+
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float f2_abs(float2 a) { return hypotf(a.x, a.y); }
+
+// Shifts for a multishift sweep: the eigenvalues of the trailing ns x ns
+// block of H, from a single-shift QR in FP32 by one warp (shifts steer
+// convergence only; they need no more accuracy than this).  If the small
+// QR stalls, the unconverged diagonal entries serve.
+__device__ __forceinline__ void trailing_shifts(int lo, int ns, const float4 *H, int ld, float2 (*a)[NSH + 1], float2 *out)
+{
+    for (int e = threadIdx.x; e < ns * ns; e += QT) {
+        int r = e % ns, c = e / ns;
+        float4 v = __ldcg(H + (lo + r) + (int64_t)(lo + c) * ld);
+        a[r][c] = (r > c + 1) ? make_float2(0.f, 0.f) : make_float2(v.x, v.z);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int hi = ns - 1, it = 0, tot = 0;
+        while (hi > 0) {
+            __syncwarp();
+            int l2 = hi;
+            while (l2 > 0) {
+                float sub = f2_abs(a[l2][l2 - 1]);
+                float loc = f2_abs(a[l2 - 1][l2 - 1]) + f2_abs(a[l2][l2]);
+                if (sub <= 3e-7f * loc || sub == 0.f) break;
+                --l2;
+            }
+            if (l2 == hi) { --hi; it = 0; continue; }
+            if (++tot > 30 * ns) break;
+            ++it;
+            float2 sig;
+            const float2 h00 = a[hi - 1][hi - 1], h01 = a[hi - 1][hi], h10 = a[hi][hi - 1], h11 = a[hi][hi];
+            if (it % 10 == 0) {
+                float s = f2_abs(h10);
+                sig = make_float2(h11.x + s, h11.y + 0.5f * s);
+            } else {
+                float2 half = make_float2(0.5f * (h00.x + h11.x), 0.5f * (h00.y + h11.y));
+                float2 det = f2_sub(f2_mul(h00, h11), f2_mul(h01, h10));
+                float2 d = f2_sub(f2_mul(half, half), det);
+                float r = f2_abs(d);
+                float2 sq = make_float2(0.f, 0.f);
+                if (r > 0.f) {
+                    if (d.x >= 0.f) {
+                        float t = sqrtf(0.5f * (r + d.x));
+                        sq = make_float2(t, d.y / (2.f * t));
+                    } else {
+                        float t = sqrtf(0.5f * (r - d.x));
+                        sq = make_float2(fabsf(d.y) / (2.f * t), copysignf(t, d.y));
+                    }
+                }
+                float2 r1 = f2_add(half, sq), r2 = f2_sub(half, sq);
+                sig = (f2_abs(f2_sub(r1, h11)) < f2_abs(f2_sub(r2, h11))) ? r1 : r2;
+            }
+            for (int k = l2; k < hi; ++k) {
+                __syncwarp();
+                float2 x, y;
+                if (k == l2) { x = f2_sub(a[k][k], sig); y = a[k + 1][k]; }
+                else { x = a[k][k - 1]; y = a[k + 1][k - 1]; }
+                const float ax = f2_abs(x), ay = f2_abs(y);
+                float c;
+                float2 sn;
+                if (ay == 0.f) { c = 1.f; sn = make_float2(0.f, 0.f); }
+                else if (ax == 0.f) { c = 0.f; sn = make_float2(1.f, 0.f); }
+                else {
+                    const float rr = hypotf(ax, ay);
+                    c = ax / rr;
+                    // (x / |x|) conj(y) / r
+                    const float2 ph = make_float2(x.x / ax, x.y / ax);
+                    sn = f2_mul(ph, make_float2(y.x / rr, -y.y / rr));
+                }
+                __syncwarp();
+                const int cs = (k == l2) ? k : k - 1;
+                for (int col = cs + lane; col <= hi; col += 32) {
+                    float2 p = a[k][col], q = a[k + 1][col];
+                    a[k][col] = f2_add(make_float2(c * p.x, c * p.y), f2_mul(sn, q));
+                    a[k + 1][col] = f2_sub(make_float2(c * q.x, c * q.y), f2_mul(make_float2(sn.x, -sn.y), p));
+                }
+                __syncwarp();
+                if (k > l2 && lane == 0) a[k + 1][k - 1] = make_float2(0.f, 0.f);
+                const int rl = (k + 2 < hi) ? k + 2 : hi;
+                for (int row = l2 + lane; row <= rl; row += 32) {
+                    float2 p = a[row][k], q = a[row][k + 1];
+                    a[row][k] = f2_add(make_float2(c * p.x, c * p.y), f2_mul(q, make_float2(sn.x, -sn.y)));
+                    a[row][k + 1] = f2_sub(make_float2(c * q.x, c * q.y), f2_mul(p, sn));
+                }
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < ns; i += 32) out[i] = a[i][i];
+    }
+}
+
 // Whole QR phase in double-single: all CTAs run the same control flow (every
-// decision is a function of values read after a grid barrier); CTA 0
-// generates each chunk of rotations in shared memory, everybody applies
-// the far parts.  H, Z: m x m double-single (float4), leading dim ld.
-__global__ void __launch_bounds__(QT) k_hqr(int m, float4 *H, float4 *Z, int ld, RotDS *rots, GridSync g,
-                                            int *fail, float tol_rel, float tol_abs)
+// decision is a function of values read after a grid barrier).  Active
+// windows of at least MS_MIN rows take multishift sweeps: ns shifts (the
+// eigenvalues of the trailing ns x ns block) drive ns bulges through the
+// window, each chased by its own CTA on its own diagonal block, and after
+// each phase the whole grid applies the chunks' far parts -- first every
+// bulge's left rotations (row segments right of its block), then every
+// bulge's right rotations (column segments above its block, and Z), so no
+// two writers meet.  Smaller windows take single-shift sweeps (Wilkinson
+// shift, exceptional shift every 11th sweep).  H, Z: m x m double-single
+// (float4), leading dim ld; rots: NSH * CH rotations; shifts: NSH entries.
+__global__ void __launch_bounds__(QT, 1) k_hqr(int m, float4 *H, float4 *Z, int ld, RotDS *rots, float2 *shifts,
+                                            GridSync g, int *fail, float tol_rel, float tol_abs)
 {
     __shared__ cds blk[BLK][BLK + 1];
-    __shared__ RotDS srot[CH];
+    __shared__ RotDS srot[NSH][CH];
+    __shared__ float2 sa[NSH][NSH + 1];
     const int gtid = blockIdx.x * QT + threadIdx.x, gthreads = gridDim.x * QT;
     int ihi = m - 1, iter = 0, total = 0;
     while (ihi > 0) {
@@ -307,8 +547,97 @@ __global__ void __launch_bounds__(QT) k_hqr(int m, float4 *H, float4 *Z, int ld,
             --l;
         }
         if (l == ihi) { --ihi; iter = 0; continue; }
-        if (++total > 40 * m) { if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(fail, 1); return; }
+        const int L = ihi - l + 1;
+        int ns = 1;
+        if (L >= MS_MIN) {
+            ns = L / (DSEP * CH);
+            if (ns > NSH) ns = NSH;
+            if (ns > (int)gridDim.x) ns = gridDim.x;
+        }
+        // budget: 30 shifts per eigenvalue
+        total += ns;
+        if (total > 30 * m) { if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(fail, 1); return; }
         ++iter;
+        if (ns > 1) {
+            // ------------------------------------------------ multishift sweep
+            if (blockIdx.x == 0) {
+                if (iter % 6 == 5) {
+                    // exceptional shifts: perturbed trailing diagonal
+                    for (int b = threadIdx.x; b < ns; b += QT) {
+                        const int i = ihi - b;
+                        float4 d = __ldcg(H + i + (int64_t)i * ld), e = __ldcg(H + i + (int64_t)(i - 1) * ld);
+                        const float s = hypotf(e.x, e.z);
+                        shifts[b] = make_float2(d.x + 0.75f * s, d.z + 0.4f * s);
+                    }
+                } else {
+                    trailing_shifts(ihi - ns + 1, ns, H, ld, sa, shifts);
+                }
+            }
+            // every CTA has finished its scan, and the shifts are out
+            if (!grid_barrier(g)) return;
+            const int nphase = (ihi - l + CH - 1) / CH + DSEP * (ns - 1);
+            for (int t = 0; t < nphase; ++t) {
+                if ((int)blockIdx.x < ns) {
+                    const int b = blockIdx.x;
+                    const Bulge bg = bulge_at(t, b, l, ihi, m);
+                    if (bg.nrot > 0) {
+                        const float2 sf = __ldcg(shifts + b);
+                        cds sigma = cds_zero();
+                        sigma.re = ds_make(sf.x, 0.f);
+                        sigma.im = ds_make(sf.y, 0.f);
+                        chase_chunk(m, H, ld, l, ihi, bg, sigma, blk, srot[0], rots + (size_t)b * CH);
+                    }
+                }
+                if (!grid_barrier(g)) return;
+                for (int e = threadIdx.x; e < ns * CH * (int)(sizeof(RotDS) / sizeof(float)); e += QT)
+                    ((float *)srot)[e] = __ldcg(((const float *)rots) + e);
+                __syncthreads();
+                // left rotations: column segments right of each block
+                {
+                    int total_l = 0;
+                    for (int b = 0; b < ns; ++b) {
+                        const Bulge bg = bulge_at(t, b, l, ihi, m);
+                        if (bg.nrot > 0) total_l += m - 1 - bg.b1;
+                    }
+                    for (int x = gtid; x < total_l; x += gthreads) {
+                        int rem = x, b = 0;
+                        Bulge bg;
+                        for (;; ++b) {
+                            bg = bulge_at(t, b, l, ihi, m);
+                            const int cnt = (bg.nrot > 0) ? m - 1 - bg.b1 : 0;
+                            if (rem < cnt) break;
+                            rem -= cnt;
+                        }
+                        far_left(H + (int64_t)(bg.b1 + 1 + rem) * ld + bg.k0, bg.nrot, srot[b]);
+                    }
+                }
+                if (!grid_barrier(g)) return;
+                // right rotations: row segments above each block, and Z
+                {
+                    int total_r = 0;
+                    for (int b = 0; b < ns; ++b) {
+                        const Bulge bg = bulge_at(t, b, l, ihi, m);
+                        if (bg.nrot > 0) total_r += bg.b0 + m;
+                    }
+                    for (int x = gtid; x < total_r; x += gthreads) {
+                        int rem = x, b = 0;
+                        Bulge bg;
+                        for (;; ++b) {
+                            bg = bulge_at(t, b, l, ihi, m);
+                            const int cnt = (bg.nrot > 0) ? bg.b0 + m : 0;
+                            if (rem < cnt) break;
+                            rem -= cnt;
+                        }
+                        float4 *row = (rem < bg.b0) ? H + rem + (int64_t)bg.k0 * ld
+                                                    : Z + (rem - bg.b0) + (int64_t)bg.k0 * ld;
+                        far_right(row, ld, bg.nrot, srot[b]);
+                    }
+                }
+                if (!grid_barrier(g)) return;
+            }
+            continue;
+        }
+        // ---------------------------------------------------- single-shift sweep
         cds sigma;
         {
             cds h00 = ld_cds(H + (ihi - 1) + (int64_t)(ihi - 1) * ld), h01 = ld_cds(H + (ihi - 1) + (int64_t)ihi * ld);
@@ -333,84 +662,29 @@ __global__ void __launch_bounds__(QT) k_hqr(int m, float4 *H, float4 *Z, int ld,
         if (!grid_barrier(g)) return;
         for (int k0 = l; k0 < ihi; k0 += CH) {
             const int k1 = (k0 + CH < ihi) ? k0 + CH : ihi;   // rotations k0 .. k1-1
-            const int b0 = (k0 - 1 > 0) ? k0 - 1 : 0;
-            const int b1 = (k1 + 1 < m - 1) ? k1 + 1 : m - 1;
-            const int nb = b1 - b0 + 1;
-            if (blockIdx.x == 0) {
-                for (int e = threadIdx.x; e < nb * nb; e += QT) {
-                    int r = e % nb, c = e / nb;
-                    blk[r][c] = ld_cds(H + (b0 + r) + (int64_t)(b0 + c) * ld);
-                }
-                __syncthreads();
-                if (threadIdx.x < 32) {
-                    const int lane = threadIdx.x;
-                    for (int k = k0; k < k1; ++k) {
-                        const int kr = k - b0;
-                        cds x, y;
-                        if (k == l) {
-                            x = cds_sub(blk[kr][kr], sigma);
-                            y = blk[kr + 1][kr];
-                        } else {
-                            x = blk[kr][kr - 1];
-                            y = blk[kr + 1][kr - 1];
-                        }
-                        RotDS gr = make_rot_ds(x, y);
-                        __syncwarp();
-                        const int cs = (k == l) ? kr : kr - 1;
-                        for (int c = cs + lane; c < nb; c += 32) rot_left_ds(gr, blk[kr][c], blk[kr + 1][c]);
-                        __syncwarp();
-                        if (k > l && lane == 0) blk[kr + 1][kr - 1] = cds_zero();
-                        const int rl = ((k + 2 < ihi) ? k + 2 : ihi) - b0;
-                        for (int r = lane; r <= rl && r < nb; r += 32) rot_right_ds(gr, blk[r][kr], blk[r][kr + 1]);
-                        __syncwarp();
-                        if (lane == 0) srot[k - k0] = gr;
-                    }
-                }
-                __syncthreads();
-                for (int e = threadIdx.x; e < nb * nb; e += QT) {
-                    int r = e % nb, c = e / nb;
-                    st_cds(H + (b0 + r) + (int64_t)(b0 + c) * ld, blk[r][c]);
-                }
-                for (int e = threadIdx.x; e < k1 - k0; e += QT) {
-                    float *dst = (float *)(rots + e);
-                    const float *src = (const float *)(srot + e);
-                    for (int w = 0; w < (int)(sizeof(RotDS) / sizeof(float)); ++w) __stcg(dst + w, src[w]);
-                }
-            }
+            Bulge bg;
+            bg.k0 = k0;
+            bg.nrot = k1 - k0;
+            bg.b0 = (k0 - 1 > 0) ? k0 - 1 : 0;
+            bg.b1 = (k1 + 1 < m - 1) ? k1 + 1 : m - 1;
+            if (blockIdx.x == 0) chase_chunk(m, H, ld, l, ihi, bg, sigma, blk, srot[0], rots);
             if (!grid_barrier(g)) return;
-            const int nrot = k1 - k0;
             if (blockIdx.x != 0) {
-                for (int e = threadIdx.x; e < nrot * (int)(sizeof(RotDS) / sizeof(float)); e += QT)
-                    ((float *)srot)[e] = __ldcg(((const float *)rots) + e);
+                for (int e = threadIdx.x; e < bg.nrot * (int)(sizeof(RotDS) / sizeof(float)); e += QT)
+                    ((float *)srot[0])[e] = __ldcg(((const float *)rots) + e);
             }
             __syncthreads();
-            const int ncol = m - 1 - b1, nrowH = b0;
+            // one writer per element: the column segments right of the block
+            // and the row segments above it do not meet
+            const int ncol = m - 1 - bg.b1, nrowH = bg.b0;
             const int lines = ncol + nrowH + m;
-            for (int t = gtid; t < lines; t += gthreads) {
-                cds seg[CH + 1];
-                if (t < ncol) {
-                    float4 *col = H + (int64_t)(b1 + 1 + t) * ld + k0;
-#pragma unroll
-                    for (int i = 0; i <= CH; ++i)
-                        if (i <= nrot) seg[i] = ld_cds(col + i);
-#pragma unroll
-                    for (int i = 0; i < CH; ++i)
-                        if (i < nrot) rot_left_ds(srot[i], seg[i], seg[i + 1]);
-#pragma unroll
-                    for (int i = 0; i <= CH; ++i)
-                        if (i <= nrot) st_cds(col + i, seg[i]);
+            for (int x = gtid; x < lines; x += gthreads) {
+                if (x < ncol) {
+                    far_left(H + (int64_t)(bg.b1 + 1 + x) * ld + k0, bg.nrot, srot[0]);
                 } else {
-                    const int r = (t < ncol + nrowH) ? t - ncol : t - ncol - nrowH;
-                    float4 *row = ((t < ncol + nrowH) ? H : Z) + r + (int64_t)k0 * ld;
-#pragma unroll
-                    for (int i = 0; i <= CH; ++i)
-                        if (i <= nrot) seg[i] = ld_cds(row + (int64_t)i * ld);
-#pragma unroll
-                    for (int i = 0; i < CH; ++i)
-                        if (i < nrot) rot_right_ds(srot[i], seg[i], seg[i + 1]);
-#pragma unroll
-                    for (int i = 0; i <= CH; ++i)
-                        if (i <= nrot) st_cds(row + (int64_t)i * ld, seg[i]);
+                    const int r = (x < ncol + nrowH) ? x - ncol : x - ncol - nrowH;
+                    float4 *row = ((x < ncol + nrowH) ? H : Z) + r + (int64_t)k0 * ld;
+                    far_right(row, ld, bg.nrot, srot[0]);
                 }
             }
             if (!grid_barrier(g)) return;
@@ -497,8 +771,8 @@ size_t zeig_large_work_bytes(int m)
     // Q (m*m) + v (m) + w (m) + u (2m) complex, tau, absmax, rotations,
     // barrier words, then the double-single copies of H and Q (m*m float4
     // each)
-    return sizeof(zd) * ((size_t)m * m + 4 * (size_t)m) + 64 + sizeof(RotDS) * CH + 64 + 256 +
-           2 * sizeof(float4) * (size_t)m * m;
+    return sizeof(zd) * ((size_t)m * m + 4 * (size_t)m) + 64 + sizeof(RotDS) * NSH * CH +
+           sizeof(float2) * NSH + 64 + 256 + 2 * sizeof(float4) * (size_t)m * m;
 }
 
 // A (m x m, overwritten), Bt (m x m upper triangular, overwritten by the
@@ -515,7 +789,8 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     double *tau = (double *)(u + 2 * m);
     double *hmax = tau + 1;
     RotDS *rots = (RotDS *)(hmax + 7);
-    unsigned *bar = (unsigned *)(rots + CH);
+    float2 *shifts = (float2 *)(rots + NSH * CH);
+    unsigned *bar = (unsigned *)(shifts + NSH);
     float4 *Hds = (float4 *)(((uintptr_t)(bar + 16) + 255) & ~(uintptr_t)255);
     float4 *Qds = Hds + (size_t)m * m;
     int e;
@@ -571,7 +846,7 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     FEAST_LAUNCH_CHECK();
     k_to_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, Q, Qds);
     FEAST_LAUNCH_CHECK();
-    void *args[] = {&mm, &Hds, &Qds, &ldh, &rots, &gs, &fail, &tol_rel, &tol_abs};
+    void *args[] = {&mm, &Hds, &Qds, &ldh, &rots, &shifts, &gs, &fail, &tol_rel, &tol_abs};
     FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hqr, dim3(grid), dim3(QT), args, 0, s));
     FEAST_LAUNCH_CHECK();
     k_from_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, Hds, C);
