@@ -4,11 +4,14 @@ A step is one pass of GFEAST lines 5-17 (projection, projected QZ, Ritz
 residuals and stopping test, then the contour-integral subspace build with
 one shifted multi-right-hand-side solve per node, the node sum and the two
 orthonormalisations) on the dense prescribed-spectrum pencil
-n = 4096, m0 = 1280, 32 trapezoid nodes on |z| = 1.  The LU set-up is timed
-separately.  One JSON line is printed by rank 0.
+n = 4096, m0 = 1280, 32 trapezoid nodes on |z| = 1, in the precision form
+(complex64 factors and solves with FP64-accurate refinement; --prec fp64
+for the plain FP64 path, which the precision form's line also times for
+comparison).  The LU set-up is timed separately.  One JSON line is printed
+by rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload NAME] [--prec fp64]
+                    [--workload NAME] [--prec c64r|fp64] [--no-fp64]
 
 --impl reference times the FP64 oracle (the plain CPU restatement of the
 method) on the host cores on a bounded sample of the same workload.
@@ -49,9 +52,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dense_n4096_m1280_q32", choices=sorted(inputs.WORKLOADS))
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "c64r"],
-                    help="fp64: every step in FP64; c64r: complex64 factors and solves with "
-                         "refinement (residual in double-single arithmetic)")
+    ap.add_argument("--prec", default="c64r", choices=["fp64", "c64r"],
+                    help="c64r (precision form): complex64 factors and solves on the tensor cores "
+                         "with FP64-accurate refinement; fp64: the plain FP64 path")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the plain-FP64 comparison passes of the precision form")
     ap.add_argument("--no-converge", action="store_true",
                     help="skip the untimed run to convergence (parity / eigpairs/s)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU baseline sample")
@@ -242,6 +247,72 @@ def config_dict(cfg, args, world):
 
 
 # ----------------------------------------------------------------------- GPU arm
+def parity_report(fe, p, cfg):
+    r = fe.eigs(want_vectors=True)
+    ref = p.lam[np.abs(p.lam - cfg["center"]) < cfg["radius"]]
+    errs = []
+    pool = list(ref)
+    for x in r["lam"]:
+        if not pool:
+            break
+        j = int(np.argmin([abs(x - y) for y in pool]))
+        errs.append(abs(x - pool[j]) / max(abs(pool[j]), 1e-300))
+        pool.pop(j)
+    return r, {"flag": r["flag"], "count": r["count"], "exact_count": int(len(ref)),
+               "max_rel_eig_err_vs_prescribed": max(errs) if errs else 0.0,
+               "max_resid_eq_5_1": float(np.max(r["res"])) if r["count"] else 0.0}
+
+
+def timed_run(fg, torch, dev, stream, host, n, m0, kw, steps, warmup, converge, world):
+    """One whole solve through the public API from pinned host buffers:
+    host -> device copies, set-up, `warmup` passes, `steps` passes timed with
+    CUDA events on the library's stream, then (if converge) passes until a
+    stop fires and the eigenpairs back to the host.  Returns the timings."""
+    hA, hB, hY = host
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dA = hA.to(dev, non_blocking=True)
+    dB = hB.to(dev, non_blocking=True)
+    dY = hY.to(dev, non_blocking=True)
+    fe = fg.Feast(dA.view(n, n).t(), dB.view(n, n).t(), dY.view(m0, n).t(), no_stop=True,
+                  device=dev, stream=stream, **kw)
+    setup_ms = fe.setup_info["ms_lu"] + fe.setup_info["ms_solve"]
+    infos = []
+    for _ in range(warmup):
+        infos.append(fe.iterate())
+    torch.cuda.synchronize()
+    launches0 = fg.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    timed = [fe.iterate() for _ in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    launches = fg.kernel_launches() - launches0
+    infos += timed
+    k_stop = None
+    for it in infos:
+        if it["flag"] != 2:
+            k_stop = it["k"]
+            break
+    res = None
+    if converge:
+        it = infos[-1]
+        while k_stop is None and it["k"] < kw["max_iter"]:
+            it = fe.iterate()
+            infos.append(it)
+            if it["flag"] != 2:
+                k_stop = it["k"]
+        if k_stop is not None:
+            res = fe.eigs(want_vectors=True)   # device -> host: values, residuals, vectors
+    torch.cuda.synchronize()
+    t_job = time.perf_counter() - t0
+    return dict(fe=fe, setup_ms=setup_ms, infos=infos, timed=timed, t_dev=t_dev, launches=launches,
+                k_stop=k_stop, t_job=t_job, res=res)
+
+
 def gpu_arm(args):
     import torch
     import paper_1404_1768_gb300 as fg
@@ -257,99 +328,76 @@ def gpu_arm(args):
     p = make_problem(cfg)
     n, m0, q = cfg["n"], cfg["m0"], cfg["q"]
     kw = feast_kwargs(cfg)
+    kw_prec = dict(kw)
     if args.prec == "c64r":
-        kw.update(prec=fg.FEAST_C64_REFINE, refine_tol=1e-13, max_refine=4)
+        kw_prec.update(prec=fg.FEAST_C64_REFINE, refine_tol=1e-13, max_refine=4)
     stream = torch.cuda.current_stream()
 
-    # pinned host inputs (column-major) for the end-to-end leg
+    # pinned host inputs (column-major)
     hA = torch.from_numpy(np.ascontiguousarray(p.A.ravel(order="F"))).pin_memory()
     hB = torch.from_numpy(np.ascontiguousarray(p.B.ravel(order="F"))).pin_memory()
     hY = torch.from_numpy(np.ascontiguousarray(p.Y.ravel(order="F"))).pin_memory()
     h2d_bytes = (hA.numel() + hB.numel() + hY.numel()) * 16
 
-    barrier(world)
-    torch.cuda.synchronize()
-    # ---- end-to-end: host inputs -> set-up -> W + K passes -> host outputs
-    t_e2e0 = time.perf_counter()
-    dA = hA.to(dev, non_blocking=True)
-    dB = hB.to(dev, non_blocking=True)
-    dY = hY.to(dev, non_blocking=True)
-    fe = fg.Feast(dA.view(n, n).t(), dB.view(n, n).t(), dY.view(m0, n).t(), no_stop=True,
-                  device=dev, **kw)
-    setup_ms = fe.setup_info["ms_lu"] + fe.setup_info["ms_solve"]
-    log(f"setup: LU {fe.setup_info['ms_lu']:.1f} ms, first subspace {fe.setup_info['ms_solve']:.1f} ms")
-    for _ in range(args.warmup):
-        it = fe.iterate()
-        log("warmup", {k: (round(v, 3) if isinstance(v, float) else v) for k, v in it.items()})
-    torch.cuda.synchronize()
-    barrier(world)
-    launches0 = fg.kernel_launches()
     clocks = ClockSampler(local)
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    infos = [fe.iterate() for _ in range(args.steps)]
-    ev1.record(stream)
-    for it in infos:
-        log("timed", {k: (round(v, 3) if isinstance(v, float) else v) for k, v in it.items()})
-    torch.cuda.synchronize()
+    run = timed_run(fg, torch, dev, stream, (hA, hB, hY), n, m0, kw_prec, args.steps, args.warmup,
+                    not args.no_converge, world)
     clk = clocks.stop()
-    launches = fg.kernel_launches() - launches0
-    t_dev = ev0.elapsed_time(ev1) / 1e3
-    # the result read back to the host (status scalars are read every pass)
-    d2h_bytes = 64 * (args.warmup + args.steps)
-    t_e2e1 = time.perf_counter()
-    t_e2e = t_e2e1 - t_e2e0
-    barrier(world)
-    t_dev_max = max_over_ranks(t_dev, world, dev)
-    t_e2e_max = max_over_ranks(t_e2e, world, dev)
-
+    for it in run["infos"]:
+        log("pass", {k: (round(v, 3) if isinstance(v, float) else v) for k, v in it.items()})
+    t_dev_max = max_over_ranks(run["t_dev"], world, dev)
     value = world * args.steps / t_dev_max
-    e2e_value = world * (args.warmup + args.steps) / t_e2e_max
-    ms_solve = statistics.mean(i["ms_solve"] for i in infos)
+    infos = run["timed"]
+    setup_ms, launches = run["setup_ms"], run["launches"]
+    parity, eig_rate, e2e = None, None, None
+    d2h_bytes = 0
+    if run["res"] is not None:
+        r = run["res"]
+        _, parity = parity_report(run["fe"], p, cfg)
+        parity["k_stop"] = run["k_stop"]
+        # eigpairs/s over the device work of the whole solve: set-up + every pass
+        t_total = (run["setup_ms"] + sum(
+            i["ms_proj"] + i["ms_qz"] + i["ms_solve"] + i["ms_qr"] for i in run["infos"])) / 1e3
+        eig_rate = r["count"] / t_total
+        d2h_bytes = 16 * m0 + 8 * m0 + 16 * n * m0 + 64 * run["k_stop"]
+        t_job = max_over_ranks(run["t_job"], world, dev)
+        e2e = {"value": world * run["k_stop"] / t_job, "unit": "iters/s",
+               "h2d_bytes_per_step": h2d_bytes / run["k_stop"],
+               "d2h_bytes_per_step": d2h_bytes / run["k_stop"],
+               "what": "whole solve through the public API: pinned host A, B, Y -> device, set-up, "
+                       "passes until the stop fires, eigenpairs back to the host; iterations / wall time"}
+    run["fe"].close()
+    del run
+
+    # the plain FP64 path on the same pencil, for the comparison the metric names
+    fp64 = None
+    if args.prec != "fp64" and not args.no_fp64:
+        r64 = timed_run(fg, torch, dev, stream, (hA, hB, hY), n, m0, kw, 2, 1, False, world)
+        fp64 = {"iters_per_s": 2 / r64["t_dev"], "ms_per_iter": 1e3 * r64["t_dev"] / 2,
+                "setup_ms": r64["setup_ms"], "warmup": 1, "steps": 2,
+                "phase_ms": {k: statistics.mean(i[k] for i in r64["timed"])
+                             for k in ("ms_proj", "ms_qz", "ms_solve", "ms_qr")}}
+        r64["fe"].close()
+        del r64
+
+    # roofline of the dominant phase: the kernel behind it and its algorithmic work
+    ph = {k: statistics.mean(i[k] for i in infos)
+          for k in ("ms_proj", "ms_qz", "ms_solve", "ms_qr", "ms_refine")}
     solve_flops = 8.0 * q * n * n * m0          # complex MAC = 8 flops, a4
     if args.prec == "fp64":
-        t_solve = ms_solve
-        peak, peak_src = FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
-        kern = "subspace-build solves (k_gemm + k_trsv_diag), FP64 pipe"
+        t_solve = ph["ms_solve"]
+        roof = {"bound": "alu", "achieved": solve_flops / (t_solve / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "kernel": "subspace-build solves (k_gemm<double2> + k_trsv_diag), FP64 pipe",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
     else:
-        # the complex64 solve of the pass (refinement sweeps timed separately)
-        t_solve = max(ms_solve - statistics.mean(i["ms_refine"] for i in infos), 1e-6)
-        peak, peak_src = FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"
-        kern = "subspace-build complex64 solves (k_gemm<float2> + k_trsv_diag), FP32 pipe"
-    achieved = solve_flops / (t_solve / 1e3) / 1e12
-
-    # ---- untimed: continue to convergence for parity and eigpairs/s
-    parity = None
-    eig_rate = None
-    if not args.no_converge:
-        k_stop = None
-        for i in infos:
-            if i["flag"] != 2:
-                k_stop = i["k"]
-                break
-        it = infos[-1]
-        while k_stop is None and it["k"] < kw["max_iter"]:
-            it = fe.iterate()
-            if it["flag"] != 2:
-                k_stop = it["k"]
-        if k_stop is not None:
-            r = fe.eigs(want_vectors=False)
-            ref = p.lam[np.abs(p.lam - cfg["center"]) < cfg["radius"]]
-            errs = []
-            pool = list(ref)
-            for x in r["lam"]:
-                j = int(np.argmin([abs(x - y) for y in pool]))
-                errs.append(abs(x - pool[j]) / max(abs(pool[j]), 1e-300))
-                pool.pop(j)
-            parity = {"flag": r["flag"], "count": r["count"], "exact_count": int(len(ref)),
-                      "k_stop": k_stop, "max_rel_eig_err_vs_prescribed": max(errs) if errs else 0.0,
-                      "max_resid_eq_5_1": float(np.max(r["res"])) if r["count"] else 0.0}
-            t_total = setup_ms / 1e3 + k_stop * (t_dev / args.steps)
-            eig_rate = r["count"] / t_total
-    fe.close()
+        t_solve = max(ph["ms_solve"] - ph["ms_refine"], 1e-6)
+        roof = {"bound": "alu", "achieved": solve_flops / (t_solve / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s",
+                "kernel": "subspace-build complex64 solves (k_gemm<float2> + k_trsv_diag), FP32 pipe",
+                "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
 
     if rank == 0:
         cb = None
@@ -361,17 +409,14 @@ def gpu_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c128" if args.prec == "fp64" else "c64+c128 refine",
             "data": "synthetic", "config": config_dict(cfg, args, world),
-            "setup_ms": setup_ms, "eigpairs_per_s": eig_rate, "parity": parity,
-            "phase_ms": {k: statistics.mean(i[k] for i in infos)
-                         for k in ("ms_proj", "ms_qz", "ms_solve", "ms_qr", "ms_refine")},
+            "setup_ms": setup_ms,
+            "eigpairs_per_s": eig_rate, "parity": parity,
+            "phase_ms": ph,
             "refine_sweeps": [i["refine_sweeps_max"] for i in infos],
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": kern, "peak_source": peak_src},
+            "fp64_path": fp64,
+            "roofline": roof,
             "cpu_baseline": cb,
-            "e2e": {"value": e2e_value, "unit": "iters/s",
-                    "h2d_bytes_per_step": h2d_bytes / (args.warmup + args.steps),
-                    "d2h_bytes_per_step": d2h_bytes / (args.warmup + args.steps)},
+            "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
         }

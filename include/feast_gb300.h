@@ -245,6 +245,23 @@ int feast_zgetrs_batched(int64_t n, int64_t nrhs, int batch, const void *M, int6
                          int64_t stride, const int *piv, void *X, int64_t ldx, int64_t sx,
                          void *stream);
 
+/* FP64-accurate complex GEMM on the bf16 tensor cores: C = beta C + alpha A B,
+ * A m x k, B k x n, C m x n, complex128 column-major (device, leading dims
+ * lda, ldb, ldc).  This is the product of the refinement residual
+ * R_j = B V - (z_j B - A) X_j of the precision form (the refinement of the
+ * shifted solves of eq. 4.2).  Each row of the real form of A and each
+ * column of B is scaled by a power of two and written as 8 base-64 digits;
+ * digit products and their sums over K-chunks of 2048 are exact in the
+ * tensor cores' FP32 accumulators, and the chunk sums are combined in FP64.
+ * Error: about 2^-47 times max_k|A_ik| * max_k|B_kj| * k per entry (not
+ * relative to |C|).  work: device, >= feast_zgemm_oz_work_bytes bytes, 256-
+ * byte aligned (digit planes).  err: device int32, set to 1 if a bounded
+ * pipeline wait gave up (C is then unspecified).  Asynchronous. */
+size_t feast_zgemm_oz_work_bytes(int64_t m, int64_t n, int64_t k);
+int feast_zgemm_oz(int64_t m, int64_t n, int64_t k, double alpha_re, double alpha_im, const void *A, int64_t lda,
+                   const void *B, int64_t ldb, double beta_re, double beta_im, void *C, int64_t ldc, void *work,
+                   size_t work_bytes, int *err, void *stream);
+
 /* Batched eigensolve of projected pencils (GFEAST line 6; the paper points
  * to the LAPACK drivers xGGES / xGGEV).  A, B: device, batch blocks of m x m
  * complex128 (B upper triangular -- its strictly lower part is ignored --

@@ -78,7 +78,7 @@ EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs",
            "feast_zgetrf_batched", "feast_zgetrs_batched", "feast_zqz_batched",
            "feast_zqz_work_bytes", "feast_kernel_launches", "feast_zqz_batched_noalloc",
            "feast_batch_workspace_size", "feast_solve_batch", "feast_cgemm_tc_scratch_bytes",
-           "feast_cgemm_tc"]
+           "feast_cgemm_tc", "feast_zgemm_oz_work_bytes", "feast_zgemm_oz"]
 
 
 def lib_path() -> str:
@@ -127,6 +127,9 @@ def load(build_if_missing: bool = True):
         F = C.c_float
         lib.feast_cgemm_tc.argtypes = [I64, I64, I64, F, F, P, I64, I64, P, I64, I64, F, F, P, I64, I64,
                                        I, P, C.c_size_t, P, P]
+        lib.feast_zgemm_oz_work_bytes.argtypes = [I64, I64, I64]
+        lib.feast_zgemm_oz_work_bytes.restype = C.c_size_t
+        lib.feast_zgemm_oz.argtypes = [I64, I64, I64, D, D, P, I64, P, I64, D, D, P, I64, P, C.c_size_t, P, P]
         lib.feast_kernel_launches.argtypes = []
         lib.feast_kernel_launches.restype = C.c_ulonglong
         _lib = lib
@@ -463,3 +466,29 @@ def cgemm_tc(A_list, X_list, C_list=None, alpha=1.0, beta=0.0, stream=None):
     if int(err.item()):
         raise FeastError(-6, "feast_cgemm_tc")
     return [from_device_colmajor(Cd[b_ * m * n:(b_ + 1) * m * n], m, n) for b_ in range(batch)]
+
+
+def zgemm_oz(A, Bm, Cm=None, alpha=1.0, beta=0.0, stream=None):
+    """complex128 C = beta C + alpha A B on the bf16 tensor cores with exact
+    digit slicing (FP64-accurate to ~2^-47 of max|A| max|B| k)."""
+    torch = _torch()
+    lib = load()
+    A = np.asarray(A, np.complex128)
+    Bm = np.asarray(Bm, np.complex128)
+    m, k = A.shape
+    n = Bm.shape[1]
+    Ad = to_device_colmajor(A)
+    Bd = to_device_colmajor(Bm)
+    Cd = (to_device_colmajor(np.asarray(Cm, np.complex128)) if Cm is not None
+          else torch.zeros(m * n, dtype=torch.complex128, device="cuda"))
+    nb = int(lib.feast_zgemm_oz_work_bytes(m, n, k))
+    work = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    wp = (work.data_ptr() + 255) // 256 * 256
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a, b = complex(alpha), complex(beta)
+    _check(lib.feast_zgemm_oz(m, n, k, a.real, a.imag, Ad.data_ptr(), m, Bd.data_ptr(), k, b.real, b.imag,
+                              Cd.data_ptr(), m, wp, nb, err.data_ptr(), _stream_ptr(stream)), "feast_zgemm_oz")
+    torch.cuda.current_stream().synchronize()
+    if int(err.item()):
+        raise FeastError(-6, "feast_zgemm_oz")
+    return from_device_colmajor(Cd, m, n)

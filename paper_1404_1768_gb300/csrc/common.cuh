@@ -273,15 +273,11 @@ int compact_pairs(cudaStream_t s, int64_t n, int m, const int *idx, const DevSta
                   double *resc);
 
 // Precision form (k_refine.cu).
-int form_shifted_split(cudaStream_t s, int64_t n, int q, const zd *A, const zd *B, int64_t ld,
-                       const zd *z, cf *M32, cf *Mhi, cf *Mlo);
-int split_hilo(cudaStream_t s, int64_t count, const zd *x, cf *hi, cf *lo);
+int form_shifted32(cudaStream_t s, int64_t n, int q, const zd *A, const zd *B, int64_t ld, const zd *z, cf *M32);
 int z2c(cudaStream_t s, int64_t count, const zd *x, cf *y);
 int c2z(cudaStream_t s, int64_t count, const cf *x, zd *y);
 int add_c32(cudaStream_t s, int64_t count, zd *x, const cf *c);
-// R_j = RHS - M_j X_j (double-single), nrm2[j] = ||R_j||_F^2
-int ds_residual(cudaStream_t s, int64_t n, int64_t m, int q, const cf *Mhi, const cf *Mlo,
-                const cf *Xhi, const cf *Xlo, const zd *RHS, zd *R, double *nrm2);
+// out = ||x||^2 over count entries
 int sumsq(cudaStream_t s, int64_t count, const zd *x, double *out);
 
 // Banded pencils (k_band.cu): LAPACK general-band factor storage
@@ -309,6 +305,21 @@ size_t tc_scratch_floats(int64_t m, int64_t k, int64_t n, int batch);
 int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf *A, int64_t lda,
              int64_t sA, const cf *X, int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC,
              int batch, float *scratch, int *err);
+// FP64-accurate complex GEMM on the bf16 tensor cores by exact base-64
+// digit slicing (k_oz.cu): prepare digit planes of the left operand (rows)
+// and the right operand (columns), then C = beta C + alpha_c A B with
+// alpha_c = alpha * zcol[c / cblk] when zcol is given.
+size_t oz_rows_bytes(int64_t M, int64_t K);
+size_t oz_cols_bytes(int64_t K, int64_t N);
+int oz_prepare_rows(cudaStream_t s, int64_t M, int64_t K, const zd *A, int64_t lda, void *work);
+int oz_prepare_cols(cudaStream_t s, int64_t K, int64_t N, const zd *B, int64_t ldb, void *work);
+int oz_gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, const void *Arows, const void *Bcols, zd alpha,
+            const zd *zcol, int64_t cblk, zd beta, zd *C, int64_t ldc, int *err);
+// R_j = BV - [xz] z_j X_j for every node j (X, R: n x (q m)); xz may be null.
+int resid_init(cudaStream_t s, int64_t n, int64_t m, int q, const zd *BV, const zd *xz, const zd *z, zd *R);
+// out[j] = ||x_j||_F^2 for q consecutive blocks of count entries.
+int sumsq_blocks(cudaStream_t s, int64_t count, int q, const zd *x, double *out);
+
 // complex64 LU whose trailing updates run on tc_cgemm (pivots and factors as
 // getrf_batched<cf>); scratch of getrf_tc_scratch_floats floats.
 size_t getrf_tc_scratch_floats(int64_t n, int batch);

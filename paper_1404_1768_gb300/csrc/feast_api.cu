@@ -59,8 +59,9 @@ struct feast_ctx {
     // precision form
     cf *F32;            // q x n x n complex64 factors
     float *tcs;         // tensor-core LU operand scratch (complex64 dense)
-    cf *Mhi, *Mlo;      // q x n x n double-single split of z_j B - A
-    cf *Xhi, *Xlo;      // q x n x m0 split of the solutions (Xhi doubles as R32)
+    void *ozA, *ozB;    // base-64 digit planes of A and B (refinement residual)
+    void *ozX;          // digit planes of the q solution blocks, n x (q m0)
+    cf *Xhi;            // q x n x m0 complex64 scratch (rounded residuals)
     cf *C32;            // q x n x m0 low-precision solves / corrections
     zd *R64;            // q x n x m0 residuals
     double *nrm2;       // q + 1 squared norms
@@ -144,10 +145,10 @@ void carve(feast_ctx *c, Carver &cv)
     } else {
         c->F32 = cv.take<cf>(q * n * n);
         c->tcs = cv.take<float>(getrf_tc_scratch_floats((int64_t)n, (int)q));
-        c->Mhi = cv.take<cf>(q * n * n);
-        c->Mlo = cv.take<cf>(q * n * n);
+        c->ozA = cv.take<char>(oz_rows_bytes((int64_t)n, (int64_t)n));
+        c->ozB = c->b_identity ? nullptr : cv.take<char>(oz_rows_bytes((int64_t)n, (int64_t)n));
+        c->ozX = cv.take<char>(oz_cols_bytes((int64_t)n, (int64_t)(q * m)));
         c->Xhi = cv.take<cf>(q * n * m);
-        c->Xlo = cv.take<cf>(q * n * m);
         c->C32 = cv.take<cf>(q * n * m);
         c->R64 = cv.take<zd>(q * n * m);
         c->nrm2 = cv.take<double>(q + 1);
@@ -297,8 +298,9 @@ int solve_band(feast_ctx *c, const zd *BV, double tol)
 }
 
 // Shifted solves of the precision form: complex64 LU solves, then
-// refinement sweeps X_j += M32_j^{-1} (R_j) with R_j = B V - M_j X_j in
-// double-single until max_j ||R_j||_F / ||B V||_F <= tol (or max_refine
+// refinement sweeps X_j += M32_j^{-1} (R_j) with R_j = B V - M_j X_j formed
+// FP64-accurately (its products A X and B X on the tensor cores, k_oz.cu)
+// until max_j ||R_j||_F / ||B V||_F <= tol (or max_refine
 // sweeps).  tol > 1e-6 (looser than what one complex64 solve reaches)
 // skips the residual altogether.  Result: X_j (FP64) in c->Xs.
 int solve_refine(feast_ctx *c, const zd *BV, double tol)
@@ -307,7 +309,7 @@ int solve_refine(feast_ctx *c, const zd *BV, double tol)
     const int64_t nm = n * m, all = q * nm;
     cudaStream_t s = c->s;
     int e;
-    cf *rhs32 = c->Xlo;  // n x m scratch before the split is needed
+    cf *rhs32 = c->Xhi;  // node 0's slot: rounded right-hand side before its gather
     if ((e = z2c(s, nm, BV, rhs32))) return e;
     if ((e = gather_rows<cf>(s, n, m, (int)q, c->perm, rhs32, n, 0, c->C32, n, nm))) return e;
     if ((e = trsm_lu_batched<cf>(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm))) return e;
@@ -321,8 +323,17 @@ int solve_refine(feast_ctx *c, const zd *BV, double tol)
     if ((e = sumsq(s, nm, BV, c->nrm2 + q))) return e;
     double h[4096 + 1];
     for (int sweep = 0; sweep <= c->max_refine; ++sweep) {
-        if ((e = split_hilo(s, all, c->Xs, c->Xhi, c->Xlo))) return e;
-        if ((e = ds_residual(s, n, m, (int)q, c->Mhi, c->Mlo, c->Xhi, c->Xlo, BV, c->R64, c->nrm2))) return e;
+        // R_j = B V - z_j (B X_j) + A X_j, FP64-accurate products on the tensor cores
+        if ((e = resid_init(s, n, m, (int)q, BV, c->b_identity ? c->Xs : nullptr, c->z, c->R64))) return e;
+        if ((e = oz_prepare_cols(s, n, q * m, c->Xs, n, c->ozX))) return e;
+        if (!c->b_identity &&
+            (e = oz_gemm(s, n, q * m, n, c->ozB, c->ozX, zmake(-1.0, 0.0), c->z, m, zmake(1.0, 0.0), c->R64, n,
+                         &c->st->timeout)))
+            return e;
+        if ((e = oz_gemm(s, n, q * m, n, c->ozA, c->ozX, zmake(1.0, 0.0), nullptr, 0, zmake(1.0, 0.0), c->R64, n,
+                         &c->st->timeout)))
+            return e;
+        if ((e = sumsq_blocks(s, nm, (int)q, c->R64, c->nrm2))) return e;
         FEAST_CUDA_TRY(cudaMemcpyAsync(h, c->nrm2, sizeof(double) * (q + 1), cudaMemcpyDeviceToHost, s));
         FEAST_CUDA_TRY(cudaStreamSynchronize(s));
         double worst = 0.0;
@@ -441,7 +452,9 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
         TRY(zform_shifted(s, n, c->q, c->A, c->B, n, c->z, c->F, n, n * n));
         TRY(zgetrf_batched(s, n, c->q, c->F, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row));
     } else {
-        TRY(form_shifted_split(s, n, c->q, c->A, c->B, n, c->z, c->F32, c->Mhi, c->Mlo));
+        TRY(form_shifted32(s, n, c->q, c->A, c->B, n, c->z, c->F32));
+        TRY(oz_prepare_rows(s, n, n, c->A, n, c->ozA));
+        if (!c->b_identity) TRY(oz_prepare_rows(s, n, n, c->B, n, c->ozB));
         TRY(getrf_batched_tc(s, n, c->q, c->F32, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row, c->tcs,
                              &c->st->timeout));
     }
@@ -770,6 +783,32 @@ int feast_cgemm_tc(int64_t m, int64_t n, int64_t k, float alpha_re, float alpha_
     FEAST_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
     return tc_cgemm(s, m, n, k, make_float2(alpha_re, alpha_im), (const cf *)A, lda, sA, (const cf *)X, ldx, sX,
                     make_float2(beta_re, beta_im), (cf *)C, ldc, sC, batch, sc, err);
+}
+
+size_t feast_zgemm_oz_work_bytes(int64_t m, int64_t n, int64_t k)
+{
+    if (m <= 0 || n <= 0 || k <= 0) return 0;
+    return oz_rows_bytes(m, k) + oz_cols_bytes(k, n) + 1024;
+}
+
+int feast_zgemm_oz(int64_t m, int64_t n, int64_t k, double alpha_re, double alpha_im, const void *A, int64_t lda,
+                   const void *B, int64_t ldb, double beta_re, double beta_im, void *C, int64_t ldc, void *work,
+                   size_t work_bytes, int *err, void *stream)
+{
+    if (m < 0 || n < 0 || k < 0 || !A || !B || !C || !work || !err) return FEAST_EINVAL;
+    if (lda < m || ldb < k || ldc < m) return FEAST_EINVAL;
+    if (((uintptr_t)work & 255u) != 0) return FEAST_EINVAL;
+    if (m == 0 || n == 0) return FEAST_OK;
+    if (work_bytes < feast_zgemm_oz_work_bytes(m, n, k)) return FEAST_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    FEAST_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    char *wa = (char *)work;
+    char *wb = wa + ((oz_rows_bytes(m, k) + 255) & ~(size_t)255);
+    int e;
+    if ((e = oz_prepare_rows(s, m, k, (const zd *)A, lda, wa))) return e;
+    if ((e = oz_prepare_cols(s, k, n, (const zd *)B, ldb, wb))) return e;
+    return oz_gemm(s, m, n, k, wa, wb, zmake(alpha_re, alpha_im), nullptr, 0, zmake(beta_re, beta_im), (zd *)C, ldc,
+                   err);
 }
 
 size_t feast_zqz_work_bytes(int m, int batch)

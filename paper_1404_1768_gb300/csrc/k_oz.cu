@@ -1,0 +1,397 @@
+// FP64-accurate complex GEMM on the bf16 tensor cores (tcgen05, kind::f16)
+// by exact integer slicing, for the refinement residual of the precision
+// form (and any FP64 product that tolerates ~2^-47 relative to |A||B|).
+//
+//   C = beta C + alpha_c A B       A: M x K, B: K x N complex128, column-major
+//
+// Complex as real: A' (2M x 2K) has rows 2i = [Re a_ik, -Im a_ik]_k and
+// 2i+1 = [Im a_ik, Re a_ik]_k; B' (2K x N) is B's columns read as
+// interleaved reals.  Every row of A' is scaled by a power of two 2^-e_i so
+// its entries lie in (-1, 1) and written in base 64 with OZ_S signed digits
+// (digit 1 in [-64, 64], later digits in [-32, 32]):
+//     A' = diag(2^e) sum_s 64^-s A_s ,   likewise B' = (sum_t 64^-t B_t) diag(2^f).
+// Digits are small integers, exact in bf16, and a digit product is exact in
+// the FP32 accumulator; so is any sum of products of one weight class
+// g = s + t over a K-chunk of OZ_KC terms (its magnitude stays below 2^24).
+// The kernel keeps one tensor-memory accumulator per class g = 2..9 (all
+// products with s + t <= OZ_S + 1; the rest weigh < 2^-60), reads the classes
+// out after each K-chunk and sums them in FP64 registers as
+// acc += sum_g 64^-(g-2) S_g; finally C gets alpha_c 2^(e_i + f_j - 12) acc.
+// Representation and truncation error: ~2^-48 relative to
+// max_k |A'_ik| * max_k |B'_kj| per entry, K-fold at most.
+//
+// Per CTA: one 128 x 64 tile of A'B'.  Warp 4 (one lane) streams K-stages of
+// 32 bf16 (64-byte swizzle rows) of all OZ_S slices of both operands with
+// TMA into a two-deep ring; warp 5 (one lane) issues the 36 slice products
+// per K-step of 16 into the eight accumulators (8 x 64 = all 512 TMEM
+// columns) and commits each stage and each K-chunk; warps 0-3 own TMEM
+// lanes 0-127 and run the chunk read-outs and the final write.  All waits
+// are bounded; on expiry the CTA raises *err and finishes.
+#include "tcgen05.cuh"
+
+namespace feast {
+
+namespace {
+using namespace tc;
+
+constexpr int OZ_S = 8;                      // digits per operand entry
+constexpr int OZ_NG = OZ_S;                  // weight classes g = 2 .. OZ_S + 1
+constexpr int OZ_BM = 128;                   // rows of A' per tile
+constexpr int OZ_BN = 64;                    // columns per tile
+constexpr int OZ_BK = 32;                    // bf16 per stage row (64 bytes)
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_KC = 2048;                  // K per exact chunk (real K)
+constexpr int OZ_GM = 8;                     // row tiles per raster group
+constexpr int OZ_THREADS = 192;
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2; // 8 KiB per slice
+constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2; // 4 KiB per slice
+constexpr int OZ_STAGE = OZ_S * (OZ_A_TILE + OZ_B_TILE);
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    // exact: |digit| <= 64
+    const uint32_t a = __float_as_uint(lo) >> 16, b = __float_as_uint(hi) >> 16;
+    return a | (b << 16);
+}
+
+// e_i with max_k max(|Re a_ik|, |Im a_ik|) < 2^e_i (0 for a zero row).
+__global__ void k_oz_rowexp(int64_t M, int64_t K, const zd *__restrict__ A, int64_t lda, int *__restrict__ e)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    double mx = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+        zd v = A[i + k * lda];
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+    int ex = 0;
+    if (mx > 0.0) frexp(mx, &ex);
+    e[i] = ex;
+}
+
+// f_j for column j of B (one warp per column).
+__global__ void k_oz_colexp(int64_t K, int64_t N, const zd *__restrict__ B, int64_t ldb, int *__restrict__ f)
+{
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= N) return;
+    double mx = 0.0;
+    for (int64_t k = lane; k < K; k += 32) {
+        zd v = B[k + j * ldb];
+        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) {
+        int ex = 0;
+        if (mx > 0.0) frexp(mx, &ex);
+        f[j] = ex;
+    }
+}
+
+// Digits of one real value already scaled into (-1, 1).
+__device__ __forceinline__ void digits(double r, float (&d)[OZ_S])
+{
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+        const double t = r * 64.0;
+        const double q = rint(t);
+        d[s] = (float)q;
+        r = t - q;
+    }
+}
+
+// A' digit planes: plane s is (2M x kp) bf16, row-major; thread per
+// (real row, complex column).  Columns K .. kp/2 - 1 are zero padding.
+__global__ void k_oz_slice_rows(int64_t M, int64_t K, const zd *__restrict__ A, int64_t lda,
+                                const int *__restrict__ e, uint32_t *__restrict__ planes, int64_t kp)
+{
+    const int64_t half = kp / 2;
+    const int64_t total = 2 * M * half;
+    const int64_t plane = 2 * M * kp / 2;   // in 32-bit words
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rr = x / half, kc = x % half;
+        const int64_t i = rr >> 1;
+        float d0[OZ_S], d1[OZ_S];
+        if (kc < K) {
+            const zd v = A[i + kc * lda];
+            const double sc = ldexp(1.0, -e[i]);
+            const double a = v.x * sc, b = v.y * sc;
+            if ((rr & 1) == 0) { digits(a, d0); digits(-b, d1); }
+            else { digits(b, d0); digits(a, d1); }
+        } else {
+#pragma unroll
+            for (int s = 0; s < OZ_S; ++s) { d0[s] = 0.f; d1[s] = 0.f; }
+        }
+        const int64_t o = rr * half + kc;
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) planes[(int64_t)s * plane + o] = pack_bf16x2(d0[s], d1[s]);
+    }
+}
+
+// B' digit planes: plane s is (N x kp) bf16, row j = column j of B as
+// interleaved reals; thread per (column, complex row).
+__global__ void k_oz_slice_cols(int64_t K, int64_t N, const zd *__restrict__ B, int64_t ldb,
+                                const int *__restrict__ f, uint32_t *__restrict__ planes, int64_t kp)
+{
+    const int64_t half = kp / 2;
+    const int64_t total = N * half;
+    const int64_t plane = N * half;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = x / half, kc = x % half;
+        float d0[OZ_S], d1[OZ_S];
+        if (kc < K) {
+            const zd v = B[kc + j * ldb];
+            const double sc = ldexp(1.0, -f[j]);
+            digits(v.x * sc, d0);
+            digits(v.y * sc, d1);
+        } else {
+#pragma unroll
+            for (int s = 0; s < OZ_S; ++s) { d0[s] = 0.f; d1[s] = 0.f; }
+        }
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) planes[(int64_t)s * plane + x] = pack_bf16x2(d0[s], d1[s]);
+    }
+}
+
+struct OzOut {
+    zd *C;
+    int64_t ldc;
+    zd alpha;
+    const zd *zcol;     // optional per-column-block factor (alpha_c = alpha * zcol[c / cblk])
+    int64_t cblk;
+    zd beta;
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int mr, int n,
+              int kr, const int *__restrict__ ea, const int *__restrict__ fb, OzOut out, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[OZ_STAGES], empty[OZ_STAGES], chunk_full, tmem_empty;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // raster: OZ_GM row tiles side by side share each column tile's operands in L2
+    const int Mt = (mr + OZ_BM - 1) / OZ_BM, Nt = (n + OZ_BN - 1) / OZ_BN;
+    const int L = blockIdx.x;
+    const int grp = L / (OZ_GM * Nt);
+    const int gbase = grp * OZ_GM;
+    const int gsz = (Mt - gbase) < OZ_GM ? (Mt - gbase) : OZ_GM;
+    const int rem = L - grp * OZ_GM * Nt;
+    const int rt = gbase + rem % gsz, ct = rem / gsz;
+    const int row0 = rt * OZ_BM, col0 = ct * OZ_BN;
+    const int kb_n = (kr + OZ_BK - 1) / OZ_BK;
+    constexpr int KB_CHUNK = OZ_KC / OZ_BK;
+    const int nchunk = (kb_n + KB_CHUNK - 1) / KB_CHUNK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&chunk_full, 1);
+        mbar_init(&tmem_empty, 128);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer
+            int issued = 0;
+            for (int kb = 0; kb < kb_n; ++kb) {
+                const int s = kb % OZ_STAGES;
+                const uint32_t ph = (uint32_t)((kb / OZ_STAGES) & 1);
+                if (!mbar_wait(&empty[s], ph ^ 1u) || *(volatile int *)&s_fail) { s_fail = 1; break; }
+                unsigned char *st = base + s * OZ_STAGE;
+                mbar_expect_tx(&full[s], OZ_STAGE);
+                const int kx = kb * OZ_BK;
+#pragma unroll 1
+                for (int sl = 0; sl < OZ_S; ++sl) {
+                    tma_load_3d(st + sl * OZ_A_TILE, &tA, &full[s], kx, row0, sl);
+                    tma_load_3d(st + OZ_S * OZ_A_TILE + sl * OZ_B_TILE, &tB, &full[s], kx, col0, sl);
+                }
+                issued = kb + 1;
+            }
+            // on failure, let the copies already issued land before the CTA exits
+            if (s_fail)
+                for (int kb = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); kb < issued; ++kb)
+                    mbar_wait(&full[kb % OZ_STAGES], (uint32_t)((kb / OZ_STAGES) & 1));
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_f32acc(1u, OZ_BM, OZ_BN);
+            bool ok = true;
+            for (int kb = 0; kb < kb_n && ok; ++kb) {
+                const int s = kb % OZ_STAGES;
+                const uint32_t ph = (uint32_t)((kb / OZ_STAGES) & 1);
+                const int chunk = kb / KB_CHUNK;
+                const bool first = (kb % KB_CHUNK) == 0;
+                if (first && chunk > 0) {
+                    // the read-out of the previous chunk must be done
+                    if (!mbar_wait(&tmem_empty, (uint32_t)((chunk - 1) & 1))) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                }
+                if (!mbar_wait(&full[s], ph) || *(volatile int *)&s_fail) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                unsigned char *st = base + s * OZ_STAGE;
+                const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + OZ_S * OZ_A_TILE);
+                const uint64_t adesc = sdesc<64>(st), bdesc = sdesc<64>(st + OZ_S * OZ_A_TILE);
+                (void)a0;
+                (void)b0;
+#pragma unroll
+                for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+#pragma unroll
+                    for (int sa = 0; sa < OZ_S; ++sa) {
+#pragma unroll
+                        for (int sb = 0; sb < OZ_S - sa; ++sb) {
+                            const int g = sa + sb;
+                            const uint64_t ad = adesc + (uint64_t)((sa * OZ_A_TILE + kk * 32) >> 4);
+                            const uint64_t bd = bdesc + (uint64_t)((sb * OZ_B_TILE + kk * 32) >> 4);
+                            const uint32_t acc = (first && kk == 0 && sa == 0) ? 0u : 1u;
+                            mma_f16(tmem + (uint32_t)(g * OZ_BN), ad, bd, idesc, acc);
+                        }
+                    }
+                }
+                mma_commit(&empty[s]);
+                if ((kb % KB_CHUNK) == KB_CHUNK - 1 || kb == kb_n - 1) mma_commit(&chunk_full);
+            }
+            if (!ok) s_fail = 1;
+        }
+    } else {
+        // read-out warps 0-3: TMEM lanes 32 * warp ..
+        double acc[OZ_BN];
+#pragma unroll
+        for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
+        bool good = true;
+        for (int c = 0; c < nchunk; ++c) {
+            if (!mbar_wait(&chunk_full, (uint32_t)(c & 1)) || *(volatile int *)&s_fail) { good = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int g = 0; g < OZ_NG; ++g) {
+                const double w = ldexp(1.0, -6 * g);
+#pragma unroll
+                for (int h = 0; h < OZ_BN / 32; ++h) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * OZ_BN + h * 32), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        acc[h * 32 + j] = fma((double)__uint_as_float(v[j]), w, acc[h * 32 + j]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(&tmem_empty);
+        }
+        if (!good) {
+            if (lane == 0) s_fail = 1;
+        } else {
+            const int r = row0 + warp * 32 + lane;           // real row
+            const bool im_row = (r & 1) != 0;
+            const int64_t ci = r >> 1;
+            const int er = (r < mr) ? ea[ci] : 0;
+#pragma unroll
+            for (int j = 0; j < OZ_BN; ++j) {
+                const int col = col0 + j;
+                const double mine = acc[j];
+                const double other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                // even lane writes columns 0..31 of the tile, odd lane 32..63
+                if (((j >> 5) & 1) == (im_row ? 1 : 0) && r < mr && col < n) {
+                    const double sc = ldexp(1.0, er + fb[col] - 12);
+                    const zd d = zmake((im_row ? other : mine) * sc, (im_row ? mine : other) * sc);
+                    zd al = out.alpha;
+                    if (out.zcol) al = zmul(al, out.zcol[col / out.cblk]);
+                    zd *dst = out.C + ci + (int64_t)col * out.ldc;
+                    zd o = *dst;
+                    zd res = zmul(al, d);
+                    res = zadd(res, zmul(out.beta, o));
+                    *dst = res;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+int64_t oz_kp(int64_t K) { return ((2 * K + 63) / 64) * 64; }
+}  // namespace
+
+size_t oz_rows_bytes(int64_t M, int64_t K) { return (size_t)OZ_S * 2 * M * oz_kp(K) * 2 + 256 + 4 * (size_t)M; }
+size_t oz_cols_bytes(int64_t K, int64_t N) { return (size_t)OZ_S * N * oz_kp(K) * 2 + 256 + 4 * (size_t)N; }
+
+// Digit planes of the left operand A (M x K): at `work`, oz_rows_bytes(M, K).
+int oz_prepare_rows(cudaStream_t s, int64_t M, int64_t K, const zd *A, int64_t lda, void *work)
+{
+    if (M <= 0 || K <= 0) return FEAST_OK;
+    const int64_t kp = oz_kp(K);
+    uint32_t *planes = (uint32_t *)work;
+    int *e = (int *)((char *)work + (size_t)OZ_S * 2 * M * kp * 2 + 256);
+    k_oz_rowexp<<<cdiv(M, 128), 128, 0, s>>>(M, K, A, lda, e);
+    FEAST_LAUNCH_CHECK();
+    const int64_t total = 2 * M * (kp / 2);
+    k_oz_slice_rows<<<cdiv(total, 256) > 16384 ? 16384 : cdiv(total, 256), 256, 0, s>>>(M, K, A, lda, e, planes, kp);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+// Digit planes of the right operand B (K x N): at `work`, oz_cols_bytes(K, N).
+int oz_prepare_cols(cudaStream_t s, int64_t K, int64_t N, const zd *B, int64_t ldb, void *work)
+{
+    if (N <= 0 || K <= 0) return FEAST_OK;
+    const int64_t kp = oz_kp(K);
+    uint32_t *planes = (uint32_t *)work;
+    int *f = (int *)((char *)work + (size_t)OZ_S * N * kp * 2 + 256);
+    k_oz_colexp<<<cdiv((size_t)N * 32, 256), 256, 0, s>>>(K, N, B, ldb, f);
+    FEAST_LAUNCH_CHECK();
+    const int64_t total = N * (kp / 2);
+    k_oz_slice_cols<<<cdiv(total, 256) > 16384 ? 16384 : cdiv(total, 256), 256, 0, s>>>(K, N, B, ldb, f, planes, kp);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+// C = beta C + alpha_c A B from prepared digit planes (A: M x K rows work,
+// B: K x N cols work).  alpha_c = alpha * zcol[c / cblk] when zcol is set.
+int oz_gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, const void *Arows, const void *Bcols, zd alpha,
+            const zd *zcol, int64_t cblk, zd beta, zd *C, int64_t ldc, int *err)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return FEAST_OK;
+    const int64_t kp = oz_kp(K);
+    const int64_t mr = 2 * M;
+    const int *ea = (const int *)((const char *)Arows + (size_t)OZ_S * mr * kp * 2 + 256);
+    const int *fb = (const int *)((const char *)Bcols + (size_t)OZ_S * N * kp * 2 + 256);
+    CUtensorMap mA, mB;
+    int e;
+    if ((e = make_map_3d(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Arows, kp, mr, OZ_S, kp * 2, mr * kp * 2, OZ_BK,
+                         OZ_BM, CU_TENSOR_MAP_SWIZZLE_64B)))
+        return e;
+    if ((e = make_map_3d(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Bcols, kp, N, OZ_S, kp * 2, N * kp * 2, OZ_BK,
+                         OZ_BN, CU_TENSOR_MAP_SWIZZLE_64B)))
+        return e;
+    const size_t smem = (size_t)OZ_STAGES * OZ_STAGE + 1024;
+    FEAST_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t tiles = ((mr + OZ_BM - 1) / OZ_BM) * ((N + OZ_BN - 1) / OZ_BN);
+    if (tiles > 0x7fffffff) return FEAST_EINVAL;
+    OzOut o{C, ldc, alpha, zcol, cblk > 0 ? cblk : 1, beta};
+    k_oz_gemm<<<(unsigned)tiles, OZ_THREADS, smem, s>>>(mA, mB, (int)mr, (int)N, (int)(2 * K), ea, fb, o, err);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+}  // namespace feast

@@ -20,81 +20,16 @@
 // then read their 32 TMEM lanes (tcgen05.ld), pair re/im rows across
 // neighbouring lanes and write C.  Every mbarrier wait has an iteration cap;
 // on expiry the kernel raises an error word and finishes without hanging.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace feast {
 
 namespace {
+using namespace tc;
 
 constexpr int TC_BM = 128;          // real rows per tile (= 64 complex rows)
 constexpr int TC_BK = 32;           // fp32 per 128-byte swizzle row
 constexpr int TC_STAGES = 3;
-constexpr long long TC_SPIN = 1ll << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < TC_SPIN; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
-                                            int z)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// K-major operand tile, 128-byte swizzle, rows 128 bytes apart, 8-row groups
-// 1024 bytes apart (descriptor version 1, layout type 2 = SWIZZLE_128B).
-__device__ __forceinline__ uint64_t sdesc(const void *p)
-{
-    const uint64_t a = (smem_u32(p) >> 4) & 0x3FFFull;
-    return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
 template <int BN>
 __global__ void __launch_bounds__(128) k_tc_cgemm(const __grid_constant__ CUtensorMap tAh,
                                                   const __grid_constant__ CUtensorMap tAt,
@@ -154,8 +89,7 @@ __global__ void __launch_bounds__(128) k_tc_cgemm(const __grid_constant__ CUtens
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: D = M=128 x N=BN, K=8 per instruction, 4 per stage
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                               ((uint32_t)(TC_BM >> 4) << 24);
+        const uint32_t idesc = idesc_f32acc(2u, TC_BM, BN);
         bool ok = true;
         for (int kb = 0; kb < kb_n && ok; ++kb) {
             const int s = kb % TC_STAGES;
@@ -163,8 +97,8 @@ __global__ void __launch_bounds__(128) k_tc_cgemm(const __grid_constant__ CUtens
             if (!mbar_wait(&full[s], ph)) { s_fail = 1; ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             unsigned char *st = base + s * STAGE;
-            const uint64_t ah = sdesc(st), at = sdesc(st + A_BYTES);
-            const uint64_t xh = sdesc(st + 2 * A_BYTES), xt = sdesc(st + 2 * A_BYTES + B_BYTES);
+            const uint64_t ah = sdesc<128>(st), at = sdesc<128>(st + A_BYTES);
+            const uint64_t xh = sdesc<128>(st + 2 * A_BYTES), xt = sdesc<128>(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 8; ++kk) {
                 const uint64_t adv = (uint64_t)((kk * 8 * 4) >> 4);   // 32 bytes per step
@@ -192,17 +126,7 @@ __global__ void __launch_bounds__(128) k_tc_cgemm(const __grid_constant__ CUtens
         for (int c0 = 0; c0 < BN; c0 += 32) {
             uint32_t v[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-                  "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-                  "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tmem_ld32(taddr, v);
             // even lane (Re row) stores columns 0..15 of this chunk, odd lane
             // (Im row) stores 16..31; each needs its partner's values
 #pragma unroll
@@ -275,6 +199,9 @@ __global__ void k_split_tf32(int64_t rows2, int n, const float *X, int64_t ldx2,
     }
 }
 
+}  // namespace
+
+namespace tc {
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -290,22 +217,31 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
     return fn;
 }
 
-// 3-D fp32 tensor map: dims {inner, rows, batch}, box {32, box_rows, 1},
-// 128-byte swizzle, zero fill out of bounds.
-int make_map(CUtensorMap *map, const float *base, int64_t inner, int64_t rows, int64_t batch,
-             int64_t ld_bytes, int64_t batch_bytes, int box_rows)
+int make_map_3d(CUtensorMap *map, CUtensorMapDataType dt, int elem_bytes, const void *base, int64_t inner,
+                int64_t rows, int64_t planes, int64_t ld_bytes, int64_t plane_bytes, int box_inner,
+                int box_rows, CUtensorMapSwizzle swz)
 {
     auto enc = get_encode();
     if (!enc) return FEAST_ECUDA;
-    if (((uintptr_t)base & 15) || (ld_bytes & 15) || (batch_bytes & 15)) return FEAST_EINVAL;
-    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)batch};
-    cuuint64_t strides[2] = {(cuuint64_t)ld_bytes, (cuuint64_t)(batch_bytes > 0 ? batch_bytes : ld_bytes * rows)};
-    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    (void)elem_bytes;
+    if (((uintptr_t)base & 15) || (ld_bytes & 15) || (plane_bytes & 15)) return FEAST_EINVAL;
+    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)ld_bytes, (cuuint64_t)(plane_bytes > 0 ? plane_bytes : ld_bytes * rows)};
+    cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? FEAST_OK : FEAST_EINVAL;
+}
+}  // namespace tc
+
+namespace {
+// 3-D fp32 tensor map {inner, rows, batch}, box {32, box_rows, 1}, 128-byte swizzle.
+int make_map(CUtensorMap *map, const float *base, int64_t inner, int64_t rows, int64_t batch,
+             int64_t ld_bytes, int64_t batch_bytes, int box_rows)
+{
+    return tc::make_map_3d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, inner, rows, batch, ld_bytes, batch_bytes,
+                           TC_BK, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 }  // namespace
 

@@ -1,5 +1,6 @@
-"""Precision form (complex64 factors and solves, refined with a residual
-evaluated in double-single arithmetic) against the FP64 oracle.
+"""Precision form (complex64 factors and solves on the tensor cores, refined
+with a residual whose products are FP64-accurate tensor-core GEMMs) against
+the FP64 oracle.
 
 Tolerances: a complex64 LU agrees with the FP64 one to ~n * 2^-24 relative;
 after refinement the shifted solves reach the refinement target
