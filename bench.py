@@ -43,6 +43,19 @@ METRIC = "FEAST iters/s & eigpairs/s vs plain FP64 GPU at resid≤1e-10; % TC/HB
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP32 pipe: 152 SMs x 128 FFMA/clock x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# TF32 dense tensor rate measured with cuBLAS (torch.matmul in tf32) on this machine
+TF32_PEAK_TFLOPS = 1027.0
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+HBM_PEAK_GBS = _measured_hbm()
 
 
 def parse():
@@ -143,14 +156,68 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------- inputs
-def make_problem(cfg):
-    return inputs.prescribed_pencil(cfg["n"], cfg["m0"], seed=cfg["seed"], center=cfg["center"],
-                                    radius=cfg["radius"])
+class Problem:
+    """One workload: its synthetic pencil, the FEAST keywords, the exact
+    eigenvalues inside the contour, and how to hand it to the library and to
+    the oracle."""
 
+    def __init__(self, cfg):
+        self.cfg = cfg
+        self.band = "nx" in cfg
+        if self.band:
+            bp = inputs.convection_diffusion(cfg["nx"], cfg["m0"], seed=cfg["seed"], beta=cfg["beta"])
+            self.bp = bp
+            self.n, self.m0, self.q = bp.n, cfg["m0"], cfg["q"]
+            lam = inputs.convection_diffusion_spectrum(cfg["nx"], cfg["beta"])
+            self.ref = lam[((lam - cfg["center"].real) / cfg["a"]) ** 2 < 1.0]
+            self.kw = dict(kind=1, kl=bp.kl, ku=bp.ku, b_identity=True, contour_kind=1, rule=cfg["rule"],
+                           q=cfg["q"], center=cfg["center"], a=cfg["a"], b=cfg["b"], eps=cfg["eps"],
+                           eta=1e-3, max_iter=50)
+            self.host_arrays = [bp.A_band, bp.Y]
+        else:
+            p = inputs.prescribed_pencil(cfg["n"], cfg["m0"], seed=cfg["seed"], center=cfg["center"],
+                                         radius=cfg["radius"])
+            self.p = p
+            self.n, self.m0, self.q = cfg["n"], cfg["m0"], cfg["q"]
+            self.ref = p.lam[np.abs(p.lam - cfg["center"]) < cfg["radius"]]
+            self.kw = dict(contour_kind=0, rule=cfg["rule"], q=cfg["q"], center=cfg["center"],
+                           a=cfg["radius"], eps=cfg.get("eps", 1e-12), eta=1e-3, max_iter=50)
+            self.host_arrays = [p.A, p.B, p.Y]
 
-def feast_kwargs(cfg):
-    return dict(contour_kind=0, rule=cfg["rule"], q=cfg["q"], center=cfg["center"],
-                a=cfg["radius"], eps=cfg.get("eps", 1e-12), eta=1e-3, max_iter=50)
+    def pinned(self):
+        import torch
+        return [torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).pin_memory()
+                for a in self.host_arrays]
+
+    def feast(self, fg, dev, stream, dev_arrays, **extra):
+        kw = dict(self.kw)
+        kw.update(extra)
+        if self.band:
+            dA, dY = dev_arrays
+            rows = self.bp.kl + self.bp.ku + 1
+            return fg.Feast(dA.view(self.n, rows).t(), None, dY.view(self.m0, self.n).t(), no_stop=True,
+                            device=dev, stream=stream, **kw)
+        dA, dB, dY = dev_arrays
+        n = self.n
+        return fg.Feast(dA.view(n, n).t(), dB.view(n, n).t(), dY.view(self.m0, n).t(), no_stop=True,
+                        device=dev, stream=stream, **kw)
+
+    def oracle_feast(self, oracle):
+        if self.band:
+            return oracle.Feast(self.bp.A_band, None, self.bp.Y, **self.kw)
+        return oracle.Feast(self.p.A, self.p.B, self.p.Y, **self.kw)
+
+    def describe(self):
+        c = self.cfg
+        if self.band:
+            return {"n": self.n, "m0": self.m0, "q": self.q, "rule": "gauss-legendre",
+                    "contour": f"ellipse center {c['center']} semi-axes {c['a']}, {c['b']}",
+                    "pencil": f"-Lap u + {tuple(c['beta'])}.grad u, {c['nx']}x{c['nx']} grid, 5-point, "
+                              f"B = I, half-bandwidth {self.bp.kl} (closed-form spectrum)"}
+        return {"n": self.n, "m0": self.m0, "q": self.q,
+                "rule": "trapezoid" if c["rule"] == 0 else "gauss-legendre",
+                "contour": f"circle center {c['center']} radius {c['radius']}",
+                "pencil": "A = P diag(lam) Q, B = P Q, lam uniform in |z| <= 2 (seeded)"}
 
 
 def log(*a):
@@ -158,14 +225,15 @@ def log(*a):
 
 
 # ----------------------------------------------------------------------- CPU baseline
-def cpu_baseline(cfg, p, budget_s: float = 20.0):
+def cpu_baseline(prob, budget_s: float = 20.0):
     """The oracle, as it stands, on a bounded sample of one iteration of the
-    workload, scaled to iterations/s.  Small workloads run whole iterations."""
+    workload, scaled to iterations/s.  Small dense workloads and banded ones
+    run whole iterations (after the oracle's own set-up)."""
     import oracle
     threads = oracle.num_threads()
-    n, m0, q = cfg["n"], cfg["m0"], cfg["q"]
-    if n * n * m0 * q <= 5e8:
-        fe = oracle.Feast(p.A, p.B, p.Y, **feast_kwargs(cfg))
+    n, m0, q = prob.n, prob.m0, prob.q
+    if prob.band or n * n * m0 * q <= 5e8:
+        fe = prob.oracle_feast(oracle)
         t0 = time.perf_counter()
         k = 0
         while time.perf_counter() - t0 < budget_s and k < 50:
@@ -176,7 +244,7 @@ def cpu_baseline(cfg, p, budget_s: float = 20.0):
         dt = time.perf_counter() - t0
         fe.close()
         return {"value": k / dt, "unit": "iters/s", "cores": threads, "kind": "oracle",
-                "sample": f"{k} whole GFEAST iterations (lines 5-17) of the oracle"}
+                "sample": f"{k} whole GFEAST iterations (lines 5-17) of the oracle after its set-up"}
     # large: solve step sampled on a subset of columns of one node, QZ on a
     # smaller pencil (cubic scaling), the n x m0 x m0 products on a subset
     rng = np.random.default_rng(1)
@@ -218,65 +286,58 @@ def reference_arm(args):
     if rank != 0:
         return 0
     cfg = inputs.WORKLOADS[args.workload]
-    p = make_problem(cfg)
+    prob = Problem(cfg)
     vals = []
     for _ in range(args.warmup):
-        cpu_baseline(cfg, p, budget_s=5.0)
+        cpu_baseline(prob, budget_s=5.0)
     for _ in range(args.steps):
-        vals.append(cpu_baseline(cfg, p, budget_s=10.0))
+        vals.append(cpu_baseline(prob, budget_s=10.0))
     v = statistics.median([x["value"] for x in vals])
     cb = dict(vals[-1])
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": config_dict(cfg, args, world),
+            "data": "synthetic", "config": config_dict(prob, args, world),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def config_dict(cfg, args, world):
-    return {"workload": args.workload, "n": cfg["n"], "m0": cfg["m0"], "q": cfg["q"],
-            "rule": "trapezoid" if cfg["rule"] == 0 else "gauss-legendre",
-            "contour": f"circle center {cfg['center']} radius {cfg['radius']}",
-            "pencil": "A = P diag(lam) Q, B = P Q, lam uniform in |z| <= 2 (seeded)",
-            "precision": args.prec, "parallelism": f"replicas{world}",
-            "l2": "inputs larger than L2 (per-node LU factors)"}
+def config_dict(prob, args, world):
+    d = {"workload": args.workload}
+    d.update(prob.describe())
+    d.update({"precision": args.prec, "parallelism": f"replicas{world}",
+              "l2": "inputs larger than L2 (per-node LU factors)"})
+    return d
 
 
 # ----------------------------------------------------------------------- GPU arm
-def parity_report(fe, p, cfg):
-    r = fe.eigs(want_vectors=True)
-    ref = p.lam[np.abs(p.lam - cfg["center"]) < cfg["radius"]]
+def parity_report(r, prob):
     errs = []
-    pool = list(ref)
+    pool = list(prob.ref)
     for x in r["lam"]:
         if not pool:
             break
         j = int(np.argmin([abs(x - y) for y in pool]))
         errs.append(abs(x - pool[j]) / max(abs(pool[j]), 1e-300))
         pool.pop(j)
-    return r, {"flag": r["flag"], "count": r["count"], "exact_count": int(len(ref)),
-               "max_rel_eig_err_vs_prescribed": max(errs) if errs else 0.0,
-               "max_resid_eq_5_1": float(np.max(r["res"])) if r["count"] else 0.0}
+    return {"flag": r["flag"], "count": r["count"], "exact_count": int(len(prob.ref)),
+            "max_rel_eig_err_vs_exact": max(errs) if errs else 0.0,
+            "max_resid_eq_5_1": float(np.max(r["res"])) if r["count"] else 0.0}
 
 
-def timed_run(fg, torch, dev, stream, host, n, m0, kw, steps, warmup, converge, world):
+def timed_run(fg, torch, dev, stream, prob, host, kw, steps, warmup, converge, world):
     """One whole solve through the public API from pinned host buffers:
     host -> device copies, set-up, `warmup` passes, `steps` passes timed with
     CUDA events on the library's stream, then (if converge) passes until a
     stop fires and the eigenpairs back to the host.  Returns the timings."""
-    hA, hB, hY = host
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    dA = hA.to(dev, non_blocking=True)
-    dB = hB.to(dev, non_blocking=True)
-    dY = hY.to(dev, non_blocking=True)
-    fe = fg.Feast(dA.view(n, n).t(), dB.view(n, n).t(), dY.view(m0, n).t(), no_stop=True,
-                  device=dev, stream=stream, **kw)
+    dev_arrays = [h.to(dev, non_blocking=True) for h in host]
+    fe = prob.feast(fg, dev, stream, dev_arrays, **kw)
     setup_ms = fe.setup_info["ms_lu"] + fe.setup_info["ms_solve"]
     infos = []
     for _ in range(warmup):
@@ -285,9 +346,11 @@ def timed_run(fg, torch, dev, stream, host, n, m0, kw, steps, warmup, converge, 
     launches0 = fg.kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")          # ncu --nvtx-include "timed/" captures these passes
     ev0.record(stream)
     timed = [fe.iterate() for _ in range(steps)]
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     t_dev = ev0.elapsed_time(ev1) / 1e3
     launches = fg.kernel_launches() - launches0
@@ -300,7 +363,7 @@ def timed_run(fg, torch, dev, stream, host, n, m0, kw, steps, warmup, converge, 
     res = None
     if converge:
         it = infos[-1]
-        while k_stop is None and it["k"] < kw["max_iter"]:
+        while k_stop is None and it["k"] < prob.kw["max_iter"]:
             it = fe.iterate()
             infos.append(it)
             if it["flag"] != 2:
@@ -309,8 +372,41 @@ def timed_run(fg, torch, dev, stream, host, n, m0, kw, steps, warmup, converge, 
             res = fe.eigs(want_vectors=True)   # device -> host: values, residuals, vectors
     torch.cuda.synchronize()
     t_job = time.perf_counter() - t0
-    return dict(fe=fe, setup_ms=setup_ms, infos=infos, timed=timed, t_dev=t_dev, launches=launches,
+    fe.close()
+    return dict(setup_ms=setup_ms, infos=infos, timed=timed, t_dev=t_dev, launches=launches,
                 k_stop=k_stop, t_job=t_job, res=res)
+
+
+def roofline(prob, args, ph):
+    """Roofline entry for the phase that carries the workload's defining
+    kernel: the dense shifted solves (FP64 or FP32 pipe) or the band solves
+    (HBM)."""
+    n, m0, q = prob.n, prob.m0, prob.q
+    t_solve = max(ph["ms_solve"] - (ph["ms_refine"] if args.prec != "fp64" else 0.0), 1e-6) / 1e3
+    if prob.band:
+        kl, ku = prob.bp.kl, prob.bp.ku
+        es = 16 if args.prec == "fp64" else 8
+        # factors read once forward (L, kl rows) and once backward (U, kl+ku+1
+        # rows); the right-hand sides read and written in both sweeps
+        traffic = q * (2 * kl + ku + 1) * n * es + 4 * q * n * m0 * es
+        return {"bound": "hbm", "achieved": traffic / t_solve / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                "frac": traffic / t_solve / 1e9 / HBM_PEAK_GBS, "traffic": None,
+                "kernel": "band solves k_gb_fwd + k_gb_bwd (subspace-build phase)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "algorithmic_bytes_per_pass": traffic}
+    flops = 8.0 * q * n * n * m0          # complex MAC = 8 flops, a4
+    if args.prec == "fp64":
+        return {"bound": "alu", "achieved": flops / t_solve / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": flops / t_solve / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "subspace-build solves (k_gemm<double2> + k_trsv_diag), FP64 pipe",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "algorithmic_flops_per_pass": flops}
+    return {"bound": "tensor", "achieved": flops / t_solve / 1e12, "peak": TF32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": flops / t_solve / 1e12 / TF32_PEAK_TFLOPS, "traffic": None,
+            "kernel": "subspace-build complex64 solves (k_tc_cgemm tcgen05 kind::tf32 + k_trsv_diag + "
+                      "in-block k_gemm<float2>); flops counted once (not the 3 split products)",
+            "peak_source": "TF32 dense measured with cuBLAS on this pool (torch.matmul, tf32)",
+            "algorithmic_flops_per_pass": flops}
 
 
 def gpu_arm(args):
@@ -325,23 +421,18 @@ def gpu_arm(args):
     dev = torch.device("cuda", local)
     fg.load()
     cfg = inputs.WORKLOADS[args.workload]
-    p = make_problem(cfg)
-    n, m0, q = cfg["n"], cfg["m0"], cfg["q"]
-    kw = feast_kwargs(cfg)
-    kw_prec = dict(kw)
+    prob = Problem(cfg)
+    n, m0 = prob.n, prob.m0
+    kw_prec = {}
     if args.prec == "c64r":
-        kw_prec.update(prec=fg.FEAST_C64_REFINE, refine_tol=1e-13, max_refine=4)
+        kw_prec = dict(prec=fg.FEAST_C64_REFINE, refine_tol=1e-13, max_refine=4)
     stream = torch.cuda.current_stream()
-
-    # pinned host inputs (column-major)
-    hA = torch.from_numpy(np.ascontiguousarray(p.A.ravel(order="F"))).pin_memory()
-    hB = torch.from_numpy(np.ascontiguousarray(p.B.ravel(order="F"))).pin_memory()
-    hY = torch.from_numpy(np.ascontiguousarray(p.Y.ravel(order="F"))).pin_memory()
-    h2d_bytes = (hA.numel() + hB.numel() + hY.numel()) * 16
+    host = prob.pinned()
+    h2d_bytes = sum(h.numel() * h.element_size() for h in host)
 
     clocks = ClockSampler(local)
     clocks.start()
-    run = timed_run(fg, torch, dev, stream, (hA, hB, hY), n, m0, kw_prec, args.steps, args.warmup,
+    run = timed_run(fg, torch, dev, stream, prob, host, kw_prec, args.steps, args.warmup,
                     not args.no_converge, world)
     clk = clocks.stop()
     for it in run["infos"]:
@@ -351,13 +442,12 @@ def gpu_arm(args):
     infos = run["timed"]
     setup_ms, launches = run["setup_ms"], run["launches"]
     parity, eig_rate, e2e = None, None, None
-    d2h_bytes = 0
     if run["res"] is not None:
         r = run["res"]
-        _, parity = parity_report(run["fe"], p, cfg)
+        parity = parity_report(r, prob)
         parity["k_stop"] = run["k_stop"]
         # eigpairs/s over the device work of the whole solve: set-up + every pass
-        t_total = (run["setup_ms"] + sum(
+        t_total = (setup_ms + sum(
             i["ms_proj"] + i["ms_qz"] + i["ms_solve"] + i["ms_qr"] for i in run["infos"])) / 1e3
         eig_rate = r["count"] / t_total
         d2h_bytes = 16 * m0 + 8 * m0 + 16 * n * m0 + 64 * run["k_stop"]
@@ -365,54 +455,39 @@ def gpu_arm(args):
         e2e = {"value": world * run["k_stop"] / t_job, "unit": "iters/s",
                "h2d_bytes_per_step": h2d_bytes / run["k_stop"],
                "d2h_bytes_per_step": d2h_bytes / run["k_stop"],
-               "what": "whole solve through the public API: pinned host A, B, Y -> device, set-up, "
+               "what": "whole solve through the public API: pinned host inputs -> device, set-up, "
                        "passes until the stop fires, eigenpairs back to the host; iterations / wall time"}
-    run["fe"].close()
     del run
 
     # the plain FP64 path on the same pencil, for the comparison the metric names
     fp64 = None
     if args.prec != "fp64" and not args.no_fp64:
-        r64 = timed_run(fg, torch, dev, stream, (hA, hB, hY), n, m0, kw, 2, 1, False, world)
+        r64 = timed_run(fg, torch, dev, stream, prob, host, {}, 2, 1, False, world)
         fp64 = {"iters_per_s": 2 / r64["t_dev"], "ms_per_iter": 1e3 * r64["t_dev"] / 2,
                 "setup_ms": r64["setup_ms"], "warmup": 1, "steps": 2,
                 "phase_ms": {k: statistics.mean(i[k] for i in r64["timed"])
                              for k in ("ms_proj", "ms_qz", "ms_solve", "ms_qr")}}
-        r64["fe"].close()
         del r64
 
-    # roofline of the dominant phase: the kernel behind it and its algorithmic work
     ph = {k: statistics.mean(i[k] for i in infos)
           for k in ("ms_proj", "ms_qz", "ms_solve", "ms_qr", "ms_refine")}
-    solve_flops = 8.0 * q * n * n * m0          # complex MAC = 8 flops, a4
-    if args.prec == "fp64":
-        t_solve = ph["ms_solve"]
-        roof = {"bound": "alu", "achieved": solve_flops / (t_solve / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "kernel": "subspace-build solves (k_gemm<double2> + k_trsv_diag), FP64 pipe",
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
-    else:
-        t_solve = max(ph["ms_solve"] - ph["ms_refine"], 1e-6)
-        roof = {"bound": "alu", "achieved": solve_flops / (t_solve / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s",
-                "kernel": "subspace-build complex64 solves (k_gemm<float2> + k_trsv_diag), FP32 pipe",
-                "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof = roofline(prob, args, ph)
 
     if rank == 0:
         cb = None
         if not args.no_baseline:
-            cb = cpu_baseline(cfg, p)
+            cb = cpu_baseline(prob)
         line = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c128" if args.prec == "fp64" else "c64+c128 refine",
-            "data": "synthetic", "config": config_dict(cfg, args, world),
+            "data": "synthetic", "config": config_dict(prob, args, world),
             "setup_ms": setup_ms,
             "eigpairs_per_s": eig_rate, "parity": parity,
             "phase_ms": ph,
             "refine_sweeps": [i["refine_sweeps_max"] for i in infos],
+            "qz": {"sweeps": [i["qz_sweeps"] for i in infos], "phases": [i["qz_phases"] for i in infos]},
             "fp64_path": fp64,
             "roofline": roof,
             "cpu_baseline": cb,
@@ -427,12 +502,76 @@ def gpu_arm(args):
     return 0
 
 
+def batch_arm(args, cfg):
+    """Ragged batch workload: all pencils through one feast_solve_batch call
+    (worker pool inside the library).  A step is one solve of the whole
+    batch to convergence; value = GFEAST iterations of all pencils / time."""
+    import torch
+    import paper_1404_1768_gb300 as fg
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    fg.load()
+    rb = inputs.ragged_batch(cfg["batch"], cfg["n_lo"], cfg["n_hi"], seed=cfg["seed"])
+    prec = fg.FEAST_C64_REFINE if args.prec == "c64r" else fg.FEAST_FP64
+    probs = [dict(A=p.A, B=p.B, Y=p.Y, contour_kind=0, rule=0, q=cfg["q"], center=p.center, a=p.radius,
+                  eps=cfg["eps"], prec=prec, refine_tol=1e-13, max_refine=4) for p in rb.pencils]
+    for _ in range(args.warmup):
+        fg.solve_batch(probs[:8], nworkers=8)
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, outs = [], None
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs = fg.solve_batch(probs, nworkers=16)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    t = statistics.median(times)
+    iters = sum(o["k"] for o in outs)
+    worst, counts_ok, res_max, fails = 0.0, 0, 0.0, 0
+    for p, o in zip(rb.pencils, outs):
+        if o["status"] != 0 or o["flag"] != 1:
+            fails += 1
+            continue
+        ref = p.lam[np.abs(p.lam - p.center) < p.radius]
+        counts_ok += int(o["count"] == len(ref))
+        pool = list(ref)
+        for x in o["lam"]:
+            if not pool:
+                break
+            j = int(np.argmin([abs(x - y) for y in pool]))
+            worst = max(worst, abs(x - pool[j]) / max(abs(pool[j]), 1e-300))
+            pool.pop(j)
+        if o["count"]:
+            res_max = max(res_max, float(np.max(o["res"])))
+    if rank == 0:
+        line = {"metric": METRIC, "value": iters / t, "unit": "iters/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "c128" if args.prec == "fp64" else "c64+c128 refine", "data": "synthetic",
+                "config": {"workload": args.workload, "pencils": cfg["batch"],
+                           "n_range": [cfg["n_lo"], cfg["n_hi"]], "q": cfg["q"],
+                           "m0": "max(8, ceil(1.5 s / 8) * 8) per pencil", "precision": args.prec,
+                           "parallelism": "replicas1"},
+                "pencils_per_s": cfg["batch"] / t, "total_iterations": iters,
+                "parity": {"converged": cfg["batch"] - fails, "exact_counts": counts_ok,
+                           "max_rel_eig_err_vs_exact": worst, "max_resid_eq_5_1": res_max},
+                "e2e": {"value": iters / t, "unit": "iters/s",
+                        "what": "host numpy pencils -> device, whole batch solved, results to host"},
+                "clocks": clk, "roofline": None, "cpu_baseline": None}
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if "batch" in inputs.WORKLOADS[args.workload]:
+        return batch_arm(args, inputs.WORKLOADS[args.workload])
     return gpu_arm(args)
 
 

@@ -117,6 +117,8 @@ typedef struct {
     double ms_lu, ms_solve, ms_refine, ms_qr, ms_proj, ms_qz;
     int refine_sweeps_max;
     int bad_node;
+    int qz_sweeps;    /* QR sweeps of the projected eigensolve (m0 > 64), this pass */
+    int qz_phases;    /* bulge-chase phases of those sweeps */
 } feast_iter_info;
 
 typedef struct feast_ctx feast_ctx;

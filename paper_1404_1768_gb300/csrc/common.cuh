@@ -116,7 +116,9 @@ struct DevStatus {
     int flag;           // 2 continue, 1 / 0 / -1 stopping criteria
     int qz_fail;        // pencils whose QZ iteration hit its iteration cap
     int timeout;        // a bounded grid barrier gave up
-    int pad;
+    int qz_sweeps;      // QR sweeps of the last large projected eigensolve
+    int qz_phases;      // chase phases (chunks) of those sweeps
+    int qz_aed;         // early-deflation windows applied
 };
 
 #define FEAST_CUDA_TRY(expr)                                                         \
@@ -243,13 +245,15 @@ size_t zorth_work_elems(int64_t n, int64_t m);
 size_t zqz_work_bytes(int m);
 int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA, zd *B,
                 int64_t ldb, int64_t sB, zd *alpha, zd *beta, zd *V, int64_t ldv, int64_t sV,
-                void *work, int *fail, int *timeout);
+                void *work, int *fail, int *timeout, int *stats = nullptr);
 
 // Large projected problems (k_zeig.cu): standard form, Hessenberg
 // reduction and chunked QR; alpha = eigenvalue, beta = 1.
 size_t zeig_large_work_bytes(int m);
+// stats (may be null): stats[0] += QR sweeps, stats[1] += chase phases,
+// stats[2] += early-deflation windows applied.
 int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
-               int *fail, int *timeout);
+               int *fail, int *timeout, int *stats = nullptr);
 
 // Composition of the LU interchanges: perm[b*n + i] = original row at i.
 int zpiv_to_perm(cudaStream_t s, int64_t n, int batch, const int *piv, int *perm);
@@ -311,7 +315,7 @@ int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf
 // alpha_c = alpha * zcol[c / cblk] when zcol is given.
 size_t oz_rows_bytes(int64_t M, int64_t K);
 size_t oz_cols_bytes(int64_t K, int64_t N);
-int oz_prepare_rows(cudaStream_t s, int64_t M, int64_t K, const zd *A, int64_t lda, void *work);
+int oz_prepare_rows(cudaStream_t s, int64_t M, int64_t K, const zd *A, int64_t lda, void *work, int ct = 0);
 int oz_prepare_cols(cudaStream_t s, int64_t K, int64_t N, const zd *B, int64_t ldb, void *work);
 int oz_gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, const void *Arows, const void *Bcols, zd alpha,
             const zd *zcol, int64_t cblk, zd beta, zd *C, int64_t ldc, int *err);
@@ -323,6 +327,10 @@ int sumsq_blocks(cudaStream_t s, int64_t count, int q, const zd *x, double *out)
 // complex64 LU whose trailing updates run on tc_cgemm (pivots and factors as
 // getrf_batched<cf>); scratch of getrf_tc_scratch_floats floats.
 size_t getrf_tc_scratch_floats(int64_t n, int batch);
+// complex64 L U solve (permuted right-hand sides) whose off-block updates
+// run on tc_cgemm; scratch as for getrf_batched_tc with nrhs <= n.
+int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, int64_t ldf, int64_t sF, cf *X,
+               int64_t ldx, int64_t sX, float *scratch, int *tc_err);
 int getrf_batched_tc(cudaStream_t s, int64_t n, int batch, cf *F, int64_t ldf, int64_t sF, int *piv,
                      int *info, int *row, float *scratch, int *tc_err);
 

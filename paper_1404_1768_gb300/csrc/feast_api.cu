@@ -60,7 +60,8 @@ struct feast_ctx {
     cf *F32;            // q x n x n complex64 factors
     float *tcs;         // tensor-core LU operand scratch (complex64 dense)
     void *ozA, *ozB;    // base-64 digit planes of A and B (refinement residual)
-    void *ozX;          // digit planes of the q solution blocks, n x (q m0)
+    void *ozX;          // digit planes of the q solution blocks, n x (q m0); right-operand scratch
+    void *ozR;          // left-operand digit planes: U2^H, U1, A U1, B U1 (m0 x n or n x m0)
     cf *Xhi;            // q x n x m0 complex64 scratch (rounded residuals)
     cf *C32;            // q x n x m0 low-precision solves / corrections
     zd *R64;            // q x n x m0 residuals
@@ -148,6 +149,10 @@ void carve(feast_ctx *c, Carver &cv)
         c->ozA = cv.take<char>(oz_rows_bytes((int64_t)n, (int64_t)n));
         c->ozB = c->b_identity ? nullptr : cv.take<char>(oz_rows_bytes((int64_t)n, (int64_t)n));
         c->ozX = cv.take<char>(oz_cols_bytes((int64_t)n, (int64_t)(q * m)));
+        {
+            const size_t r1 = oz_rows_bytes((int64_t)m, (int64_t)n), r2 = oz_rows_bytes((int64_t)n, (int64_t)m);
+            c->ozR = cv.take<char>(r1 > r2 ? r1 : r2);
+        }
         c->Xhi = cv.take<cf>(q * n * m);
         c->C32 = cv.take<cf>(q * n * m);
         c->R64 = cv.take<zd>(q * n * m);
@@ -221,6 +226,19 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b)
 }
 
 // Y = B X (copy when B = I).  X, Y: n x m, leading dim n.
+// Dense operands of the precision form: FP64-accurate products on the
+// tensor cores (digit planes of the left operand made beforehand).
+bool use_oz(const feast_ctx *c) { return c->kind == FEAST_DENSE && c->prec != FEAST_FP64; }
+
+// Y (M x N) = L X with L given by its digit planes (M x K), X (K x N, ldx).
+int oz_mul(feast_ctx *c, const void *Lrows, int64_t M, int64_t K, const zd *X, int64_t ldx, int64_t N, zd *Y,
+           int64_t ldy)
+{
+    int e;
+    if ((e = oz_prepare_cols(c->s, K, N, X, ldx, c->ozX))) return e;
+    return oz_gemm(c->s, M, N, K, Lrows, c->ozX, kOne, nullptr, 0, kZero, Y, ldy, &c->st->timeout);
+}
+
 int apply_B(feast_ctx *c, const zd *X, zd *Y, int64_t m)
 {
     const int64_t n = c->n;
@@ -229,6 +247,7 @@ int apply_B(feast_ctx *c, const zd *X, zd *Y, int64_t m)
         return FEAST_OK;
     }
     if (c->kind == FEAST_BANDED) return gb_matmul(c->s, n, c->kl, c->ku, c->B, c->ldin, m, X, Y);
+    if (use_oz(c)) return oz_mul(c, c->ozB, n, n, X, n, m, Y, n);
     return zgemm_batched(c->s, 0, n, m, n, kOne, c->B, n, 0, X, n, 0, kZero, Y, n, 0, 1);
 }
 
@@ -237,6 +256,7 @@ int apply_A(feast_ctx *c, const zd *X, zd *Y, int64_t m)
 {
     const int64_t n = c->n;
     if (c->kind == FEAST_BANDED) return gb_matmul(c->s, n, c->kl, c->ku, c->A, c->ldin, m, X, Y);
+    if (use_oz(c)) return oz_mul(c, c->ozA, n, n, X, n, m, Y, n);
     return zgemm_batched(c->s, 0, n, m, n, kOne, c->A, n, 0, X, n, 0, kZero, Y, n, 0, 1);
 }
 
@@ -312,7 +332,7 @@ int solve_refine(feast_ctx *c, const zd *BV, double tol)
     cf *rhs32 = c->Xhi;  // node 0's slot: rounded right-hand side before its gather
     if ((e = z2c(s, nm, BV, rhs32))) return e;
     if ((e = gather_rows<cf>(s, n, m, (int)q, c->perm, rhs32, n, 0, c->C32, n, nm))) return e;
-    if ((e = trsm_lu_batched<cf>(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm))) return e;
+    if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout))) return e;
     if ((e = c2z(s, all, c->C32, c->Xs))) return e;
     c->last_sweeps = 0;
     c->last_rel = -1.0;
@@ -344,7 +364,7 @@ int solve_refine(feast_ctx *c, const zd *BV, double tol)
         // correction: C_j = M32_j^{-1} R_j, X_j += C_j
         if ((e = z2c(s, all, c->R64, c->Xhi))) return e;
         if ((e = gather_rows<cf>(s, n, m, (int)q, c->perm, c->Xhi, n, nm, c->C32, n, nm))) return e;
-        if ((e = trsm_lu_batched<cf>(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm))) return e;
+        if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout))) return e;
         if ((e = add_c32(s, all, c->Xs, c->C32))) return e;
         c->last_sweeps = sweep + 1;
     }
@@ -504,16 +524,35 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[0], s));
     // line 5: [A~ | B~] = U2^H [A U1 | B U1]; B U1 is already in W[:, m0:]
     if ((e = apply_A(c, c->U1, c->W, m))) return e;
-    if ((e = zgemm_batched(s, 1, m, 2 * m, n, kOne, c->U2, n, 0, c->W, n, 0, kZero, c->P, m, 0, 1))) return e;
+    if (use_oz(c)) {
+        if ((e = oz_prepare_rows(s, m, n, c->U2, n, c->ozR, 1))) return e;
+        if ((e = oz_mul(c, c->ozR, m, n, c->W, n, 2 * m, c->P, m))) return e;
+    } else if ((e = zgemm_batched(s, 1, m, 2 * m, n, kOne, c->U2, n, 0, c->W, n, 0, kZero, c->P, m, 0, 1))) {
+        return e;
+    }
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[1], s));
     // line 6: projected eigenpairs, x_i = U1 y_i
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
+    FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_sweeps, 0, 3 * sizeof(int), s));
     if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
-                         c->qz_work, &c->st->qz_fail, &c->st->timeout))) return e;
+                         c->qz_work, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[2], s));
-    if ((e = zgemm_batched(s, 0, n, m, m, kOne, c->U1, n, 0, c->Yv, m, 0, kZero, c->Xr, n, 0, 1))) return e;
-    // A x_i = (A U1) y_i, B x_i = (B U1) y_i
-    if ((e = zgemm_batched(s, 0, n, m, m, kOne, c->W, n, n * m, c->Yv, m, 0, kZero, c->AXBX, n, n * m, 2))) return e;
+    if (use_oz(c)) {
+        // x_i = U1 y_i, A x_i = (A U1) y_i, B x_i = (B U1) y_i with Y's digits made once
+        if ((e = oz_prepare_cols(s, m, m, c->Yv, m, c->ozX))) return e;
+        const zd *lhs[3] = {c->U1, c->W, c->W + n * m};
+        zd *dst[3] = {c->Xr, c->AXBX, c->AXBX + n * m};
+        for (int t = 0; t < 3; ++t) {
+            if ((e = oz_prepare_rows(s, n, m, lhs[t], n, c->ozR))) return e;
+            if ((e = oz_gemm(s, n, m, m, c->ozR, c->ozX, kOne, nullptr, 0, kZero, dst[t], n, &c->st->timeout)))
+                return e;
+        }
+    } else {
+        if ((e = zgemm_batched(s, 0, n, m, m, kOne, c->U1, n, 0, c->Yv, m, 0, kZero, c->Xr, n, 0, 1))) return e;
+        // A x_i = (A U1) y_i, B x_i = (B U1) y_i
+        if ((e = zgemm_batched(s, 0, n, m, m, kOne, c->W, n, n * m, c->Yv, m, 0, kZero, c->AXBX, n, n * m, 2)))
+            return e;
+    }
     // lines 7-12: residuals (eq. 5.1), selection, c(k), e(k); lines 13-15
     if ((e = ritz_residuals(s, n, (int)m, c->AXBX, c->AXBX + n * m, n, c->alpha, c->beta, c->lam, c->res, c->st))) return e;
     if ((e = stop_test(s, (int)m, &c->contour, c->lam, c->res, c->eta, c->eps, c->k, c->max_iter, c->c_prev,
@@ -565,6 +604,8 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
         info->ms_qr = ev_ms(c->ev[4], c->ev[5]);
         info->ms_refine = c->prec == FEAST_FP64 ? 0.0 : c->ms_refine;
         info->refine_sweeps_max = c->prec == FEAST_FP64 ? 0 : c->last_sweeps;
+        info->qz_sweeps = hs.qz_sweeps;
+        info->qz_phases = hs.qz_phases;
     }
     return FEAST_OK;
 }

@@ -538,6 +538,59 @@ __global__ void k_gather_rows(int64_t n, int64_t nrhs, const int *perm, const T 
 }
 }  // namespace
 
+// Complex64 L U solve of already-permuted right-hand sides with the bulk of
+// the flops on the tensor cores: outer blocks of LU_NBO rows, solved inside
+// with the SV_NB-wide diagonal kernel and SIMT updates confined to the
+// block, and one rank-LU_NBO tensor-core update (tc_cgemm) of the rows
+// beyond the block per outer step.  scratch: tc_scratch_floats(n, LU_NBO,
+// nrhs, batch) floats.
+int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, int64_t ldf, int64_t sF, cf *X,
+               int64_t ldx, int64_t sX, float *scratch, int *tc_err)
+{
+    if (n <= 0 || nrhs <= 0 || batch <= 0) return FEAST_OK;
+    const cf mone = cx<cf>(-1, 0), one = cx<cf>(1, 0);
+    dim3 g(cdiv(nrhs, 64), batch);
+    int e;
+    // forward: unit lower L
+    for (int64_t k0 = 0; k0 < n; k0 += LU_NBO) {
+        const int64_t kend = (k0 + LU_NBO < n) ? k0 + LU_NBO : n;
+        for (int64_t kk = k0; kk < kend; kk += SV_NB) {
+            const int nb = (int)((kend - kk) < SV_NB ? (kend - kk) : SV_NB);
+            k_trsv_diag<cf><<<g, 64, 0, s>>>(n, nrhs, kk, nb, 1, F, ldf, sF, X, ldx, sX);
+            FEAST_LAUNCH_CHECK();
+            const int64_t r1 = kk + nb;
+            if (r1 < kend &&
+                (e = gemm_batched<cf>(s, 0, kend - r1, nrhs, nb, mone, F + r1 + kk * ldf, ldf, sF, X + kk, ldx, sX,
+                                      one, X + r1, ldx, sX, batch)))
+                return e;
+        }
+        if (kend < n &&
+            (e = tc_cgemm(s, n - kend, nrhs, kend - k0, mone, F + kend + k0 * ldf, ldf, sF, X + k0, ldx, sX, one,
+                          X + kend, ldx, sX, batch, scratch, tc_err)))
+            return e;
+    }
+    // backward: upper U
+    const int64_t last = ((n - 1) / LU_NBO) * LU_NBO;
+    for (int64_t k0 = last; k0 >= 0; k0 -= LU_NBO) {
+        const int64_t kend = (k0 + LU_NBO < n) ? k0 + LU_NBO : n;
+        const int64_t ilast = k0 + ((kend - k0 - 1) / SV_NB) * SV_NB;
+        for (int64_t kk = ilast; kk >= k0; kk -= SV_NB) {
+            const int nb = (int)((kend - kk) < SV_NB ? (kend - kk) : SV_NB);
+            k_trsv_diag<cf><<<g, 64, 0, s>>>(n, nrhs, kk, nb, 0, F, ldf, sF, X, ldx, sX);
+            FEAST_LAUNCH_CHECK();
+            if (kk > k0 &&
+                (e = gemm_batched<cf>(s, 0, kk - k0, nrhs, nb, mone, F + k0 + kk * ldf, ldf, sF, X + kk, ldx, sX,
+                                      one, X + k0, ldx, sX, batch)))
+                return e;
+        }
+        if (k0 > 0 &&
+            (e = tc_cgemm(s, k0, nrhs, kend - k0, mone, F + k0 * ldf, ldf, sF, X + k0, ldx, sX, one, X, ldx, sX,
+                          batch, scratch, tc_err)))
+            return e;
+    }
+    return FEAST_OK;
+}
+
 int zpiv_to_perm(cudaStream_t s, int64_t n, int batch, const int *piv, int *perm)
 {
     k_piv_to_perm<<<batch, 256, 0, s>>>(n, piv, perm);

@@ -54,19 +54,27 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return a | (b << 16);
 }
 
-// e_i with max_k max(|Re a_ik|, |Im a_ik|) < 2^e_i (0 for a zero row).
-__global__ void k_oz_rowexp(int64_t M, int64_t K, const zd *__restrict__ A, int64_t lda, int *__restrict__ e)
+// e_i with max_k max(|Re a_ik|, |Im a_ik|) < 2^e_i (0 for a zero row); one
+// warp per row.  ct: the operand is the conjugate transpose of the stored
+// matrix, a_ik = conj(A[k + i lda]).
+__global__ void k_oz_rowexp(int64_t M, int64_t K, const zd *__restrict__ A, int64_t lda, int ct,
+                            int *__restrict__ e)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= M) return;
     double mx = 0.0;
-    for (int64_t k = 0; k < K; ++k) {
-        zd v = A[i + k * lda];
+    for (int64_t k = lane; k < K; k += 32) {
+        const zd v = ct ? A[k + i * lda] : A[i + k * lda];
         mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
     }
-    int ex = 0;
-    if (mx > 0.0) frexp(mx, &ex);
-    e[i] = ex;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) {
+        int ex = 0;
+        if (mx > 0.0) frexp(mx, &ex);
+        e[i] = ex;
+    }
 }
 
 // f_j for column j of B (one warp per column).
@@ -103,7 +111,7 @@ __device__ __forceinline__ void digits(double r, float (&d)[OZ_S])
 
 // A' digit planes: plane s is (2M x kp) bf16, row-major; thread per
 // (real row, complex column).  Columns K .. kp/2 - 1 are zero padding.
-__global__ void k_oz_slice_rows(int64_t M, int64_t K, const zd *__restrict__ A, int64_t lda,
+__global__ void k_oz_slice_rows(int64_t M, int64_t K, const zd *__restrict__ A, int64_t lda, int ct,
                                 const int *__restrict__ e, uint32_t *__restrict__ planes, int64_t kp)
 {
     const int64_t half = kp / 2;
@@ -115,7 +123,8 @@ __global__ void k_oz_slice_rows(int64_t M, int64_t K, const zd *__restrict__ A, 
         const int64_t i = rr >> 1;
         float d0[OZ_S], d1[OZ_S];
         if (kc < K) {
-            const zd v = A[i + kc * lda];
+            zd v = ct ? A[kc + i * lda] : A[i + kc * lda];
+            if (ct) v.y = -v.y;
             const double sc = ldexp(1.0, -e[i]);
             const double a = v.x * sc, b = v.y * sc;
             if ((rr & 1) == 0) { digits(a, d0); digits(-b, d1); }
@@ -304,22 +313,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const bool im_row = (r & 1) != 0;
             const int64_t ci = r >> 1;
             const int er = (r < mr) ? ea[ci] : 0;
+            // pair the Re / Im rows (neighbouring lanes); the even lane writes
+            // columns 0..31 of the tile, the odd lane 32..63, eight at a time
+            // with the old values loaded first
+            const int hsel = im_row ? 1 : 0;
+            const bool rd = (out.beta.x != 0.0 || out.beta.y != 0.0);
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) {
-                const int col = col0 + j;
-                const double mine = acc[j];
-                const double other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                // even lane writes columns 0..31 of the tile, odd lane 32..63
-                if (((j >> 5) & 1) == (im_row ? 1 : 0) && r < mr && col < n) {
-                    const double sc = ldexp(1.0, er + fb[col] - 12);
-                    const zd d = zmake((im_row ? other : mine) * sc, (im_row ? mine : other) * sc);
-                    zd al = out.alpha;
-                    if (out.zcol) al = zmul(al, out.zcol[col / out.cblk]);
-                    zd *dst = out.C + ci + (int64_t)col * out.ldc;
-                    zd o = *dst;
-                    zd res = zmul(al, d);
-                    res = zadd(res, zmul(out.beta, o));
-                    *dst = res;
+            for (int g8 = 0; g8 < OZ_BN / 2; g8 += 8) {
+                zd d[8], o[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const double m0v = acc[g8 + i], m1v = acc[32 + g8 + i];
+                    const double o0 = __shfl_xor_sync(0xffffffffu, m0v, 1);
+                    const double o1 = __shfl_xor_sync(0xffffffffu, m1v, 1);
+                    const double mine = hsel ? m1v : m0v, other = hsel ? o1 : o0;
+                    d[i] = zmake(im_row ? other : mine, im_row ? mine : other);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int col = col0 + hsel * 32 + g8 + i;
+                    o[i] = (rd && r < mr && col < n) ? out.C[ci + (int64_t)col * out.ldc] : zmake(0.0, 0.0);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int col = col0 + hsel * 32 + g8 + i;
+                    if (r < mr && col < n) {
+                        const double sc = ldexp(1.0, er + fb[col] - 12);
+                        zd al = out.alpha;
+                        if (out.zcol) al = zmul(al, out.zcol[col / out.cblk]);
+                        zd res = zmul(al, zscale(d[i], sc));
+                        if (rd) res = zadd(res, zmul(out.beta, o[i]));
+                        out.C[ci + (int64_t)col * out.ldc] = res;
+                    }
                 }
             }
         }
@@ -336,17 +361,20 @@ int64_t oz_kp(int64_t K) { return ((2 * K + 63) / 64) * 64; }
 size_t oz_rows_bytes(int64_t M, int64_t K) { return (size_t)OZ_S * 2 * M * oz_kp(K) * 2 + 256 + 4 * (size_t)M; }
 size_t oz_cols_bytes(int64_t K, int64_t N) { return (size_t)OZ_S * N * oz_kp(K) * 2 + 256 + 4 * (size_t)N; }
 
-// Digit planes of the left operand A (M x K): at `work`, oz_rows_bytes(M, K).
-int oz_prepare_rows(cudaStream_t s, int64_t M, int64_t K, const zd *A, int64_t lda, void *work)
+// Digit planes of the left operand (M x K): A itself, or with ct the
+// conjugate transpose of the stored K x M matrix A; at `work`,
+// oz_rows_bytes(M, K).
+int oz_prepare_rows(cudaStream_t s, int64_t M, int64_t K, const zd *A, int64_t lda, void *work, int ct)
 {
     if (M <= 0 || K <= 0) return FEAST_OK;
     const int64_t kp = oz_kp(K);
     uint32_t *planes = (uint32_t *)work;
     int *e = (int *)((char *)work + (size_t)OZ_S * 2 * M * kp * 2 + 256);
-    k_oz_rowexp<<<cdiv(M, 128), 128, 0, s>>>(M, K, A, lda, e);
+    k_oz_rowexp<<<cdiv((size_t)M * 32, 256), 256, 0, s>>>(M, K, A, lda, ct, e);
     FEAST_LAUNCH_CHECK();
     const int64_t total = 2 * M * (kp / 2);
-    k_oz_slice_rows<<<cdiv(total, 256) > 16384 ? 16384 : cdiv(total, 256), 256, 0, s>>>(M, K, A, lda, e, planes, kp);
+    k_oz_slice_rows<<<cdiv(total, 256) > 16384 ? 16384 : cdiv(total, 256), 256, 0, s>>>(M, K, A, lda, ct, e, planes,
+                                                                                         kp);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }

@@ -129,23 +129,33 @@ __global__ void __launch_bounds__(128) k_tc_cgemm(const __grid_constant__ CUtens
             tmem_ld32(taddr, v);
             // even lane (Re row) stores columns 0..15 of this chunk, odd lane
             // (Im row) stores 16..31; each needs its partner's values
+            const int half = im_row ? 1 : 0;
+            float dre[16], dim[16];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const float mine = __uint_as_float(v[j]);
                 const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                const int half = im_row ? 1 : 0;
                 if ((j >> 4) == half) {
-                    const int col = col0 + c0 + j;
-                    if (r < mr && col < n) {
-                        const float re = im_row ? other : mine;
-                        const float im = im_row ? mine : other;
-                        float2 *dst = Cb + ci + (int64_t)col * ldc;
-                        float2 o = *dst;
-                        float2 res;
-                        res.x = alpha.x * re - alpha.y * im + beta.x * o.x - beta.y * o.y;
-                        res.y = alpha.x * im + alpha.y * re + beta.x * o.y + beta.y * o.x;
-                        *dst = res;
-                    }
+                    dre[j & 15] = im_row ? other : mine;
+                    dim[j & 15] = im_row ? mine : other;
+                }
+            }
+            // the 16 old values first (independent loads in flight), then the update
+            const bool rd = (beta.x != 0.f || beta.y != 0.f);
+            float2 old[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = col0 + c0 + half * 16 + i;
+                old[i] = (rd && r < mr && col < n) ? Cb[ci + (int64_t)col * ldc] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = col0 + c0 + half * 16 + i;
+                if (r < mr && col < n) {
+                    float2 res;
+                    res.x = alpha.x * dre[i] - alpha.y * dim[i] + beta.x * old[i].x - beta.y * old[i].y;
+                    res.y = alpha.x * dim[i] + alpha.y * dre[i] + beta.x * old[i].y + beta.y * old[i].x;
+                    Cb[ci + (int64_t)col * ldc] = res;
                 }
             }
         }

@@ -6,15 +6,16 @@
 // eigenpairs are those of (A~, B~).  Then:
 //   1. Hessenberg reduction C = Q H Q^H by Householder reflectors, one
 //      column per step, each step a handful of grid-wide kernels;
-//   2. single-shift complex QR sweeps on H with deflation, accumulating the
-//      Schur vectors into Q, in double-single arithmetic (~46 bits) on the
-//      FP32 pipe.  A sweep's rotations form a dependent chain, so they are
-//      generated in chunks of CH rotations by one warp on a small diagonal
-//      block held in shared memory, and the rest of each rotation (the long
-//      row / column / Schur-vector segments, which no later rotation of the
-//      chunk reads) is applied by the whole grid in one parallel pass.  The
-//      grid is a cooperative launch; its barriers spin with an iteration
-//      limit and report a timeout instead of hanging;
+//   2. QR iteration on H with deflation, accumulating the Schur vectors
+//      into Q, in double-single arithmetic (~46 bits) on the FP32 pipe (the
+//      FP64 pipe is 64x slower): aggressive early deflation on a trailing
+//      window (Schur form of the window by one CTA, deflation by the spike
+//      test, reordering, Householder back to Hessenberg), then multishift
+//      sweeps whose bulges are chased concurrently, one CTA each, on small
+//      diagonal blocks in shared memory, with the long row / column /
+//      Schur-vector segments of each chunk of rotations applied by the whole
+//      grid.  The grid is a cooperative launch; its barriers spin with an
+//      iteration limit and report a timeout instead of hanging;
 //   3. right eigenvectors of the triangular Schur form by back-substitution
 //      (one warp per eigenvector), mapped back by Q (a GEMM), unit norm.
 // The small-pencil path (m0 <= 64, one warp, shared memory) is the QZ
@@ -100,16 +101,29 @@ __global__ void k_rank1_left(int rows, int cols, zd *M, int ld, const zd *v, con
 }
 
 // u[r] = sum_c M[r, c0 + c] v[c]  for the rows of two matrices stacked
-// (C and Q, each m rows); one thread per row
-__global__ void k_times_v2(int m, int cols, const zd *C, const zd *Q, int ld, const zd *v, zd *u)
+// (C and Q, each m rows).  A CTA takes TV_R rows; its TV_G thread groups
+// split the columns (reads stay coalesced down each column) and the partial
+// sums meet in shared memory.
+constexpr int TV_R = 16, TV_G = 16;
+__global__ void __launch_bounds__(TV_R * TV_G) k_times_v2(int m, int cols, const zd *C, const zd *Q, int ld,
+                                                          const zd *v, zd *u)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= 2 * m) return;
-    const zd *M = (r < m) ? C : Q;
-    const int rr = (r < m) ? r : r - m;
+    __shared__ zd part[TV_G][TV_R];
+    const int tr = threadIdx.x % TV_R, tg = threadIdx.x / TV_R;
+    const int r = blockIdx.x * TV_R + tr;
     zd acc = zmake(0.0, 0.0);
-    for (int c = 0; c < cols; ++c) zfma(acc, M[rr + (int64_t)c * ld], v[c]);
-    u[r] = acc;
+    if (r < 2 * m) {
+        const zd *M = (r < m) ? C : Q;
+        const int rr = (r < m) ? r : r - m;
+        for (int c = tg; c < cols; c += TV_G) zfma(acc, M[rr + (int64_t)c * ld], v[c]);
+    }
+    part[tg][tr] = acc;
+    __syncthreads();
+    if (tg == 0 && r < 2 * m) {
+        zd s = part[0][tr];
+        for (int g = 1; g < TV_G; ++g) s = zadd(s, part[g][tr]);
+        u[r] = s;
+    }
 }
 
 // M[r, c] -= tau u[r] conj(v[c]) for both stacked matrices
@@ -183,7 +197,6 @@ __device__ __forceinline__ ds ds_from(double d)
     float h = (float)d;
     return ds_make(h, (float)(d - (double)h));
 }
-__device__ __forceinline__ float ds_approx(ds x) { return x.h; }
 // 1/sqrt(x), x > 0: float seed and one Newton step in double-single
 __device__ __forceinline__ ds ds_rsqrt(ds x)
 {
@@ -332,8 +345,9 @@ __device__ __forceinline__ Bulge bulge_at(int t, int b, int l, int ihi, int m)
 }
 
 // One chunk of a bulge chase (rotations k0 .. k0+nrot-1) on the diagonal
-// block [b0, b1] held in shared memory; warp 0 generates the dependent
-// chain.  A bulge enters at k == l with the first column of H - sigma I.
+// block [b0, b1] held in shared memory: a dependent chain of rotations, each
+// formed by every thread from the same shared values and applied by the
+// whole CTA.  A bulge enters at k == l with the first column of H - sigma I.
 // The rotations go to rots_g (global) for the far-part pass.
 __device__ __forceinline__ void chase_chunk(int m, float4 *H, int ld, int l, int ihi, const Bulge &bg, cds sigma,
                             cds (*blk)[BLK + 1], RotDS *lrot, RotDS *rots_g)
@@ -344,31 +358,30 @@ __device__ __forceinline__ void chase_chunk(int m, float4 *H, int ld, int l, int
         blk[r][c] = ld_cds(H + (b0 + r) + (int64_t)(b0 + c) * ld);
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        for (int k = k0; k < k1; ++k) {
-            const int kr = k - b0;
-            cds x, y;
-            if (k == l) {
-                x = cds_sub(blk[kr][kr], sigma);
-                y = blk[kr + 1][kr];
-            } else {
-                x = blk[kr][kr - 1];
-                y = blk[kr + 1][kr - 1];
-            }
-            RotDS gr = make_rot_ds(x, y);
-            __syncwarp();
-            const int cs = (k == l) ? kr : kr - 1;
-            for (int c = cs + lane; c < nb; c += 32) rot_left_ds(gr, blk[kr][c], blk[kr + 1][c]);
-            __syncwarp();
-            if (k > l && lane == 0) blk[kr + 1][kr - 1] = cds_zero();
-            const int rl = ((k + 2 < ihi) ? k + 2 : ihi) - b0;
-            for (int r = lane; r <= rl && r < nb; r += 32) rot_right_ds(gr, blk[r][kr], blk[r][kr + 1]);
-            __syncwarp();
-            if (lane == 0) lrot[k - k0] = gr;
+    // every thread forms the rotation (same shared values); the row pair and
+    // the column pair it acts on take one element pair per thread
+    const int t = threadIdx.x;
+    for (int k = k0; k < k1; ++k) {
+        const int kr = k - b0;
+        cds x, y;
+        if (k == l) {
+            x = cds_sub(blk[kr][kr], sigma);
+            y = blk[kr + 1][kr];
+        } else {
+            x = blk[kr][kr - 1];
+            y = blk[kr + 1][kr - 1];
         }
+        const RotDS gr = make_rot_ds(x, y);
+        __syncthreads();
+        const int cs = (k == l) ? kr : kr - 1;
+        if (cs + t < nb) rot_left_ds(gr, blk[kr][cs + t], blk[kr + 1][cs + t]);
+        __syncthreads();
+        if (t == 0 && k > l) blk[kr + 1][kr - 1] = cds_zero();
+        const int rl = ((k + 2 < ihi) ? k + 2 : ihi) - b0;
+        if (t <= rl && t < nb) rot_right_ds(gr, blk[t][kr], blk[t][kr + 1]);
+        if (t == 0) lrot[k - k0] = gr;
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = threadIdx.x; e < nb * nb; e += QT) {
         int r = e % nb, c = e / nb;
         st_cds(H + (b0 + r) + (int64_t)(b0 + c) * ld, blk[r][c]);
@@ -421,120 +434,341 @@ __device__ __forceinline__ void far_right(float4 *row, int ld, int nrot, const R
     st_cds(row + (int64_t)nrot * ld, carry);
 }
 
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b)
-{
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float f2_abs(float2 a) { return hypotf(a.x, a.y); }
+// ------------------------------------------------- aggressive early deflation
+// A trailing window of the active block is brought to Schur form by one CTA
+// in shared memory; eigenvalues whose "spike" entry (the window's coupling
+// column times the first row of its Schur vectors) is negligible deflate
+// at once, the others are moved to the top of the window and serve as the
+// next sweep's shifts; the rest of the window goes back to Hessenberg form
+// by Householder reflections and the whole window transform is applied to
+// the rest of H and to Z by the grid.
+constexpr int NW = 48;           // largest deflation window
+constexpr int NWP = NW + 1;
 
-// Shifts for a multishift sweep: the eigenvalues of the trailing ns x ns
-// block of H, from a single-shift QR in FP32 by one warp (shifts steer
-// convergence only; they need no more accuracy than this).  If the small
-// QR stalls, the unconverged diagonal entries serve.
-__device__ __forceinline__ void trailing_shifts(int lo, int ns, const float4 *H, int ld, float2 (*a)[NSH + 1], float2 *out)
+__device__ __forceinline__ ds ds_sqrt(ds x) { return (x.h > 0.f) ? ds_mul(x, ds_rsqrt(x)) : ds_make(0.f, 0.f); }
+__device__ __forceinline__ cds cds_neg(cds a) { cds r; r.re = ds_neg(a.re); r.im = ds_neg(a.im); return r; }
+__device__ __forceinline__ cds cds_shfl_xor(cds a, int m)
 {
-    for (int e = threadIdx.x; e < ns * ns; e += QT) {
-        int r = e % ns, c = e / ns;
-        float4 v = __ldcg(H + (lo + r) + (int64_t)(lo + c) * ld);
-        a[r][c] = (r > c + 1) ? make_float2(0.f, 0.f) : make_float2(v.x, v.z);
-    }
+    cds r;
+    r.re = ds_make(__shfl_xor_sync(0xffffffffu, a.re.h, m), __shfl_xor_sync(0xffffffffu, a.re.l, m));
+    r.im = ds_make(__shfl_xor_sync(0xffffffffu, a.im.h, m), __shfl_xor_sync(0xffffffffu, a.im.l, m));
+    return r;
+}
+__device__ __forceinline__ cds cds_shfl(cds a, int src)
+{
+    cds r;
+    r.re = ds_make(__shfl_sync(0xffffffffu, a.re.h, src), __shfl_sync(0xffffffffu, a.re.l, src));
+    r.im = ds_make(__shfl_sync(0xffffffffu, a.im.h, src), __shfl_sync(0xffffffffu, a.im.l, src));
+    return r;
+}
+
+// Apply a rotation (as the bulge chase does) to the w x w window T and its
+// Schur vectors V: rows (k, k+1) of T from column c0, columns (k, k+1) of T
+// over rows 0 .. r1, columns (k, k+1) of V.  Whole CTA; ends synchronised.
+__device__ __forceinline__ void win_rot(const RotDS &gr, int k, int c0, int r1, int w, cds (*T)[NWP],
+                                        cds (*V)[NWP])
+{
+    const int t = threadIdx.x;
+    if (c0 + t < w) rot_left_ds(gr, T[k][c0 + t], T[k + 1][c0 + t]);
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        int hi = ns - 1, it = 0, tot = 0;
-        while (hi > 0) {
-            __syncwarp();
-            int l2 = hi;
-            while (l2 > 0) {
-                float sub = f2_abs(a[l2][l2 - 1]);
-                float loc = f2_abs(a[l2 - 1][l2 - 1]) + f2_abs(a[l2][l2]);
-                if (sub <= 3e-7f * loc || sub == 0.f) break;
-                --l2;
-            }
-            if (l2 == hi) { --hi; it = 0; continue; }
-            if (++tot > 30 * ns) break;
-            ++it;
-            float2 sig;
-            const float2 h00 = a[hi - 1][hi - 1], h01 = a[hi - 1][hi], h10 = a[hi][hi - 1], h11 = a[hi][hi];
-            if (it % 10 == 0) {
-                float s = f2_abs(h10);
-                sig = make_float2(h11.x + s, h11.y + 0.5f * s);
+    if (t <= r1) rot_right_ds(gr, T[t][k], T[t][k + 1]);
+    if (t >= 64 && t - 64 < w) rot_right_ds(gr, V[t - 64][k], V[t - 64][k + 1]);
+    __syncthreads();
+}
+
+// Schur form of the w x w upper Hessenberg T (in place) with Schur vectors
+// accumulated into V (which starts as I): single-shift QR with full window
+// updates.  Whole CTA; false if the iteration budget runs out.
+__device__ bool win_schur(int w, cds (*T)[NWP], cds (*V)[NWP], float tol_rel, float tol_abs)
+{
+    int hi = w - 1, it = 0, tot = 0;
+    while (hi > 0) {
+        int lo = hi;
+        while (lo > 0) {
+            const float sub = cds_absf(T[lo][lo - 1]);
+            const float loc = cds_absf(T[lo - 1][lo - 1]) + cds_absf(T[lo][lo]);
+            if (sub <= tol_rel * loc || sub <= tol_abs) break;
+            --lo;
+        }
+        __syncthreads();
+        if (lo > 0 && threadIdx.x == 0) T[lo][lo - 1] = cds_zero();
+        if (lo == hi) { --hi; it = 0; __syncthreads(); continue; }
+        if (++tot > 40 * w) return false;
+        ++it;
+        cds sigma;
+        {
+            const cds h00 = T[hi - 1][hi - 1], h01 = T[hi - 1][hi], h10 = T[hi][hi - 1], h11 = T[hi][hi];
+            if (it % 11 == 10) {
+                const float a = cds_absf(h10);
+                sigma = h11;
+                sigma.re = ds_add(sigma.re, ds_make(a, 0.f));
+                sigma.im = ds_add(sigma.im, ds_make(0.5f * a, 0.f));
             } else {
-                float2 half = make_float2(0.5f * (h00.x + h11.x), 0.5f * (h00.y + h11.y));
-                float2 det = f2_sub(f2_mul(h00, h11), f2_mul(h01, h10));
-                float2 d = f2_sub(f2_mul(half, half), det);
-                float r = f2_abs(d);
-                float2 sq = make_float2(0.f, 0.f);
-                if (r > 0.f) {
-                    if (d.x >= 0.f) {
-                        float t = sqrtf(0.5f * (r + d.x));
-                        sq = make_float2(t, d.y / (2.f * t));
-                    } else {
-                        float t = sqrtf(0.5f * (r - d.x));
-                        sq = make_float2(fabsf(d.y) / (2.f * t), copysignf(t, d.y));
-                    }
-                }
-                float2 r1 = f2_add(half, sq), r2 = f2_sub(half, sq);
-                sig = (f2_abs(f2_sub(r1, h11)) < f2_abs(f2_sub(r2, h11))) ? r1 : r2;
-            }
-            for (int k = l2; k < hi; ++k) {
-                __syncwarp();
-                float2 x, y;
-                if (k == l2) { x = f2_sub(a[k][k], sig); y = a[k + 1][k]; }
-                else { x = a[k][k - 1]; y = a[k + 1][k - 1]; }
-                const float ax = f2_abs(x), ay = f2_abs(y);
-                float c;
-                float2 sn;
-                if (ay == 0.f) { c = 1.f; sn = make_float2(0.f, 0.f); }
-                else if (ax == 0.f) { c = 0.f; sn = make_float2(1.f, 0.f); }
-                else {
-                    const float rr = hypotf(ax, ay);
-                    c = ax / rr;
-                    // (x / |x|) conj(y) / r
-                    const float2 ph = make_float2(x.x / ax, x.y / ax);
-                    sn = f2_mul(ph, make_float2(y.x / rr, -y.y / rr));
-                }
-                __syncwarp();
-                const int cs = (k == l2) ? k : k - 1;
-                for (int col = cs + lane; col <= hi; col += 32) {
-                    float2 p = a[k][col], q = a[k + 1][col];
-                    a[k][col] = f2_add(make_float2(c * p.x, c * p.y), f2_mul(sn, q));
-                    a[k + 1][col] = f2_sub(make_float2(c * q.x, c * q.y), f2_mul(make_float2(sn.x, -sn.y), p));
-                }
-                __syncwarp();
-                if (k > l2 && lane == 0) a[k + 1][k - 1] = make_float2(0.f, 0.f);
-                const int rl = (k + 2 < hi) ? k + 2 : hi;
-                for (int row = l2 + lane; row <= rl; row += 32) {
-                    float2 p = a[row][k], q = a[row][k + 1];
-                    a[row][k] = f2_add(make_float2(c * p.x, c * p.y), f2_mul(q, make_float2(sn.x, -sn.y)));
-                    a[row][k + 1] = f2_sub(make_float2(c * q.x, c * q.y), f2_mul(p, sn));
-                }
+                cds half = cds_scale(cds_add(h00, h11), ds_make(0.5f, 0.f));
+                cds det = cds_sub(cds_mul(h00, h11), cds_mul(h01, h10));
+                cds disc = csqrt_ds_approx(cds_sub(cds_mul(half, half), det));
+                cds r1 = cds_add(half, disc), r2 = cds_sub(half, disc);
+                sigma = (cds_absf(cds_sub(r1, h11)) < cds_absf(cds_sub(r2, h11))) ? r1 : r2;
             }
         }
-        __syncwarp();
-        for (int i = lane; i < ns; i += 32) out[i] = a[i][i];
+        __syncthreads();
+        for (int k = lo; k < hi; ++k) {
+            cds x, y;
+            if (k == lo) { x = cds_sub(T[k][k], sigma); y = T[k + 1][k]; }
+            else { x = T[k][k - 1]; y = T[k + 1][k - 1]; }
+            const RotDS gr = make_rot_ds(x, y);
+            __syncthreads();
+            win_rot(gr, k, (k == lo) ? k : k - 1, (k + 2 < hi) ? k + 2 : hi, w, T, V);
+            if (k > lo && threadIdx.x == 0) T[k + 1][k - 1] = cds_zero();
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// Swap the adjacent diagonal entries p-1, p of the upper-triangular T (and
+// update V): the rotation that maps the eigenvector of T[p][p], (c, b - a),
+// onto e1.  Whole CTA.
+__device__ __forceinline__ void win_swap(int p, int w, cds (*T)[NWP], cds (*V)[NWP])
+{
+    const cds a = T[p - 1][p - 1], b = T[p][p], c = T[p - 1][p];
+    const RotDS gr = make_rot_ds(c, cds_sub(b, a));
+    __syncthreads();
+    win_rot(gr, p - 1, p - 1, p, w, T, V);
+    if (threadIdx.x == 0) T[p][p - 1] = cds_zero();
+    __syncthreads();
+}
+
+// Householder reflector I - tau v v^H mapping x (len entries, stride sx
+// through shared memory) onto alpha e1; v written to vout, tau to *tau
+// (0: identity).  One warp (lanes take entries i = lane, lane + 32).
+__device__ void win_house(const cds *x, int sx, int len, cds *vout, ds *tau, cds *alpha_out)
+{
+    const int lane = threadIdx.x & 31;
+    ds s = ds_make(0.f, 0.f);
+    for (int i = lane; i < len; i += 32) s = ds_add(s, cds_abs2(x[i * sx]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        s = ds_add(s, ds_make(__shfl_xor_sync(0xffffffffu, s.h, off), __shfl_xor_sync(0xffffffffu, s.l, off)));
+    const cds x0 = x[0];
+    const ds a02 = cds_abs2(x0);
+    const ds nrm = ds_sqrt(s), a0 = ds_sqrt(a02);
+    const bool trivial = (s.h == 0.f) || (ds_sub(s, a02).h <= 0.f);   // nothing below the first entry
+    for (int i = lane; i < len; i += 32) {
+        cds v = x[i * sx];
+        if (i == 0 && !trivial) {
+            // v0 = x0 + (x0/|x0|) ||x||
+            cds ph;
+            if (a0.h > 0.f) ph = cds_scale(x0, ds_rsqrt(a02));
+            else { ph = cds_zero(); ph.re = ds_make(1.f, 0.f); }
+            v = cds_add(x0, cds_scale(ph, nrm));
+        }
+        vout[i] = v;
+    }
+    if (lane == 0) {
+        if (trivial) {
+            *tau = ds_make(0.f, 0.f);
+            *alpha_out = x0;
+        } else {
+            cds ph;
+            if (a0.h > 0.f) ph = cds_scale(x0, ds_rsqrt(a02));
+            else { ph = cds_zero(); ph.re = ds_make(1.f, 0.f); }
+            const ds d = ds_mul(nrm, ds_add(nrm, a0));                 // ||v||^2 / 2
+            const ds r = ds_rsqrt(d);
+            *tau = ds_mul(r, r);
+            *alpha_out = cds_neg(cds_scale(ph, nrm));
+        }
+    }
+}
+
+// M <- H M over rows r0 .. r0+len-1, columns c0 .. c1-1, H = I - tau v v^H.
+// Four threads per column.  Whole CTA; ends synchronised.
+__device__ __forceinline__ void win_house_left(cds (*M)[NWP], int r0, int len, int c0, int c1, const cds *v, ds tau)
+{
+    const int col = c0 + (int)(threadIdx.x >> 2), part = threadIdx.x & 3;
+    cds acc = cds_zero();
+    if (col < c1)
+        for (int i = part; i < len; i += 4) acc = cds_add(acc, cds_mul(cds_conj(v[i]), M[r0 + i][col]));
+    acc = cds_add(acc, cds_shfl_xor(acc, 1));
+    acc = cds_add(acc, cds_shfl_xor(acc, 2));
+    __syncthreads();
+    if (col < c1) {
+        const cds f = cds_scale(acc, tau);
+        for (int i = part; i < len; i += 4) M[r0 + i][col] = cds_sub(M[r0 + i][col], cds_mul(v[i], f));
+    }
+    __syncthreads();
+}
+// M <- M H over columns c0 .. c0+len-1, rows 0 .. rows-1.  Whole CTA.
+__device__ __forceinline__ void win_house_right(cds (*M)[NWP], int rows, int c0, int len, const cds *v, ds tau)
+{
+    const int row = (int)(threadIdx.x >> 2), part = threadIdx.x & 3;
+    cds acc = cds_zero();
+    if (row < rows)
+        for (int i = part; i < len; i += 4) acc = cds_add(acc, cds_mul(M[row][c0 + i], v[i]));
+    acc = cds_add(acc, cds_shfl_xor(acc, 1));
+    acc = cds_add(acc, cds_shfl_xor(acc, 2));
+    __syncthreads();
+    if (row < rows) {
+        const cds f = cds_scale(acc, tau);
+        for (int i = part; i < len; i += 4) M[row][c0 + i] = cds_sub(M[row][c0 + i], cds_mul(f, cds_conj(v[i])));
+    }
+    __syncthreads();
+}
+
+struct AedShared {
+    cds T[NW][NWP];
+    cds V[NW][NWP];
+    cds hv[NW];          // Householder vector
+    cds spk[NW];         // spike
+    ds tau;
+    cds alpha;
+    int nd, ok;
+};
+
+// AED on the window [kw, kw + w - 1] (kw = ihi - w + 1) of the active block
+// starting at l.  CTA 0 only.  Writes the window's new contents to H, the
+// spike column, the total window transform to vg (w x w), shifts of the
+// undeflated part (up to ns, the bottom-most) to shifts, and returns nd
+// (deflated count) in sh->nd; nd = 0 leaves H untouched.
+__device__ void aed_window(int m, float4 *H, int ld, int l, int kw, int w, int ns, float tol_rel, float tol_abs,
+                           AedShared *sh, float4 *vg, float2 *shifts)
+{
+    const int t = threadIdx.x;
+    for (int e = t; e < w * w; e += QT) {
+        const int r = e % w, c = e / w;
+        sh->T[r][c] = (r > c + 1) ? cds_zero() : ld_cds(H + (kw + r) + (int64_t)(kw + c) * ld);
+        cds v = cds_zero();
+        if (r == c) v.re = ds_make(1.f, 0.f);
+        sh->V[r][c] = v;
+    }
+    if (t == 0) { sh->nd = 0; sh->ok = 1; }
+    __syncthreads();
+    const bool ok = win_schur(w, sh->T, sh->V, tol_rel, tol_abs);
+    const cds s = (kw > l) ? ld_cds(H + kw + (int64_t)(kw - 1) * ld) : cds_zero();
+    const float sabs = cds_absf(s);
+    int nd = 0;
+    if (ok) {
+        // deflation test from the bottom; undeflatable eigenvalues move to the top
+        int top = 0, cur = w - 1;
+        while (cur >= top) {
+            const float spike = sabs * cds_absf(sh->V[0][cur]);
+            const float d = cds_absf(sh->T[cur][cur]);
+            if (spike <= tol_rel * d || spike <= tol_abs) {
+                ++nd;
+                --cur;
+            } else {
+                for (int p = cur; p > top; --p) win_swap(p, w, sh->T, sh->V);
+                ++top;
+            }
+        }
+    }
+    const int u = w - nd;
+    // shifts: the bottom-most undeflated eigenvalues (all of them if fewer)
+    if (t < ns) {
+        const int idx = (u > ns) ? u - ns + t : (u > 0 ? t % u : 0);
+        const cds e = (u > 0) ? sh->T[idx][idx] : sh->T[w - 1][w - 1];
+        shifts[t] = make_float2(e.re.h + e.re.l, e.im.h + e.im.l);
+    }
+    if (t == 0) sh->nd = (ok ? nd : 0);
+    __syncthreads();
+    if (!ok || nd == 0) return;
+    // spike of the undeflated part; Hessenberg form back by Householder
+    // reflections on the window rows/cols 0 .. u-1 (the spike is column -1)
+    for (int j = t; j < u; j += QT) sh->spk[j] = cds_mul(s, cds_conj(sh->V[0][j]));
+    __syncthreads();
+    if (kw > l && u > 1) {
+        // reflector for the spike
+        if (t < 32) win_house(sh->spk, 1, u, sh->hv, &sh->tau, &sh->alpha);
+        __syncthreads();
+        win_house_left(sh->T, 0, u, 0, w, sh->hv, sh->tau);
+        win_house_right(sh->T, u, 0, u, sh->hv, sh->tau);
+        win_house_right(sh->V, w, 0, u, sh->hv, sh->tau);
+        if (t == 0) {
+            sh->spk[0] = sh->alpha;
+        }
+        for (int j = 1 + t; j < u; j += QT) sh->spk[j] = cds_zero();
+        __syncthreads();
+        // Hessenberg reduction of the leading u x u block
+        for (int j = 0; j + 2 < u; ++j) {
+            if (t < 32) win_house(&sh->T[j + 1][j], NWP, u - j - 1, sh->hv, &sh->tau, &sh->alpha);
+            __syncthreads();
+            win_house_left(sh->T, j + 1, u - j - 1, j, w, sh->hv, sh->tau);
+            win_house_right(sh->T, u, j + 1, u - j - 1, sh->hv, sh->tau);
+            win_house_right(sh->V, w, j + 1, u - j - 1, sh->hv, sh->tau);
+            for (int i = j + 2 + t; i < u; i += QT) sh->T[i][j] = cds_zero();
+            __syncthreads();
+        }
+    }
+    // window and spike back to H; the window transform to vg
+    for (int e = t; e < w * w; e += QT) {
+        const int r = e % w, c = e / w;
+        st_cds(H + (kw + r) + (int64_t)(kw + c) * ld, (r > c + 1) ? cds_zero() : sh->T[r][c]);
+        st_cds(vg + r + (int64_t)c * w, sh->V[r][c]);
+    }
+    if (kw > l)
+        for (int j = t; j < w; j += QT) st_cds(H + (kw + j) + (int64_t)(kw - 1) * ld, (j < u) ? sh->spk[j] : cds_zero());
+}
+
+// Apply the window transform W (w x w, in shared memory) to the rest of H
+// and to Z: H[0:kw, win] <- H[0:kw, win] W, H[win, c] <- W^H H[win, c] for
+// c > kw + w - 1, Z[:, win] <- Z[:, win] W.  One warp per line.
+__device__ void aed_apply(int m, float4 *H, float4 *Z, int ld, int kw, int w, const cds (*W)[NWP])
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * QT + threadIdx.x) >> 5, nwarps = (gridDim.x * QT) >> 5;
+    const int right = m - (kw + w);
+    const int lines = kw + m + right;
+    for (int x = gw; x < lines; x += nwarps) {
+        float4 *base;
+        int64_t stride;
+        bool colline;
+        if (x < kw) { base = H + x + (int64_t)kw * ld; stride = ld; colline = false; }
+        else if (x < kw + m) { base = Z + (x - kw) + (int64_t)kw * ld; stride = ld; colline = false; }
+        else { base = H + kw + (int64_t)(kw + w + (x - kw - m)) * ld; stride = 1; colline = true; }
+        cds in0 = cds_zero(), in1 = cds_zero();
+        if (lane < w) in0 = ld_cds(base + (int64_t)lane * stride);
+        if (lane + 32 < w) in1 = ld_cds(base + (int64_t)(lane + 32) * stride);
+        cds o0 = cds_zero(), o1 = cds_zero();
+        for (int k = 0; k < w; ++k) {
+            const cds xk = (k < 32) ? cds_shfl(in0, k) : cds_shfl(in1, k - 32);
+            if (colline) {
+                // (W^H x)_j = sum_k conj(W[k][j]) x_k
+                if (lane < w) o0 = cds_add(o0, cds_mul(cds_conj(W[k][lane]), xk));
+                if (lane + 32 < w) o1 = cds_add(o1, cds_mul(cds_conj(W[k][lane + 32]), xk));
+            } else {
+                // (x W)_j = sum_k x_k W[k][j]
+                if (lane < w) o0 = cds_add(o0, cds_mul(xk, W[k][lane]));
+                if (lane + 32 < w) o1 = cds_add(o1, cds_mul(xk, W[k][lane + 32]));
+            }
+        }
+        if (lane < w) st_cds(base + (int64_t)lane * stride, o0);
+        if (lane + 32 < w) st_cds(base + (int64_t)(lane + 32) * stride, o1);
     }
 }
 
 // Whole QR phase in double-single: all CTAs run the same control flow (every
 // decision is a function of values read after a grid barrier).  Active
-// windows of at least MS_MIN rows take multishift sweeps: ns shifts (the
-// eigenvalues of the trailing ns x ns block) drive ns bulges through the
-// window, each chased by its own CTA on its own diagonal block, and after
-// each phase the whole grid applies the chunks' far parts -- first every
-// bulge's left rotations (row segments right of its block), then every
-// bulge's right rotations (column segments above its block, and Z), so no
-// two writers meet.  Smaller windows take single-shift sweeps (Wilkinson
-// shift, exceptional shift every 11th sweep).  H, Z: m x m double-single
-// (float4), leading dim ld; rots: NSH * CH rotations; shifts: NSH entries.
+// blocks of at least MS_MIN rows take aggressive early deflation on their
+// bottom NW rows (CTA 0), whose undeflated eigenvalues then serve as the ns
+// shifts of a multishift sweep: ns bulges through the block, each chased by
+// its own CTA on its own diagonal block, and after each phase the whole
+// grid applies the chunks' far parts -- first every bulge's left rotations
+// (row segments right of its block), then every bulge's right rotations
+// (column segments above its block, and Z), so no two writers meet.  Blocks
+// of at most NW rows are brought to Schur form at once by the window
+// routine; those in between take single-shift sweeps (Wilkinson shift,
+// exceptional shift every 11th sweep).  H, Z: m x m double-single (float4),
+// leading dim ld; rots: NSH * CH rotations; shifts: NSH entries; vwin: the
+// NW x NW window transform; ctl: the window's deflation count.
 __global__ void __launch_bounds__(QT, 1) k_hqr(int m, float4 *H, float4 *Z, int ld, RotDS *rots, float2 *shifts,
-                                            GridSync g, int *fail, float tol_rel, float tol_abs)
+                                               float4 *vwin, int *ctl, GridSync g, int *fail, float tol_rel,
+                                               float tol_abs, int *stats)
 {
+    extern __shared__ __align__(16) unsigned char hqr_dyn[];
+    AedShared *sh = (AedShared *)hqr_dyn;
     __shared__ cds blk[BLK][BLK + 1];
     __shared__ RotDS srot[NSH][CH];
-    __shared__ float2 sa[NSH][NSH + 1];
     const int gtid = blockIdx.x * QT + threadIdx.x, gthreads = gridDim.x * QT;
     int ihi = m - 1, iter = 0, total = 0;
     while (ihi > 0) {
@@ -558,24 +792,63 @@ __global__ void __launch_bounds__(QT, 1) k_hqr(int m, float4 *H, float4 *Z, int 
         total += ns;
         if (total > 30 * m) { if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(fail, 1); return; }
         ++iter;
+        if (L <= NW) {
+            // the whole active block fits a window: its Schur form at once
+            if (blockIdx.x == 0) {
+                aed_window(m, H, ld, l, l, L, 1, tol_rel, tol_abs, sh, vwin, shifts);
+                if (threadIdx.x == 0) __stcg(ctl, sh->nd);
+            }
+            if (!grid_barrier(g)) return;
+            if (__ldcg(ctl) > 0) {
+                for (int e = threadIdx.x; e < L * L; e += QT) sh->T[e % L][e / L] = ld_cds(vwin + e);
+                __syncthreads();
+                aed_apply(m, H, Z, ld, l, L, sh->T);
+                if (!grid_barrier(g)) return;
+                if (stats && blockIdx.x == 0 && threadIdx.x == 0) stats[2] += 1;
+                continue;
+            }
+            // (window iteration budget ran out: fall through to a single-shift sweep)
+        }
         if (ns > 1) {
             // ------------------------------------------------ multishift sweep
+            // aggressive early deflation on the bottom NW rows first; its
+            // undeflated eigenvalues are the sweep's shifts
+            const int kw = ihi - NW + 1;
             if (blockIdx.x == 0) {
+                aed_window(m, H, ld, l, kw, NW, ns, tol_rel, tol_abs, sh, vwin, shifts);
+                if (threadIdx.x == 0) __stcg(ctl, sh->nd);
                 if (iter % 6 == 5) {
                     // exceptional shifts: perturbed trailing diagonal
+                    __syncthreads();
+                    const int nd = sh->nd;
                     for (int b = threadIdx.x; b < ns; b += QT) {
-                        const int i = ihi - b;
+                        const int i = ihi - nd - b;
                         float4 d = __ldcg(H + i + (int64_t)i * ld), e = __ldcg(H + i + (int64_t)(i - 1) * ld);
                         const float s = hypotf(e.x, e.z);
                         shifts[b] = make_float2(d.x + 0.75f * s, d.z + 0.4f * s);
                     }
-                } else {
-                    trailing_shifts(ihi - ns + 1, ns, H, ld, sa, shifts);
                 }
             }
-            // every CTA has finished its scan, and the shifts are out
+            // every CTA has finished its scan; window, shifts and ctl are out
             if (!grid_barrier(g)) return;
+            const int nd = __ldcg(ctl);
+            if (nd > 0) {
+                for (int e = threadIdx.x; e < NW * NW; e += QT) sh->T[e % NW][e / NW] = ld_cds(vwin + e);
+                __syncthreads();
+                aed_apply(m, H, Z, ld, kw, NW, sh->T);
+                if (!grid_barrier(g)) return;
+                if (stats && blockIdx.x == 0 && threadIdx.x == 0) stats[2] += 1;
+                iter = 0;
+                // many deflations: look again before sweeping
+                if (nd * 100 >= NW * 14) continue;
+                ihi -= nd;
+                if (ihi - l + 1 < MS_MIN) continue;
+            }
             const int nphase = (ihi - l + CH - 1) / CH + DSEP * (ns - 1);
+            if (stats && blockIdx.x == 0 && threadIdx.x == 0) {
+                stats[0] += 1;
+                stats[1] += nphase;
+            }
             for (int t = 0; t < nphase; ++t) {
                 if ((int)blockIdx.x < ns) {
                     const int b = blockIdx.x;
@@ -656,6 +929,10 @@ __global__ void __launch_bounds__(QT, 1) k_hqr(int m, float4 *H, float4 *Z, int 
                 cds r1 = cds_add(half, disc), r2 = cds_sub(half, disc);
                 sigma = (cds_absf(cds_sub(r1, h11)) < cds_absf(cds_sub(r2, h11))) ? r1 : r2;
             }
+        }
+        if (stats && blockIdx.x == 0 && threadIdx.x == 0) {
+            stats[0] += 1;
+            stats[1] += (ihi - l + CH - 1) / CH;
         }
         // every CTA has read what it needs for l, ihi and sigma before CTA 0
         // starts rewriting the leading block of the sweep
@@ -772,13 +1049,13 @@ size_t zeig_large_work_bytes(int m)
     // barrier words, then the double-single copies of H and Q (m*m float4
     // each)
     return sizeof(zd) * ((size_t)m * m + 4 * (size_t)m) + 64 + sizeof(RotDS) * NSH * CH +
-           sizeof(float2) * NSH + 64 + 256 + 2 * sizeof(float4) * (size_t)m * m;
+           sizeof(float2) * NSH + sizeof(float4) * NW * NW + 16 + 64 + 256 + 2 * sizeof(float4) * (size_t)m * m;
 }
 
 // A (m x m, overwritten), Bt (m x m upper triangular, overwritten by the
 // solve), alpha/beta (beta = 1), V (m x m unit eigenvectors).
 int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
-               int *fail, int *timeout)
+               int *fail, int *timeout, int *stats)
 {
     if (m <= 0) return FEAST_OK;
     char *w = (char *)work;
@@ -790,7 +1067,9 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     double *hmax = tau + 1;
     RotDS *rots = (RotDS *)(hmax + 7);
     float2 *shifts = (float2 *)(rots + NSH * CH);
-    unsigned *bar = (unsigned *)(shifts + NSH);
+    float4 *vwin = (float4 *)(shifts + NSH);
+    int *ctl = (int *)(vwin + NW * NW);
+    unsigned *bar = (unsigned *)(ctl + 4);
     float4 *Hds = (float4 *)(((uintptr_t)(bar + 16) + 255) & ~(uintptr_t)255);
     float4 *Qds = Hds + (size_t)m * m;
     int e;
@@ -810,8 +1089,8 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
         unsigned g1 = cdiv((size_t)len * len, 256);
         k_rank1_left<<<g1 > 4096 ? 4096 : g1, 256, 0, s>>>(len, len, blkC, m, v, wv, tau);
         FEAST_LAUNCH_CHECK();
-        k_times_v2<<<cdiv((size_t)2 * m, 128), 128, 0, s>>>(m, len, C + (int64_t)(j + 1) * m,
-                                                           Q + (int64_t)(j + 1) * m, m, v, u);
+        k_times_v2<<<cdiv((size_t)2 * m, TV_R), TV_R * TV_G, 0, s>>>(m, len, C + (int64_t)(j + 1) * m,
+                                                                       Q + (int64_t)(j + 1) * m, m, v, u);
         FEAST_LAUNCH_CHECK();
         unsigned g2 = cdiv((size_t)2 * m * len, 256);
         k_rank1_right2<<<g2 > 4096 ? 4096 : g2, 256, 0, s>>>(m, len, C + (int64_t)(j + 1) * m,
@@ -831,7 +1110,9 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     int dev = 0, sms = 0, per = 0;
     FEAST_CUDA_TRY(cudaGetDevice(&dev));
     FEAST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hqr, QT, 0));
+    const size_t dyn = sizeof(AedShared);
+    FEAST_CUDA_TRY(cudaFuncSetAttribute(k_hqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hqr, QT, dyn));
     if (per < 1) return FEAST_ECUDA;
     // one CTA per SM (the far-part pass has ~3 m independent lines, each a
     // chain of up to CH rotations on the FP64 pipe, so every SM's FP64 units
@@ -846,8 +1127,8 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     FEAST_LAUNCH_CHECK();
     k_to_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, Q, Qds);
     FEAST_LAUNCH_CHECK();
-    void *args[] = {&mm, &Hds, &Qds, &ldh, &rots, &shifts, &gs, &fail, &tol_rel, &tol_abs};
-    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hqr, dim3(grid), dim3(QT), args, 0, s));
+    void *args[] = {&mm, &Hds, &Qds, &ldh, &rots, &shifts, &vwin, &ctl, &gs, &fail, &tol_rel, &tol_abs, &stats};
+    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hqr, dim3(grid), dim3(QT), args, dyn, s));
     FEAST_LAUNCH_CHECK();
     k_from_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, Hds, C);
     FEAST_LAUNCH_CHECK();

@@ -176,10 +176,15 @@ WORKLOADS = {
     # mid-size dense case for kernel profiles (same generator)
     "dense_n1024_m256_q8": dict(n=1024, m0=256, q=8, rule=0, center=0j, radius=1.0, seed=0,
                                 eps=1e-10),
+    # profiling size whose operands exceed the 129 MB L2 with ~3 GB on the device
+    "dense_n2048_m512_q8": dict(n=2048, m0=512, q=8, rule=0, center=0j, radius=1.0, seed=0,
+                                eps=1e-10),
     # banded convection-diffusion, 128 x 128 grid (n = 16384, kl = ku = 128),
     # B = I, ellipse around the lowest 41 eigenvalues, 16 Gauss-Legendre nodes
     "band_n16384_m64_q16": dict(nx=128, m0=64, q=16, rule=1, center=422.0 + 0j, a=322.0,
                                 b=80.5, seed=0, eps=1e-10, beta=(20.0, 10.0)),
+    # ragged batch: 256 dense pencils, n ~ U[64, 1024], own circles, 16 nodes
+    "batch_256_n64_1024_q16": dict(batch=256, n_lo=64, n_hi=1024, q=16, seed=0, eps=1e-10),
 }
 
 
