@@ -44,7 +44,7 @@ extern "C" {
 #define FEAST_ESINGULAR  -4   /* a shifted matrix z_j B - A has an exact zero pivot */
 #define FEAST_ENONFINITE -5   /* NaN or Inf reached a residual                    */
 #define FEAST_ETIMEOUT   -6   /* a bounded device wait gave up                    */
-#define FEAST_ENOCONV    -7   /* the projected QZ iteration hit its iteration cap */
+#define FEAST_ENOCONV    -7   /* the projected QZ hit its iteration cap, or two runs disagree */
 #define FEAST_EDONE      -8   /* feast_iterate called after the algorithm stopped */
 
 /* ------------------------------------------------------------- problem types */
@@ -246,6 +246,22 @@ int feast_zgetrf_batched(int64_t n, int batch, void *M, int64_t ld, int64_t stri
 int feast_zgetrs_batched(int64_t n, int64_t nrhs, int batch, const void *M, int64_t ld,
                          int64_t stride, const int *piv, void *X, int64_t ldx, int64_t sx,
                          void *stream);
+
+/* Differentiation form: L = sum over the eigenvalues inside the contour of
+ * |lambda|^2 and its gradients G_A, G_B for a real loss of complex inputs
+ * (dL = Re sum conj(G_A) dA + Re sum conj(G_B) dB).  First-order
+ * perturbation of a simple eigenvalue (right vector x, left vector v):
+ * d lambda = v^H (dA - lambda dB) x / (v^H B x), hence
+ * G_A = sum 2 lambda_i v_i x_i^H / conj(c_i), G_B = -sum 2 |lambda_i|^2
+ * v_i x_i^H / conj(c_i), c_i = v_i^H B x_i.  The paper has no gradient; it
+ * is built on top of the method.  right: a finished run (flag set) on
+ * (A, B); left: a finished run on (A^H, B^H) over the conjugated contour,
+ * whose Ritz vectors are the left eigenvectors (its eigenvalues, conjugated,
+ * are paired with the right ones by nearness).  Dense pencils only.  gA,
+ * gB: device n x n complex128 (leading dim ldg), overwritten; L, count:
+ * host.  FEAST_ENOCONV if the two runs found different inside counts.
+ * Uses the right run's internal scratch; synchronises its stream. */
+int feast_grad_abs2(feast_ctx *right, feast_ctx *left, void *gA, void *gB, int64_t ldg, double *L, int *count);
 
 /* FP64-accurate complex GEMM on the bf16 tensor cores: C = beta C + alpha A B,
  * A m x k, B k x n, C m x n, complex128 column-major (device, leading dims

@@ -13,7 +13,11 @@ the method from the paper:
 * Householder QR (GFEAST lines 2, 17);
 * oblique projection A~ = U2^H A U1, B~ = U2^H B U1 (eq. 3.10, GFEAST line 5);
 * complex QZ for the projected pencil (GFEAST line 6);
-* residual of eq. 5.1, selection, and the three stopping tests (lines 7-15).
+* residual of eq. 5.1, selection, and the three stopping tests (lines 7-15);
+* the derivative of sum_{lambda inside} |lambda|^2 with respect to A and B
+  from first-order perturbation of simple eigenvalues (left / right
+  eigenvectors of the whole pencil by the own QZ) -- for the
+  differentiation form built on top of the method.
 
 Every entry point takes numpy complex128 arrays in Fortran (column-major)
 order.  Parity of each routine is pinned in ``tests/test_oracle_*.py``.
@@ -204,6 +208,45 @@ def ggev(a, b):
     if st:
         raise RuntimeError(f"or_zggev status {st}")
     return al, be, v
+
+
+# --------------------------------------------------------------------------
+# Derivative of L = sum over the eigenvalues inside the contour of |lambda|^2
+# --------------------------------------------------------------------------
+def eig_grad_abs2(A, B, ckind: int, center: complex, a: float, b: float = 0.0):
+    """L and its gradients with respect to A and B for a real loss of complex
+    inputs (dL = Re sum conj(G_A) * dA + Re sum conj(G_B) * dB).
+
+    A simple eigenvalue with right vector x (A x = lam B x) and left vector
+    v (v^H A = lam v^H B) moves by d lam = v^H (dA - lam dB) x / (v^H B x);
+    with dL = sum 2 Re(conj(lam) d lam) this gives
+        G_A = sum_i 2 lam_i v_i x_i^H / conj(c_i),
+        G_B = -sum_i 2 |lam_i|^2 v_i x_i^H / conj(c_i),   c_i = v_i^H B x_i.
+    Right vectors come from the QZ of (A, B), left vectors from the QZ of
+    (A^H, B^H) (its eigenvalues are the conjugates), both over the whole
+    pencil.  Returns (L, G_A, G_B, inside eigenvalues)."""
+    A = _zf(A); B = _zf(B)
+    n = A.shape[0]
+    al, be, X = ggev(A, B)
+    lam = al / be
+    alL, beL, V = ggev(np.conj(A.T), np.conj(B.T))
+    mu = np.conj(alL / beL)
+    ins = [i for i in range(n) if inside(ckind, center, a, b, complex(lam[i]))]
+    free = list(range(n))
+    gA = np.zeros((n, n), np.complex128)
+    gB = np.zeros((n, n), np.complex128)
+    L = 0.0
+    for i in ins:
+        k = min(free, key=lambda j: abs(mu[j] - lam[i]))
+        free.remove(k)
+        x = X[:, i]
+        v = V[:, k]
+        c = np.vdot(v, B @ x)
+        outer = np.outer(v, np.conj(x)) / np.conj(c)
+        gA += 2.0 * lam[i] * outer
+        gB -= 2.0 * abs(lam[i]) ** 2 * outer
+        L += abs(lam[i]) ** 2
+    return L, gA, gB, lam[ins]
 
 
 # --------------------------------------------------------------------------

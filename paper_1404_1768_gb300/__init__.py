@@ -79,7 +79,7 @@ EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs",
            "feast_zgetrf_batched", "feast_zgetrs_batched", "feast_zqz_batched",
            "feast_zqz_work_bytes", "feast_kernel_launches", "feast_zqz_batched_noalloc",
            "feast_batch_workspace_size", "feast_solve_batch", "feast_cgemm_tc_scratch_bytes",
-           "feast_cgemm_tc", "feast_zgemm_oz_work_bytes", "feast_zgemm_oz"]
+           "feast_cgemm_tc", "feast_zgemm_oz_work_bytes", "feast_zgemm_oz", "feast_grad_abs2"]
 
 
 def lib_path() -> str:
@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True):
         F = C.c_float
         lib.feast_cgemm_tc.argtypes = [I64, I64, I64, F, F, P, I64, I64, P, I64, I64, F, F, P, I64, I64,
                                        I, P, C.c_size_t, P, P]
+        lib.feast_grad_abs2.argtypes = [P, P, P, P, I64, C.POINTER(D), C.POINTER(I)]
         lib.feast_zgemm_oz_work_bytes.argtypes = [I64, I64, I64]
         lib.feast_zgemm_oz_work_bytes.restype = C.c_size_t
         lib.feast_zgemm_oz.argtypes = [I64, I64, I64, D, D, P, I64, P, I64, D, D, P, I64, P, C.c_size_t, P, P]
@@ -157,7 +158,7 @@ def to_device_colmajor(x, device="cuda", dtype=None):
     """numpy / torch (rows x cols) -> flat device tensor in column-major order."""
     torch = _torch()
     if isinstance(x, torch.Tensor):
-        t = x.to(device)
+        t = x.resolve_conj().to(device)
         if dtype is not None:
             t = t.to(dtype)
         if t.dim() == 1:
@@ -298,6 +299,20 @@ class Feast:
         _check(self._lib.feast_filter(self._ctx, Vd.data_ptr(), Ud.data_ptr()), "feast_filter")
         torch.cuda.current_stream().synchronize()
         return from_device_colmajor(Ud, self.n, self.m0)
+
+    def grad_abs2(self, left: "Feast"):
+        """L = sum over the inside eigenvalues of |lambda|^2 and its gradients
+        (G_A, G_B) as device tensors (n x n, row-major views of column-major
+        storage transposed back), from this finished run and a finished run
+        on the conjugate-transposed pencil (``left``)."""
+        torch = _torch()
+        n = self.n
+        gA = torch.empty(n * n, dtype=torch.complex128, device=self.device)
+        gB = torch.empty(n * n, dtype=torch.complex128, device=self.device)
+        L, cnt = C.c_double(), C.c_int()
+        _check(self._lib.feast_grad_abs2(self._ctx, left._ctx, gA.data_ptr(), gB.data_ptr(), n, C.byref(L),
+                                         C.byref(cnt)), "feast_grad_abs2")
+        return L.value, gA.view(n, n).t(), gB.view(n, n).t(), cnt.value
 
     def set_subspace(self, U1):
         Ud = to_device_colmajor(U1, self.device)
@@ -493,3 +508,60 @@ def zgemm_oz(A, Bm, Cm=None, alpha=1.0, beta=0.0, stream=None):
     if int(err.item()):
         raise FeastError(-6, "feast_zgemm_oz")
     return from_device_colmajor(Cd, m, n)
+
+
+def _eig_abs2_runs(A, B, Y, kw):
+    f = Feast(A, B, Y, **kw)
+    f.run()
+    return f
+
+
+def _conj_contour(kw):
+    kk = dict(kw)
+    kk["center"] = complex(kw.get("center", 0j)).conjugate()
+    return kk
+
+
+def _make_eig_abs2_function():
+    torch = _torch()
+
+    class EigSumAbs2(torch.autograd.Function):
+        """L = sum over the eigenvalues of (A, B) inside the contour of
+        |lambda|^2, by GFEAST; backward runs GFEAST on (A^H, B^H) over the
+        conjugated contour for the left eigenvectors and forms dL/dA, dL/dB
+        with the library's adjoint kernels."""
+
+        @staticmethod
+        def forward(ctx, A, B, Y, kw):
+            right = _eig_abs2_runs(A, B, Y, kw)
+            r = right.eigs(want_vectors=False)
+            ctx.right, ctx.kw = right, kw
+            ctx.save_for_backward(A, B, Y)
+            L = float(np.sum(np.abs(r["lam"]) ** 2))
+            return torch.tensor(L, dtype=torch.float64, device=A.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            A, B, Y = ctx.saved_tensors
+            left = _eig_abs2_runs(A.conj().t().resolve_conj(), B.conj().t().resolve_conj(), Y,
+                                  _conj_contour(ctx.kw))
+            _, gA, gB, _ = ctx.right.grad_abs2(left)
+            left.close()
+            ctx.right.close()
+            g = gout.to(torch.complex128)
+            return g * gA, g * gB, None, None
+
+    return EigSumAbs2
+
+
+_EIG_ABS2 = None
+
+
+def eig_sum_abs2(A, B, Y, **kw):
+    """Differentiable L = sum_{lambda inside} |lambda|^2 of the dense pencil
+    (A, B) (torch complex128 tensors on the GPU, rows x cols); kw are Feast's
+    contour / tolerance / precision keywords."""
+    global _EIG_ABS2
+    if _EIG_ABS2 is None:
+        _EIG_ABS2 = _make_eig_abs2_function()
+    return _EIG_ABS2.apply(A, B, Y, kw)

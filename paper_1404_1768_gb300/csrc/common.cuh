@@ -139,6 +139,23 @@ void count_launch();
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
+// Raise a kernel's dynamic shared-memory limit to everything the device
+// allows beside its static shared memory.  The value depends only on the
+// kernel and the device, so concurrent callers (the batch solver's worker
+// threads) never lower each other's limit below what a launch needs.
+template <typename K>
+inline cudaError_t allow_dyn_smem(K kernel)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, (const void *)kernel)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 // ---------------------------------------------------------------- grid barrier
 constexpr long long SPIN_LIMIT = 1ll << 24;
 struct GridSync {
@@ -232,8 +249,14 @@ int znode_sum(cudaStream_t s, int64_t n, int64_t m, int q, const zd *w, const zd
 // Thin QR by block classical Gram-Schmidt with re-orthogonalisation:
 // V (n x m, overwritten by Q), R (m x m upper, real positive diagonal).
 // timeout: flag raised if a grid barrier of the tall-panel form gives up
+// oz (may be null): digit-plane scratch (rows >= oz_rows_bytes(n, m), cols
+// >= oz_cols_bytes(m, 32)) to run the tall updates on the tensor cores.
+struct OzScratch {
+    void *rows, *cols;
+    int *err;
+};
 int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr,
-          zd *work, int *timeout);
+          zd *work, int *timeout, const OzScratch *oz = nullptr);
 size_t zorth_work_elems(int64_t n, int64_t m);
 
 // Batched projected eigensolve: alpha / beta eigenvalue pairs and unit right
@@ -323,6 +346,13 @@ int oz_gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, const void *Arows, 
 int resid_init(cudaStream_t s, int64_t n, int64_t m, int q, const zd *BV, const zd *xz, const zd *z, zd *R);
 // out[j] = ||x_j||_F^2 for q consecutive blocks of count entries.
 int sumsq_blocks(cudaStream_t s, int64_t count, int q, const zd *x, double *out);
+
+// Differentiation form (k_adjoint.cu): pair coefficients alpha_i, beta_i
+// from c_i = v_{k_i}^H (B X)_i, and G_A = V_k diag(alpha) X^H, G_B likewise.
+int adjoint_coef(cudaStream_t s, int64_t n, int cnt, const zd *V, int64_t ldv, const int *kidx, const zd *BX,
+                 int64_t ldb, const zd *lam, zd *alpha, zd *beta);
+int adjoint_grad(cudaStream_t s, int64_t n, int cnt, const zd *V, int64_t ldv, const int *kidx, const zd *X,
+                 int64_t ldx, const zd *alpha, const zd *beta, zd *GA, zd *GB, int64_t ldg);
 
 // complex64 LU whose trailing updates run on tc_cgemm (pivots and factors as
 // getrf_batched<cf>); scratch of getrf_tc_scratch_floats floats.

@@ -62,6 +62,7 @@ struct feast_ctx {
     void *ozA, *ozB;    // base-64 digit planes of A and B (refinement residual)
     void *ozX;          // digit planes of the q solution blocks, n x (q m0); right-operand scratch
     void *ozR;          // left-operand digit planes: U2^H, U1, A U1, B U1 (m0 x n or n x m0)
+    OzScratch oz_orth;  // the same scratch, handed to the orthonormalisation
     cf *Xhi;            // q x n x m0 complex64 scratch (rounded residuals)
     cf *C32;            // q x n x m0 low-precision solves / corrections
     zd *R64;            // q x n x m0 residuals
@@ -229,6 +230,14 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b)
 // Dense operands of the precision form: FP64-accurate products on the
 // tensor cores (digit planes of the left operand made beforehand).
 bool use_oz(const feast_ctx *c) { return c->kind == FEAST_DENSE && c->prec != FEAST_FP64; }
+
+// Digit-plane scratch for the orthonormalisation's tall updates (precision form).
+const OzScratch *orth_oz(feast_ctx *c)
+{
+    if (!use_oz(c)) return nullptr;
+    c->oz_orth = OzScratch{c->ozR, c->ozX, &c->st->timeout};
+    return &c->oz_orth;
+}
 
 // Y (M x N) = L X with L given by its digit planes (M x K), X (K x N, ldx).
 int oz_mul(feast_ctx *c, const void *Lrows, int64_t M, int64_t K, const zd *X, int64_t ldx, int64_t N, zd *Y,
@@ -399,11 +408,11 @@ int orthonormalise(feast_ctx *c, const zd *Usrc)
     int e;
     if (Usrc != c->U1)
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->U1, Usrc, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    if ((e = zorth(c->s, n, m, c->U1, n, c->R1, m, c->orth_work, &c->st->timeout))) return e;
+    if ((e = zorth(c->s, n, m, c->U1, n, c->R1, m, c->orth_work, &c->st->timeout, orth_oz(c)))) return e;
     zd *BU1 = c->W + n * m;
     if ((e = apply_B(c, c->U1, BU1, m))) return e;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work, &c->st->timeout);
+    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work, &c->st->timeout, orth_oz(c));
 }
 
 }  // namespace
@@ -444,7 +453,7 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
     carve(c, cv);
     for (int i = 0; i < 8; ++i)
         if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; }
-    const int64_t n = c->n, m = c->m0;
+    const int64_t n = c->n;
     cudaStream_t s = c->s;
 #define TRY(x) do { int _r = (x); if (_r) { feast_destroy(c); return _r; } } while (0)
 #define CTRY(x) do { if ((x) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; } } while (0)
@@ -675,7 +684,7 @@ int feast_set_subspace(feast_ctx *c, const void *U1)
     int e = apply_B(c, c->U1, BU1, m);
     if (e) return e;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work, &c->st->timeout);
+    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work, &c->st->timeout, orth_oz(c));
 }
 
 void feast_destroy(feast_ctx *c)
@@ -824,6 +833,55 @@ int feast_cgemm_tc(int64_t m, int64_t n, int64_t k, float alpha_re, float alpha_
     FEAST_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
     return tc_cgemm(s, m, n, k, make_float2(alpha_re, alpha_im), (const cf *)A, lda, sA, (const cf *)X, ldx, sX,
                     make_float2(beta_re, beta_im), (cf *)C, ldc, sC, batch, sc, err);
+}
+
+int feast_grad_abs2(feast_ctx *r, feast_ctx *l, void *gA, void *gB, int64_t ldg, double *L, int *count)
+{
+    if (!r || !l || !gA || !gB || !L || !count) return FEAST_EINVAL;
+    if (!r->done || !l->done) return FEAST_EINVAL;
+    if (r->kind != FEAST_DENSE || l->kind != FEAST_DENSE || r->n != l->n || ldg < r->n) return FEAST_EINVAL;
+    const int64_t n = r->n;
+    const int cnt = r->out_count;
+    *count = 0;
+    *L = 0.0;
+    if (l->out_count != cnt) return FEAST_ENOCONV;   // the two runs disagree on the inside count
+    cudaStream_t s = r->s;
+    std::vector<zd> lam(cnt > 0 ? cnt : 1), mu(cnt > 0 ? cnt : 1);
+    if (cnt > 0) {
+        FEAST_CUDA_TRY(cudaMemcpyAsync(lam.data(), r->lamo, sizeof(zd) * cnt, cudaMemcpyDeviceToHost, s));
+        FEAST_CUDA_TRY(cudaMemcpyAsync(mu.data(), l->lamo, sizeof(zd) * cnt, cudaMemcpyDeviceToHost, s));
+        FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // pair each right eigenvalue with the nearest unused conjugate of a left one
+    std::vector<int> kidx(cnt > 0 ? cnt : 1);
+    std::vector<char> used(cnt > 0 ? cnt : 1, 0);
+    double L2 = 0.0;
+    for (int i = 0; i < cnt; ++i) {
+        int best = -1;
+        double bd = 0.0;
+        for (int k = 0; k < cnt; ++k) {
+            if (used[k]) continue;
+            const double dx = mu[k].x - lam[i].x, dy = -mu[k].y - lam[i].y;
+            const double d = dx * dx + dy * dy;
+            if (best < 0 || d < bd) { best = k; bd = d; }
+        }
+        used[best] = 1;
+        kidx[i] = best;
+        L2 += lam[i].x * lam[i].x + lam[i].y * lam[i].y;
+    }
+    int *dk = r->idx;              // scratch once the run is done
+    zd *BX = r->AXBX, *alpha = r->lamc[0], *beta = r->lamc[1];
+    int e;
+    if (cnt > 0) {
+        FEAST_CUDA_TRY(cudaMemcpyAsync(dk, kidx.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+        if ((e = apply_B(r, r->Xo, BX, cnt))) return e;
+        if ((e = adjoint_coef(s, n, cnt, l->Xo, n, dk, BX, n, r->lamo, alpha, beta))) return e;
+    }
+    if ((e = adjoint_grad(s, n, cnt, l->Xo, n, dk, r->Xo, n, alpha, beta, (zd *)gA, (zd *)gB, ldg))) return e;
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    *count = cnt;
+    *L = L2;
+    return FEAST_OK;
 }
 
 size_t feast_zgemm_oz_work_bytes(int64_t m, int64_t n, int64_t k)

@@ -433,8 +433,8 @@ int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *
     const int64_t ldab = 2 * kl + ku + 1, sF = ldab * n, kv = kl + ku;
     dim3 g(cdiv(nrhs, GB_CW), q);
     size_t smf = (size_t)(kl + 1) * GB_CW * sizeof(T), smb = (size_t)(kv + 1) * GB_CW * sizeof(T);
-    if (smf > 48 * 1024) FEAST_CUDA_TRY(cudaFuncSetAttribute(k_gb_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf));
-    if (smb > 48 * 1024) FEAST_CUDA_TRY(cudaFuncSetAttribute(k_gb_bwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    if (smf > 48 * 1024) FEAST_CUDA_TRY(allow_dyn_smem(k_gb_fwd<T>));
+    if (smb > 48 * 1024) FEAST_CUDA_TRY(allow_dyn_smem(k_gb_bwd<T>));
     k_gb_fwd<T><<<g, GB_ST, smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX);
     FEAST_LAUNCH_CHECK();
     k_gb_bwd<T><<<g, GB_ST, smb, s>>>(n, kl, ku, nrhs, F, ldab, sF, X, ldx, sX);

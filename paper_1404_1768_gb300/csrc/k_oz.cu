@@ -413,7 +413,7 @@ int oz_gemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, const void *Arows, 
                          OZ_BN, CU_TENSOR_MAP_SWIZZLE_64B)))
         return e;
     const size_t smem = (size_t)OZ_STAGES * OZ_STAGE + 1024;
-    FEAST_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FEAST_CUDA_TRY(allow_dyn_smem(k_oz_gemm));
     const int64_t tiles = ((mr + OZ_BM - 1) / OZ_BM) * ((N + OZ_BN - 1) / OZ_BN);
     if (tiles > 0x7fffffff) return FEAST_EINVAL;
     OzOut o{C, ldc, alpha, zcol, cblk > 0 ? cblk : 1, beta};

@@ -214,16 +214,16 @@ __global__ void k_split_tf32(int64_t rows2, int n, const float *X, int64_t ldx2,
 namespace tc {
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // looked up once (thread-safe static initialisation)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess)
             return nullptr;
-        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
     return fn;
 }
 
@@ -298,7 +298,7 @@ int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf
     if ((e = make_map(&mXh, Xh, kr, n, batch, kr * 4, kr * n * 4, TC_BN))) return e;
     if ((e = make_map(&mXt, Xt, kr, n, batch, kr * 4, kr * n * 4, TC_BN))) return e;
     const size_t smem = (size_t)TC_STAGES * (2 * TC_BM * TC_BK * 4 + 2 * TC_BN * TC_BK * 4) + 1024;
-    FEAST_CUDA_TRY(cudaFuncSetAttribute(k_tc_cgemm<TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FEAST_CUDA_TRY(allow_dyn_smem(k_tc_cgemm<TC_BN>));
     dim3 grid(cdiv(mr, TC_BM), cdiv(n, TC_BN), batch);
     k_tc_cgemm<TC_BN><<<grid, 128, smem, s>>>(mAh, mAt, mXh, mXt, (int)mr, (int)n, (int)kr, C, ldc, sC, alpha,
                                               beta, err);

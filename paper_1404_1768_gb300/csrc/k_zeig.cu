@@ -657,10 +657,17 @@ __device__ void aed_window(int m, float4 *H, int ld, int l, int kw, int w, int n
             if (spike <= tol_rel * d || spike <= tol_abs) {
                 ++nd;
                 --cur;
-            } else {
-                for (int p = cur; p > top; --p) win_swap(p, w, sh->T, sh->V);
-                ++top;
+                continue;
             }
+            // moving it up only pays if some candidate above could still
+            // deflate (a swap changes spike entries by rotations of
+            // neighbours, so a candidate far above the threshold stays above)
+            bool any = false;
+            for (int j = top; j < cur && !any; ++j)
+                any = sabs * cds_absf(sh->V[0][j]) <= 64.f * (tol_rel * cds_absf(sh->T[j][j]) + tol_abs);
+            if (!any) break;
+            for (int p = cur; p > top; --p) win_swap(p, w, sh->T, sh->V);
+            ++top;
         }
     }
     const int u = w - nd;
@@ -1111,7 +1118,7 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     FEAST_CUDA_TRY(cudaGetDevice(&dev));
     FEAST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t dyn = sizeof(AedShared);
-    FEAST_CUDA_TRY(cudaFuncSetAttribute(k_hqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    FEAST_CUDA_TRY(allow_dyn_smem(k_hqr));
     FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hqr, QT, dyn));
     if (per < 1) return FEAST_ECUDA;
     // one CTA per SM (the far-part pass has ~3 m independent lines, each a

@@ -230,7 +230,7 @@ int plan_intra(int64_t n, IntraPlan &pl)
     const int rp = (int)((n + G - 1) / G);
     const size_t smem = (size_t)rp * (OB + 1) * sizeof(zd);
     if (smem + 8192 > (size_t)smem_max) return FEAST_OK;
-    FEAST_CUDA_TRY(cudaFuncSetAttribute(k_cgs2_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FEAST_CUDA_TRY(allow_dyn_smem(k_cgs2_grid));
     int per = 0;
     FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgs2_grid, OT, smem));
     if (per < 1 || G > per * sms) return FEAST_OK;
@@ -263,7 +263,7 @@ size_t zorth_work_elems(int64_t n, int64_t m)
 }
 
 int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr,
-          zd *work, int *timeout)
+          zd *work, int *timeout, const OzScratch *oz)
 {
     if (m <= 0) return FEAST_OK;
     if (m > n) return FEAST_EINVAL;
@@ -289,12 +289,25 @@ int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64
         }
         zd *Ro = R + c0 * ldr;  // R[0:c0, c0:c0+w]
         // pass 1: S1 = Q^H Vk (into R), Vk -= Q S1, Vk = W1 T1
+        // (with oz: the tall updates V_k -= Q S on the tensor cores, Q's
+        // digit planes made once per block)
+        if (oz && (e = oz_prepare_rows(s, n, c0, V, ldv, oz->rows))) return e;
         if ((e = zgemm_batched(s, 1, c0, w, n, one, V, ldv, 0, Vk, ldv, 0, zero, Ro, ldr, 0, 1))) return e;
-        if ((e = zgemm_batched(s, 0, n, w, c0, mone, V, ldv, 0, Ro, ldr, 0, one, Vk, ldv, 0, 1))) return e;
+        if (oz) {
+            if ((e = oz_prepare_cols(s, c0, w, Ro, ldr, oz->cols))) return e;
+            if ((e = oz_gemm(s, n, w, c0, oz->rows, oz->cols, mone, nullptr, 0, one, Vk, ldv, oz->err))) return e;
+        } else if ((e = zgemm_batched(s, 0, n, w, c0, mone, V, ldv, 0, Ro, ldr, 0, one, Vk, ldv, 0, 1))) {
+            return e;
+        }
         if ((e = run_intra(s, pl, n, w, Vk, ldv, T1, OB, part, gs))) return e;
         // pass 2: S2 = Q^H W1, W1 -= Q S2, W1 = Qk T2
         if ((e = zgemm_batched(s, 1, c0, w, n, one, V, ldv, 0, Vk, ldv, 0, zero, S2, m, 0, 1))) return e;
-        if ((e = zgemm_batched(s, 0, n, w, c0, mone, V, ldv, 0, S2, m, 0, one, Vk, ldv, 0, 1))) return e;
+        if (oz) {
+            if ((e = oz_prepare_cols(s, c0, w, S2, m, oz->cols))) return e;
+            if ((e = oz_gemm(s, n, w, c0, oz->rows, oz->cols, mone, nullptr, 0, one, Vk, ldv, oz->err))) return e;
+        } else if ((e = zgemm_batched(s, 0, n, w, c0, mone, V, ldv, 0, S2, m, 0, one, Vk, ldv, 0, 1))) {
+            return e;
+        }
         if ((e = run_intra(s, pl, n, w, Vk, ldv, T2, OB, part, gs))) return e;
         // R[0:c0, blk] = S1 + S2 T1,  R[blk, blk] = T2 T1
         if ((e = zgemm_batched(s, 0, c0, w, w, one, S2, m, 0, T1, OB, 0, one, Ro, ldr, 0, 1))) return e;

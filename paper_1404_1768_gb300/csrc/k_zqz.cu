@@ -338,7 +338,7 @@ int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA
     if (m <= 64) {
         size_t sm = 3 * (size_t)m * m * sizeof(zd);
         if (sm > 48 * 1024)
-            FEAST_CUDA_TRY(cudaFuncSetAttribute(k_qz<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            FEAST_CUDA_TRY(allow_dyn_smem(k_qz<128>));
         k_qz<128><<<batch, 128, sm, s>>>(m, A, lda, sA, B, ldb, sB, alpha, beta, V, ldv, sV, (zd *)work, 1, fail);
         FEAST_LAUNCH_CHECK();
         return FEAST_OK;

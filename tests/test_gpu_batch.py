@@ -42,3 +42,23 @@ def test_ragged_batch_matches_oracle(prec):
         ro = orc.result()
         assert ro["count"] == o["count"]
         orc.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ragged_batch_mixed_paths(prec):
+    """Pencils large enough that their projected problems take both
+    eigensolver paths (m0 <= 64: one-CTA QZ with a size-dependent shared
+    memory request; m0 > 64: the cooperative QR), solved by 8 concurrent
+    workers: every pencil converges to its exact inside count."""
+    import paper_1404_1768_gb300 as fg
+    rb = inputs.ragged_batch(12, 64, 480, seed=5)
+    assert min(rb.m0) <= 64 < max(rb.m0)
+    probs = [dict(A=p.A, B=p.B, Y=p.Y, contour_kind=0, rule=0, q=16, center=p.center, a=p.radius, eps=1e-10,
+                  prec=prec, refine_tol=1e-13, max_refine=4) for p in rb.pencils]
+    out = fg.solve_batch(probs, nworkers=8)
+    for p, o in zip(rb.pencils, out):
+        assert o["status"] == 0 and o["flag"] == 1
+        ref = p.lam[np.abs(p.lam - p.center) < p.radius]
+        assert o["count"] == len(ref)
+        if len(ref):
+            assert _match(o["lam"], ref) / max(1.0, np.max(np.abs(ref))) < 1e-8
