@@ -95,7 +95,11 @@ typedef struct {
  *   stream    : cudaStream_t for every launch of this context.
  *   no_stop   : benchmark aid -- when non-zero, feast_iterate always performs
  *               lines 16-17 and keeps iterating after a stop has fired (the
- *               stopped result stays available through feast_eigs). */
+ *               stopped result stays available through feast_eigs).
+ *   converged_only : when non-zero, line 14 (stop with flag 0 when e(k)
+ *               grows) is not applied: the run ends only with flag 1 (count
+ *               fixed and e(k) < eps, line 13) or -1 (max_iter).  For users
+ *               that need converged pairs, e.g. the differentiation form. */
 typedef struct {
     int m0;
     const void *Y0;
@@ -106,6 +110,7 @@ typedef struct {
     double refine_tol;
     void *stream;
     int no_stop;
+    int converged_only;
 } feast_options;
 
 /* Per-pass report.  flag: 2 = continue, 1 = converged (line 13), 0 = no

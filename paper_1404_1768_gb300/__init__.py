@@ -51,7 +51,8 @@ class Contour(C.Structure):
 class Options(C.Structure):
     _fields_ = [("m0", C.c_int), ("Y0", C.c_void_p), ("eps", C.c_double), ("eta", C.c_double),
                 ("max_iter", C.c_int), ("prec", C.c_int), ("max_refine", C.c_int),
-                ("refine_tol", C.c_double), ("stream", C.c_void_p), ("no_stop", C.c_int)]
+                ("refine_tol", C.c_double), ("stream", C.c_void_p), ("no_stop", C.c_int),
+                ("converged_only", C.c_int)]
 
 
 class BatchItem(C.Structure):
@@ -193,7 +194,7 @@ class Feast:
     def __init__(self, A, B, Y, *, contour_kind=0, rule=0, q=16, center=0j, a=1.0, b=0.0,
                  eps=1e-12, eta=1e-3, max_iter=50, prec=FEAST_FP64, no_stop=False, kind=0, kl=0,
                  ku=0, b_identity=False, device="cuda", stream=None, max_refine=5,
-                 refine_tol=1e-14):
+                 refine_tol=1e-14, converged_only=False):
         torch = _torch()
         self._lib = load()
         self.device = torch.device(device)
@@ -212,7 +213,7 @@ class Feast:
                                 float(b if contour_kind == FEAST_ELLIPSE else a), int(q), int(rule))
         self._opts = Options(self.m0, self._Y.data_ptr(), float(eps), float(eta), int(max_iter),
                              int(prec), int(max_refine), float(refine_tol),
-                             _stream_ptr(stream), int(bool(no_stop)))
+                             _stream_ptr(stream), int(bool(no_stop)), int(bool(converged_only)))
         nbytes = C.c_size_t(0)
         _check(self._lib.feast_workspace_size(C.byref(self._pencil), C.byref(self._contour),
                                               C.byref(self._opts), C.byref(nbytes)),
@@ -431,7 +432,7 @@ def solve_batch(problems, nworkers: int = 16, device="cuda"):
                         int(pr.get("rule", 0)))
         O[i] = Options(m0, Y.data_ptr(), float(pr.get("eps", 1e-12)), float(pr.get("eta", 1e-3)),
                        int(pr.get("max_iter", 50)), int(pr.get("prec", 0)),
-                       int(pr.get("max_refine", 5)), float(pr.get("refine_tol", 1e-14)), None, 0)
+                       int(pr.get("max_refine", 5)), float(pr.get("refine_tol", 1e-14)), None, 0, 0)
     nbytes = int(lib.feast_batch_workspace_size(cnt, P, Cn, O, nworkers))
     if nbytes == 0:
         raise FeastError(-1, "feast_batch_workspace_size")
@@ -511,7 +512,8 @@ def zgemm_oz(A, Bm, Cm=None, alpha=1.0, beta=0.0, stream=None):
 
 
 def _eig_abs2_runs(A, B, Y, kw):
-    f = Feast(A, B, Y, **kw)
+    # converged pairs only: the gradient is only as accurate as the pairs
+    f = Feast(A, B, Y, converged_only=True, **kw)
     f.run()
     return f
 

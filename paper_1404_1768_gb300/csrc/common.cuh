@@ -292,8 +292,8 @@ int ritz_residuals(cudaStream_t s, int64_t n, int m, const zd *AX, const zd *BX,
                    const zd *alpha, const zd *beta, zd *lam, double *res, DevStatus *st);
 // Selection and stopping tests of GFEAST lines 7-15 (device side).
 int stop_test(cudaStream_t s, int m, const feast_contour *c, const zd *lam, const double *res,
-              double eta, double eps, int k, int max_iter, int c_prev, double e_prev, int *sel,
-              int *idx, DevStatus *st);
+              double eta, double eps, int k, int max_iter, int c_prev, double e_prev, int converged_only,
+              int *sel, int *idx, DevStatus *st);
 // Accepted pairs to the front of Xc / lamc / resc.
 int compact_pairs(cudaStream_t s, int64_t n, int m, const int *idx, const DevStatus *st,
                   const zd *X, int64_t ldx, const zd *lam, const double *res, zd *Xc, zd *lamc,

@@ -29,7 +29,7 @@ struct feast_ctx {
     int q, m0;
     feast_contour contour;
     double eps, eta;
-    int max_iter, prec, no_stop;
+    int max_iter, prec, no_stop, converged_only;
     cudaStream_t s;
     // device arrays
     zd *A, *B;          // n x n copies (B null when identity)
@@ -212,6 +212,7 @@ void fill_ctx_params(feast_ctx *c, const feast_pencil *p, const feast_contour *c
     c->max_iter = o->max_iter;
     c->prec = o->prec;
     c->no_stop = o->no_stop;
+    c->converged_only = o->converged_only;
     c->s = (cudaStream_t)o->stream;
     c->max_refine = o->max_refine;
     c->refine_tol = o->refine_tol;
@@ -565,7 +566,7 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     // lines 7-12: residuals (eq. 5.1), selection, c(k), e(k); lines 13-15
     if ((e = ritz_residuals(s, n, (int)m, c->AXBX, c->AXBX + n * m, n, c->alpha, c->beta, c->lam, c->res, c->st))) return e;
     if ((e = stop_test(s, (int)m, &c->contour, c->lam, c->res, c->eta, c->eps, c->k, c->max_iter, c->c_prev,
-                       c->e_prev, c->sel, c->idx, c->st))) return e;
+                       c->e_prev, c->converged_only, c->sel, c->idx, c->st))) return e;
     if ((e = compact_pairs(s, n, (int)m, c->idx, c->st, c->Xr, n, c->lam, c->res, c->Xc[c->cur], c->lamc[c->cur],
                            c->resc[c->cur]))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[3], s));

@@ -111,8 +111,8 @@ __device__ __forceinline__ bool inside_contour(int kind, double cre, double cim,
 // c(k), e(k) = max r over the selection (0 if empty), and the flag.  The
 // count is taken as fixed (lines 13-14) only once it is non-zero.
 __global__ void k_stop(int m, feast_contour c, const zd *lam, const double *res, double eta,
-                       double eps, int k, int max_iter, int c_prev, double e_prev, int *sel,
-                       int *idx, DevStatus *st)
+                       double eps, int k, int max_iter, int c_prev, double e_prev, int converged_only,
+                       int *sel, int *idx, DevStatus *st)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int cnt = 0;
@@ -128,7 +128,7 @@ __global__ void k_stop(int m, feast_contour c, const zd *lam, const double *res,
     const bool fixed = (cnt == c_prev) && cnt > 0;
     int flag = 2;
     if (fixed && e < eps) flag = 1;
-    else if (fixed && e > e_prev) flag = 0;
+    else if (fixed && e > e_prev && !converged_only) flag = 0;
     else if (k == max_iter) flag = -1;
     st->count = cnt;
     st->err = e;
@@ -171,10 +171,11 @@ int ritz_residuals(cudaStream_t s, int64_t n, int m, const zd *AX, const zd *BX,
 }
 
 int stop_test(cudaStream_t s, int m, const feast_contour *c, const zd *lam, const double *res,
-              double eta, double eps, int k, int max_iter, int c_prev, double e_prev, int *sel,
-              int *idx, DevStatus *st)
+              double eta, double eps, int k, int max_iter, int c_prev, double e_prev, int converged_only,
+              int *sel, int *idx, DevStatus *st)
 {
-    k_stop<<<1, 32, 0, s>>>(m, *c, lam, res, eta, eps, k, max_iter, c_prev, e_prev, sel, idx, st);
+    k_stop<<<1, 32, 0, s>>>(m, *c, lam, res, eta, eps, k, max_iter, c_prev, e_prev, converged_only, sel, idx,
+                            st);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }

@@ -1121,10 +1121,13 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     FEAST_CUDA_TRY(allow_dyn_smem(k_hqr));
     FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hqr, QT, dyn));
     if (per < 1) return FEAST_ECUDA;
-    // one CTA per SM (the far-part pass has ~3 m independent lines, each a
-    // chain of up to CH rotations on the FP64 pipe, so every SM's FP64 units
-    // are worth having even when there are fewer lines than threads)
-    int grid = sms * (per < 1 ? 1 : 1);
+    // at most one CTA per SM; the far-part passes have ~3 m independent
+    // lines and a sweep at most NSH bulges, so a small projected problem
+    // takes a proportionally small grid (and leaves the rest of the GPU to
+    // other pencils of a batch)
+    int grid = m / 8;
+    if (grid < NSH) grid = NSH;
+    if (grid > sms) grid = sms;
     GridSync gs{bar, bar + 1, timeout};
     // deflation thresholds at double-single resolution (2^-44 relative)
     float tol_rel = 5.7e-14f, tol_abs = (float)(5.7e-14 * (hn > 0.0 ? hn : 1e-300));

@@ -185,6 +185,10 @@ WORKLOADS = {
                                 b=80.5, seed=0, eps=1e-10, beta=(20.0, 10.0)),
     # ragged batch: 256 dense pencils, n ~ U[64, 1024], own circles, 16 nodes
     "batch_256_n64_1024_q16": dict(batch=256, n_lo=64, n_hi=1024, q=16, seed=0, eps=1e-10),
+    # differentiation form: dense n = 2048, circle |z| < 1, 24 trapezoid nodes,
+    # m0 = 640; gradient of the sum of |lambda|^2 over the inside eigenvalues
+    "grad_n2048_m640_q24": dict(n=2048, m0=640, q=24, rule=0, center=0j, radius=1.0, seed=0, eps=1e-10,
+                                grad=True),
 }
 
 

@@ -49,10 +49,10 @@ def test_workspace_size_validation_without_gpu():
     lib = fg.load()
     p = fg.Pencil(0, 200, 1, 1, 200, 0, 0, 0)
     c = fg.Contour(0, 0.0, 0.0, 1.0, 1.0, 16, 0)
-    o = fg.Options(64, 1, 1e-12, 1e-3, 50, 0, 5, 1e-14, None, 0)
+    o = fg.Options(64, 1, 1e-12, 1e-3, 50, 0, 5, 1e-14, None, 0, 0)
     nb = ctypes.c_size_t(0)
     assert lib.feast_workspace_size(ctypes.byref(p), ctypes.byref(c), ctypes.byref(o), ctypes.byref(nb)) == 0
     # factors alone: 16 * 200 * 200 complex128
     assert nb.value > 16 * 200 * 200 * 16
-    bad = fg.Options(300, 1, 1e-12, 1e-3, 50, 0, 5, 1e-14, None, 0)  # m0 > n
+    bad = fg.Options(300, 1, 1e-12, 1e-3, 50, 0, 5, 1e-14, None, 0, 0)  # m0 > n
     assert lib.feast_workspace_size(ctypes.byref(p), ctypes.byref(c), ctypes.byref(bad), ctypes.byref(nb)) == -1
