@@ -456,16 +456,24 @@ def roofline(prob, args, ph):
     n, m0, q = prob.n, prob.m0, prob.q
     t_solve = max(ph["ms_solve"] - (ph["ms_refine"] if args.prec != "fp64" else 0.0), 1e-6) / 1e3
     if prob.band:
+        # forward sweep over kl multipliers, backward over kl + ku + 1 factor
+        # entries per column, per right-hand side and node: 8 flops per
+        # complex multiply-add.  At ~47 flops per byte of factors the band
+        # solves sit above GB300's FP64 ridge (0.16 flop/B) and FP32 ridge
+        # (~10 flop/B): arithmetic-bound, not HBM-bound.
         kl, ku = prob.bp.kl, prob.bp.ku
+        flops = 8.0 * q * m0 * n * (2 * kl + ku + 1)
         es = 16 if args.prec == "fp64" else 8
-        # factors read once forward (L, kl rows) and once backward (U, kl+ku+1
-        # rows); the right-hand sides read and written in both sweeps
         traffic = q * (2 * kl + ku + 1) * n * es + 4 * q * n * m0 * es
-        return {"bound": "hbm", "achieved": traffic / t_solve / 1e9, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                "frac": traffic / t_solve / 1e9 / HBM_PEAK_GBS, "traffic": None,
-                "kernel": "band solves k_gb_fwd + k_gb_bwd (subspace-build phase)",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-                "algorithmic_bytes_per_pass": traffic}
+        peak = FP64_PEAK_TFLOPS if args.prec == "fp64" else FP32_PEAK_TFLOPS
+        return {"bound": "alu", "achieved": flops / t_solve / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / t_solve / 1e12 / peak, "traffic": None,
+                "kernel": "band solves k_gb_fwd + k_gb_bwd (subspace-build phase), "
+                          + ("FP64 pipe" if args.prec == "fp64" else "FP32 pipe"),
+                "peak_source": "derived: 152 SMs x " + ("2 DFMA" if args.prec == "fp64" else "128 FFMA")
+                               + "/clk x 2 flop x 2.07 GHz",
+                "algorithmic_flops_per_pass": flops, "algorithmic_bytes_per_pass": traffic,
+                "hbm_gbs": traffic / t_solve / 1e9}
     flops = 8.0 * q * n * n * m0          # complex MAC = 8 flops, a4
     if args.prec == "fp64":
         return {"bound": "alu", "achieved": flops / t_solve / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

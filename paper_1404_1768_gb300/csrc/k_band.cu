@@ -27,6 +27,7 @@ namespace {
 constexpr int GB_NB = 32;     // panel width
 constexpr int GB_CW = 8;      // right-hand sides per solve CTA
 constexpr int GB_ST = 256;    // solve threads (>= kl and >= kv handled by striding)
+constexpr int GB_JC = 16;     // solve steps whose factor columns are staged at once
 
 __host__ __device__ __forceinline__ int64_t bidx(int64_t kv, int64_t ldab, int64_t i, int64_t c)
 {
@@ -209,110 +210,137 @@ __global__ void k_gb_writeback(int64_t n, int64_t kl, int64_t ku, int64_t k0, in
 
 // Forward pass of the solve: for j = 0..n-1: swap rows j, piv[j]; rows
 // j+1 .. j+kl -= l(:, j) x_j.  CTA = (chunk of GB_CW right-hand sides, node).
+// The right-hand sides live in a circular window of WL = kl + 1 + GB_JC rows
+// in shared memory; the multipliers and pivots of GB_JC columns are staged
+// in shared memory at once, and the window rows retired by a chunk are
+// refilled after it, so the sequential steps touch shared memory only.
 template <typename T>
 __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF,
                                                   const int *piv, T *X, int64_t ldx, int64_t sX)
 {
     extern __shared__ unsigned char sm_raw[];
-    T *W = reinterpret_cast<T *>(sm_raw);      // (kl + 1) x GB_CW window
+    const int64_t WL = kl + 1 + GB_JC, kv = kl + ku;
+    T *W = reinterpret_cast<T *>(sm_raw);      // WL x GB_CW window, row r at slot r % WL
+    T *Ls = W + WL * GB_CW;                    // GB_JC x kl multipliers
+    int *ps = reinterpret_cast<int *>(Ls + GB_JC * kl);
     const int b = blockIdx.y;
     const T *Fb = F + (int64_t)b * sF;
     const int *pv = piv + (int64_t)b * n;
     T *Xb = X + (int64_t)b * sX;
     const int64_t c0 = (int64_t)blockIdx.x * GB_CW;
     const int ncol = (int)((nrhs - c0) < GB_CW ? (nrhs - c0) : GB_CW);
-    const int64_t L = kl + 1, kv = kl + ku;
-    for (int e = threadIdx.x; e < L * GB_CW; e += GB_ST) {
-        const int64_t r = e % L;
-        const int cc = (int)(e / L);
+    for (int64_t e = threadIdx.x; e < WL * GB_CW; e += GB_ST) {
+        const int64_t r = e % WL;
+        const int cc = (int)(e / WL);
         W[r * GB_CW + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
     }
-    __syncthreads();
-    for (int64_t j = 0; j < n; ++j) {
-        const int64_t p = pv[j];
-        const int64_t sj = j % L;
-        if (p != j && threadIdx.x < GB_CW) {
-            const int64_t sp = p % L;
-            T t = W[sj * GB_CW + threadIdx.x];
-            W[sj * GB_CW + threadIdx.x] = W[sp * GB_CW + threadIdx.x];
-            W[sp * GB_CW + threadIdx.x] = t;
-        }
+    for (int64_t j0 = 0; j0 < n; j0 += GB_JC) {
+        const int jc = (int)((n - j0) < GB_JC ? (n - j0) : GB_JC);
         __syncthreads();
-        for (int e = threadIdx.x; e < kl * GB_CW; e += GB_ST) {
-            const int64_t t = e / GB_CW;
-            const int cc = e % GB_CW;
-            const int64_t r = j + 1 + t;
-            if (r < n) {
-                const T l = Fb[bidx(kv, ldab, r, j)];
-                T &w = W[(r % L) * GB_CW + cc];
-                T v = w;
-                cfma(v, cneg(l), W[sj * GB_CW + cc]);
-                w = v;
+        for (int64_t e = threadIdx.x; e < (int64_t)jc * kl; e += GB_ST) {
+            const int jj = (int)(e / kl);
+            const int64_t t = e % kl, c = j0 + jj, r = c + 1 + t;
+            Ls[jj * kl + t] = (r < n) ? Fb[bidx(kv, ldab, r, c)] : cx<T>(0, 0);
+        }
+        if (threadIdx.x < jc) ps[threadIdx.x] = pv[j0 + threadIdx.x];
+        __syncthreads();
+        for (int jj = 0; jj < jc; ++jj) {
+            const int64_t j = j0 + jj, sj = j % WL, p = ps[jj];
+            if (p != j && threadIdx.x < GB_CW) {
+                const int64_t sp = p % WL;
+                T t = W[sj * GB_CW + threadIdx.x];
+                W[sj * GB_CW + threadIdx.x] = W[sp * GB_CW + threadIdx.x];
+                W[sp * GB_CW + threadIdx.x] = t;
             }
-        }
-        __syncthreads();
-        if (threadIdx.x < GB_CW) {
+            __syncthreads();
+            for (int64_t e = threadIdx.x; e < kl * GB_CW; e += GB_ST) {
+                const int64_t t = e / GB_CW;
+                const int cc = (int)(e % GB_CW);
+                const int64_t r = j + 1 + t;
+                if (r < n) {
+                    T &w = W[(r % WL) * GB_CW + cc];
+                    T v = w;
+                    cfma(v, cneg(Ls[jj * kl + t]), W[sj * GB_CW + cc]);
+                    w = v;
+                }
+            }
+            __syncthreads();
             if (threadIdx.x < ncol) Xb[j + (c0 + threadIdx.x) * ldx] = W[sj * GB_CW + threadIdx.x];
-            const int64_t nr = j + L;
-            W[sj * GB_CW + threadIdx.x] =
-                (nr < n && threadIdx.x < ncol) ? Xb[nr + (c0 + threadIdx.x) * ldx] : cx<T>(0, 0);
         }
         __syncthreads();
+        // rows j0 .. j0+jc-1 are final; their slots take rows j0+WL .. (first
+        // touched at step j0 + GB_JC + 1 or later)
+        for (int e = threadIdx.x; e < jc * GB_CW; e += GB_ST) {
+            const int jj = e / GB_CW, cc = e % GB_CW;
+            const int64_t r = j0 + jj + WL;
+            W[(r % WL) * GB_CW + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+        }
     }
 }
 
 // Backward pass: for j = n-1..0: x_j /= U(j,j); rows j-kv .. j-1 -= U(:, j) x_j.
+// Same window / staging scheme: WL = kv + 1 + GB_JC rows, GB_JC columns of U
+// (diagonal included) staged per chunk.
 template <typename T>
 __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF, T *X,
                                                   int64_t ldx, int64_t sX)
 {
     extern __shared__ unsigned char sm_raw[];
-    T *W = reinterpret_cast<T *>(sm_raw);      // (kv + 1) x GB_CW window
+    const int64_t kv = kl + ku, WL = kv + 1 + GB_JC;
+    T *W = reinterpret_cast<T *>(sm_raw);      // WL x GB_CW window, row r at slot r % WL
+    T *Us = W + WL * GB_CW;                    // GB_JC x (kv + 1): U(j - t, j), t = 0..kv
     __shared__ T s_x[GB_CW];
     const int b = blockIdx.y;
     const T *Fb = F + (int64_t)b * sF;
     T *Xb = X + (int64_t)b * sX;
     const int64_t c0 = (int64_t)blockIdx.x * GB_CW;
     const int ncol = (int)((nrhs - c0) < GB_CW ? (nrhs - c0) : GB_CW);
-    const int64_t kv = kl + ku, L = kv + 1;
-    // window holds rows j-kv .. j (slot = row % L)
-    for (int e = threadIdx.x; e < L * GB_CW; e += GB_ST) {
-        const int64_t t = e % L;
-        const int cc = (int)(e / L);
+    for (int64_t e = threadIdx.x; e < WL * GB_CW; e += GB_ST) {
+        const int64_t t = e % WL;
+        const int cc = (int)(e / WL);
         const int64_t r = n - 1 - t;
-        if (r >= 0) W[(r % L) * GB_CW + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+        if (r >= 0) W[(r % WL) * GB_CW + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
     }
-    __syncthreads();
-    for (int64_t j = n - 1; j >= 0; --j) {
-        const int64_t sj = j % L;
-        if (threadIdx.x < GB_CW) {
-            T v = cdiv(W[sj * GB_CW + threadIdx.x], Fb[bidx(kv, ldab, j, j)]);
-            W[sj * GB_CW + threadIdx.x] = v;
-            s_x[threadIdx.x] = v;
+    for (int64_t j1 = n - 1; j1 >= 0; j1 -= GB_JC) {
+        const int jc = (int)((j1 + 1) < GB_JC ? (j1 + 1) : GB_JC);
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < (int64_t)jc * (kv + 1); e += GB_ST) {
+            const int jj = (int)(e / (kv + 1));
+            const int64_t t = e % (kv + 1), c = j1 - jj, r = c - t;
+            Us[jj * (kv + 1) + t] = (r >= 0) ? Fb[bidx(kv, ldab, r, c)] : cx<T>(0, 0);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < kv * GB_CW; e += GB_ST) {
-            const int64_t t = e / GB_CW;
-            const int cc = e % GB_CW;
-            const int64_t r = j - 1 - t;
-            if (r >= 0) {
-                const T u = Fb[bidx(kv, ldab, r, j)];
-                T &w = W[(r % L) * GB_CW + cc];
-                T v = w;
-                cfma(v, cneg(u), s_x[cc]);
-                w = v;
+        for (int jj = 0; jj < jc; ++jj) {
+            const int64_t j = j1 - jj, sj = j % WL;
+            const T *u = Us + jj * (kv + 1);
+            if (threadIdx.x < GB_CW) {
+                const T v = cdiv(W[sj * GB_CW + threadIdx.x], u[0]);
+                W[sj * GB_CW + threadIdx.x] = v;
+                s_x[threadIdx.x] = v;
+                if (threadIdx.x < ncol) Xb[j + (c0 + threadIdx.x) * ldx] = v;
             }
+            __syncthreads();
+            for (int64_t e = threadIdx.x; e < kv * GB_CW; e += GB_ST) {
+                const int64_t t = e / GB_CW;
+                const int cc = (int)(e % GB_CW);
+                const int64_t r = j - 1 - t;
+                if (r >= 0) {
+                    T &w = W[(r % WL) * GB_CW + cc];
+                    T v = w;
+                    cfma(v, cneg(u[t + 1]), s_x[cc]);
+                    w = v;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (threadIdx.x < GB_CW) {
-            if (threadIdx.x < ncol) Xb[j + (c0 + threadIdx.x) * ldx] = W[sj * GB_CW + threadIdx.x];
-            const int64_t nr = j - L;
-            if (nr >= 0)
-                W[sj * GB_CW + threadIdx.x] = (threadIdx.x < ncol) ? Xb[nr + (c0 + threadIdx.x) * ldx] : cx<T>(0, 0);
+        // rows j1-jc+1 .. j1 are final; their slots take rows j - WL
+        for (int e = threadIdx.x; e < jc * GB_CW; e += GB_ST) {
+            const int jj = e / GB_CW, cc = e % GB_CW;
+            const int64_t r = j1 - jj - WL;
+            if (r >= 0) W[(r % WL) * GB_CW + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
         }
-        __syncthreads();
     }
 }
 
@@ -432,7 +460,8 @@ int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *
 {
     const int64_t ldab = 2 * kl + ku + 1, sF = ldab * n, kv = kl + ku;
     dim3 g(cdiv(nrhs, GB_CW), q);
-    size_t smf = (size_t)(kl + 1) * GB_CW * sizeof(T), smb = (size_t)(kv + 1) * GB_CW * sizeof(T);
+    const size_t smf = ((size_t)(kl + 1 + GB_JC) * GB_CW + (size_t)GB_JC * kl) * sizeof(T) + GB_JC * sizeof(int) + 16;
+    const size_t smb = ((size_t)(kv + 1 + GB_JC) * GB_CW + (size_t)GB_JC * (kv + 1)) * sizeof(T);
     if (smf > 48 * 1024) FEAST_CUDA_TRY(allow_dyn_smem(k_gb_fwd<T>));
     if (smb > 48 * 1024) FEAST_CUDA_TRY(allow_dyn_smem(k_gb_bwd<T>));
     k_gb_fwd<T><<<g, GB_ST, smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX);
