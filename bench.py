@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-converge", action="store_true",
                     help="skip the untimed run to convergence (parity / eigpairs/s)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU baseline sample")
+    ap.add_argument("--nworkers", type=int, default=16,
+                    help="ragged batch: host worker threads (one CUDA stream each)")
     return ap.parse_args()
 
 
@@ -580,7 +582,9 @@ def gpu_arm(args):
             "eigpairs_per_s": eig_rate, "parity": parity,
             "phase_ms": ph,
             "refine_sweeps": [i["refine_sweeps_max"] for i in infos],
-            "qz": {"sweeps": [i["qz_sweeps"] for i in infos], "phases": [i["qz_phases"] for i in infos]},
+            "qz": {"sweeps": [i["qz_sweeps"] for i in infos], "phases": [i["qz_phases"] for i in infos],
+                   "warm": [i["qz_warm"] for i in infos], "qr_rows": [i["qz_rows"] for i in infos],
+                   "warm_resid": [i["qz_warm_resid"] for i in infos]},
             "fp64_path": fp64,
             "roofline": roof,
             "roofline_kernels": roof_kernels,
@@ -617,7 +621,7 @@ def batch_arm(args, cfg):
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        outs = fg.solve_batch(probs, nworkers=16)
+        outs = fg.solve_batch(probs, nworkers=args.nworkers)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     clk = clocks.stop()
@@ -647,7 +651,7 @@ def batch_arm(args, cfg):
                 "config": {"workload": args.workload, "pencils": cfg["batch"],
                            "n_range": [cfg["n_lo"], cfg["n_hi"]], "q": cfg["q"],
                            "m0": "max(8, ceil(1.5 s / 8) * 8) per pencil", "precision": args.prec,
-                           "parallelism": "replicas1"},
+                           "parallelism": "replicas1", "workers": args.nworkers},
                 "pencils_per_s": cfg["batch"] / t, "total_iterations": iters,
                 "parity": {"converged": cfg["batch"] - fails, "exact_counts": counts_ok,
                            "max_rel_eig_err_vs_exact": worst, "max_resid_eq_5_1": res_max},

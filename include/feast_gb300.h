@@ -124,6 +124,11 @@ typedef struct {
     int bad_node;
     int qz_sweeps;    /* QR sweeps of the projected eigensolve (m0 > 64), this pass */
     int qz_phases;    /* bulge-chase phases of those sweeps */
+    int qz_warm;      /* 1: the projected problem was solved warm (only its
+                         unconverged trailing block went through the QR) */
+    int qz_rows;      /* rows given to the QR this pass (m0 when cold) */
+    double qz_warm_resid; /* largest relative eigen-residual of the warm
+                         solve's Newton step (0 when not tried) */
 } feast_iter_info;
 
 typedef struct feast_ctx feast_ctx;

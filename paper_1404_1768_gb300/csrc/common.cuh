@@ -277,6 +277,53 @@ size_t zeig_large_work_bytes(int m);
 // stats[2] += early-deflation windows applied.
 int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
                int *fail, int *timeout, int *stats = nullptr);
+// Schur form of a contiguous m x m matrix (k_zeig.cu): C <- T = Q^H C Q
+// (upper triangle; Hessenberg reduction then the double-single QR), Q
+// unitary.  work: schur_large_work_bytes(m).  hn_out (may be null): max
+// |C_ij| of the Hessenberg matrix.
+size_t schur_large_work_bytes(int m);
+int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int *timeout, int *stats,
+                double *hn_out);
+// Eigenvectors of the upper triangle of T (m x m), unit diagonal, by
+// back-substitution; unit 2-norm columns.
+int schur_vectors(cudaStream_t s, int m, const zd *T, zd *Y, double snorm);
+int normalise_cols(cudaStream_t s, int m, zd *V);
+
+// Warm-started projected eigensolve (k_warm.cu).
+struct WarmParams {
+    int min_m;          // smallest m that tries it
+    int min_tail;       // smallest trailing block given to the QR
+    double tau;         // column of C counted converged: ||C[j+1:, j]|| <= tau max|C|
+    double accept_tol;  // largest relative eigen-residual accepted
+};
+struct WarmResult {
+    int accepted;   // 1: alpha, beta, V hold the eigenpairs
+    int k;          // converged leading columns found
+    int tail;       // rows of the block given to the QR
+    double resid;   // largest relative eigen-residual of the Newton step
+};
+size_t zeig_warm_work_bytes(int m);
+// A, Bt as zeig_large (both overwritten whether accepted or not).  qz_work:
+// zeig_large_work_bytes(m) bytes.
+int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *warm_work, void *qz_work,
+              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats);
+// Line 16 on Ritz pairs in defect form (k_defect.cu):
+// U = X rho(Lambda) + sum_j w_j M_j^{-1} (R D_j), R = A X - B X Lambda.
+struct DefectScratch {
+    cf *d32;     // q x m: 1 / (z_j - lambda_i) (1 for plain columns)
+    zd *rho;     // m: rho(lambda_i) (0 for plain columns)
+    int *plain;  // m: 1 when the column takes the plain right-hand side B x
+    cf *S;       // n x m: R (or B X) rounded to complex64
+};
+int defect_prepare(cudaStream_t s, int64_t n, int m, int q, const zd *z, const zd *w, const zd *lam, double dmin,
+                   const zd *AX, const zd *BX, DefectScratch &d);
+// X_j (slot stride sX) = rows perm_j of S scaled by d_j (perm null: no interchange)
+int defect_rhs(cudaStream_t s, int64_t n, int m, int q, const int *perm, const DefectScratch &d, cf *X, int64_t sX);
+// U = sum_j w_j Y_j + X rho
+int defect_sum(cudaStream_t s, int64_t n, int m, int q, const cf *Y, int64_t sY, const zd *w, const zd *X,
+               const DefectScratch &d, zd *U);
+// Vout[:, i] = Vin[:, perm[i]] (rows x m, leading dim rows).
+int permute_cols(cudaStream_t s, int64_t rows, int m, const int *perm, const zd *Vin, zd *Vout);
 
 // Composition of the LU interchanges: perm[b*n + i] = original row at i.
 int zpiv_to_perm(cudaStream_t s, int64_t n, int batch, const int *piv, int *perm);
@@ -325,6 +372,12 @@ int gb_matmul(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *M, in
 int gb_residual(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *A, const zd *B,
                 int64_t ldin, int q, const zd *z, int64_t m, const zd *RHS, const zd *X, zd *R,
                 double *nrm2);
+// B = I: the same residual with the band product A X_j in double-single
+// arithmetic; Ads is A's band as packed (hi, lo) pairs (z2ds), Xds scratch
+// for the split X (q n m entries).
+int z2ds(cudaStream_t s, int64_t count, const zd *x, float4 *y);
+int gb_residual_ds(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const float4 *Ads, int64_t ldin, int q,
+                   const zd *z, int64_t m, const zd *RHS, const zd *X, float4 *Xds, zd *R, double *nrm2);
 
 // Tensor-core complex64 GEMM (k_tc.cu): C_b = beta C_b + alpha A_b X_b on
 // tcgen05 (kind::tf32, 3-pass split); scratch of tc_scratch_floats floats.

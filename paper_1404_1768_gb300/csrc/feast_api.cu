@@ -6,7 +6,9 @@
 // context record itself is the only host allocation.  Every step runs in
 // this library's kernels on the caller's stream; the host only sequences
 // launches and reads c(k), e(k) and the flag once per pass.
+#include <algorithm>
 #include <atomic>
+#include <complex>
 #include <stdlib.h>
 #include <string.h>
 #include <thread>
@@ -55,10 +57,14 @@ struct feast_ctx {
     zd *tmp;            // n x m0
     zd *orth_work;
     void *qz_work;
+    void *warm_work;    // warm-started projected eigensolve (m0 >= kWarmMinM)
+    int *pair_perm;     // m0: order of the Ritz pairs (most converged next pass first)
+    zd *ord_x, *ord_ab; // gather targets for X (n x m0) and [A X | B X] (n x 2 m0)
     DevStatus *st;
     // precision form
     cf *F32;            // q x n x n complex64 factors
     float *tcs;         // tensor-core LU operand scratch (complex64 dense)
+    float4 *Ads, *Xds;  // band A and the solutions as double-single pairs (banded precision form, B = I)
     void *ozA, *ozB;    // base-64 digit planes of A and B (refinement residual)
     void *ozX;          // digit planes of the q solution blocks, n x (q m0); right-operand scratch
     void *ozR;          // left-operand digit planes: U2^H, U1, A U1, B U1 (m0 x n or n x m0)
@@ -66,6 +72,7 @@ struct feast_ctx {
     cf *Xhi;            // q x n x m0 complex64 scratch (rounded residuals)
     cf *C32;            // q x n x m0 low-precision solves / corrections
     zd *R64;            // q x n x m0 residuals
+    DefectScratch dfx;  // line 16 on Ritz pairs in defect form (precision form)
     double *nrm2;       // q + 1 squared norms
     int max_refine;
     double refine_tol;
@@ -79,6 +86,10 @@ struct feast_ctx {
     double last_rel;
     float ms_refine;
     // host state
+    double *zw_host;    // nodes and weights (2 q complex), for rho(lambda)
+    int ritz_filter;    // line 16 of this pass filters the Ritz vectors
+    int warm_ready;     // U1 comes from ordered Ritz vectors: line 6 may start warm
+    WarmResult last_warm;
     int k, c_prev, done, cur;
     double e_prev;
     int out_count, out_flag, out_k;
@@ -87,6 +98,13 @@ struct feast_ctx {
 };
 
 namespace {
+
+// Projected problems this large take the warm-started solve (k_warm.cu)
+// once a pass has ordered its Ritz pairs.
+constexpr int kWarmMinM = 96;
+constexpr int kWarmMinTail = 65;     // the QR's own size range (m > 64)
+constexpr double kWarmTauMin = 1e-8; // converged column: strictly lower part <= tau max|C|
+constexpr double kWarmAccMin = 1e-13;
 
 struct Carver {
     char *base;
@@ -121,6 +139,15 @@ int validate(const feast_pencil *p, const feast_contour *c, const feast_options 
     return FEAST_OK;
 }
 
+void carve_defect(feast_ctx *c, Carver &cv)
+{
+    const size_t n = (size_t)c->n, m = (size_t)c->m0, q = (size_t)c->q;
+    c->dfx.d32 = cv.take<cf>(q * m);
+    c->dfx.rho = cv.take<zd>(m);
+    c->dfx.plain = cv.take<int>(m);
+    c->dfx.S = cv.take<cf>(n * m);
+}
+
 void carve(feast_ctx *c, Carver &cv)
 {
     const size_t n = (size_t)c->n, m = (size_t)c->m0, q = (size_t)c->q;
@@ -137,9 +164,14 @@ void carve(feast_ctx *c, Carver &cv)
         } else {
             c->Fb32 = cv.take<cf>(fsz);
             c->gb_scratch = cv.take<cf>(gb_scratch_elems(c->kl, c->ku, (int)q));
+            if (c->b_identity) {
+                c->Ads = cv.take<float4>((size_t)c->ldin * n);
+                c->Xds = cv.take<float4>(q * n * m);
+            }
             c->C32 = cv.take<cf>(q * n * m);
             c->R64 = cv.take<zd>(q * n * m);
             c->nrm2 = cv.take<double>(q + 1);
+            carve_defect(c, cv);
         }
         c->gb_pivl = cv.take<int>(gb_piv_scratch(c->kl, (int)q));
     } else if (c->prec == FEAST_FP64) {
@@ -158,6 +190,7 @@ void carve(feast_ctx *c, Carver &cv)
         c->C32 = cv.take<cf>(q * n * m);
         c->R64 = cv.take<zd>(q * n * m);
         c->nrm2 = cv.take<double>(q + 1);
+        carve_defect(c, cv);
     }
     c->piv = cv.take<int>(q * n);
     c->perm = cv.take<int>(q * n);
@@ -190,6 +223,12 @@ void carve(feast_ctx *c, Carver &cv)
     c->tmp = cv.take<zd>(n * m);
     c->orth_work = cv.take<zd>(zorth_work_elems((int64_t)n, (int64_t)m));
     c->qz_work = cv.take<char>(zqz_work_bytes((int)m));
+    if ((int)m >= kWarmMinM) {
+        c->warm_work = cv.take<char>(zeig_warm_work_bytes((int)m));
+        c->pair_perm = cv.take<int>(m);
+        c->ord_x = cv.take<zd>(n * m);
+        c->ord_ab = cv.take<zd>(2 * n * m);
+    }
     c->st = cv.take<DevStatus>(1);
 }
 
@@ -307,8 +346,13 @@ int solve_band(feast_ctx *c, const zd *BV, double tol)
     if ((e = sumsq(s, nm, BV, c->nrm2 + q))) return e;
     double h[4096 + 1];
     for (int sweep = 0; sweep <= c->max_refine; ++sweep) {
-        if ((e = gb_residual(s, n, c->kl, c->ku, c->A, c->B, c->ldin, (int)q, c->z, m, BV, c->Xs, c->R64,
-                             c->nrm2))) return e;
+        if (c->Ads) {
+            if ((e = gb_residual_ds(s, n, c->kl, c->ku, c->Ads, c->ldin, (int)q, c->z, m, BV, c->Xs, c->Xds, c->R64,
+                                    c->nrm2))) return e;
+        } else if ((e = gb_residual(s, n, c->kl, c->ku, c->A, c->B, c->ldin, (int)q, c->z, m, BV, c->Xs, c->R64,
+                                    c->nrm2))) {
+            return e;
+        }
         FEAST_CUDA_TRY(cudaMemcpyAsync(h, c->nrm2, sizeof(double) * (q + 1), cudaMemcpyDeviceToHost, s));
         FEAST_CUDA_TRY(cudaStreamSynchronize(s));
         double worst = 0.0;
@@ -402,6 +446,31 @@ int filter(feast_ctx *c, const zd *V, zd *Uout, double tol)
     return znode_sum(c->s, n, m, c->q, c->w, c->Xs, n, n * m, Uout, n);
 }
 
+// Line 16 of the precision form on the Ritz block X = c->Xr with Ritz
+// values c->lam (k_defect.cu): U = X rho(Lambda) + sum_j w_j M_j^{-1}
+// (R D_j), R = A X - B X Lambda from the products of line 9 (c->AXBX).
+// The complex64 solves see only R, so no refinement sweeps are needed.
+int filter_defect(feast_ctx *c, zd *Uout)
+{
+    const int64_t n = c->n, m = c->m0, q = c->q, nm = n * m;
+    cudaStream_t s = c->s;
+    int e;
+    const double dmin = 1e-6 * fmin(c->contour.a, c->contour.b);
+    if ((e = defect_prepare(s, n, (int)m, (int)q, c->z, c->w, c->lam, dmin, c->AXBX, c->AXBX + nm, c->dfx)))
+        return e;
+    if (c->kind == FEAST_BANDED) {
+        if ((e = defect_rhs(s, n, (int)m, (int)q, nullptr, c->dfx, c->C32, nm))) return e;
+        if ((e = gb_solve<cf>(s, n, c->kl, c->ku, (int)q, c->Fb32, c->piv, m, c->C32, n, nm))) return e;
+    } else {
+        if ((e = defect_rhs(s, n, (int)m, (int)q, c->perm, c->dfx, c->C32, nm))) return e;
+        if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout))) return e;
+    }
+    c->last_sweeps = 0;
+    c->last_rel = -1.0;
+    c->ms_refine = 0.f;
+    return defect_sum(s, n, (int)m, (int)q, c->C32, nm, c->w, c->Xr, c->dfx, Uout);
+}
+
 // U1 R1 = U ; W[:, m0:] = B U1 ; U2 R2 = B U1   (GFEAST lines 2, 17)
 int orthonormalise(feast_ctx *c, const zd *Usrc)
 {
@@ -467,6 +536,13 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
                                cudaMemcpyDeviceToDevice, s));
     CTRY(cudaEventRecord(c->ev[0], s));
     TRY(contour_nodes(s, &c->contour, c->z, c->w));
+    c->zw_host = (double *)malloc(sizeof(double) * 4 * (size_t)c->q);
+    if (!c->zw_host) {
+        feast_destroy(c);
+        return FEAST_EINVAL;
+    }
+    CTRY(cudaMemcpyAsync(c->zw_host, c->z, sizeof(zd) * c->q, cudaMemcpyDeviceToHost, s));
+    CTRY(cudaMemcpyAsync(c->zw_host + 2 * c->q, c->w, sizeof(zd) * c->q, cudaMemcpyDeviceToHost, s));
     // z_j B - A and its LU factors (factored once, reused every pass)
     if (c->kind == FEAST_BANDED) {
         if (c->prec == FEAST_FP64) {
@@ -475,6 +551,7 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
                              &c->st->lu_info, &c->st->lu_row));
         } else {
             TRY(gb_form<cf>(s, n, c->kl, c->ku, c->A, c->B, c->ldin, c->q, c->z, c->Fb32));
+            if (c->Ads) TRY(z2ds(s, c->ldin * n, c->A, c->Ads));
             TRY(gb_getrf<cf>(s, n, c->kl, c->ku, c->q, c->Fb32, c->piv, c->gb_scratch, c->gb_pivl,
                              &c->st->lu_info, &c->st->lu_row));
         }
@@ -523,6 +600,55 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
 #undef CTRY
 }
 
+// Ritz pairs ordered by the residual they are expected to have after the
+// next filter application, r_i / |rho(lambda_i)| (r_i of eq. 5.1, rho the
+// filter of eq. 4.1: an eigenvector x gives sum_j w_j (z_j B - A)^{-1} B x
+// = rho(lambda) x, so a pair's residual shrinks by |rho(lambda_{m0+1})| /
+// |rho(lambda_i)| per pass).  The columns of X and [A X | B X] are gathered
+// on the device, lambda and r re-uploaded; lines 7-15 of this pass have
+// already used them, line 16 uses the new order.
+static int order_pairs(feast_ctx *c)
+{
+    const int m = c->m0, q = c->q;
+    const int64_t n = c->n;
+    cudaStream_t s = c->s;
+    std::vector<double> lam(2 * (size_t)m), res(m), key(m), lam2(2 * (size_t)m), res2(m);
+    std::vector<int> perm(m);
+    FEAST_CUDA_TRY(cudaMemcpyAsync(lam.data(), c->lam, sizeof(zd) * m, cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaMemcpyAsync(res.data(), c->res, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    const double *zh = c->zw_host, *wh = c->zw_host + 2 * q;
+    for (int i = 0; i < m; ++i) {
+        const std::complex<double> l(lam[2 * i], lam[2 * i + 1]);
+        std::complex<double> r(0.0, 0.0);
+        for (int j = 0; j < q; ++j)
+            r += std::complex<double>(wh[2 * j], wh[2 * j + 1]) / (std::complex<double>(zh[2 * j], zh[2 * j + 1]) - l);
+        const double a = std::abs(r);
+        key[i] = (a > 0.0) ? res[i] / a : 1e300;
+        if (!(key[i] == key[i])) key[i] = 1e300;
+    }
+    for (int i = 0; i < m; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return key[x] < key[y]; });
+    for (int i = 0; i < m; ++i) {
+        lam2[2 * i] = lam[2 * perm[i]];
+        lam2[2 * i + 1] = lam[2 * perm[i] + 1];
+        res2[i] = res[perm[i]];
+    }
+    // (pageable host-to-device copies are staged before cudaMemcpyAsync
+    // returns, so the vectors may go out of scope)
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->pair_perm, perm.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->lam, lam2.data(), sizeof(zd) * m, cudaMemcpyHostToDevice, s));
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->res, res2.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    int e;
+    if ((e = permute_cols(s, n, m, c->pair_perm, c->Xr, c->ord_x))) return e;
+    if ((e = permute_cols(s, n, m, c->pair_perm, c->AXBX, c->ord_ab))) return e;
+    if ((e = permute_cols(s, n, m, c->pair_perm, c->AXBX + n * m, c->ord_ab + n * m))) return e;
+    std::swap(c->Xr, c->ord_x);
+    std::swap(c->AXBX, c->ord_ab);
+    c->ritz_filter = 1;
+    return FEAST_OK;
+}
+
 int feast_iterate(feast_ctx *c, feast_iter_info *info)
 {
     if (!c) return FEAST_EINVAL;
@@ -542,10 +668,30 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     }
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[1], s));
     // line 6: projected eigenpairs, x_i = U1 y_i
-    FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
     FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_sweeps, 0, 3 * sizeof(int), s));
-    if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
-                         c->qz_work, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps))) return e;
+    c->last_warm = WarmResult{};
+    if (c->warm_ready) {
+        // the previous pass filtered its |rho|-ordered Ritz vectors: C is
+        // block upper triangular up to a remainder of the size of its
+        // residuals; the projected solve is held to 1e-3 of the accuracy
+        // already reached (eta before any pair is accepted)
+        const double eref = (c->c_prev > 0 && c->e_prev > 0.0) ? c->e_prev : c->eta;
+        // a converged column's remainder enters the Newton step squared over
+        // an eigenvalue gap (~1e-3 of max|C| and up): tau^2 / 1e-3 <= tol
+        const double acc = fmax(kWarmAccMin, 1e-3 * eref);
+        const double tau = fmin(1e-5, fmax(kWarmTauMin, sqrt(1e-3 * acc)));
+        const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc};
+        FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
+        if ((e = zeig_warm(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->warm_work, c->qz_work, prm,
+                           &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps)))
+            return e;
+        if (!c->last_warm.accepted) FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_fail, 0, sizeof(int), s));
+    }
+    if (!c->last_warm.accepted) {
+        FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
+        if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
+                             c->qz_work, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps))) return e;
+    }
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[2], s));
     if (use_oz(c)) {
         // x_i = U1 y_i, A x_i = (A U1) y_i, B x_i = (B U1) y_i with Y's digits made once
@@ -569,15 +715,25 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
                        c->e_prev, c->converged_only, c->sel, c->idx, c->st))) return e;
     if ((e = compact_pairs(s, n, (int)m, c->idx, c->st, c->Xr, n, c->lam, c->res, c->Xc[c->cur], c->lamc[c->cur],
                            c->resc[c->cur]))) return e;
+    // the precision form always filters the Ritz pairs (defect form); the
+    // pairs are ordered when the next pass may solve warm
+    c->ritz_filter = (c->prec != FEAST_FP64);
+    if (c->pair_perm && (e = order_pairs(c))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[3], s));
     // lines 16-17, issued before the flag is read back so that the whole pass
     // is one stream-ordered sequence; when a stop fires the new subspace is
     // simply not used (the stopped pairs were compacted above).
-    // refinement target of this pass: tied to the accuracy already reached
-    // (no pair accepted yet -> the plain low-precision solve suffices)
-    double tol = 1.0;
-    if (c->c_prev > 0 && c->e_prev > 0.0) tol = fmax(c->refine_tol, 1e-3 * c->e_prev);
-    if ((e = filter(c, c->U1, c->U, tol))) return e;
+    // line 16.  Precision form: on the Ritz pairs in defect form (no
+    // refinement sweeps; the solves see only the residual block).  FP64: on
+    // U1, or on the |rho|-ordered Ritz vectors when the next pass may solve
+    // warm (the same subspace, x_i = U1 y_i, in a basis whose leading
+    // columns converge first).
+    if (c->prec != FEAST_FP64) {
+        if ((e = filter_defect(c, c->U))) return e;
+    } else if ((e = filter(c, c->ritz_filter ? c->Xr : c->U1, c->U, 1.0))) {
+        return e;
+    }
+    c->warm_ready = c->ritz_filter && c->pair_perm;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[4], s));
     if ((e = orthonormalise(c, c->U))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[5], s));
@@ -616,6 +772,9 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
         info->refine_sweeps_max = c->prec == FEAST_FP64 ? 0 : c->last_sweeps;
         info->qz_sweeps = hs.qz_sweeps;
         info->qz_phases = hs.qz_phases;
+        info->qz_warm = c->last_warm.accepted;
+        info->qz_rows = c->last_warm.accepted ? c->last_warm.tail : (int)m;
+        info->qz_warm_resid = c->last_warm.resid;
     }
     return FEAST_OK;
 }
@@ -681,6 +840,7 @@ int feast_set_subspace(feast_ctx *c, const void *U1)
     if (!c || !U1) return FEAST_EINVAL;
     const int64_t n = c->n, m = c->m0;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U1, U1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
+    c->warm_ready = 0;  // an arbitrary basis: the next projected solve starts cold
     zd *BU1 = c->W + n * m;
     int e = apply_B(c, c->U1, BU1, m);
     if (e) return e;
@@ -693,6 +853,7 @@ void feast_destroy(feast_ctx *c)
     if (!c) return;
     for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    free(c->zw_host);
     free(c);
 }
 

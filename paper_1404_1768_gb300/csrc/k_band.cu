@@ -396,6 +396,93 @@ __global__ void k_gb_residual(int64_t n, int64_t kl, int64_t ku, const zd *A, co
         atomicAdd(nrm2 + jn, s);
     }
 }
+
+// ---------------------------------------------- double-single band residual
+// Unevaluated float pairs (hi, lo) with error-free products (FMA) and sums;
+// the explicit _rn intrinsics keep the compiler from contracting the error
+// terms away.  ~48 significant bits.
+struct BDS {
+    float h, l;
+};
+__device__ __forceinline__ void bds_mac(BDS &acc, float ah, float al, float xh, float xl)
+{
+    float p = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -p);
+    e = __fmaf_rn(ah, xl, e);
+    e = __fmaf_rn(al, xh, e);
+    float s = __fadd_rn(acc.h, p);
+    float bb = __fsub_rn(s, acc.h);
+    float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    float t = __fadd_rn(acc.l, __fadd_rn(err, e));
+    float h = __fadd_rn(s, t);
+    acc.l = __fsub_rn(t, __fsub_rn(h, s));
+    acc.h = h;
+}
+
+// Complex FP64 values as double-single pairs, packed (hi.re, hi.im, lo.re,
+// lo.im): the band of A once at set-up, the solutions X_j before each
+// residual.
+__global__ void k_z2ds(int64_t count, const zd *__restrict__ x, float4 *__restrict__ y)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const zd v = x[e];
+        const float hr = (float)v.x, hm = (float)v.y;
+        y[e] = make_float4(hr, hm, (float)(v.x - (double)hr), (float)(v.y - (double)hm));
+    }
+}
+
+// R_j = RHS - z_j X_j + A X_j for B = I (M_j = z_j I - A), the band product
+// A X_j in double-single arithmetic on the FP32 pipe (the FP64 pipe is 64x
+// slower); nrm2[j] += ||R_j||_F^2.  Thread per (row, column) of one node:
+// a warp's A loads are one column of the band (coalesced), its X loads one
+// broadcast element.
+__global__ void k_gb_residual_ds(int64_t n, int64_t kl, int64_t ku, const float4 *__restrict__ Ads, int64_t ldin,
+                                 const zd *__restrict__ z, int64_t m, const zd *__restrict__ RHS,
+                                 const zd *__restrict__ X, const float4 *__restrict__ Xds, zd *__restrict__ R,
+                                 double *__restrict__ nrm2)
+{
+    __shared__ double red[32];
+    const int jn = blockIdx.y;
+    const zd zj = z[jn];
+    const zd *Xj = X + (int64_t)jn * n * m;
+    const float4 *Dj = Xds + (int64_t)jn * n * m;
+    zd *Rj = R + (int64_t)jn * n * m;
+    const int64_t total = n * m;
+    double part = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n, c = e / n;
+        const int64_t j0 = i - kl > 0 ? i - kl : 0, j1 = i + ku < n - 1 ? i + ku : n - 1;
+        BDS re{0.f, 0.f}, im{0.f, 0.f};
+        const float4 *xc = Dj + c * n;
+        for (int64_t j = j0; j <= j1; ++j) {
+            const float4 a = Ads[ku + i - j + j * ldin];
+            const float4 x = xc[j];
+            // (a.re + i a.im)(x.re + i x.im), each part hi + lo
+            bds_mac(re, a.x, a.z, x.x, x.z);
+            bds_mac(re, -a.y, -a.w, x.y, x.w);
+            bds_mac(im, a.x, a.z, x.y, x.w);
+            bds_mac(im, a.y, a.w, x.x, x.z);
+        }
+        const zd x = Xj[i + c * n];
+        const zd rhs = RHS[i + c * n];
+        const zd zx = zmul(zj, x);
+        const zd acc = zmake(rhs.x - zx.x + ((double)re.h + (double)re.l),
+                             rhs.y - zx.y + ((double)im.h + (double)im.l));
+        Rj[i + c * n] = acc;
+        part += zabs2(acc);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+        atomicAdd(nrm2 + jn, s);
+    }
+}
 }  // namespace
 
 size_t gb_scratch_elems(int64_t kl, int64_t ku, int q)
@@ -505,5 +592,27 @@ template int gb_solve<double2>(cudaStream_t, int64_t, int64_t, int64_t, int, con
                                int64_t, double2 *, int64_t, int64_t);
 template int gb_solve<float2>(cudaStream_t, int64_t, int64_t, int64_t, int, const float2 *, const int *,
                               int64_t, float2 *, int64_t, int64_t);
+
+int z2ds(cudaStream_t s, int64_t count, const zd *x, float4 *y)
+{
+    unsigned g = cdiv(count, 256);
+    if (g > 4096) g = 4096;
+    k_z2ds<<<g, 256, 0, s>>>(count, x, y);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+int gb_residual_ds(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const float4 *Ads, int64_t ldin, int q,
+                   const zd *z, int64_t m, const zd *RHS, const zd *X, float4 *Xds, zd *R, double *nrm2)
+{
+    int e;
+    if ((e = z2ds(s, (int64_t)q * n * m, X, Xds))) return e;
+    FEAST_CUDA_TRY(cudaMemsetAsync(nrm2, 0, sizeof(double) * q, s));
+    unsigned gx = cdiv(n * m, 256);
+    if (gx > 1024) gx = 1024;
+    k_gb_residual_ds<<<dim3(gx, q), 256, 0, s>>>(n, kl, ku, Ads, ldin, z, m, RHS, X, Xds, R, nrm2);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
 
 }  // namespace feast

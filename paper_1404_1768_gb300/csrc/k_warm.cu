@@ -1,0 +1,267 @@
+// Warm-started solve of the projected eigenproblem (GFEAST line 6).
+//
+// When the filter of line 16 is applied to the Ritz vectors of the previous
+// pass, ordered by their expected residual after filtering (r_i /
+// |rho(lambda_i)|, rho the filter function of eq. 4.1, so the most
+// converged pairs come first), the QR factorisation of line 17
+// keeps the order, and every leading group of converged Ritz vectors spans
+// an (almost) invariant subspace.  The projected matrix C = B~^{-1} A~ is
+// then block upper triangular up to a small remainder:
+//
+//     C = [ T11 + E11   C12 ]      T11 upper triangular (k x k),
+//         [ E21         C22 ]      E11 strictly lower, E11 and E21 small.
+//
+// The solve below takes k from the column norms of C's strictly lower
+// part, computes the Schur form of the trailing block only (C22 = Z T22
+// Z^H, the double-single multishift QR of k_zeig.cu on m - k instead of m
+// rows), and treats what is left as a perturbation: with Zh = diag(I, Z)
+// and C' = Zh^H C Zh = T^ + D (T^ upper triangular, D small), one Newton
+// step for the eigen-decomposition of C' starting from the eigenvectors V^
+// of T^ gives
+//
+//     F = V^{-1} C' V^,   lambda_i = F_ii,   G_ij = F_ij / (lambda_j - lambda_i),
+//     Y' = V^ (I + G),    Y = Zh Y'          (error O(|D|^2 / gap)).
+//
+// Every product is FP64.  The eigenpairs are accepted only if each
+// ||C' y'_i - lambda_i y'_i|| / ((max|C_ij| + |lambda_i|) ||y'_i||) is at
+// most accept_tol; otherwise the caller runs the cold solve (Hessenberg
+// reduction and QR of the whole matrix).  The subspace of every pass is the
+// paper's (span of the filtered Ritz vectors = span of the filtered U1);
+// only the way the projected problem is solved changes.
+#include "common.cuh"
+
+namespace feast {
+namespace {
+
+// Per column j: ||C[j+1:m, j]||_2 and max_i |C_ij|.  Warp per column.
+__global__ void k_col_stats(int m, const zd *__restrict__ C, double *__restrict__ lower, double *__restrict__ cmax)
+{
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (j >= m) return;
+    const zd *c = C + (int64_t)j * m;
+    double s = 0.0, mx = 0.0;
+    for (int i = lane; i < m; i += 32) {
+        const double a2 = zabs2(c[i]);
+        if (i > j) s += a2;
+        mx = fmax(mx, a2);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, off);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    if (lane == 0) {
+        lower[j] = sqrt(s);
+        cmax[j] = sqrt(mx);
+    }
+}
+
+__global__ void k_diag_lambda(int m, const zd *__restrict__ F, zd *__restrict__ alpha, zd *__restrict__ beta)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    alpha[i] = F[i + (int64_t)i * m];
+    beta[i] = zmake(1.0, 0.0);
+}
+
+// G_ij = F_ij / (lambda_j - lambda_i) off the diagonal, G_ii = 0 (in place).
+// A correction entry above 1/4 means the first-order step is not valid for
+// this pair: *bad is set and the solve is not accepted.
+__global__ void k_newton_g(int m, zd *__restrict__ F, const zd *__restrict__ lam, int *__restrict__ bad)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        if (i == j) {
+            F[e] = zmake(0.0, 0.0);
+            continue;
+        }
+        const zd d = zsub(lam[j], lam[i]);
+        const zd f = F[e];
+        const double d2 = zabs2(d), f2 = zabs2(f);
+        if (!(f2 <= 0.0625 * d2)) {
+            if (f2 > 0.0) *bad = 1;
+            F[e] = zmake(0.0, 0.0);
+            continue;
+        }
+        F[e] = zdiv(f, d);
+    }
+}
+
+// max_i ||W_i - lambda_i Y_i|| / ((cnorm + |lambda_i|) ||Y_i||) into *out
+// (non-negative doubles order like their bit patterns).  Warp per column.
+__global__ void k_eig_resid(int m, const zd *__restrict__ W, const zd *__restrict__ Y, const zd *__restrict__ lam,
+                            double cnorm, unsigned long long *__restrict__ out)
+{
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= m) return;
+    const zd l = lam[i];
+    const zd *w = W + (int64_t)i * m;
+    const zd *y = Y + (int64_t)i * m;
+    double r = 0.0, yy = 0.0;
+    for (int p = lane; p < m; p += 32) {
+        const zd yv = y[p];
+        const zd d = zsub(w[p], zmul(l, yv));
+        r += zabs2(d);
+        yy += zabs2(yv);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        r += __shfl_xor_sync(0xffffffffu, r, off);
+        yy += __shfl_xor_sync(0xffffffffu, yy, off);
+    }
+    if (lane == 0) {
+        double rel = (yy > 0.0) ? sqrt(r / yy) / (cnorm + zabs(l)) : 1e300;
+        if (!(rel == rel)) rel = 1e300;
+        atomicMax(out, (unsigned long long)__double_as_longlong(rel));
+    }
+}
+
+// Column gather: Vout[:, i] = Vin[:, perm[i]] (rows x m, leading dim rows).
+__global__ void k_permute_cols(int64_t rows, int m, const int *__restrict__ perm, const zd *__restrict__ Vin,
+                               zd *__restrict__ Vout)
+{
+    const int64_t total = rows * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % rows;
+        const int j = (int)(e / rows);
+        Vout[e] = Vin[i + (int64_t)perm[j] * rows];
+    }
+}
+
+struct WarmCarve {
+    zd *Cp, *W, *Yp, *S, *Z;
+    double *lower, *cmax;
+    unsigned long long *res;
+    int *bad;
+};
+
+WarmCarve warm_carve(void *work, int m)
+{
+    WarmCarve w;
+    const size_t mm = (size_t)m * m;
+    zd *p = (zd *)work;
+    w.Cp = p;
+    w.W = p + mm;
+    w.Yp = p + 2 * mm;
+    w.S = p + 3 * mm;
+    w.Z = p + 4 * mm;
+    w.lower = (double *)(p + 5 * mm);
+    w.cmax = w.lower + m;
+    w.res = (unsigned long long *)(w.cmax + m);
+    w.bad = (int *)(w.res + 1);
+    return w;
+}
+
+unsigned grid_for(size_t count)
+{
+    const unsigned g = cdiv(count, 256);
+    return g > 4096 ? 4096 : g;
+}
+
+}  // namespace
+
+size_t zeig_warm_work_bytes(int m)
+{
+    return sizeof(zd) * 5 * (size_t)m * m + sizeof(double) * 2 * (size_t)m + 64;
+}
+
+int permute_cols(cudaStream_t s, int64_t rows, int m, const int *perm, const zd *Vin, zd *Vout)
+{
+    k_permute_cols<<<grid_for((size_t)rows * m), 256, 0, s>>>(rows, m, perm, Vin, Vout);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *warm_work, void *qz_work,
+              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats)
+{
+    *res = WarmResult{};
+    if (m < prm.min_m) return FEAST_OK;
+    const WarmCarve w = warm_carve(warm_work, m);
+    const size_t mm = (size_t)m * m;
+    const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
+    int e;
+    // C = B~^{-1} A~ (B~ = R2 is upper triangular)
+    if ((e = trsm_upper_batched<zd>(s, m, m, 1, Bt, m, 0, A, m, 0))) return e;
+    zd *C = A;
+    k_col_stats<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, C, w.lower, w.cmax);
+    FEAST_LAUNCH_CHECK();
+    double *h = (double *)malloc(sizeof(double) * 2 * (size_t)m);
+    if (!h) return FEAST_EINVAL;
+    if (cudaMemcpyAsync(h, w.lower, sizeof(double) * 2 * (size_t)m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        free(h);
+        return FEAST_ECUDA;
+    }
+    double hn = 0.0;
+    for (int j = 0; j < m; ++j) hn = fmax(hn, h[m + j]);
+    int k = 0;
+    while (k < m && h[k] <= prm.tau * hn) ++k;
+    free(h);
+    res->k = k;
+    if (k < m - prm.min_tail) {
+        if (k < m / 4) return FEAST_OK;  // too little has converged: cold solve
+    } else {
+        k = m - prm.min_tail;
+    }
+    const int mb = m - k;
+    // Schur form of the trailing block: C22 = Z T22 Z^H
+    FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.S, sizeof(zd) * mb, C + k + (int64_t)k * m, sizeof(zd) * m, sizeof(zd) * mb,
+                                     mb, cudaMemcpyDeviceToDevice, s));
+    if ((e = schur_large(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr))) return e;
+    // C' = Zh^H C Zh, Zh = diag(I_k, Z)
+    FEAST_CUDA_TRY(cudaMemcpyAsync(w.Cp, C, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+    if ((e = zgemm_batched(s, 0, m, mb, mb, one, C + (int64_t)k * m, m, 0, w.Z, mb, 0, zero, w.Cp + (int64_t)k * m, m,
+                           0, 1)))
+        return e;
+    if ((e = zgemm_batched(s, 1, mb, m, mb, one, w.Z, mb, 0, w.Cp + k, m, 0, zero, C + k, m, 0, 1))) return e;
+    FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.Cp + k, sizeof(zd) * m, C + k, sizeof(zd) * m, sizeof(zd) * mb, m,
+                                     cudaMemcpyDeviceToDevice, s));
+    // T^: C' with T22 from the QR in its trailing block (upper triangles are
+    // all that the eigenvector recurrence reads)
+    FEAST_CUDA_TRY(cudaMemcpyAsync(C, w.Cp, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+    FEAST_CUDA_TRY(cudaMemcpy2DAsync(C + k + (int64_t)k * m, sizeof(zd) * m, w.S, sizeof(zd) * mb, sizeof(zd) * mb,
+                                     mb, cudaMemcpyDeviceToDevice, s));
+    zd *Vh = Bt;  // V^, unit upper triangular
+    if ((e = schur_vectors(s, m, C, Vh, hn))) return e;
+    // F = V^{-1} (C' V^)
+    if ((e = zgemm_batched(s, 0, m, m, m, one, w.Cp, m, 0, Vh, m, 0, zero, w.W, m, 0, 1))) return e;
+    zd *F = V;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(F, w.W, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+    if ((e = trsm_upper_batched<zd>(s, m, m, 1, Vh, m, 0, F, m, 0))) return e;
+    k_diag_lambda<<<cdiv(m, 128), 128, 0, s>>>(m, F, alpha, beta);
+    FEAST_LAUNCH_CHECK();
+    FEAST_CUDA_TRY(cudaMemsetAsync(w.res, 0, 16, s));
+    k_newton_g<<<grid_for(mm), 256, 0, s>>>(m, F, alpha, w.bad);
+    FEAST_LAUNCH_CHECK();
+    // Y' = V^ + V^ G, and its residual against C'
+    FEAST_CUDA_TRY(cudaMemcpyAsync(w.Yp, Vh, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+    if ((e = zgemm_batched(s, 0, m, m, m, one, Vh, m, 0, F, m, 0, one, w.Yp, m, 0, 1))) return e;
+    if ((e = zgemm_batched(s, 0, m, m, m, one, w.Cp, m, 0, w.Yp, m, 0, zero, w.W, m, 0, 1))) return e;
+    k_eig_resid<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, w.W, w.Yp, alpha, hn, w.res);
+    FEAST_LAUNCH_CHECK();
+    struct {
+        unsigned long long r;
+        int bad;
+        int pad;
+    } hr{};
+    FEAST_CUDA_TRY(cudaMemcpyAsync(&hr, w.res, 16, cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    double worst;
+    memcpy(&worst, &hr.r, sizeof(double));
+    res->resid = worst;
+    res->tail = mb;
+    if (hr.bad || !(worst <= prm.accept_tol)) return FEAST_OK;
+    // Y = Zh Y', unit columns
+    FEAST_CUDA_TRY(cudaMemcpy2DAsync(V, sizeof(zd) * m, w.Yp, sizeof(zd) * m, sizeof(zd) * k, m,
+                                     cudaMemcpyDeviceToDevice, s));
+    if ((e = zgemm_batched(s, 0, mb, m, mb, one, w.Z, mb, 0, w.Yp + k, m, 0, zero, V + k, m, 0, 1))) return e;
+    if ((e = normalise_cols(s, m, V))) return e;
+    res->accepted = 1;
+    return FEAST_OK;
+}
+
+}  // namespace feast

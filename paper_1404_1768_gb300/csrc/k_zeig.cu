@@ -1050,24 +1050,23 @@ __global__ void k_absmax(int64_t count, const zd *x, double *out)
 
 }  // namespace
 
-size_t zeig_large_work_bytes(int m)
+size_t schur_large_work_bytes(int m)
 {
-    // Q (m*m) + v (m) + w (m) + u (2m) complex, tau, absmax, rotations,
-    // barrier words, then the double-single copies of H and Q (m*m float4
-    // each)
-    return sizeof(zd) * ((size_t)m * m + 4 * (size_t)m) + 64 + sizeof(RotDS) * NSH * CH +
-           sizeof(float2) * NSH + sizeof(float4) * NW * NW + 16 + 64 + 256 + 2 * sizeof(float4) * (size_t)m * m;
+    // v (m) + w (m) + u (2m) complex, tau, absmax, rotations, barrier words,
+    // then the double-single copies of H and Q (m*m float4 each)
+    return sizeof(zd) * (4 * (size_t)m) + 64 + sizeof(RotDS) * NSH * CH + sizeof(float2) * NSH +
+           sizeof(float4) * NW * NW + 16 + 64 + 256 + 2 * sizeof(float4) * (size_t)m * m;
 }
 
-// A (m x m, overwritten), Bt (m x m upper triangular, overwritten by the
-// solve), alpha/beta (beta = 1), V (m x m unit eigenvectors).
-int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
-               int *fail, int *timeout, int *stats)
+size_t zeig_large_work_bytes(int m)
+{
+    return sizeof(zd) * (size_t)m * m + schur_large_work_bytes(m);
+}
+
+int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int *timeout, int *stats, double *hn_out)
 {
     if (m <= 0) return FEAST_OK;
-    char *w = (char *)work;
-    zd *Q = (zd *)w;
-    zd *v = Q + (size_t)m * m;
+    zd *v = (zd *)work;
     zd *wv = v + m;
     zd *u = wv + m;
     double *tau = (double *)(u + 2 * m);
@@ -1079,10 +1078,6 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     unsigned *bar = (unsigned *)(ctl + 4);
     float4 *Hds = (float4 *)(((uintptr_t)(bar + 16) + 255) & ~(uintptr_t)255);
     float4 *Qds = Hds + (size_t)m * m;
-    int e;
-    // C = B~^{-1} A~  (upper-triangular solve with m right-hand sides)
-    if ((e = trsm_upper_batched<zd>(s, m, m, 1, Bt, m, 0, A, m, 0))) return e;
-    zd *C = A;
     k_eye<<<cdiv((size_t)m * m, 256) > 2048 ? 2048 : cdiv((size_t)m * m, 256), 256, 0, s>>>(m, Q, m);
     FEAST_LAUNCH_CHECK();
     // Hessenberg reduction C <- Q^H C Q
@@ -1113,6 +1108,7 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     FEAST_CUDA_TRY(cudaMemsetAsync(bar, 0, 16, s));
     FEAST_CUDA_TRY(cudaMemsetAsync(timeout, 0, sizeof(int), s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hn_out) *hn_out = hn;
     // QR sweeps: cooperative grid, one CTA per SM at most
     int dev = 0, sms = 0, per = 0;
     FEAST_CUDA_TRY(cudaGetDevice(&dev));
@@ -1144,6 +1140,23 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     FEAST_LAUNCH_CHECK();
     k_from_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, Qds, Q);
     FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+// A (m x m, overwritten), Bt (m x m upper triangular, overwritten by the
+// solve), alpha/beta (beta = 1), V (m x m unit eigenvectors).
+int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
+               int *fail, int *timeout, int *stats)
+{
+    if (m <= 0) return FEAST_OK;
+    zd *Q = (zd *)work;
+    int e;
+    // C = B~^{-1} A~  (upper-triangular solve with m right-hand sides)
+    if ((e = trsm_upper_batched<zd>(s, m, m, 1, Bt, m, 0, A, m, 0))) return e;
+    zd *C = A;
+    double hn = 0.0;
+    if ((e = schur_large(s, m, C, Q, (char *)work + sizeof(zd) * (size_t)m * m, fail, timeout, stats, &hn)))
+        return e;
     // eigenvalues and eigenvectors
     k_diag_out<<<cdiv(m, 128), 128, 0, s>>>(m, C, m, alpha, beta);
     FEAST_LAUNCH_CHECK();
@@ -1152,6 +1165,21 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     FEAST_LAUNCH_CHECK();
     if ((e = zgemm_batched(s, 0, m, m, m, zmake(1.0, 0.0), Q, m, 0, Yh, m, 0, zmake(0.0, 0.0), V, m, 0, 1)))
         return e;
+    k_normalise_cols<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, V, m);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+// Launch helpers for the warm-started solve (k_warm.cu).
+int schur_vectors(cudaStream_t s, int m, const zd *T, zd *Y, double snorm)
+{
+    k_schur_vectors<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, T, m, Y, snorm);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+int normalise_cols(cudaStream_t s, int m, zd *V)
+{
     k_normalise_cols<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, V, m);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;

@@ -56,6 +56,27 @@ def test_band_filter_matches_oracle(prec, n, kl, ku, m0, q):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,kl,ku,m0,q", [(100, 10, 10, 8, 8), (333, 37, 21, 11, 6)])
+def test_band_filter_identity_b_matches_oracle(prec, n, kl, ku, m0, q):
+    """B = I: the precision form's refinement residual takes its band product
+    A X in double-single arithmetic; the filtered block still agrees with the
+    oracle's to 1e-10."""
+    fg = _fg()
+    A = _random_band(n, kl, ku, 5 * n)
+    A[ku, :] *= 4.0
+    Y = inputs.complex_normal(np.random.default_rng(7), (n, m0))
+    kw = dict(contour_kind=1, rule=1, q=q, center=0.3 - 0.4j, a=2.5, b=1.2, kind=1, kl=kl, ku=ku,
+              b_identity=True)
+    g = fg.Feast(A, None, Y, prec=prec, refine_tol=1e-14, max_refine=8, **kw)
+    o = oracle.Feast(A, None, Y, **kw)
+    V = inputs.complex_normal(np.random.default_rng(8), (n, m0))
+    Ug, Uo = g.filter(V), o.filter(V)
+    err = np.abs(Ug - Uo).max() / np.abs(Uo).max()
+    assert err < (1e-11 if prec == 0 else 1e-10), err
+    g.close(); o.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_band_gfeast_small_grid_closed_form(prec):
     """12 x 12 grid, ellipse around the lowest 5 eigenvalues: exact count,
     closed-form eigenvalues, and agreement with the oracle's run."""

@@ -69,10 +69,12 @@ def test_singular_matrix_reports_info():
 
 
 # ------------------------------------------------------------------ QZ
-@pytest.mark.parametrize("m", [1, 2, 5, 16, 40, 64, 65, 100, 300])
+@pytest.mark.parametrize("m", [1, 2, 5, 16, 40, 64, 65, 100, 300, 400])
 def test_qz_matches_oracle(m):
     """Eigenvalues as multisets (the order of a QZ run is not unique) and the
-    generalized eigen-residual of every returned vector."""
+    generalized eigen-residual of every returned vector.  m <= 64: one-CTA QZ;
+    65..320: one-CTA double-single QR with window solves; 400: the cooperative
+    multishift QR with early deflation."""
     fg = _fg()
     rng = np.random.default_rng(30 + m)
     As = [inputs.complex_normal(rng, (m, m)) for _ in range(2)]

@@ -1,12 +1,15 @@
-"""Precision form (complex64 factors and solves on the tensor cores, refined
-with a residual whose products are FP64-accurate tensor-core GEMMs) against
+"""Precision form (complex64 factors and solves on the tensor cores) against
 the FP64 oracle.
 
-Tolerances: a complex64 LU agrees with the FP64 one to ~n * 2^-24 relative;
-after refinement the shifted solves reach the refinement target
-(relative residual 1e-14 -> forward error ~kappa * 1e-14) and the whole
-method must meet the stated bars: eigenvalues within 1e-8 relative of the
-oracle, exact count, residual of eq. 5.1 below 1e-10."""
+Tolerances: a complex64 LU agrees with the FP64 one to ~n * 2^-24 relative.
+The standalone subspace build (feast_filter) refines each shifted solve with
+a residual whose products are FP64-accurate tensor-core GEMMs, to the
+refinement target (relative residual 1e-14 -> forward error ~kappa *
+1e-14).  Inside the iteration line 16 takes the defect form on the Ritz
+pairs (the solves see only the residual block), and the whole method must
+reach FP64-level results: exact count, eigenvalues within 1e-10 relative of
+the oracle, residuals of eq. 5.1 below 1e-12.
+"""
 import numpy as np
 import pytest
 
@@ -65,12 +68,14 @@ def test_unrefined_filter_is_single_precision():
 
 def test_gfeast_precision_form_n200():
     """Whole GFEAST in the precision form on the n = 200 workload: exact
-    count, eigenvalues within 1e-8 relative of the oracle's and of the
-    prescribed spectrum, every residual of eq. 5.1 below 1e-10."""
+    count, eigenvalues within 1e-10 relative of the oracle's and of the
+    prescribed spectrum, every residual of eq. 5.1 below 1e-12 -- FP64-level
+    accuracy with complex64 solves and no refinement sweep inside the
+    iteration (line 16 takes the defect form on the Ritz pairs)."""
     fg = _fg()
     p = inputs.prescribed_pencil(CFG1["n"], CFG1["m0"], seed=CFG1["seed"])
     kw = dict(contour_kind=0, rule=CFG1["rule"], q=CFG1["q"], center=CFG1["center"],
-              a=CFG1["radius"], eps=1e-10, eta=1e-3, max_iter=50)
+              a=CFG1["radius"], eps=1e-12, eta=1e-3, max_iter=50)
     g = fg.Feast(p.A, p.B, p.Y, prec=fg.FEAST_C64_REFINE, refine_tol=1e-14, max_refine=5, **kw)
     hist = g.run()
     rg = g.eigs()
@@ -80,13 +85,12 @@ def test_gfeast_precision_form_n200():
     assert rg["flag"] == 1
     assert rg["count"] == ro["count"] == p.inside_count()
     ref = p.lam[np.abs(p.lam - CFG1["center"]) < CFG1["radius"]]
-    assert _match(rg["lam"], ro["lam"]) < 1e-8
-    assert _match(rg["lam"], ref) < 1e-8
-    assert np.all(rg["res"] < 1e-10)
+    assert _match(rg["lam"], ro["lam"]) < 1e-10
+    assert _match(rg["lam"], ref) < 1e-10
+    assert np.all(rg["res"] < 1e-12)
     for i in range(rg["count"]):
         x = rg["X"][:, i]
         r = p.A @ x - rg["lam"][i] * (p.B @ x)
-        assert np.linalg.norm(r) / (np.linalg.norm(p.A @ x) + np.linalg.norm(p.B @ x)) < 1e-10
-    # the refinement actually ran in the late passes
-    assert max(h["refine_sweeps_max"] for h in hist) >= 1
+        assert np.linalg.norm(r) / (np.linalg.norm(p.A @ x) + np.linalg.norm(p.B @ x)) < 1e-12
+    assert all(h["refine_sweeps_max"] == 0 for h in hist)
     g.close(); o.close()
