@@ -255,6 +255,17 @@ struct OzScratch {
     void *rows, *cols;
     int *err;
 };
+// QR by Cholesky QR twice (k_chol.cu): V (n x m, ldv) <- Q, R (may be null)
+// <- upper triangular with real positive diagonal.  Gram matrices and the
+// products V R^{-1} on the tensor cores (oz.rows >= oz_rows_bytes(max(n, m),
+// max(n, m)), oz.cols >= oz_cols_bytes(n, m)); Cholesky and triangular
+// inverses FP64.  *ok = 0 (V untouched) when a pivot shows cond(V) beyond
+// reach (checked on the first factorisation); the caller then runs
+// BCGS2.  work: zorth_chol_work_bytes(m).
+size_t zorth_chol_work_bytes(int64_t m);
+int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr, void *work,
+               const OzScratch &oz, int *ok);
+
 int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr,
           zd *work, int *timeout, const OzScratch *oz = nullptr);
 size_t zorth_work_elems(int64_t n, int64_t m);

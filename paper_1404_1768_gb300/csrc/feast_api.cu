@@ -56,6 +56,7 @@ struct feast_ctx {
     double *reso;
     zd *tmp;            // n x m0
     zd *orth_work;
+    void *chol_work;    // Cholesky QR (dense precision form)
     void *qz_work;
     void *warm_work;    // warm-started projected eigensolve (m0 >= kWarmMinM)
     int *pair_perm;     // m0: order of the Ritz pairs (most converged next pass first)
@@ -187,6 +188,7 @@ void carve(feast_ctx *c, Carver &cv)
             c->ozR = cv.take<char>(r1 > r2 ? r1 : r2);
         }
         c->Xhi = cv.take<cf>(q * n * m);
+        c->chol_work = cv.take<char>(zorth_chol_work_bytes((int64_t)m));
         c->C32 = cv.take<cf>(q * n * m);
         c->R64 = cv.take<zd>(q * n * m);
         c->nrm2 = cv.take<double>(q + 1);
@@ -471,6 +473,21 @@ int filter_defect(feast_ctx *c, zd *Uout)
     return defect_sum(s, n, (int)m, (int)q, c->C32, nm, c->w, c->Xr, c->dfx, Uout);
 }
 
+// V = Q R in place (n x m0).  Dense precision form: Cholesky QR twice on
+// the tensor-core products (k_chol.cu), BCGS2 if V is too ill-conditioned
+// for it; otherwise BCGS2 (k_zorth.cu).
+int orth_block(feast_ctx *c, zd *V, zd *R)
+{
+    const int64_t n = c->n, m = c->m0;
+    int e;
+    if (c->chol_work) {
+        int ok = 0;
+        if ((e = zorth_chol(c->s, n, m, V, n, R, m, c->chol_work, *orth_oz(c), &ok))) return e;
+        if (ok) return FEAST_OK;
+    }
+    return zorth(c->s, n, m, V, n, R, m, c->orth_work, &c->st->timeout, orth_oz(c));
+}
+
 // U1 R1 = U ; W[:, m0:] = B U1 ; U2 R2 = B U1   (GFEAST lines 2, 17)
 int orthonormalise(feast_ctx *c, const zd *Usrc)
 {
@@ -478,11 +495,11 @@ int orthonormalise(feast_ctx *c, const zd *Usrc)
     int e;
     if (Usrc != c->U1)
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->U1, Usrc, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    if ((e = zorth(c->s, n, m, c->U1, n, c->R1, m, c->orth_work, &c->st->timeout, orth_oz(c)))) return e;
+    if ((e = orth_block(c, c->U1, c->R1))) return e;
     zd *BU1 = c->W + n * m;
     if ((e = apply_B(c, c->U1, BU1, m))) return e;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work, &c->st->timeout, orth_oz(c));
+    return orth_block(c, c->U2, c->R2);
 }
 
 }  // namespace
@@ -845,7 +862,7 @@ int feast_set_subspace(feast_ctx *c, const void *U1)
     int e = apply_B(c, c->U1, BU1, m);
     if (e) return e;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    return zorth(c->s, n, m, c->U2, n, c->R2, m, c->orth_work, &c->st->timeout, orth_oz(c));
+    return orth_block(c, c->U2, c->R2);
 }
 
 void feast_destroy(feast_ctx *c)

@@ -94,3 +94,34 @@ def test_gfeast_precision_form_n200():
         assert np.linalg.norm(r) / (np.linalg.norm(p.A @ x) + np.linalg.norm(p.B @ x)) < 1e-12
     assert all(h["refine_sweeps_max"] == 0 for h in hist)
     g.close(); o.close()
+
+
+@pytest.mark.parametrize("n,m0,cond", [(200, 64, 1e2), (700, 230, 1e4), (700, 230, 1e9)])
+def test_cholesky_qr_of_b_u1(n, m0, cond):
+    """U2 R2 = B U1 in the precision form (Cholesky QR twice on tensor-core
+    Gram matrices; BCGS2 when the block is too ill-conditioned for it -- the
+    cond = 1e9 case): U2 orthonormal, R2 upper triangular with a real
+    positive diagonal, U2 R2 = B U1, and both equal to the unique Householder
+    factors with that sign convention (numpy's QR, signs fixed)."""
+    fg = _fg()
+    p = inputs.prescribed_pencil(n, m0, seed=n + 1)
+    g = fg.Feast(p.A, p.B, p.Y, prec=fg.FEAST_C64_REFINE, q=8, center=0j, a=1.0)
+    rng = np.random.default_rng(11)
+    # U1 with the chosen condition number (U1 itself need not be orthonormal
+    # for this entry point; B U1 inherits the conditioning)
+    Qa, _ = np.linalg.qr(inputs.complex_normal(rng, (n, m0)))
+    Qb, _ = np.linalg.qr(inputs.complex_normal(rng, (m0, m0)))
+    U1 = (Qa * np.logspace(0, -np.log10(cond), m0)[None, :]) @ Qb
+    g.set_subspace(U1)
+    U2, R2 = g.get("U2"), g.get("R2")
+    BU1 = p.B @ U1
+    assert np.abs(U2.conj().T @ U2 - np.eye(m0)).max() < 1e-12
+    assert np.allclose(np.tril(R2, -1), 0) and np.all(np.diag(R2).real > 0)
+    assert np.abs(np.diag(R2).imag).max() <= 1e-14 * np.abs(R2).max()
+    assert np.abs(U2 @ R2 - BU1).max() <= 1e-12 * np.abs(BU1).max()
+    Qn, Rn = np.linalg.qr(BU1)
+    ph = np.diag(Rn) / np.abs(np.diag(Rn))
+    Qn, Rn = Qn * ph[None, :], ph.conj()[:, None] * Rn
+    if cond <= 1e4:
+        np.testing.assert_allclose(U2, Qn, rtol=0, atol=1e-9)
+    g.close()
