@@ -584,7 +584,8 @@ def gpu_arm(args):
             "refine_sweeps": [i["refine_sweeps_max"] for i in infos],
             "qz": {"sweeps": [i["qz_sweeps"] for i in infos], "phases": [i["qz_phases"] for i in infos],
                    "warm": [i["qz_warm"] for i in infos], "qr_rows": [i["qz_rows"] for i in infos],
-                   "warm_resid": [i["qz_warm_resid"] for i in infos]},
+                   "warm_resid": [i["qz_warm_resid"] for i in infos],
+                   "warm_k": [i["qz_warm_k"] for i in infos]},
             "fp64_path": fp64,
             "roofline": roof,
             "roofline_kernels": roof_kernels,

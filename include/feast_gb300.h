@@ -129,6 +129,8 @@ typedef struct {
     int qz_rows;      /* rows given to the QR this pass (m0 when cold) */
     double qz_warm_resid; /* largest relative eigen-residual of the warm
                          solve's Newton step (0 when not tried) */
+    int qz_warm_k;    /* converged leading columns the warm solve found
+                         (-1 when it was not tried) */
 } feast_iter_info;
 
 typedef struct feast_ctx feast_ctx;

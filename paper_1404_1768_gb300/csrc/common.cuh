@@ -198,10 +198,15 @@ __device__ __forceinline__ bool grid_barrier(const GridSync &g)
 
 // ---------------------------------------------------------------- kernels (FP64)
 // Templated dense kernels (T = double2 or float2), instantiated in k_dense.cu.
+// tri (structure the GEMM may skip): 0 none; 1 op(A) upper triangular
+// (row tile i0 starts its K loop at i0); 2 B upper triangular (column tile
+// j0 ends it at j0 + tile width); 3 only the upper triangle of C is wanted
+// (tiles strictly below the diagonal are not computed).  1 and 2 need
+// conj_a = 0.
 template <typename T>
 int gemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, T alpha,
                  const T *A, int64_t lda, int64_t sA, const T *B, int64_t ldb, int64_t sB,
-                 T beta, T *C, int64_t ldc, int64_t sC, int batch);
+                 T beta, T *C, int64_t ldc, int64_t sC, int batch, int tri = 0);
 template <typename T>
 int getrf_batched(cudaStream_t s, int64_t n, int batch, T *F, int64_t ldf, int64_t sF, int *piv,
                   int *info, int *row);
@@ -224,7 +229,7 @@ int gather_rows(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const int *p
 // Strides are in elements between consecutive batch members.
 int zgemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, zd alpha,
                   const zd *A, int64_t lda, int64_t sA, const zd *B, int64_t ldb, int64_t sB,
-                  zd beta, zd *C, int64_t ldc, int64_t sC, int batch);
+                  zd beta, zd *C, int64_t ldc, int64_t sC, int batch, int tri = 0);
 
 // M_j = z_j B - A for j = 0..q-1 into F (q blocks of ldf x n); B may be null
 // (identity).
@@ -262,6 +267,11 @@ struct OzScratch {
 // inverses FP64.  *ok = 0 (V untouched) when a pivot shows cond(V) beyond
 // reach (checked on the first factorisation); the caller then runs
 // BCGS2.  work: zorth_chol_work_bytes(m).
+// Ri (m x m, ld m) = R^{-1}, R upper triangular (ld ldr); recursive
+// doubling over 32 x 32 diagonal blocks with batched FP64 GEMMs (k_chol.cu).
+// T: tri_inverse_scratch_elems(m) entries.
+size_t tri_inverse_scratch_elems(int m);
+int tri_inverse(cudaStream_t s, int m, const zd *R, int64_t ldr, zd *Ri, zd *T);
 size_t zorth_chol_work_bytes(int64_t m);
 int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr, void *work,
                const OzScratch &oz, int *ok);

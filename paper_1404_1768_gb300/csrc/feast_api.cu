@@ -91,6 +91,7 @@ struct feast_ctx {
     int ritz_filter;    // line 16 of this pass filters the Ritz vectors
     int warm_ready;     // U1 comes from ordered Ritz vectors: line 6 may start warm
     WarmResult last_warm;
+    int warm_tried;
     int k, c_prev, done, cur;
     double e_prev;
     int out_count, out_flag, out_k;
@@ -105,7 +106,7 @@ namespace {
 constexpr int kWarmMinM = 96;
 constexpr int kWarmMinTail = 65;     // the QR's own size range (m > 64)
 constexpr double kWarmTauMin = 1e-8; // converged column: strictly lower part <= tau max|C|
-constexpr double kWarmAccMin = 1e-13;
+constexpr double kWarmAccMin = 1e-12;  // the cold double-single QR's own backward error (2^-44 of ||H||)
 
 struct Carver {
     char *base;
@@ -687,6 +688,7 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     // line 6: projected eigenpairs, x_i = U1 y_i
     FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_sweeps, 0, 3 * sizeof(int), s));
     c->last_warm = WarmResult{};
+    c->warm_tried = c->warm_ready;
     if (c->warm_ready) {
         // the previous pass filtered its |rho|-ordered Ritz vectors: C is
         // block upper triangular up to a remainder of the size of its
@@ -792,6 +794,7 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
         info->qz_warm = c->last_warm.accepted;
         info->qz_rows = c->last_warm.accepted ? c->last_warm.tail : (int)m;
         info->qz_warm_resid = c->last_warm.resid;
+        info->qz_warm_k = c->warm_tried ? c->last_warm.k : -1;
     }
     return FEAST_OK;
 }

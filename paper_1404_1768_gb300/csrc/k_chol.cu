@@ -27,18 +27,19 @@ __global__ void k_diag_copy(int m, const zd *__restrict__ G, double *__restrict_
 }
 
 // Unblocked Cholesky of the diagonal block G[k0:k0+nb, k0:k0+nb] (upper
-// triangle in, R's upper triangle out), one warp: lane k owns column k.
-__global__ void __launch_bounds__(32) k_chol_diag(int m, zd *__restrict__ G, int k0, int nb,
-                                                  const double *__restrict__ d0, int *__restrict__ fail)
+// triangle in, R's upper triangle out).  Thread (i, k) of 32 x 32 owns
+// entry (i, k); three barriers per column.
+__global__ void __launch_bounds__(CB * CB) k_chol_diag(int m, zd *__restrict__ G, int k0, int nb,
+                                                       const double *__restrict__ d0, int *__restrict__ fail)
 {
     __shared__ zd T[CB][CB + 1];
-    __shared__ double rjj;
-    const int k = threadIdx.x;
-    for (int i = 0; i < nb; ++i)
-        if (k < nb) T[i][k] = G[(k0 + i) + (int64_t)(k0 + k) * m];
-    __syncwarp();
+    __shared__ double rinv;
+    const int i = threadIdx.x % CB, k = threadIdx.x / CB;
+    const bool live = (i < nb && k < nb);
+    if (live) T[i][k] = G[(k0 + i) + (int64_t)(k0 + k) * m];
+    __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        if (k == j) {
+        if (threadIdx.x == 0) {
             const double d = T[j][j].x;
             const double ref = d0[k0 + j];
             double r;
@@ -49,24 +50,19 @@ __global__ void __launch_bounds__(32) k_chol_diag(int m, zd *__restrict__ G, int
                 r = sqrt(d);
             }
             T[j][j] = zmake(r, 0.0);
-            rjj = r;
+            rinv = 1.0 / r;
         }
-        __syncwarp();
-        const double inv = 1.0 / rjj;
-        if (k > j && k < nb) T[j][k] = zscale(T[j][k], inv);
-        __syncwarp();
-        if (k > j && k < nb) {
-            const zd rjk = T[j][k];
-            for (int i = j + 1; i <= k; ++i) {
-                const zd rji = T[j][i];
-                // T[i][k] -= conj(r_ji) r_jk
-                T[i][k] = zsub(T[i][k], zmake(rji.x * rjk.x + rji.y * rjk.y, rji.x * rjk.y - rji.y * rjk.x));
-            }
+        __syncthreads();
+        if (live && i == j && k > j) T[j][k] = zscale(T[j][k], rinv);
+        __syncthreads();
+        if (live && i > j && k >= i) {
+            const zd rji = T[j][i], rjk = T[j][k];
+            // T[i][k] -= conj(r_ji) r_jk
+            T[i][k] = zsub(T[i][k], zmake(rji.x * rjk.x + rji.y * rjk.y, rji.x * rjk.y - rji.y * rjk.x));
         }
-        __syncwarp();
+        __syncthreads();
     }
-    for (int i = 0; i < nb; ++i)
-        if (k >= i && k < nb) G[(k0 + i) + (int64_t)(k0 + k) * m] = T[i][k];
+    if (live && k >= i) G[(k0 + i) + (int64_t)(k0 + k) * m] = T[i][k];
 }
 
 // Row block of R right of the diagonal block: R[k0:k0+nb, c] solves
@@ -113,14 +109,35 @@ __global__ void k_zero_lower(int m, zd *__restrict__ R, int64_t ld)
     }
 }
 
-__global__ void k_identity(int m, zd *__restrict__ X)
+// Inverse of each CB x CB diagonal block of the upper triangular R (ld
+// ldr) into Ri (ld m): block b by CTA b, thread k builds column k of the
+// block's inverse by back-substitution.
+__global__ void __launch_bounds__(CB) k_trinv_diag(int m, const zd *__restrict__ R, int64_t ldr, zd *__restrict__ Ri)
 {
-    const int64_t total = (int64_t)m * m;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % m), j = (int)(e / m);
-        X[e] = zmake(i == j ? 1.0 : 0.0, 0.0);
+    __shared__ zd T[CB][CB + 1];
+    const int b0 = blockIdx.x * CB;
+    const int nb = (m - b0) < CB ? (m - b0) : CB;
+    const int k = threadIdx.x;
+    for (int i = 0; i < nb; ++i)
+        if (k < nb) T[i][k] = R[(b0 + i) + (int64_t)(b0 + k) * ldr];
+    __syncthreads();
+    if (k >= nb) return;
+    zd x[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) x[i] = zmake(0.0, 0.0);
+    x[k] = zdiv(zmake(1.0, 0.0), T[k][k]);
+#pragma unroll
+    for (int i = CB - 1; i >= 0; --i) {
+        if (i >= k) continue;
+        zd acc = zmake(0.0, 0.0);
+#pragma unroll
+        for (int p = 0; p < CB; ++p)
+            if (p > i && p <= k) zfma(acc, T[i][p], x[p]);
+        x[i] = zdiv(zmake(-acc.x, -acc.y), T[i][i]);
     }
+#pragma unroll
+    for (int i = 0; i < CB; ++i)
+        if (i < nb) Ri[(b0 + i) + (int64_t)(b0 + k) * m] = x[i];
 }
 
 unsigned grid_for(size_t count)
@@ -138,14 +155,15 @@ int cholesky(cudaStream_t s, int m, zd *G, double *d0, int *fail)
     const zd mone = zmake(-1.0, 0.0), one = zmake(1.0, 0.0);
     for (int k0 = 0; k0 < m; k0 += CB) {
         const int nb = (m - k0) < CB ? (m - k0) : CB;
-        k_chol_diag<<<1, 32, 0, s>>>(m, G, k0, nb, d0, fail);
+        k_chol_diag<<<1, CB * CB, 0, s>>>(m, G, k0, nb, d0, fail);
         FEAST_LAUNCH_CHECK();
         const int k1 = k0 + nb;
         if (k1 >= m) break;
-        k_chol_row<<<cdiv(m - k1, 64), 64, 0, s>>>(m, G, k0, nb);
+        k_chol_row<<<cdiv(m - k1, 32), 32, 0, s>>>(m, G, k0, nb);
         FEAST_LAUNCH_CHECK();
+        // only the upper triangle of the trailing block is ever read
         int e = zgemm_batched(s, 1, m - k1, m - k1, nb, mone, G + k0 + (int64_t)k1 * m, m, 0,
-                              G + k0 + (int64_t)k1 * m, m, 0, one, G + k1 + (int64_t)k1 * m, m, 0, 1);
+                              G + k0 + (int64_t)k1 * m, m, 0, one, G + k1 + (int64_t)k1 * m, m, 0, 1, 3);
         if (e) return e;
     }
     return FEAST_OK;
@@ -153,9 +171,53 @@ int cholesky(cudaStream_t s, int m, zd *G, double *d0, int *fail)
 
 }  // namespace
 
+// Ri (m x m, ld m) = R^{-1} for upper triangular R (ld ldr): inverses of
+// the 32 x 32 diagonal blocks, then, level by level, adjacent inverted
+// blocks [A^{-1} X; 0 C^{-1}] get X = -A^{-1} B C^{-1} (B the block of R
+// between them) -- batched GEMMs over the equal pairs of a level, one more
+// pair for a shorter last block.  T: scratch of m * m / 2 + 32 * m entries.
+int tri_inverse(cudaStream_t s, int m, const zd *R, int64_t ldr, zd *Ri, zd *T)
+{
+    if (m <= 0) return FEAST_OK;
+    FEAST_CUDA_TRY(cudaMemsetAsync(Ri, 0, sizeof(zd) * (size_t)m * m, s));
+    k_trinv_diag<<<cdiv(m, CB), CB, 0, s>>>(m, R, ldr, Ri);
+    FEAST_LAUNCH_CHECK();
+    const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);
+    int e;
+    for (int64_t L = CB; L < m; L *= 2) {
+        const int64_t full = m / (2 * L);  // pairs with two L-blocks
+        const int64_t sR = 2 * L * (ldr + 1), sI = 2 * L * ((int64_t)m + 1);
+        if (full > 0) {
+            // T_p = A_p^{-1} B_p, then X_p = -T_p C_p^{-1}
+            if ((e = zgemm_batched(s, 0, L, L, L, one, Ri, m, sI, R + L * ldr, ldr, sR, zero, T, L, L * L, (int)full,
+                                   1)))
+                return e;
+            if ((e = zgemm_batched(s, 0, L, L, L, mone, T, L, L * L, Ri + L + L * (int64_t)m, m, sI, zero,
+                                   Ri + L * (int64_t)m, m, sI, (int)full, 2)))
+                return e;
+        }
+        const int64_t a0 = full * 2 * L, b0 = a0 + L;  // a leftover pair with a shorter second block
+        if (b0 < m) {
+            const int64_t w = m - b0;
+            if ((e = zgemm_batched(s, 0, L, w, L, one, Ri + a0 + a0 * (int64_t)m, m, 0, R + a0 + b0 * ldr, ldr, 0,
+                                   zero, T, L, 0, 1, 1)))
+                return e;
+            if ((e = zgemm_batched(s, 0, L, w, w, mone, T, L, 0, Ri + b0 + b0 * (int64_t)m, m, 0, zero,
+                                   Ri + a0 + b0 * (int64_t)m, m, 0, 1, 2)))
+                return e;
+        }
+    }
+    return FEAST_OK;
+}
+
+size_t tri_inverse_scratch_elems(int m)
+{
+    return (size_t)m * m / 2 + (size_t)CB * m + 64;
+}
+
 size_t zorth_chol_work_bytes(int64_t m)
 {
-    return sizeof(zd) * 3 * (size_t)m * m + sizeof(double) * (size_t)m + 64;
+    return sizeof(zd) * (3 * (size_t)m * m + tri_inverse_scratch_elems((int)m)) + sizeof(double) * (size_t)m + 64;
 }
 
 int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr, void *work,
@@ -171,7 +233,8 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
     zd *F0 = (zd *)work;
     zd *F1 = F0 + mm;
     zd *Ti = F1 + mm;
-    double *d0 = (double *)(Ti + mm);
+    zd *Ts = Ti + mm;
+    double *d0 = (double *)(Ts + tri_inverse_scratch_elems((int)m));
     int *fail = (int *)(d0 + m);
     const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
     int e;
@@ -192,9 +255,7 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
         k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F, m);
         FEAST_LAUNCH_CHECK();
         // V <- V F^{-1} (the digit planes of V are taken before V is overwritten)
-        k_identity<<<grid_for(mm), 256, 0, s>>>((int)m, Ti);
-        FEAST_LAUNCH_CHECK();
-        if ((e = trsm_upper_batched<zd>(s, m, m, 1, F, m, 0, Ti, m, 0))) return e;
+        if ((e = tri_inverse(s, (int)m, F, m, Ti, Ts))) return e;
         if ((e = oz_prepare_rows(s, n, m, V, ldv, oz.rows))) return e;
         if ((e = oz_prepare_cols(s, m, m, Ti, m, oz.cols))) return e;
         if ((e = oz_gemm(s, n, m, m, oz.rows, oz.cols, one, nullptr, 0, zero, V, ldv, oz.err))) return e;

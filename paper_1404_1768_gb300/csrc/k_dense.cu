@@ -37,17 +37,20 @@ __global__ void __launch_bounds__(GB_T) k_gemm(int conj_a, int64_t m, int64_t n,
                                                int64_t sA, const T *__restrict__ B,
                                                int64_t ldb, int64_t sB, T beta,
                                                T *__restrict__ C, int64_t ldc, int64_t sC,
-                                               int splits, int64_t kchunk)
+                                               int splits, int64_t kchunk, int tri)
 {
     __shared__ T As[GB_K][GB_M + 1];
     __shared__ T Bs[GB_K][GB_N + 1];
     const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
-    const int64_t kbeg = (int64_t)sp * kchunk;
-    const int64_t kend = (kbeg + kchunk < k) ? kbeg + kchunk : k;
+    const int64_t i0 = (int64_t)blockIdx.x * GB_M, j0 = (int64_t)blockIdx.y * GB_N;
+    if (tri == 3 && i0 >= j0 + GB_N) return;  // tile below the diagonal (uniform per CTA)
+    int64_t kbeg = (int64_t)sp * kchunk;
+    int64_t kend = (kbeg + kchunk < k) ? kbeg + kchunk : k;
+    if (tri == 1 && kbeg < i0) kbeg = i0;            // op(A)(i, k) = 0 for k < i
+    if (tri == 2 && kend > j0 + GB_N) kend = j0 + GB_N;  // B(k, j) = 0 for k > j
     A += (int64_t)b * sA;
     B += (int64_t)b * sB;
     C += (int64_t)b * sC;
-    const int64_t i0 = (int64_t)blockIdx.x * GB_M, j0 = (int64_t)blockIdx.y * GB_N;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     T acc[4][4];
 #pragma unroll
@@ -121,10 +124,11 @@ __global__ void k_scale(int64_t m, int64_t n, T beta, T *C, int64_t ldc, int64_t
 template <typename T>
 int gemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, T alpha,
                  const T *A, int64_t lda, int64_t sA, const T *B, int64_t ldb, int64_t sB,
-                 T beta, T *C, int64_t ldc, int64_t sC, int batch)
+                 T beta, T *C, int64_t ldc, int64_t sC, int batch, int tri)
 {
     if (m <= 0 || n <= 0 || batch <= 0) return FEAST_OK;
     if (batch > 65535) return FEAST_EINVAL;
+    if (tri < 0 || tri > 3 || (conj_a && (tri == 1 || tri == 2))) return FEAST_EINVAL;
     const unsigned tiles = cdiv(m, GB_M) * cdiv(n, GB_N) * (unsigned)batch;
     // split K when the output tiles cannot fill the GPU twice over (the
     // FP64 pipe is the bound, so every SM counts)
@@ -149,22 +153,22 @@ int gemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, T 
     dim3 grid(cdiv(m, GB_M), cdiv(n, GB_N), batch * splits);
     if (grid.y > 65535) return FEAST_EINVAL;
     k_gemm<T><<<grid, GB_T, 0, s>>>(conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
-                                    splits, kchunk);
+                                    splits, kchunk, tri);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }
 template int gemm_batched<double2>(cudaStream_t, int, int64_t, int64_t, int64_t, double2, const double2 *,
                                    int64_t, int64_t, const double2 *, int64_t, int64_t, double2, double2 *,
-                                   int64_t, int64_t, int);
+                                   int64_t, int64_t, int, int);
 template int gemm_batched<float2>(cudaStream_t, int, int64_t, int64_t, int64_t, float2, const float2 *,
                                   int64_t, int64_t, const float2 *, int64_t, int64_t, float2, float2 *,
-                                  int64_t, int64_t, int);
+                                  int64_t, int64_t, int, int);
 
 int zgemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, zd alpha,
                   const zd *A, int64_t lda, int64_t sA, const zd *B, int64_t ldb, int64_t sB,
-                  zd beta, zd *C, int64_t ldc, int64_t sC, int batch)
+                  zd beta, zd *C, int64_t ldc, int64_t sC, int batch, int tri)
 {
-    return gemm_batched<zd>(s, conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+    return gemm_batched<zd>(s, conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, tri);
 }
 
 // ------------------------------------------------------------------ z_j B - A

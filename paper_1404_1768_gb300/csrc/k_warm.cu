@@ -22,7 +22,11 @@
 //     F = V^{-1} C' V^,   lambda_i = F_ii,   G_ij = F_ij / (lambda_j - lambda_i),
 //     Y' = V^ (I + G),    Y = Zh Y'          (error O(|D|^2 / gap)).
 //
-// Every product is FP64.  The eigenpairs are accepted only if each
+// Every product is an FP64 GEMM (the triangular factors' zero halves
+// skipped); the triangular solves are products with explicit triangular
+// inverses.  (The digit-sliced tensor-core GEMM is 48-bit fixed point per
+// row and column: at m0 = 1280 it left the Newton residual near 3e-12
+// instead of 1e-13.)  The eigenpairs are accepted only if each
 // ||C' y'_i - lambda_i y'_i|| / ((max|C_ij| + |lambda_i|) ||y'_i||) is at
 // most accept_tol; otherwise the caller runs the cold solve (Hessenberg
 // reduction and QR of the whole matrix).  The subspace of every pass is the
@@ -132,7 +136,7 @@ __global__ void k_permute_cols(int64_t rows, int m, const int *__restrict__ perm
 }
 
 struct WarmCarve {
-    zd *Cp, *W, *Yp, *S, *Z;
+    zd *Cp, *W, *Yp, *S, *Z, *Ts;
     double *lower, *cmax;
     unsigned long long *res;
     int *bad;
@@ -148,7 +152,8 @@ WarmCarve warm_carve(void *work, int m)
     w.Yp = p + 2 * mm;
     w.S = p + 3 * mm;
     w.Z = p + 4 * mm;
-    w.lower = (double *)(p + 5 * mm);
+    w.Ts = p + 5 * mm;
+    w.lower = (double *)(w.Ts + tri_inverse_scratch_elems(m));
     w.cmax = w.lower + m;
     w.res = (unsigned long long *)(w.cmax + m);
     w.bad = (int *)(w.res + 1);
@@ -165,7 +170,7 @@ unsigned grid_for(size_t count)
 
 size_t zeig_warm_work_bytes(int m)
 {
-    return sizeof(zd) * 5 * (size_t)m * m + sizeof(double) * 2 * (size_t)m + 64;
+    return sizeof(zd) * (5 * (size_t)m * m + tri_inverse_scratch_elems(m)) + sizeof(double) * 2 * (size_t)m + 64;
 }
 
 int permute_cols(cudaStream_t s, int64_t rows, int m, const int *perm, const zd *Vin, zd *Vout)
@@ -184,9 +189,10 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     const size_t mm = (size_t)m * m;
     const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
     int e;
-    // C = B~^{-1} A~ (B~ = R2 is upper triangular)
-    if ((e = trsm_upper_batched<zd>(s, m, m, 1, Bt, m, 0, A, m, 0))) return e;
-    zd *C = A;
+    // C = B~^{-1} A~ (B~ = R2 is upper triangular), into Cp
+    if ((e = tri_inverse(s, m, Bt, m, w.W, w.Ts))) return e;
+    if ((e = zgemm_batched(s, 0, m, m, m, one, w.W, m, 0, A, m, 0, zero, w.Cp, m, 0, 1, 1))) return e;
+    const zd *C = w.Cp;
     k_col_stats<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, C, w.lower, w.cmax);
     FEAST_LAUNCH_CHECK();
     double *h = (double *)malloc(sizeof(double) * 2 * (size_t)m);
@@ -212,26 +218,27 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.S, sizeof(zd) * mb, C + k + (int64_t)k * m, sizeof(zd) * m, sizeof(zd) * mb,
                                      mb, cudaMemcpyDeviceToDevice, s));
     if ((e = schur_large(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr))) return e;
-    // C' = Zh^H C Zh, Zh = diag(I_k, Z)
-    FEAST_CUDA_TRY(cudaMemcpyAsync(w.Cp, C, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
-    if ((e = zgemm_batched(s, 0, m, mb, mb, one, C + (int64_t)k * m, m, 0, w.Z, mb, 0, zero, w.Cp + (int64_t)k * m, m,
-                           0, 1)))
+    // C' = Zh^H C Zh, Zh = diag(I_k, Z), into A (Bt as the row-block scratch)
+    zd *Cq = A;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(Cq, C, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+    if ((e = zgemm_batched(s, 0, m, mb, mb, one, C + (int64_t)k * m, m, 0, w.Z, mb, 0, zero, Cq + (int64_t)k * m, m, 0,
+                           1)))
         return e;
-    if ((e = zgemm_batched(s, 1, mb, m, mb, one, w.Z, mb, 0, w.Cp + k, m, 0, zero, C + k, m, 0, 1))) return e;
-    FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.Cp + k, sizeof(zd) * m, C + k, sizeof(zd) * m, sizeof(zd) * mb, m,
+    if ((e = zgemm_batched(s, 1, mb, m, mb, one, w.Z, mb, 0, Cq + k, m, 0, zero, Bt + k, m, 0, 1))) return e;
+    FEAST_CUDA_TRY(cudaMemcpy2DAsync(Cq + k, sizeof(zd) * m, Bt + k, sizeof(zd) * m, sizeof(zd) * mb, m,
                                      cudaMemcpyDeviceToDevice, s));
     // T^: C' with T22 from the QR in its trailing block (upper triangles are
-    // all that the eigenvector recurrence reads)
-    FEAST_CUDA_TRY(cudaMemcpyAsync(C, w.Cp, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
-    FEAST_CUDA_TRY(cudaMemcpy2DAsync(C + k + (int64_t)k * m, sizeof(zd) * m, w.S, sizeof(zd) * mb, sizeof(zd) * mb,
-                                     mb, cudaMemcpyDeviceToDevice, s));
+    // all that the eigenvector recurrence reads), into Cp
+    FEAST_CUDA_TRY(cudaMemcpyAsync(w.Cp, Cq, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+    FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.Cp + k + (int64_t)k * m, sizeof(zd) * m, w.S, sizeof(zd) * mb,
+                                     sizeof(zd) * mb, mb, cudaMemcpyDeviceToDevice, s));
     zd *Vh = Bt;  // V^, unit upper triangular
-    if ((e = schur_vectors(s, m, C, Vh, hn))) return e;
+    if ((e = schur_vectors(s, m, w.Cp, Vh, hn))) return e;
     // F = V^{-1} (C' V^)
-    if ((e = zgemm_batched(s, 0, m, m, m, one, w.Cp, m, 0, Vh, m, 0, zero, w.W, m, 0, 1))) return e;
+    if ((e = zgemm_batched(s, 0, m, m, m, one, Cq, m, 0, Vh, m, 0, zero, w.W, m, 0, 1, 2))) return e;
+    if ((e = tri_inverse(s, m, Vh, m, w.Cp, w.Ts))) return e;
     zd *F = V;
-    FEAST_CUDA_TRY(cudaMemcpyAsync(F, w.W, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
-    if ((e = trsm_upper_batched<zd>(s, m, m, 1, Vh, m, 0, F, m, 0))) return e;
+    if ((e = zgemm_batched(s, 0, m, m, m, one, w.Cp, m, 0, w.W, m, 0, zero, F, m, 0, 1, 1))) return e;
     k_diag_lambda<<<cdiv(m, 128), 128, 0, s>>>(m, F, alpha, beta);
     FEAST_LAUNCH_CHECK();
     FEAST_CUDA_TRY(cudaMemsetAsync(w.res, 0, 16, s));
@@ -239,8 +246,8 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     FEAST_LAUNCH_CHECK();
     // Y' = V^ + V^ G, and its residual against C'
     FEAST_CUDA_TRY(cudaMemcpyAsync(w.Yp, Vh, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
-    if ((e = zgemm_batched(s, 0, m, m, m, one, Vh, m, 0, F, m, 0, one, w.Yp, m, 0, 1))) return e;
-    if ((e = zgemm_batched(s, 0, m, m, m, one, w.Cp, m, 0, w.Yp, m, 0, zero, w.W, m, 0, 1))) return e;
+    if ((e = zgemm_batched(s, 0, m, m, m, one, Vh, m, 0, F, m, 0, one, w.Yp, m, 0, 1, 1))) return e;
+    if ((e = zgemm_batched(s, 0, m, m, m, one, Cq, m, 0, w.Yp, m, 0, zero, w.W, m, 0, 1))) return e;
     k_eig_resid<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, w.W, w.Yp, alpha, hn, w.res);
     FEAST_LAUNCH_CHECK();
     struct {
