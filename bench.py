@@ -5,8 +5,10 @@ residuals and stopping test, then the contour-integral subspace build with
 one shifted multi-right-hand-side solve per node, the node sum and the two
 orthonormalisations) on the dense prescribed-spectrum pencil
 n = 4096, m0 = 1280, 32 trapezoid nodes on |z| = 1, in the precision form
-(complex64 factors and solves with FP64-accurate refinement; --prec fp64
-for the plain FP64 path, which the precision form's line also times for
+(complex64 factors and solves on the tensor cores, the subspace build in
+defect form on the Ritz pairs, FP64-accurate tensor-core products, the
+projected problem solved warm from the second pass on; --prec fp64 for the
+plain FP64 path, which the precision form's line also times for
 comparison).  The LU set-up is timed separately.  One JSON line is printed
 by rank 0.
 
@@ -41,21 +43,23 @@ from paper_1404_1768_gb300 import inputs  # noqa: E402
 METRIC = "FEAST iters/s & eigpairs/s vs plain FP64 GPU at resid≤1e-10; % TC/HBM peak"
 # FP64 pipe of a GB300: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 dense rate measured with torch.matmul (complex128) on this machine
+FP64_MEASURED_TFLOPS = 1.05
 # FP32 pipe: 152 SMs x 128 FFMA/clock x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # TF32 dense tensor rate measured with cuBLAS (torch.matmul in tf32) on this machine
 TF32_PEAK_TFLOPS = 1027.0
 
 
-def _measured_hbm():
+def _measured(key, fallback):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
+            return float(json.load(f)[key])
     except Exception:
-        return 6800.0
+        return fallback
 
 
-HBM_PEAK_GBS = _measured_hbm()
+HBM_PEAK_GBS = _measured("hbm_gbs", 6800.0)
 
 
 def parse():
@@ -66,8 +70,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dense_n4096_m1280_q32", choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--prec", default="c64r", choices=["fp64", "c64r"],
-                    help="c64r (precision form): complex64 factors and solves on the tensor cores "
-                         "with FP64-accurate refinement; fp64: the plain FP64 path")
+                    help="c64r (precision form): complex64 factors and solves on the tensor cores, "
+                         "FP64-accurate products, defect-form subspace build; fp64: the plain FP64 path")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the plain-FP64 comparison passes of the precision form")
     ap.add_argument("--no-converge", action="store_true",
@@ -424,31 +428,89 @@ def timed_run(fg, torch, dev, stream, prob, host, kw, steps, warmup, converge, w
                 k_stop=k_stop, t_job=t_job, res=res)
 
 
-def roofline_dominant(prob, args, ph, infos):
-    """Roofline of the pass's dominant phase.  The projected eigensolve is a
-    serial chain of double-single rotations: its "achieved" counts the FP32
-    operations of the rotations it applied (estimated from the chase phases:
-    32 rotations x ~2 m0 element pairs each, ~172 FP32 operations per
-    element-pair rotation) against the FP32 pipe -- it is latency-bound, so
-    the fraction is small by nature."""
-    solve = ph["ms_solve"] - (ph["ms_refine"] if args.prec != "fp64" else 0.0)
-    phases = {"projected eigensolve (k_hqr + Hessenberg)": ph["ms_qz"], "refinement": ph["ms_refine"],
-              "subspace-build solves": solve, "orthonormalisation": ph["ms_qr"], "projection": ph["ms_proj"]}
-    dom = max(phases, key=phases.get)
-    if dom.startswith("projected") and infos and infos[0].get("qz_phases"):
-        m0 = prob.m0
+def _bf16_peak():
+    return _measured("bf16_tflops_sustained", 1753.1)
+
+
+def roofline_phases(prob, args, ph, infos):
+    """One roofline entry per phase of a pass, each for the kernel class that
+    carries the phase; "achieved" = the phase's algorithmic work / the
+    phase's CUDA-event time on the library's stream (so every other kernel
+    of the phase counts against it: a lower bound on the kernel's own rate).
+    Complex multiply-add = 8 flops."""
+    n, m0, q = prob.n, prob.m0, prob.q
+    out = {}
+    # subspace-build solves (and the band solves)
+    out["subspace-build solves"] = roofline(prob, args, ph)
+    if prob.band:
+        return out
+    warm = [i for i in infos if i.get("qz_warm")]
+    t_qz = ph["ms_qz"] / 1e3
+    if warm and len(warm) == len(infos):
+        # warm solve: FP64 products at m0 (4 with a triangular factor, half
+        # the MACs; 1 full), 2 triangular inverses (~m0^3/3 MACs each); the
+        # tail QR and the Hessenberg reduction of the tail count as time only
+        macs = (4 * 0.5 + 1 + 2.0 / 3.0) * m0 ** 3
+        flops = 8.0 * macs
+        tail = statistics.mean(i["qz_rows"] for i in warm)
+        out["projected eigensolve"] = {
+            "bound": "alu", "achieved": flops / t_qz / 1e12, "peak": FP64_MEASURED_TFLOPS, "unit": "TFLOP/s",
+            "frac": flops / t_qz / 1e12 / FP64_MEASURED_TFLOPS, "traffic": None,
+            "kernel": "k_gemm<double2> (warm Newton step: C = B~^-1 A~, C' V^, V^-1 W, V^ G, C' Y') on the FP64 "
+                      "pipe, with the tail Schur form (k_small_schur, %.0f rows) inside the same phase time" % tail,
+            "peak_source": "FP64 dense measured with cuBLAS on this pool (torch.matmul, complex128 / 4)",
+            "algorithmic_flops_per_pass": flops}
+    elif infos and infos[0].get("qz_phases"):
         qph = statistics.mean(i["qz_phases"] for i in infos)
         ops = qph * 32 * 2 * m0 * 172.0
-        t = ph["ms_qz"] / 1e3
-        return {"bound": "alu", "achieved": ops / t / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ops / t / 1e12 / FP32_PEAK_TFLOPS, "traffic": None, "phase": dom,
-                "kernel": "k_hqr (double-single multishift QR with early deflation), latency-bound rotation chain",
-                "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz",
-                "algorithmic_ops_per_pass": ops, "share_of_pass": phases[dom] / sum(phases.values())}
-    r = roofline(prob, args, ph)
-    r["phase"] = dom
-    r["share_of_pass"] = phases[dom] / sum(phases.values())
-    return r
+        out["projected eigensolve"] = {
+            "bound": "alu", "achieved": ops / t_qz / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ops / t_qz / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_hqr (double-single multishift QR with early deflation), latency-bound rotation chain",
+            "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz",
+            "algorithmic_ops_per_pass": ops}
+    if args.prec != "fp64":
+        # orthonormalisation: two Cholesky-QR-twice (U and B U1) + B U1:
+        # Gram m0^2 n and V R^-1 n m0^2 MACs per Cholesky-QR pass on the
+        # digit-sliced tensor-core GEMM (36 bf16 products of the realified
+        # operands per real product: 36 * 8 tensor flops per complex MAC)
+        tc_macs = 2 * (2 * (2 * n * m0 * m0) + m0 ** 3) + (0 if prob.kw.get("b_identity") else n * n * m0)
+        tflops = 36 * 8.0 * tc_macs
+        t_qr = ph["ms_qr"] / 1e3
+        pk = _bf16_peak()
+        out["orthonormalisation"] = {
+            "bound": "tensor", "achieved": tflops / t_qr / 1e12, "peak": pk, "unit": "TFLOP/s",
+            "frac": tflops / t_qr / 1e12 / pk, "traffic": None,
+            "kernel": "k_oz_gemm (Gram matrices, V R^-1, B U1; bf16 digit products) with the FP64 Cholesky and "
+                      "triangular inverses inside the same phase time",
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (timed inside a pass)",
+            "fp64_equivalent_tflops": 8.0 * tc_macs / t_qr / 1e12,
+            "algorithmic_flops_per_pass": tflops}
+        # projection U2^H [A U1 | B U1] + A U1 (and the Ritz products of line 6)
+        pm = n * n * m0 + 2 * m0 * n * m0 + 3 * n * m0 * m0
+        pf = 36 * 8.0 * pm
+        t_p = ph["ms_proj"] / 1e3
+        out["projection"] = {
+            "bound": "tensor", "achieved": pf / t_p / 1e12, "peak": pk, "unit": "TFLOP/s",
+            "frac": pf / t_p / 1e12 / pk, "traffic": None,
+            "kernel": "k_oz_gemm (A U1, U2^H [A U1 | B U1], U1 Y, [A U1 | B U1] Y)",
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (timed inside a pass)", "algorithmic_flops_per_pass": pf}
+    return out
+
+
+def roofline_dominant(prob, args, ph, infos):
+    """Roofline of the pass's dominant phase (largest CUDA-event time), with
+    the others listed beside it."""
+    solve = ph["ms_solve"] - (ph["ms_refine"] if args.prec != "fp64" else 0.0)
+    times = {"projected eigensolve": ph["ms_qz"], "subspace-build solves": solve,
+             "orthonormalisation": ph["ms_qr"], "projection": ph["ms_proj"]}
+    rows = roofline_phases(prob, args, ph, infos)
+    for k, r in rows.items():
+        r["phase"] = k
+        r["share_of_pass"] = times.get(k, 0.0) / sum(times.values())
+    dom = max((k for k in rows), key=lambda k: times.get(k, 0.0))
+    others = [rows[k] for k in rows if k != dom]
+    return rows[dom], others
 
 
 def roofline(prob, args, ph):
@@ -553,9 +615,7 @@ def gpu_arm(args):
 
     ph = {k: statistics.mean(i[k] for i in infos)
           for k in ("ms_proj", "ms_qz", "ms_solve", "ms_qr", "ms_refine")}
-    roof = roofline_dominant(prob, args, ph, infos)
-    # the subspace build's own kernel, and the refinement's tensor-core GEMM
-    roof_kernels = [roofline(prob, args, ph)]
+    roof, roof_kernels = roofline_dominant(prob, args, ph, infos)
     if args.prec != "fp64" and not prob.band and ph["ms_refine"] > 0:
         sweeps = statistics.mean(max(i["refine_sweeps_max"], 1) for i in infos)
         n, m0, q = prob.n, prob.m0, prob.q
@@ -566,7 +626,7 @@ def gpu_arm(args):
                              "kernel": "k_oz_gemm (refinement residual A X, B X; bf16 digit products), "
                                        "lower bound: whole refinement phase time including the complex64 "
                                        "correction solve",
-                             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"})
+                             "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (timed inside a pass)"})
 
     if rank == 0:
         cb = None
@@ -576,7 +636,7 @@ def gpu_arm(args):
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c128" if args.prec == "fp64" else "c64+c128 refine",
+            "dtype": "c128" if args.prec == "fp64" else "c64+c128",
             "data": "synthetic", "config": config_dict(prob, args, world),
             "setup_ms": setup_ms,
             "eigpairs_per_s": eig_rate, "parity": parity,
@@ -648,7 +708,7 @@ def batch_arm(args, cfg):
         line = {"metric": METRIC, "value": iters / t, "unit": "iters/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "c128" if args.prec == "fp64" else "c64+c128 refine", "data": "synthetic",
+                "dtype": "c128" if args.prec == "fp64" else "c64+c128", "data": "synthetic",
                 "config": {"workload": args.workload, "pencils": cfg["batch"],
                            "n_range": [cfg["n_lo"], cfg["n_hi"]], "q": cfg["q"],
                            "m0": "max(8, ceil(1.5 s / 8) * 8) per pencil", "precision": args.prec,
@@ -728,7 +788,7 @@ def grad_arm(args, cfg):
     if rank == 0:
         line = {"metric": METRIC, "value": 1.0 / t, "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c128" if args.prec == "fp64" else "c64+c128 refine",
+                "vs_baseline": None, "dtype": "c128" if args.prec == "fp64" else "c64+c128",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "n": n, "m0": cfg["m0"], "q": cfg["q"],
                            "loss": "sum of |lambda|^2 over the eigenvalues inside |z| < 1",

@@ -307,7 +307,8 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
                 double *hn_out);
 // Eigenvectors of the upper triangle of T (m x m), unit diagonal, by
 // back-substitution; unit 2-norm columns.
-int schur_vectors(cudaStream_t s, int m, const zd *T, zd *Y, double snorm);
+// scratch: m x m (T transposed, for contiguous row reads).
+int schur_vectors(cudaStream_t s, int m, const zd *T, zd *Y, double snorm, zd *scratch);
 int normalise_cols(cudaStream_t s, int m, zd *V);
 
 // Warm-started projected eigensolve (k_warm.cu).
@@ -406,6 +407,14 @@ size_t tc_scratch_floats(int64_t m, int64_t k, int64_t n, int batch);
 int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf *A, int64_t lda,
              int64_t sA, const cf *X, int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC,
              int batch, float *scratch, int *err);
+// The same product with A's realified planes made beforehand
+// (tc_prepare_A into tc_prepA_floats floats); scratch then only holds X's.
+size_t tc_prepA_floats(int64_t m, int64_t k, int batch);
+int tc_prepare_A(cudaStream_t s, int64_t m, int64_t k, const cf *A, int64_t lda, int64_t sA, int batch,
+                 float *Aprep);
+int tc_cgemm_prepA(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const float *Aprep, const cf *X,
+                   int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC, int batch, float *scratch,
+                   int *err);
 // FP64-accurate complex GEMM on the bf16 tensor cores by exact base-64
 // digit slicing (k_oz.cu): prepare digit planes of the left operand (rows)
 // and the right operand (columns), then C = beta C + alpha_c A B with
@@ -433,8 +442,13 @@ int adjoint_grad(cudaStream_t s, int64_t n, int cnt, const zd *V, int64_t ldv, c
 size_t getrf_tc_scratch_floats(int64_t n, int batch);
 // complex64 L U solve (permuted right-hand sides) whose off-block updates
 // run on tc_cgemm; scratch as for getrf_batched_tc with nrhs <= n.
+// cache (may be null): the factors' off-block panels prepared once by
+// trsm_tc_cache_fill (trsm_tc_cache_floats floats), so that a solve only
+// prepares its right-hand sides.
 int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, int64_t ldf, int64_t sF, cf *X,
-               int64_t ldx, int64_t sX, float *scratch, int *tc_err);
+               int64_t ldx, int64_t sX, float *scratch, int *tc_err, const float *cache = nullptr);
+size_t trsm_tc_cache_floats(int64_t n, int batch);
+int trsm_tc_cache_fill(cudaStream_t s, int64_t n, int batch, const cf *F, int64_t ldf, int64_t sF, float *cache);
 int getrf_batched_tc(cudaStream_t s, int64_t n, int batch, cf *F, int64_t ldf, int64_t sF, int *piv,
                      int *info, int *row, float *scratch, int *tc_err);
 

@@ -65,6 +65,7 @@ struct feast_ctx {
     // precision form
     cf *F32;            // q x n x n complex64 factors
     float *tcs;         // tensor-core LU operand scratch (complex64 dense)
+    float *tcA;         // the factors' off-block panels as tensor-core operands (made once)
     float4 *Ads, *Xds;  // band A and the solutions as double-single pairs (banded precision form, B = I)
     void *ozA, *ozB;    // base-64 digit planes of A and B (refinement residual)
     void *ozX;          // digit planes of the q solution blocks, n x (q m0); right-operand scratch
@@ -181,6 +182,7 @@ void carve(feast_ctx *c, Carver &cv)
     } else {
         c->F32 = cv.take<cf>(q * n * n);
         c->tcs = cv.take<float>(getrf_tc_scratch_floats((int64_t)n, (int)q));
+        c->tcA = cv.take<float>(trsm_tc_cache_floats((int64_t)n, (int)q));
         c->ozA = cv.take<char>(oz_rows_bytes((int64_t)n, (int64_t)n));
         c->ozB = c->b_identity ? nullptr : cv.take<char>(oz_rows_bytes((int64_t)n, (int64_t)n));
         c->ozX = cv.take<char>(oz_cols_bytes((int64_t)n, (int64_t)(q * m)));
@@ -389,7 +391,7 @@ int solve_refine(feast_ctx *c, const zd *BV, double tol)
     cf *rhs32 = c->Xhi;  // node 0's slot: rounded right-hand side before its gather
     if ((e = z2c(s, nm, BV, rhs32))) return e;
     if ((e = gather_rows<cf>(s, n, m, (int)q, c->perm, rhs32, n, 0, c->C32, n, nm))) return e;
-    if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout))) return e;
+    if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout, c->tcA))) return e;
     if ((e = c2z(s, all, c->C32, c->Xs))) return e;
     c->last_sweeps = 0;
     c->last_rel = -1.0;
@@ -421,7 +423,7 @@ int solve_refine(feast_ctx *c, const zd *BV, double tol)
         // correction: C_j = M32_j^{-1} R_j, X_j += C_j
         if ((e = z2c(s, all, c->R64, c->Xhi))) return e;
         if ((e = gather_rows<cf>(s, n, m, (int)q, c->perm, c->Xhi, n, nm, c->C32, n, nm))) return e;
-        if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout))) return e;
+        if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout, c->tcA))) return e;
         if ((e = add_c32(s, all, c->Xs, c->C32))) return e;
         c->last_sweeps = sweep + 1;
     }
@@ -466,7 +468,7 @@ int filter_defect(feast_ctx *c, zd *Uout)
         if ((e = gb_solve<cf>(s, n, c->kl, c->ku, (int)q, c->Fb32, c->piv, m, c->C32, n, nm))) return e;
     } else {
         if ((e = defect_rhs(s, n, (int)m, (int)q, c->perm, c->dfx, c->C32, nm))) return e;
-        if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout))) return e;
+        if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout, c->tcA))) return e;
     }
     c->last_sweeps = 0;
     c->last_rel = -1.0;
@@ -582,6 +584,7 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
         if (!c->b_identity) TRY(oz_prepare_rows(s, n, n, c->B, n, c->ozB));
         TRY(getrf_batched_tc(s, n, c->q, c->F32, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row, c->tcs,
                              &c->st->timeout));
+        TRY(trsm_tc_cache_fill(s, n, c->q, c->F32, n, n * n, c->tcA));
     }
     if (c->kind == FEAST_DENSE) TRY(zpiv_to_perm(s, n, c->q, c->piv, c->perm));
     CTRY(cudaEventRecord(c->ev[1], s));

@@ -6,7 +6,8 @@
 //
 // The Gram matrices and the products V R^{-1} are FP64-accurate GEMMs on the
 // tensor cores (k_oz.cu); the Cholesky factorisations and the triangular
-// inverses are FP64.  The first pass leaves Q_1 orthonormal to ~eps
+// inverses are FP64 (the Cholesky one cooperative launch, the inverse by
+// recursive doubling).  The first pass leaves Q_1 orthonormal to ~eps
 // cond(V)^2, the second to ~eps, while cond(V) stays below ~1e6.  Every
 // pivot is checked against its column's original norm: a pivot below
 // 1e-12 of it (cond(V) out of reach) reports failure and the caller runs
@@ -24,78 +25,6 @@ __global__ void k_diag_copy(int m, const zd *__restrict__ G, double *__restrict_
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) d[i] = G[i + (int64_t)i * m].x;
-}
-
-// Unblocked Cholesky of the diagonal block G[k0:k0+nb, k0:k0+nb] (upper
-// triangle in, R's upper triangle out).  Thread (i, k) of 32 x 32 owns
-// entry (i, k); three barriers per column.
-__global__ void __launch_bounds__(CB * CB) k_chol_diag(int m, zd *__restrict__ G, int k0, int nb,
-                                                       const double *__restrict__ d0, int *__restrict__ fail)
-{
-    __shared__ zd T[CB][CB + 1];
-    __shared__ double rinv;
-    const int i = threadIdx.x % CB, k = threadIdx.x / CB;
-    const bool live = (i < nb && k < nb);
-    if (live) T[i][k] = G[(k0 + i) + (int64_t)(k0 + k) * m];
-    __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-        if (threadIdx.x == 0) {
-            const double d = T[j][j].x;
-            const double ref = d0[k0 + j];
-            double r;
-            if (!(d > 1e-12 * ref) || !(ref > 0.0)) {
-                *fail = 1;
-                r = 1.0;
-            } else {
-                r = sqrt(d);
-            }
-            T[j][j] = zmake(r, 0.0);
-            rinv = 1.0 / r;
-        }
-        __syncthreads();
-        if (live && i == j && k > j) T[j][k] = zscale(T[j][k], rinv);
-        __syncthreads();
-        if (live && i > j && k >= i) {
-            const zd rji = T[j][i], rjk = T[j][k];
-            // T[i][k] -= conj(r_ji) r_jk
-            T[i][k] = zsub(T[i][k], zmake(rji.x * rjk.x + rji.y * rjk.y, rji.x * rjk.y - rji.y * rjk.x));
-        }
-        __syncthreads();
-    }
-    if (live && k >= i) G[(k0 + i) + (int64_t)(k0 + k) * m] = T[i][k];
-}
-
-// Row block of R right of the diagonal block: R[k0:k0+nb, c] solves
-// R_kk^H x = G[k0:k0+nb, c] (forward substitution), thread per column c.
-__global__ void k_chol_row(int m, zd *__restrict__ G, int k0, int nb)
-{
-    __shared__ zd T[CB][CB + 1];
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        const int r = e % nb, c = e / nb;
-        T[r][c] = G[(k0 + r) + (int64_t)(k0 + c) * m];
-    }
-    __syncthreads();
-    const int c = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m) return;
-    zd x[CB];
-#pragma unroll
-    for (int i = 0; i < CB; ++i)
-        if (i < nb) x[i] = G[(k0 + i) + (int64_t)c * m];
-#pragma unroll
-    for (int i = 0; i < CB; ++i) {
-        if (i >= nb) break;
-        zd acc = x[i];
-#pragma unroll
-        for (int p = 0; p < CB; ++p) {
-            if (p >= i) break;
-            const zd t = T[p][i];  // R_pi; (R^H)_ip = conj(R_pi)
-            acc = zsub(acc, zmake(t.x * x[p].x + t.y * x[p].y, t.x * x[p].y - t.y * x[p].x));
-        }
-        x[i] = zscale(acc, 1.0 / T[i][i].x);
-    }
-#pragma unroll
-    for (int i = 0; i < CB; ++i)
-        if (i < nb) G[(k0 + i) + (int64_t)c * m] = x[i];
 }
 
 // Zero the strictly lower triangle (m x m, leading dim ld).
@@ -140,32 +69,218 @@ __global__ void __launch_bounds__(CB) k_trinv_diag(int m, const zd *__restrict__
         if (i < nb) Ri[(b0 + i) + (int64_t)(b0 + k) * m] = x[i];
 }
 
+// The whole right-looking Cholesky in one cooperative launch (one CTA per
+// SM): per 32-column step, CTA 0 factors and inverts the diagonal block;
+// after a grid barrier every warp takes columns of the row panel
+// R12 = R11^{-H} G12; after another, the CTAs share the 32 x 32 tiles of the
+// trailing block's upper triangle (G22 -= R12^H R12).  FP64 throughout; the
+// launch sequence of the blocked form (three launches per step, each too
+// small to fill the GPU) becomes grid barriers.
+constexpr int PT = 256;
+__global__ void __launch_bounds__(PT, 1) k_chol_grid(int m, zd *__restrict__ G, const double *__restrict__ d0,
+                                                     int *__restrict__ fail, zd *__restrict__ rinv, GridSync gs)
+{
+    __shared__ zd T[CB][CB + 1];
+    __shared__ zd P2[CB][CB + 1];
+    __shared__ double rsh;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int gwarp = blockIdx.x * (PT / 32) + (tid >> 5), nwarp = gridDim.x * (PT / 32);
+    for (int k0 = 0; k0 < m; k0 += CB) {
+        const int nb = (m - k0) < CB ? (m - k0) : CB;
+        const int k1 = k0 + nb;
+        if (blockIdx.x == 0) {
+            for (int e = tid; e < CB * CB; e += PT) {
+                const int i = e % CB, k = e / CB;
+                T[i][k] = (i < nb && k < nb) ? G[(k0 + i) + (int64_t)(k0 + k) * m] : zmake(0.0, 0.0);
+            }
+            __syncthreads();
+            for (int j = 0; j < nb; ++j) {
+                if (tid == 0) {
+                    const double d = T[j][j].x, ref = d0[k0 + j];
+                    double r;
+                    if (!(d > 1e-12 * ref) || !(ref > 0.0)) {
+                        *fail = 1;
+                        r = 1.0;
+                    } else {
+                        r = sqrt(d);
+                    }
+                    T[j][j] = zmake(r, 0.0);
+                    rsh = 1.0 / r;
+                }
+                __syncthreads();
+                for (int k = j + 1 + tid; k < nb; k += PT) T[j][k] = zscale(T[j][k], rsh);
+                __syncthreads();
+                for (int e = tid; e < CB * CB; e += PT) {
+                    const int i = e % CB, k = e / CB;
+                    if (i > j && k >= i && k < nb) {
+                        const zd rji = T[j][i], rjk = T[j][k];
+                        T[i][k] = zsub(T[i][k], zmake(rji.x * rjk.x + rji.y * rjk.y, rji.x * rjk.y - rji.y * rjk.x));
+                    }
+                }
+                __syncthreads();
+            }
+            for (int e = tid; e < CB * CB; e += PT) {
+                const int i = e % CB, k = e / CB;
+                if (i < nb && k < nb && k >= i) G[(k0 + i) + (int64_t)(k0 + k) * m] = T[i][k];
+            }
+            // R11^{-1} (upper), column k by thread k: back-substitution
+            if (tid < nb) {
+                const int k = tid;
+                zd x[CB];
+#pragma unroll
+                for (int i = 0; i < CB; ++i) x[i] = zmake(0.0, 0.0);
+                x[k] = zmake(1.0 / T[k][k].x, 0.0);
+#pragma unroll
+                for (int i = CB - 1; i >= 0; --i) {
+                    if (i >= k) continue;
+                    zd acc = zmake(0.0, 0.0);
+#pragma unroll
+                    for (int p = 0; p < CB; ++p)
+                        if (p > i && p <= k) zfma(acc, T[i][p], x[p]);
+                    x[i] = zscale(zmake(-acc.x, -acc.y), 1.0 / T[i][i].x);
+                }
+#pragma unroll
+                for (int i = 0; i < CB; ++i) rinv[i + k * CB] = x[i];
+            }
+        }
+        if (!grid_barrier(gs)) return;
+        if (k1 >= m) break;
+        // row panel: column c by one warp, lane i -> entry i
+        for (int e = tid; e < CB * CB; e += PT) {
+            const int i = e % CB, k = e / CB;
+            T[i][k] = (i < nb && k < nb) ? rinv[i + k * CB] : zmake(0.0, 0.0);
+        }
+        __syncthreads();
+        for (int c = k1 + gwarp; c < m; c += nwarp) {
+            const zd g = (lane < nb) ? G[(k0 + lane) + (int64_t)c * m] : zmake(0.0, 0.0);
+            zd acc = zmake(0.0, 0.0);
+            for (int p = 0; p < nb; ++p) {
+                zd gp;
+                gp.x = __shfl_sync(0xffffffffu, g.x, p);
+                gp.y = __shfl_sync(0xffffffffu, g.y, p);
+                if (p <= lane) {
+                    const zd rp = T[p][lane];  // (R11^{-H})_{lane, p} = conj(rinv_{p, lane})
+                    acc = zadd(acc, zmake(rp.x * gp.x + rp.y * gp.y, rp.x * gp.y - rp.y * gp.x));
+                }
+            }
+            if (lane < nb) G[(k0 + lane) + (int64_t)c * m] = acc;
+        }
+        if (!grid_barrier(gs)) return;
+        // trailing update, upper-triangle tiles (ti <= tj) of G[k1:, k1:]
+        const int nt = (m - k1 + CB - 1) / CB;
+        const int ntiles = nt * (nt + 1) / 2;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int tj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+            while ((tj + 1) * (tj + 2) / 2 <= t) ++tj;
+            while (tj * (tj + 1) / 2 > t) --tj;
+            const int ti = t - tj * (tj + 1) / 2;
+            const int r0 = k1 + ti * CB, c0 = k1 + tj * CB;
+            __syncthreads();
+            for (int e = tid; e < CB * CB; e += PT) {
+                const int p = e % CB, a = e / CB;
+                const bool okp = p < nb;
+                T[p][a] = (okp && r0 + a < m) ? G[(k0 + p) + (int64_t)(r0 + a) * m] : zmake(0.0, 0.0);
+                P2[p][a] = (okp && c0 + a < m) ? G[(k0 + p) + (int64_t)(c0 + a) * m] : zmake(0.0, 0.0);
+            }
+            __syncthreads();
+            for (int e = tid; e < CB * CB; e += PT) {
+                const int a = e % CB, b = e / CB;
+                const int gi = r0 + a, gj = c0 + b;
+                if (gi >= m || gj >= m) continue;
+                zd acc = zmake(0.0, 0.0);
+#pragma unroll 8
+                for (int p = 0; p < CB; ++p) {
+                    const zd x = T[p][a], y = P2[p][b];  // conj(x) y
+                    acc.x += x.x * y.x + x.y * y.y;
+                    acc.y += x.x * y.y - x.y * y.x;
+                }
+                zd &gv = G[gi + (int64_t)gj * m];
+                gv = zsub(gv, acc);
+            }
+        }
+        if (!grid_barrier(gs)) return;
+    }
+}
+
+// S = phi(G - I - P) (P may be null): strictly upper part plus half the
+// (real) diagonal; zero below.
+__global__ void k_phi(int m, const zd *__restrict__ G, const zd *__restrict__ P, zd *__restrict__ S)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        zd v = zmake(0.0, 0.0);
+        if (i <= j) {
+            v = G[e];
+            if (P) v = zsub(v, P[e]);
+            if (i == j) v = zmake(0.5 * (v.x - 1.0), 0.0);
+        }
+        S[e] = v;
+    }
+}
+
+// *out = max |G_ij - delta_ij| (non-negative doubles order like their bits)
+__global__ void k_offident_max(int m, const zd *__restrict__ G, unsigned long long *__restrict__ out)
+{
+    const int64_t total = (int64_t)m * m;
+    double mx = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        zd v = G[e];
+        if (i == j) v.x -= 1.0;
+        const double a = zabs(v);
+        mx = (a > mx || !(a == a)) ? a : mx;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (!(mx == mx)) mx = 1e300;
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
 unsigned grid_for(size_t count)
 {
     const unsigned g = cdiv(count, 256);
     return g > 4096 ? 4096 : g;
 }
 
+// C = alpha op(A) B + beta C on the digit-sliced tensor-core GEMM (op(A) =
+// A^H when conj_a; C may alias A or B: their digit planes are taken first).
+int oz_mm(cudaStream_t s, const OzScratch &oz, int conj_a, int64_t M, int64_t N, int64_t K, zd alpha, const zd *A,
+          int64_t lda, const zd *B, int64_t ldb, zd beta, zd *C, int64_t ldc)
+{
+    int e;
+    if ((e = oz_prepare_rows(s, M, K, A, lda, oz.rows, conj_a))) return e;
+    if ((e = oz_prepare_cols(s, K, N, B, ldb, oz.cols))) return e;
+    return oz_gemm(s, M, N, K, oz.rows, oz.cols, alpha, nullptr, 0, beta, C, ldc, oz.err);
+}
+
 // G (m x m, Hermitian positive definite) -> R upper triangular in place,
-// G = R^H R.  Right-looking, CB-wide blocks; FP64.
-int cholesky(cudaStream_t s, int m, zd *G, double *d0, int *fail)
+// G = R^H R (upper triangle; the lower one is left as it was).  One
+// cooperative launch (k_chol_grid).  work: 2 barrier words + a 32 x 32
+// scratch.
+int cholesky(cudaStream_t s, int m, zd *G, double *d0, int *fail, unsigned *bar, zd *rinv, int *timeout)
 {
     k_diag_copy<<<cdiv(m, 128), 128, 0, s>>>(m, G, d0);
     FEAST_LAUNCH_CHECK();
-    const zd mone = zmake(-1.0, 0.0), one = zmake(1.0, 0.0);
-    for (int k0 = 0; k0 < m; k0 += CB) {
-        const int nb = (m - k0) < CB ? (m - k0) : CB;
-        k_chol_diag<<<1, CB * CB, 0, s>>>(m, G, k0, nb, d0, fail);
-        FEAST_LAUNCH_CHECK();
-        const int k1 = k0 + nb;
-        if (k1 >= m) break;
-        k_chol_row<<<cdiv(m - k1, 32), 32, 0, s>>>(m, G, k0, nb);
-        FEAST_LAUNCH_CHECK();
-        // only the upper triangle of the trailing block is ever read
-        int e = zgemm_batched(s, 1, m - k1, m - k1, nb, mone, G + k0 + (int64_t)k1 * m, m, 0,
-                              G + k0 + (int64_t)k1 * m, m, 0, one, G + k1 + (int64_t)k1 * m, m, 0, 1, 3);
-        if (e) return e;
-    }
+    int dev = 0, sms = 0, per = 0;
+    FEAST_CUDA_TRY(cudaGetDevice(&dev));
+    FEAST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_grid, PT, 0));
+    if (per < 1) return FEAST_ECUDA;
+    FEAST_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    GridSync gs{bar, bar + 1, timeout};
+    void *args[] = {&m, &G, &d0, &fail, &rinv, &gs};
+    // as many CTAs as the first trailing update has ~4 tiles for (at least
+    // 8, at most one per SM): a small factorisation leaves the rest of the
+    // GPU to other work (the pencils of a batch)
+    const int nt = (m + CB - 1) / CB;
+    int grid = nt * (nt + 1) / 8;
+    if (grid < 8) grid = 8;
+    if (grid > sms) grid = sms;
+    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_chol_grid, dim3(grid), dim3(PT), args, 0, s));
+    FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }
 
@@ -217,7 +332,8 @@ size_t tri_inverse_scratch_elems(int m)
 
 size_t zorth_chol_work_bytes(int64_t m)
 {
-    return sizeof(zd) * (3 * (size_t)m * m + tri_inverse_scratch_elems((int)m)) + sizeof(double) * (size_t)m + 64;
+    return sizeof(zd) * (4 * (size_t)m * m + tri_inverse_scratch_elems((int)m) + CB * CB) +
+           sizeof(double) * (size_t)m + 64;
 }
 
 int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr, void *work,
@@ -234,37 +350,85 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
     zd *F1 = F0 + mm;
     zd *Ti = F1 + mm;
     zd *Ts = Ti + mm;
-    double *d0 = (double *)(Ts + tri_inverse_scratch_elems((int)m));
+    zd *rinv = Ts + tri_inverse_scratch_elems((int)m);
+    zd *rinv_big = rinv + CB * CB;  // m x m
+    double *d0 = (double *)(rinv_big + mm);
     int *fail = (int *)(d0 + m);
+    unsigned *bar = (unsigned *)(fail + 2);
+    unsigned long long *emax = (unsigned long long *)(bar + 2);
     const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
     int e;
     FEAST_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), s));
-    for (int pass = 0; pass < 2; ++pass) {
-        zd *F = pass == 0 ? F0 : F1;
-        // G = V^H V
-        if ((e = oz_prepare_rows(s, m, n, V, ldv, oz.rows, 1))) return e;
-        if ((e = oz_prepare_cols(s, n, m, V, ldv, oz.cols))) return e;
-        if ((e = oz_gemm(s, m, m, n, oz.rows, oz.cols, one, nullptr, 0, zero, F, m, oz.err))) return e;
-        if ((e = cholesky(s, (int)m, F, d0, fail))) return e;
-        if (pass == 0) {
-            int hf = 0;
-            FEAST_CUDA_TRY(cudaMemcpyAsync(&hf, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
-            FEAST_CUDA_TRY(cudaStreamSynchronize(s));
-            if (hf) return FEAST_OK;  // V too ill-conditioned: caller falls back
-        }
-        k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F, m);
+    // pass 1: G = V^H V = R_a^H R_a, V <- V R_a^{-1}
+    if ((e = oz_prepare_rows(s, m, n, V, ldv, oz.rows, 1))) return e;
+    if ((e = oz_prepare_cols(s, n, m, V, ldv, oz.cols))) return e;
+    if ((e = oz_gemm(s, m, m, n, oz.rows, oz.cols, one, nullptr, 0, zero, F0, m, oz.err))) return e;
+    if ((e = cholesky(s, (int)m, F0, d0, fail, bar, rinv, oz.err))) return e;
+    {
+        int hf = 0;
+        FEAST_CUDA_TRY(cudaMemcpyAsync(&hf, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hf) return FEAST_OK;  // V too ill-conditioned: caller falls back
+    }
+    k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F0, m);
+    FEAST_LAUNCH_CHECK();
+    if ((e = tri_inverse(s, (int)m, F0, m, Ti, Ts))) return e;
+    if ((e = oz_prepare_rows(s, n, m, V, ldv, oz.rows))) return e;
+    if ((e = oz_prepare_cols(s, m, m, Ti, m, oz.cols))) return e;
+    if ((e = oz_gemm(s, n, m, m, oz.rows, oz.cols, one, nullptr, 0, zero, V, ldv, oz.err))) return e;
+    // pass 2: G = V^H V = I + E with E ~ eps cond(V)^2.  R_b = I + S with
+    // S + S^H = E - S^H S; S_0 = phi(E), S = phi(E - S_0^H S_0) (error
+    // O(|E|^3), phi = strict upper part + half the diagonal), R_b^{-1} =
+    // I - S + S^2 (error O(|E|^3)): V <- V + V (S^2 - S).  Only when
+    // max|E| <= 1e-4; otherwise a second Cholesky and inverse.
+    if ((e = oz_prepare_rows(s, m, n, V, ldv, oz.rows, 1))) return e;
+    if ((e = oz_prepare_cols(s, n, m, V, ldv, oz.cols))) return e;
+    if ((e = oz_gemm(s, m, m, n, oz.rows, oz.cols, one, nullptr, 0, zero, F1, m, oz.err))) return e;
+    FEAST_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), s));
+    k_offident_max<<<grid_for(mm), 256, 0, s>>>((int)m, F1, emax);
+    FEAST_LAUNCH_CHECK();
+    unsigned long long hb = 0;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(&hb, emax, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    double hemax;
+    memcpy(&hemax, &hb, sizeof(double));
+    if (hemax <= 1e-4) {
+        // S_0 = phi(G - I) into Ti; S = phi(G - I - S_0^H S_0) into Ts (m x m)
+        // (the products of these small corrections on the tensor cores: the
+        // digit planes scale per row and column, so their error is relative
+        // to the corrections themselves)
+        zd *S = Ti, *D = rinv_big;
+        k_phi<<<grid_for(mm), 256, 0, s>>>((int)m, F1, nullptr, S);
         FEAST_LAUNCH_CHECK();
-        // V <- V F^{-1} (the digit planes of V are taken before V is overwritten)
-        if ((e = tri_inverse(s, (int)m, F, m, Ti, Ts))) return e;
+        if ((e = oz_mm(s, oz, 1, m, m, m, one, S, m, S, m, zero, D, m))) return e;   // S_0^H S_0
+        k_phi<<<grid_for(mm), 256, 0, s>>>((int)m, F1, D, S);
+        FEAST_LAUNCH_CHECK();
+        // D = S^2 - S, then V <- V + V D
+        FEAST_CUDA_TRY(cudaMemcpyAsync(D, S, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+        if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, S, m, zmake(-1.0, 0.0), D, m))) return e;
+        if ((e = oz_mm(s, oz, 0, n, m, m, one, V, ldv, D, m, one, V, ldv))) return e;
+        // R = (I + S) R_a
+        if (R) {
+            FEAST_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(zd) * ldr, F0, sizeof(zd) * m, sizeof(zd) * m, m,
+                                             cudaMemcpyDeviceToDevice, s));
+            if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, F0, m, one, R, ldr))) return e;
+        }
+    } else {
+        if ((e = cholesky(s, (int)m, F1, d0, fail, bar, rinv, oz.err))) return e;
+        k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F1, m);
+        FEAST_LAUNCH_CHECK();
+        if ((e = tri_inverse(s, (int)m, F1, m, Ti, Ts))) return e;
         if ((e = oz_prepare_rows(s, n, m, V, ldv, oz.rows))) return e;
         if ((e = oz_prepare_cols(s, m, m, Ti, m, oz.cols))) return e;
         if ((e = oz_gemm(s, n, m, m, oz.rows, oz.cols, one, nullptr, 0, zero, V, ldv, oz.err))) return e;
+        // R = R_b R_a
+        if (R) {
+            if ((e = oz_prepare_rows(s, m, m, F1, m, oz.rows))) return e;
+            if ((e = oz_prepare_cols(s, m, m, F0, m, oz.cols))) return e;
+            if ((e = oz_gemm(s, m, m, m, oz.rows, oz.cols, one, nullptr, 0, zero, R, ldr, oz.err))) return e;
+        }
     }
-    // R = R_b R_a
     if (R) {
-        if ((e = oz_prepare_rows(s, m, m, F1, m, oz.rows))) return e;
-        if ((e = oz_prepare_cols(s, m, m, F0, m, oz.cols))) return e;
-        if ((e = oz_gemm(s, m, m, m, oz.rows, oz.cols, one, nullptr, 0, zero, R, ldr, oz.err))) return e;
         k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, R, ldr);
         FEAST_LAUNCH_CHECK();
     }

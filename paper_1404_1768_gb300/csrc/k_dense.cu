@@ -548,10 +548,48 @@ __global__ void k_gather_rows(int64_t n, int64_t nrhs, const int *perm, const T 
 // block, and one rank-LU_NBO tensor-core update (tc_cgemm) of the rows
 // beyond the block per outer step.  scratch: tc_scratch_floats(n, LU_NBO,
 // nrhs, batch) floats.
+// The off-block panels of the factors as tensor-core left operands, in the
+// order trsm_lu_tc uses them: forward (L) panels F[kend:, k0:kend] for
+// k0 = 0, LU_NBO, ...; then backward (U) panels F[0:k0, k0:kend] for k0
+// from the last block down.
+size_t trsm_tc_cache_floats(int64_t n, int batch)
+{
+    size_t tot = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += LU_NBO) {
+        const int64_t kend = (k0 + LU_NBO < n) ? k0 + LU_NBO : n;
+        if (kend < n) tot += tc_prepA_floats(n - kend, kend - k0, batch);
+        if (k0 > 0) tot += tc_prepA_floats(k0, kend - k0, batch);
+    }
+    return tot;
+}
+
+int trsm_tc_cache_fill(cudaStream_t s, int64_t n, int batch, const cf *F, int64_t ldf, int64_t sF, float *cache)
+{
+    int e;
+    size_t off = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += LU_NBO) {
+        const int64_t kend = (k0 + LU_NBO < n) ? k0 + LU_NBO : n;
+        if (kend < n) {
+            if ((e = tc_prepare_A(s, n - kend, kend - k0, F + kend + k0 * ldf, ldf, sF, batch, cache + off))) return e;
+            off += tc_prepA_floats(n - kend, kend - k0, batch);
+        }
+    }
+    const int64_t last = ((n - 1) / LU_NBO) * LU_NBO;
+    for (int64_t k0 = last; k0 >= 0; k0 -= LU_NBO) {
+        const int64_t kend = (k0 + LU_NBO < n) ? k0 + LU_NBO : n;
+        if (k0 > 0) {
+            if ((e = tc_prepare_A(s, k0, kend - k0, F + k0 * ldf, ldf, sF, batch, cache + off))) return e;
+            off += tc_prepA_floats(k0, kend - k0, batch);
+        }
+    }
+    return FEAST_OK;
+}
+
 int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, int64_t ldf, int64_t sF, cf *X,
-               int64_t ldx, int64_t sX, float *scratch, int *tc_err)
+               int64_t ldx, int64_t sX, float *scratch, int *tc_err, const float *cache)
 {
     if (n <= 0 || nrhs <= 0 || batch <= 0) return FEAST_OK;
+    size_t coff = 0;
     const cf mone = cx<cf>(-1, 0), one = cx<cf>(1, 0);
     dim3 g(cdiv(nrhs, 64), batch);
     int e;
@@ -568,10 +606,17 @@ int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, 
                                       one, X + r1, ldx, sX, batch)))
                 return e;
         }
-        if (kend < n &&
-            (e = tc_cgemm(s, n - kend, nrhs, kend - k0, mone, F + kend + k0 * ldf, ldf, sF, X + k0, ldx, sX, one,
-                          X + kend, ldx, sX, batch, scratch, tc_err)))
-            return e;
+        if (kend < n) {
+            if (cache) {
+                e = tc_cgemm_prepA(s, n - kend, nrhs, kend - k0, mone, cache + coff, X + k0, ldx, sX, one, X + kend,
+                                   ldx, sX, batch, scratch, tc_err);
+                coff += tc_prepA_floats(n - kend, kend - k0, batch);
+            } else {
+                e = tc_cgemm(s, n - kend, nrhs, kend - k0, mone, F + kend + k0 * ldf, ldf, sF, X + k0, ldx, sX, one,
+                             X + kend, ldx, sX, batch, scratch, tc_err);
+            }
+            if (e) return e;
+        }
     }
     // backward: upper U
     const int64_t last = ((n - 1) / LU_NBO) * LU_NBO;
@@ -587,10 +632,17 @@ int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, 
                                       one, X + k0, ldx, sX, batch)))
                 return e;
         }
-        if (k0 > 0 &&
-            (e = tc_cgemm(s, k0, nrhs, kend - k0, mone, F + k0 * ldf, ldf, sF, X + k0, ldx, sX, one, X, ldx, sX,
-                          batch, scratch, tc_err)))
-            return e;
+        if (k0 > 0) {
+            if (cache) {
+                e = tc_cgemm_prepA(s, k0, nrhs, kend - k0, mone, cache + coff, X + k0, ldx, sX, one, X, ldx, sX,
+                                   batch, scratch, tc_err);
+                coff += tc_prepA_floats(k0, kend - k0, batch);
+            } else {
+                e = tc_cgemm(s, k0, nrhs, kend - k0, mone, F + k0 * ldf, ldf, sF, X + k0, ldx, sX, one, X, ldx, sX,
+                             batch, scratch, tc_err);
+            }
+            if (e) return e;
+        }
     }
     return FEAST_OK;
 }

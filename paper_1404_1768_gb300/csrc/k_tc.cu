@@ -264,37 +264,50 @@ size_t tc_scratch_floats(int64_t m, int64_t k, int64_t n, int batch)
     return (size_t)batch * (2 * (size_t)mr * kr + 2 * (size_t)kr * n);
 }
 
-// C_b = beta C_b + alpha A_b X_b on tensor cores (see the file comment).
-// scratch: tc_scratch_floats(m, k, n, batch) floats (16-byte aligned).
-int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf *A, int64_t lda,
-             int64_t sA, const cf *X, int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC,
-             int batch, float *scratch, int *err)
+size_t tc_prepA_floats(int64_t m, int64_t k, int batch)
+{
+    const int64_t kr = ((2 * k + TC_BK - 1) / TC_BK) * TC_BK;
+    return (size_t)batch * 2 * (size_t)(2 * m) * kr;
+}
+
+// The left operand's realified head / tail planes (A' of the file comment),
+// made once when A is reused by many products (the LU factors' off-block
+// panels in every shifted solve).
+int tc_prepare_A(cudaStream_t s, int64_t m, int64_t k, const cf *A, int64_t lda, int64_t sA, int batch,
+                 float *Aprep)
+{
+    if (m <= 0 || k <= 0 || batch <= 0) return FEAST_OK;
+    const int64_t kr = ((2 * k + TC_BK - 1) / TC_BK) * TC_BK;
+    const int64_t mr = 2 * m;
+    float *Ah = Aprep, *At = Ah + (size_t)batch * mr * kr;
+    if (kr != 2 * k) FEAST_CUDA_TRY(cudaMemsetAsync(Ah, 0, sizeof(float) * 2 * (size_t)batch * mr * kr, s));
+    unsigned g = cdiv((size_t)m * k, 256);
+    k_realify_split<<<dim3(g > 4096 ? 4096 : g, batch), 256, 0, s>>>((int)m, (int)k, A, lda, sA, Ah, At, kr,
+                                                                     mr * kr);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
+// C_b = beta C_b + alpha A_b X_b with A given by tc_prepare_A's planes;
+// scratch: the right operand's planes (2 * batch * kr * n floats).
+int tc_cgemm_prepA(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const float *Aprep, const cf *X,
+                   int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC, int batch, float *scratch,
+                   int *err)
 {
     if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return FEAST_OK;
-    const int64_t kr = ((2 * k + TC_BK - 1) / TC_BK) * TC_BK;   // padded real K
+    const int64_t kr = ((2 * k + TC_BK - 1) / TC_BK) * TC_BK;
     const int64_t mr = 2 * m;
-    float *Ah = scratch, *At = Ah + (size_t)batch * mr * kr;
-    float *Xh = At + (size_t)batch * mr * kr, *Xt = Xh + (size_t)batch * kr * n;
-    // operand preparation: A' head/tail (pad columns, if any, zeroed first),
-    // X head/tail as K-major real columns of length kr
-    if (kr != 2 * k) {
-        FEAST_CUDA_TRY(cudaMemsetAsync(Ah, 0, sizeof(float) * 2 * (size_t)batch * mr * kr, s));
-        FEAST_CUDA_TRY(cudaMemsetAsync(Xh, 0, sizeof(float) * 2 * (size_t)batch * kr * n, s));
-    }
-    {
-        unsigned g = cdiv((size_t)m * k, 256);
-        k_realify_split<<<dim3(g > 4096 ? 4096 : g, batch), 256, 0, s>>>((int)m, (int)k, A, lda, sA, Ah, At, kr,
-                                                                         mr * kr);
-        FEAST_LAUNCH_CHECK();
-        unsigned g2 = cdiv((size_t)2 * k * n, 256);
-        k_split_tf32<<<dim3(g2 > 4096 ? 4096 : g2, batch), 256, 0, s>>>(2 * k, (int)n, (const float *)X, 2 * ldx,
-                                                                        2 * sX, Xh, Xt, kr, kr * n);
-        FEAST_LAUNCH_CHECK();
-    }
+    const float *Ah = Aprep, *At = Ah + (size_t)batch * mr * kr;
+    float *Xh = scratch, *Xt = Xh + (size_t)batch * kr * n;
+    if (kr != 2 * k) FEAST_CUDA_TRY(cudaMemsetAsync(Xh, 0, sizeof(float) * 2 * (size_t)batch * kr * n, s));
+    unsigned g2 = cdiv((size_t)2 * k * n, 256);
+    k_split_tf32<<<dim3(g2 > 4096 ? 4096 : g2, batch), 256, 0, s>>>(2 * k, (int)n, (const float *)X, 2 * ldx,
+                                                                    2 * sX, Xh, Xt, kr, kr * n);
+    FEAST_LAUNCH_CHECK();
     CUtensorMap mAh, mAt, mXh, mXt;
     int e;
-    if ((e = make_map(&mAh, Ah, kr, mr, batch, kr * 4, mr * kr * 4, TC_BM))) return e;
-    if ((e = make_map(&mAt, At, kr, mr, batch, kr * 4, mr * kr * 4, TC_BM))) return e;
+    if ((e = make_map(&mAh, (float *)Ah, kr, mr, batch, kr * 4, mr * kr * 4, TC_BM))) return e;
+    if ((e = make_map(&mAt, (float *)At, kr, mr, batch, kr * 4, mr * kr * 4, TC_BM))) return e;
     if ((e = make_map(&mXh, Xh, kr, n, batch, kr * 4, kr * n * 4, TC_BN))) return e;
     if ((e = make_map(&mXt, Xt, kr, n, batch, kr * 4, kr * n * 4, TC_BN))) return e;
     const size_t smem = (size_t)TC_STAGES * (2 * TC_BM * TC_BK * 4 + 2 * TC_BN * TC_BK * 4) + 1024;
@@ -304,6 +317,19 @@ int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf
                                               beta, err);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
+}
+
+// C_b = beta C_b + alpha A_b X_b on tensor cores (see the file comment).
+// scratch: tc_scratch_floats(m, k, n, batch) floats (16-byte aligned).
+int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf *A, int64_t lda,
+             int64_t sA, const cf *X, int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC,
+             int batch, float *scratch, int *err)
+{
+    if (m <= 0 || n <= 0 || k <= 0 || batch <= 0) return FEAST_OK;
+    int e;
+    if ((e = tc_prepare_A(s, m, k, A, lda, sA, batch, scratch))) return e;
+    return tc_cgemm_prepA(s, m, n, k, alpha, scratch, X, ldx, sX, beta, C, ldc, sC, batch,
+                          scratch + tc_prepA_floats(m, k, batch), err);
 }
 
 }  // namespace feast

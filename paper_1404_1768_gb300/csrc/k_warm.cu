@@ -233,7 +233,7 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.Cp + k + (int64_t)k * m, sizeof(zd) * m, w.S, sizeof(zd) * mb,
                                      sizeof(zd) * mb, mb, cudaMemcpyDeviceToDevice, s));
     zd *Vh = Bt;  // V^, unit upper triangular
-    if ((e = schur_vectors(s, m, w.Cp, Vh, hn))) return e;
+    if ((e = schur_vectors(s, m, w.Cp, Vh, hn, w.W))) return e;
     // F = V^{-1} (C' V^)
     if ((e = zgemm_batched(s, 0, m, m, m, one, Cq, m, 0, Vh, m, 0, zero, w.W, m, 0, 1, 2))) return e;
     if ((e = tri_inverse(s, m, Vh, m, w.Cp, w.Ts))) return e;

@@ -977,34 +977,52 @@ __global__ void __launch_bounds__(QT, 1) k_hqr(int m, float4 *H, float4 *Z, int 
 }
 
 // Eigenvector k of the upper-triangular Schur form S: (S - S_kk I) y = 0,
-// y_k = 1, back-substitution; one warp per eigenvector.  Y is m x m
-// (upper triangular on output).
-__global__ void k_schur_vectors(int m, const zd *S, int ld, zd *Y, double snorm)
+// y_k = 1, back-substitution; one warp per eigenvector.  St is S
+// transposed (St[p + i ld] = S[i, p]), so that a warp's dot product over a
+// row of S reads contiguous memory.  Y is m x m (upper triangular on output).
+__global__ void k_schur_vectors(int m, const zd *St, int ld, zd *Y, double snorm)
 {
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (k >= m) return;
     const double eps = 2.220446049250313e-16;
     const double small = eps * fmax(snorm, 1e-300);
     zd *y = Y + (int64_t)k * ld;
-    const zd lam = S[k + (int64_t)k * ld];
+    const zd lam = St[k + (int64_t)k * ld];
     for (int i = k + 1 + lane; i < m; i += 32) y[i] = zmake(0.0, 0.0);
     if (lane == 0) y[k] = zmake(1.0, 0.0);
     __syncwarp();
     for (int i = k - 1; i >= 0; --i) {
+        const zd *srow = St + (int64_t)i * ld;   // S[i, :]
         zd acc = zmake(0.0, 0.0);
-        for (int p = i + 1 + lane; p <= k; p += 32) zfma(acc, S[i + (int64_t)p * ld], y[p]);
+        for (int p = i + 1 + lane; p <= k; p += 32) zfma(acc, srow[p], y[p]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
         }
         if (lane == 0) {
-            zd d = zsub(S[i + (int64_t)i * ld], lam);
+            zd d = zsub(srow[i], lam);
             if (zabs(d) < small) d = zmake(small, 0.0);
             zd q = zdiv(acc, d);
             y[i] = zmake(-q.x, -q.y);
         }
         __syncwarp();
+    }
+}
+
+__global__ void k_transpose(int m, const zd *__restrict__ A, int ld, zd *__restrict__ At)
+{
+    __shared__ zd tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bx + tx, j = by + r;
+        if (i < m && j < m) tile[r][tx] = A[i + (int64_t)j * ld];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = by + tx, j = bx + r;
+        if (i < m && j < m) At[i + (int64_t)j * ld] = tile[tx][r];
     }
 }
 
@@ -1050,12 +1068,283 @@ __global__ void k_absmax(int64_t count, const zd *x, double *out)
 
 }  // namespace
 
+// ------------------------------------------------- small matrices: one CTA
+// Schur form of an m x m upper Hessenberg matrix, m <= SQ_MAX, by one CTA
+// with the whole matrix in shared memory: packed by columns (column j keeps
+// rows 0 .. j+2, one row below the subdiagonal for the bulge), double-single
+// entries.  Single-shift QR sweeps (Wilkinson shift, an exceptional shift
+// every 11th sweep at one eigenvalue), the standard deflation test on the
+// subdiagonal.  Each rotation G_k (rows k, k+1) is applied to the full rows
+// and the columns above and logged; the Schur vectors are the Hessenberg
+// reduction's Q times the logged rotations (k_apply_rotlog, one thread per
+// row of Q), so the serial chain here touches shared memory only.
+constexpr int SQ_MAX = 164;      // largest m: the packed matrix fills ~222 KB
+constexpr int SQ_T = 256;        // threads of the one-CTA kernel
+constexpr int SQ_LOG = 4;        // rotation log capacity: SQ_LOG * m^2 entries
+
+struct RotLog {
+    float ch, cl, srh, srl, sih, sil;  // c (real) and s (complex), double-single
+    int k;
+    int pad;
+};
+
+__host__ __device__ inline int sq_elems(int m)
+{
+    int e = 0;
+    for (int j = 0; j < m; ++j) e += (j + 3 < m) ? j + 3 : m;
+    return e;
+}
+inline size_t sq_smem_bytes(int m) { return sizeof(float4) * (size_t)sq_elems(m) + sizeof(int) * (size_t)(m + 1); }
+
+__device__ __forceinline__ cds sq_ld(const float4 *S, const int *off, int i, int j)
+{
+    const float4 v = S[off[j] + i];
+    cds r;
+    r.re = ds_make(v.x, v.y);
+    r.im = ds_make(v.z, v.w);
+    return r;
+}
+__device__ __forceinline__ void sq_st(float4 *S, const int *off, int i, int j, cds v)
+{
+    S[off[j] + i] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+}
+
+// status[0]: 0 done, 1 iteration budget spent, 2 rotation log full;
+// status[1]: rotations logged; status[2]: sweeps.  T (= H in place) is
+// written only when status[0] = 0.
+__global__ void __launch_bounds__(SQ_T, 1) k_small_schur(int m, zd *__restrict__ H, RotLog *__restrict__ log,
+                                                         int max_log, int *__restrict__ status, float tol_rel,
+                                                         float tol_abs)
+{
+    extern __shared__ float4 S[];
+    int *off = (int *)(S + sq_elems(m));
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) {
+        int o = 0;
+        for (int j = 0; j < m; ++j) {
+            off[j] = o;
+            o += (j + 3 < m) ? j + 3 : m;
+        }
+        off[m] = o;
+    }
+    __syncthreads();
+    for (int j = warp; j < m; j += SQ_T / 32) {
+        const int len = (j + 3 < m) ? j + 3 : m;
+        for (int i = lane; i < len; i += 32) {
+            cds v = cds_zero();
+            if (i <= j + 1) {
+                const zd h = H[i + (int64_t)j * m];
+                v.re = ds_from(h.x);
+                v.im = ds_from(h.y);
+            }
+            sq_st(S, off, i, j, v);
+        }
+    }
+    __syncthreads();
+    __shared__ RotDS g_sh;
+    __shared__ int ctl[2];   // lo of the active block, sweep status (0 go, 1 deflated one, 2 stop)
+    int hi = m - 1, it = 0, tot = 0, nr = 0, st = 0;
+    while (hi > 0) {
+        // warp 0: deflation scan, shift and every rotation of the sweep;
+        // the CTA applies them
+        if (warp == 0) {
+            int lo = hi;
+            while (lo > 0) {
+                const float sub = cds_absf(sq_ld(S, off, lo, lo - 1));
+                const float loc = cds_absf(sq_ld(S, off, lo - 1, lo - 1)) + cds_absf(sq_ld(S, off, lo, lo));
+                if (sub <= tol_rel * loc || sub <= tol_abs) break;
+                --lo;
+            }
+            if (lane == 0) {
+                if (lo > 0) sq_st(S, off, lo, lo - 1, cds_zero());
+                ctl[0] = lo;
+                ctl[1] = (lo == hi) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        const int lo = ctl[0];
+        const int defl = ctl[1];
+        __syncthreads();  // everyone has read ctl before warp 0 writes it again
+        if (defl == 1) {
+            --hi;
+            it = 0;
+            continue;
+        }
+        if (++tot > 30 * m) {
+            st = 1;
+            break;
+        }
+        if (nr + (hi - lo) > max_log) {
+            st = 2;
+            break;
+        }
+        ++it;
+        cds sigma = cds_zero();
+        if (warp == 0) {
+            const cds h00 = sq_ld(S, off, hi - 1, hi - 1), h01 = sq_ld(S, off, hi - 1, hi);
+            const cds h10 = sq_ld(S, off, hi, hi - 1), h11 = sq_ld(S, off, hi, hi);
+            if (it % 11 == 10) {
+                const float a = cds_absf(h10);
+                sigma = h11;
+                sigma.re = ds_add(sigma.re, ds_make(a, 0.f));
+                sigma.im = ds_add(sigma.im, ds_make(0.5f * a, 0.f));
+            } else {
+                // Wilkinson shift: eigenvalue of the trailing 2 x 2 closest to h11
+                cds half = cds_scale(cds_add(h00, h11), ds_make(0.5f, 0.f));
+                cds det = cds_sub(cds_mul(h00, h11), cds_mul(h01, h10));
+                cds disc = csqrt_ds_approx(cds_sub(cds_mul(half, half), det));
+                cds r1 = cds_add(half, disc), r2 = cds_sub(half, disc);
+                sigma = (cds_absf(cds_sub(r1, h11)) < cds_absf(cds_sub(r2, h11))) ? r1 : r2;
+            }
+        }
+        for (int k = lo; k < hi; ++k) {
+            if (warp == 0) {
+                cds x, y;
+                if (k == lo) {
+                    x = cds_sub(sq_ld(S, off, k, k), sigma);
+                    y = sq_ld(S, off, k + 1, k);
+                } else {
+                    x = sq_ld(S, off, k, k - 1);
+                    y = sq_ld(S, off, k + 1, k - 1);
+                }
+                const RotDS gr = make_rot_ds(x, y);
+                if (lane == 0) {
+                    g_sh = gr;
+                    RotLog L;
+                    L.ch = gr.c.h;
+                    L.cl = gr.c.l;
+                    L.srh = gr.s.re.h;
+                    L.srl = gr.s.re.l;
+                    L.sih = gr.s.im.h;
+                    L.sil = gr.s.im.l;
+                    L.k = k;
+                    L.pad = 0;
+                    log[nr] = L;
+                }
+            }
+            ++nr;
+            __syncthreads();
+            const RotDS gr = g_sh;
+            // rows k, k+1 (columns from the bulge's column to the right edge)
+            const int c0 = (k == lo) ? k : k - 1;
+            for (int c = c0 + t; c < m; c += SQ_T) {
+                cds a = sq_ld(S, off, k, c), b = sq_ld(S, off, k + 1, c);
+                rot_left_ds(gr, a, b);
+                sq_st(S, off, k, c, a);
+                sq_st(S, off, k + 1, c, b);
+            }
+            __syncthreads();
+            // columns k, k+1 (rows from the top to the new bulge)
+            const int r1 = (k + 2 < hi) ? k + 2 : hi;
+            for (int r = t; r <= r1; r += SQ_T) {
+                cds a = sq_ld(S, off, r, k), b = sq_ld(S, off, r, k + 1);
+                rot_right_ds(gr, a, b);
+                sq_st(S, off, r, k, a);
+                sq_st(S, off, r, k + 1, b);
+            }
+            // the annihilated bulge entry (k+1, k-1) is set to zero exactly
+            if (k > lo && t == 0) sq_st(S, off, k + 1, k - 1, cds_zero());
+            __syncthreads();
+        }
+    }
+    if (t == 0) {
+        status[0] = st;
+        status[1] = nr;
+        status[2] = tot;
+    }
+    if (st) return;
+    for (int j = warp; j < m; j += SQ_T / 32)
+        for (int i = lane; i < m; i += 32) {
+            zd v = zmake(0.0, 0.0);
+            if (i <= j) {
+                const cds c = sq_ld(S, off, i, j);
+                v = zmake((double)c.re.h + (double)c.re.l, (double)c.im.h + (double)c.im.l);
+            }
+            H[i + (int64_t)j * m] = v;
+        }
+}
+
+__global__ void k_add_stats(int *stats, int sweeps) { stats[0] += sweeps; }
+
+// Q <- Q G_1^H G_2^H ... (the logged rotations, in order): thread per row of
+// Q, the row held in shared memory (double-single) and the log streamed
+// through shared memory in chunks, the two entries a rotation touches
+// carried in registers along a sweep.  AR rows per CTA.
+constexpr int AR = 32, ALOG = 256;
+__global__ void __launch_bounds__(AR) k_apply_rotlog(int m, zd *__restrict__ Q, const RotLog *__restrict__ log,
+                                                    const int *__restrict__ status)
+{
+    extern __shared__ float4 zrow[];             // AR rows x m entries
+    __shared__ RotLog chunk[ALOG];
+    const int t = threadIdx.x;
+    const int r = blockIdx.x * AR + t;
+    const int nr = status[1];
+    float4 *zr = zrow + (size_t)t * m;
+    if (r < m)
+        for (int c = 0; c < m; ++c) {
+            const zd v = Q[r + (int64_t)c * m];
+            const ds re = ds_from(v.x), im = ds_from(v.y);
+            zr[c] = make_float4(re.h, re.l, im.h, im.l);
+        }
+    int cur = -2;
+    cds a = cds_zero(), b = cds_zero();
+    for (int e0 = 0; e0 < nr; e0 += ALOG) {
+        const int cnt = (nr - e0) < ALOG ? (nr - e0) : ALOG;
+        __syncthreads();
+        for (int e = t; e < cnt; e += AR) chunk[e] = log[e0 + e];
+        __syncthreads();
+        if (r >= m) continue;
+        for (int e = 0; e < cnt; ++e) {
+            const RotLog L = chunk[e];
+            const int k = L.k;
+            if (k != cur) {
+                if (k == cur + 1) {
+                    zr[cur] = make_float4(a.re.h, a.re.l, a.im.h, a.im.l);
+                    a = b;
+                    const float4 v = zr[k + 1];
+                    b.re = ds_make(v.x, v.y);
+                    b.im = ds_make(v.z, v.w);
+                } else {
+                    if (cur >= 0) {
+                        zr[cur] = make_float4(a.re.h, a.re.l, a.im.h, a.im.l);
+                        zr[cur + 1] = make_float4(b.re.h, b.re.l, b.im.h, b.im.l);
+                    }
+                    const float4 v0 = zr[k], v1 = zr[k + 1];
+                    a.re = ds_make(v0.x, v0.y);
+                    a.im = ds_make(v0.z, v0.w);
+                    b.re = ds_make(v1.x, v1.y);
+                    b.im = ds_make(v1.z, v1.w);
+                }
+                cur = k;
+            }
+            RotDS g;
+            g.c = ds_make(L.ch, L.cl);
+            g.s.re = ds_make(L.srh, L.srl);
+            g.s.im = ds_make(L.sih, L.sil);
+            rot_right_ds(g, a, b);
+        }
+    }
+    if (r >= m) return;
+    if (cur >= 0) {
+        zr[cur] = make_float4(a.re.h, a.re.l, a.im.h, a.im.l);
+        zr[cur + 1] = make_float4(b.re.h, b.re.l, b.im.h, b.im.l);
+    }
+    for (int c = 0; c < m; ++c) {
+        const float4 v = zr[c];
+        Q[r + (int64_t)c * m] = zmake((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+}
+
 size_t schur_large_work_bytes(int m)
 {
     // v (m) + w (m) + u (2m) complex, tau, absmax, rotations, barrier words,
-    // then the double-single copies of H and Q (m*m float4 each)
+    // then either the double-single copies of H and Q (m*m float4 each) or
+    // the one-CTA kernel's rotation log (monotone in m, so that a block of a
+    // larger problem fits the larger problem's work)
+    const size_t mq = (size_t)(m < SQ_MAX ? m : SQ_MAX);
+    const size_t big = 2 * sizeof(float4) * (size_t)m * m, small = sizeof(RotLog) * SQ_LOG * mq * mq + 16;
     return sizeof(zd) * (4 * (size_t)m) + 64 + sizeof(RotDS) * NSH * CH + sizeof(float2) * NSH +
-           sizeof(float4) * NW * NW + 16 + 64 + 256 + 2 * sizeof(float4) * (size_t)m * m;
+           sizeof(float4) * NW * NW + 16 + 64 + 256 + (big > small ? big : small);
 }
 
 size_t zeig_large_work_bytes(int m)
@@ -1109,6 +1398,30 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     FEAST_CUDA_TRY(cudaMemsetAsync(timeout, 0, sizeof(int), s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
     if (hn_out) *hn_out = hn;
+    // deflation thresholds at double-single resolution (2^-44 relative)
+    float tol_rel = 5.7e-14f, tol_abs = (float)(5.7e-14 * (hn > 0.0 ? hn : 1e-300));
+    if (m >= 2 && m <= SQ_MAX) {
+        // one CTA, the matrix in shared memory; falls through to the grid
+        // QR if its iteration budget or rotation log runs out
+        RotLog *rlog = (RotLog *)Hds;
+        int *sst = (int *)(rlog + (size_t)SQ_LOG * m * m);
+        FEAST_CUDA_TRY(allow_dyn_smem(k_small_schur));
+        k_small_schur<<<1, SQ_T, sq_smem_bytes(m), s>>>(m, C, rlog, SQ_LOG * m * m, sst, tol_rel, tol_abs);
+        FEAST_LAUNCH_CHECK();
+        int hs[3] = {0, 0, 0};
+        FEAST_CUDA_TRY(cudaMemcpyAsync(hs, sst, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs[0] == 0) {
+            FEAST_CUDA_TRY(allow_dyn_smem(k_apply_rotlog));
+            k_apply_rotlog<<<cdiv(m, AR), AR, sizeof(float4) * AR * (size_t)m, s>>>(m, Q, rlog, sst);
+            FEAST_LAUNCH_CHECK();
+            if (stats) {
+                k_add_stats<<<1, 1, 0, s>>>(stats, hs[2]);
+                FEAST_LAUNCH_CHECK();
+            }
+            return FEAST_OK;
+        }
+    }
     // QR sweeps: cooperative grid, one CTA per SM at most
     int dev = 0, sms = 0, per = 0;
     FEAST_CUDA_TRY(cudaGetDevice(&dev));
@@ -1125,8 +1438,6 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     if (grid < NSH) grid = NSH;
     if (grid > sms) grid = sms;
     GridSync gs{bar, bar + 1, timeout};
-    // deflation thresholds at double-single resolution (2^-44 relative)
-    float tol_rel = 5.7e-14f, tol_abs = (float)(5.7e-14 * (hn > 0.0 ? hn : 1e-300));
     int mm = m, ldh = m;
     const unsigned gcv = cdiv((size_t)m * m, 256) > 4096 ? 4096 : cdiv((size_t)m * m, 256);
     k_to_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, C, Hds);
@@ -1161,8 +1472,7 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     k_diag_out<<<cdiv(m, 128), 128, 0, s>>>(m, C, m, alpha, beta);
     FEAST_LAUNCH_CHECK();
     zd *Yh = Bt;  // B~ is no longer needed
-    k_schur_vectors<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, C, m, Yh, hn);
-    FEAST_LAUNCH_CHECK();
+    if ((e = schur_vectors(s, m, C, Yh, hn, V))) return e;   // V: transpose scratch until the product below
     if ((e = zgemm_batched(s, 0, m, m, m, zmake(1.0, 0.0), Q, m, 0, Yh, m, 0, zmake(0.0, 0.0), V, m, 0, 1)))
         return e;
     k_normalise_cols<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, V, m);
@@ -1171,9 +1481,11 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
 }
 
 // Launch helpers for the warm-started solve (k_warm.cu).
-int schur_vectors(cudaStream_t s, int m, const zd *T, zd *Y, double snorm)
+int schur_vectors(cudaStream_t s, int m, const zd *T, zd *Y, double snorm, zd *scratch)
 {
-    k_schur_vectors<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, T, m, Y, snorm);
+    k_transpose<<<dim3(cdiv(m, 32), cdiv(m, 32)), 256, 0, s>>>(m, T, m, scratch);
+    FEAST_LAUNCH_CHECK();
+    k_schur_vectors<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, scratch, m, Y, snorm);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }

@@ -69,12 +69,14 @@ def test_singular_matrix_reports_info():
 
 
 # ------------------------------------------------------------------ QZ
-@pytest.mark.parametrize("m", [1, 2, 5, 16, 40, 64, 65, 100, 300, 400])
+@pytest.mark.parametrize("m", [1, 2, 5, 16, 40, 64, 65, 100, 164, 165, 300, 400])
 def test_qz_matches_oracle(m):
     """Eigenvalues as multisets (the order of a QZ run is not unique) and the
     generalized eigen-residual of every returned vector.  m <= 64: one-CTA QZ;
-    65..320: one-CTA double-single QR with window solves; 400: the cooperative
-    multishift QR with early deflation."""
+    65..164: Hessenberg reduction, then one CTA with the matrix in shared
+    memory (single-shift double-single QR, logged rotations applied to the
+    Schur vectors afterwards); 165 and up: the cooperative grid QR (single
+    shift below 192 active rows, multishift with early deflation above)."""
     fg = _fg()
     rng = np.random.default_rng(30 + m)
     As = [inputs.complex_normal(rng, (m, m)) for _ in range(2)]
