@@ -90,8 +90,14 @@ typedef struct {
  *               EIGENPAIRS, line 2).  Required (no internal RNG).
  *   eps, eta  : accuracy and spurious-detection tolerances of lines 10, 13.
  *   max_iter  : line 15.
- *   prec      : FEAST_FP64 (every step in FP64) or FEAST_C64_REFINE.
- *   max_refine, refine_tol : refinement controls of FEAST_C64_REFINE.
+ *   prec      : FEAST_FP64 (every step in FP64) or FEAST_C64_REFINE
+ *               (complex64 factors and solves on the tensor cores; inside
+ *               feast_iterate line 16 runs in defect form on the Ritz pairs,
+ *               U = X rho(Lambda) + sum_j w_j M_j^{-1} (R D_j) with
+ *               R = A X - B X Lambda, which needs no refinement sweeps).
+ *   max_refine, refine_tol : refinement of each shifted solve in
+ *               feast_filter under FEAST_C64_REFINE (sweeps until the
+ *               relative residual is <= refine_tol, at most max_refine).
  *   stream    : cudaStream_t for every launch of this context.
  *   no_stop   : benchmark aid -- when non-zero, feast_iterate always performs
  *               lines 16-17 and keeps iterating after a stop has fired (the
@@ -155,8 +161,14 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
  * eigenpairs and Ritz vectors x_i = U1 y_i (line 6), residuals r_i of
  * eq. 5.1 and the selection of line 10, c(k), e(k) and the stopping tests
  * of lines 13-15 (evaluated on the device), then -- unless a test fired --
- * U = Q U1 by quadrature (line 16, eq. 4.1-4.2) and U = U1 R1, B U1 = U2 R2
- * (line 17).  Synchronises once to read c(k), e(k) and the flag.  Returns
+ * the quadrature of line 16 (eq. 4.1-4.2) and U = U1 R1, B U1 = U2 R2
+ * (line 17).  Line 16 is applied to the Ritz vectors X = U1 Y (the same
+ * subspace as U1's) when m0 >= 96 (ordered by r_i / |rho(lambda_i)|, most
+ * converged first) and always under FEAST_C64_REFINE; from the second pass
+ * on, line 6 for m0 >= 96 reuses that order (QR of the unconverged
+ * trailing block only, one FP64 Newton step for the rest, accepted against
+ * a residual bound, else the full solve).  Synchronises the stream a few
+ * times (projected-solve decisions, c(k), e(k) and the flag).  Returns
  * FEAST_EDONE if the algorithm has stopped and no_stop is 0. */
 int feast_iterate(feast_ctx *ctx, feast_iter_info *info);
 
