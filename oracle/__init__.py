@@ -14,6 +14,9 @@ the method from the paper:
 * oblique projection A~ = U2^H A U1, B~ = U2^H B U1 (eq. 3.10, GFEAST line 5);
 * complex QZ for the projected pencil (GFEAST line 6);
 * residual of eq. 5.1, selection, and the three stopping tests (lines 7-15);
+* SEARCH (Section 4.1): trace estimate of the inside count and the
+  numerical rank of the filtered block by Householder QR with column
+  pivoting (lines 1-10 of the algorithm);
 * the derivative of sum_{lambda inside} |lambda|^2 with respect to A and B
   from first-order perturbation of simple eigenvalues (left / right
   eigenvectors of the whole pencil by the own QZ) -- for the
@@ -83,6 +86,8 @@ def _load():
             lib.or_result.argtypes = [P, C.POINTER(I), P, P, P, C.POINTER(D), C.POINTER(I),
                                       C.POINTER(I)]
             lib.or_free.argtypes = [P]
+            lib.or_zqrcp.argtypes = [I, I, P, I, D, P, P, C.POINTER(I), P, I]
+            lib.or_search.argtypes = [P, P, I, D, I, D, P, C.POINTER(I), C.POINTER(I)]
             lib.or_num_threads.restype = I
             _lib = lib
     return _lib
@@ -252,6 +257,21 @@ def eig_grad_abs2(A, B, ckind: int, center: complex, a: float, b: float = 0.0):
 # --------------------------------------------------------------------------
 # GFEAST driver
 # --------------------------------------------------------------------------
+def qrcp(a, tol: float):
+    """Householder QR with column pivoting (largest remaining norm first).
+    Returns (rank, jpvt, |R_jj|, Q[:, :rank]); rank counts |R_jj| > tol |R_00|."""
+    a = _zf(a)
+    m, k = a.shape
+    jp = np.zeros(k, np.int32)
+    rd = np.zeros(k)
+    q = np.zeros((m, k), np.complex128, order="F")
+    r = C.c_int(0)
+    st = _load().or_zqrcp(m, k, _p(a), m, float(tol), _p(jp), _p(rd), C.byref(r), _p(q), m)
+    if st:
+        raise RuntimeError(f"or_zqrcp status {st}")
+    return r.value, jp, rd, q[:, :r.value].copy()
+
+
 class Feast:
     """Lines 1-17 of GFEAST with the start block Y in place of SEARCH.
 
@@ -322,6 +342,19 @@ class Feast:
         res = np.zeros(self.m0); sel = np.zeros(self.m0, np.int32)
         _load().or_get_ritz_info(self._c, _p(res), _p(sel))
         return res, sel.astype(bool)
+
+    def search(self, Ypool, alpha: float, p: int, rank_tol: float):
+        """Algorithm SEARCH (Section 4.1) with the random columns supplied by
+        Ypool (n x npool, used in order); the working width is bounded by
+        this context's m0.  Returns dict(t, s0, U1 (n x t))."""
+        Ypool = _zf(Ypool)
+        U1 = np.zeros((self.n, self.m0), np.complex128, order="F")
+        t, s0 = C.c_int(0), C.c_int(0)
+        st = _load().or_search(self._c, _p(Ypool), Ypool.shape[1], float(alpha), int(p), float(rank_tol),
+                               _p(U1), C.byref(t), C.byref(s0))
+        if st:
+            raise RuntimeError(f"or_search status {st}")
+        return dict(t=t.value, s0=s0.value, U1=U1[:, :t.value].copy())
 
     def set_U1(self, U1):
         U1 = _zf(U1)

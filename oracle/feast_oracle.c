@@ -847,3 +847,150 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* SEARCH (Algorithm "SEARCH", Section 4.1): an upper bound t of the number  */
+/* s of eigenvalues inside the contour and a basis of the filtered subspace. */
+/* ------------------------------------------------------------------------ */
+
+/* Householder QR with column pivoting (Businger-Golub): at step j the
+ * remaining column of largest norm is brought to position j.  a (m x k) is
+ * copied; on return jpvt holds the column order, rdiag |R_jj|, *rank the
+ * number of j with |R_jj| > tol |R_00|, and q (m x k) the first *rank
+ * columns of Q (the rest are left as computed). */
+int or_zqrcp(int m, int k, const zc *a, int lda, double tol, int *jpvt, double *rdiag, int *rank, zc *q, int ldq)
+{
+    if (k > m || k < 1) return OR_EINVAL;
+    zc *w = malloc(sizeof(zc) * (size_t)m * k);
+    zc *v = malloc(sizeof(zc) * (size_t)m * k);
+    if (!w || !v) { free(w); free(v); return OR_ENOMEM; }
+    for (int j = 0; j < k; ++j) {
+        jpvt[j] = j;
+        for (int i = 0; i < m; ++i) w[IDX(i, j, m)] = a[IDX(i, j, lda)];
+    }
+    memset(v, 0, sizeof(zc) * (size_t)m * k);
+    int r = k;
+    for (int j = 0; j < k; ++j) {
+        /* pivot: largest remaining norm of rows j..m-1 */
+        int best = j;
+        double bn = -1.0;
+        for (int c = j; c < k; ++c) {
+            double s = 0.0;
+            for (int i = j; i < m; ++i) s += creal(w[IDX(i, c, m)] * conj(w[IDX(i, c, m)]));
+            if (s > bn) { bn = s; best = c; }
+        }
+        if (best != j) {
+            for (int i = 0; i < m; ++i) {
+                zc t = w[IDX(i, j, m)];
+                w[IDX(i, j, m)] = w[IDX(i, best, m)];
+                w[IDX(i, best, m)] = t;
+            }
+            int tp = jpvt[j]; jpvt[j] = jpvt[best]; jpvt[best] = tp;
+        }
+        double nrm = sqrt(bn > 0.0 ? bn : 0.0);
+        rdiag[j] = nrm;   /* |R_jj| = norm of the pivot column below row j */
+        zc x0 = w[IDX(j, j, m)];
+        zc ph = (cabs(x0) > 0.0) ? x0 / cabs(x0) : 1.0;
+        zc alpha = -ph * nrm;
+        zc *vj = v + (size_t)j * m;
+        for (int i = j; i < m; ++i) vj[i] = w[IDX(i, j, m)];
+        vj[j] -= alpha;
+        double vn = 0.0;
+        for (int i = j; i < m; ++i) vn += creal(vj[i] * conj(vj[i]));
+        vn = sqrt(vn);
+        if (vn > 0.0) {
+            for (int i = j; i < m; ++i) vj[i] /= vn;
+            for (int c = j; c < k; ++c) {
+                zc s = 0.0;
+                for (int i = j; i < m; ++i) s += conj(vj[i]) * w[IDX(i, c, m)];
+                for (int i = j; i < m; ++i) w[IDX(i, c, m)] -= 2.0 * vj[i] * s;
+            }
+        }
+    }
+    for (int j = 0; j < k; ++j)
+        if (!(rdiag[j] > tol * rdiag[0])) { r = j; break; }
+    *rank = r;
+    /* Q = H_0 ... H_{k-1} [I; 0], first r columns, phases fixed so that R_jj > 0 */
+    for (int c = 0; c < r; ++c) {
+        zc *qc = q + (size_t)c * ldq;
+        for (int i = 0; i < m; ++i) qc[i] = (i == c) ? 1.0 : 0.0;
+        for (int j = k - 1; j >= 0; --j) {
+            zc *vj = v + (size_t)j * m;
+            zc s = 0.0;
+            for (int i = j; i < m; ++i) s += conj(vj[i]) * qc[i];
+            for (int i = j; i < m; ++i) qc[i] -= 2.0 * vj[i] * s;
+        }
+        zc d = w[IDX(c, c, m)];
+        zc ph = (cabs(d) > 0.0) ? d / cabs(d) : 1.0;
+        for (int i = 0; i < m; ++i) qc[i] *= ph;
+    }
+    free(w); free(v);
+    return OR_OK;
+}
+
+/* Filter w columns of Y (leading dim n) into U (leading dim n) with the
+ * context's factors: the block is zero-padded to the context's width. */
+static void filter_cols(const or_ctx *c, const zc *Y, int w, zc *U)
+{
+    int n = c->n, m = c->m0;
+    zc *V = calloc((size_t)n * m, sizeof(zc));
+    zc *F = malloc(sizeof(zc) * (size_t)n * m);
+    memcpy(V, Y, sizeof(zc) * (size_t)n * w);
+    or_filter(c, V, F);
+    memcpy(U, F, sizeof(zc) * (size_t)n * w);
+    free(V); free(F);
+}
+
+/* Algorithm SEARCH with the random columns supplied: Ypool (n x npool)
+ * gives Y_0 (its first p columns) and every augmentation (the next columns
+ * in order).  alpha > 1: growth factor; rank_tol: the numerical rank of
+ * line 9 counts |R_jj| > rank_tol |R_00|.  The working width may not exceed
+ * the context's m0.  Out: *t, *s0 (line 2's estimate), U1 (n x t,
+ * orthonormal, leading dim n).  OR_EINVAL when the pool or the width runs
+ * out before a rank deficiency shows. */
+int or_search(const or_ctx *c, const zc *Ypool, int npool, double alpha, int p, double rank_tol, zc *U1, int *t,
+              int *s0)
+{
+    int n = c->n, cap = c->m0;
+    if (p < 1 || p > cap || p > npool || !(alpha > 1.0) || !(rank_tol > 0.0)) return OR_EINVAL;
+    zc *U = malloc(sizeof(zc) * (size_t)n * cap);
+    zc *Q = malloc(sizeof(zc) * (size_t)n * cap);
+    int *jp = malloc(sizeof(int) * cap);
+    double *rd = malloc(sizeof(double) * cap);
+    int st = OR_OK;
+    /* line 1: U = Q Y_0 */
+    filter_cols(c, Ypool, p, U);
+    int used = p, have = p;
+    /* line 2: s0 = ceil(trace(Y_0^H U) / p), real part of the trace */
+    double tr = 0.0;
+    for (int j = 0; j < p; ++j)
+        for (int i = 0; i < n; ++i) tr += creal(conj(Ypool[IDX(i, j, n)]) * U[IDX(i, j, n)]);
+    *s0 = (int)ceil(tr / p);
+    int sd = *s0 > p ? *s0 : p;
+    if (sd > n) sd = n;
+    for (;;) {
+        if (sd > cap) { st = OR_EINVAL; break; }
+        if (sd > have) {   /* lines 3-5: augment with the next sd - have filtered columns */
+            if (used + (sd - have) > npool) { st = OR_EINVAL; break; }
+            filter_cols(c, Ypool + (size_t)used * n, sd - have, U + (size_t)have * n);
+            used += sd - have;
+            have = sd;
+        }
+        /* lines 9-10: rank-revealing QR */
+        int r = 0;
+        st = or_zqrcp(n, sd, U, n, rank_tol, jp, rd, &r, Q, n);
+        if (st) break;
+        memcpy(U, Q, sizeof(zc) * (size_t)n * r);
+        have = r;
+        if (r < sd) {
+            *t = r;
+            memcpy(U1, Q, sizeof(zc) * (size_t)n * r);
+            break;
+        }
+        sd = (int)ceil(alpha * r);
+        if (sd > n) sd = n;
+        if (sd == r) { st = OR_EINVAL; break; }   /* the whole space is full rank */
+    }
+    free(U); free(Q); free(jp); free(rd);
+    return st;
+}

@@ -87,6 +87,31 @@ def prescribed_pencil(n: int, m0: int, seed: int = 0, center: complex = 0j, radi
     return DensePencil(A=A, B=B, Y=Y, lam=lam, center=center, radius=radius, P=P, Q=Q)
 
 
+def gapped_pencil(n: int, m0: int, n_in: int, seed: int = 0, r_in: float = 0.7, r_out: float = 1.5,
+                  lam_radius: float = 2.0) -> DensePencil:
+    """A = P diag(lam) Q, B = P Q (as prescribed_pencil) with n_in eigenvalues
+    uniform in |z| < r_in and the rest uniform in the annulus r_out < |z| <
+    lam_radius: a clean gap around the unit circle, so that the filtered
+    block has a well-defined numerical rank (SEARCH).  Draw order: inside
+    radii/angles, outside radii/angles, G_P, G_Q, Y."""
+    rng = np.random.default_rng(seed)
+    u, v = rng.random(n_in), rng.random(n_in)
+    lam_in = r_in * np.sqrt(u) * np.exp(2j * np.pi * v)
+    k = n - n_in
+    u2, v2 = rng.random(k), rng.random(k)
+    rad = np.sqrt(r_out ** 2 + (lam_radius ** 2 - r_out ** 2) * u2)
+    lam = np.concatenate([lam_in, rad * np.exp(2j * np.pi * v2)])
+    gp = complex_normal(rng, (n, n))
+    gq = complex_normal(rng, (n, n))
+    Y = complex_normal(rng, (n, m0))
+    eye = np.eye(n, dtype=np.complex128)
+    P = eye + 0.1 * gp / math.sqrt(n)
+    Q = eye + 0.1 * gq / math.sqrt(n)
+    B = np.asfortranarray(P @ Q)
+    A = np.asfortranarray((P * lam[None, :]) @ Q)
+    return DensePencil(A=A, B=B, Y=Y, lam=lam, center=0j, radius=1.0, P=P, Q=Q)
+
+
 @dataclass
 class BandPencil:
     A_band: np.ndarray     # (kl + ku + 1) x n compact band storage, row ku + i - j
