@@ -44,7 +44,8 @@ extern "C" {
 #define FEAST_ESINGULAR  -4   /* a shifted matrix z_j B - A has an exact zero pivot */
 #define FEAST_ENONFINITE -5   /* NaN or Inf reached a residual                    */
 #define FEAST_ETIMEOUT   -6   /* a bounded device wait gave up                    */
-#define FEAST_ENOCONV    -7   /* the projected QZ hit its iteration cap, or two runs disagree */
+#define FEAST_ENOCONV    -7   /* the projected QZ hit its iteration cap, two runs disagree, or SEARCH
+                                  outgrew the workspace's width */
 #define FEAST_EDONE      -8   /* feast_iterate called after the algorithm stopped */
 
 /* ------------------------------------------------------------- problem types */
@@ -189,6 +190,26 @@ int feast_eigs(feast_ctx *ctx, int *count, double *lambda, void *X, int64_t ldx,
  * 10 weights (q), 11 residuals r_i (m0 doubles), 12 selection flags
  * (m0 int32).  All complex128 column-major with leading dim = rows. */
 int feast_get(const feast_ctx *ctx, int what, void *dst);
+
+/* SEARCH (Section 4.1, Algorithm SEARCH): an upper bound t of the number of
+ * eigenvalues inside the contour and a basis of the filtered subspace, which
+ * then replaces the start block (Algorithm 6, line 1): on success the
+ * context's width becomes t and feast_iterate starts from U1 = that basis.
+ *   Ypool   : device n x npool complex128 (leading dim n), the random columns
+ *             the algorithm draws, used in order (its first p are Y_0, each
+ *             augmentation takes the next ones); the caller draws them.
+ *   alpha   : growth factor (> 1) of line 10; p: first sample size (line 1),
+ *             1 <= p <= the context's m0.
+ *   rank_tol: the numerical rank of line 9 counts R_kk > rank_tol R_00 in the
+ *             column-pivoted factorisation (0 < rank_tol < 1; resolved down
+ *             to ~1e-7, the factorisation runs on the Gram matrix).
+ *   t, s0   : host out: the bound (width) and the trace estimate of line 2.
+ * The working width may not exceed the m0 given to feast_setup (its
+ * workspace): FEAST_ENOCONV if the search would grow beyond it, or if the
+ * filtered block stays of full rank up to n; FEAST_EINVAL if Ypool runs out.
+ * Synchronises the stream. */
+int feast_search(feast_ctx *ctx, const void *Ypool, int npool, double alpha, int p, double rank_tol, int *t,
+                 int *s0);
 
 /* The subspace build alone (GFEAST line 16, eq. 4.1-4.2) with the stored
  * factors: U = sum_j w_j (z_j B - A)^{-1} B V.  V, U: device n x m0

@@ -81,7 +81,8 @@ EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs",
            "feast_zgetrf_batched", "feast_zgetrs_batched", "feast_zqz_batched",
            "feast_zqz_work_bytes", "feast_kernel_launches", "feast_zqz_batched_noalloc",
            "feast_batch_workspace_size", "feast_solve_batch", "feast_cgemm_tc_scratch_bytes",
-           "feast_cgemm_tc", "feast_zgemm_oz_work_bytes", "feast_zgemm_oz", "feast_grad_abs2"]
+           "feast_cgemm_tc", "feast_zgemm_oz_work_bytes", "feast_zgemm_oz", "feast_grad_abs2",
+           "feast_search"]
 
 
 def lib_path() -> str:
@@ -110,6 +111,8 @@ def load(build_if_missing: bool = True):
         lib.feast_get.argtypes = [P, I, P]
         lib.feast_filter.argtypes = [P, P, P]
         lib.feast_set_subspace.argtypes = [P, P]
+        lib.feast_search.argtypes = [P, P, C.c_int, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int)]
         lib.feast_destroy.argtypes = [P]
         lib.feast_destroy.restype = None
         lib.feast_strerror.argtypes = [I]
@@ -315,6 +318,19 @@ class Feast:
         _check(self._lib.feast_grad_abs2(self._ctx, left._ctx, gA.data_ptr(), gB.data_ptr(), n, C.byref(L),
                                          C.byref(cnt)), "feast_grad_abs2")
         return L.value, gA.view(n, n).t(), gB.view(n, n).t(), cnt.value
+
+    def search(self, Ypool, alpha: float, p: int, rank_tol: float) -> dict:
+        """SEARCH (Section 4.1): Ypool (n x npool) supplies the random columns
+        in order.  On return the context's width is t and the iteration starts
+        from the search's basis.  Returns dict(t, s0)."""
+        Yd = to_device_colmajor(Ypool, self.device)
+        npool = int(np.asarray(Ypool).shape[1]) if not hasattr(Ypool, "shape") else int(Ypool.shape[1])
+        t, s0 = C.c_int(0), C.c_int(0)
+        _check(self._lib.feast_search(self._ctx, Yd.data_ptr(), npool, float(alpha), int(p), float(rank_tol),
+                                      C.byref(t), C.byref(s0)), "feast_search")
+        _torch().cuda.current_stream().synchronize()
+        self.m0 = t.value
+        return dict(t=t.value, s0=s0.value)
 
     def set_subspace(self, U1):
         Ud = to_device_colmajor(U1, self.device)

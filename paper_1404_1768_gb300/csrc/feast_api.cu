@@ -28,7 +28,8 @@ struct feast_ctx {
     int kind;
     int64_t n, kl, ku;
     int b_identity;
-    int q, m0;
+    int q, m0;          // m0: the active width (<= m0cap, the width the workspace holds)
+    int m0cap;
     feast_contour contour;
     double eps, eta;
     int max_iter, prec, no_stop, converged_only;
@@ -57,6 +58,7 @@ struct feast_ctx {
     zd *tmp;            // n x m0
     zd *orth_work;
     void *chol_work;    // Cholesky QR (dense precision form)
+    void *search_work;  // SEARCH's rank-revealing factorisation
     void *qz_work;
     void *warm_work;    // warm-started projected eigensolve (m0 >= kWarmMinM)
     int *pair_perm;     // m0: order of the Ritz pairs (most converged next pass first)
@@ -228,6 +230,7 @@ void carve(feast_ctx *c, Carver &cv)
     c->tmp = cv.take<zd>(n * m);
     c->orth_work = cv.take<zd>(zorth_work_elems((int64_t)n, (int64_t)m));
     c->qz_work = cv.take<char>(zqz_work_bytes((int)m));
+    c->search_work = cv.take<char>(rrqr_work_bytes((int64_t)n, (int)m));
     if ((int)m >= kWarmMinM) {
         c->warm_work = cv.take<char>(zeig_warm_work_bytes((int)m));
         c->pair_perm = cv.take<int>(m);
@@ -249,6 +252,7 @@ void fill_ctx_params(feast_ctx *c, const feast_pencil *p, const feast_contour *c
     c->b_identity = p->b_is_identity ? 1 : 0;
     c->q = ct->q;
     c->m0 = o->m0;
+    c->m0cap = o->m0;
     c->contour = *ct;
     if (c->contour.kind == FEAST_CIRCLE) c->contour.b = c->contour.a;
     c->eps = o->eps;
@@ -740,7 +744,7 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     // the precision form always filters the Ritz pairs (defect form); the
     // pairs are ordered when the next pass may solve warm
     c->ritz_filter = (c->prec != FEAST_FP64);
-    if (c->pair_perm && (e = order_pairs(c))) return e;
+    if (c->pair_perm && m >= kWarmMinM && (e = order_pairs(c))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[3], s));
     // lines 16-17, issued before the flag is read back so that the whole pass
     // is one stream-ordered sequence; when a stop fires the new subspace is
@@ -755,7 +759,7 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     } else if ((e = filter(c, c->ritz_filter ? c->Xr : c->U1, c->U, 1.0))) {
         return e;
     }
-    c->warm_ready = c->ritz_filter && c->pair_perm;
+    c->warm_ready = c->ritz_filter && c->pair_perm && m >= kWarmMinM;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[4], s));
     if ((e = orthonormalise(c, c->U))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[5], s));
@@ -869,6 +873,78 @@ int feast_set_subspace(feast_ctx *c, const void *U1)
     if (e) return e;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
     return orth_block(c, c->U2, c->R2);
+}
+
+int feast_search(feast_ctx *c, const void *Ypool, int npool, double alpha, int p, double rank_tol, int *t,
+                 int *s0)
+{
+    if (!c || !Ypool || !t || !s0) return FEAST_EINVAL;
+    const int64_t n = c->n;
+    const int cap = c->m0cap;
+    if (p < 1 || p > cap || npool < p || !(alpha > 1.0) || !(rank_tol > 0.0 && rank_tol < 1.0)) return FEAST_EINVAL;
+    cudaStream_t s = c->s;
+    int e;
+    c->m0 = cap;  // filter at the full width the workspace holds
+    const zd *Y = (const zd *)Ypool;
+    zd *Ucur = c->Xr, *V = c->W, *Uf = c->U;
+    const double ftol = (c->prec == FEAST_FP64) ? 1.0 : c->refine_tol;
+    // U[:, at:at+w] = Q Y[:, from:from+w] (zero-padded block through the quadrature)
+    auto filt = [&](int from, int w, int at) -> int {
+        FEAST_CUDA_TRY(cudaMemsetAsync(V, 0, sizeof(zd) * n * cap, s));
+        FEAST_CUDA_TRY(cudaMemcpyAsync(V, Y + (size_t)from * n, sizeof(zd) * n * w, cudaMemcpyDeviceToDevice, s));
+        int r = filter(c, V, Uf, ftol);
+        if (r) return r;
+        FEAST_CUDA_TRY(cudaMemcpyAsync(Ucur + (size_t)at * n, Uf, sizeof(zd) * n * w, cudaMemcpyDeviceToDevice, s));
+        return FEAST_OK;
+    };
+    // line 1
+    if ((e = filt(0, p, 0))) return e;
+    int used = p, have = p;
+    // line 2: s0 = ceil(Re trace(Y_0^H U) / p)
+    double *dtr = c->nrm2 ? c->nrm2 : (double *)c->res;
+    if ((e = trace_real(s, n, p, Y, n, Ucur, n, dtr))) return e;
+    double tr = 0.0;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(&tr, dtr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    const int est = (int)ceil(tr / p);
+    int sd = est > p ? est : p;
+    if (sd > n) sd = (int)n;
+    int r = 0;
+    for (;;) {
+        if (sd > cap) return FEAST_ENOCONV;   // the workspace's width is too small
+        if (sd > have) {                      // lines 3-5
+            if (used + (sd - have) > npool) return FEAST_EINVAL;
+            if ((e = filt(used, sd - have, have))) return e;
+            used += sd - have;
+            have = sd;
+        }
+        // lines 9-10: rank-revealing factorisation, then an orthonormal basis
+        if ((e = rrqr_basis(s, n, sd, Ucur, rank_tol, c->search_work, &c->st->timeout, &r))) return e;
+        if (r <= 0) return FEAST_ENOCONV;
+        if ((e = zorth(s, n, r, Ucur, n, c->R1, r, c->orth_work, &c->st->timeout, nullptr))) return e;
+        have = r;
+        if (r < sd) break;
+        sd = (int)ceil(alpha * r);
+        if (sd > n) sd = (int)n;
+        if (sd == r) return FEAST_ENOCONV;   // full rank over the whole space
+    }
+    // Algorithm 6, line 1: the search's basis is U1; line 2: B U1 = U2 R2
+    c->m0 = r;
+    if ((e = feast_set_subspace(c, Ucur))) return e;
+    c->k = 0;
+    c->c_prev = 0;
+    c->e_prev = 0.0;
+    c->done = 0;
+    c->cur = 0;
+    c->warm_ready = 0;
+    c->ritz_filter = 0;
+    DevStatus hs;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(&hs, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs.timeout) return FEAST_ETIMEOUT;
+    *t = r;
+    *s0 = est;
+    return FEAST_OK;
 }
 
 void feast_destroy(feast_ctx *c)
