@@ -309,6 +309,29 @@ def reference_special(args, cfg):
         return {"value": cfg["batch"] / t_all, "unit": "pencils/s", "cores": threads, "kind": "oracle",
                 "sample": f"whole oracle runs of the 2 smallest pencils ({dt:.1f} s), scaled by sum n^3 "
                           f"(x{scale:.0f}) to the {cfg['batch']} pencils"}
+    if cfg.get("search"):
+        # the complete algorithm (SEARCH then GFEAST from its basis) at n/4,
+        # width and counts scaled alike, time scaled by n^3
+        sc = cfg["search"]
+        n = cfg["n"] // 4
+        m0 = cfg["m0"] // 4
+        p = inputs.gapped_pencil(n, m0, cfg["n_in"] // 4, seed=cfg["seed"])
+        kw = dict(contour_kind=0, rule=cfg["rule"], q=cfg["q"], center=cfg["center"], a=cfg["radius"],
+                  eps=cfg["eps"])
+        pool = inputs.complex_normal(np.random.default_rng(cfg["seed"] + 1), (n, sc["pool"] // 4))
+        t0 = time.perf_counter()
+        o = oracle.Feast(p.A, p.B, p.Y, **kw)
+        r = o.search(pool, sc["alpha"], max(1, sc["p"] // 4), sc["rank_tol"])
+        o.close()
+        o2 = oracle.Feast(p.A, p.B, r["U1"], **kw)
+        o2.set_U1(r["U1"])
+        passes = len(o2.run())
+        o2.close()
+        dt = time.perf_counter() - t0
+        t_full = dt * 64.0
+        return {"value": passes / t_full, "unit": "iters/s", "cores": threads, "kind": "oracle",
+                "sample": f"oracle SEARCH + GFEAST at n={n} ({dt:.1f} s, {passes} passes) scaled by (4)^3 "
+                          f"to n={cfg['n']}"}
     # differentiation: the oracle's gradient (two whole-pencil QZs) at n/4, scaled by n^3
     n = cfg["n"] // 4
     p = inputs.prescribed_pencil(n, 8, seed=cfg["seed"])
@@ -325,7 +348,7 @@ def reference_arm(args):
     if rank != 0:
         return 0
     cfg = inputs.WORKLOADS[args.workload]
-    if "batch" in cfg or cfg.get("grad"):
+    if "batch" in cfg or cfg.get("grad") or cfg.get("search"):
         vals = [reference_special(args, cfg) for _ in range(max(1, args.steps))]
         v = statistics.median([x["value"] for x in vals])
         cb = dict(vals[-1])
@@ -804,6 +827,78 @@ def grad_arm(args, cfg):
     return 0
 
 
+def search_arm(args, cfg):
+    """The complete algorithm on a gapped pencil: SEARCH (Section 4.1) then
+    GFEAST from its basis.  A step is one whole solve (set-up, SEARCH, passes
+    until the stop fires); value = GFEAST passes / time, with SEARCH's own
+    time and its bound t beside it."""
+    import torch
+    import paper_1404_1768_gb300 as fg
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    fg.load()
+    sc = cfg["search"]
+    p = inputs.gapped_pencil(cfg["n"], cfg["m0"], cfg["n_in"], seed=cfg["seed"])
+    inside = np.abs(p.lam - cfg["center"]) < cfg["radius"]
+    pool_np = inputs.complex_normal(np.random.default_rng(cfg["seed"] + 1), (cfg["n"], sc["pool"]))
+    kw = dict(contour_kind=0, rule=cfg["rule"], q=cfg["q"], center=cfg["center"], a=cfg["radius"], eps=cfg["eps"])
+    if args.prec == "c64r":
+        kw.update(prec=fg.FEAST_C64_REFINE, refine_tol=1e-13, max_refine=4)
+
+    def solve():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = fg.Feast(p.A, p.B, p.Y, **kw)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = g.search(pool_np, sc["alpha"], sc["p"], sc["rank_tol"])
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        hist = g.run()
+        res = g.eigs(want_vectors=False)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        g.close()
+        return dict(setup=t1 - t0, search=t2 - t1, iterate=t3 - t2, passes=len(hist), t=r["t"], s0=r["s0"],
+                    res=res)
+
+    for _ in range(args.warmup):
+        solve()
+    clocks = ClockSampler(local)
+    clocks.start()
+    runs = [solve() for _ in range(args.steps)]
+    clk = clocks.stop()
+    med = sorted(runs, key=lambda x: x["setup"] + x["search"] + x["iterate"])[len(runs) // 2]
+    tot = med["setup"] + med["search"] + med["iterate"]
+    res = med["res"]
+    pool_ = list(p.lam[inside])
+    worst = 0.0
+    for x in res["lam"]:
+        j = int(np.argmin([abs(x - y) for y in pool_]))
+        worst = max(worst, abs(x - pool_[j]) / abs(pool_[j]))
+        pool_.pop(j)
+    if rank == 0:
+        line = {"metric": METRIC, "value": med["passes"] / tot, "unit": "iters/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "c128" if args.prec == "fp64" else "c64+c128", "data": "synthetic",
+                "config": {"workload": args.workload, "n": cfg["n"], "m0_workspace": cfg["m0"], "q": cfg["q"],
+                           "pencil": "A = P diag(lam) Q, B = P Q, %d eigenvalues in |z| < 0.7, the rest in "
+                                     "1.5 < |z| < 2 (seeded)" % cfg["n_in"],
+                           "search": sc, "precision": args.prec, "parallelism": "replicas1"},
+                "search_ms": 1e3 * med["search"], "setup_ms": 1e3 * med["setup"],
+                "iterate_ms": 1e3 * med["iterate"],
+                "parity": {"t": med["t"], "exact_inside": int(inside.sum()), "s0": med["s0"],
+                           "flag": res["flag"], "count": res["count"],
+                           "max_rel_eig_err_vs_exact": worst, "max_resid_eq_5_1": float(np.max(res["res"]))},
+                "e2e": {"value": med["passes"] / tot, "unit": "iters/s",
+                        "what": "host pencil -> device, set-up, SEARCH, GFEAST passes until the stop fires, "
+                                "eigenvalues back to the host"},
+                "clocks": clk, "roofline": None, "cpu_baseline": None}
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -814,6 +909,8 @@ def main():
         return batch_arm(args, inputs.WORKLOADS[args.workload])
     if inputs.WORKLOADS[args.workload].get("grad"):
         return grad_arm(args, inputs.WORKLOADS[args.workload])
+    if inputs.WORKLOADS[args.workload].get("search"):
+        return search_arm(args, inputs.WORKLOADS[args.workload])
     return gpu_arm(args)
 
 

@@ -976,17 +976,19 @@ int or_search(const or_ctx *c, const zc *Ypool, int npool, double alpha, int p, 
             used += sd - have;
             have = sd;
         }
-        /* lines 9-10: rank-revealing QR */
+        /* lines 9-10: rank-revealing QR.  On full rank the block is kept as
+         * filtered columns (the span of U1, on the scale of the columns that
+         * join it next), so that the relative rank test compares like with
+         * like */
         int r = 0;
         st = or_zqrcp(n, sd, U, n, rank_tol, jp, rd, &r, Q, n);
         if (st) break;
-        memcpy(U, Q, sizeof(zc) * (size_t)n * r);
-        have = r;
         if (r < sd) {
             *t = r;
             memcpy(U1, Q, sizeof(zc) * (size_t)n * r);
             break;
         }
+        have = sd;
         sd = (int)ceil(alpha * r);
         if (sd > n) sd = n;
         if (sd == r) { st = OR_EINVAL; break; }   /* the whole space is full rank */

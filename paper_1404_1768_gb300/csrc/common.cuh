@@ -313,11 +313,13 @@ int normalise_cols(cudaStream_t s, int m, zd *V);
 
 // SEARCH (k_search.cu): out = sum_j Re(y_j^H u_j) over p columns; the
 // rank-revealing factorisation of an n x m block U (pivoted Cholesky of
-// U^H U): *t = numerical rank at rank_tol, U[:, :t] <- U[:, piv] R_t^{-1}
-// (a basis of the selected columns' span, orthonormal to ~eps cond^2).
+// U^H U): *t = numerical rank at rank_tol, Q[:, :t] <- U[:, piv] R_t^{-1}
+// (a basis of the selected columns' span, orthonormal to ~eps cond^2; U is
+// left as it was).
 int trace_real(cudaStream_t s, int64_t n, int p, const zd *Y, int64_t ldy, const zd *U, int64_t ldu, double *out);
 size_t rrqr_work_bytes(int64_t n, int m);
-int rrqr_basis(cudaStream_t s, int64_t n, int m, zd *U, double rank_tol, void *work, int *timeout, int *t_out);
+int rrqr_basis(cudaStream_t s, int64_t n, int m, const zd *U, zd *Q, double rank_tol, void *work, int *timeout,
+               int *t_out);
 
 // Warm-started projected eigensolve (k_warm.cu).
 struct WarmParams {

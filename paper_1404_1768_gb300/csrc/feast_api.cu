@@ -918,19 +918,25 @@ int feast_search(feast_ctx *c, const void *Ypool, int npool, double alpha, int p
             used += sd - have;
             have = sd;
         }
-        // lines 9-10: rank-revealing factorisation, then an orthonormal basis
-        if ((e = rrqr_basis(s, n, sd, Ucur, rank_tol, c->search_work, &c->st->timeout, &r))) return e;
+        // lines 9-10: rank-revealing factorisation.  On full rank the block
+        // stays as filtered columns (the span of U1, on the scale of the
+        // columns that join it next, so the relative rank test compares like
+        // with like); on a deficiency its selected columns' orthonormal basis
+        // is U1.
+        if ((e = rrqr_basis(s, n, sd, Ucur, Uf, rank_tol, c->search_work, &c->st->timeout, &r))) return e;
         if (r <= 0) return FEAST_ENOCONV;
-        if ((e = zorth(s, n, r, Ucur, n, c->R1, r, c->orth_work, &c->st->timeout, nullptr))) return e;
-        have = r;
-        if (r < sd) break;
+        if (r < sd) {
+            if ((e = zorth(s, n, r, Uf, n, c->R1, r, c->orth_work, &c->st->timeout, nullptr))) return e;
+            break;
+        }
+        have = sd;
         sd = (int)ceil(alpha * r);
         if (sd > n) sd = (int)n;
         if (sd == r) return FEAST_ENOCONV;   // full rank over the whole space
     }
     // Algorithm 6, line 1: the search's basis is U1; line 2: B U1 = U2 R2
     c->m0 = r;
-    if ((e = feast_set_subspace(c, Ucur))) return e;
+    if ((e = feast_set_subspace(c, Uf))) return e;
     c->k = 0;
     c->c_prev = 0;
     c->e_prev = 0.0;

@@ -168,7 +168,8 @@ int trace_real(cudaStream_t s, int64_t n, int p, const zd *Y, int64_t ldy, const
     return FEAST_OK;
 }
 
-int rrqr_basis(cudaStream_t s, int64_t n, int m, zd *U, double rank_tol, void *work, int *timeout, int *t_out)
+int rrqr_basis(cudaStream_t s, int64_t n, int m, const zd *U, zd *Q, double rank_tol, void *work, int *timeout,
+               int *t_out)
 {
     *t_out = 0;
     if (m <= 0) return FEAST_OK;
@@ -210,11 +211,11 @@ int rrqr_basis(cudaStream_t s, int64_t n, int m, zd *U, double rank_tol, void *w
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
     *t_out = t;
     if (t <= 0) return FEAST_OK;
-    // basis: U[:, piv[:t]] R_t^{-1}, into U[:, :t]
+    // basis: U[:, piv[:t]] R_t^{-1}, into Q[:, :t]
     k_gather_pivoted<<<grid_for((size_t)n * t), 256, 0, s>>>(n, t, piv, U, n, Up, R, m, Rt);
     FEAST_LAUNCH_CHECK();
     if ((e = tri_inverse(s, t, Rt, t, G, Ts))) return e;
-    if ((e = zgemm_batched(s, 0, n, t, t, one, Up, n, 0, G, t, 0, zero, U, n, 0, 1, 2))) return e;
+    if ((e = zgemm_batched(s, 0, n, t, t, one, Up, n, 0, G, t, 0, zero, Q, n, 0, 1, 2))) return e;
     return FEAST_OK;
 }
 

@@ -214,6 +214,13 @@ WORKLOADS = {
     # m0 = 640; gradient of the sum of |lambda|^2 over the inside eigenvalues
     "grad_n2048_m640_q24": dict(n=2048, m0=640, q=24, rule=0, center=0j, radius=1.0, seed=0, eps=1e-10,
                                 grad=True),
+    # SEARCH then GFEAST (the complete algorithm): dense gapped pencil
+    # n = 2048 with 400 eigenvalues inside |z| < 0.7 and the rest beyond 1.5,
+    # 32 trapezoid nodes on |z| = 1 (the filter leaves < 3e-6 of the outside
+    # part), a workspace of width 640, first sample p = 64, growth alpha =
+    # 1.5, rank threshold 1e-4
+    "search_n2048_s400_q32": dict(n=2048, m0=640, n_in=400, q=32, rule=0, center=0j, radius=1.0, seed=0,
+                                  eps=1e-10, search=dict(p=64, alpha=1.5, rank_tol=1e-4, pool=1024)),
 }
 
 
