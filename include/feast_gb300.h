@@ -54,6 +54,15 @@ typedef enum { FEAST_CIRCLE = 0, FEAST_ELLIPSE = 1 } feast_contour_kind;
 typedef enum { FEAST_TRAPEZOID = 0, FEAST_GAUSS_LEGENDRE = 1 } feast_rule;
 typedef enum { FEAST_FP64 = 0, FEAST_C64_REFINE = 1 } feast_precision;
 
+/* Projection of line 5.  FEAST_OBLIQUE: the paper's method, test basis U2
+ * with U2 R2 = B U1 (eq. 3.10, Algorithm GFEAST).  FEAST_RAYLEIGH_RITZ: the
+ * Rayleigh-Ritz projection of Algorithm FEAST (Section 3), A~ = U1^H A U1,
+ * B~ = U1^H B U1 -- made for Hermitian A with Hermitian positive definite B,
+ * and failing where U1^H B U1 is singular (Example 3.1: every Ritz pair is
+ * then rejected; a projected pencil singular to rounding may instead end
+ * the projected solve with FEAST_ENOCONV). */
+typedef enum { FEAST_OBLIQUE = 0, FEAST_RAYLEIGH_RITZ = 1 } feast_projection;
+
 /* The regular pencil z B - A of eq. 1.1 (Section 1: only regularity is
  * required).
  *   kind = FEAST_DENSE : A, B are device n x n complex128, leading dim ld.
@@ -106,7 +115,10 @@ typedef struct {
  *   converged_only : when non-zero, line 14 (stop with flag 0 when e(k)
  *               grows) is not applied: the run ends only with flag 1 (count
  *               fixed and e(k) < eps, line 13) or -1 (max_iter).  For users
- *               that need converged pairs, e.g. the differentiation form. */
+ *               that need converged pairs, e.g. the differentiation form.
+ *   projection : FEAST_OBLIQUE (default, zero) or FEAST_RAYLEIGH_RITZ.  Under
+ *               Rayleigh-Ritz no test basis is built (feast_get's U2 / R2
+ *               are not maintained) and every projected solve starts cold. */
 typedef struct {
     int m0;
     const void *Y0;
@@ -118,6 +130,7 @@ typedef struct {
     void *stream;
     int no_stop;
     int converged_only;
+    int projection;
 } feast_options;
 
 /* Per-pass report.  flag: 2 = continue, 1 = converged (line 13), 0 = no

@@ -14,6 +14,11 @@ the method from the paper:
 * oblique projection A~ = U2^H A U1, B~ = U2^H B U1 (eq. 3.10, GFEAST line 5);
 * complex QZ for the projected pencil (GFEAST line 6);
 * residual of eq. 5.1, selection, and the three stopping tests (lines 7-15);
+* the Rayleigh-Ritz projection of Algorithm FEAST (Section 3) as an option
+  of the same driver (test space = search space), for comparison;
+* Block CIRR (Section 2.1, Algorithm Block_CIRR), the comparison method:
+  quadrature moments F_i Y, a one-sided Jacobi SVD of the moment block, the
+  Rayleigh-Ritz pencil and its eigenpairs, selected like GFEAST's;
 * SEARCH (Section 4.1): trace estimate of the inside count and the
   numerical rank of the filtered block by Householder QR with column
   pivoting (lines 1-10 of the algorithm);
@@ -87,6 +92,9 @@ def _load():
                                       C.POINTER(I)]
             lib.or_free.argtypes = [P]
             lib.or_zqrcp.argtypes = [I, I, P, I, D, P, P, C.POINTER(I), P, I]
+            lib.or_set_projection.argtypes = [P, I]
+            lib.or_zsvd_jacobi.argtypes = [I, I, P, I, P, I, P]
+            lib.or_cirr.argtypes = [P, P, I, I, C.POINTER(I), P, P, P, P]
             lib.or_search.argtypes = [P, P, I, D, I, D, P, C.POINTER(I), C.POINTER(I)]
             lib.or_num_threads.restype = I
             _lib = lib
@@ -272,6 +280,19 @@ def qrcp(a, tol: float):
     return r.value, jp, rd, q[:, :r.value].copy()
 
 
+def svd_jacobi(a):
+    """One-sided Jacobi SVD of the m x k matrix a (m >= k): returns (U, sigma),
+    the left singular vectors (m x k) and singular values, decreasing."""
+    a = _zf(a)
+    m, k = a.shape
+    u = np.zeros((m, k), np.complex128, order="F")
+    sg = np.zeros(k)
+    st = _load().or_zsvd_jacobi(m, k, _p(a), m, _p(u), m, _p(sg))
+    if st:
+        raise RuntimeError(f"or_zsvd_jacobi status {st}")
+    return u, sg
+
+
 class Feast:
     """Lines 1-17 of GFEAST with the start block Y in place of SEARCH.
 
@@ -279,7 +300,7 @@ class Feast:
     """
 
     def __init__(self, A, B, Y, *, contour_kind=0, rule=0, q=16, center=0j, a=1.0, b=0.0,
-                 eps=1e-12, eta=1e-3, max_iter=50, kind=0, kl=0, ku=0, b_identity=False):
+                 eps=1e-12, eta=1e-3, max_iter=50, kind=0, kl=0, ku=0, b_identity=False, projection=0):
         lib = _load()
         self.A = _zf(A)
         self.B = _zf(B) if B is not None else np.zeros_like(self.A)
@@ -294,6 +315,8 @@ class Feast:
                                self.m0, _p(self.Y), eps, eta, max_iter, C.byref(st))
         if not self._c:
             raise RuntimeError(f"or_setup status {st.value}")
+        if lib.or_set_projection(self._c, int(projection)):
+            raise ValueError("projection must be 0 (oblique) or 1 (Rayleigh-Ritz)")
 
     def close(self):
         if getattr(self, "_c", None):
@@ -355,6 +378,25 @@ class Feast:
         if st:
             raise RuntimeError(f"or_search status {st}")
         return dict(t=t.value, s0=s0.value, U1=U1[:, :t.value].copy())
+
+    def cirr(self, Y, g: int):
+        """Algorithm Block_CIRR (Section 2.1) on this context's pencil and
+        quadrature: Y (n x h) random columns, g moments, t = h g.  Returns
+        dict(count, lam, X, res) of the selected pairs and sigma, the
+        singular values of the moment block."""
+        Y = _zf(Y)
+        h = Y.shape[1]
+        t = h * g
+        lam = np.zeros(t, np.complex128)
+        X = np.zeros((self.n, t), np.complex128, order="F")
+        res = np.zeros(t)
+        sg = np.zeros(t)
+        cnt = C.c_int(0)
+        st = _load().or_cirr(self._c, _p(Y), h, int(g), C.byref(cnt), _p(lam), _p(X), _p(res), _p(sg))
+        if st:
+            raise RuntimeError(f"or_cirr status {st}")
+        c = cnt.value
+        return dict(count=c, lam=lam[:c].copy(), X=X[:, :c].copy(), res=res[:c].copy(), sigma=sg)
 
     def set_U1(self, U1):
         U1 = _zf(U1)

@@ -539,6 +539,7 @@ typedef struct or_ctx {
     size_t fac_stride;                   /* elements per factor                */
     int ldf;                             /* leading dim of each factor         */
     int m0;
+    int projection;                      /* 0: oblique (test space U2), 1: Rayleigh-Ritz (U1) */
     zc *U1, *U2, *R2, *AU1, *BU1;        /* n x m0, n x m0, m0 x m0, n x m0 x2 */
     double eps, eta;
     int max_iter;
@@ -718,11 +719,14 @@ int or_iterate(or_ctx *c, int *k_out, int *count, int *flag, double *err)
     int n = c->n, m = c->m0;
     size_t nm = (size_t)n * m;
     c->k += 1;
-    /* line 5: A~ = U2^H A U1, B~ = U2^H B U1 */
+    /* line 5: A~ = U2^H A U1, B~ = U2^H B U1 (oblique, eq. 3.10); with the
+     * Rayleigh-Ritz projection of Algorithm FEAST (Section 3) the test space
+     * is the search space itself: A~ = U1^H A U1, B~ = U1^H B U1 */
     pencil_apply(c, 0, m, c->U1, c->AU1);
     pencil_apply(c, 1, m, c->U1, c->BU1);
-    or_zgemm(1, m, m, n, c->U2, n, c->AU1, n, c->At, m);
-    or_zgemm(1, m, m, n, c->U2, n, c->BU1, n, c->Bt, m);
+    const zc *T = c->projection ? c->U1 : c->U2;
+    or_zgemm(1, m, m, n, T, n, c->AU1, n, c->At, m);
+    or_zgemm(1, m, m, n, T, n, c->BU1, n, c->Bt, m);
     /* line 6: projected eigenpairs, x_i = U1 y_i */
     zc *al = malloc(sizeof(zc) * m), *be = malloc(sizeof(zc) * m), *Yv = malloc(sizeof(zc) * (size_t)m * m);
     int st = or_zggev(m, c->At, m, c->Bt, m, al, be, Yv, m);
@@ -820,6 +824,14 @@ void or_get_ritz_info(const or_ctx *c, double *res, int *sel)
 {
     memcpy(res, c->res, sizeof(double) * c->m0);
     memcpy(sel, c->sel, sizeof(int) * c->m0);
+}
+/* 0: the oblique projection of GFEAST (the paper's method); 1: the
+ * Rayleigh-Ritz projection of Algorithm FEAST (comparison system). */
+int or_set_projection(or_ctx *c, int projection)
+{
+    if (projection != 0 && projection != 1) return OR_EINVAL;
+    c->projection = projection;
+    return OR_OK;
 }
 /* Replace U1 (and recompute U2 = orth(B U1)) -- lets a test drive one
  * filter step from a chosen subspace. */
@@ -994,5 +1006,154 @@ int or_search(const or_ctx *c, const zc *Ypool, int npool, double alpha, int p, 
         if (sd == r) { st = OR_EINVAL; break; }   /* the whole space is full rank */
     }
     free(U); free(Q); free(jp); free(rd);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Block CIRR (Section 2.1, Algorithm Block_CIRR) -- the comparison method   */
+/* ------------------------------------------------------------------------ */
+
+/* Singular value decomposition a = U Sigma V^H of the m x k matrix a
+ * (m >= k) by one-sided Jacobi (Hestenes): rotate column pairs of a copy W
+ * until every pair is orthogonal; then sigma_i = ||w_i|| and u_i = w_i /
+ * sigma_i, sorted by decreasing sigma.  A pair (p, q) with Gram entries
+ * alpha = ||w_p||^2, beta = ||w_q||^2, gamma = w_p^H w_q = |gamma| e^{i phi}
+ * is made orthogonal by w_q <- e^{-i phi} w_q followed by the real rotation
+ * [c s; -s c] with t = s/c the smaller root of t^2 + 2 zeta t - 1 = 0,
+ * zeta = (beta - alpha) / (2 |gamma|).  A column with sigma = 0 gives a zero
+ * u column.  Returns 0, or OR_ENOCONV after 60 sweeps. */
+int or_zsvd_jacobi(int m, int k, const zc *a, int lda, zc *u, int ldu, double *sigma)
+{
+    if (m < k || k < 0) return OR_EINVAL;
+    zc *w = malloc(sizeof(zc) * (size_t)m * k);
+    for (int j = 0; j < k; ++j) memcpy(w + (size_t)j * m, a + (size_t)j * lda, sizeof(zc) * m);
+    const double tol = 1e-15;
+    int st = OR_ENOCONV;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < k - 1; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                zc *wp = w + (size_t)p * m, *wq = w + (size_t)q * m;
+                double al = 0.0, be = 0.0;
+                zc ga = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    al += creal(wp[i] * conj(wp[i]));
+                    be += creal(wq[i] * conj(wq[i]));
+                    ga += conj(wp[i]) * wq[i];
+                }
+                double g = cabs(ga);
+                if (g == 0.0 || g <= tol * sqrt(al * be)) continue;
+                rotated = 1;
+                zc ph = conj(ga) / g;               /* e^{-i phi} */
+                double zeta = (be - al) / (2.0 * g);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                for (int i = 0; i < m; ++i) {
+                    zc x = wp[i], y = ph * wq[i];
+                    wp[i] = cs * x - sn * y;
+                    wq[i] = sn * x + cs * y;
+                }
+            }
+        if (!rotated) { st = OR_OK; break; }
+    }
+    /* sigma, u, sorted by decreasing sigma (selection sort on columns) */
+    for (int j = 0; j < k; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += creal(w[IDX(i, j, m)] * conj(w[IDX(i, j, m)]));
+        sigma[j] = sqrt(s);
+    }
+    for (int j = 0; j < k; ++j) {
+        int best = j;
+        for (int l = j + 1; l < k; ++l)
+            if (sigma[l] > sigma[best]) best = l;
+        if (best != j) {
+            double ts = sigma[j]; sigma[j] = sigma[best]; sigma[best] = ts;
+            for (int i = 0; i < m; ++i) {
+                zc tz = w[IDX(i, j, m)]; w[IDX(i, j, m)] = w[IDX(i, best, m)]; w[IDX(i, best, m)] = tz;
+            }
+        }
+        double inv = sigma[j] > 0.0 ? 1.0 / sigma[j] : 0.0;
+        for (int i = 0; i < m; ++i) u[IDX(i, j, ldu)] = w[IDX(i, j, m)] * inv;
+    }
+    free(w);
+    return st;
+}
+
+/* Algorithm Block_CIRR with the context's pencil, contour and quadrature:
+ *   1. R_i = F_i Y (i = 0..g-1), F_i the moment integrals of Section 2.1
+ *      taken by the context's quadrature; the moments are the shifted and
+ *      scaled ((z - centre) / a)^i (they span the same space as z^i,
+ *      degree by degree);
+ *   2. the SVD [R_0, ..., R_{g-1}] = U Sigma V^H (all t = h g columns of U);
+ *   3. A^ = U^H A U, B^ = U^H B U;  4. its t eigenpairs;
+ *   5. x_i = U y_i, and the selection GFEAST uses (inside the contour and
+ *      eq. 5.1 residual below eta).
+ * Y: n x h.  Outputs (each t long / n x t): lam, X, res of the selected
+ * pairs, *count of them; sigma (t) the singular values of step 2.  Returns
+ * 0, OR_EINVAL, or OR_ENOCONV (SVD or QZ). */
+int or_cirr(const or_ctx *c, const zc *Y, int h, int g, int *count, zc *lam, zc *X, double *res, double *sigma)
+{
+    int n = c->n, q = c->q;
+    *count = 0;
+    if (h < 1 || g < 1 || (size_t)h * g > (size_t)n) return OR_EINVAL;
+    int t = h * g;
+    size_t nh = (size_t)n * h, nt = (size_t)n * t;
+    zc *Xs = malloc(sizeof(zc) * nh * q), *R = calloc(nt, sizeof(zc)), *U = malloc(sizeof(zc) * nt);
+    zc *AU = malloc(sizeof(zc) * nt), *BU = malloc(sizeof(zc) * nt);
+    zc *Ah = malloc(sizeof(zc) * (size_t)t * t), *Bh = malloc(sizeof(zc) * (size_t)t * t);
+    zc *al = malloc(sizeof(zc) * t), *be = malloc(sizeof(zc) * t), *Yv = malloc(sizeof(zc) * (size_t)t * t);
+    zc *Xr = malloc(sizeof(zc) * nt), *AX = malloc(sizeof(zc) * nt), *BX = malloc(sizeof(zc) * nt);
+    /* step 1: X_j = (z_j B - A)^{-1} Y, then the weighted moments */
+#pragma omp parallel for collapse(2) schedule(dynamic)
+    for (int j = 0; j < q; ++j)
+        for (int col = 0; col < h; ++col) {
+            zc *x = Xs + ((size_t)j * h + col) * n;
+            memcpy(x, Y + (size_t)col * n, sizeof(zc) * n);
+            if (c->kind == 0)
+                or_zgetrs(n, 1, c->fac + j * c->fac_stride, c->ldf, c->piv + (size_t)j * n, x, n);
+            else
+                or_zgbtrs(n, c->kl, c->ku, 1, c->fac + j * c->fac_stride, c->ldf, c->piv + (size_t)j * n, x, n);
+        }
+    zc centre = c->cre + I * c->cim;
+    for (int i = 0; i < g; ++i)
+        for (int j = 0; j < q; ++j) {
+            zc wz = c->w[j] * cpow((c->z[j] - centre) / c->ca, (double)i);
+            for (size_t e = 0; e < nh; ++e) R[(size_t)i * nh + e] += wz * Xs[(size_t)j * nh + e];
+        }
+    /* step 2 */
+    int st = or_zsvd_jacobi(n, t, R, n, U, n, sigma);
+    if (!st) {
+        /* step 3 */
+        pencil_apply(c, 0, t, U, AU);
+        pencil_apply(c, 1, t, U, BU);
+        or_zgemm(1, t, t, n, U, n, AU, n, Ah, t);
+        or_zgemm(1, t, t, n, U, n, BU, n, Bh, t);
+        /* step 4 */
+        st = or_zggev(t, Ah, t, Bh, t, al, be, Yv, t);
+    }
+    if (!st) {
+        /* step 5 */
+        or_zgemm(0, n, t, t, U, n, Yv, t, Xr, n);
+        pencil_apply(c, 0, t, Xr, AX);
+        pencil_apply(c, 1, t, Xr, BX);
+        for (int i = 0; i < t; ++i) {
+            if (!(cabs(be[i]) > 0.0)) continue;
+            zc l = al[i] / be[i];
+            double num = 0.0, na = 0.0, nb = 0.0;
+            for (int p = 0; p < n; ++p) {
+                zc ax = AX[IDX(p, i, n)], bx = BX[IDX(p, i, n)], d = ax - l * bx;
+                num += creal(d * conj(d)); na += creal(ax * conj(ax)); nb += creal(bx * conj(bx));
+            }
+            double r = sqrt(num) / (sqrt(na) + sqrt(nb));
+            if (or_inside(c->ckind, c->cre, c->cim, c->ca, c->cb, creal(l), cimag(l)) && r < c->eta) {
+                lam[*count] = l;
+                res[*count] = r;
+                memcpy(X + (size_t)(*count) * n, Xr + (size_t)i * n, sizeof(zc) * n);
+                ++*count;
+            }
+        }
+    }
+    free(Xs); free(R); free(U); free(AU); free(BU); free(Ah); free(Bh);
+    free(al); free(be); free(Yv); free(Xr); free(AX); free(BX);
     return st;
 }

@@ -27,6 +27,7 @@ FEAST_DENSE, FEAST_BANDED = 0, 1
 FEAST_CIRCLE, FEAST_ELLIPSE = 0, 1
 FEAST_TRAPEZOID, FEAST_GAUSS_LEGENDRE = 0, 1
 FEAST_FP64, FEAST_C64_REFINE = 0, 1
+FEAST_OBLIQUE, FEAST_RAYLEIGH_RITZ = 0, 1
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESINGULAR", -5: "ENONFINITE",
           -6: "ETIMEOUT", -7: "ENOCONV", -8: "EDONE"}
 
@@ -52,7 +53,7 @@ class Options(C.Structure):
     _fields_ = [("m0", C.c_int), ("Y0", C.c_void_p), ("eps", C.c_double), ("eta", C.c_double),
                 ("max_iter", C.c_int), ("prec", C.c_int), ("max_refine", C.c_int),
                 ("refine_tol", C.c_double), ("stream", C.c_void_p), ("no_stop", C.c_int),
-                ("converged_only", C.c_int)]
+                ("converged_only", C.c_int), ("projection", C.c_int)]
 
 
 class BatchItem(C.Structure):
@@ -198,7 +199,7 @@ class Feast:
     def __init__(self, A, B, Y, *, contour_kind=0, rule=0, q=16, center=0j, a=1.0, b=0.0,
                  eps=1e-12, eta=1e-3, max_iter=50, prec=FEAST_FP64, no_stop=False, kind=0, kl=0,
                  ku=0, b_identity=False, device="cuda", stream=None, max_refine=5,
-                 refine_tol=1e-14, converged_only=False):
+                 refine_tol=1e-14, converged_only=False, projection=0):
         torch = _torch()
         self._lib = load()
         self.device = torch.device(device)
@@ -217,7 +218,8 @@ class Feast:
                                 float(b if contour_kind == FEAST_ELLIPSE else a), int(q), int(rule))
         self._opts = Options(self.m0, self._Y.data_ptr(), float(eps), float(eta), int(max_iter),
                              int(prec), int(max_refine), float(refine_tol),
-                             _stream_ptr(stream), int(bool(no_stop)), int(bool(converged_only)))
+                             _stream_ptr(stream), int(bool(no_stop)), int(bool(converged_only)),
+                             int(projection))
         nbytes = C.c_size_t(0)
         _check(self._lib.feast_workspace_size(C.byref(self._pencil), C.byref(self._contour),
                                               C.byref(self._opts), C.byref(nbytes)),

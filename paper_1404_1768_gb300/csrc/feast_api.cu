@@ -33,6 +33,7 @@ struct feast_ctx {
     feast_contour contour;
     double eps, eta;
     int max_iter, prec, no_stop, converged_only;
+    int projection;     // FEAST_OBLIQUE or FEAST_RAYLEIGH_RITZ
     cudaStream_t s;
     // device arrays
     zd *A, *B;          // n x n copies (B null when identity)
@@ -140,6 +141,7 @@ int validate(const feast_pencil *p, const feast_contour *c, const feast_options 
     if (c->kind != FEAST_CIRCLE && c->kind != FEAST_ELLIPSE) return FEAST_EINVAL;
     if (c->rule != FEAST_TRAPEZOID && c->rule != FEAST_GAUSS_LEGENDRE) return FEAST_EINVAL;
     if (o->max_iter < 1 || !(o->eta > 0.0)) return FEAST_EINVAL;
+    if (o->projection != FEAST_OBLIQUE && o->projection != FEAST_RAYLEIGH_RITZ) return FEAST_EINVAL;
     if (!p->A || (!p->B && !p->b_is_identity) || !o->Y0) return FEAST_EINVAL;
     return FEAST_OK;
 }
@@ -261,6 +263,7 @@ void fill_ctx_params(feast_ctx *c, const feast_pencil *p, const feast_contour *c
     c->prec = o->prec;
     c->no_stop = o->no_stop;
     c->converged_only = o->converged_only;
+    c->projection = o->projection;
     c->s = (cudaStream_t)o->stream;
     c->max_refine = o->max_refine;
     c->refine_tol = o->refine_tol;
@@ -495,7 +498,8 @@ int orth_block(feast_ctx *c, zd *V, zd *R)
     return zorth(c->s, n, m, V, n, R, m, c->orth_work, &c->st->timeout, orth_oz(c));
 }
 
-// U1 R1 = U ; W[:, m0:] = B U1 ; U2 R2 = B U1   (GFEAST lines 2, 17)
+// U1 R1 = U ; W[:, m0:] = B U1 ; U2 R2 = B U1   (GFEAST lines 2, 17; the
+// Rayleigh-Ritz projection has no test basis to build)
 int orthonormalise(feast_ctx *c, const zd *Usrc)
 {
     const int64_t n = c->n, m = c->m0;
@@ -505,6 +509,7 @@ int orthonormalise(feast_ctx *c, const zd *Usrc)
     if ((e = orth_block(c, c->U1, c->R1))) return e;
     zd *BU1 = c->W + n * m;
     if ((e = apply_B(c, c->U1, BU1, m))) return e;
+    if (c->projection == FEAST_RAYLEIGH_RITZ) return FEAST_OK;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
     return orth_block(c, c->U2, c->R2);
 }
@@ -674,6 +679,24 @@ static int order_pairs(feast_ctx *c)
     return FEAST_OK;
 }
 
+// Rayleigh-Ritz: B~ = U1^H B U1 is a full matrix, while both projected
+// solvers take B~ upper triangular (as the oblique projection's R2).  With
+// B~ = Q_b R_b the pencil (Q_b^H A~, R_b) has the same eigenpairs.  Works on
+// c->Q = [A~ | B~]; R2 (no test basis under Rayleigh-Ritz) holds R_b.
+int triangularise_bt(feast_ctx *c)
+{
+    const int64_t m = c->m0;
+    cudaStream_t s = c->s;
+    zd *At = c->Q, *Bt = c->Q + m * m;
+    int e;
+    if ((e = zorth(s, m, m, Bt, m, c->R2, m, c->orth_work, &c->st->timeout, nullptr))) return e;
+    // A~ <- Q_b^H A~ (through the residual buffer as scratch: m <= n)
+    if ((e = zgemm_batched(s, 1, m, m, m, kOne, Bt, m, 0, c->P, m, 0, kZero, c->AXBX, m, 0, 1))) return e;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(At, c->AXBX, sizeof(zd) * m * m, cudaMemcpyDeviceToDevice, s));
+    FEAST_CUDA_TRY(cudaMemcpyAsync(Bt, c->R2, sizeof(zd) * m * m, cudaMemcpyDeviceToDevice, s));
+    return FEAST_OK;
+}
+
 int feast_iterate(feast_ctx *c, feast_iter_info *info)
 {
     if (!c) return FEAST_EINVAL;
@@ -683,12 +706,16 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     int e;
     c->k += 1;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[0], s));
-    // line 5: [A~ | B~] = U2^H [A U1 | B U1]; B U1 is already in W[:, m0:]
+    // line 5: [A~ | B~] = T^H [A U1 | B U1] with the test basis T = U2
+    // (oblique, eq. 3.10) or T = U1 (Rayleigh-Ritz, Algorithm FEAST); B U1 is
+    // already in W[:, m0:]
+    const bool rr = c->projection == FEAST_RAYLEIGH_RITZ;
+    const zd *Tb = rr ? c->U1 : c->U2;
     if ((e = apply_A(c, c->U1, c->W, m))) return e;
     if (use_oz(c)) {
-        if ((e = oz_prepare_rows(s, m, n, c->U2, n, c->ozR, 1))) return e;
+        if ((e = oz_prepare_rows(s, m, n, Tb, n, c->ozR, 1))) return e;
         if ((e = oz_mul(c, c->ozR, m, n, c->W, n, 2 * m, c->P, m))) return e;
-    } else if ((e = zgemm_batched(s, 1, m, 2 * m, n, kOne, c->U2, n, 0, c->W, n, 0, kZero, c->P, m, 0, 1))) {
+    } else if ((e = zgemm_batched(s, 1, m, 2 * m, n, kOne, Tb, n, 0, c->W, n, 0, kZero, c->P, m, 0, 1))) {
         return e;
     }
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[1], s));
@@ -715,6 +742,7 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     }
     if (!c->last_warm.accepted) {
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
+        if (rr && (e = triangularise_bt(c))) return e;
         if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
                              c->qz_work, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps))) return e;
     }
@@ -744,7 +772,7 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     // the precision form always filters the Ritz pairs (defect form); the
     // pairs are ordered when the next pass may solve warm
     c->ritz_filter = (c->prec != FEAST_FP64);
-    if (c->pair_perm && m >= kWarmMinM && (e = order_pairs(c))) return e;
+    if (!rr && c->pair_perm && m >= kWarmMinM && (e = order_pairs(c))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[3], s));
     // lines 16-17, issued before the flag is read back so that the whole pass
     // is one stream-ordered sequence; when a stop fires the new subspace is
@@ -759,7 +787,8 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     } else if ((e = filter(c, c->ritz_filter ? c->Xr : c->U1, c->U, 1.0))) {
         return e;
     }
-    c->warm_ready = c->ritz_filter && c->pair_perm && m >= kWarmMinM;
+    // (the warm solve relies on B~ = R2 being upper triangular: oblique only)
+    c->warm_ready = !rr && c->ritz_filter && c->pair_perm && m >= kWarmMinM;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[4], s));
     if ((e = orthonormalise(c, c->U))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[5], s));
@@ -871,6 +900,7 @@ int feast_set_subspace(feast_ctx *c, const void *U1)
     zd *BU1 = c->W + n * m;
     int e = apply_B(c, c->U1, BU1, m);
     if (e) return e;
+    if (c->projection == FEAST_RAYLEIGH_RITZ) return FEAST_OK;
     FEAST_CUDA_TRY(cudaMemcpyAsync(c->U2, BU1, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
     return orth_block(c, c->U2, c->R2);
 }

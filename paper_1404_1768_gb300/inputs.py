@@ -13,6 +13,8 @@ here; these generators stand in for them with the same kind of structure:
   Dirichlet, 5-point central differences on an nx x nx grid (B = I), in
   compact band storage; its spectrum has a closed form.
 * ``ragged_batch``: many prescribed-spectrum pencils of uneven size.
+* ``hermitian_pencil``: A Hermitian, B Hermitian positive definite, real
+  prescribed spectrum (the Rayleigh-Ritz comparison case).
 
 Random draws use ``numpy.random.default_rng(seed)`` (PCG64) in a fixed
 order: lam (u then v, then any re-draws), G_P, G_Q, Y.  With seed 0 and
@@ -110,6 +112,33 @@ def gapped_pencil(n: int, m0: int, n_in: int, seed: int = 0, r_in: float = 0.7, 
     B = np.asfortranarray(P @ Q)
     A = np.asfortranarray((P * lam[None, :]) @ Q)
     return DensePencil(A=A, B=B, Y=Y, lam=lam, center=0j, radius=1.0, P=P, Q=Q)
+
+
+def hermitian_pencil(n: int, m0: int, seed: int = 0, lam_radius: float = 2.0,
+                     guard: float = 1e-3) -> DensePencil:
+    """A Hermitian / B Hermitian positive definite: A = Q^H diag(lam) Q,
+    B = Q^H Q with Q = I + 0.1 G / sqrt(n) and lam real, uniform in
+    (-lam_radius, lam_radius) (values within ``guard`` of +-1 re-drawn).  It is
+    the prescribed pencil with P = Q^H, so the eigenvalues are ``lam`` and the
+    eigenvectors Q^{-1} e_i -- the class of pencils Algorithm FEAST's
+    Rayleigh-Ritz projection is made for.  Draw order: lam (then re-draws),
+    G_Q, Y."""
+    rng = np.random.default_rng(seed)
+    lam = lam_radius * (2.0 * rng.random(n) - 1.0)
+    for _ in range(1000):
+        bad = np.abs(np.abs(lam) - 1.0) < guard
+        if not bad.any():
+            break
+        lam[bad] = lam_radius * (2.0 * rng.random(int(bad.sum())) - 1.0)
+    gq = complex_normal(rng, (n, n))
+    Y = complex_normal(rng, (n, m0))
+    Q = np.eye(n, dtype=np.complex128) + 0.1 * gq / math.sqrt(n)
+    P = np.ascontiguousarray(Q.conj().T)
+    B = np.asfortranarray(P @ Q)
+    A = np.asfortranarray((P * lam[None, :]) @ Q)
+    A = np.asfortranarray(0.5 * (A + A.conj().T))   # exactly Hermitian in floating point
+    B = np.asfortranarray(0.5 * (B + B.conj().T))
+    return DensePencil(A=A, B=B, Y=Y, lam=lam.astype(np.complex128), center=0j, radius=1.0, P=P, Q=Q)
 
 
 @dataclass
