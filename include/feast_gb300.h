@@ -204,6 +204,25 @@ int feast_eigs(feast_ctx *ctx, int *count, double *lambda, void *X, int64_t ldx,
  * (m0 int32).  All complex128 column-major with leading dim = rows. */
 int feast_get(const feast_ctx *ctx, int what, void *dst);
 
+/* Block CIRR (Section 2.1, Algorithm Block_CIRR), the comparison method the
+ * paper measures GFEAST against, on this context's pencil, contour and
+ * factors (the context must have been set up with FEAST_RAYLEIGH_RITZ):
+ *   1. R_i = F_i Y, i = 0..g-1, by the context's quadrature, in the shifted
+ *      and scaled form sum_j w_j ((z_j - centre) / max(a, b))^i
+ *      (z_j B - A)^{-1} Y (degree by degree the span of the z^i moments);
+ *   2. an orthonormal basis U1 of [R_0, ..., R_{g-1}] (QR: the SVD's U of
+ *      the algorithm spans the same space);
+ *   3-5. one Rayleigh-Ritz pass (feast_iterate with the stop of line 15):
+ *      the pairs inside the contour with eq. 5.1 residual below eta are the
+ *      result, read with feast_eigs (flag -1: one pass, no convergence test).
+ *   Y    : device n x h complex128 (leading dim n), the random block.
+ *   h, g : block width and number of moments; t = h g <= the m0 given to
+ *          feast_setup, and the context's width becomes t.
+ *   info : host out, the pass report of step 3-5.
+ * FEAST_EINVAL for a bad argument or an oblique context.  Synchronises the
+ * stream. */
+int feast_cirr(feast_ctx *ctx, const void *Y, int h, int g, feast_iter_info *info);
+
 /* SEARCH (Section 4.1, Algorithm SEARCH): an upper bound t of the number of
  * eigenvalues inside the contour and a basis of the filtered subspace, which
  * then replaces the start block (Algorithm 6, line 1): on success the
@@ -285,6 +304,12 @@ int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contou
 /* Number of CUDA kernels this library has launched in the process so far
  * (host-side counter; every launch site increments it). */
 unsigned long long feast_kernel_launches(void);
+
+/* The CUDA error behind the calling thread's last FEAST_ECUDA: the error's
+ * name and the library source location that saw it ("" if none yet).  The
+ * string belongs to the library and stays valid until the thread's next
+ * failing call. */
+const char *feast_last_cuda_error(void);
 
 /* ---------------------------------------------------- standalone kernels */
 

@@ -33,9 +33,10 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESINGULAR", -5:
 
 
 class FeastError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)} ({status})")
+        msg = f"{where}: {STATUS.get(status, status)} ({status})"
+        super().__init__(msg + (f" [{detail}]" if detail else ""))
 
 
 class Pencil(C.Structure):
@@ -80,10 +81,10 @@ _lock = threading.Lock()
 EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs", "feast_get",
            "feast_filter", "feast_set_subspace", "feast_destroy", "feast_strerror",
            "feast_zgetrf_batched", "feast_zgetrs_batched", "feast_zqz_batched",
-           "feast_zqz_work_bytes", "feast_kernel_launches", "feast_zqz_batched_noalloc",
+           "feast_zqz_work_bytes", "feast_kernel_launches", "feast_last_cuda_error", "feast_zqz_batched_noalloc",
            "feast_batch_workspace_size", "feast_solve_batch", "feast_cgemm_tc_scratch_bytes",
            "feast_cgemm_tc", "feast_zgemm_oz_work_bytes", "feast_zgemm_oz", "feast_grad_abs2",
-           "feast_search"]
+           "feast_search", "feast_cirr"]
 
 
 def lib_path() -> str:
@@ -114,6 +115,7 @@ def load(build_if_missing: bool = True):
         lib.feast_set_subspace.argtypes = [P, P]
         lib.feast_search.argtypes = [P, P, C.c_int, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_int),
                                      C.POINTER(C.c_int)]
+        lib.feast_cirr.argtypes = [P, P, C.c_int, C.c_int, C.POINTER(IterInfo)]
         lib.feast_destroy.argtypes = [P]
         lib.feast_destroy.restype = None
         lib.feast_strerror.argtypes = [I]
@@ -140,6 +142,7 @@ def load(build_if_missing: bool = True):
         lib.feast_zgemm_oz.argtypes = [I64, I64, I64, D, D, P, I64, P, I64, D, D, P, I64, P, C.c_size_t, P, P]
         lib.feast_kernel_launches.argtypes = []
         lib.feast_kernel_launches.restype = C.c_ulonglong
+        lib.feast_last_cuda_error.restype = C.c_char_p
         _lib = lib
         return lib
 
@@ -188,7 +191,10 @@ def from_device_colmajor(t, rows: int, cols: int) -> np.ndarray:
 
 def _check(st: int, where: str):
     if st != 0:
-        raise FeastError(st, where)
+        detail = ""
+        if st == -3 and _lib is not None:
+            detail = (_lib.feast_last_cuda_error() or b"").decode()
+        raise FeastError(st, where, detail)
 
 
 class Feast:
@@ -333,6 +339,18 @@ class Feast:
         _torch().cuda.current_stream().synchronize()
         self.m0 = t.value
         return dict(t=t.value, s0=s0.value)
+
+    def cirr(self, Y, g: int) -> dict:
+        """Block CIRR (Section 2.1) on this context (set up with
+        projection=FEAST_RAYLEIGH_RITZ): Y (n x h) random columns, g moments,
+        t = h g <= m0.  Returns the pass report; the selected pairs are read
+        with eigs()."""
+        h = int(Y.shape[1])
+        Yd = to_device_colmajor(Y, self.device, _torch().complex128)
+        info = IterInfo()
+        _check(self._lib.feast_cirr(self._ctx, Yd.data_ptr(), h, int(g), C.byref(info)), "feast_cirr")
+        self.m0 = h * int(g)
+        return info.as_dict()
 
     def set_subspace(self, U1):
         Ud = to_device_colmajor(U1, self.device)

@@ -121,10 +121,13 @@ struct DevStatus {
     int qz_aed;         // early-deflation windows applied
 };
 
+// Records the failing CUDA call (error name, file, line) for
+// feast_last_cuda_error; returns FEAST_ECUDA.
+int note_cuda_error(cudaError_t e, const char *file, int line);
 #define FEAST_CUDA_TRY(expr)                                                         \
     do {                                                                             \
         cudaError_t _e = (expr);                                                     \
-        if (_e != cudaSuccess) return FEAST_ECUDA;                                   \
+        if (_e != cudaSuccess) return ::feast::note_cuda_error(_e, __FILE__, __LINE__); \
     } while (0)
 
 // Every kernel launch of the library is followed by this check, which also
@@ -134,7 +137,7 @@ void count_launch();
     do {                                                                             \
         ::feast::count_launch();                                                     \
         cudaError_t _e = cudaGetLastError();                                         \
-        if (_e != cudaSuccess) return FEAST_ECUDA;                                   \
+        if (_e != cudaSuccess) return ::feast::note_cuda_error(_e, __FILE__, __LINE__); \
     } while (0)
 
 static inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
@@ -154,6 +157,18 @@ inline cudaError_t allow_dyn_smem(K kernel)
     if ((e = cudaFuncGetAttributes(&fa, (const void *)kernel)) != cudaSuccess) return e;
     return cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 optin - (int)fa.sharedSizeBytes);
+}
+
+// Opt a launch with `bytes` of dynamic shared memory in above the 48 KB
+// default when the kernel's static plus dynamic shared memory exceeds it.
+template <typename K>
+inline cudaError_t ensure_dyn_smem(K kernel, size_t bytes)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void *)kernel);
+    if (e != cudaSuccess) return e;
+    if (bytes + fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
+    return allow_dyn_smem(kernel);
 }
 
 // ---------------------------------------------------------------- grid barrier
@@ -317,6 +332,10 @@ int normalise_cols(cudaStream_t s, int m, zd *V);
 // (a basis of the selected columns' span, orthonormal to ~eps cond^2; U is
 // left as it was).
 int trace_real(cudaStream_t s, int64_t n, int p, const zd *Y, int64_t ldy, const zd *U, int64_t ldu, double *out);
+// Block CIRR step 1 (k_cirr.cu): R[:, i h + c] = sum_j w_j ((z_j - centre) /
+// scale)^i X_j[:, c] for i < g, c < h (X_j at stride sX, leading dim n).
+int moment_sum(cudaStream_t s, int64_t n, int h, int q, int g, const zd *z, const zd *w, double cre, double cim,
+               double scale, const zd *X, int64_t sX, zd *R, int64_t ldr);
 size_t rrqr_work_bytes(int64_t n, int m);
 int rrqr_basis(cudaStream_t s, int64_t n, int m, const zd *U, zd *Q, double rank_tol, void *work, int *timeout,
                int *t_out);

@@ -10,6 +10,7 @@
 #include <atomic>
 #include <complex>
 #include <stdlib.h>
+#include <stdio.h>
 #include <string.h>
 #include <thread>
 #include <vector>
@@ -21,6 +22,13 @@ using namespace feast;
 namespace feast {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local char g_cuda_error[256] = "";
+int note_cuda_error(cudaError_t e, const char *file, int line)
+{
+    const char *base = strrchr(file, '/');
+    snprintf(g_cuda_error, sizeof(g_cuda_error), "%s (%s:%d)", cudaGetErrorName(e), base ? base + 1 : file, line);
+    return FEAST_ECUDA;
+}
 }  // namespace feast
 
 struct feast_ctx {
@@ -442,19 +450,24 @@ int solve_refine(feast_ctx *c, const zd *BV, double tol)
 
 // U = sum_j w_j (z_j B - A)^{-1} B V   (eq. 4.1 - 4.2).  tol applies to the
 // precision form only.
+// X_j = M_j^{-1} RHS for every node j into c->Xs (stride n m0), the
+// precision form refined to tol.
+int solve_nodes(feast_ctx *c, const zd *rhs, double tol)
+{
+    const int64_t n = c->n, m = c->m0;
+    if (c->kind == FEAST_BANDED) return solve_band(c, rhs, tol);
+    if (c->prec != FEAST_FP64) return solve_refine(c, rhs, tol);
+    int e;
+    if ((e = zgather_rows(c->s, n, m, c->q, c->perm, rhs, n, c->Xs, n, n * m))) return e;
+    return ztrsm_lu_batched(c->s, n, m, c->q, c->F, n, n * n, c->Xs, n, n * m);
+}
+
 int filter(feast_ctx *c, const zd *V, zd *Uout, double tol)
 {
     const int64_t n = c->n, m = c->m0;
     int e;
     if ((e = apply_B(c, V, c->tmp, m))) return e;
-    if (c->kind == FEAST_BANDED) {
-        if ((e = solve_band(c, c->tmp, tol))) return e;
-    } else if (c->prec == FEAST_FP64) {
-        if ((e = zgather_rows(c->s, n, m, c->q, c->perm, c->tmp, n, c->Xs, n, n * m))) return e;
-        if ((e = ztrsm_lu_batched(c->s, n, m, c->q, c->F, n, n * n, c->Xs, n, n * m))) return e;
-    } else {
-        if ((e = solve_refine(c, c->tmp, tol))) return e;
-    }
+    if ((e = solve_nodes(c, c->tmp, tol))) return e;
     return znode_sum(c->s, n, m, c->q, c->w, c->Xs, n, n * m, Uout, n);
 }
 
@@ -782,15 +795,17 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     // U1, or on the |rho|-ordered Ritz vectors when the next pass may solve
     // warm (the same subspace, x_i = U1 y_i, in a basis whose leading
     // columns converge first).
-    if (c->prec != FEAST_FP64) {
-        if ((e = filter_defect(c, c->U))) return e;
-    } else if ((e = filter(c, c->ritz_filter ? c->Xr : c->U1, c->U, 1.0))) {
-        return e;
+    // (a pass at max_iter stops whatever the tests say: no next subspace)
+    const bool last = c->k >= c->max_iter && !c->no_stop;
+    if (!last) {
+        if (c->prec != FEAST_FP64) e = filter_defect(c, c->U);
+        else e = filter(c, c->ritz_filter ? c->Xr : c->U1, c->U, 1.0);
+        if (e) return e;
     }
     // (the warm solve relies on B~ = R2 being upper triangular: oblique only)
     c->warm_ready = !rr && c->ritz_filter && c->pair_perm && m >= kWarmMinM;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[4], s));
-    if ((e = orthonormalise(c, c->U))) return e;
+    if (!last && (e = orthonormalise(c, c->U))) return e;
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[5], s));
     DevStatus hs;
     FEAST_CUDA_TRY(cudaMemcpyAsync(&hs, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -983,6 +998,44 @@ int feast_search(feast_ctx *c, const void *Ypool, int npool, double alpha, int p
     return FEAST_OK;
 }
 
+int feast_cirr(feast_ctx *c, const void *Y, int h, int g, feast_iter_info *info)
+{
+    if (!c || !Y || !info || h < 1 || g < 1) return FEAST_EINVAL;
+    if (c->projection != FEAST_RAYLEIGH_RITZ) return FEAST_EINVAL;
+    const int64_t n = c->n, t = (int64_t)h * g;
+    if (t > c->m0cap) return FEAST_EINVAL;
+    cudaStream_t s = c->s;
+    int e;
+    // step 1: X_j = M_j^{-1} Y at width h, then the moment block (width t)
+    c->m0 = h;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->tmp, Y, sizeof(zd) * n * h, cudaMemcpyDeviceToDevice, s));
+    e = solve_nodes(c, c->tmp, (c->prec == FEAST_FP64) ? 1.0 : c->refine_tol);
+    if (!e)
+        e = moment_sum(s, n, h, c->q, g, c->z, c->w, c->contour.center_re, c->contour.center_im,
+                       fmax(c->contour.a, c->contour.b), c->Xs, n * h, c->U, n);
+    c->m0 = (int)t;
+    if (e) return e;
+    // step 2: an orthonormal basis of the moment block (QR; the SVD's U spans
+    // the same space), and B U1 for the projection
+    if ((e = orthonormalise(c, c->U))) return e;
+    // steps 3-5: one Rayleigh-Ritz pass; the stop of line 15 keeps the
+    // selected pairs for feast_eigs
+    c->k = 0;
+    c->c_prev = 0;
+    c->e_prev = 0.0;
+    c->done = 0;
+    c->cur = 0;
+    c->warm_ready = 0;
+    c->ritz_filter = 0;
+    const int mi = c->max_iter, ns = c->no_stop;
+    c->max_iter = 1;
+    c->no_stop = 0;
+    e = feast_iterate(c, info);
+    c->max_iter = mi;
+    c->no_stop = ns;
+    return e;
+}
+
 void feast_destroy(feast_ctx *c)
 {
     if (!c) return;
@@ -1076,6 +1129,8 @@ int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contou
 }
 
 unsigned long long feast_kernel_launches(void) { return g_launches.load(); }
+
+const char *feast_last_cuda_error(void) { return g_cuda_error; }
 
 const char *feast_strerror(int status)
 {

@@ -549,8 +549,8 @@ int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *
     dim3 g(cdiv(nrhs, GB_CW), q);
     const size_t smf = ((size_t)(kl + 1 + GB_JC) * GB_CW + (size_t)GB_JC * kl) * sizeof(T) + GB_JC * sizeof(int) + 16;
     const size_t smb = ((size_t)(kv + 1 + GB_JC) * GB_CW + (size_t)GB_JC * (kv + 1)) * sizeof(T);
-    if (smf > 48 * 1024) FEAST_CUDA_TRY(allow_dyn_smem(k_gb_fwd<T>));
-    if (smb > 48 * 1024) FEAST_CUDA_TRY(allow_dyn_smem(k_gb_bwd<T>));
+    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_fwd<T>, smf));
+    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_bwd<T>, smb));
     k_gb_fwd<T><<<g, GB_ST, smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX);
     FEAST_LAUNCH_CHECK();
     k_gb_bwd<T><<<g, GB_ST, smb, s>>>(n, kl, ku, nrhs, F, ldab, sF, X, ldx, sX);

@@ -337,8 +337,7 @@ int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA
     if (m <= 0 || batch <= 0) return FEAST_OK;
     if (m <= 64) {
         size_t sm = 3 * (size_t)m * m * sizeof(zd);
-        if (sm > 48 * 1024)
-            FEAST_CUDA_TRY(allow_dyn_smem(k_qz<128>));
+        FEAST_CUDA_TRY(ensure_dyn_smem(k_qz<128>, sm));
         k_qz<128><<<batch, 128, sm, s>>>(m, A, lda, sA, B, ldb, sB, alpha, beta, V, ldv, sV, (zd *)work, 1, fail);
         FEAST_LAUNCH_CHECK();
         return FEAST_OK;

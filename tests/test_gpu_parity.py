@@ -69,7 +69,7 @@ def test_singular_matrix_reports_info():
 
 
 # ------------------------------------------------------------------ QZ
-@pytest.mark.parametrize("m", [1, 2, 5, 16, 40, 64, 65, 100, 164, 165, 300, 400])
+@pytest.mark.parametrize("m", [1, 2, 5, 16, 32, 40, 64, 65, 100, 164, 165, 300, 400])
 def test_qz_matches_oracle(m):
     """Eigenvalues as multisets (the order of a QZ run is not unique) and the
     generalized eigen-residual of every returned vector.  m <= 64: one-CTA QZ;
