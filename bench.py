@@ -332,6 +332,20 @@ def reference_special(args, cfg):
         return {"value": passes / t_full, "unit": "iters/s", "cores": threads, "kind": "oracle",
                 "sample": f"oracle SEARCH + GFEAST at n={n} ({dt:.1f} s, {passes} passes) scaled by (4)^3 "
                           f"to n={cfg['n']}"}
+    if cfg.get("compare"):
+        # the oracle's GFEAST on the gapped pencil at n/4 (width and count
+        # scaled alike), time scaled by n^3
+        n = cfg["n"] // 4
+        p = inputs.gapped_pencil(n, cfg["m0"] // 4, cfg["n_in"] // 4, seed=cfg["seed"])
+        t0 = time.perf_counter()
+        o = oracle.Feast(p.A, p.B, p.Y, contour_kind=0, rule=cfg["rule"], q=cfg["q"], center=cfg["center"],
+                         a=cfg["radius"], eps=cfg["eps"])
+        passes = len(o.run())
+        o.close()
+        dt = time.perf_counter() - t0
+        t_full = dt * 64.0
+        return {"value": passes / t_full, "unit": "iters/s", "cores": threads, "kind": "oracle",
+                "sample": f"oracle GFEAST at n={n} ({dt:.1f} s, {passes} passes) scaled by (4)^3 to n={cfg['n']}"}
     # differentiation: the oracle's gradient (two whole-pencil QZs) at n/4, scaled by n^3
     n = cfg["n"] // 4
     p = inputs.prescribed_pencil(n, 8, seed=cfg["seed"])
@@ -348,7 +362,7 @@ def reference_arm(args):
     if rank != 0:
         return 0
     cfg = inputs.WORKLOADS[args.workload]
-    if "batch" in cfg or cfg.get("grad") or cfg.get("search"):
+    if "batch" in cfg or cfg.get("grad") or cfg.get("search") or cfg.get("compare"):
         vals = [reference_special(args, cfg) for _ in range(max(1, args.steps))]
         v = statistics.median([x["value"] for x in vals])
         cb = dict(vals[-1])
@@ -899,6 +913,96 @@ def search_arm(args, cfg):
     return 0
 
 
+def compare_arm(args, cfg):
+    """The comparison of Section 5 on one gapped pencil: GFEAST (oblique
+    projection), the Rayleigh-Ritz FEAST of Section 3 (same driver, test
+    basis U1) and Block CIRR of Section 2.1 (one pass over g moments of h
+    random columns), all on the GPU at the same width.  A step solves the
+    pencil with all three (each: set-up, solve, eigenvalues to the host);
+    value = GFEAST passes / GFEAST time, the other methods' times and
+    accuracies beside it."""
+    import torch
+    import paper_1404_1768_gb300 as fg
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    fg.load()
+    cc = cfg["compare"]
+    p = inputs.gapped_pencil(cfg["n"], cfg["m0"], cfg["n_in"], seed=cfg["seed"])
+    inside = np.abs(p.lam - cfg["center"]) < cfg["radius"]
+    exact = p.lam[inside]
+    Yc = inputs.complex_normal(np.random.default_rng(cfg["seed"] + 2), (cfg["n"], cc["h"]))
+    kw = dict(contour_kind=0, rule=cfg["rule"], q=cfg["q"], center=cfg["center"], a=cfg["radius"], eps=cfg["eps"])
+    if args.prec == "c64r":
+        kw.update(prec=fg.FEAST_C64_REFINE, refine_tol=1e-13, max_refine=4)
+
+    def accuracy(res):
+        pool_ = list(exact)
+        worst = 0.0
+        for x in res["lam"]:
+            if not pool_:
+                break
+            j = int(np.argmin([abs(x - y) for y in pool_]))
+            worst = max(worst, abs(x - pool_[j]) / abs(pool_[j]))
+            pool_.pop(j)
+        return worst
+
+    def one(method):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        proj = fg.FEAST_OBLIQUE if method == "gfeast" else fg.FEAST_RAYLEIGH_RITZ
+        g = fg.Feast(p.A, p.B, p.Y, projection=proj, **kw)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if method == "cirr":
+            g.cirr(Yc, cc["g"])
+            passes = 1
+        else:
+            passes = len(g.run())
+        res = g.eigs(want_vectors=False)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        g.close()
+        return dict(setup=t1 - t0, solve=t2 - t1, passes=passes, res=res)
+
+    methods = ("gfeast", "rayleigh_ritz", "cirr")
+
+    def step():
+        return {m: one(m) for m in methods}
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    runs = [step() for _ in range(args.steps)]
+    clk = clocks.stop()
+    out = {}
+    for m in methods:
+        rs = sorted((r[m] for r in runs), key=lambda x: x["setup"] + x["solve"])
+        med = rs[len(rs) // 2]
+        res = med["res"]
+        out[m] = {"ms_total": 1e3 * (med["setup"] + med["solve"]), "ms_setup": 1e3 * med["setup"],
+                  "ms_solve": 1e3 * med["solve"], "passes": med["passes"], "flag": res["flag"],
+                  "count": res["count"], "max_rel_eig_err_vs_exact": accuracy(res),
+                  "max_resid_eq_5_1": float(np.max(res["res"])) if res["count"] else None}
+    gf = out["gfeast"]
+    if rank == 0:
+        line = {"metric": METRIC, "value": gf["passes"] / (1e-3 * gf["ms_total"]), "unit": "iters/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": gf["ms_total"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "c128" if args.prec == "fp64" else "c64+c128", "data": "synthetic",
+                "config": {"workload": args.workload, "n": cfg["n"], "m0": cfg["m0"], "q": cfg["q"],
+                           "pencil": "A = P diag(lam) Q, B = P Q, %d eigenvalues in |z| < 0.7, the rest in "
+                                     "1.5 < |z| < 2 (seeded)" % cfg["n_in"],
+                           "cirr": cc, "precision": args.prec, "parallelism": "replicas1"},
+                "exact_inside": int(inside.sum()), "compare": out,
+                "e2e": {"value": gf["passes"] / (1e-3 * gf["ms_total"]), "unit": "iters/s",
+                        "what": "host pencil -> device, set-up, GFEAST passes until the stop fires, "
+                                "eigenvalues back to the host"},
+                "clocks": clk, "roofline": None, "cpu_baseline": None}
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -911,6 +1015,8 @@ def main():
         return grad_arm(args, inputs.WORKLOADS[args.workload])
     if inputs.WORKLOADS[args.workload].get("search"):
         return search_arm(args, inputs.WORKLOADS[args.workload])
+    if inputs.WORKLOADS[args.workload].get("compare"):
+        return compare_arm(args, inputs.WORKLOADS[args.workload])
     return gpu_arm(args)
 
 

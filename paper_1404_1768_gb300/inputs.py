@@ -250,6 +250,11 @@ WORKLOADS = {
     # 1.5, rank threshold 1e-4
     "search_n2048_s400_q32": dict(n=2048, m0=640, n_in=400, q=32, rule=0, center=0j, radius=1.0, seed=0,
                                   eps=1e-10, search=dict(p=64, alpha=1.5, rank_tol=1e-4, pool=1024)),
+    # the comparison of Section 5 on a gapped pencil: GFEAST (oblique), the
+    # Rayleigh-Ritz FEAST of Section 3 and Block CIRR of Section 2.1 (h = 80
+    # random columns, g = 4 moments), all at width 320 for 200 inside
+    "compare_n2048_s200_q32": dict(n=2048, m0=320, n_in=200, q=32, rule=0, center=0j, radius=1.0, seed=0,
+                                   eps=1e-10, compare=dict(h=80, g=4)),
 }
 
 
