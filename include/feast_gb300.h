@@ -223,6 +223,29 @@ int feast_get(const feast_ctx *ctx, int what, void *dst);
  * stream. */
 int feast_cirr(feast_ctx *ctx, const void *Y, int h, int g, feast_iter_info *info);
 
+/* Sparse pencils onto the banded path.  The paper's pencils are sparse
+ * discretisations; a symmetric permutation P A P^T, P B P^T keeps the
+ * eigenvalues (eigenvectors are permuted), so a bandwidth-reducing ordering
+ * lets such a pencil run as FEAST_BANDED.
+ *
+ * feast_csr_rcm: reverse Cuthill-McKee ordering of the symmetrised joint
+ * pattern of A and B (host arrays; CSR with int64 row pointers rowptr[0..n]
+ * from 0 and column indices; B may be NULL for B = I).  perm (host, n):
+ * perm[new] = old.  kl, ku (host out): the lower / upper bandwidth of both
+ * permuted matrices.  FEAST_EINVAL for malformed CSR.  Host only; no CUDA. */
+int feast_csr_rcm(int64_t n, const int64_t *a_rowptr, const int64_t *a_col, const int64_t *b_rowptr,
+                  const int64_t *b_col, int64_t *perm, int64_t *kl, int64_t *ku);
+
+/* feast_csr_to_band: writes P M P^T of the CSR matrix M (device rowptr,
+ * col, complex128 val) into compact band storage band (device,
+ * (kl + ku + 1) x n column-major, entry (i, j) at row ku + i - j), zero
+ * elsewhere; duplicate entries are summed.  iperm (device, n): iperm[old] =
+ * new.  status: a device int of scratch.  FEAST_EINVAL if an entry falls
+ * outside the band or a column index is out of range (those entries are
+ * skipped).  Synchronises the stream. */
+int feast_csr_to_band(int64_t n, const int64_t *rowptr, const int64_t *col, const void *val, const int64_t *iperm,
+                      int64_t kl, int64_t ku, void *band, int *status, void *stream);
+
 /* SEARCH (Section 4.1, Algorithm SEARCH): an upper bound t of the number of
  * eigenvalues inside the contour and a basis of the filtered subspace, which
  * then replaces the start block (Algorithm 6, line 1): on success the

@@ -84,7 +84,7 @@ EXPORTS = ["feast_workspace_size", "feast_setup", "feast_iterate", "feast_eigs",
            "feast_zqz_work_bytes", "feast_kernel_launches", "feast_last_cuda_error", "feast_zqz_batched_noalloc",
            "feast_batch_workspace_size", "feast_solve_batch", "feast_cgemm_tc_scratch_bytes",
            "feast_cgemm_tc", "feast_zgemm_oz_work_bytes", "feast_zgemm_oz", "feast_grad_abs2",
-           "feast_search", "feast_cirr"]
+           "feast_search", "feast_cirr", "feast_csr_rcm", "feast_csr_to_band"]
 
 
 def lib_path() -> str:
@@ -116,6 +116,8 @@ def load(build_if_missing: bool = True):
         lib.feast_search.argtypes = [P, P, C.c_int, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_int),
                                      C.POINTER(C.c_int)]
         lib.feast_cirr.argtypes = [P, P, C.c_int, C.c_int, C.POINTER(IterInfo)]
+        lib.feast_csr_rcm.argtypes = [I64, P, P, P, P, P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        lib.feast_csr_to_band.argtypes = [I64, P, P, P, P, I64, I64, P, P, P]
         lib.feast_destroy.argtypes = [P]
         lib.feast_destroy.restype = None
         lib.feast_strerror.argtypes = [I]
@@ -604,3 +606,80 @@ def eig_sum_abs2(A, B, Y, **kw):
     if _EIG_ABS2 is None:
         _EIG_ABS2 = _make_eig_abs2_function()
     return _EIG_ABS2.apply(A, B, Y, kw)
+
+
+def _csr_arrays(M, n):
+    """(indptr, indices, data) of a CSR matrix (a scipy.sparse matrix or a
+    triple) as int64 / int64 / complex128 numpy arrays."""
+    if hasattr(M, "tocsr"):
+        M = M.tocsr()
+        M = (M.indptr, M.indices, M.data)
+    indptr, indices, data = M
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(indices, dtype=np.int64)
+    data = np.ascontiguousarray(data, dtype=np.complex128)
+    if indptr.shape != (n + 1,) or indices.shape != data.shape:
+        raise ValueError("malformed CSR triple")
+    return indptr, indices, data
+
+
+def csr_rcm(n: int, A, B=None):
+    """Reverse Cuthill-McKee ordering of the joint pattern of the sparse
+    pencil (host; feast_csr_rcm).  Returns (perm, kl, ku): perm[new] = old
+    and the bandwidths of the permuted A and B."""
+    lib = load()
+    a = _csr_arrays(A, n)
+    b = _csr_arrays(B, n) if B is not None else None
+    perm = np.zeros(n, np.int64)
+    kl, ku = C.c_int64(0), C.c_int64(0)
+    _check(lib.feast_csr_rcm(n, a[0].ctypes.data, a[1].ctypes.data, b[0].ctypes.data if b else None,
+                             b[1].ctypes.data if b else None, perm.ctypes.data, C.byref(kl), C.byref(ku)),
+           "feast_csr_rcm")
+    return perm, int(kl.value), int(ku.value)
+
+
+def csr_to_band(n: int, M, perm, kl: int, ku: int, device="cuda"):
+    """P M P^T of a CSR matrix in compact band storage on the device (flat
+    column-major (kl + ku + 1) x n complex128 tensor; feast_csr_to_band)."""
+    torch = _torch()
+    lib = load()
+    indptr, indices, data = _csr_arrays(M, n)
+    iperm = np.empty(n, np.int64)
+    iperm[np.asarray(perm, np.int64)] = np.arange(n, dtype=np.int64)
+    d_ptr = torch.from_numpy(indptr).to(device)
+    d_col = torch.from_numpy(indices).to(device)
+    d_val = torch.from_numpy(data).to(device)
+    d_ip = torch.from_numpy(iperm).to(device)
+    band = torch.empty((kl + ku + 1) * n, dtype=torch.complex128, device=device)
+    status = torch.zeros(1, dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream(torch.device(device))
+    _check(lib.feast_csr_to_band(n, d_ptr.data_ptr(), d_col.data_ptr(), d_val.data_ptr(), d_ip.data_ptr(), kl, ku,
+                                 band.data_ptr(), status.data_ptr(), stream.cuda_stream), "feast_csr_to_band")
+    return band
+
+
+class SparseFeast(Feast):
+    """GFEAST on a sparse pencil (A, B in CSR; B = None for B = I): the
+    rows and columns are reordered by reverse Cuthill-McKee, both matrices
+    are scattered into band storage on the device, and the banded path runs
+    on (P A P^T, P B P^T) with the start block P Y.  eigs() returns the
+    eigenvectors in the original ordering."""
+
+    def __init__(self, n: int, A, B, Y, **kw):
+        for k in ("kind", "kl", "ku", "b_identity"):
+            if k in kw:
+                raise TypeError(f"SparseFeast sets {k} itself")
+        device = kw.get("device", "cuda")
+        self.perm, kl, ku = csr_rcm(n, A, B)
+        Ab = csr_to_band(n, A, self.perm, kl, ku, device)
+        Bb = csr_to_band(n, B, self.perm, kl, ku, device) if B is not None else None
+        Yp = np.asarray(Y)[self.perm, :] if not hasattr(Y, "device") else Y[_torch().from_numpy(self.perm)]
+        super().__init__(Ab, Bb, Yp, kind=FEAST_BANDED, kl=kl, ku=ku, b_identity=B is None, **kw)
+        self._iperm = np.empty(n, np.int64)
+        self._iperm[self.perm] = np.arange(n, dtype=np.int64)
+
+    def eigs(self, want_vectors: bool = True) -> dict:
+        out = super().eigs(want_vectors)
+        if want_vectors:
+            out["X"] = out["X"][self._iperm, :]
+        return out

@@ -15,6 +15,9 @@ here; these generators stand in for them with the same kind of structure:
 * ``ragged_batch``: many prescribed-spectrum pencils of uneven size.
 * ``hermitian_pencil``: A Hermitian, B Hermitian positive definite, real
   prescribed spectrum (the Rayleigh-Ritz comparison case).
+* ``sparse_pencil``: the convection-diffusion operator with a non-identity
+  sparse B, rows and columns in a random order, in CSR (the structure of
+  the paper's sparse test pencils without a banded ordering).
 
 Random draws use ``numpy.random.default_rng(seed)`` (PCG64) in a fixed
 order: lam (u then v, then any re-draws), G_P, G_Q, Y.  With seed 0 and
@@ -185,6 +188,65 @@ def convection_diffusion(nx: int, m0: int, seed: int = 0, beta=(20.0, 10.0)) -> 
     rng = np.random.default_rng(seed)
     Y = complex_normal(rng, (n, m0))
     return BandPencil(A_band=ab, n=n, kl=kl, ku=ku, Y=Y, nx=nx, h=h, beta=tuple(beta))
+
+
+@dataclass
+class SparsePencil:
+    n: int
+    nx: int
+    A: tuple               # CSR (indptr int64, indices int64, data complex128)
+    B: tuple
+    Y: np.ndarray          # n x m0 start block (stored ordering)
+    shuffle: np.ndarray    # stored index k is grid node shuffle[k]
+
+    @staticmethod
+    def dense(M, n: int) -> np.ndarray:
+        indptr, indices, data = M
+        D = np.zeros((n, n), np.complex128, order="F")
+        for i in range(n):
+            for p in range(indptr[i], indptr[i + 1]):
+                D[i, indices[p]] += data[p]
+        return D
+
+
+def sparse_pencil(nx: int, m0: int, seed: int = 0, beta=(20.0, 10.0), mass: float = 0.1) -> SparsePencil:
+    """A sparse pencil with the structure of a discretised PDE and no useful
+    ordering: A = the convection-diffusion operator of convection_diffusion,
+    B = I + mass * (sum of the 4 grid neighbours) / 4 (symmetric, eigenvalues
+    in (1 - mass, 1 + mass)), both with rows and columns in a random order
+    (rng.permutation, drawn first; then Y), in CSR with sorted columns."""
+    n = nx * nx
+    h = 1.0 / (nx + 1)
+    b1, b2 = beta
+    inv = 1.0 / (h * h)
+    rng = np.random.default_rng(seed)
+    shuffle = rng.permutation(n).astype(np.int64)
+    pos = np.empty(n, np.int64)
+    pos[shuffle] = np.arange(n, dtype=np.int64)       # grid node -> stored index
+    ra, ca, va, rb, cb, vb = [], [], [], [], [], []
+    for gy in range(nx):
+        for gx in range(nx):
+            i = gx + gy * nx
+            ra.append(i); ca.append(i); va.append(4.0 * inv)
+            rb.append(i); cb.append(i); vb.append(1.0)
+            for (ok, j, coef) in ((gx > 0, i - 1, -1.0 - b1 * h / 2), (gx < nx - 1, i + 1, -1.0 + b1 * h / 2),
+                                  (gy > 0, i - nx, -1.0 - b2 * h / 2), (gy < nx - 1, i + nx, -1.0 + b2 * h / 2)):
+                if ok:
+                    ra.append(i); ca.append(j); va.append(coef * inv)
+                    rb.append(i); cb.append(j); vb.append(mass / 4.0)
+
+    def csr(r, c, v):
+        r = pos[np.asarray(r)]
+        c = pos[np.asarray(c)]
+        v = np.asarray(v, np.complex128)
+        order = np.lexsort((c, r))
+        r, c, v = r[order], c[order], v[order]
+        indptr = np.zeros(n + 1, np.int64)
+        np.add.at(indptr, r + 1, 1)
+        return np.cumsum(indptr).astype(np.int64), c.astype(np.int64), v
+
+    Y = complex_normal(rng, (n, m0))
+    return SparsePencil(n=n, nx=nx, A=csr(ra, ca, va), B=csr(rb, cb, vb), Y=Y, shuffle=shuffle)
 
 
 @dataclass
