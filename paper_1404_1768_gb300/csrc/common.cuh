@@ -304,22 +304,24 @@ size_t zorth_work_elems(int64_t n, int64_t m);
 size_t zqz_work_bytes(int m);
 int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA, zd *B,
                 int64_t ldb, int64_t sB, zd *alpha, zd *beta, zd *V, int64_t ldv, int64_t sV,
-                void *work, int *fail, int *timeout, int *stats = nullptr);
+                void *work, int *fail, int *timeout, int *stats = nullptr, double defl = 0.0);
 
 // Large projected problems (k_zeig.cu): standard form, Hessenberg
 // reduction and chunked QR; alpha = eigenvalue, beta = 1.
 size_t zeig_large_work_bytes(int m);
 // stats (may be null): stats[0] += QR sweeps, stats[1] += chase phases,
 // stats[2] += early-deflation windows applied.
+// defl: relative deflation tolerance of the QR (0: the double-single floor,
+// 2^-44); a looser one when the eigenpairs are wanted to less accuracy.
 int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
-               int *fail, int *timeout, int *stats = nullptr);
+               int *fail, int *timeout, int *stats = nullptr, double defl = 0.0);
 // Schur form of a contiguous m x m matrix (k_zeig.cu): C <- T = Q^H C Q
 // (upper triangle; Hessenberg reduction then the double-single QR), Q
 // unitary.  work: schur_large_work_bytes(m).  hn_out (may be null): max
 // |C_ij| of the Hessenberg matrix.
 size_t schur_large_work_bytes(int m);
 int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int *timeout, int *stats,
-                double *hn_out);
+                double *hn_out, double defl = 0.0);
 // Eigenvectors of the upper triangle of T (m x m), unit diagonal, by
 // back-substitution; unit 2-norm columns.
 // scratch: m x m (T transposed, for contiguous row reads).

@@ -754,10 +754,18 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
         if (!c->last_warm.accepted) FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_fail, 0, sizeof(int), s));
     }
     if (!c->last_warm.accepted) {
+        // a cold solve's eigenpairs are needed only to about the accuracy
+        // the iteration has reached: the QR deflates at 1e-2 of the warm
+        // solve's target (at most 1e-8, at least the double-single floor),
+        // so the early passes stop sweeping once their pairs are accurate
+        // far beyond their residuals
+        const double eref = (c->c_prev > 0 && c->e_prev > 0.0) ? c->e_prev : c->eta;
+        const double defl = fmin(1e-8, 1e-2 * fmax(kWarmAccMin, 1e-3 * eref));
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if (rr && (e = triangularise_bt(c))) return e;
         if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
-                             c->qz_work, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps))) return e;
+                             c->qz_work, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, defl)))
+            return e;
     }
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[2], s));
     if (use_oz(c)) {

@@ -1352,7 +1352,8 @@ size_t zeig_large_work_bytes(int m)
     return sizeof(zd) * (size_t)m * m + schur_large_work_bytes(m);
 }
 
-int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int *timeout, int *stats, double *hn_out)
+int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int *timeout, int *stats, double *hn_out,
+                double defl)
 {
     if (m <= 0) return FEAST_OK;
     zd *v = (zd *)work;
@@ -1399,7 +1400,9 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
     if (hn_out) *hn_out = hn;
     // deflation thresholds at double-single resolution (2^-44 relative)
-    float tol_rel = 5.7e-14f, tol_abs = (float)(5.7e-14 * (hn > 0.0 ? hn : 1e-300));
+    // (or the caller's looser one)
+    const double tr = defl > 5.7e-14 ? defl : 5.7e-14;
+    float tol_rel = (float)tr, tol_abs = (float)(tr * (hn > 0.0 ? hn : 1e-300));
     if (m >= 2 && m <= SQ_MAX) {
         // one CTA, the matrix in shared memory; falls through to the grid
         // QR if its iteration budget or rotation log runs out
@@ -1457,7 +1460,7 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
 // A (m x m, overwritten), Bt (m x m upper triangular, overwritten by the
 // solve), alpha/beta (beta = 1), V (m x m unit eigenvectors).
 int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
-               int *fail, int *timeout, int *stats)
+               int *fail, int *timeout, int *stats, double defl)
 {
     if (m <= 0) return FEAST_OK;
     zd *Q = (zd *)work;
@@ -1466,7 +1469,7 @@ int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V,
     if ((e = trsm_upper_batched<zd>(s, m, m, 1, Bt, m, 0, A, m, 0))) return e;
     zd *C = A;
     double hn = 0.0;
-    if ((e = schur_large(s, m, C, Q, (char *)work + sizeof(zd) * (size_t)m * m, fail, timeout, stats, &hn)))
+    if ((e = schur_large(s, m, C, Q, (char *)work + sizeof(zd) * (size_t)m * m, fail, timeout, stats, &hn, defl)))
         return e;
     // eigenvalues and eigenvectors
     k_diag_out<<<cdiv(m, 128), 128, 0, s>>>(m, C, m, alpha, beta);

@@ -332,7 +332,7 @@ size_t zqz_work_bytes(int m)
 
 int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA, zd *B,
                 int64_t ldb, int64_t sB, zd *alpha, zd *beta, zd *V, int64_t ldv, int64_t sV,
-                void *work, int *fail, int *timeout, int *stats)
+                void *work, int *fail, int *timeout, int *stats, double defl)
 {
     if (m <= 0 || batch <= 0) return FEAST_OK;
     if (m <= 64) {
@@ -347,7 +347,7 @@ int zqz_batched(cudaStream_t s, int m, int batch, zd *A, int64_t lda, int64_t sA
     for (int b = 0; b < batch; ++b) {
         int e = zeig_large(s, m, A + (int64_t)b * sA, B + (int64_t)b * sB, alpha + (int64_t)b * m,
                            beta + (int64_t)b * m, V + (int64_t)b * sV, (char *)work + b * wb, fail,
-                           timeout, stats);
+                           timeout, stats, defl);
         if (e) return e;
     }
     return FEAST_OK;
