@@ -312,6 +312,11 @@ WORKLOADS = {
     # 1.5, rank threshold 1e-4
     "search_n2048_s400_q32": dict(n=2048, m0=640, n_in=400, q=32, rule=0, center=0j, radius=1.0, seed=0,
                                   eps=1e-10, search=dict(p=64, alpha=1.5, rank_tol=1e-4, pool=1024)),
+    # the banded workload's operator stored as a sparse matrix in a random
+    # order (CSR), B = I stored explicitly: reverse Cuthill-McKee must
+    # recover the band before the banded path runs; closed-form spectrum
+    "sparse_n16384_m64_q16": dict(nx=128, m0=64, q=16, rule=1, center=422.0 + 0j, a=322.0, b=80.5, seed=0,
+                                  eps=1e-10, beta=(20.0, 10.0), sparse=dict(mass=0.0)),
     # the comparison of Section 5 on a gapped pencil: GFEAST (oblique), the
     # Rayleigh-Ritz FEAST of Section 3 and Block CIRR of Section 2.1 (h = 80
     # random columns, g = 4 moments), all at width 320 for 200 inside
