@@ -151,6 +151,9 @@ typedef struct {
                          solve's Newton step (0 when not tried) */
     int qz_warm_k;    /* converged leading columns the warm solve found
                          (-1 when it was not tried) */
+    double ms_warm_gemm;   /* device time of the warm solve's FP64 product
+                              segments (GEMMs and triangular inverses) */
+    double warm_gemm_flop; /* their algorithmic flops (complex MAC = 8) */
 } feast_iter_info;
 
 typedef struct feast_ctx feast_ctx;

@@ -68,7 +68,8 @@ class IterInfo(C.Structure):
                 ("ms_qr", C.c_double), ("ms_proj", C.c_double), ("ms_qz", C.c_double),
                 ("refine_sweeps_max", C.c_int), ("bad_node", C.c_int), ("qz_sweeps", C.c_int),
                 ("qz_phases", C.c_int), ("qz_warm", C.c_int), ("qz_rows", C.c_int),
-                ("qz_warm_resid", C.c_double), ("qz_warm_k", C.c_int)]
+                ("qz_warm_resid", C.c_double), ("qz_warm_k", C.c_int),
+                ("ms_warm_gemm", C.c_double), ("warm_gemm_flop", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

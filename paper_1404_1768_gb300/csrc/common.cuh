@@ -356,10 +356,19 @@ struct WarmResult {
     double resid;   // largest relative eigen-residual of the Newton step
 };
 size_t zeig_warm_work_bytes(int m);
+// Events around the warm solve's FP64 product segments (GEMMs and
+// triangular inverses), for the per-kernel roofline: pairs (begin, end) in
+// ev[0 .. used), with the segments' algorithmic flops (complex MAC = 8).
+struct GemmTimer {
+    static constexpr int kMax = 10;
+    cudaEvent_t ev[kMax];
+    int used;
+    double flops;
+};
 // A, Bt as zeig_large (both overwritten whether accepted or not).  qz_work:
-// zeig_large_work_bytes(m) bytes.
+// zeig_large_work_bytes(m) bytes.  gt (may be null): segment timer.
 int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *warm_work, void *qz_work,
-              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats);
+              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats, GemmTimer *gt = nullptr);
 // Line 16 on Ritz pairs in defect form (k_defect.cu):
 // U = X rho(Lambda) + sum_j w_j M_j^{-1} (R D_j), R = A X - B X Lambda.
 struct DefectScratch {

@@ -109,6 +109,7 @@ struct feast_ctx {
     int out_count, out_flag, out_k;
     double out_err;
     cudaEvent_t ev[8];
+    GemmTimer gt;       // the warm solve's FP64 product segments
 };
 
 namespace {
@@ -565,6 +566,8 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
     carve(c, cv);
     for (int i = 0; i < 8; ++i)
         if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; }
+    for (int i = 0; i < GemmTimer::kMax; ++i)
+        if (cudaEventCreate(&c->gt.ev[i]) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; }
     const int64_t n = c->n;
     cudaStream_t s = c->s;
 #define TRY(x) do { int _r = (x); if (_r) { feast_destroy(c); return _r; } } while (0)
@@ -735,6 +738,8 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
     // line 6: projected eigenpairs, x_i = U1 y_i
     FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_sweeps, 0, 3 * sizeof(int), s));
     c->last_warm = WarmResult{};
+    c->gt.used = 0;
+    c->gt.flops = 0.0;
     c->warm_tried = c->warm_ready;
     if (c->warm_ready) {
         // the previous pass filtered its |rho|-ordered Ritz vectors: C is
@@ -749,7 +754,7 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
         const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc};
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if ((e = zeig_warm(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->warm_work, c->qz_work, prm,
-                           &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps)))
+                           &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt)))
             return e;
         if (!c->last_warm.accepted) FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_fail, 0, sizeof(int), s));
     }
@@ -854,6 +859,10 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
         info->qz_rows = c->last_warm.accepted ? c->last_warm.tail : (int)m;
         info->qz_warm_resid = c->last_warm.resid;
         info->qz_warm_k = c->warm_tried ? c->last_warm.k : -1;
+        double gms = 0.0;
+        for (int i = 0; i + 1 < c->gt.used; i += 2) gms += ev_ms(c->gt.ev[i], c->gt.ev[i + 1]);
+        info->ms_warm_gemm = gms;
+        info->warm_gemm_flop = c->gt.used >= 2 ? c->gt.flops : 0.0;
     }
     return FEAST_OK;
 }
@@ -1049,6 +1058,8 @@ void feast_destroy(feast_ctx *c)
     if (!c) return;
     for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < GemmTimer::kMax; ++i)
+        if (c->gt.ev[i]) cudaEventDestroy(c->gt.ev[i]);
     free(c->zw_host);
     free(c);
 }

@@ -181,17 +181,27 @@ int permute_cols(cudaStream_t s, int64_t rows, int m, const int *perm, const zd 
 }
 
 int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *warm_work, void *qz_work,
-              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats)
+              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats, GemmTimer *gt)
 {
     *res = WarmResult{};
     if (m < prm.min_m) return FEAST_OK;
     const WarmCarve w = warm_carve(warm_work, m);
     const size_t mm = (size_t)m * m;
     const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
+    const double m3 = (double)m * m * m, tri_inv = 8.0 * m3 / 6.0;   // m^3/6 MACs
+    // segment marks: begin, then end with the segment's algorithmic flops
+    auto mark = [&](double flops) -> int {
+        if (!gt || gt->used >= GemmTimer::kMax) return FEAST_OK;
+        FEAST_CUDA_TRY(cudaEventRecord(gt->ev[gt->used++], s));
+        gt->flops += flops;
+        return FEAST_OK;
+    };
     int e;
     // C = B~^{-1} A~ (B~ = R2 is upper triangular), into Cp
+    if ((e = mark(0.0))) return e;
     if ((e = tri_inverse(s, m, Bt, m, w.W, w.Ts))) return e;
     if ((e = zgemm_batched(s, 0, m, m, m, one, w.W, m, 0, A, m, 0, zero, w.Cp, m, 0, 1, 1))) return e;
+    if ((e = mark(tri_inv + 4.0 * m3))) return e;
     const zd *C = w.Cp;
     k_col_stats<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, C, w.lower, w.cmax);
     FEAST_LAUNCH_CHECK();
@@ -221,10 +231,12 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     // C' = Zh^H C Zh, Zh = diag(I_k, Z), into A (Bt as the row-block scratch)
     zd *Cq = A;
     FEAST_CUDA_TRY(cudaMemcpyAsync(Cq, C, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+    if ((e = mark(0.0))) return e;
     if ((e = zgemm_batched(s, 0, m, mb, mb, one, C + (int64_t)k * m, m, 0, w.Z, mb, 0, zero, Cq + (int64_t)k * m, m, 0,
                            1)))
         return e;
     if ((e = zgemm_batched(s, 1, mb, m, mb, one, w.Z, mb, 0, Cq + k, m, 0, zero, Bt + k, m, 0, 1))) return e;
+    if ((e = mark(16.0 * (double)m * mb * mb))) return e;
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(Cq + k, sizeof(zd) * m, Bt + k, sizeof(zd) * m, sizeof(zd) * mb, m,
                                      cudaMemcpyDeviceToDevice, s));
     // T^: C' with T22 from the QR in its trailing block (upper triangles are
@@ -235,10 +247,12 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     zd *Vh = Bt;  // V^, unit upper triangular
     if ((e = schur_vectors(s, m, w.Cp, Vh, hn, w.W))) return e;
     // F = V^{-1} (C' V^)
+    if ((e = mark(0.0))) return e;
     if ((e = zgemm_batched(s, 0, m, m, m, one, Cq, m, 0, Vh, m, 0, zero, w.W, m, 0, 1, 2))) return e;
     if ((e = tri_inverse(s, m, Vh, m, w.Cp, w.Ts))) return e;
     zd *F = V;
     if ((e = zgemm_batched(s, 0, m, m, m, one, w.Cp, m, 0, w.W, m, 0, zero, F, m, 0, 1, 1))) return e;
+    if ((e = mark(8.0 * m3 + tri_inv))) return e;
     k_diag_lambda<<<cdiv(m, 128), 128, 0, s>>>(m, F, alpha, beta);
     FEAST_LAUNCH_CHECK();
     FEAST_CUDA_TRY(cudaMemsetAsync(w.res, 0, 16, s));
@@ -246,8 +260,10 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     FEAST_LAUNCH_CHECK();
     // Y' = V^ + V^ G, and its residual against C'
     FEAST_CUDA_TRY(cudaMemcpyAsync(w.Yp, Vh, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+    if ((e = mark(0.0))) return e;
     if ((e = zgemm_batched(s, 0, m, m, m, one, Vh, m, 0, F, m, 0, one, w.Yp, m, 0, 1, 1))) return e;
     if ((e = zgemm_batched(s, 0, m, m, m, one, Cq, m, 0, w.Yp, m, 0, zero, w.W, m, 0, 1))) return e;
+    if ((e = mark(12.0 * m3))) return e;
     k_eig_resid<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, w.W, w.Yp, alpha, hn, w.res);
     FEAST_LAUNCH_CHECK();
     struct {

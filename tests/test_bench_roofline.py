@@ -39,3 +39,21 @@ def test_band_rows():
     dom, others = bench.roofline_dominant(prob, args, ph, _infos(False))
     assert dom["phase"] == "subspace-build solves" and dom["bound"] == "alu"
     assert KEYS <= set(dom)
+
+
+def test_warm_products_roofline_uses_the_library_events():
+    """With the warm solve's own segment timing in the pass reports, the
+    projected-eigensolve entry is that kernel's rate: total algorithmic
+    flops / total segment time over the timed passes."""
+    prob = bench.Problem(inputs.WORKLOADS["dense_n200_m64_q16"])
+    args = argparse.Namespace(prec="c64r")
+    ph = dict(ms_proj=1.0, ms_qz=5.0, ms_solve=2.0, ms_qr=3.0, ms_refine=0.0)
+    infos = _infos(True)
+    for i, inf in enumerate(infos):
+        inf.update(ms_warm_gemm=2.0 + i, warm_gemm_flop=3.0e9)
+    dom, _ = bench.roofline_dominant(prob, args, ph, infos)
+    assert dom["phase"] == "projected eigensolve"
+    expect = 9.0e9 / (9.0 / 1e3) / 1e12
+    assert abs(dom["achieved"] - expect) < 1e-12 * expect
+    assert abs(dom["kernel_ms_per_pass"] - 3.0) < 1e-12
+    assert abs(dom["frac"] - dom["achieved"] / dom["peak"]) < 1e-12
