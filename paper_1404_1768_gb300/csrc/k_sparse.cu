@@ -14,13 +14,16 @@ namespace feast {
 namespace {
 
 // Breadth-first level structure from root over the unvisited part of the
-// graph (mark = stamp for visited in this search).  Returns the number of
-// levels; `last` receives the nodes of the last level.
+// graph (stamp[v] = s marks v as reached by this search).  Returns the
+// number of levels; `last` receives the nodes of the last level and `all`
+// (if given) every node reached.
 int bfs_levels(int64_t root, const std::vector<int64_t> &xadj, const std::vector<int64_t> &adj,
-               const std::vector<char> &done, std::vector<int64_t> &stamp, int64_t s, std::vector<int64_t> &last)
+               const std::vector<char> &done, std::vector<int64_t> &stamp, int64_t s, std::vector<int64_t> &last,
+               std::vector<int64_t> *all = nullptr)
 {
     std::vector<int64_t> cur{root}, next;
     stamp[root] = s;
+    if (all) all->assign(1, root);
     int levels = 0;
     while (!cur.empty()) {
         ++levels;
@@ -29,7 +32,11 @@ int bfs_levels(int64_t root, const std::vector<int64_t> &xadj, const std::vector
         for (int64_t v : cur)
             for (int64_t p = xadj[v]; p < xadj[v + 1]; ++p) {
                 const int64_t w = adj[p];
-                if (!done[w] && stamp[w] != s) { stamp[w] = s; next.push_back(w); }
+                if (!done[w] && stamp[w] != s) {
+                    stamp[w] = s;
+                    next.push_back(w);
+                    if (all) all->push_back(w);
+                }
             }
         cur.swap(next);
     }
@@ -104,10 +111,10 @@ int feast_csr_rcm(int64_t n, const int64_t *a_rowptr, const int64_t *a_col, cons
         // eccentricity grows
         int64_t r = seed;
         {
-            std::vector<int64_t> comp;
-            bfs_levels(seed, xadj, adj, done, stamp, s++, comp);
-            for (int64_t v = 0; v < n; ++v)
-                if (stamp[v] == s - 1 && (deg(v) < deg(r) || (deg(v) == deg(r) && v < r))) r = v;
+            std::vector<int64_t> lev, comp;
+            bfs_levels(seed, xadj, adj, done, stamp, s++, lev, &comp);
+            for (int64_t v : comp)
+                if (deg(v) < deg(r) || (deg(v) == deg(r) && v < r)) r = v;
         }
         int ecc = bfs_levels(r, xadj, adj, done, stamp, s++, last);
         for (int it = 0; it < 32; ++it) {

@@ -92,3 +92,40 @@ def test_cirr_arguments_checked():
         g.cirr(Y, 3)        # t = 12 > m0 = 8
     assert ei.value.status == -1
     g.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cirr_and_rayleigh_ritz_on_a_banded_pencil(prec):
+    """The comparison methods on the banded path (12 x 12 convection-diffusion
+    grid, ellipse around its lowest 5 eigenvalues): Block CIRR and the
+    Rayleigh-Ritz FEAST against the oracle's on the same band storage, and
+    both against the closed-form spectrum."""
+    fg = _fg()
+    nx = 12
+    bp = inputs.convection_diffusion(nx, 12, seed=1)
+    lam = inputs.convection_diffusion_spectrum(nx)
+    lo, hi = lam[0] * 0.5, 0.5 * (lam[4] + lam[5])
+    cen, a = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    kw = dict(kind=1, kl=bp.kl, ku=bp.ku, b_identity=True, contour_kind=1, rule=1, q=32,
+              center=complex(cen), a=a, b=a / 4)
+    Y = inputs.complex_normal(np.random.default_rng(3), (bp.n, 4))
+    g = fg.Feast(bp.A_band, None, bp.Y, projection=fg.FEAST_RAYLEIGH_RITZ, prec=prec, refine_tol=1e-14, **kw)
+    g.cirr(Y, 3)
+    r = g.eigs()
+    o = oracle.Feast(bp.A_band, None, bp.Y, **kw)
+    ro = o.cirr(Y, 3)
+    assert r["count"] == ro["count"] == 5
+    assert _match(r["lam"], ro["lam"]) < 1e-9 * lam[4]
+    assert _match(r["lam"], lam[:5]) < 1e-9 * lam[4]
+    g.close(); o.close()
+    g = fg.Feast(bp.A_band, None, bp.Y, projection=fg.FEAST_RAYLEIGH_RITZ, prec=prec, refine_tol=1e-14,
+                 eps=1e-11, **kw)
+    g.run()
+    r = g.eigs()
+    o = oracle.Feast(bp.A_band, None, bp.Y, projection=1, eps=1e-11, **kw)
+    o.run()
+    ro = o.result()
+    assert r["flag"] == ro["flag"] == 1
+    assert r["count"] == ro["count"] == 5
+    assert _match(r["lam"], lam[:5]) < 1e-9 * lam[4]
+    g.close(); o.close()
