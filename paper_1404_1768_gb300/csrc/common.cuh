@@ -348,6 +348,7 @@ struct WarmParams {
     int min_tail;       // smallest trailing block given to the QR
     double tau;         // column of C counted converged: ||C[j+1:, j]|| <= tau max|C|
     double accept_tol;  // largest relative eigen-residual accepted
+    double tail_defl;   // relative deflation tolerance of the tail QR (0: the floor)
 };
 struct WarmResult {
     int accepted;   // 1: alpha, beta, V hold the eigenpairs

@@ -751,7 +751,9 @@ int feast_iterate(feast_ctx *c, feast_iter_info *info)
         // an eigenvalue gap (~1e-3 of max|C| and up): tau^2 / 1e-3 <= tol
         const double acc = fmax(kWarmAccMin, 1e-3 * eref);
         const double tau = fmin(1e-5, fmax(kWarmTauMin, sqrt(1e-3 * acc)));
-        const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc};
+        // the tail QR deflates at 1e-3 of the acceptance tolerance (the
+        // double-single floor once the residuals approach 1e-12)
+        const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc, 1e-3 * acc};
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if ((e = zeig_warm(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->warm_work, c->qz_work, prm,
                            &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt)))

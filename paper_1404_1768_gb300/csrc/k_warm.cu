@@ -227,7 +227,7 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     // Schur form of the trailing block: C22 = Z T22 Z^H
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.S, sizeof(zd) * mb, C + k + (int64_t)k * m, sizeof(zd) * m, sizeof(zd) * mb,
                                      mb, cudaMemcpyDeviceToDevice, s));
-    if ((e = schur_large(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr))) return e;
+    if ((e = schur_large(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr, prm.tail_defl))) return e;
     // C' = Zh^H C Zh, Zh = diag(I_k, Z), into A (Bt as the row-block scratch)
     zd *Cq = A;
     FEAST_CUDA_TRY(cudaMemcpyAsync(Cq, C, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
