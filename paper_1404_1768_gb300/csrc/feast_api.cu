@@ -713,7 +713,18 @@ int triangularise_bt(feast_ctx *c)
     return FEAST_OK;
 }
 
+static int iterate_impl(feast_ctx *c, feast_iter_info *info);
+
 int feast_iterate(feast_ctx *c, feast_iter_info *info)
+{
+    try {   // no C++ exception (a host allocation) may cross the C boundary
+        return iterate_impl(c, info);
+    } catch (...) {
+        return FEAST_ENOMEM;
+    }
+}
+
+static int iterate_impl(feast_ctx *c, feast_iter_info *info)
 {
     if (!c) return FEAST_EINVAL;
     if (c->done && !c->no_stop) return FEAST_EDONE;
@@ -1099,7 +1110,12 @@ int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contou
     if (workspace_bytes < need || ((uintptr_t)workspace & 255u)) return FEAST_ENOMEM;
     const int w = nworkers < count ? nworkers : count;
     const size_t slice = need / (size_t)w;
-    std::vector<size_t> off((size_t)count + 1, 0);
+    std::vector<size_t> off;
+    try {
+        off.assign((size_t)count + 1, 0);
+    } catch (...) {
+        return FEAST_ENOMEM;
+    }
     for (int i = 0; i < count; ++i) off[i + 1] = off[i] + (size_t)opts[i].m0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FEAST_ECUDA;
@@ -1144,7 +1160,14 @@ int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contou
         cudaStreamDestroy(st);
     };
     std::vector<std::thread> pool;
-    for (int t = 0; t < w; ++t) pool.emplace_back(worker, t);
+    try {
+        pool.reserve((size_t)w);
+        for (int t = 0; t < w; ++t) pool.emplace_back(worker, t);
+    } catch (...) {
+        // the workers already running take the whole batch; none running:
+        // nothing was solved
+        if (pool.empty()) return FEAST_ENOMEM;
+    }
     for (auto &th : pool) th.join();
     return worst.load();
 }
@@ -1208,7 +1231,18 @@ int feast_cgemm_tc(int64_t m, int64_t n, int64_t k, float alpha_re, float alpha_
                     make_float2(beta_re, beta_im), (cf *)C, ldc, sC, batch, sc, err);
 }
 
+static int grad_abs2_impl(feast_ctx *r, feast_ctx *l, void *gA, void *gB, int64_t ldg, double *L, int *count);
+
 int feast_grad_abs2(feast_ctx *r, feast_ctx *l, void *gA, void *gB, int64_t ldg, double *L, int *count)
+{
+    try {
+        return grad_abs2_impl(r, l, gA, gB, ldg, L, count);
+    } catch (...) {
+        return FEAST_ENOMEM;
+    }
+}
+
+static int grad_abs2_impl(feast_ctx *r, feast_ctx *l, void *gA, void *gB, int64_t ldg, double *L, int *count)
 {
     if (!r || !l || !gA || !gB || !L || !count) return FEAST_EINVAL;
     if (!r->done || !l->done) return FEAST_EINVAL;

@@ -68,8 +68,21 @@ using namespace feast;
 
 extern "C" {
 
+static int csr_rcm(int64_t n, const int64_t *a_rowptr, const int64_t *a_col, const int64_t *b_rowptr,
+                   const int64_t *b_col, int64_t *perm, int64_t *kl_out, int64_t *ku_out);
+
 int feast_csr_rcm(int64_t n, const int64_t *a_rowptr, const int64_t *a_col, const int64_t *b_rowptr,
                   const int64_t *b_col, int64_t *perm, int64_t *kl_out, int64_t *ku_out)
+{
+    try {   // no C++ exception may cross the C boundary
+        return csr_rcm(n, a_rowptr, a_col, b_rowptr, b_col, perm, kl_out, ku_out);
+    } catch (...) {
+        return FEAST_ENOMEM;
+    }
+}
+
+static int csr_rcm(int64_t n, const int64_t *a_rowptr, const int64_t *a_col, const int64_t *b_rowptr,
+                   const int64_t *b_col, int64_t *perm, int64_t *kl_out, int64_t *ku_out)
 {
     if (n < 1 || !a_rowptr || !a_col || !perm || !kl_out || !ku_out || (!b_rowptr) != (!b_col)) return FEAST_EINVAL;
     const int64_t *rp[2] = {a_rowptr, b_rowptr};
