@@ -56,3 +56,11 @@ def test_workspace_size_validation_without_gpu():
     assert nb.value > 16 * 200 * 200 * 16
     bad = fg.Options(300, 1, 1e-12, 1e-3, 50, 0, 5, 1e-14, None, 0, 0)  # m0 > n
     assert lib.feast_workspace_size(ctypes.byref(p), ctypes.byref(c), ctypes.byref(bad), ctypes.byref(nb)) == -1
+
+
+def test_last_cuda_error_without_gpu():
+    """The error-detail accessor is host-only: an empty string while no CUDA
+    call of this thread has failed."""
+    from paper_1404_1768_gb300 import load
+    lib = load()
+    assert lib.feast_last_cuda_error() == b""
