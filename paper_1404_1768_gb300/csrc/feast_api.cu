@@ -762,9 +762,10 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         // an eigenvalue gap (~1e-3 of max|C| and up): tau^2 / 1e-3 <= tol
         const double acc = fmax(kWarmAccMin, 1e-3 * eref);
         const double tau = fmin(1e-5, fmax(kWarmTauMin, sqrt(1e-3 * acc)));
-        // the tail QR deflates at 1e-3 of the acceptance tolerance (the
-        // double-single floor once the residuals approach 1e-12)
-        const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc, 1e-3 * acc};
+        // the tail QR deflates at 1e-3 of the acceptance tolerance, and at
+        // most at 1e-2 eps: its backward error (~ the deflation times
+        // max|C|) then stays far below the residual a stop needs
+        const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc, fmin(1e-3 * acc, 1e-2 * c->eps)};
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if ((e = zeig_warm(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->warm_work, c->qz_work, prm,
                            &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt)))
@@ -772,13 +773,12 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         if (!c->last_warm.accepted) FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_fail, 0, sizeof(int), s));
     }
     if (!c->last_warm.accepted) {
-        // a cold solve's eigenpairs are needed only to about the accuracy
-        // the iteration has reached: the QR deflates at 1e-2 of the warm
-        // solve's target (at most 1e-8, at least the double-single floor),
-        // so the early passes stop sweeping once their pairs are accurate
-        // far beyond their residuals
-        const double eref = (c->c_prev > 0 && c->e_prev > 0.0) ? c->e_prev : c->eta;
-        const double defl = fmin(1e-8, 1e-2 * fmax(kWarmAccMin, 1e-3 * eref));
+        // before any pair has been accepted the stop cannot fire at this
+        // pass (lines 13-14 need a fixed non-zero count), so its eigenpairs
+        // are needed only far beyond their residuals (>= eta): the QR
+        // deflates at 1e-8.  Any pass that may stop deflates at the
+        // double-single floor, so that its pairs reach eps.
+        const double defl = (c->c_prev > 0) ? 0.0 : 1e-8;
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if (rr && (e = triangularise_bt(c))) return e;
         if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
