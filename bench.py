@@ -1097,23 +1097,26 @@ def compare_arm(args, cfg):
     return 0
 
 
+def arm_for(cfg):
+    """The GPU arm that measures a workload (its configuration's kind)."""
+    if "batch" in cfg:
+        return batch_arm
+    for key, arm in (("grad", grad_arm), ("search", search_arm), ("compare", compare_arm),
+                     ("sparse", sparse_arm)):
+        if cfg.get(key):
+            return arm
+    return None     # the dense / banded pass of gpu_arm
+
+
 def main():
     args = parse()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
-    if "batch" in inputs.WORKLOADS[args.workload]:
-        return batch_arm(args, inputs.WORKLOADS[args.workload])
-    if inputs.WORKLOADS[args.workload].get("grad"):
-        return grad_arm(args, inputs.WORKLOADS[args.workload])
-    if inputs.WORKLOADS[args.workload].get("search"):
-        return search_arm(args, inputs.WORKLOADS[args.workload])
-    if inputs.WORKLOADS[args.workload].get("compare"):
-        return compare_arm(args, inputs.WORKLOADS[args.workload])
-    if inputs.WORKLOADS[args.workload].get("sparse"):
-        return sparse_arm(args, inputs.WORKLOADS[args.workload])
-    return gpu_arm(args)
+    cfg = inputs.WORKLOADS[args.workload]
+    arm = arm_for(cfg)
+    return arm(args, cfg) if arm else gpu_arm(args)
 
 
 if __name__ == "__main__":

@@ -57,3 +57,15 @@ def test_warm_products_roofline_uses_the_library_events():
     assert abs(dom["achieved"] - expect) < 1e-12 * expect
     assert abs(dom["kernel_ms_per_pass"] - 3.0) < 1e-12
     assert abs(dom["frac"] - dom["achieved"] / dom["peak"]) < 1e-12
+
+
+def test_every_workload_has_an_arm_and_a_reference():
+    """Each named workload dispatches to a GPU arm (or the dense/banded pass)
+    and its kind is one the reference arm knows."""
+    for name, cfg in inputs.WORKLOADS.items():
+        arm = bench.arm_for(cfg)
+        if arm is None:
+            assert "nx" in cfg or "n" in cfg, name
+            bench.Problem(dict(cfg, **({"nx": 24, "m0": 4} if "nx" in cfg else {"n": 40, "m0": 8})))
+        else:
+            assert callable(arm), name
