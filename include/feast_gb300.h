@@ -68,7 +68,10 @@ typedef enum { FEAST_OBLIQUE = 0, FEAST_RAYLEIGH_RITZ = 1 } feast_projection;
  *   kind = FEAST_DENSE : A, B are device n x n complex128, leading dim ld.
  *   kind = FEAST_BANDED: A, B are device complex128 in compact band storage,
  *                        entry (i, j) at row ku + i - j of column j,
- *                        ld >= kl + ku + 1.
+ *                        ld >= kl + ku + 1.  The band solves stage the
+ *                        band in shared memory, which bounds it: about
+ *                        kl + ku <= 597 with FEAST_FP64 and <= 1199 with
+ *                        FEAST_C64_REFINE (FEAST_EINVAL beyond).
  *   b_is_identity != 0 : B = I and the B pointer is ignored (may be NULL).
  * The matrices are read during feast_setup only (copied into the context). */
 typedef struct {

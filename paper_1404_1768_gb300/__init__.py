@@ -664,7 +664,9 @@ class SparseFeast(Feast):
     rows and columns are reordered by reverse Cuthill-McKee, both matrices
     are scattered into band storage on the device, and the banded path runs
     on (P A P^T, P B P^T) with the start block P Y.  eigs() returns the
-    eigenvectors in the original ordering."""
+    eigenvectors in the original ordering.  The reordered bandwidth must fit
+    the band solves (kl + ku up to ~600 in FP64, ~1200 in the precision
+    form); a wider one raises FeastError (EINVAL) at set-up."""
 
     def __init__(self, n: int, A, B, Y, **kw):
         for k in ("kind", "kl", "ku", "b_identity"):

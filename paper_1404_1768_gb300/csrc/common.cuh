@@ -427,6 +427,10 @@ int gb_form(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *A, cons
 template <typename T>
 int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int *piv, void *scratch,
              int *pivl, int *info, int *row);
+// the largest dynamic shared memory a band solve of elements of es bytes
+// needs (k_band.cu); it bounds the bandwidths the band path takes
+size_t gb_solve_smem_bytes(int64_t kl, int64_t ku, size_t es);
+constexpr size_t kSmemOptinMax = 227 * 1024;   // sm_100-family opt-in limit per CTA
 template <typename T>
 int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *F, const int *piv,
              int64_t nrhs, T *X, int64_t ldx, int64_t sX);

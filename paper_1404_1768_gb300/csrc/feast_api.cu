@@ -145,6 +145,11 @@ int validate(const feast_pencil *p, const feast_contour *c, const feast_options 
         return FEAST_EINVAL;
     if (o->prec != FEAST_FP64 && o->prec != FEAST_C64_REFINE) return FEAST_EINVAL;
     if (o->prec == FEAST_C64_REFINE && (o->max_refine < 0 || !(o->refine_tol > 0.0))) return FEAST_EINVAL;
+    // the band solves stage a band's worth of factor columns in shared
+    // memory: kl + ku up to ~600 (FP64) or ~1200 (precision form)
+    if (p->kind == FEAST_BANDED &&
+        gb_solve_smem_bytes(p->kl, p->ku, o->prec == FEAST_FP64 ? sizeof(zd) : sizeof(cf)) + 1024 > kSmemOptinMax)
+        return FEAST_EINVAL;
     if (p->kind == FEAST_DENSE && p->ld < p->n) return FEAST_EINVAL;
     if (!(c->a > 0.0) || (c->kind == FEAST_ELLIPSE && !(c->b > 0.0))) return FEAST_EINVAL;
     if (c->kind != FEAST_CIRCLE && c->kind != FEAST_ELLIPSE) return FEAST_EINVAL;

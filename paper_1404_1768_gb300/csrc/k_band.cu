@@ -541,14 +541,32 @@ int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int
     return FEAST_OK;
 }
 
+// Dynamic shared memory of the band solves (forward, backward) for elements
+// of es bytes: the staged factor columns and right-hand-side chunks.
+static size_t gb_fwd_smem(int64_t kl, size_t es)
+{
+    return ((size_t)(kl + 1 + GB_JC) * GB_CW + (size_t)GB_JC * kl) * es + GB_JC * sizeof(int) + 16;
+}
+static size_t gb_bwd_smem(int64_t kl, int64_t ku, size_t es)
+{
+    const int64_t kv = kl + ku;
+    return ((size_t)(kv + 1 + GB_JC) * GB_CW + (size_t)GB_JC * (kv + 1)) * es;
+}
+
+size_t gb_solve_smem_bytes(int64_t kl, int64_t ku, size_t es)
+{
+    const size_t f = gb_fwd_smem(kl, es), b = gb_bwd_smem(kl, ku, es);
+    return f > b ? f : b;
+}
+
 template <typename T>
 int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *F, const int *piv,
              int64_t nrhs, T *X, int64_t ldx, int64_t sX)
 {
-    const int64_t ldab = 2 * kl + ku + 1, sF = ldab * n, kv = kl + ku;
+    const int64_t ldab = 2 * kl + ku + 1, sF = ldab * n;
     dim3 g(cdiv(nrhs, GB_CW), q);
-    const size_t smf = ((size_t)(kl + 1 + GB_JC) * GB_CW + (size_t)GB_JC * kl) * sizeof(T) + GB_JC * sizeof(int) + 16;
-    const size_t smb = ((size_t)(kv + 1 + GB_JC) * GB_CW + (size_t)GB_JC * (kv + 1)) * sizeof(T);
+    const size_t smf = gb_fwd_smem(kl, sizeof(T));
+    const size_t smb = gb_bwd_smem(kl, ku, sizeof(T));
     FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_fwd<T>, smf));
     FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_bwd<T>, smb));
     k_gb_fwd<T><<<g, GB_ST, smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX);

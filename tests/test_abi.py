@@ -64,3 +64,19 @@ def test_last_cuda_error_without_gpu():
     from paper_1404_1768_gb300 import load
     lib = load()
     assert lib.feast_last_cuda_error() == b""
+
+
+def test_band_width_bounded_by_the_solve_staging():
+    """The band solves stage kl + ku factor columns in shared memory: wider
+    bands are refused at set-up (FEAST_EINVAL) rather than failing to
+    launch -- kl = ku = 298 is the FP64 limit, 599 the precision form's."""
+    import paper_1404_1768_gb300 as fg
+    lib = fg.load()
+    c = fg.Contour(1, 0.0, 0.0, 2.0, 1.0, 8, 1)
+    nb = ctypes.c_size_t(0)
+    for prec, ok_w, bad_w in ((0, 298, 299), (1, 599, 600)):
+        o = fg.Options(8, 1, 1e-12, 1e-3, 50, prec, 5, 1e-14, None, 0, 0)
+        for w, expect in ((ok_w, 0), (bad_w, -1)):
+            p = fg.Pencil(1, 5000, 1, 1, 2 * w + 1, w, w, 0)
+            assert lib.feast_workspace_size(ctypes.byref(p), ctypes.byref(c), ctypes.byref(o),
+                                            ctypes.byref(nb)) == expect, (prec, w)
