@@ -420,8 +420,10 @@ int feast_zqz_batched(int m, int batch, void *A, void *B, void *alpha, void *bet
  * requests return FEAST_EINVAL and queue no work.  No device memory is
  * allocated or freed.  All calls on a device share the array: calls that
  * overlap on the GPU (other streams or host threads) race and must be
- * serialised by the caller.  The first call on each device looks up the
- * array's address and should come before any stream capture.  Asynchronous. */
+ * serialised by the caller.  The first call in each CUDA context (per
+ * device; a new primary context after cudaDeviceReset, or a context the
+ * caller created, counts as new) looks up the array's address in that
+ * context and should come before any stream capture.  Asynchronous. */
 int feast_zqz_batched_noalloc(int m, int batch, void *A, void *B, void *alpha, void *beta,
                               void *V, int *status, void *stream);
 

@@ -22,9 +22,14 @@
 //     reads, so nothing has to be cleared between calls, but two calls
 //     whose work overlaps on the GPU (different streams, or different host
 //     threads) would overwrite each other's scratch: serialise them;
-//   * the first call on a device looks up the array's device address (with
-//     that device current) and remembers it; make that first call outside
-//     any stream capture.
+//   * the first call in a CUDA context looks up the array's device address
+//     (with that context current) and remembers it together with the
+//     context's unique ID; make that first call outside any stream capture.
+//     A later call in another context (a new primary context after
+//     cudaDeviceReset, or a context the caller created) sees a different ID
+//     and looks the address up again, so no call ever hands a kernel an
+//     address from a context that is gone.
+#include <cuda.h>
 #include <mutex>
 
 #include "common.cuh"
@@ -37,9 +42,33 @@ constexpr int MAX_DEVICES = 64;
 static __device__ __align__(256) double2 g_noalloc_scratch[NOALLOC_ELEMS];
 
 std::mutex g_noalloc_mutex;
-void *g_noalloc_ptr[MAX_DEVICES] = {nullptr};
 
-// Device address of the scratch array on the current device (host code may
+// The driver's context queries, reached through the runtime (the library
+// links the CUDA runtime only).
+typedef CUresult (*ctx_get_current_fn)(CUcontext *);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long *);
+ctx_get_current_fn g_ctx_get_current = nullptr;
+ctx_get_id_fn g_ctx_get_id = nullptr;
+
+struct ScratchAddr {
+    unsigned long long ctx_id;  // 0: none cached
+    void *ptr;
+};
+ScratchAddr g_noalloc_addr[MAX_DEVICES] = {};
+
+// ID of the context current on this thread (unique for the process's
+// lifetime, unlike the CUcontext handle, which may be reused), or 0.
+unsigned long long current_ctx_id()
+{
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    unsigned long long id = 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current context (host code may
 // not use the symbol itself as a device pointer).
 int noalloc_scratch(void **out)
 {
@@ -47,12 +76,30 @@ int noalloc_scratch(void **out)
     if (cudaGetDevice(&dev) != cudaSuccess) return FEAST_ECUDA;
     if (dev < 0 || dev >= MAX_DEVICES) return FEAST_EINVAL;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FEAST_ECUDA;
-        g_noalloc_ptr[dev] = p;
+    if (!g_ctx_get_current) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || !f1 ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f2)
+            return FEAST_ECUDA;
+        g_ctx_get_id = (ctx_get_id_fn)f2;
+        g_ctx_get_current = (ctx_get_current_fn)f1;
     }
-    *out = g_noalloc_ptr[dev];
+    unsigned long long id = current_ctx_id();
+    if (id != 0 && g_noalloc_addr[dev].ctx_id == id && g_noalloc_addr[dev].ptr) {
+        *out = g_noalloc_addr[dev].ptr;
+        return FEAST_OK;
+    }
+    // first call in this context: the lookup also makes the runtime's
+    // context current when none was yet
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FEAST_ECUDA;
+    id = current_ctx_id();
+    if (id == 0) return FEAST_ECUDA;
+    g_noalloc_addr[dev] = ScratchAddr{id, p};
+    *out = p;
     return FEAST_OK;
 }
 

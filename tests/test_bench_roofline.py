@@ -11,7 +11,8 @@ KEYS = {"bound", "achieved", "peak", "unit", "frac", "traffic", "phase", "share_
 
 def _infos(warm):
     base = dict(qz_sweeps=300, qz_phases=0 if warm else 5000, qz_warm=int(warm), qz_rows=60 if warm else 64,
-                qz_warm_resid=1e-14 if warm else 0.0, qz_warm_k=4 if warm else -1, refine_sweeps_max=0)
+                qz_warm_resid=1e-14 if warm else 0.0, qz_warm_k=4 if warm else -1, refine_sweeps_max=0,
+                ms_qz=5.0)
     return [dict(base) for _ in range(3)]
 
 
@@ -69,3 +70,46 @@ def test_every_workload_has_an_arm_and_a_reference():
             bench.Problem(dict(cfg, **({"nx": 24, "m0": 4} if "nx" in cfg else {"n": 40, "m0": 8})))
         else:
             assert callable(arm), name
+
+
+def test_oracle_sample_scales_every_term_cubically():
+    """The bounded oracle sample of the n = 4096 workload is the same
+    generator at n/4, m0/4 (same q), and its pass time is scaled by 4^3;
+    small dense and banded workloads are sampled as they are."""
+    prob = bench.Problem.__new__(bench.Problem)
+    prob.cfg = dict(inputs.WORKLOADS["dense_n4096_m1280_q32"], n=4096, m0=1280)
+    prob.band, prob.n, prob.m0, prob.q = False, 4096, 1280, 32
+    # (construct the sample's size only: the generator is not run here)
+    s = 1
+    while (prob.n / s) ** 2 * (prob.m0 / s) * prob.q > bench.ORACLE_PASS_WORK:
+        s *= 2
+    assert s == 4
+    small = bench.Problem(inputs.WORKLOADS["dense_n200_m64_q16"])
+    sp, sc = bench.oracle_sample(small)
+    assert sp is small and sc == 1
+
+
+def test_golden_oracle_run_parser_and_matching(tmp_path, monkeypatch):
+    """The stored oracle run is read back as written (eigenvalues, counts,
+    timings) and matched as a multiset: a permuted copy with one value moved
+    by 1e-9 relative shows exactly that error and the count."""
+    lam = [complex(0.5, -0.25), complex(-0.1, 0.7), complex(0.3, 0.3)]
+    gdir = tmp_path / "tests" / "golden"
+    gdir.mkdir(parents=True)
+    lines = ["# header", "host Some CPU", "threads 8", "setup_s 12.5",
+             "pass 1 0 2 0.000000e+00 40.0", "pass 2 3 1 1.0e-11 41.0",
+             "flag 1", "k 2", "count 3", "exact_count 3", "err 1.0e-11"]
+    lines += [f"eig {x.real:.17e} {x.imag:.17e} 1.0e-12" for x in lam]
+    (gdir / "wl_oracle.txt").write_text("\n".join(lines) + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    g = bench.golden_oracle_run("wl")
+    assert g["count"] == 3 and g["flag"] == 1 and g["k"] == 2 and g["threads"] == 8
+    assert [p["s"] for p in g["passes"]] == [40.0, 41.0]
+    assert list(g["lam"]) == lam
+    got = {"lam": [lam[2], lam[0] * (1 + 1e-9), lam[1]], "count": 3}
+    rep = bench.oracle_parity(got, g, 2)
+    assert rep["count_match"] and rep["within_1e-8"]
+    assert abs(rep["max_rel_eig_err_vs_oracle"] - 1e-9) < 1e-12
+    got["lam"][1] = lam[0] * (1 + 1e-7)
+    assert not bench.oracle_parity(got, g, 2)["within_1e-8"]
+    assert bench.golden_oracle_run("absent") is None
