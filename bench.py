@@ -1,24 +1,28 @@
 """Benchmark of the GB300 oblique-projection FEAST hot path.
 
-A step is one pass of GFEAST lines 5-17 (projection, projected QZ, Ritz
-residuals and stopping test, then the contour-integral subspace build with
-one shifted multi-right-hand-side solve per node, the node sum and the two
-orthonormalisations) on the dense prescribed-spectrum pencil
-n = 4096, m0 = 1280, 32 trapezoid nodes on |z| = 1, in the precision form
-(complex64 factors and solves on the tensor cores, the subspace build in
-defect form on the Ritz pairs, FP64-accurate tensor-core products, the
-projected problem solved warm from the second pass on; --prec fp64 for the
-plain FP64 path, which the precision form's line also times for
-comparison).  The LU set-up is timed separately.  One JSON line is printed
-by rank 0.
+A step is one whole GFEAST solve through the public API on the dense
+prescribed-spectrum pencil n = 4096, m0 = 1280, 32 trapezoid nodes on
+|z| = 1, in the precision form (complex64 factors and solves on the tensor
+cores, the subspace build in defect form on the Ritz pairs, FP64-accurate
+tensor-core products, the projected problem solved warm once its pairs have
+converged; --prec fp64 for the plain FP64 path, which the precision form's
+line also times on one whole solve for comparison): the pencil and start
+block from pinned host memory, set-up (lines 1-3), passes of lines 5-17
+until a stopping test fires, the eigenpairs back to the host.  value =
+GFEAST passes of the timed solves / CUDA-event time of exactly those passes
+(no pass after the stop); e2e = the same passes / wall time of the whole
+solves.  One JSON line is printed by rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                     [--workload NAME] [--prec c64r|fp64] [--no-fp64]
 
 --impl reference times the FP64 oracle (the plain CPU restatement of the
-method) on the host cores on a bounded sample of the same workload.
-N > 1 (launched by torchrun): independent replicas, one per GPU, no
-collective on the data path; value = iterations of all ranks / max time.
+method) on the host cores: whole oracle passes of a bounded sample of the
+same workload, scaled to it.
+N > 1 (launched by torchrun): one solve shared by N GPUs, node-sharded --
+each rank owns a range of the quadrature nodes (their factors and solves)
+and the partial quadrature sums are all-reduced with NCCL once per pass;
+value = passes / slowest rank's pass time (strong scaling).
 """
 from __future__ import annotations
 
@@ -43,12 +47,8 @@ from paper_1404_1768_gb300 import inputs  # noqa: E402
 METRIC = "FEAST iters/s & eigpairs/s vs plain FP64 GPU at resid≤1e-10; % TC/HBM peak"
 # FP64 pipe of a GB300: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# FP64 dense rate measured with torch.matmul (complex128) on this machine
-FP64_MEASURED_TFLOPS = 1.05
 # FP32 pipe: 152 SMs x 128 FFMA/clock x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# TF32 dense tensor rate measured with cuBLAS (torch.matmul in tf32) on this machine
-TF32_PEAK_TFLOPS = 1027.0
 
 
 def _measured(key, fallback):
@@ -57,6 +57,16 @@ def _measured(key, fallback):
             return float(json.load(f)[key])
     except Exception:
         return fallback
+
+
+# Dense peaks for the kernels timed inside a solve: the measured sustained
+# bf16 rate (MEASURED_PEAKS.json) times GB300's nominal ratio to bf16 (dense
+# per GPU: bf16 2250, tf32 1100, fp64 1.25 TFLOP/s).
+BF16_SUSTAINED_TFLOPS = _measured("bf16_tflops_sustained", 1700.0)
+TF32_PEAK_TFLOPS = BF16_SUSTAINED_TFLOPS * 1100.0 / 2250.0
+FP64_MEASURED_TFLOPS = BF16_SUSTAINED_TFLOPS * 1.25 / 2250.0
+TF32_SOURCE = "MEASURED_PEAKS.json bf16_tflops_sustained x nominal tf32/bf16 ratio (1100/2250)"
+FP64_SOURCE = "MEASURED_PEAKS.json bf16_tflops_sustained x nominal fp64/bf16 ratio (1.25/2250)"
 
 
 HBM_PEAK_GBS = _measured("hbm_gbs", 6800.0)
@@ -478,7 +488,8 @@ def reference_arm(args):
 def config_dict(prob, args, world):
     d = {"workload": args.workload}
     d.update(prob.describe())
-    d.update({"precision": args.prec, "parallelism": f"replicas{world}",
+    d.update({"precision": args.prec,
+              "parallelism": "one GPU" if world == 1 else f"node-sharded over {world} GPUs (NCCL all-reduce of U)",
               "l2": "inputs larger than L2 (per-node LU factors)"})
     return d
 
@@ -560,8 +571,8 @@ def solve_once(fg, torch, dev, stream, prob, host, kw, nvtx_pass=None):
     t_wall = time.perf_counter() - t0
     fe.close()
     pass_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(infos))]
-    return dict(setup_ms=setup_ms, infos=infos, pass_ms=pass_ms, k_stop=infos[-1]["k"], t_wall=t_wall,
-                res=res)
+    return dict(setup_ms=setup_ms, setup_info=fe.setup_info, infos=infos, pass_ms=pass_ms, k_stop=infos[-1]["k"],
+                t_wall=t_wall, res=res)
 
 
 
@@ -597,7 +608,7 @@ def roofline_phases(prob, args, ph, infos):
             "kernel": "k_gemm<double2> + triangular inverses of the warm Newton step (C = B~^-1 A~, "
                       "C' = Zh^H C Zh, V^-1 (C' V^), V^ G, C' Y') on the FP64 pipe; CUDA events around "
                       "exactly those launches",
-            "peak_source": "FP64 dense measured with cuBLAS on this pool (torch.matmul, complex128 / 4)",
+            "peak_source": FP64_SOURCE,
             "algorithmic_flops_per_pass": gfl / len(warm), "kernel_ms_per_pass": gms / len(warm),
             "warm_passes": len(warm), "cold_passes": len(cold),
             "tail_schur_rows": statistics.mean(i["qz_rows"] for i in warm)}
@@ -612,7 +623,7 @@ def roofline_phases(prob, args, ph, infos):
             "frac": ach / FP64_MEASURED_TFLOPS, "traffic": None,
             "kernel": "k_gemm<double2> (warm Newton step) on the FP64 pipe, with the tail Schur form inside "
                       "the same phase time",
-            "peak_source": "FP64 dense measured with cuBLAS on this pool (torch.matmul, complex128 / 4)",
+            "peak_source": FP64_SOURCE,
             "algorithmic_flops_per_pass": flops / len(warm), "warm_passes": len(warm), "cold_passes": len(cold)}
     elif cold:
         # cold projected solve: the multishift QR's rotations (phases x 32
@@ -703,12 +714,39 @@ def roofline(prob, args, ph):
                 "kernel": "subspace-build solves (k_gemm<double2> + k_trsv_diag), FP64 pipe",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "algorithmic_flops_per_pass": flops}
-    return {"bound": "tensor", "achieved": flops / t_solve / 1e12, "peak": TF32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": flops / t_solve / 1e12 / TF32_PEAK_TFLOPS, "traffic": None,
-            "kernel": "subspace-build complex64 solves (k_tc_cgemm tcgen05 kind::tf32 + k_trsv_diag + "
-                      "in-block k_gemm<float2>); flops counted once (not the 3 split products)",
-            "peak_source": "TF32 dense measured with cuBLAS on this pool (torch.matmul, tf32)",
+    pk = TF32_PEAK_TFLOPS / 3.0
+    return {"bound": "tensor", "achieved": flops / t_solve / 1e12, "peak": pk, "unit": "TFLOP/s",
+            "frac": flops / t_solve / 1e12 / pk, "traffic": None,
+            "kernel": "subspace-build complex64 solves, whole phase (k_tc_cgemm2 tcgen05 kind::tf32 + "
+                      "k_trsv_diag + in-block k_gemm<float2> + right-hand-side splits); complex flops of the "
+                      "solves",
+            "peak_source": TF32_SOURCE + ", / 3 (three TF32 products per FP32-accurate product)",
             "algorithmic_flops_per_pass": flops}
+
+
+def tc_gemm_rooflines(setup_infos, pass_infos):
+    """The tensor-core GEMM (k_tc_cgemm2) alone, from the library's CUDA
+    events around exactly its launches: the set-up LU's trailing updates
+    A22 -= L21 U12, and the off-block updates of each pass's shifted solves.
+    achieved = complex flops (8 per complex multiply-add) / launch time; the
+    peak is the TF32 peak / 3 -- three TF32 products (head x head, head x
+    tail, tail x head of the realified operands) make one FP32-accurate
+    product, so frac is the tensor pipe's share of its peak."""
+    pk = TF32_PEAK_TFLOPS / 3.0
+    out = []
+    for what, infos in (("LU trailing updates (set-up)", setup_infos), ("shifted-solve updates (passes)", pass_infos)):
+        ms = sum(i.get("ms_tc_gemm", 0.0) for i in infos)
+        fl = sum(i.get("tc_gemm_flop", 0.0) for i in infos)
+        if ms <= 0.0 or fl <= 0.0:
+            continue
+        ach = fl / (ms / 1e3) / 1e12
+        out.append({"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "phase": what,
+                    "kernel": "k_tc_cgemm2 (persistent, cta_group::2 256 x 256 tiles, tcgen05 kind::tf32, 3 "
+                              "split products); CUDA events around exactly its launches",
+                    "peak_source": TF32_SOURCE + ", / 3 (three TF32 products per FP32-accurate product)",
+                    "launch_ms_total": ms, "algorithmic_flops_total": fl, "runs": len(infos)})
+    return out
 
 
 def gpu_arm(args):
@@ -728,6 +766,13 @@ def gpu_arm(args):
     kw_prec = {}
     if args.prec == "c64r":
         kw_prec = dict(prec=fg.FEAST_C64_REFINE, refine_tol=1e-13, max_refine=4)
+    if world > 1:
+        # node-sharded (end of Section 4.3): each rank owns a contiguous range
+        # of the q quadrature nodes -- their factors and solves -- and the
+        # partial quadrature sums of line 16 are all-reduced with NCCL; lines
+        # 5-15 and 17 run on every rank.  One solve is shared by all ranks.
+        kw_prec = dict(kw_prec, node_range=fg.shard_nodes(prob.q, world, rank),
+                       collective=fg.dist_collective())
     stream = torch.cuda.current_stream()
     host = prob.pinned()
     h2d_bytes = sum(h.numel() * h.element_size() for h in host)
@@ -756,7 +801,7 @@ def gpu_arm(args):
     t_pass = sum(sum(r["pass_ms"]) for r in runs) / 1e3
     t_pass_max = max_over_ranks(t_pass, world, dev)
     t_region_max = max_over_ranks(t_region, world, dev)
-    value = world * passes / t_pass_max
+    value = passes / t_pass_max                 # one solve shared by all ranks
     infos = [it for r in runs for it in r["infos"]]
     warm = [(it, ms) for r in runs for it, ms in zip(r["infos"], r["pass_ms"]) if it["k"] >= 4]
     warm_rate = len(warm) / (sum(ms for _, ms in warm) / 1e3) if warm else None
@@ -772,9 +817,9 @@ def gpu_arm(args):
     counts = sum(x["res"]["count"] for x in runs)
     t_dev_solve = sum(x["setup_ms"] + sum(x["pass_ms"]) for x in runs) / 1e3
     d2h_bytes = statistics.mean((16 + 8) * x["res"]["count"] + 16 * n * x["res"]["count"] for x in runs)
-    e2e = {"value": world * passes / t_region_max, "unit": "iters/s",
+    e2e = {"value": passes / t_region_max, "unit": "iters/s",
            "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
-           "eigpairs_per_s": world * counts / t_region_max,
+           "eigpairs_per_s": counts / t_region_max,
            "what": "whole solves through the public API: pinned host pencil and start block -> device, "
                    "set-up, passes until the stop fires, eigenvalues, residuals and eigenvectors back to "
                    "the host; passes / wall time of exactly those solves"}
@@ -783,7 +828,8 @@ def gpu_arm(args):
     # timed the same way (the same pass indices 1..k_stop of its own run)
     fp64 = None
     if args.prec != "fp64" and not args.no_fp64:
-        r64 = solve_once(fg, torch, dev, stream, prob, host, {})
+        r64 = solve_once(fg, torch, dev, stream, prob, host,
+                         {k: v for k, v in kw_prec.items() if k in ("node_range", "collective")})
         rate64 = r64["k_stop"] / (sum(r64["pass_ms"]) / 1e3)
         fp64 = {"iters_per_s": rate64, "ms_per_iter": sum(r64["pass_ms"]) / r64["k_stop"],
                 "setup_ms": r64["setup_ms"], "k_stop": r64["k_stop"], "flag": r64["res"]["flag"],
@@ -791,7 +837,7 @@ def gpu_arm(args):
                 "pass_ms": [round(x, 1) for x in r64["pass_ms"]],
                 "phase_ms": {k: statistics.mean(i[k] for i in r64["infos"])
                              for k in ("ms_proj", "ms_qz", "ms_solve", "ms_qr")},
-                "speedup_passes": value / world / rate64,
+                "speedup_passes": value / rate64,
                 "speedup_whole_solve": r64["t_wall"] / statistics.mean(x["t_wall"] for x in runs),
                 "parity": parity_report(r64["res"], prob)}
         del r64
@@ -799,6 +845,7 @@ def gpu_arm(args):
     ph = {k: statistics.mean(i[k] for i in infos)
           for k in ("ms_proj", "ms_qz", "ms_solve", "ms_qr", "ms_refine")}
     roof, roof_kernels = roofline_dominant(prob, args, ph, infos)
+    roof_kernels += tc_gemm_rooflines([r["setup_info"] for r in runs], infos)
 
     if rank == 0:
         cb = None
@@ -809,7 +856,7 @@ def gpu_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_region_max / args.steps,
             "step": "one whole GFEAST solve (set-up, passes 1..k_stop, eigenpairs to the host); value = "
                     "GFEAST passes of the timed solves / CUDA-event time of exactly those passes",
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
             "dtype": "c128" if args.prec == "fp64" else "c64+c128",
             "data": "synthetic", "config": config_dict(prob, args, world),
             "setup_ms": setup_ms,

@@ -96,6 +96,26 @@ typedef struct {
     int rule;
 } feast_contour;
 
+/* Collective hook of a node-sharded run (one rank per GPU, each owning a
+ * range of quadrature nodes; see feast_options.node_begin).
+ *   op = FEAST_COLL_SUM  : buf <- the elementwise sum of every rank's buf
+ *                          (in place, on every rank);
+ *   op = FEAST_COLL_BCAST: buf <- rank 0's buf on every rank.
+ * buf is feast_options.collective_buf (device), ndoubles its used length.
+ * The library calls it from the thread of feast_setup / feast_iterate /
+ * feast_filter after enqueuing on `stream` the work that wrote buf; the
+ * hook must order its collective after that work and make the result
+ * visible to work enqueued on `stream` after it returns (an NCCL collective
+ * issued on or ordered with `stream`, or a synchronisation, a host copy,
+ * a host collective and a copy back).  Every rank makes the same sequence
+ * of calls.  Return 0, or non-zero on failure (the library then returns
+ * FEAST_ECUDA).  Uses: the partial sums of line 16 and of the first
+ * subspace (SUM, 2 n m0 doubles), the set-up's singular-pivot verdict
+ * (SUM, 1 double) and each pass's stopping flag (BCAST, 1 double: rank 0's
+ * flag is every rank's, so that all ranks stop at the same pass). */
+enum { FEAST_COLL_SUM = 0, FEAST_COLL_BCAST = 1 };
+typedef int (*feast_collective_fn)(void *user, int op, void *buf, int64_t ndoubles, void *stream);
+
 /* Iteration controls (GFEAST inputs, Section 4.3).
  *   m0        : subspace width t (>= the number of eigenvalues inside).
  *   Y0        : device n x m0 complex128 start block (leading dim n); the
@@ -134,6 +154,20 @@ typedef struct {
     int no_stop;
     int converged_only;
     int projection;
+    /* Node sharding (end of Section 4.3: the q shifted systems of eq. 4.2
+     * are independent).  node_begin = node_end = 0: this context owns every
+     * node.  Otherwise 0 <= node_begin < node_end <= q: it forms, factors
+     * and solves only nodes j in [node_begin, node_end) (the LU memory
+     * shrinks accordingly), its line-16 quadrature sum covers those nodes
+     * only, and collective (required) combines the ranks: see
+     * feast_collective_fn.  collective_buf: device, 256-byte aligned, at
+     * least 2 * n * m0 doubles, owned by the caller, handed to every
+     * collective call.  Every other step (lines 5-15, 17) runs on every
+     * rank on the summed subspace. */
+    int node_begin, node_end;
+    feast_collective_fn collective;
+    void *collective_user;
+    void *collective_buf;
 } feast_options;
 
 /* Per-pass report.  flag: 2 = continue, 1 = converged (line 13), 0 = no
@@ -157,6 +191,11 @@ typedef struct {
     double ms_warm_gemm;   /* device time of the warm solve's FP64 product
                               segments (GEMMs and triangular inverses) */
     double warm_gemm_flop; /* their algorithmic flops (complex MAC = 8) */
+    double ms_tc_gemm;     /* dense precision form: device time of the
+                              tensor-core GEMM launches alone -- the LU's
+                              trailing updates (feast_setup) or this pass's
+                              shifted solves' off-block updates (feast_iterate) */
+    double tc_gemm_flop;   /* their algorithmic flops (complex MAC = 8) */
 } feast_iter_info;
 
 typedef struct feast_ctx feast_ctx;

@@ -21,7 +21,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Feast", "load", "lib_path", "to_device_colmajor", "from_device_colmajor",
-           "zgetrf_batched", "zgetrs_batched", "zqz_batched", "FeastError"]
+           "zgetrf_batched", "zgetrs_batched", "zqz_batched", "FeastError", "shard_nodes", "dist_collective"]
 
 FEAST_DENSE, FEAST_BANDED = 0, 1
 FEAST_CIRCLE, FEAST_ELLIPSE = 0, 1
@@ -50,11 +50,18 @@ class Contour(C.Structure):
                 ("a", C.c_double), ("b", C.c_double), ("q", C.c_int), ("rule", C.c_int)]
 
 
+FEAST_COLL_SUM, FEAST_COLL_BCAST = 0, 1
+# int (*)(void *user, int op, void *buf, int64_t ndoubles, void *stream)
+COLLECTIVE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p)
+
+
 class Options(C.Structure):
     _fields_ = [("m0", C.c_int), ("Y0", C.c_void_p), ("eps", C.c_double), ("eta", C.c_double),
                 ("max_iter", C.c_int), ("prec", C.c_int), ("max_refine", C.c_int),
                 ("refine_tol", C.c_double), ("stream", C.c_void_p), ("no_stop", C.c_int),
-                ("converged_only", C.c_int), ("projection", C.c_int)]
+                ("converged_only", C.c_int), ("projection", C.c_int),
+                ("node_begin", C.c_int), ("node_end", C.c_int), ("collective", COLLECTIVE_FN),
+                ("collective_user", C.c_void_p), ("collective_buf", C.c_void_p)]
 
 
 class BatchItem(C.Structure):
@@ -69,7 +76,8 @@ class IterInfo(C.Structure):
                 ("refine_sweeps_max", C.c_int), ("bad_node", C.c_int), ("qz_sweeps", C.c_int),
                 ("qz_phases", C.c_int), ("qz_warm", C.c_int), ("qz_rows", C.c_int),
                 ("qz_warm_resid", C.c_double), ("qz_warm_k", C.c_int),
-                ("ms_warm_gemm", C.c_double), ("warm_gemm_flop", C.c_double)]
+                ("ms_warm_gemm", C.c_double), ("warm_gemm_flop", C.c_double),
+                ("ms_tc_gemm", C.c_double), ("tc_gemm_flop", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -200,15 +208,73 @@ def _check(st: int, where: str):
         raise FeastError(st, where, detail)
 
 
+def shard_nodes(q: int, world: int, rank: int):
+    """The contiguous range [j0, j1) of the q quadrature nodes that rank owns
+    when world ranks share one contour (sizes differ by at most one)."""
+    if not (0 <= rank < world) or q < world:
+        raise ValueError("need 0 <= rank < world <= q")
+    base, extra = divmod(q, world)
+    j0 = rank * base + min(rank, extra)
+    return j0, j0 + base + (1 if rank < extra else 0)
+
+
+def dist_collective(group=None):
+    """The collective hook of a node-sharded run over torch.distributed:
+    ``fn(op, buf, stream)`` sums buf over the ranks (FEAST_COLL_SUM) or
+    copies rank 0's buf to every rank (FEAST_COLL_BCAST), in place.  With a
+    NCCL group the collective is issued on the library's stream (ordered
+    after the work that wrote buf, and before what follows); with a CPU
+    group (gloo) the stream is synchronised, buf goes through host memory
+    and is copied back before the hook returns."""
+    import torch.distributed as dist
+    torch = _torch()
+
+    def fn(op, buf, stream):
+        backend = dist.get_backend(group)
+        if backend == "nccl":
+            ext = torch.cuda.ExternalStream(stream, device=buf.device) if stream else None
+            with torch.cuda.stream(ext) if ext is not None else _nullctx():
+                if op == FEAST_COLL_SUM:
+                    dist.all_reduce(buf, group=group)
+                else:
+                    dist.broadcast(buf, src=0, group=group)
+            return
+        if buf.is_cuda:
+            torch.cuda.synchronize(buf.device)
+        h = buf.cpu()
+        if op == FEAST_COLL_SUM:
+            dist.all_reduce(h, group=group)
+        else:
+            dist.broadcast(h, src=0, group=group)
+        buf.copy_(h)
+        if buf.is_cuda:
+            torch.cuda.synchronize(buf.device)
+    return fn
+
+
+class _nullctx:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
 class Feast:
     """GFEAST on the GPU (lines 1-3 at construction, one pass of lines 5-17 per
     ``iterate``).  A, B, Y: numpy arrays or torch tensors (rows x cols); they
-    are copied to column-major complex128 device buffers."""
+    are copied to column-major complex128 device buffers.
+
+    Node-sharded runs (one rank per GPU): ``node_range=(j0, j1)`` makes this
+    context own quadrature nodes j0..j1-1 only, and ``collective(op, buf,
+    stream)`` (e.g. ``dist_collective()``) combines the ranks' partial sums
+    and stopping flags; every rank constructs its Feast and calls
+    ``iterate`` in step."""
 
     def __init__(self, A, B, Y, *, contour_kind=0, rule=0, q=16, center=0j, a=1.0, b=0.0,
                  eps=1e-12, eta=1e-3, max_iter=50, prec=FEAST_FP64, no_stop=False, kind=0, kl=0,
                  ku=0, b_identity=False, device="cuda", stream=None, max_refine=5,
-                 refine_tol=1e-14, converged_only=False, projection=0):
+                 refine_tol=1e-14, converged_only=False, projection=0, node_range=None, collective=None):
         torch = _torch()
         self._lib = load()
         self.device = torch.device(device)
@@ -229,6 +295,30 @@ class Feast:
                              int(prec), int(max_refine), float(refine_tol),
                              _stream_ptr(stream), int(bool(no_stop)), int(bool(converged_only)),
                              int(projection))
+        self.node_range = None
+        if node_range is not None:
+            if collective is None:
+                raise ValueError("a node range needs a collective hook")
+            j0, j1 = int(node_range[0]), int(node_range[1])
+            self.node_range = (j0, j1)
+            # one n x m0 complex128 block, as doubles (caller-owned by this object)
+            self._coll_buf = torch.empty(2 * self.n * self.m0, dtype=torch.float64, device=self.device)
+            buf = self._coll_buf
+            user_fn = collective
+
+            def _hook(user, op, ptr, nd, strm):
+                try:
+                    user_fn(int(op), buf[: int(nd)], int(strm or 0))
+                    return 0
+                except Exception as ex:  # no exception may cross the C boundary
+                    self._coll_error = ex
+                    return 1
+
+            self._coll_cb = COLLECTIVE_FN(_hook)
+            self._opts.node_begin, self._opts.node_end = j0, j1
+            self._opts.collective = self._coll_cb
+            self._opts.collective_buf = buf.data_ptr()
+        self._coll_error = None
         nbytes = C.c_size_t(0)
         _check(self._lib.feast_workspace_size(C.byref(self._pencil), C.byref(self._contour),
                                               C.byref(self._opts), C.byref(nbytes)),
@@ -241,6 +331,8 @@ class Feast:
                                    C.byref(self._opts), self._ws.data_ptr(), self.workspace_bytes,
                                    C.byref(info))
         self.setup_info = info.as_dict()
+        if st != 0 and self._coll_error is not None:
+            raise FeastError(st, "feast_setup", f"collective hook: {self._coll_error!r}")
         _check(st, "feast_setup")
 
     def close(self):
@@ -256,7 +348,10 @@ class Feast:
 
     def iterate(self) -> dict:
         info = IterInfo()
-        _check(self._lib.feast_iterate(self._ctx, C.byref(info)), "feast_iterate")
+        st = self._lib.feast_iterate(self._ctx, C.byref(info))
+        if st != 0 and self._coll_error is not None:
+            raise FeastError(st, "feast_iterate", f"collective hook: {self._coll_error!r}")
+        _check(st, "feast_iterate")
         return info.as_dict()
 
     def run(self) -> list:
@@ -472,7 +567,8 @@ def solve_batch(problems, nworkers: int = 16, device="cuda"):
                         int(pr.get("rule", 0)))
         O[i] = Options(m0, Y.data_ptr(), float(pr.get("eps", 1e-12)), float(pr.get("eta", 1e-3)),
                        int(pr.get("max_iter", 50)), int(pr.get("prec", 0)),
-                       int(pr.get("max_refine", 5)), float(pr.get("refine_tol", 1e-14)), None, 0, 0)
+                       int(pr.get("max_refine", 5)), float(pr.get("refine_tol", 1e-14)), None, 0, 0, 0,
+                       0, 0)
     nbytes = int(lib.feast_batch_workspace_size(cnt, P, Cn, O, nworkers))
     if nbytes == 0:
         raise FeastError(-1, "feast_batch_workspace_size")

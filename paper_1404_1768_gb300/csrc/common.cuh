@@ -446,12 +446,22 @@ int z2ds(cudaStream_t s, int64_t count, const zd *x, float4 *y);
 int gb_residual_ds(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const float4 *Ads, int64_t ldin, int q,
                    const zd *z, int64_t m, const zd *RHS, const zd *X, float4 *Xds, zd *R, double *nrm2);
 
+// CUDA events around the tensor-core GEMM launches of one phase (the
+// set-up LU's trailing updates, or one pass's shifted solves) and their
+// algorithmic flops (complex multiply-add = 8): each launch of k_tc_cgemm2
+// records an event before and after itself while room is left.
+struct TcTimer {
+    static constexpr int kMax = 64;   // launches timed per phase
+    cudaEvent_t ev[2 * kMax];
+    int used;                         // events recorded
+    double flops;
+};
 // Tensor-core complex64 GEMM (k_tc.cu): C_b = beta C_b + alpha A_b X_b on
 // tcgen05 (kind::tf32, 3-pass split); scratch of tc_scratch_floats floats.
 size_t tc_scratch_floats(int64_t m, int64_t k, int64_t n, int batch);
 int tc_cgemm(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const cf *A, int64_t lda,
              int64_t sA, const cf *X, int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC,
-             int batch, float *scratch, int *err);
+             int batch, float *scratch, int *err, TcTimer *tt = nullptr);
 // The same product with A's realified planes made beforehand
 // (tc_prepare_A into tc_prepA_floats floats); scratch then only holds X's.
 size_t tc_prepA_floats(int64_t m, int64_t k, int batch);
@@ -459,7 +469,7 @@ int tc_prepare_A(cudaStream_t s, int64_t m, int64_t k, const cf *A, int64_t lda,
                  float *Aprep);
 int tc_cgemm_prepA(cudaStream_t s, int64_t m, int64_t n, int64_t k, cf alpha, const float *Aprep, const cf *X,
                    int64_t ldx, int64_t sX, cf beta, cf *C, int64_t ldc, int64_t sC, int batch, float *scratch,
-                   int *err);
+                   int *err, TcTimer *tt = nullptr);
 // FP64-accurate complex GEMM on the bf16 tensor cores by exact base-64
 // digit slicing (k_oz.cu): prepare digit planes of the left operand (rows)
 // and the right operand (columns), then C = beta C + alpha_c A B with
@@ -491,11 +501,12 @@ size_t getrf_tc_scratch_floats(int64_t n, int batch);
 // trsm_tc_cache_fill (trsm_tc_cache_floats floats), so that a solve only
 // prepares its right-hand sides.
 int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, int64_t ldf, int64_t sF, cf *X,
-               int64_t ldx, int64_t sX, float *scratch, int *tc_err, const float *cache = nullptr);
+               int64_t ldx, int64_t sX, float *scratch, int *tc_err, const float *cache = nullptr,
+               TcTimer *tt = nullptr);
 size_t trsm_tc_cache_floats(int64_t n, int batch);
 int trsm_tc_cache_fill(cudaStream_t s, int64_t n, int batch, const cf *F, int64_t ldf, int64_t sF, float *cache);
 int getrf_batched_tc(cudaStream_t s, int64_t n, int batch, cf *F, int64_t ldf, int64_t sF, int *piv,
-                     int *info, int *row, float *scratch, int *tc_err);
+                     int *info, int *row, float *scratch, int *tc_err, TcTimer *tt = nullptr);
 
 // Contour nodes / weights on the device.
 int contour_nodes(cudaStream_t s, const feast_contour *c, zd *z, zd *w);

@@ -36,7 +36,8 @@ struct feast_ctx {
     int kind;
     int64_t n, kl, ku;
     int b_identity;
-    int q, m0;          // m0: the active width (<= m0cap, the width the workspace holds)
+    int q, m0;          // q: nodes this context owns; m0: the active width (<= m0cap)
+    int qall, j0;       // all nodes of the contour; the first node this context owns
     int m0cap;
     feast_contour contour;
     double eps, eta;
@@ -45,7 +46,11 @@ struct feast_ctx {
     cudaStream_t s;
     // device arrays
     zd *A, *B;          // n x n copies (B null when identity)
-    zd *z, *w;          // nodes, weights
+    zd *z, *w;          // this context's nodes and weights (zall + j0, wall + j0)
+    zd *zall, *wall;    // every node and weight of the contour
+    feast_collective_fn coll;   // node-sharded run: combines the ranks (null: all nodes here)
+    void *coll_user;
+    double *coll_buf;
     zd *F;              // q x n x n factors
     int *piv, *perm;    // q x n
     zd *Xs;             // q x n x m0 per-node solutions
@@ -110,6 +115,7 @@ struct feast_ctx {
     double out_err;
     cudaEvent_t ev[8];
     GemmTimer gt;       // the warm solve's FP64 product segments
+    TcTimer tct;        // tensor-core GEMM launches: set-up LU updates, or one pass's solves
 };
 
 namespace {
@@ -157,6 +163,11 @@ int validate(const feast_pencil *p, const feast_contour *c, const feast_options 
     if (o->max_iter < 1 || !(o->eta > 0.0)) return FEAST_EINVAL;
     if (o->projection != FEAST_OBLIQUE && o->projection != FEAST_RAYLEIGH_RITZ) return FEAST_EINVAL;
     if (!p->A || (!p->B && !p->b_is_identity) || !o->Y0) return FEAST_EINVAL;
+    if (o->node_begin != 0 || o->node_end != 0) {
+        // a range of nodes: the other ranks' partial sums come through the hook
+        if (o->node_begin < 0 || o->node_end <= o->node_begin || o->node_end > c->q) return FEAST_EINVAL;
+        if (!o->collective || !o->collective_buf || ((uintptr_t)o->collective_buf & 255u)) return FEAST_EINVAL;
+    }
     return FEAST_OK;
 }
 
@@ -175,8 +186,10 @@ void carve(feast_ctx *c, Carver &cv)
     const size_t asz = (c->kind == FEAST_DENSE) ? n * n : (size_t)c->ldin * n;
     c->A = cv.take<zd>(asz);
     c->B = c->b_identity ? nullptr : cv.take<zd>(asz);
-    c->z = cv.take<zd>(q);
-    c->w = cv.take<zd>(q);
+    c->zall = cv.take<zd>((size_t)c->qall);
+    c->wall = cv.take<zd>((size_t)c->qall);
+    c->z = c->zall ? c->zall + c->j0 : nullptr;
+    c->w = c->wall ? c->wall + c->j0 : nullptr;
     if (c->kind == FEAST_BANDED) {
         const size_t fsz = q * (size_t)c->ldab * n;
         if (c->prec == FEAST_FP64) {
@@ -266,7 +279,13 @@ void fill_ctx_params(feast_ctx *c, const feast_pencil *p, const feast_contour *c
     c->ldin = c->kl + c->ku + 1;
     c->ldab = 2 * c->kl + c->ku + 1;
     c->b_identity = p->b_is_identity ? 1 : 0;
-    c->q = ct->q;
+    c->qall = ct->q;
+    const bool sharded = o->node_begin != 0 || o->node_end != 0;
+    c->j0 = sharded ? o->node_begin : 0;
+    c->q = sharded ? o->node_end - o->node_begin : ct->q;
+    c->coll = sharded ? o->collective : nullptr;
+    c->coll_user = sharded ? o->collective_user : nullptr;
+    c->coll_buf = sharded ? (double *)o->collective_buf : nullptr;
     c->m0 = o->m0;
     c->m0cap = o->m0;
     c->contour = *ct;
@@ -290,6 +309,38 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b)
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
     return ms;
+}
+
+// Sum of the timed launches' durations (ms) of a TcTimer whose events have completed.
+double tc_timer_ms(const TcTimer &t)
+{
+    double ms = 0.0;
+    for (int i = 0; i + 1 < t.used; i += 2) ms += ev_ms(t.ev[i], t.ev[i + 1]);
+    return ms;
+}
+
+// Node-sharded run: U (n x m0, this rank's partial quadrature sum over its
+// own nodes) <- the sum of every rank's partial sum, through the caller's
+// collective hook (a no-op when this context owns every node).
+int collect_nodes(feast_ctx *c, zd *U)
+{
+    if (!c->coll) return FEAST_OK;
+    const size_t nd = 2 * (size_t)c->n * (size_t)c->m0;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->coll_buf, U, sizeof(double) * nd, cudaMemcpyDeviceToDevice, c->s));
+    if (c->coll(c->coll_user, FEAST_COLL_SUM, c->coll_buf, (int64_t)nd, c->s)) return FEAST_ECUDA;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(U, c->coll_buf, sizeof(double) * nd, cudaMemcpyDeviceToDevice, c->s));
+    return FEAST_OK;
+}
+
+// One host scalar through the hook (FEAST_COLL_SUM or FEAST_COLL_BCAST);
+// synchronises the stream.
+int collect_scalar(feast_ctx *c, int op, double *v)
+{
+    FEAST_CUDA_TRY(cudaMemcpyAsync(c->coll_buf, v, sizeof(double), cudaMemcpyHostToDevice, c->s));
+    if (c->coll(c->coll_user, op, c->coll_buf, 1, c->s)) return FEAST_ECUDA;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(v, c->coll_buf, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(c->s));
+    return FEAST_OK;
 }
 
 // Y = B X (copy when B = I).  X, Y: n x m, leading dim n.
@@ -412,7 +463,9 @@ int solve_refine(feast_ctx *c, const zd *BV, double tol)
     cf *rhs32 = c->Xhi;  // node 0's slot: rounded right-hand side before its gather
     if ((e = z2c(s, nm, BV, rhs32))) return e;
     if ((e = gather_rows<cf>(s, n, m, (int)q, c->perm, rhs32, n, 0, c->C32, n, nm))) return e;
-    if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout, c->tcA))) return e;
+    if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout, c->tcA,
+                        &c->tct)))
+        return e;
     if ((e = c2z(s, all, c->C32, c->Xs))) return e;
     c->last_sweeps = 0;
     c->last_rel = -1.0;
@@ -474,7 +527,8 @@ int filter(feast_ctx *c, const zd *V, zd *Uout, double tol)
     int e;
     if ((e = apply_B(c, V, c->tmp, m))) return e;
     if ((e = solve_nodes(c, c->tmp, tol))) return e;
-    return znode_sum(c->s, n, m, c->q, c->w, c->Xs, n, n * m, Uout, n);
+    if ((e = znode_sum(c->s, n, m, c->q, c->w, c->Xs, n, n * m, Uout, n))) return e;
+    return collect_nodes(c, Uout);
 }
 
 // Line 16 of the precision form on the Ritz block X = c->Xr with Ritz
@@ -494,12 +548,15 @@ int filter_defect(feast_ctx *c, zd *Uout)
         if ((e = gb_solve<cf>(s, n, c->kl, c->ku, (int)q, c->Fb32, c->piv, m, c->C32, n, nm))) return e;
     } else {
         if ((e = defect_rhs(s, n, (int)m, (int)q, c->perm, c->dfx, c->C32, nm))) return e;
-        if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout, c->tcA))) return e;
+        if ((e = trsm_lu_tc(s, n, m, (int)q, c->F32, n, n * n, c->C32, n, nm, c->tcs, &c->st->timeout, c->tcA,
+                            &c->tct)))
+            return e;
     }
     c->last_sweeps = 0;
     c->last_rel = -1.0;
     c->ms_refine = 0.f;
-    return defect_sum(s, n, (int)m, (int)q, c->C32, nm, c->w, c->Xr, c->dfx, Uout);
+    if ((e = defect_sum(s, n, (int)m, (int)q, c->C32, nm, c->w, c->Xr, c->dfx, Uout))) return e;
+    return collect_nodes(c, Uout);
 }
 
 // V = Q R in place (n x m0).  Dense precision form: Cholesky QR twice on
@@ -573,6 +630,9 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
         if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; }
     for (int i = 0; i < GemmTimer::kMax; ++i)
         if (cudaEventCreate(&c->gt.ev[i]) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; }
+    if (c->kind == FEAST_DENSE && c->prec != FEAST_FP64)
+        for (int i = 0; i < 2 * TcTimer::kMax; ++i)
+            if (cudaEventCreate(&c->tct.ev[i]) != cudaSuccess) { feast_destroy(c); return FEAST_ECUDA; }
     const int64_t n = c->n;
     cudaStream_t s = c->s;
 #define TRY(x) do { int _r = (x); if (_r) { feast_destroy(c); return _r; } } while (0)
@@ -585,14 +645,14 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
         CTRY(cudaMemcpy2DAsync(c->B, rowsA * sizeof(zd), pencil->B, pencil->ld * sizeof(zd), rowsA * sizeof(zd), n,
                                cudaMemcpyDeviceToDevice, s));
     CTRY(cudaEventRecord(c->ev[0], s));
-    TRY(contour_nodes(s, &c->contour, c->z, c->w));
-    c->zw_host = (double *)malloc(sizeof(double) * 4 * (size_t)c->q);
+    TRY(contour_nodes(s, &c->contour, c->zall, c->wall));
+    c->zw_host = (double *)malloc(sizeof(double) * 4 * (size_t)c->qall);
     if (!c->zw_host) {
         feast_destroy(c);
         return FEAST_EINVAL;
     }
-    CTRY(cudaMemcpyAsync(c->zw_host, c->z, sizeof(zd) * c->q, cudaMemcpyDeviceToHost, s));
-    CTRY(cudaMemcpyAsync(c->zw_host + 2 * c->q, c->w, sizeof(zd) * c->q, cudaMemcpyDeviceToHost, s));
+    CTRY(cudaMemcpyAsync(c->zw_host, c->zall, sizeof(zd) * c->qall, cudaMemcpyDeviceToHost, s));
+    CTRY(cudaMemcpyAsync(c->zw_host + 2 * c->qall, c->wall, sizeof(zd) * c->qall, cudaMemcpyDeviceToHost, s));
     // z_j B - A and its LU factors (factored once, reused every pass)
     if (c->kind == FEAST_BANDED) {
         if (c->prec == FEAST_FP64) {
@@ -612,12 +672,32 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
         TRY(form_shifted32(s, n, c->q, c->A, c->B, n, c->z, c->F32));
         TRY(oz_prepare_rows(s, n, n, c->A, n, c->ozA));
         if (!c->b_identity) TRY(oz_prepare_rows(s, n, n, c->B, n, c->ozB));
+        c->tct.used = 0;
+        c->tct.flops = 0.0;
         TRY(getrf_batched_tc(s, n, c->q, c->F32, n, n * n, c->piv, &c->st->lu_info, &c->st->lu_row, c->tcs,
-                             &c->st->timeout));
+                             &c->st->timeout, &c->tct));
         TRY(trsm_tc_cache_fill(s, n, c->q, c->F32, n, n * n, c->tcA));
     }
     if (c->kind == FEAST_DENSE) TRY(zpiv_to_perm(s, n, c->q, c->piv, c->perm));
     CTRY(cudaEventRecord(c->ev[1], s));
+    if (c->coll) {
+        // every rank learns whether any rank's factors failed before the
+        // first collective of the subspace build
+        DevStatus hl;
+        CTRY(cudaMemcpyAsync(&hl, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        CTRY(cudaStreamSynchronize(s));
+        double bad = (hl.timeout ? 1000.0 : 0.0) + (hl.lu_info ? 1.0 : 0.0);
+        TRY(collect_scalar(c, FEAST_COLL_SUM, &bad));
+        if (bad > 0.0) {
+            if (info) {
+                memset(info, 0, sizeof(*info));
+                info->flag = 2;
+                info->bad_node = hl.lu_info ? hl.lu_info + c->j0 : 0;
+            }
+            feast_destroy(c);
+            return bad >= 1000.0 ? FEAST_ETIMEOUT : FEAST_ESINGULAR;
+        }
+    }
     // first subspace U = Q Y0, then U1, U2
     TRY(filter(c, (const zd *)opts->Y0, c->U, 1.0));
     TRY(orthonormalise(c, c->U));
@@ -629,8 +709,11 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
         memset(info, 0, sizeof(*info));
         info->ms_lu = ev_ms(c->ev[0], c->ev[1]);
         info->ms_solve = ev_ms(c->ev[1], c->ev[2]);
+        // the LU's trailing updates on the tensor cores (k_tc_cgemm2 launches only)
+        info->ms_tc_gemm = tc_timer_ms(c->tct);
+        info->tc_gemm_flop = c->tct.used >= 2 ? c->tct.flops : 0.0;
         info->flag = 2;
-        info->bad_node = hs.lu_info;
+        info->bad_node = hs.lu_info ? hs.lu_info + c->j0 : 0;
     }
     if (hs.lu_info) {
         feast_destroy(c);
@@ -660,7 +743,7 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
 // already used them, line 16 uses the new order.
 static int order_pairs(feast_ctx *c)
 {
-    const int m = c->m0, q = c->q;
+    const int m = c->m0, q = c->qall;   // the whole contour's filter rho
     const int64_t n = c->n;
     cudaStream_t s = c->s;
     std::vector<double> lam(2 * (size_t)m), res(m), key(m), lam2(2 * (size_t)m), res2(m);
@@ -828,6 +911,8 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
     // columns converge first).
     // (a pass at max_iter stops whatever the tests say: no next subspace)
     const bool last = c->k >= c->max_iter && !c->no_stop;
+    c->tct.used = 0;
+    c->tct.flops = 0.0;
     if (!last) {
         if (c->prec != FEAST_FP64) e = filter_defect(c, c->U);
         else e = filter(c, c->ritz_filter ? c->Xr : c->U1, c->U, 1.0);
@@ -841,6 +926,19 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
     DevStatus hs;
     FEAST_CUDA_TRY(cudaMemcpyAsync(&hs, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    if (c->coll) {
+        // node-sharded: lines 5-15 ran on every rank from the same summed
+        // subspace, but rounding may differ between ranks; all ranks stop
+        // (or fail) together, with rank 0's flag
+        double bad = (hs.timeout || hs.nonfinite || hs.qz_fail) ? 1.0 : 0.0;
+        if ((e = collect_scalar(c, FEAST_COLL_SUM, &bad))) return e;
+        if (bad > 0.0 && !(hs.timeout || hs.nonfinite || hs.qz_fail)) return FEAST_ENOCONV;
+        double f = (double)hs.flag;
+        if (bad == 0.0) {
+            if ((e = collect_scalar(c, FEAST_COLL_BCAST, &f))) return e;
+            hs.flag = (int)f;
+        }
+    }
     if (hs.timeout) return FEAST_ETIMEOUT;
     if (hs.nonfinite) return FEAST_ENONFINITE;
     if (hs.qz_fail) return FEAST_ENOCONV;
@@ -881,6 +979,9 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         for (int i = 0; i + 1 < c->gt.used; i += 2) gms += ev_ms(c->gt.ev[i], c->gt.ev[i + 1]);
         info->ms_warm_gemm = gms;
         info->warm_gemm_flop = c->gt.used >= 2 ? c->gt.flops : 0.0;
+        // this pass's shifted solves: the k_tc_cgemm2 launches only
+        info->ms_tc_gemm = tc_timer_ms(c->tct);
+        info->tc_gemm_flop = c->tct.used >= 2 ? c->tct.flops : 0.0;
     }
     return FEAST_OK;
 }
@@ -925,8 +1026,8 @@ int feast_get(const feast_ctx *c, int what, void *dst)
     case 6: src = c->lam; bytes = m * sizeof(zd); break;
     case 7: src = c->W; bytes = n * m * sizeof(zd); break;
     case 8: src = c->W + n * m; bytes = n * m * sizeof(zd); break;
-    case 9: src = c->z; bytes = (size_t)c->q * sizeof(zd); break;
-    case 10: src = c->w; bytes = (size_t)c->q * sizeof(zd); break;
+    case 9: src = c->zall; bytes = (size_t)c->qall * sizeof(zd); break;
+    case 10: src = c->wall; bytes = (size_t)c->qall * sizeof(zd); break;
     case 11: src = c->res; bytes = m * sizeof(double); break;
     case 12: src = c->sel; bytes = m * sizeof(int); break;
     default: return FEAST_EINVAL;
@@ -959,6 +1060,7 @@ int feast_search(feast_ctx *c, const void *Ypool, int npool, double alpha, int p
                  int *s0)
 {
     if (!c || !Ypool || !t || !s0) return FEAST_EINVAL;
+    if (c->coll) return FEAST_EINVAL;   // SEARCH runs on a context that owns every node
     const int64_t n = c->n;
     const int cap = c->m0cap;
     if (p < 1 || p > cap || npool < p || !(alpha > 1.0) || !(rank_tol > 0.0 && rank_tol < 1.0)) return FEAST_EINVAL;
@@ -1036,7 +1138,7 @@ int feast_search(feast_ctx *c, const void *Ypool, int npool, double alpha, int p
 int feast_cirr(feast_ctx *c, const void *Y, int h, int g, feast_iter_info *info)
 {
     if (!c || !Y || !info || h < 1 || g < 1) return FEAST_EINVAL;
-    if (c->projection != FEAST_RAYLEIGH_RITZ) return FEAST_EINVAL;
+    if (c->projection != FEAST_RAYLEIGH_RITZ || c->coll) return FEAST_EINVAL;
     const int64_t n = c->n, t = (int64_t)h * g;
     if (t > c->m0cap) return FEAST_EINVAL;
     cudaStream_t s = c->s;
@@ -1078,6 +1180,8 @@ void feast_destroy(feast_ctx *c)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     for (int i = 0; i < GemmTimer::kMax; ++i)
         if (c->gt.ev[i]) cudaEventDestroy(c->gt.ev[i]);
+    for (int i = 0; i < 2 * TcTimer::kMax; ++i)
+        if (c->tct.ev[i]) cudaEventDestroy(c->tct.ev[i]);
     free(c->zw_host);
     free(c);
 }
@@ -1108,6 +1212,7 @@ int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contou
                       const feast_options *opts, void *workspace, size_t workspace_bytes,
                       int nworkers, feast_batch_item *items, double *lambda, double *resid)
 {
+    if (count > 0 && opts && (opts->node_begin != 0 || opts->node_end != 0)) return FEAST_EINVAL;
     if (count <= 0 || !pencils || !contours || !opts || !workspace || !items || !lambda || nworkers <= 0)
         return FEAST_EINVAL;
     const size_t need = feast_batch_workspace_size(count, pencils, contours, opts, nworkers);

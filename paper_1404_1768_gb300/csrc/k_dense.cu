@@ -371,7 +371,7 @@ size_t getrf_tc_scratch_floats(int64_t n, int batch)
 }
 
 int getrf_batched_tc(cudaStream_t s, int64_t n, int batch, cf *F, int64_t ldf, int64_t sF, int *piv,
-                     int *info, int *row, float *scratch, int *tc_err)
+                     int *info, int *row, float *scratch, int *tc_err, TcTimer *tt)
 {
     if (n <= 0 || batch <= 0) return FEAST_OK;
     const cf mone = cx<cf>(-1, 0), one = cx<cf>(1, 0);
@@ -413,7 +413,7 @@ int getrf_batched_tc(cudaStream_t s, int64_t n, int batch, cf *F, int64_t ldf, i
         }
         // A22 -= L21 U12   (rest x rest, inner dimension nbo)
         if ((e = tc_cgemm(s, rest, rest, nbo, mone, F + kend + k0 * ldf, ldf, sF, F + k0 + kend * ldf, ldf, sF,
-                          one, F + kend + kend * ldf, ldf, sF, batch, scratch, tc_err)))
+                          one, F + kend + kend * ldf, ldf, sF, batch, scratch, tc_err, tt)))
             return e;
     }
     return FEAST_OK;
@@ -586,7 +586,7 @@ int trsm_tc_cache_fill(cudaStream_t s, int64_t n, int batch, const cf *F, int64_
 }
 
 int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, int64_t ldf, int64_t sF, cf *X,
-               int64_t ldx, int64_t sX, float *scratch, int *tc_err, const float *cache)
+               int64_t ldx, int64_t sX, float *scratch, int *tc_err, const float *cache, TcTimer *tt)
 {
     if (n <= 0 || nrhs <= 0 || batch <= 0) return FEAST_OK;
     size_t coff = 0;
@@ -609,11 +609,11 @@ int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, 
         if (kend < n) {
             if (cache) {
                 e = tc_cgemm_prepA(s, n - kend, nrhs, kend - k0, mone, cache + coff, X + k0, ldx, sX, one, X + kend,
-                                   ldx, sX, batch, scratch, tc_err);
+                                   ldx, sX, batch, scratch, tc_err, tt);
                 coff += tc_prepA_floats(n - kend, kend - k0, batch);
             } else {
                 e = tc_cgemm(s, n - kend, nrhs, kend - k0, mone, F + kend + k0 * ldf, ldf, sF, X + k0, ldx, sX, one,
-                             X + kend, ldx, sX, batch, scratch, tc_err);
+                             X + kend, ldx, sX, batch, scratch, tc_err, tt);
             }
             if (e) return e;
         }
@@ -635,11 +635,11 @@ int trsm_lu_tc(cudaStream_t s, int64_t n, int64_t nrhs, int batch, const cf *F, 
         if (k0 > 0) {
             if (cache) {
                 e = tc_cgemm_prepA(s, k0, nrhs, kend - k0, mone, cache + coff, X + k0, ldx, sX, one, X, ldx, sX,
-                                   batch, scratch, tc_err);
+                                   batch, scratch, tc_err, tt);
                 coff += tc_prepA_floats(k0, kend - k0, batch);
             } else {
                 e = tc_cgemm(s, k0, nrhs, kend - k0, mone, F + k0 * ldf, ldf, sF, X + k0, ldx, sX, one, X, ldx, sX,
-                             batch, scratch, tc_err);
+                             batch, scratch, tc_err, tt);
             }
             if (e) return e;
         }

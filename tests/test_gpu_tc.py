@@ -11,7 +11,13 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("m,n,k,batch", [(64, 128, 32, 1), (200, 70, 32, 3), (1000, 300, 96, 2),
-                                         (33, 5, 7, 1)])
+                                         (33, 5, 7, 1),
+                                         # more 256 x 256 tiles than clusters: every cluster takes
+                                         # several tiles, both tensor-memory accumulators in turn
+                                         (2048, 1280, 256, 2), (1536, 1000, 256, 3),
+                                         # ragged rows and columns in the last tiles, K not a
+                                         # multiple of 16
+                                         (700, 600, 250, 4)])
 def test_tc_cgemm_matches_reference(m, n, k, batch):
     import paper_1404_1768_gb300 as fg
     rng = np.random.default_rng(m + n + k)
