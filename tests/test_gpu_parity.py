@@ -282,13 +282,25 @@ def test_iterate_after_stop_is_refused():
 
 
 def test_rebound_flag_returns_previous_iterate():
-    """eps unreachable: the run ends by line 14 (previous iterate, flag 0) or
-    line 15; the GPU and the oracle agree on which."""
+    """eps unreachable: this pencil (the oracle pin's: n = 60, seed 5, 8
+    nodes) reaches the rounding floor and line 14 of GFEAST ends the run with
+    flag 0 on both sides; what the GPU returns is the previous pass's
+    selection -- the pairs that pass selected (line 10), its count and e(k)."""
     p = inputs.prescribed_pencil(60, 24, seed=5)
     cfg = dict(CFG1, q=8)
     g, o = _pair(p, cfg, eps=1e-30, max_iter=40)
-    hg, ho = g.run(), o.run()
+    prev = None
+    while True:
+        it = g.iterate()
+        if it["flag"] != 2:
+            break
+        lam, res, sel = g.get("lam"), g.get("res"), g.get("sel")
+        prev = (lam[sel], res[sel], it)
+    o.run()
     rg, ro = g.eigs(), o.result()
-    assert rg["flag"] == ro["flag"]
-    assert rg["count"] == ro["count"]
+    assert rg["flag"] == ro["flag"] == 0
+    assert rg["count"] == ro["count"] == prev[2]["count"] == len(prev[0])
+    assert rg["err"] == prev[2]["err"]
+    np.testing.assert_array_equal(np.sort_complex(rg["lam"]), np.sort_complex(prev[0]))
+    np.testing.assert_array_equal(np.sort(rg["res"]), np.sort(prev[1]))
     g.close(); o.close()

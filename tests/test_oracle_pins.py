@@ -384,6 +384,34 @@ def test_gfeast_max_iter_and_rebound_flags():
     fe.close()
 
 
+def test_gfeast_line14_returns_the_previous_iterate():
+    """Line 14 of Algorithm GFEAST: once the count is fixed, a pass whose
+    largest residual e(k) exceeds e(k-1) stops with flag 0 and returns the
+    previous iterate.  With an unreachable eps this n = 60 pencil (seed 5,
+    8 nodes) reaches the rounding floor and rebounds at pass 25.  A second
+    run ended by line 15 one pass earlier (max_iter = 24, flag -1) returns
+    that previous iterate as its own result, so the two outputs must be
+    identical -- eigenvalues, residuals, vectors, count and e(k)."""
+    p = inputs.prescribed_pencil(60, 24, seed=5)
+    kw = dict(q=8, center=0j, a=1.0, eps=1e-30)
+    fe = oracle.Feast(p.A, p.B, p.Y, max_iter=40, **kw)
+    h = fe.run()
+    r = fe.result()
+    fe.close()
+    k = len(h)                        # the pass at which line 14 fired
+    assert r["flag"] == 0 and k == 25
+    assert h[-1]["count"] == h[-2]["count"] > 0 and h[-1]["err"] > h[-2]["err"]
+    assert r["k"] == k - 1 and r["err"] == h[-2]["err"] and r["count"] == h[-2]["count"]
+    fe2 = oracle.Feast(p.A, p.B, p.Y, max_iter=k - 1, **kw)
+    h2 = fe2.run()
+    r2 = fe2.result()
+    fe2.close()
+    assert len(h2) == k - 1 and r2["flag"] == -1 and r2["k"] == k - 1
+    assert r2["count"] == r["count"] and r2["err"] == r["err"]
+    assert np.array_equal(r["lam"], r2["lam"]) and np.array_equal(r["res"], r2["res"])
+    assert np.array_equal(r["X"], r2["X"])
+
+
 def test_gfeast_banded_convection_diffusion_closed_form():
     """Banded pencil, B = I: the eigenvalues found inside an ellipse match the
     closed-form spectrum of the 5-point convection-diffusion operator
