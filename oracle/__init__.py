@@ -93,6 +93,7 @@ def _load():
             lib.or_free.argtypes = [P]
             lib.or_zqrcp.argtypes = [I, I, P, I, D, P, P, C.POINTER(I), P, I]
             lib.or_set_projection.argtypes = [P, I]
+            lib.or_set_search_literal.argtypes = [P, I]
             lib.or_zsvd_jacobi.argtypes = [I, I, P, I, P, I, P]
             lib.or_cirr.argtypes = [P, P, I, I, C.POINTER(I), P, P, P, P]
             lib.or_search.argtypes = [P, P, I, D, I, D, P, C.POINTER(I), C.POINTER(I)]
@@ -365,6 +366,11 @@ class Feast:
         res = np.zeros(self.m0); sel = np.zeros(self.m0, np.int32)
         _load().or_get_ritz_info(self._c, _p(res), _p(sel))
         return res, sel.astype(bool)
+
+    def set_search_literal(self, literal: bool):
+        """Read SEARCH's line 10 literally (U = U1 after a full-rank step)
+        instead of keeping the block as filtered columns."""
+        _load().or_set_search_literal(self._c, int(bool(literal)))
 
     def search(self, Ypool, alpha: float, p: int, rank_tol: float):
         """Algorithm SEARCH (Section 4.1) with the random columns supplied by

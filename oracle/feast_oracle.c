@@ -540,6 +540,7 @@ typedef struct or_ctx {
     int ldf;                             /* leading dim of each factor         */
     int m0;
     int projection;                      /* 0: oblique (test space U2), 1: Rayleigh-Ritz (U1) */
+    int search_literal;                  /* SEARCH line 10 read literally (U = U1 after a full-rank step) */
     zc *U1, *U2, *R2, *AU1, *BU1;        /* n x m0, n x m0, m0 x m0, n x m0 x2 */
     double eps, eta;
     int max_iter;
@@ -833,6 +834,13 @@ int or_set_projection(or_ctx *c, int projection)
     c->projection = projection;
     return OR_OK;
 }
+/* 1: SEARCH's line 10 read literally (U = U1, orthonormal, after a
+ * full-rank step); 0 (default): the block is kept as filtered columns. */
+int or_set_search_literal(or_ctx *c, int literal)
+{
+    c->search_literal = literal ? 1 : 0;
+    return OR_OK;
+}
 /* Replace U1 (and recompute U2 = orth(B U1)) -- lets a test drive one
  * filter step from a chosen subspace. */
 int or_set_U1(or_ctx *c, const zc *U1)
@@ -999,6 +1007,11 @@ int or_search(const or_ctx *c, const zc *Ypool, int npool, double alpha, int p, 
             *t = r;
             memcpy(U1, Q, sizeof(zc) * (size_t)n * r);
             break;
+        }
+        if (c->search_literal) {
+            /* line 10 as printed: U = U1, the orthonormal basis of the
+             * full-rank block, before the next filtered columns join it */
+            memcpy(U, Q, sizeof(zc) * (size_t)n * r);
         }
         have = sd;
         sd = (int)ceil(alpha * r);

@@ -435,3 +435,22 @@ def test_gfeast_banded_convection_diffusion_closed_form():
     assert r["flag"] == 1 and r["count"] == 5
     assert _match(r["lam"], lam[:5]) < 1e-9 * lam[4]
     fe.close()
+
+
+def test_count_fixed_only_once_nonzero_reading():
+    """Lines 13-14 of GFEAST compare c(k) with c(k-1), and the paper sets
+    c(0) = 0.  Read literally, a first pass with no pair below eta would end
+    the run at k = 1 with flag 1 and no pairs (c(1) = c(0) = 0 and
+    e(1) = 0 < eps).  On the n = 200 workload the first pass selects nothing
+    although 44 eigenvalues lie inside the circle -- why the count is taken as
+    fixed only once it is non-zero; with that reading the run finds all 44."""
+    cfg = inputs.WORKLOADS["dense_n200_m64_q16"]
+    p = inputs.prescribed_pencil(cfg["n"], cfg["m0"], seed=cfg["seed"])
+    fe = oracle.Feast(p.A, p.B, p.Y, contour_kind=0, rule=cfg["rule"], q=cfg["q"], center=cfg["center"],
+                      a=cfg["radius"], eps=cfg["eps"])
+    it = fe.iterate()
+    assert it["k"] == 1 and it["count"] == 0 and it["err"] == 0.0 and it["flag"] == 2
+    fe.run()
+    r = fe.result()
+    fe.close()
+    assert p.inside_count() == 44 and r["flag"] == 1 and r["count"] == 44

@@ -107,3 +107,36 @@ def test_search_matches_brute_force_rank():
     # the pivoted QR's |R_jj| and the singular values agree on a clean gap
     assert r["t"] == brute
     o.close()
+
+
+def test_line10_reading_scale():
+    """Algorithm SEARCH, line 10, prints U = U1 after a full-rank step: the
+    orthonormal basis (unit columns) then meets fresh filtered columns whose
+    norms are ~sqrt(s) (the filter keeps the inside part of a random column
+    whole), and line 9's rank test is relative to the largest |R_jj|.  With a
+    coarse threshold (rank_tol 0.1) and a start below the inside count, the
+    literal reading discards directions of U1 and stops at t = 25 for s = 41;
+    keeping the block as filtered columns (the span of U1 on the scale of
+    the columns that join it) finds all 41.  At the threshold the SEARCH
+    workload uses (1e-4, 32 nodes) both readings give t = s."""
+    n, cap, n_in = 300, 96, 41
+    p = inputs.gapped_pencil(n, cap, n_in, seed=11)
+    assert int(np.sum(np.abs(p.lam) < 1.0)) == n_in
+    pool = inputs.complex_normal(np.random.default_rng(12), (n, 400))
+
+    def t_of(literal, tol, p0):
+        o = oracle.Feast(p.A, p.B, p.Y, contour_kind=0, rule=0, q=32, center=0j, a=1.0)
+        o.set_search_literal(literal)
+        r = o.search(pool, 1.5, p0, tol)
+        o.close()
+        return r["t"]
+
+    assert t_of(False, 0.1, 8) == n_in
+    assert t_of(True, 0.1, 8) == 25
+    assert t_of(False, 1e-4, 8) == t_of(True, 1e-4, 8) == n_in
+    # the scale mismatch itself: unit columns against filtered ones
+    o = oracle.Feast(p.A, p.B, p.Y, contour_kind=0, rule=0, q=32, center=0j, a=1.0)
+    F = o.filter(np.hstack([pool[:, :20], np.zeros((n, cap - 20))]))[:, :20]
+    o.close()
+    norms = np.linalg.norm(F, axis=0)
+    assert np.median(norms) > 3.0 * np.sqrt(1.0) and np.median(norms) < 3.0 * np.sqrt(n_in)
