@@ -196,6 +196,11 @@ typedef struct {
                               trailing updates (feast_setup) or this pass's
                               shifted solves' off-block updates (feast_iterate) */
     double tc_gemm_flop;   /* their algorithmic flops (complex MAC = 8) */
+    int qz_cold_fp32;      /* the projected solve started cold: 1 = its Schur
+                              form came from the FP32 QR, polished by the
+                              FP64 Newton step and accepted; -1 = that was
+                              tried and rejected (the double-single QR ran);
+                              0 = not tried */
 } feast_iter_info;
 
 typedef struct feast_ctx feast_ctx;

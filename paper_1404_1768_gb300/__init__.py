@@ -77,7 +77,7 @@ class IterInfo(C.Structure):
                 ("qz_phases", C.c_int), ("qz_warm", C.c_int), ("qz_rows", C.c_int),
                 ("qz_warm_resid", C.c_double), ("qz_warm_k", C.c_int),
                 ("ms_warm_gemm", C.c_double), ("warm_gemm_flop", C.c_double),
-                ("ms_tc_gemm", C.c_double), ("tc_gemm_flop", C.c_double)]
+                ("ms_tc_gemm", C.c_double), ("tc_gemm_flop", C.c_double), ("qz_cold_fp32", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -326,6 +326,12 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
 // back-substitution; unit 2-norm columns.
 // scratch: m x m (T transposed, for contiguous row reads).
 int schur_vectors(cudaStream_t s, int m, const zd *T, zd *Y, double snorm, zd *scratch);
+// The same Schur form with the QR in plain FP32 (k_zeig32.cu): Q unitary
+// and T triangular to ~1e-6 relative -- a start for an FP64 polish.
+// work: schur_large_work_bytes_fp32(m) (= schur_large_work_bytes(m)).
+size_t schur_large_work_bytes_fp32(int m);
+int schur_large_fp32(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int *timeout, int *stats,
+                     double *hn_out, double defl);
 int normalise_cols(cudaStream_t s, int m, zd *V);
 
 // SEARCH (k_search.cu): out = sum_j Re(y_j^H u_j) over p columns; the
@@ -349,6 +355,9 @@ struct WarmParams {
     double tau;         // column of C counted converged: ||C[j+1:, j]|| <= tau max|C|
     double accept_tol;  // largest relative eigen-residual accepted
     double tail_defl;   // relative deflation tolerance of the tail QR (0: the floor)
+    int cold_fp32;      // 1: no converged block assumed -- the whole matrix
+                        // through the FP32 QR, its Schur vectors made unitary
+                        // in FP64 (BCGS2), then the Newton step
 };
 struct WarmResult {
     int accepted;   // 1: alpha, beta, V hold the eigenpairs

@@ -109,6 +109,7 @@ struct feast_ctx {
     int warm_ready;     // U1 comes from ordered Ritz vectors: line 6 may start warm
     WarmResult last_warm;
     int warm_tried;
+    int cold_fp32;      // this pass: 1 FP32 QR + Newton accepted, -1 tried and not accepted
     int k, c_prev, done, cur;
     double e_prev;
     int out_count, out_flag, out_k;
@@ -126,6 +127,10 @@ constexpr int kWarmMinM = 96;
 constexpr int kWarmMinTail = 65;     // the QR's own size range (m > 64)
 constexpr double kWarmTauMin = 1e-8; // converged column: strictly lower part <= tau max|C|
 constexpr double kWarmAccMin = 1e-12;  // the cold double-single QR's own backward error (2^-44 of ||H||)
+// A cold pass whose pairs are needed to at least this (relative eigen-
+// residual) tries the FP32 QR polished by the Newton step first: from an
+// FP32 Schur form (~1e-6 remainder) one Newton step reaches ~1e-10.
+constexpr double kColdFp32AccMin = 1e-8;
 
 struct Carver {
     char *base;
@@ -840,24 +845,39 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
     c->gt.used = 0;
     c->gt.flops = 0.0;
     c->warm_tried = c->warm_ready;
+    c->cold_fp32 = 0;
+    // the projected solve is held to 1e-3 of the accuracy already reached
+    // (eta before any pair is accepted)
+    const double eref = (c->c_prev > 0 && c->e_prev > 0.0) ? c->e_prev : c->eta;
+    const double acc = fmax(kWarmAccMin, 1e-3 * eref);
     if (c->warm_ready) {
         // the previous pass filtered its |rho|-ordered Ritz vectors: C is
         // block upper triangular up to a remainder of the size of its
-        // residuals; the projected solve is held to 1e-3 of the accuracy
-        // already reached (eta before any pair is accepted)
-        const double eref = (c->c_prev > 0 && c->e_prev > 0.0) ? c->e_prev : c->eta;
-        // a converged column's remainder enters the Newton step squared over
-        // an eigenvalue gap (~1e-3 of max|C| and up): tau^2 / 1e-3 <= tol
-        const double acc = fmax(kWarmAccMin, 1e-3 * eref);
+        // residuals.  A converged column's remainder enters the Newton step
+        // squared over an eigenvalue gap (~1e-3 of max|C| and up):
+        // tau^2 / 1e-3 <= tol
         const double tau = fmin(1e-5, fmax(kWarmTauMin, sqrt(1e-3 * acc)));
         // the tail QR deflates at 1e-3 of the acceptance tolerance, and at
         // most at 1e-2 eps: its backward error (~ the deflation times
         // max|C|) then stays far below the residual a stop needs
-        const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc, fmin(1e-3 * acc, 1e-2 * c->eps)};
+        const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc, fmin(1e-3 * acc, 1e-2 * c->eps), 0};
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if ((e = zeig_warm(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->warm_work, c->qz_work, prm,
                            &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt)))
             return e;
+        if (!c->last_warm.accepted) FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_fail, 0, sizeof(int), s));
+    }
+    if (!c->last_warm.accepted && !rr && c->warm_work && acc >= kColdFp32AccMin) {
+        // cold, but the pairs are needed only to acc: the Schur form of the
+        // whole matrix by the FP32 QR (its rotation chains are shorter),
+        // made exact by the FP64 Newton step -- whose error, the square of
+        // the FP32 remainder over an eigenvalue gap, is far below acc
+        const WarmParams prm{kWarmMinM, kWarmMinTail, kWarmTauMin, acc, 0.0, 1};
+        FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
+        if ((e = zeig_warm(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->warm_work, c->qz_work, prm,
+                           &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt)))
+            return e;
+        c->cold_fp32 = c->last_warm.accepted ? 1 : -1;
         if (!c->last_warm.accepted) FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_fail, 0, sizeof(int), s));
     }
     if (!c->last_warm.accepted) {
@@ -971,7 +991,8 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         info->refine_sweeps_max = c->prec == FEAST_FP64 ? 0 : c->last_sweeps;
         info->qz_sweeps = hs.qz_sweeps;
         info->qz_phases = hs.qz_phases;
-        info->qz_warm = c->last_warm.accepted;
+        info->qz_warm = c->last_warm.accepted && !c->cold_fp32;
+        info->qz_cold_fp32 = c->cold_fp32;
         info->qz_rows = c->last_warm.accepted ? c->last_warm.tail : (int)m;
         info->qz_warm_resid = c->last_warm.resid;
         info->qz_warm_k = c->warm_tried ? c->last_warm.k : -1;

@@ -215,10 +215,13 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     double hn = 0.0;
     for (int j = 0; j < m; ++j) hn = fmax(hn, h[m + j]);
     int k = 0;
-    while (k < m && h[k] <= prm.tau * hn) ++k;
+    if (!prm.cold_fp32)
+        while (k < m && h[k] <= prm.tau * hn) ++k;
     free(h);
     res->k = k;
-    if (k < m - prm.min_tail) {
+    if (prm.cold_fp32) {
+        k = 0;           // the whole matrix is the "tail"
+    } else if (k < m - prm.min_tail) {
         if (k < m / 4) return FEAST_OK;  // too little has converged: cold solve
     } else {
         k = m - prm.min_tail;
@@ -227,7 +230,20 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     // Schur form of the trailing block: C22 = Z T22 Z^H
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.S, sizeof(zd) * mb, C + k + (int64_t)k * m, sizeof(zd) * m, sizeof(zd) * mb,
                                      mb, cudaMemcpyDeviceToDevice, s));
-    if ((e = schur_large(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr, prm.tail_defl))) return e;
+    if (prm.cold_fp32) {
+        // FP32 QR, then Z made unitary to FP64 rounding (BCGS2 in FP64;
+        // Z moves by its FP32 error, ~1e-6), so that Zh^H C Zh below is a
+        // similarity of C and its lower part is that small
+        // (the orthonormalisation's scratch -- panel products, partial sums
+        // and its grid-barrier words -- is the QR's work area, free once the
+        // QR is done; an m x m block is too small for it below m ~ 160)
+        if (zorth_work_elems(mb, mb) * sizeof(zd) > zqz_work_bytes(m)) return FEAST_OK;
+        FEAST_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), s));
+        if ((e = schur_large_fp32(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr, 0.0))) return e;
+        if ((e = zorth(s, mb, mb, w.Z, mb, w.Yp, mb, (zd *)qz_work, timeout, nullptr))) return e;
+    } else if ((e = schur_large(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr, prm.tail_defl))) {
+        return e;
+    }
     // C' = Zh^H C Zh, Zh = diag(I_k, Z), into A (Bt as the row-block scratch)
     zd *Cq = A;
     FEAST_CUDA_TRY(cudaMemcpyAsync(Cq, C, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
@@ -240,10 +256,12 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(Cq + k, sizeof(zd) * m, Bt + k, sizeof(zd) * m, sizeof(zd) * mb, m,
                                      cudaMemcpyDeviceToDevice, s));
     // T^: C' with T22 from the QR in its trailing block (upper triangles are
-    // all that the eigenvector recurrence reads), into Cp
+    // all that the eigenvector recurrence reads), into Cp -- or C' itself
+    // after the FP32 QR, whose T22 is only FP32-accurate
     FEAST_CUDA_TRY(cudaMemcpyAsync(w.Cp, Cq, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
-    FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.Cp + k + (int64_t)k * m, sizeof(zd) * m, w.S, sizeof(zd) * mb,
-                                     sizeof(zd) * mb, mb, cudaMemcpyDeviceToDevice, s));
+    if (!prm.cold_fp32)
+        FEAST_CUDA_TRY(cudaMemcpy2DAsync(w.Cp + k + (int64_t)k * m, sizeof(zd) * m, w.S, sizeof(zd) * mb,
+                                         sizeof(zd) * mb, mb, cudaMemcpyDeviceToDevice, s));
     zd *Vh = Bt;  // V^, unit upper triangular
     if ((e = schur_vectors(s, m, w.Cp, Vh, hn, w.W))) return e;
     // F = V^{-1} (C' V^)
@@ -271,13 +289,15 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
         int bad;
         int pad;
     } hr{};
+    int qfail = 0;
     FEAST_CUDA_TRY(cudaMemcpyAsync(&hr, w.res, 16, cudaMemcpyDeviceToHost, s));
+    if (prm.cold_fp32) FEAST_CUDA_TRY(cudaMemcpyAsync(&qfail, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
     double worst;
     memcpy(&worst, &hr.r, sizeof(double));
     res->resid = worst;
     res->tail = mb;
-    if (hr.bad || !(worst <= prm.accept_tol)) return FEAST_OK;
+    if (hr.bad || qfail || !(worst <= prm.accept_tol)) return FEAST_OK;
     // Y = Zh Y', unit columns
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(V, sizeof(zd) * m, w.Yp, sizeof(zd) * m, sizeof(zd) * k, m,
                                      cudaMemcpyDeviceToDevice, s));

@@ -24,6 +24,10 @@
 
 #include "common.cuh"
 
+#ifndef FEAST_QR_FP32
+#define FEAST_QR_FP32 0
+#endif
+
 namespace feast {
 
 namespace {
@@ -168,6 +172,19 @@ struct cds {
     ds re, im;
 };
 
+#if FEAST_QR_FP32
+// Plain FP32 build (k_zeig32.cu): the same algorithm with every value a
+// single float (the low word stays zero), for projected problems whose
+// Schur form is polished afterwards in FP64 (the Newton step of k_warm.cu).
+__device__ __forceinline__ ds ds_make(float h, float l) { ds r; r.h = h + l; r.l = 0.f; return r; }
+__device__ __forceinline__ ds ds_qts(float a, float b) { return ds_make(a + b, 0.f); }
+__device__ __forceinline__ ds ds_add(ds x, ds y) { return ds_make(x.h + y.h, 0.f); }
+__device__ __forceinline__ ds ds_neg(ds x) { return ds_make(-x.h, 0.f); }
+__device__ __forceinline__ ds ds_sub(ds x, ds y) { return ds_make(x.h - y.h, 0.f); }
+__device__ __forceinline__ ds ds_mul(ds x, ds y) { return ds_make(x.h * y.h, 0.f); }
+__device__ __forceinline__ ds ds_from(double d) { return ds_make((float)d, 0.f); }
+__device__ __forceinline__ ds ds_rsqrt(ds x) { return ds_make(rsqrtf(x.h), 0.f); }
+#else
 __device__ __forceinline__ ds ds_make(float h, float l) { ds r; r.h = h; r.l = l; return r; }
 __device__ __forceinline__ ds ds_qts(float a, float b)   // |a| >= |b|
 {
@@ -207,6 +224,7 @@ __device__ __forceinline__ ds ds_rsqrt(ds x)
     ds corr = ds_mul(ds_mul(y, e), ds_make(0.5f, 0.f));
     return ds_add(y, corr);
 }
+#endif
 __device__ __forceinline__ cds cds_add(cds a, cds b) { cds r; r.re = ds_add(a.re, b.re); r.im = ds_add(a.im, b.im); return r; }
 __device__ __forceinline__ cds cds_sub(cds a, cds b) { cds r; r.re = ds_sub(a.re, b.re); r.im = ds_sub(a.im, b.im); return r; }
 __device__ __forceinline__ cds cds_mul(cds a, cds b)
@@ -374,9 +392,11 @@ __device__ __forceinline__ void chase_chunk(int m, float4 *H, int ld, int l, int
         const RotDS gr = make_rot_ds(x, y);
         __syncthreads();
         const int cs = (k == l) ? kr : kr - 1;
-        if (cs + t < nb) rot_left_ds(gr, blk[kr][cs + t], blk[kr + 1][cs + t]);
+        if (cs + t < nb) {
+            rot_left_ds(gr, blk[kr][cs + t], blk[kr + 1][cs + t]);
+            if (t == 0 && k > l) blk[kr + 1][kr - 1] = cds_zero();   // the bulge, annihilated exactly
+        }
         __syncthreads();
-        if (t == 0 && k > l) blk[kr + 1][kr - 1] = cds_zero();
         const int rl = ((k + 2 < ihi) ? k + 2 : ihi) - b0;
         if (t <= rl && t < nb) rot_right_ds(gr, blk[t][kr], blk[t][kr + 1]);
         if (t == 0) lrot[k - k0] = gr;
@@ -466,10 +486,13 @@ __device__ __forceinline__ cds cds_shfl(cds a, int src)
 // Schur vectors V: rows (k, k+1) of T from column c0, columns (k, k+1) of T
 // over rows 0 .. r1, columns (k, k+1) of V.  Whole CTA; ends synchronised.
 __device__ __forceinline__ void win_rot(const RotDS &gr, int k, int c0, int r1, int w, cds (*T)[NWP],
-                                        cds (*V)[NWP])
+                                        cds (*V)[NWP], bool zero_bulge = false)
 {
     const int t = threadIdx.x;
-    if (c0 + t < w) rot_left_ds(gr, T[k][c0 + t], T[k + 1][c0 + t]);
+    if (c0 + t < w) {
+        rot_left_ds(gr, T[k][c0 + t], T[k + 1][c0 + t]);
+        if (zero_bulge && t == 0) T[k + 1][c0] = cds_zero();   // the bulge, annihilated exactly
+    }
     __syncthreads();
     if (t <= r1) rot_right_ds(gr, T[t][k], T[t][k + 1]);
     if (t >= 64 && t - 64 < w) rot_right_ds(gr, V[t - 64][k], V[t - 64][k + 1]);
@@ -518,9 +541,7 @@ __device__ bool win_schur(int w, cds (*T)[NWP], cds (*V)[NWP], float tol_rel, fl
             else { x = T[k][k - 1]; y = T[k + 1][k - 1]; }
             const RotDS gr = make_rot_ds(x, y);
             __syncthreads();
-            win_rot(gr, k, (k == lo) ? k : k - 1, (k + 2 < hi) ? k + 2 : hi, w, T, V);
-            if (k > lo && threadIdx.x == 0) T[k + 1][k - 1] = cds_zero();
-            __syncthreads();
+            win_rot(gr, k, (k == lo) ? k : k - 1, (k + 2 < hi) ? k + 2 : hi, w, T, V, k > lo);
         }
     }
     __syncthreads();
@@ -754,6 +775,32 @@ __device__ void aed_apply(int m, float4 *H, float4 *Z, int ld, int kw, int w, co
     }
 }
 
+// Largest p in [1, ihi] whose subdiagonal entry H[p][p-1] is negligible
+// (|h| <= tol_rel (|H[p-1][p-1]| + |H[p][p]|) or |h| <= tol_abs), else 0.
+// The CTA tests QT candidates at a time from the bottom (the first hit of a
+// scan from ihi downwards).  Whole CTA, ihi uniform; every CTA finds the
+// same p from the same H.
+__device__ int scan_deflation(const float4 *H, int ld, int ihi, float tol_rel, float tol_abs)
+{
+    __shared__ int s_l;
+    for (int top = ihi; top >= 1; top -= QT) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_l = 0;
+        __syncthreads();
+        const int p = top - (int)threadIdx.x;
+        if (p >= 1) {
+            const float sub = cds_absf(ld_cds(H + p + (int64_t)(p - 1) * ld));
+            const float loc = cds_absf(ld_cds(H + (p - 1) + (int64_t)(p - 1) * ld)) +
+                              cds_absf(ld_cds(H + p + (int64_t)p * ld));
+            if (sub <= tol_rel * loc || sub <= tol_abs) atomicMax(&s_l, p);
+        }
+        __syncthreads();
+        const int v = s_l;
+        if (v > 0) return v;
+    }
+    return 0;
+}
+
 // Whole QR phase in double-single: all CTAs run the same control flow (every
 // decision is a function of values read after a grid barrier).  Active
 // blocks of at least MS_MIN rows take aggressive early deflation on their
@@ -779,14 +826,7 @@ __global__ void __launch_bounds__(QT, 1) k_hqr(int m, float4 *H, float4 *Z, int 
     const int gtid = blockIdx.x * QT + threadIdx.x, gthreads = gridDim.x * QT;
     int ihi = m - 1, iter = 0, total = 0;
     while (ihi > 0) {
-        int l = ihi;
-        while (l > 0) {
-            float sub = cds_absf(ld_cds(H + l + (int64_t)(l - 1) * ld));
-            float loc = cds_absf(ld_cds(H + (l - 1) + (int64_t)(l - 1) * ld)) +
-                        cds_absf(ld_cds(H + l + (int64_t)l * ld));
-            if (sub <= tol_rel * loc || sub <= tol_abs) break;
-            --l;
-        }
+        const int l = scan_deflation(H, ld, ihi, tol_rel, tol_abs);
         if (l == ihi) { --ihi; iter = 0; continue; }
         const int L = ihi - l + 1;
         int ns = 1;
@@ -1068,6 +1108,9 @@ __global__ void k_absmax(int64_t count, const zd *x, double *out)
 
 }  // namespace
 
+#if FEAST_QR_FP32
+namespace {   // the FP32 build's own copies of the one-CTA kernels
+#endif
 // ------------------------------------------------- small matrices: one CTA
 // Schur form of an m x m upper Hessenberg matrix, m <= SQ_MAX, by one CTA
 // with the whole matrix in shared memory: packed by columns (column j keeps
@@ -1335,6 +1378,15 @@ __global__ void __launch_bounds__(AR) k_apply_rotlog(int m, zd *__restrict__ Q, 
     }
 }
 
+#if FEAST_QR_FP32
+}  // namespace
+#endif
+
+#if FEAST_QR_FP32
+#define schur_large_work_bytes schur_large_work_bytes_fp32
+#define zeig_large_work_bytes zeig_large_work_bytes_fp32
+#define schur_large schur_large_fp32
+#endif
 size_t schur_large_work_bytes(int m)
 {
     // v (m) + w (m) + u (2m) complex, tau, absmax, rotations, barrier words,
@@ -1399,9 +1451,10 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     FEAST_CUDA_TRY(cudaMemsetAsync(timeout, 0, sizeof(int), s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
     if (hn_out) *hn_out = hn;
-    // deflation thresholds at double-single resolution (2^-44 relative)
-    // (or the caller's looser one)
-    const double tr = defl > 5.7e-14 ? defl : 5.7e-14;
+    // deflation thresholds at double-single resolution (2^-44 relative),
+    // or a few FP32 units in the FP32 build (or the caller's looser one)
+    const double floor_rel = FEAST_QR_FP32 ? 1e-6 : 5.7e-14;
+    const double tr = defl > floor_rel ? defl : floor_rel;
     float tol_rel = (float)tr, tol_abs = (float)(tr * (hn > 0.0 ? hn : 1e-300));
     if (m >= 2 && m <= SQ_MAX) {
         // one CTA, the matrix in shared memory; falls through to the grid
@@ -1459,6 +1512,7 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
 
 // A (m x m, overwritten), Bt (m x m upper triangular, overwritten by the
 // solve), alpha/beta (beta = 1), V (m x m unit eigenvectors).
+#if !FEAST_QR_FP32
 int zeig_large(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *work,
                int *fail, int *timeout, int *stats, double defl)
 {
@@ -1499,5 +1553,6 @@ int normalise_cols(cudaStream_t s, int m, zd *V)
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }
+#endif  // !FEAST_QR_FP32
 
 }  // namespace feast
