@@ -378,7 +378,8 @@ struct GemmTimer {
 // A, Bt as zeig_large (both overwritten whether accepted or not).  qz_work:
 // zeig_large_work_bytes(m) bytes.  gt (may be null): segment timer.
 int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *warm_work, void *qz_work,
-              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats, GemmTimer *gt = nullptr);
+              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats, GemmTimer *gt = nullptr,
+              const OzScratch *oz = nullptr);
 // Line 16 on Ritz pairs in defect form (k_defect.cu):
 // U = X rho(Lambda) + sum_j w_j M_j^{-1} (R D_j), R = A X - B X Lambda.
 struct DefectScratch {

@@ -872,10 +872,12 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         // whole matrix by the FP32 QR (its rotation chains are shorter),
         // made exact by the FP64 Newton step -- whose error, the square of
         // the FP32 remainder over an eigenvalue gap, is far below acc
+        // (its products on the digit-sliced tensor-core GEMM where the
+        // context has the scratch: ~48-bit per row and column, far beyond acc)
         const WarmParams prm{kWarmMinM, kWarmMinTail, kWarmTauMin, acc, 0.0, 1};
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if ((e = zeig_warm(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->warm_work, c->qz_work, prm,
-                           &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt)))
+                           &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt, orth_oz(c))))
             return e;
         c->cold_fp32 = c->last_warm.accepted ? 1 : -1;
         if (!c->last_warm.accepted) FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_fail, 0, sizeof(int), s));

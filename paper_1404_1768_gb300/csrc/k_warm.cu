@@ -122,6 +122,19 @@ __global__ void k_eig_resid(int m, const zd *__restrict__ W, const zd *__restric
     }
 }
 
+// E <- (E - I) / 2 in place (m x m): the first-order term of (I + E)^{-1/2}.
+__global__ void k_sub_identity_half(int m, zd *__restrict__ E)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        zd v = E[e];
+        if (i == j) v.x -= 1.0;
+        E[e] = zmake(0.5 * v.x, 0.5 * v.y);
+    }
+}
+
 // Column gather: Vout[:, i] = Vin[:, perm[i]] (rows x m, leading dim rows).
 __global__ void k_permute_cols(int64_t rows, int m, const int *__restrict__ perm, const zd *__restrict__ Vin,
                                zd *__restrict__ Vout)
@@ -181,7 +194,8 @@ int permute_cols(cudaStream_t s, int64_t rows, int m, const int *perm, const zd 
 }
 
 int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, void *warm_work, void *qz_work,
-              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats, GemmTimer *gt)
+              const WarmParams &prm, WarmResult *res, int *fail, int *timeout, int *stats, GemmTimer *gt,
+              const OzScratch *oz)
 {
     *res = WarmResult{};
     if (m < prm.min_m) return FEAST_OK;
@@ -197,10 +211,21 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
         return FEAST_OK;
     };
     int e;
+    // C = beta C + alpha op(A) B: the FP64 GEMM (tri: the triangular zeros it
+    // may skip), or -- with oz, for a pass whose pairs are needed only well
+    // above FP64 rounding -- the FP64-accurate digit-sliced tensor-core GEMM
+    auto mul = [&](int conj_a, int64_t M, int64_t N, int64_t K, zd alpha, const zd *Am, int64_t lda, const zd *Bm,
+                   int64_t ldb, zd beta, zd *Cm, int64_t ldc, int tri) -> int {
+        if (!oz) return zgemm_batched(s, conj_a, M, N, K, alpha, Am, lda, 0, Bm, ldb, 0, beta, Cm, ldc, 0, 1, tri);
+        int r;
+        if ((r = oz_prepare_rows(s, M, K, Am, lda, oz->rows, conj_a))) return r;
+        if ((r = oz_prepare_cols(s, K, N, Bm, ldb, oz->cols))) return r;
+        return oz_gemm(s, M, N, K, oz->rows, oz->cols, alpha, nullptr, 0, beta, Cm, ldc, oz->err);
+    };
     // C = B~^{-1} A~ (B~ = R2 is upper triangular), into Cp
     if ((e = mark(0.0))) return e;
     if ((e = tri_inverse(s, m, Bt, m, w.W, w.Ts))) return e;
-    if ((e = zgemm_batched(s, 0, m, m, m, one, w.W, m, 0, A, m, 0, zero, w.Cp, m, 0, 1, 1))) return e;
+    if ((e = mul(0, m, m, m, one, w.W, m, A, m, zero, w.Cp, m, 1))) return e;
     if ((e = mark(tri_inv + 4.0 * m3))) return e;
     const zd *C = w.Cp;
     k_col_stats<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, C, w.lower, w.cmax);
@@ -234,13 +259,17 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
         // FP32 QR, then Z made unitary to FP64 rounding (BCGS2 in FP64;
         // Z moves by its FP32 error, ~1e-6), so that Zh^H C Zh below is a
         // similarity of C and its lower part is that small
-        // (the orthonormalisation's scratch -- panel products, partial sums
-        // and its grid-barrier words -- is the QR's work area, free once the
-        // QR is done; an m x m block is too small for it below m ~ 160)
-        if (zorth_work_elems(mb, mb) * sizeof(zd) > zqz_work_bytes(m)) return FEAST_OK;
         FEAST_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), s));
         if ((e = schur_large_fp32(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr, 0.0))) return e;
-        if ((e = zorth(s, mb, mb, w.Z, mb, w.Yp, mb, (zd *)qz_work, timeout, nullptr))) return e;
+        // Z^H Z = I + E with |E| ~ 1e-6: Z (I - E / 2) is unitary to O(|E|^2)
+        // (one step of the series of (I + E)^{-1/2}), i.e. to ~1e-12
+        if ((e = mark(0.0))) return e;
+        if ((e = mul(1, mb, mb, mb, one, w.Z, mb, w.Z, mb, zero, w.Yp, mb, 0))) return e;
+        k_sub_identity_half<<<grid_for((size_t)mb * mb), 256, 0, s>>>(mb, w.Yp);
+        FEAST_LAUNCH_CHECK();
+        FEAST_CUDA_TRY(cudaMemcpyAsync(w.W, w.Z, sizeof(zd) * (size_t)mb * mb, cudaMemcpyDeviceToDevice, s));
+        if ((e = mul(0, mb, mb, mb, zmake(-1.0, 0.0), w.W, mb, w.Yp, mb, one, w.Z, mb, 0))) return e;
+        if ((e = mark(16.0 * (double)mb * mb * mb))) return e;
     } else if ((e = schur_large(s, mb, w.S, w.Z, qz_work, fail, timeout, stats, nullptr, prm.tail_defl))) {
         return e;
     }
@@ -248,10 +277,8 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     zd *Cq = A;
     FEAST_CUDA_TRY(cudaMemcpyAsync(Cq, C, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
     if ((e = mark(0.0))) return e;
-    if ((e = zgemm_batched(s, 0, m, mb, mb, one, C + (int64_t)k * m, m, 0, w.Z, mb, 0, zero, Cq + (int64_t)k * m, m, 0,
-                           1)))
-        return e;
-    if ((e = zgemm_batched(s, 1, mb, m, mb, one, w.Z, mb, 0, Cq + k, m, 0, zero, Bt + k, m, 0, 1))) return e;
+    if ((e = mul(0, m, mb, mb, one, C + (int64_t)k * m, m, w.Z, mb, zero, Cq + (int64_t)k * m, m, 0))) return e;
+    if ((e = mul(1, mb, m, mb, one, w.Z, mb, Cq + k, m, zero, Bt + k, m, 0))) return e;
     if ((e = mark(16.0 * (double)m * mb * mb))) return e;
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(Cq + k, sizeof(zd) * m, Bt + k, sizeof(zd) * m, sizeof(zd) * mb, m,
                                      cudaMemcpyDeviceToDevice, s));
@@ -266,10 +293,10 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     if ((e = schur_vectors(s, m, w.Cp, Vh, hn, w.W))) return e;
     // F = V^{-1} (C' V^)
     if ((e = mark(0.0))) return e;
-    if ((e = zgemm_batched(s, 0, m, m, m, one, Cq, m, 0, Vh, m, 0, zero, w.W, m, 0, 1, 2))) return e;
+    if ((e = mul(0, m, m, m, one, Cq, m, Vh, m, zero, w.W, m, 2))) return e;
     if ((e = tri_inverse(s, m, Vh, m, w.Cp, w.Ts))) return e;
     zd *F = V;
-    if ((e = zgemm_batched(s, 0, m, m, m, one, w.Cp, m, 0, w.W, m, 0, zero, F, m, 0, 1, 1))) return e;
+    if ((e = mul(0, m, m, m, one, w.Cp, m, w.W, m, zero, F, m, 1))) return e;
     if ((e = mark(8.0 * m3 + tri_inv))) return e;
     k_diag_lambda<<<cdiv(m, 128), 128, 0, s>>>(m, F, alpha, beta);
     FEAST_LAUNCH_CHECK();
@@ -279,8 +306,8 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     // Y' = V^ + V^ G, and its residual against C'
     FEAST_CUDA_TRY(cudaMemcpyAsync(w.Yp, Vh, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
     if ((e = mark(0.0))) return e;
-    if ((e = zgemm_batched(s, 0, m, m, m, one, Vh, m, 0, F, m, 0, one, w.Yp, m, 0, 1, 1))) return e;
-    if ((e = zgemm_batched(s, 0, m, m, m, one, Cq, m, 0, w.Yp, m, 0, zero, w.W, m, 0, 1))) return e;
+    if ((e = mul(0, m, m, m, one, Vh, m, F, m, one, w.Yp, m, 1))) return e;
+    if ((e = mul(0, m, m, m, one, Cq, m, w.Yp, m, zero, w.W, m, 0))) return e;
     if ((e = mark(12.0 * m3))) return e;
     k_eig_resid<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, w.W, w.Yp, alpha, hn, w.res);
     FEAST_LAUNCH_CHECK();
@@ -301,7 +328,7 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     // Y = Zh Y', unit columns
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(V, sizeof(zd) * m, w.Yp, sizeof(zd) * m, sizeof(zd) * k, m,
                                      cudaMemcpyDeviceToDevice, s));
-    if ((e = zgemm_batched(s, 0, mb, m, mb, one, w.Z, mb, 0, w.Yp + k, m, 0, zero, V + k, m, 0, 1))) return e;
+    if ((e = mul(0, mb, m, mb, one, w.Z, mb, w.Yp + k, m, zero, V + k, m, 0))) return e;
     if ((e = normalise_cols(s, m, V))) return e;
     res->accepted = 1;
     return FEAST_OK;
