@@ -147,6 +147,148 @@ __global__ void k_rank1_right2(int m, int cols, zd *C, zd *Q, int ld, const zd *
     }
 }
 
+// The whole Hessenberg reduction C <- Q^H C Q (Q <- Q P_0 P_1 ..., P_j =
+// I - tau v v^H from column j) in one cooperative launch, two grid barriers
+// per column instead of five launches: every CTA forms the same reflector
+// from column j (the same reduction in the same order, so the CTAs agree
+// bit for bit) and keeps v in shared memory; the CTAs' warps own columns of
+// the trailing block for the left update w = v^H C, C -= tau v w (read,
+// then rewrite, the same column); after a barrier the CTAs own 16-row
+// slabs of [C; Q] for the right update u = M v, M -= tau u v^H; column j
+// becomes (beta, 0, ..., 0).  The same arithmetic as the five-kernel form.
+constexpr int HG_T = 256;        // threads per CTA
+constexpr int HG_R = 16;         // rows per slab of the right update
+constexpr int HG_U = 8;          // loads in flight per thread
+__global__ void __launch_bounds__(HG_T) k_hess_grid(int m, zd *C, zd *Q, int ld, GridSync g)
+{
+    extern __shared__ zd hv[];                   // v (m - 1 entries at most)
+    __shared__ double red[HG_T / 32];
+    __shared__ zd part[HG_T / HG_R][HG_R];
+    __shared__ zd uslab[HG_R];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gwarp = blockIdx.x * (HG_T / 32) + wid, nwarps = gridDim.x * (HG_T / 32);
+    for (int j = 0; j + 2 < m; ++j) {
+        const int len = m - j - 1;
+        const zd *x = C + (j + 1) + (int64_t)j * ld;
+        // reflector (every CTA, same order)
+        double pn = 0.0;
+        for (int i = threadIdx.x; i < len; i += HG_T) pn += zabs2(__ldcg(x + i));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) pn += __shfl_xor_sync(0xffffffffu, pn, off);
+        if (lane == 0) red[wid] = pn;
+        __syncthreads();
+        double ss = 0.0;
+        for (int w = 0; w < HG_T / 32; ++w) ss += red[w];
+        const double nrm = sqrt(ss);
+        const zd x0 = __ldcg(x);
+        const double a0 = zabs(x0);
+        const zd ph = a0 > 0.0 ? zscale(x0, 1.0 / a0) : zmake(1.0, 0.0);
+        const zd beta = zscale(ph, -nrm);
+        const double vv = 2.0 * nrm * (nrm + a0);
+        const double tau = vv > 0.0 ? 2.0 / vv : 0.0;
+        for (int i = threadIdx.x; i < len; i += HG_T) hv[i] = (i == 0) ? zsub(x0, beta) : __ldcg(x + i);
+        __syncthreads();
+        // left update of the trailing block, one warp per column (HG_U
+        // loads in flight per lane: the steps are latency-bound otherwise)
+        for (int c = gwarp; c < len; c += nwarps) {
+            zd *col = C + (j + 1) + (int64_t)(j + 1 + c) * ld;
+            zd acc = zmake(0.0, 0.0);
+            for (int i0 = lane; i0 < len; i0 += 32 * HG_U) {
+                zd a[HG_U];
+#pragma unroll
+                for (int u = 0; u < HG_U; ++u) {
+                    const int i = i0 + 32 * u;
+                    a[u] = (i < len) ? __ldcg(col + i) : zmake(0.0, 0.0);
+                }
+#pragma unroll
+                for (int u = 0; u < HG_U; ++u) {
+                    const int i = i0 + 32 * u;
+                    if (i < len) zfma_conj(acc, hv[i], a[u]);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            }
+            const zd f = zscale(acc, -tau);
+            for (int i0 = lane; i0 < len; i0 += 32 * HG_U) {
+                zd a[HG_U];
+#pragma unroll
+                for (int u = 0; u < HG_U; ++u) {
+                    const int i = i0 + 32 * u;
+                    a[u] = (i < len) ? __ldcg(col + i) : zmake(0.0, 0.0);
+                }
+#pragma unroll
+                for (int u = 0; u < HG_U; ++u) {
+                    const int i = i0 + 32 * u;
+                    if (i < len) {
+                        zfma(a[u], hv[i], f);
+                        __stcg(col + i, a[u]);
+                    }
+                }
+            }
+        }
+        if (!grid_barrier(g)) return;
+        // right update of the stacked [C; Q] over columns j+1 .., 16-row slabs
+        const int tr = threadIdx.x % HG_R, tg = threadIdx.x / HG_R;
+        for (int slab = blockIdx.x; slab * HG_R < 2 * m; slab += gridDim.x) {
+            const int r = slab * HG_R + tr;
+            zd *M = (r < m) ? C : Q;
+            const int rr = (r < m) ? r : r - m;
+            constexpr int CG = HG_T / HG_R;          // column groups
+            zd acc = zmake(0.0, 0.0);
+            if (r < 2 * m)
+                for (int c0 = tg; c0 < len; c0 += CG * HG_U) {
+                    zd a[HG_U];
+#pragma unroll
+                    for (int u = 0; u < HG_U; ++u) {
+                        const int c = c0 + CG * u;
+                        a[u] = (c < len) ? __ldcg(M + rr + (int64_t)(j + 1 + c) * ld) : zmake(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < HG_U; ++u) {
+                        const int c = c0 + CG * u;
+                        if (c < len) zfma(acc, a[u], hv[c]);
+                    }
+                }
+            part[tg][tr] = acc;
+            __syncthreads();
+            if (tg == 0) {
+                zd s = part[0][tr];
+                for (int q = 1; q < HG_T / HG_R; ++q) s = zadd(s, part[q][tr]);
+                uslab[tr] = zscale(s, -tau);
+            }
+            __syncthreads();
+            if (r < 2 * m) {
+                const zd f = uslab[tr];
+                for (int c0 = tg; c0 < len; c0 += CG * HG_U) {
+                    zd a[HG_U];
+#pragma unroll
+                    for (int u = 0; u < HG_U; ++u) {
+                        const int c = c0 + CG * u;
+                        a[u] = (c < len) ? __ldcg(M + rr + (int64_t)(j + 1 + c) * ld) : zmake(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < HG_U; ++u) {
+                        const int c = c0 + CG * u;
+                        if (c < len) {
+                            zfma(a[u], f, zconj(hv[c]));
+                            __stcg(M + rr + (int64_t)(j + 1 + c) * ld, a[u]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // column j: (beta, 0, ..., 0) -- every CTA has read it
+        if (blockIdx.x == 0)
+            for (int i = threadIdx.x; i < len; i += HG_T)
+                __stcg(C + (j + 1 + i) + (int64_t)j * ld, (i == 0) ? beta : zmake(0.0, 0.0));
+        if (!grid_barrier(g)) return;
+    }
+}
+
 __global__ void k_eye(int m, zd *Q, int ld)
 {
     const int64_t total = (int64_t)m * m;
@@ -1422,8 +1564,31 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     float4 *Qds = Hds + (size_t)m * m;
     k_eye<<<cdiv((size_t)m * m, 256) > 2048 ? 2048 : cdiv((size_t)m * m, 256), 256, 0, s>>>(m, Q, m);
     FEAST_LAUNCH_CHECK();
-    // Hessenberg reduction C <- Q^H C Q
-    for (int j = 0; j + 2 < m; ++j) {
+    // Hessenberg reduction C <- Q^H C Q: one cooperative launch (the
+    // per-column kernels below when the grid form cannot be launched)
+    unsigned *hbar = (unsigned *)(((uintptr_t)(wv + m) + 15) & ~(uintptr_t)15);   // (w is unused by it)
+    int hgrid = 0;
+    if (m >= 3) {
+        int dev = 0, sms = 0, per = 0;
+        const size_t hsm = sizeof(zd) * (size_t)m;
+        FEAST_CUDA_TRY(cudaGetDevice(&dev));
+        FEAST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FEAST_CUDA_TRY(ensure_dyn_smem(k_hess_grid, hsm));
+        FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hess_grid, HG_T, hsm));
+        hgrid = (per >= 1) ? sms : 0;
+        const int need = (2 * m + HG_R - 1) / HG_R;     // right-update slabs
+        if (hgrid > need) hgrid = need;
+        if (hgrid > 0) {
+            FEAST_CUDA_TRY(cudaMemsetAsync(hbar, 0, 2 * sizeof(unsigned), s));
+            FEAST_CUDA_TRY(cudaMemsetAsync(timeout, 0, sizeof(int), s));
+            GridSync hg{hbar, hbar + 1, timeout};
+            int mm = m, ldq = m;
+            void *hargs[] = {&mm, &C, &Q, &ldq, &hg};
+            FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hess_grid, dim3(hgrid), dim3(HG_T), hargs, hsm, s));
+            FEAST_LAUNCH_CHECK();
+        }
+    }
+    for (int j = 0; hgrid == 0 && j + 2 < m; ++j) {
         const int len = m - j - 1;
         k_house<<<1, 256, 0, s>>>(m, j, C, m, v, tau);
         FEAST_LAUNCH_CHECK();
@@ -1446,10 +1611,13 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     k_absmax<<<64, 256, 0, s>>>((int64_t)m * m, C, hmax);
     FEAST_LAUNCH_CHECK();
     double hn = 0.0;
+    int htimeout = 0;
     FEAST_CUDA_TRY(cudaMemcpyAsync(&hn, hmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (hgrid > 0) FEAST_CUDA_TRY(cudaMemcpyAsync(&htimeout, timeout, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEAST_CUDA_TRY(cudaMemsetAsync(bar, 0, 16, s));
     FEAST_CUDA_TRY(cudaMemsetAsync(timeout, 0, sizeof(int), s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    if (htimeout) return FEAST_ETIMEOUT;   // the reduction's grid barrier gave up
     if (hn_out) *hn_out = hn;
     // deflation thresholds at double-single resolution (2^-44 relative),
     // or a few FP32 units in the FP32 build (or the caller's looser one)
