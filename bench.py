@@ -632,15 +632,18 @@ def roofline_phases(prob, args, ph, infos):
             "algorithmic_flops_per_pass": flops / len(warm), "warm_passes": len(warm), "cold_passes": len(cold)}
     elif cold:
         # cold projected solve: the multishift QR's rotations (phases x 32
-        # rotations x 2 m0 element pairs x ~172 FP32 ops of double-single
-        # arithmetic), over the whole cold projected-eigensolve phase time
-        qph = sum(i["qz_phases"] for i in cold)
-        ops = qph * 32 * 2 * m0 * 172.0
+        # rotations x 2 m0 element pairs x the FP32 operations of one
+        # element-pair rotation: ~172 in double-single arithmetic, ~24 in the
+        # FP32 build that the cold passes with a loose acceptance take), over
+        # the whole cold projected-eigensolve phase time
+        fp32 = [i for i in cold if i.get("qz_cold_fp32") == 1]
+        ops = sum(i["qz_phases"] * 32 * 2 * m0 * (24.0 if i.get("qz_cold_fp32") == 1 else 172.0) for i in cold)
         out["projected eigensolve"] = {
             "bound": "alu", "achieved": ops / (t_cold / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ops / (t_cold / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
-            "kernel": "k_hqr (double-single multishift QR with early deflation), latency-bound rotation chain; "
-                      "phase time of the cold passes (Hessenberg reduction and eigenvectors included)",
+            "kernel": ("k_hqr multishift QR with early deflation (FP32 build on %d of %d cold passes, then the FP64 "
+                       "Newton polish; double-single otherwise): a latency-bound rotation chain; phase time of the "
+                       "cold passes (Hessenberg reduction, Newton step and eigenvectors included)" % (len(fp32), len(cold))),
             "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz",
             "algorithmic_ops_per_pass": ops / len(cold), "warm_passes": len(warm), "cold_passes": len(cold)}
     if args.prec != "fp64":
