@@ -351,6 +351,11 @@ typedef struct {
     int count;       /* eigenpairs returned                                 */
     int k;           /* passes run                                          */
     double err;      /* Err of lines 13-15                                  */
+    double ms_setup; /* device time of the set-up (LU and first subspace)   */
+    double ms_pass;  /* device time of all passes (on this pencil's stream;
+                        other pencils' kernels run beside it)             */
+    double ms_solve; /* of which the subspace-build solves (line 16)        */
+    double ms_qz;    /* of which the projected eigensolves (line 6)         */
 } feast_batch_item;
 
 /* Device workspace for feast_solve_batch with nworkers concurrent pencils

@@ -66,7 +66,8 @@ class Options(C.Structure):
 
 class BatchItem(C.Structure):
     _fields_ = [("status", C.c_int), ("flag", C.c_int), ("count", C.c_int), ("k", C.c_int),
-                ("err", C.c_double)]
+                ("err", C.c_double), ("ms_setup", C.c_double), ("ms_pass", C.c_double),
+                ("ms_solve", C.c_double), ("ms_qz", C.c_double)]
 
 
 class IterInfo(C.Structure):
@@ -587,7 +588,8 @@ def solve_batch(problems, nworkers: int = 16, device="cuda"):
         c = it.count
         l = lam[2 * off[i]:2 * off[i] + 2 * c]
         out.append(dict(status=it.status, flag=it.flag, count=c, k=it.k, err=it.err,
-                        lam=l[0::2] + 1j * l[1::2], res=res[off[i]:off[i] + c].copy()))
+                        lam=l[0::2] + 1j * l[1::2], res=res[off[i]:off[i] + c].copy(),
+                        ms_setup=it.ms_setup, ms_pass=it.ms_pass, ms_solve=it.ms_solve, ms_qz=it.ms_qz))
     if st != 0:
         bad = [i for i, o in enumerate(out) if o["status"] != 0]
         raise FeastError(st, f"feast_solve_batch (pencils {bad[:8]})")

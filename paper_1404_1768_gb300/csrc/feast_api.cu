@@ -1268,11 +1268,17 @@ int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contou
             o.stream = st;
             o.no_stop = 0;
             feast_ctx *ctx = nullptr;
-            int e = feast_setup(&ctx, pencils + i, contours + i, &o, ws, slice, nullptr);
             feast_iter_info info;
             memset(&info, 0, sizeof(info));
+            int e = feast_setup(&ctx, pencils + i, contours + i, &o, ws, slice, &info);
+            it.ms_setup = info.ms_lu + info.ms_solve;
             while (e == FEAST_OK) {
                 e = feast_iterate(ctx, &info);
+                if (e == FEAST_OK) {
+                    it.ms_pass += info.ms_proj + info.ms_qz + info.ms_solve + info.ms_qr;
+                    it.ms_solve += info.ms_solve;
+                    it.ms_qz += info.ms_qz;
+                }
                 if (e == FEAST_OK && info.flag != 2) break;
             }
             if (e == FEAST_OK) {

@@ -690,6 +690,74 @@ __device__ bool win_schur(int w, cds (*T)[NWP], cds (*V)[NWP], float tol_rel, fl
     return true;
 }
 
+#if FEAST_QR_FP32
+// FP32 build: the same single-shift QR by one warp.  The window's rows and
+// columns (at most NW = 48) take one or two lanes each, and in FP32 a
+// rotation is a few operations per lane -- less than the CTA barriers the
+// whole-CTA form spends on each one; lanes order their shared-memory
+// updates with __syncwarp.  The other warps of the CTA wait at the caller's
+// barrier.
+__device__ bool win_schur_warp(int w, cds (*T)[NWP], cds (*V)[NWP], float tol_rel, float tol_abs)
+{
+    const int lane = threadIdx.x & 31;
+    int hi = w - 1, it = 0, tot = 0;
+    while (hi > 0) {
+        // lo: the largest p in [1, hi] with a negligible subdiagonal entry, else 0
+        int lo = 0;
+        for (int base = hi; base >= 1 && lo == 0; base -= 32) {
+            const int p = base - lane;
+            bool neg = false;
+            if (p >= 1) {
+                const float sub = cds_absf(T[p][p - 1]);
+                const float loc = cds_absf(T[p - 1][p - 1]) + cds_absf(T[p][p]);
+                neg = (sub <= tol_rel * loc || sub <= tol_abs);
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, neg);
+            if (b) lo = base - (__ffs(b) - 1);
+        }
+        __syncwarp();
+        if (lo > 0 && lane == 0) T[lo][lo - 1] = cds_zero();
+        __syncwarp();
+        if (lo == hi) { --hi; it = 0; continue; }
+        if (++tot > 40 * w) return false;
+        ++it;
+        cds sigma;
+        {
+            const cds h00 = T[hi - 1][hi - 1], h01 = T[hi - 1][hi], h10 = T[hi][hi - 1], h11 = T[hi][hi];
+            if (it % 11 == 10) {
+                const float a = cds_absf(h10);
+                sigma = h11;
+                sigma.re = ds_add(sigma.re, ds_make(a, 0.f));
+                sigma.im = ds_add(sigma.im, ds_make(0.5f * a, 0.f));
+            } else {
+                cds half = cds_scale(cds_add(h00, h11), ds_make(0.5f, 0.f));
+                cds det = cds_sub(cds_mul(h00, h11), cds_mul(h01, h10));
+                cds disc = csqrt_ds_approx(cds_sub(cds_mul(half, half), det));
+                cds r1 = cds_add(half, disc), r2 = cds_sub(half, disc);
+                sigma = (cds_absf(cds_sub(r1, h11)) < cds_absf(cds_sub(r2, h11))) ? r1 : r2;
+            }
+        }
+        __syncwarp();
+        for (int k = lo; k < hi; ++k) {
+            cds x, y;
+            if (k == lo) { x = cds_sub(T[k][k], sigma); y = T[k + 1][k]; }
+            else { x = T[k][k - 1]; y = T[k + 1][k - 1]; }
+            const RotDS gr = make_rot_ds(x, y);
+            __syncwarp();
+            const int c0 = (k == lo) ? k : k - 1;
+            for (int j = c0 + lane; j < w; j += 32) rot_left_ds(gr, T[k][j], T[k + 1][j]);
+            if (k > lo && lane == 0) T[k + 1][k - 1] = cds_zero();   // (lane 0 rotated that column)
+            __syncwarp();
+            const int r1 = (k + 2 < hi) ? k + 2 : hi;
+            for (int i = lane; i <= r1; i += 32) rot_right_ds(gr, T[i][k], T[i][k + 1]);
+            for (int i = lane; i < w; i += 32) rot_right_ds(gr, V[i][k], V[i][k + 1]);
+            __syncwarp();
+        }
+    }
+    return true;
+}
+#endif
+
 // Swap the adjacent diagonal entries p-1, p of the upper-triangular T (and
 // update V): the rotation that maps the eigenvector of T[p][p], (c, b - a),
 // onto e1.  Whole CTA.
@@ -807,7 +875,16 @@ __device__ void aed_window(int m, float4 *H, int ld, int l, int kw, int w, int n
     }
     if (t == 0) { sh->nd = 0; sh->ok = 1; }
     __syncthreads();
+#if FEAST_QR_FP32
+    if (t < 32) {
+        const bool r = win_schur_warp(w, sh->T, sh->V, tol_rel, tol_abs);
+        if (t == 0) sh->ok = r ? 1 : 0;
+    }
+    __syncthreads();
+    const bool ok = sh->ok != 0;
+#else
     const bool ok = win_schur(w, sh->T, sh->V, tol_rel, tol_abs);
+#endif
     const cds s = (kw > l) ? ld_cds(H + kw + (int64_t)(kw - 1) * ld) : cds_zero();
     const float sabs = cds_absf(s);
     int nd = 0;
