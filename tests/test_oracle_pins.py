@@ -454,3 +454,35 @@ def test_count_fixed_only_once_nonzero_reading():
     r = fe.result()
     fe.close()
     assert p.inside_count() == 44 and r["flag"] == 1 and r["count"] == 44
+
+
+def test_stored_n4096_oracle_run_matches_the_prescribed_spectrum():
+    """The stored converged oracle run of the n = 4096 workload
+    (tests/golden/dense_n4096_m1280_q32_oracle.txt, written by the script
+    beside it) against what the construction fixes: its eigenvalues are the
+    prescribed ones inside |z| < 1 (count exact, 1e-10 relative), every
+    residual of eq. 5.1 is below eps, and line 13 ended the run."""
+    g = {"lam": [], "res": []}
+    for line in open(os.path.join(GOLDEN, "dense_n4096_m1280_q32_oracle.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, _, rest = line.strip().partition(" ")
+        if key == "eig":
+            a, b, r = rest.split()
+            g["lam"].append(complex(float(a), float(b)))
+            g["res"].append(float(r))
+        elif key in ("flag", "k", "count", "exact_count"):
+            g[key] = int(rest)
+    cfg = inputs.WORKLOADS["dense_n4096_m1280_q32"]
+    p = inputs.prescribed_pencil(cfg["n"], cfg["m0"], seed=cfg["seed"])
+    ref = p.lam[np.abs(p.lam - cfg["center"]) < cfg["radius"]]
+    assert g["flag"] == 1 and g["count"] == g["exact_count"] == len(ref) == len(g["lam"])
+    pool = list(ref)
+    worst = 0.0
+    for x in g["lam"]:
+        d = np.abs(np.asarray(pool) - x)
+        j = int(np.argmin(d))
+        worst = max(worst, d[j] / abs(pool[j]))
+        pool.pop(j)
+    assert worst < 1e-10
+    assert max(g["res"]) < cfg["eps"]
