@@ -896,15 +896,27 @@ def batch_arm(args, cfg):
     prec = fg.FEAST_C64_REFINE if args.prec == "c64r" else fg.FEAST_FP64
     probs = [dict(A=p.A, B=p.B, Y=p.Y, contour_kind=0, rule=0, q=cfg["q"], center=p.center, a=p.radius,
                   eps=cfg["eps"], prec=prec, refine_tol=1e-13, max_refine=4) for p in rb.pencils]
+    # warm-up batches double as the schedule autotuner's trials: each times
+    # the whole batch at one candidate concurrency; the timed batches use
+    # the fastest
+    tuner = fg.BatchSchedule(candidates=sorted({16, 32, 64, args.nworkers}))
     for _ in range(args.warmup):
-        fg.solve_batch(probs[:8], nworkers=8)
+        nw = tuner.next()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fg.solve_batch(probs, nworkers=nw)
+        torch.cuda.synchronize()
+        tuner.record(nw, time.perf_counter() - t0)
+        torch.cuda.empty_cache()           # (each worker count sizes its own workspace)
+        log("batch schedule trial", nw, "workers", round(tuner.times[nw], 2), "s")
+    nworkers = tuner.best
     clocks = ClockSampler(local)
     clocks.start()
     times, outs = [], None
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        outs = fg.solve_batch(probs, nworkers=args.nworkers)
+        outs = fg.solve_batch(probs, nworkers=nworkers)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     clk = clocks.stop()
@@ -957,7 +969,9 @@ def batch_arm(args, cfg):
                 "config": {"workload": args.workload, "pencils": cfg["batch"],
                            "n_range": [cfg["n_lo"], cfg["n_hi"]], "q": cfg["q"],
                            "m0": "max(8, ceil(1.5 s / 8) * 8) per pencil", "precision": args.prec,
-                           "parallelism": "replicas1", "workers": args.nworkers},
+                           "parallelism": "replicas1", "workers": nworkers},
+                "schedule_autotune": {"trials_s": {str(k): round(v, 3) for k, v in tuner.times.items()},
+                                      "chosen_workers": nworkers},
                 "pencils_per_s": cfg["batch"] / t, "total_iterations": iters,
                 "parity": {"converged": cfg["batch"] - fails, "exact_counts": counts_ok,
                            "max_rel_eig_err_vs_exact": worst, "max_resid_eq_5_1": res_max},

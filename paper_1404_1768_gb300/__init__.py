@@ -21,7 +21,8 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Feast", "load", "lib_path", "to_device_colmajor", "from_device_colmajor",
-           "zgetrf_batched", "zgetrs_batched", "zqz_batched", "FeastError", "shard_nodes", "dist_collective"]
+           "zgetrf_batched", "zgetrs_batched", "zqz_batched", "FeastError", "shard_nodes", "dist_collective",
+           "BatchSchedule"]
 
 FEAST_DENSE, FEAST_BANDED = 0, 1
 FEAST_CIRCLE, FEAST_ELLIPSE = 0, 1
@@ -538,6 +539,35 @@ def zqz_batched_noalloc(A_list, B_list, stream=None):
     stv = st.cpu().numpy()
     return (al.cpu().numpy().reshape(batch, m), be.cpu().numpy().reshape(batch, m), Vs,
             int(stv[0]))
+
+
+class BatchSchedule:
+    """Schedule autotuner of solve_batch: the number of pencils solved
+    concurrently (one worker thread and CUDA stream each) is picked by
+    measurement.  ``next()`` gives the candidate to time next (each once, in
+    order), then the fastest; ``record(nworkers, seconds)`` enters a timing
+    of the same batch.  The small projected eigensolves are latency-bound
+    one-CTA kernels, so how many pencils share the GPU decides the
+    throughput; the best count depends on the batch's size mix."""
+
+    def __init__(self, candidates=(16, 32, 64)):
+        self.candidates = [int(c) for c in candidates]
+        self.times = {}
+
+    def next(self) -> int:
+        for c in self.candidates:
+            if c not in self.times:
+                return c
+        return self.best
+
+    def record(self, nworkers: int, seconds: float):
+        self.times[int(nworkers)] = min(float(seconds), self.times.get(int(nworkers), float("inf")))
+
+    @property
+    def best(self) -> int:
+        if not self.times:
+            return self.candidates[0]
+        return min(self.times, key=lambda c: self.times[c])
 
 
 def solve_batch(problems, nworkers: int = 16, device="cuda"):

@@ -113,3 +113,19 @@ def test_golden_oracle_run_parser_and_matching(tmp_path, monkeypatch):
     got["lam"][1] = lam[0] * (1 + 1e-7)
     assert not bench.oracle_parity(got, g, 2)["within_1e-8"]
     assert bench.golden_oracle_run("absent") is None
+
+
+def test_batch_schedule_autotuner_picks_the_fastest_trial():
+    """The ragged batch's schedule autotuner times each candidate worker
+    count once, in order, then keeps the fastest."""
+    import paper_1404_1768_gb300 as fg
+    t = fg.BatchSchedule(candidates=(16, 32, 64))
+    seen = []
+    for secs in (40.0, 30.0, 35.0):
+        nw = t.next()
+        seen.append(nw)
+        t.record(nw, secs)
+    assert seen == [16, 32, 64]
+    assert t.best == 32 and t.next() == 32
+    t.record(32, 50.0)            # a slower repeat keeps the best time
+    assert t.times[32] == 30.0 and t.best == 32

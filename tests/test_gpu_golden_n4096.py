@@ -32,7 +32,6 @@ def _read_golden(path):
     return out
 
 
-@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="stored oracle run not written yet")
 def test_precision_form_n4096_matches_the_stored_oracle_run():
     import paper_1404_1768_gb300 as fg
     gold = _read_golden(GOLDEN)
