@@ -43,7 +43,8 @@ extern "C" {
 #define FEAST_ECUDA      -3   /* a CUDA runtime call or kernel launch failed      */
 #define FEAST_ESINGULAR  -4   /* a shifted matrix z_j B - A has an exact zero pivot */
 #define FEAST_ENONFINITE -5   /* NaN or Inf reached a residual                    */
-#define FEAST_ETIMEOUT   -6   /* a bounded device wait gave up                    */
+#define FEAST_ETIMEOUT   -6   /* a bounded device wait gave up (after 4 s of device
+                                 time); feast_last_cuda_error names the wait      */
 #define FEAST_ENOCONV    -7   /* the projected QZ hit its iteration cap, two runs disagree, or SEARCH
                                   outgrew the workspace's width */
 #define FEAST_EDONE      -8   /* feast_iterate called after the algorithm stopped */
@@ -334,8 +335,10 @@ const char *feast_strerror(int status);
  * batch, column-major interleaved complex64, A m x k, X k x n.  This is the
  * update product of the complex64 factorization and solves of eq. 4.2 in the
  * precision form.  scratch: device, >= feast_cgemm_tc_scratch_bytes bytes
- * (operand copies in the tensor-core layout).  err: device int32, set to 1
- * if a bounded pipeline wait gave up.  Asynchronous. */
+ * (operand copies in the tensor-core layout).  err: device int32, set
+ * non-zero (a bit per wait site: 0x40 loads, 0x80 MMA issue, 0x100 epilogue,
+ * 0x200 final drain) if a bounded pipeline wait (4 s of device time) gave
+ * up.  Asynchronous. */
 size_t feast_cgemm_tc_scratch_bytes(int64_t m, int64_t n, int64_t k, int batch);
 int feast_cgemm_tc(int64_t m, int64_t n, int64_t k, float alpha_re, float alpha_im, const void *A,
                    int64_t lda, int64_t sA, const void *X, int64_t ldx, int64_t sX, float beta_re,
@@ -384,9 +387,10 @@ int feast_solve_batch(int count, const feast_pencil *pencils, const feast_contou
 unsigned long long feast_kernel_launches(void);
 
 /* The CUDA error behind the calling thread's last FEAST_ECUDA: the error's
- * name and the library source location that saw it ("" if none yet).  The
- * string belongs to the library and stays valid until the thread's next
- * failing call. */
+ * name and the library source location that saw it ("" if none yet); after
+ * a FEAST_ETIMEOUT, the kernels whose bounded waits gave up.  The string
+ * belongs to the library and stays valid until the thread's next failing
+ * call. */
 const char *feast_last_cuda_error(void);
 
 /* ---------------------------------------------------- standalone kernels */
@@ -434,8 +438,9 @@ int feast_grad_abs2(feast_ctx *right, feast_ctx *left, void *gA, void *gB, int64
  * tensor cores' FP32 accumulators, and the chunk sums are combined in FP64.
  * Error: about 2^-47 times max_k|A_ik| * max_k|B_kj| * k per entry (not
  * relative to |C|).  work: device, >= feast_zgemm_oz_work_bytes bytes, 256-
- * byte aligned (digit planes).  err: device int32, set to 1 if a bounded
- * pipeline wait gave up (C is then unspecified).  Asynchronous. */
+ * byte aligned (digit planes).  err: device int32, set non-zero (0x400) if
+ * a bounded pipeline wait (4 s of device time) gave up (C is then
+ * unspecified).  Asynchronous. */
 size_t feast_zgemm_oz_work_bytes(int64_t m, int64_t n, int64_t k);
 int feast_zgemm_oz(int64_t m, int64_t n, int64_t k, double alpha_re, double alpha_im, const void *A, int64_t lda,
                    const void *B, int64_t ldb, double beta_re, double beta_im, void *C, int64_t ldc, void *work,

@@ -205,7 +205,7 @@ def from_device_colmajor(t, rows: int, cols: int) -> np.ndarray:
 def _check(st: int, where: str):
     if st != 0:
         detail = ""
-        if st == -3 and _lib is not None:
+        if st in (-3, -6) and _lib is not None:
             detail = (_lib.feast_last_cuda_error() or b"").decode()
         raise FeastError(st, where, detail)
 

@@ -115,7 +115,7 @@ struct DevStatus {
     double err;         // e(k)
     int flag;           // 2 continue, 1 / 0 / -1 stopping criteria
     int qz_fail;        // pencils whose QZ iteration hit its iteration cap
-    int timeout;        // a bounded grid barrier gave up
+    int timeout;        // TO_* bits of the bounded waits that gave up
     int qz_sweeps;      // QR sweeps of the last large projected eigensolve
     int qz_phases;      // chase phases (chunks) of those sweeps
     int qz_aed;         // early-deflation windows applied
@@ -124,6 +124,9 @@ struct DevStatus {
 // Records the failing CUDA call (error name, file, line) for
 // feast_last_cuda_error; returns FEAST_ECUDA.
 int note_cuda_error(cudaError_t e, const char *file, int line);
+// Records which bounded waits gave up (TO_* bits) for feast_last_cuda_error;
+// returns FEAST_ETIMEOUT.
+int note_timeout(int bits);
 #define FEAST_CUDA_TRY(expr)                                                         \
     do {                                                                             \
         cudaError_t _e = (expr);                                                     \
@@ -171,12 +174,40 @@ inline cudaError_t ensure_dyn_smem(K kernel, size_t bytes)
     return allow_dyn_smem(kernel);
 }
 
-// ---------------------------------------------------------------- grid barrier
-constexpr long long SPIN_LIMIT = 1ll << 24;
+// ---------------------------------------------------------------- bounded waits
+// Where a bounded wait gave up: bits of DevStatus::timeout, set only by the
+// wait that ran out (a wait that stops because another one already gave up
+// adds nothing), so the host can name the first site.
+enum : int {
+    TO_HESS = 1 << 1,       // k_hess_grid grid barrier
+    TO_HQR = 1 << 2,        // k_hqr grid barrier
+    TO_CHOL = 1 << 3,       // k_chol_grid grid barrier
+    TO_CGS2 = 1 << 4,       // k_cgs2_grid grid barrier
+    TO_PCHOL = 1 << 5,      // k_pchol_grid grid barrier
+    TO_TC_LOAD = 1 << 6,    // k_tc_cgemm2 producer (free stage)
+    TO_TC_MMA = 1 << 7,     // k_tc_cgemm2 MMA issuer (loaded stage / free accumulator)
+    TO_TC_EPI = 1 << 8,     // k_tc_cgemm2 epilogue (finished accumulator)
+    TO_TC_DRAIN = 1 << 9,   // k_tc_cgemm2 final MMA completion
+    TO_OZ = 1 << 10,        // k_oz_gemm (any of its mbarrier waits)
+};
+// Every wait polls until its condition holds, another wait has given up,
+// or WAIT_NS of device time (%globaltimer) have passed; the iteration cap
+// is a second bound in case the timer does not advance.
+constexpr unsigned long long WAIT_NS = 4000000000ull;
+constexpr long long SPIN_LIMIT = 1ll << 30;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 struct GridSync {
     unsigned *count;
     unsigned *gen;
     int *err;
+    int site;       // TO_* bit raised when this barrier's wait runs out
 };
 
 // Sense-counting grid barrier for a cooperative launch, with a bounded spin:
@@ -197,8 +228,14 @@ __device__ __forceinline__ bool grid_barrier(const GridSync &g)
             atomicAdd(g.gen, 1u);
         } else {
             long long it = 0;
+            const unsigned long long t0 = global_ns();
             while (*vgen == my) {
-                if (++it > SPIN_LIMIT || *(volatile int *)g.err) { ok = 0; atomicExch(g.err, 1); break; }
+                if (*(volatile int *)g.err) { ok = 0; break; }
+                if (++it > SPIN_LIMIT || ((it & 255) == 0 && global_ns() - t0 > WAIT_NS)) {
+                    ok = 0;
+                    atomicOr(g.err, g.site);
+                    break;
+                }
                 __nanosleep(20);
             }
         }

@@ -29,6 +29,18 @@ int note_cuda_error(cudaError_t e, const char *file, int line)
     snprintf(g_cuda_error, sizeof(g_cuda_error), "%s (%s:%d)", cudaGetErrorName(e), base ? base + 1 : file, line);
     return FEAST_ECUDA;
 }
+int note_timeout(int bits)
+{
+    static const char *const names[] = {"?", "k_hess_grid barrier", "k_hqr barrier", "k_chol_grid barrier",
+                                        "k_cgs2_grid barrier", "k_pchol_grid barrier", "k_tc_cgemm2 producer",
+                                        "k_tc_cgemm2 MMA", "k_tc_cgemm2 epilogue", "k_tc_cgemm2 drain",
+                                        "k_oz_gemm"};
+    int at = snprintf(g_cuda_error, sizeof(g_cuda_error), "bounded wait gave up (0x%x):", bits);
+    for (int b = 0; b < 11 && at > 0 && at < (int)sizeof(g_cuda_error); ++b)
+        if (bits & (1 << b))
+            at += snprintf(g_cuda_error + at, sizeof(g_cuda_error) - at, " %s", names[b]);
+    return FEAST_ETIMEOUT;
+}
 }  // namespace feast
 
 struct feast_ctx {
@@ -156,8 +168,9 @@ int validate(const feast_pencil *p, const feast_contour *c, const feast_options 
         return FEAST_EINVAL;
     if (o->prec != FEAST_FP64 && o->prec != FEAST_C64_REFINE) return FEAST_EINVAL;
     if (o->prec == FEAST_C64_REFINE && (o->max_refine < 0 || !(o->refine_tol > 0.0))) return FEAST_EINVAL;
-    // the band solves stage a band's worth of factor columns in shared
-    // memory: kl + ku up to ~600 (FP64) or ~1200 (precision form)
+    // the band solves keep a window of kl + ku + 2 right-hand-side rows and
+    // one factor column in shared memory at the least: kl + ku up to ~7200
+    // in FP64 (the precision form fits every band the limits above allow)
     if (p->kind == FEAST_BANDED &&
         gb_solve_smem_bytes(p->kl, p->ku, o->prec == FEAST_FP64 ? sizeof(zd) : sizeof(cf)) + 1024 > kSmemOptinMax)
         return FEAST_EINVAL;
@@ -700,7 +713,7 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
                 info->bad_node = hl.lu_info ? hl.lu_info + c->j0 : 0;
             }
             feast_destroy(c);
-            return bad >= 1000.0 ? FEAST_ETIMEOUT : FEAST_ESINGULAR;
+            return bad >= 1000.0 ? note_timeout(hl.timeout) : FEAST_ESINGULAR;
         }
     }
     // first subspace U = Q Y0, then U1, U2
@@ -726,7 +739,7 @@ int feast_setup(feast_ctx **out, const feast_pencil *pencil, const feast_contour
     }
     if (hs.timeout) {
         feast_destroy(c);
-        return FEAST_ETIMEOUT;
+        return note_timeout(hs.timeout);
     }
     c->k = 0;
     c->c_prev = 0;
@@ -961,7 +974,7 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
             hs.flag = (int)f;
         }
     }
-    if (hs.timeout) return FEAST_ETIMEOUT;
+    if (hs.timeout) return note_timeout(hs.timeout);
     if (hs.nonfinite) return FEAST_ENONFINITE;
     if (hs.qz_fail) return FEAST_ENOCONV;
     if (hs.flag != 2 && !c->done) {
@@ -1152,7 +1165,7 @@ int feast_search(feast_ctx *c, const void *Ypool, int npool, double alpha, int p
     DevStatus hs;
     FEAST_CUDA_TRY(cudaMemcpyAsync(&hs, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hs.timeout) return FEAST_ETIMEOUT;
+    if (hs.timeout) return note_timeout(hs.timeout);
     *t = r;
     *s0 = est;
     return FEAST_OK;

@@ -25,9 +25,9 @@ namespace feast {
 
 namespace {
 constexpr int GB_NB = 32;     // panel width
-constexpr int GB_CW = 8;      // right-hand sides per solve CTA
+constexpr int GB_CW = 8;      // right-hand sides per solve CTA (at most; fewer for wide bands)
 constexpr int GB_ST = 256;    // solve threads (>= kl and >= kv handled by striding)
-constexpr int GB_JC = 16;     // solve steps whose factor columns are staged at once
+constexpr int GB_JC = 16;     // solve steps whose factor columns are staged at once (at most)
 
 __host__ __device__ __forceinline__ int64_t bidx(int64_t kv, int64_t ldab, int64_t i, int64_t c)
 {
@@ -209,34 +209,34 @@ __global__ void k_gb_writeback(int64_t n, int64_t kl, int64_t ku, int64_t k0, in
 }
 
 // Forward pass of the solve: for j = 0..n-1: swap rows j, piv[j]; rows
-// j+1 .. j+kl -= l(:, j) x_j.  CTA = (chunk of GB_CW right-hand sides, node).
-// The right-hand sides live in a circular window of WL = kl + 1 + GB_JC rows
-// in shared memory; the multipliers and pivots of GB_JC columns are staged
+// j+1 .. j+kl -= l(:, j) x_j.  CTA = (chunk of cw <= GB_CW right-hand sides,
+// node).  The right-hand sides live in a circular window of WL = kl + 1 + jcm
+// rows in shared memory; the multipliers and pivots of jcm <= GB_JC columns are staged
 // in shared memory at once, and the window rows retired by a chunk are
 // refilled after it, so the sequential steps touch shared memory only.
 template <typename T>
 __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF,
-                                                  const int *piv, T *X, int64_t ldx, int64_t sX)
+                                                  const int *piv, T *X, int64_t ldx, int64_t sX, int cw, int jcm)
 {
     extern __shared__ unsigned char sm_raw[];
-    const int64_t WL = kl + 1 + GB_JC, kv = kl + ku;
-    T *W = reinterpret_cast<T *>(sm_raw);      // WL x GB_CW window, row r at slot r % WL
-    T *Ls = W + WL * GB_CW;                    // GB_JC x kl multipliers
-    int *ps = reinterpret_cast<int *>(Ls + GB_JC * kl);
+    const int64_t WL = kl + 1 + jcm, kv = kl + ku;
+    T *W = reinterpret_cast<T *>(sm_raw);      // WL x cw window, row r at slot r % WL
+    T *Ls = W + WL * cw;                       // jcm x kl multipliers
+    int *ps = reinterpret_cast<int *>(Ls + (int64_t)jcm * kl);
     const int b = blockIdx.y;
     const T *Fb = F + (int64_t)b * sF;
     const int *pv = piv + (int64_t)b * n;
     T *Xb = X + (int64_t)b * sX;
-    const int64_t c0 = (int64_t)blockIdx.x * GB_CW;
-    const int ncol = (int)((nrhs - c0) < GB_CW ? (nrhs - c0) : GB_CW);
-    for (int64_t e = threadIdx.x; e < WL * GB_CW; e += GB_ST) {
+    const int64_t c0 = (int64_t)blockIdx.x * cw;
+    const int ncol = (int)((nrhs - c0) < cw ? (nrhs - c0) : cw);
+    for (int64_t e = threadIdx.x; e < WL * cw; e += GB_ST) {
         const int64_t r = e % WL;
         const int cc = (int)(e / WL);
-        W[r * GB_CW + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+        W[r * cw + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
     }
-    for (int64_t j0 = 0; j0 < n; j0 += GB_JC) {
-        const int jc = (int)((n - j0) < GB_JC ? (n - j0) : GB_JC);
+    for (int64_t j0 = 0; j0 < n; j0 += jcm) {
+        const int jc = (int)((n - j0) < jcm ? (n - j0) : jcm);
         __syncthreads();
         for (int64_t e = threadIdx.x; e < (int64_t)jc * kl; e += GB_ST) {
             const int jj = (int)(e / kl);
@@ -247,64 +247,64 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
         __syncthreads();
         for (int jj = 0; jj < jc; ++jj) {
             const int64_t j = j0 + jj, sj = j % WL, p = ps[jj];
-            if (p != j && threadIdx.x < GB_CW) {
+            if (p != j && threadIdx.x < cw) {
                 const int64_t sp = p % WL;
-                T t = W[sj * GB_CW + threadIdx.x];
-                W[sj * GB_CW + threadIdx.x] = W[sp * GB_CW + threadIdx.x];
-                W[sp * GB_CW + threadIdx.x] = t;
+                T t = W[sj * cw + threadIdx.x];
+                W[sj * cw + threadIdx.x] = W[sp * cw + threadIdx.x];
+                W[sp * cw + threadIdx.x] = t;
             }
             __syncthreads();
-            for (int64_t e = threadIdx.x; e < kl * GB_CW; e += GB_ST) {
-                const int64_t t = e / GB_CW;
-                const int cc = (int)(e % GB_CW);
+            for (int64_t e = threadIdx.x; e < kl * cw; e += GB_ST) {
+                const int64_t t = e / cw;
+                const int cc = (int)(e % cw);
                 const int64_t r = j + 1 + t;
                 if (r < n) {
-                    T &w = W[(r % WL) * GB_CW + cc];
+                    T &w = W[(r % WL) * cw + cc];
                     T v = w;
-                    cfma(v, cneg(Ls[jj * kl + t]), W[sj * GB_CW + cc]);
+                    cfma(v, cneg(Ls[jj * kl + t]), W[sj * cw + cc]);
                     w = v;
                 }
             }
             __syncthreads();
-            if (threadIdx.x < ncol) Xb[j + (c0 + threadIdx.x) * ldx] = W[sj * GB_CW + threadIdx.x];
+            if (threadIdx.x < ncol) Xb[j + (c0 + threadIdx.x) * ldx] = W[sj * cw + threadIdx.x];
         }
         __syncthreads();
         // rows j0 .. j0+jc-1 are final; their slots take rows j0+WL .. (first
-        // touched at step j0 + GB_JC + 1 or later)
-        for (int e = threadIdx.x; e < jc * GB_CW; e += GB_ST) {
-            const int jj = e / GB_CW, cc = e % GB_CW;
+        // touched at step j0 + jcm + 1 or later)
+        for (int e = threadIdx.x; e < jc * cw; e += GB_ST) {
+            const int jj = e / cw, cc = e % cw;
             const int64_t r = j0 + jj + WL;
-            W[(r % WL) * GB_CW + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+            W[(r % WL) * cw + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
         }
     }
 }
 
 // Backward pass: for j = n-1..0: x_j /= U(j,j); rows j-kv .. j-1 -= U(:, j) x_j.
-// Same window / staging scheme: WL = kv + 1 + GB_JC rows, GB_JC columns of U
+// Same window / staging scheme: WL = kv + 1 + jcm rows, jcm columns of U
 // (diagonal included) staged per chunk.
 template <typename T>
 __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF, T *X,
-                                                  int64_t ldx, int64_t sX)
+                                                  int64_t ldx, int64_t sX, int cw, int jcm)
 {
     extern __shared__ unsigned char sm_raw[];
-    const int64_t kv = kl + ku, WL = kv + 1 + GB_JC;
-    T *W = reinterpret_cast<T *>(sm_raw);      // WL x GB_CW window, row r at slot r % WL
-    T *Us = W + WL * GB_CW;                    // GB_JC x (kv + 1): U(j - t, j), t = 0..kv
+    const int64_t kv = kl + ku, WL = kv + 1 + jcm;
+    T *W = reinterpret_cast<T *>(sm_raw);      // WL x cw window, row r at slot r % WL
+    T *Us = W + WL * cw;                       // jcm x (kv + 1): U(j - t, j), t = 0..kv
     __shared__ T s_x[GB_CW];
     const int b = blockIdx.y;
     const T *Fb = F + (int64_t)b * sF;
     T *Xb = X + (int64_t)b * sX;
-    const int64_t c0 = (int64_t)blockIdx.x * GB_CW;
-    const int ncol = (int)((nrhs - c0) < GB_CW ? (nrhs - c0) : GB_CW);
-    for (int64_t e = threadIdx.x; e < WL * GB_CW; e += GB_ST) {
+    const int64_t c0 = (int64_t)blockIdx.x * cw;
+    const int ncol = (int)((nrhs - c0) < cw ? (nrhs - c0) : cw);
+    for (int64_t e = threadIdx.x; e < WL * cw; e += GB_ST) {
         const int64_t t = e % WL;
         const int cc = (int)(e / WL);
         const int64_t r = n - 1 - t;
-        if (r >= 0) W[(r % WL) * GB_CW + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+        if (r >= 0) W[(r % WL) * cw + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
     }
-    for (int64_t j1 = n - 1; j1 >= 0; j1 -= GB_JC) {
-        const int jc = (int)((j1 + 1) < GB_JC ? (j1 + 1) : GB_JC);
+    for (int64_t j1 = n - 1; j1 >= 0; j1 -= jcm) {
+        const int jc = (int)((j1 + 1) < jcm ? (j1 + 1) : jcm);
         __syncthreads();
         for (int64_t e = threadIdx.x; e < (int64_t)jc * (kv + 1); e += GB_ST) {
             const int jj = (int)(e / (kv + 1));
@@ -315,19 +315,19 @@ __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t
         for (int jj = 0; jj < jc; ++jj) {
             const int64_t j = j1 - jj, sj = j % WL;
             const T *u = Us + jj * (kv + 1);
-            if (threadIdx.x < GB_CW) {
-                const T v = cdiv(W[sj * GB_CW + threadIdx.x], u[0]);
-                W[sj * GB_CW + threadIdx.x] = v;
+            if (threadIdx.x < cw) {
+                const T v = cdiv(W[sj * cw + threadIdx.x], u[0]);
+                W[sj * cw + threadIdx.x] = v;
                 s_x[threadIdx.x] = v;
                 if (threadIdx.x < ncol) Xb[j + (c0 + threadIdx.x) * ldx] = v;
             }
             __syncthreads();
-            for (int64_t e = threadIdx.x; e < kv * GB_CW; e += GB_ST) {
-                const int64_t t = e / GB_CW;
-                const int cc = (int)(e % GB_CW);
+            for (int64_t e = threadIdx.x; e < kv * cw; e += GB_ST) {
+                const int64_t t = e / cw;
+                const int cc = (int)(e % cw);
                 const int64_t r = j - 1 - t;
                 if (r >= 0) {
-                    T &w = W[(r % WL) * GB_CW + cc];
+                    T &w = W[(r % WL) * cw + cc];
                     T v = w;
                     cfma(v, cneg(u[t + 1]), s_x[cc]);
                     w = v;
@@ -336,10 +336,10 @@ __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t
             __syncthreads();
         }
         // rows j1-jc+1 .. j1 are final; their slots take rows j - WL
-        for (int e = threadIdx.x; e < jc * GB_CW; e += GB_ST) {
-            const int jj = e / GB_CW, cc = e % GB_CW;
+        for (int e = threadIdx.x; e < jc * cw; e += GB_ST) {
+            const int jj = e / cw, cc = e % cw;
             const int64_t r = j1 - jj - WL;
-            if (r >= 0) W[(r % WL) * GB_CW + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+            if (r >= 0) W[(r % WL) * cw + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
         }
     }
 }
@@ -534,6 +534,7 @@ int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int
                 FEAST_LAUNCH_CHECK();
             }
         }
+        FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_writeback<T>, (size_t)rows * sizeof(T)));
         k_gb_writeback<T><<<q, 256, (size_t)rows * sizeof(T), s>>>(n, kl, ku, k0, nb, rows, F, ldab, sF, D,
                                                                   ldd, sD, pivl, ldd, piv);
         FEAST_LAUNCH_CHECK();
@@ -543,20 +544,41 @@ int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int
 
 // Dynamic shared memory of the band solves (forward, backward) for elements
 // of es bytes: the staged factor columns and right-hand-side chunks.
-static size_t gb_fwd_smem(int64_t kl, size_t es)
+static size_t gb_fwd_smem(int64_t kl, size_t es, int cw, int jcm)
 {
-    return ((size_t)(kl + 1 + GB_JC) * GB_CW + (size_t)GB_JC * kl) * es + GB_JC * sizeof(int) + 16;
+    return ((size_t)(kl + 1 + jcm) * cw + (size_t)jcm * kl) * es + jcm * sizeof(int) + 16;
 }
-static size_t gb_bwd_smem(int64_t kl, int64_t ku, size_t es)
+static size_t gb_bwd_smem(int64_t kl, int64_t ku, size_t es, int cw, int jcm)
 {
     const int64_t kv = kl + ku;
-    return ((size_t)(kv + 1 + GB_JC) * GB_CW + (size_t)GB_JC * (kv + 1)) * es;
+    return ((size_t)(kv + 1 + jcm) * cw + (size_t)jcm * (kv + 1)) * es;
+}
+
+// Staging of the band solves: the most right-hand sides per CTA (cw) and
+// the deepest factor staging (jcm) whose shared memory fits, preferring
+// width (parallel work per step) over depth.  Wide bands trade both for
+// the band itself: cw = jcm = 1 holds just a window of kv + 2 rows and one
+// factor column.
+struct GbPlan {
+    int cw, jcm;
+    size_t smf, smb;
+};
+static GbPlan gb_plan(int64_t kl, int64_t ku, size_t es)
+{
+    const size_t lim = kSmemOptinMax - 1024;
+    GbPlan p{1, 1, gb_fwd_smem(kl, es, 1, 1), gb_bwd_smem(kl, ku, es, 1, 1)};
+    for (int cw = GB_CW; cw >= 1; cw /= 2)
+        for (int jcm = GB_JC; jcm >= 1; jcm /= 2) {
+            const size_t f = gb_fwd_smem(kl, es, cw, jcm), b = gb_bwd_smem(kl, ku, es, cw, jcm);
+            if (f <= lim && b <= lim) return GbPlan{cw, jcm, f, b};
+        }
+    return p;   // (does not fit: the caller refuses the band)
 }
 
 size_t gb_solve_smem_bytes(int64_t kl, int64_t ku, size_t es)
 {
-    const size_t f = gb_fwd_smem(kl, es), b = gb_bwd_smem(kl, ku, es);
-    return f > b ? f : b;
+    const GbPlan p = gb_plan(kl, ku, es);
+    return p.smf > p.smb ? p.smf : p.smb;
 }
 
 template <typename T>
@@ -564,14 +586,14 @@ int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *
              int64_t nrhs, T *X, int64_t ldx, int64_t sX)
 {
     const int64_t ldab = 2 * kl + ku + 1, sF = ldab * n;
-    dim3 g(cdiv(nrhs, GB_CW), q);
-    const size_t smf = gb_fwd_smem(kl, sizeof(T));
-    const size_t smb = gb_bwd_smem(kl, ku, sizeof(T));
-    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_fwd<T>, smf));
-    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_bwd<T>, smb));
-    k_gb_fwd<T><<<g, GB_ST, smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX);
+    const GbPlan pl = gb_plan(kl, ku, sizeof(T));
+    if (pl.smf > kSmemOptinMax - 1024 || pl.smb > kSmemOptinMax - 1024) return FEAST_EINVAL;
+    dim3 g(cdiv(nrhs, pl.cw), q);
+    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_fwd<T>, pl.smf));
+    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_bwd<T>, pl.smb));
+    k_gb_fwd<T><<<g, GB_ST, pl.smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX, pl.cw, pl.jcm);
     FEAST_LAUNCH_CHECK();
-    k_gb_bwd<T><<<g, GB_ST, smb, s>>>(n, kl, ku, nrhs, F, ldab, sF, X, ldx, sX);
+    k_gb_bwd<T><<<g, GB_ST, pl.smb, s>>>(n, kl, ku, nrhs, F, ldab, sF, X, ldx, sX, pl.cw, pl.jcm);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }

@@ -270,7 +270,7 @@ int cholesky(cudaStream_t s, int m, zd *G, double *d0, int *fail, unsigned *bar,
     FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_grid, PT, 0));
     if (per < 1) return FEAST_ECUDA;
     FEAST_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
-    GridSync gs{bar, bar + 1, timeout};
+    GridSync gs{bar, bar + 1, timeout, TO_CHOL};
     void *args[] = {&m, &G, &d0, &fail, &rinv, &gs};
     // as many CTAs as the first trailing update has ~4 tiles for (at least
     // 8, at most one per SM): a small factorisation leaves the rest of the

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+    if (threadIdx.x == 0 && s_fail) atomicOr(err, TO_OZ);
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 

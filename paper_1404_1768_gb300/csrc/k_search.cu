@@ -201,7 +201,7 @@ int rrqr_basis(cudaStream_t s, int64_t n, int m, const zd *U, zd *Q, double rank
     if (grid > sms) grid = sms;
     if (grid > 1024) grid = 1024;
     FEAST_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
-    GridSync gs{bar, bar + 1, timeout};
+    GridSync gs{bar, bar + 1, timeout, TO_PCHOL};
     int mm_ = m;
     void *args[] = {&mm_, &G, &R, &piv, &d, &used, &pval, &pidx, &rank_tol, &rk, &gs};
     FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_pchol_grid, dim3(grid), dim3(ST), args, 0, s));

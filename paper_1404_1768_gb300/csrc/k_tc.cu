@@ -71,10 +71,16 @@ __device__ __forceinline__ void cluster_sync()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// Bounded wait that also gives up once any thread has raised *err.
-__device__ __forceinline__ bool wait2(uint64_t *bar, uint32_t parity, const int *err)
+// Bounded wait that also gives up once any thread has raised *err (unless
+// it waits for this CTA's own copies or MMAs in flight: those are waited
+// out, up to the time bound); a wait that runs out itself raises the
+// site's bit in *err.
+constexpr unsigned long long DRAIN_NS = 200000000ull;   // bound of a wait for this CTA's own work in flight
+__device__ __forceinline__ bool wait2(uint64_t *bar, uint32_t parity, int *err, int site, bool stop_on_err = true)
 {
+    const unsigned long long limit = stop_on_err ? WAIT_NS : DRAIN_NS;
     const uint32_t a = smem_u32(bar);
+    const unsigned long long t0 = global_ns();
     for (long long it = 0; it < SPIN; ++it) {
         uint32_t done;
         asm volatile(
@@ -83,8 +89,12 @@ __device__ __forceinline__ bool wait2(uint64_t *bar, uint32_t parity, const int 
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if ((it & 1023) == 1023 && *(volatile const int *)err) return false;
+        if ((it & 1023) == 1023) {
+            if (stop_on_err && *(volatile const int *)err) return false;
+            if (global_ns() - t0 > limit) break;
+        }
     }
+    atomicOr(err, site);
     return false;
 }
 // TMA tile load into this CTA's shared memory, completion counted on the
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
             for (int kb = 0; kb < kb_n; ++kb, ++it) {
                 const int s = (int)(it % K2_STAGES);
                 const uint32_t ph = (uint32_t)((it / K2_STAGES) & 1);
-                if (!wait2(&empty[s], ph ^ 1u, err)) { atomicExch(err, 1); ok = false; break; }
+                if (!wait2(&empty[s], ph ^ 1u, err, TO_TC_LOAD)) { ok = false; break; }
                 unsigned char *st = base + s * K2_STAGE_BYTES;
                 const uint32_t fb = full0 + (uint32_t)(s * sizeof(uint64_t));
                 if (rank == 0) mbar_expect_tx(&full[s], 2 * K2_STAGE_BYTES);
@@ -186,7 +196,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
             // let the loads already issued land before the CTA can exit
             for (int s = 0; s < K2_STAGES; ++s) {
                 const long long last = it - 1 - ((it - 1 - s) % K2_STAGES + K2_STAGES) % K2_STAGES;
-                if (last >= 0) wait2(&full[s], (uint32_t)((last / K2_STAGES) & 1), err);
+                if (last >= 0) wait2(&full[s], (uint32_t)((last / K2_STAGES) & 1), err, TO_TC_LOAD, false);
             }
         }
     } else if (warp == 1 && lane == 0 && rank == 0) {
@@ -198,13 +208,13 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
         for (long long t = pair; t < tiles && ok; t += npairs, ++tl) {
             const int ab = tl & 1;
             const uint32_t aph = (uint32_t)((tl >> 1) & 1);
-            if (!wait2(&tempty[ab], aph ^ 1u, err)) { atomicExch(err, 1); ok = false; break; }
+            if (!wait2(&tempty[ab], aph ^ 1u, err, TO_TC_MMA)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t d = tmem + (uint32_t)(ab * K2_BN);
             for (int kb = 0; kb < kb_n; ++kb, ++it) {
                 const int s = (int)(it % K2_STAGES);
                 const uint32_t ph = (uint32_t)((it / K2_STAGES) & 1);
-                if (!wait2(&full[s], ph, err)) { atomicExch(err, 1); ok = false; break; }
+                if (!wait2(&full[s], ph, err, TO_TC_MMA)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 unsigned char *st = base + s * K2_STAGE_BYTES;
                 const uint64_t ah = sdesc<64>(st), at = sdesc<64>(st + K2_TILE_BYTES);
@@ -226,7 +236,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
         asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&drain))
                      : "memory");
-        if (!wait2(&drain, 0, err)) atomicExch(err, 1);
+        wait2(&drain, 0, err, TO_TC_DRAIN, false);
     } else if (warp >= 2) {
         // epilogue: TMEM lanes 32 (warp % 4) .. +31 of this CTA's 128 rows
         const int quarter = warp & 3;
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
         for (long long t = pair; t < tiles; t += npairs, ++tl) {
             const int ab = tl & 1;
             const uint32_t aph = (uint32_t)((tl >> 1) & 1);
-            if (!wait2(&tfull[ab], aph, err)) { atomicExch(err, 1); break; }
+            if (!wait2(&tfull[ab], aph, err, TO_TC_EPI)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int b = (int)(t / ((long long)mt * nt));
             const int rem = (int)(t % ((long long)mt * nt));

@@ -1657,8 +1657,7 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
         if (hgrid > need) hgrid = need;
         if (hgrid > 0) {
             FEAST_CUDA_TRY(cudaMemsetAsync(hbar, 0, 2 * sizeof(unsigned), s));
-            FEAST_CUDA_TRY(cudaMemsetAsync(timeout, 0, sizeof(int), s));
-            GridSync hg{hbar, hbar + 1, timeout};
+            GridSync hg{hbar, hbar + 1, timeout, TO_HESS};
             int mm = m, ldq = m;
             void *hargs[] = {&mm, &C, &Q, &ldq, &hg};
             FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hess_grid, dim3(hgrid), dim3(HG_T), hargs, hsm, s));
@@ -1692,9 +1691,10 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     FEAST_CUDA_TRY(cudaMemcpyAsync(&hn, hmax, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (hgrid > 0) FEAST_CUDA_TRY(cudaMemcpyAsync(&htimeout, timeout, sizeof(int), cudaMemcpyDeviceToHost, s));
     FEAST_CUDA_TRY(cudaMemsetAsync(bar, 0, 16, s));
-    FEAST_CUDA_TRY(cudaMemsetAsync(timeout, 0, sizeof(int), s));
     FEAST_CUDA_TRY(cudaStreamSynchronize(s));
-    if (htimeout) return FEAST_ETIMEOUT;   // the reduction's grid barrier gave up
+    // the reduction's grid barrier gave up (or a wait before it did, and
+    // the reduction stopped at its first barrier)
+    if (htimeout) return note_timeout(htimeout);
     if (hn_out) *hn_out = hn;
     // deflation thresholds at double-single resolution (2^-44 relative),
     // or a few FP32 units in the FP32 build (or the caller's looser one)
@@ -1738,7 +1738,7 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     int grid = m / 8;
     if (grid < NSH) grid = NSH;
     if (grid > sms) grid = sms;
-    GridSync gs{bar, bar + 1, timeout};
+    GridSync gs{bar, bar + 1, timeout, TO_HQR};
     int mm = m, ldh = m;
     const unsigned gcv = cdiv((size_t)m * m, 256) > 4096 ? 4096 : cdiv((size_t)m * m, 256);
     k_to_ds<<<gcv, 256, 0, s>>>((int64_t)m * m, C, Hds);

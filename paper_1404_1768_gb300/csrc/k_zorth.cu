@@ -275,7 +275,7 @@ int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64
     IntraPlan pl;
     int e = plan_intra(n, pl);
     if (e) return e;
-    GridSync gs{bar, bar + 1, timeout};
+    GridSync gs{bar, bar + 1, timeout, TO_CGS2};
     if (pl.grid) FEAST_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
     FEAST_CUDA_TRY(cudaMemset2DAsync(R, (size_t)ldr * sizeof(zd), 0, (size_t)m * sizeof(zd), (size_t)m, s));
     const zd one = zmake(1.0, 0.0), mone = zmake(-1.0, 0.0), zero = zmake(0.0, 0.0);

@@ -12,7 +12,7 @@
 namespace feast {
 namespace tc {
 
-constexpr long long SPIN = 1ll << 26;   // mbarrier poll limit before a wait gives up
+constexpr long long SPIN = 1ll << 32;   // mbarrier poll cap (the device-time bound WAIT_NS comes first)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -32,10 +32,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// Bounded wait for the phase with the given parity; false on timeout.
+// Bounded wait for the phase with the given parity; false once WAIT_NS of
+// device time (or SPIN polls) have passed without it.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
     const uint32_t a = smem_u32(bar);
+    const unsigned long long t0 = global_ns();
     for (long long it = 0; it < SPIN; ++it) {
         uint32_t done;
         asm volatile(
@@ -44,6 +46,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((it & 1023) == 1023 && global_ns() - t0 > WAIT_NS) return false;
     }
     return false;
 }

@@ -67,16 +67,20 @@ def test_last_cuda_error_without_gpu():
 
 
 def test_band_width_bounded_by_the_solve_staging():
-    """The band solves stage kl + ku factor columns in shared memory: wider
-    bands are refused at set-up (FEAST_EINVAL) rather than failing to
-    launch -- kl = ku = 298 is the FP64 limit, 599 the precision form's."""
+    """The band solves keep a circular window of kl + ku + 1 + jc right-hand-
+    side rows and jc staged factor columns in shared memory (jc >= 1 staged
+    steps, fewer right-hand sides per CTA for wide bands): in FP64 (16-byte
+    elements) the narrowest staging, 2 (kl + ku) + 3 elements, fits up to
+    kl = ku = 3615 and not 3616; in the precision form (8-byte elements)
+    every band up to the kl, ku <= 4096 limit fits.  Wider bands are refused
+    at set-up (FEAST_EINVAL) rather than failing to launch."""
     import paper_1404_1768_gb300 as fg
     lib = fg.load()
     c = fg.Contour(1, 0.0, 0.0, 2.0, 1.0, 8, 1)
     nb = ctypes.c_size_t(0)
-    for prec, ok_w, bad_w in ((0, 298, 299), (1, 599, 600)):
+    for prec, ok_w, bad_w in ((0, 3615, 3616), (1, 4096, 4097)):
         o = fg.Options(8, 1, 1e-12, 1e-3, 50, prec, 5, 1e-14, None, 0, 0)
         for w, expect in ((ok_w, 0), (bad_w, -1)):
-            p = fg.Pencil(1, 5000, 1, 1, 2 * w + 1, w, w, 0)
+            p = fg.Pencil(1, 9000, 1, 1, 2 * w + 1, w, w, 0)
             assert lib.feast_workspace_size(ctypes.byref(p), ctypes.byref(c), ctypes.byref(o),
                                             ctypes.byref(nb)) == expect, (prec, w)

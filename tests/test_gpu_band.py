@@ -55,6 +55,44 @@ def test_band_filter_matches_oracle(prec, n, kl, ku, m0, q):
     g.close(); o.close()
 
 
+def _fast_band(n, kl, ku, seed):
+    """Like _random_band, a column at a time (for the wide bands)."""
+    rng = np.random.default_rng(seed)
+    ab = np.zeros((kl + ku + 1, n), complex, order="F")
+    for j in range(n):
+        i0, i1 = max(0, j - ku), min(n, j + kl + 1)
+        ab[ku + i0 - j:ku + i1 - j, j] = rng.standard_normal(i1 - i0) + 1j * rng.standard_normal(i1 - i0)
+    return ab
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,kl,ku,q,b_identity", [(1900, 900, 900, 4, False), (2000, 1500, 1400, 3, True),
+                                                  (3064, 3000, 2800, 2, True)])
+def test_wide_band_filter_matches_oracle(prec, n, kl, ku, q, b_identity):
+    """Bands too wide for the full solve staging (8 right-hand sides x 16
+    factor columns per CTA): the solves stage fewer of each, down to one
+    right-hand side and one factor column per CTA for kl + ku = 5800 in FP64.
+    13 right-hand sides leave a ragged last chunk at every staging width."""
+    fg = _fg()
+    m0 = 13
+    A = _fast_band(n, kl, ku, 11 * n)
+    A[ku, :] += 60.0
+    B = None
+    if not b_identity:
+        B = _fast_band(n, kl, ku, 11 * n + 1)
+        B[ku, :] += 90.0
+    Y = inputs.complex_normal(np.random.default_rng(5), (n, m0))
+    kw = dict(contour_kind=1, rule=1, q=q, center=0.5 + 0.2j, a=1.5, b=0.8, kind=1, kl=kl, ku=ku,
+              b_identity=b_identity)
+    g = fg.Feast(A, B, Y, prec=prec, refine_tol=1e-14, max_refine=8, **kw)
+    o = oracle.Feast(A, B, Y, **kw)
+    V = inputs.complex_normal(np.random.default_rng(6), (n, m0))
+    Ug, Uo = g.filter(V), o.filter(V)
+    err = np.abs(Ug - Uo).max() / np.abs(Uo).max()
+    assert err < (1e-11 if prec == 0 else 1e-10), err
+    g.close(); o.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n,kl,ku,m0,q", [(100, 10, 10, 8, 8), (333, 37, 21, 11, 6)])
 def test_band_filter_identity_b_matches_oracle(prec, n, kl, ku, m0, q):
