@@ -223,7 +223,7 @@ __device__ __forceinline__ bool grid_barrier(const GridSync &g)
         const unsigned arrived = atomicAdd(g.count, 1u);
         int ok = 1;
         if (arrived == gridDim.x - 1) {
-            *g.count = 0;
+            atomicExch(g.count, 0u);
             __threadfence();
             atomicAdd(g.gen, 1u);
         } else {

@@ -143,6 +143,7 @@ constexpr double kWarmAccMin = 1e-12;  // the cold double-single QR's own backwa
 // residual) tries the FP32 QR polished by the Newton step first: from an
 // FP32 Schur form (~1e-6 remainder) one Newton step reaches ~1e-10.
 constexpr double kColdFp32AccMin = 1e-8;
+constexpr int kZeigMinM = 8;         // smallest projected problem on the standard-form QR
 
 struct Carver {
     char *base;
@@ -276,7 +277,7 @@ void carve(feast_ctx *c, Carver &cv)
     c->reso = cv.take<double>(m);
     c->tmp = cv.take<zd>(n * m);
     c->orth_work = cv.take<zd>(zorth_work_elems((int64_t)n, (int64_t)m));
-    c->qz_work = cv.take<char>(zqz_work_bytes((int)m));
+    c->qz_work = cv.take<char>(std::max(zqz_work_bytes((int)m), (zeig_large_work_bytes((int)m) + 255) & ~(size_t)255));
     c->search_work = cv.take<char>(rrqr_work_bytes((int64_t)n, (int)m));
     if ((int)m >= kWarmMinM) {
         c->warm_work = cv.take<char>(zeig_warm_work_bytes((int)m));
@@ -875,8 +876,10 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         // max|C|) then stays far below the residual a stop needs
         const WarmParams prm{kWarmMinM, kWarmMinTail, tau, acc, fmin(1e-3 * acc, 1e-2 * c->eps), 0};
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
+        // (the Newton step's defect-form products on the digit-sliced
+        // tensor-core GEMM where the context has its scratch)
         if ((e = zeig_warm(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->warm_work, c->qz_work, prm,
-                           &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt)))
+                           &c->last_warm, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, &c->gt, orth_oz(c))))
             return e;
         if (!c->last_warm.accepted) FEAST_CUDA_TRY(cudaMemsetAsync(&c->st->qz_fail, 0, sizeof(int), s));
     }
@@ -904,9 +907,17 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         const double defl = (c->c_prev > 0) ? 0.0 : 1e-8;
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if (rr && (e = triangularise_bt(c))) return e;
-        if ((e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
-                             c->qz_work, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, defl)))
-            return e;
+        // B~ is upper triangular here (R2, or made so for Rayleigh-Ritz):
+        // the standard-form QR on the FP32 pipe (double-single) from m =
+        // kZeigMinM up; the FP64 QZ of the pencil only below (GB300's FP64
+        // pipe made it ~50 ms at m0 = 64)
+        if (m >= kZeigMinM)
+            e = zeig_large(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->qz_work, &c->st->qz_fail,
+                           &c->st->timeout, &c->st->qz_sweeps, defl);
+        else
+            e = zqz_batched(s, (int)m, 1, c->Q, m, 0, c->Q + m * m, m, 0, c->alpha, c->beta, c->Yv, m, 0,
+                            c->qz_work, &c->st->qz_fail, &c->st->timeout, &c->st->qz_sweeps, defl);
+        if (e) return e;
     }
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[2], s));
     if (use_oz(c)) {

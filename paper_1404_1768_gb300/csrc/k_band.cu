@@ -27,11 +27,20 @@ namespace {
 constexpr int GB_NB = 32;     // panel width
 constexpr int GB_CW = 8;      // right-hand sides per solve CTA (at most; fewer for wide bands)
 constexpr int GB_ST = 256;    // solve threads (>= kl and >= kv handled by striding)
-constexpr int GB_JC = 16;     // solve steps whose factor columns are staged at once (at most)
+constexpr int GB_JC = 32;     // solve steps per staged chunk (at most: one warp's lanes)
 
 __host__ __device__ __forceinline__ int64_t bidx(int64_t kv, int64_t ldab, int64_t i, int64_t c)
 {
     return kv + i - c + c * ldab;
+}
+
+__device__ __forceinline__ float2 shfl_cx(float2 v, int src)
+{
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ double2 shfl_cx(double2 v, int src)
+{
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
 // F_j = z_j B - A in factor storage; rows 0..kl-1 of each column (fill) = 0.
@@ -208,138 +217,201 @@ __global__ void k_gb_writeback(int64_t n, int64_t kl, int64_t ku, int64_t k0, in
     }
 }
 
-// Forward pass of the solve: for j = 0..n-1: swap rows j, piv[j]; rows
-// j+1 .. j+kl -= l(:, j) x_j.  CTA = (chunk of cw <= GB_CW right-hand sides,
-// node).  The right-hand sides live in a circular window of WL = kl + 1 + jcm
-// rows in shared memory; the multipliers and pivots of jcm <= GB_JC columns are staged
-// in shared memory at once, and the window rows retired by a chunk are
-// refilled after it, so the sequential steps touch shared memory only.
+// Forward pass of the solve (unblocked convention: for j = 0..n-1, swap
+// rows j and piv[j], then rows j+1 .. j+kl -= l_j x_j), taken jc steps at a
+// time.  Within a chunk the interchanges commute to the front: the chunk is
+// x <- L'_{jc-1} .. L'_0 P_{jc-1} .. P_0 x with L'_i's column = the later
+// interchanges of the chunk applied to l_i (they touch only rows below
+// i).  So a chunk is (1) its interchanges on the right-hand sides, (2) a
+// unit lower triangular solve on its jc rows (one warp per right-hand
+// side, a lane per row, the solved value passed by shuffles), (3) one
+// rank-jc update of the kl rows below it.  CTA = (chunk of cw <= GB_CW
+// right-hand sides, node); the right-hand sides live in a circular window
+// of WL = kl + 1 + jcm rows in shared memory, the chunk's multipliers
+// (jcm + kl rows x jcm columns, column-major) and pivots beside it.
 template <typename T>
 __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF,
                                                   const int *piv, T *X, int64_t ldx, int64_t sX, int cw, int jcm)
 {
     extern __shared__ unsigned char sm_raw[];
-    const int64_t WL = kl + 1 + jcm, kv = kl + ku;
+    const int WL = (int)(kl + 1 + jcm), LR = (int)(jcm + kl), kv = (int)(kl + ku);
     T *W = reinterpret_cast<T *>(sm_raw);      // WL x cw window, row r at slot r % WL
-    T *Ls = W + WL * cw;                       // jcm x kl multipliers
-    int *ps = reinterpret_cast<int *>(Ls + (int64_t)jcm * kl);
+    T *Lb = W + (size_t)WL * cw;               // LR x jcm: Lb[jj * LR + rho] = L'(j0 + rho, j0 + jj)
+    int *ps = reinterpret_cast<int *>(Lb + (size_t)LR * jcm);   // pivots of the chunk, minus j0
     const int b = blockIdx.y;
     const T *Fb = F + (int64_t)b * sF;
     const int *pv = piv + (int64_t)b * n;
     T *Xb = X + (int64_t)b * sX;
     const int64_t c0 = (int64_t)blockIdx.x * cw;
     const int ncol = (int)((nrhs - c0) < cw ? (nrhs - c0) : cw);
-    for (int64_t e = threadIdx.x; e < WL * cw; e += GB_ST) {
-        const int64_t r = e % WL;
-        const int cc = (int)(e / WL);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < WL * cw; e += GB_ST) {
+        const int r = e % WL, cc = e / WL;
         W[r * cw + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
     }
     for (int64_t j0 = 0; j0 < n; j0 += jcm) {
         const int jc = (int)((n - j0) < jcm ? (n - j0) : jcm);
+        const int s0 = (int)(j0 % WL);
         __syncthreads();
-        for (int64_t e = threadIdx.x; e < (int64_t)jc * kl; e += GB_ST) {
-            const int jj = (int)(e / kl);
-            const int64_t t = e % kl, c = j0 + jj, r = c + 1 + t;
-            Ls[jj * kl + t] = (r < n) ? Fb[bidx(kv, ldab, r, c)] : cx<T>(0, 0);
+        // multipliers of the chunk's columns, rows j+1 .. j+kl of column j
+        for (int e = threadIdx.x; e < LR * jc; e += GB_ST) {
+            const int jj = e / LR, rho = e % LR;
+            const int64_t r = j0 + rho, c = j0 + jj;
+            Lb[jj * LR + rho] = (rho > jj && rho <= jj + kl && r < n) ? Fb[bidx(kv, ldab, r, c)] : cx<T>(0, 0);
         }
-        if (threadIdx.x < jc) ps[threadIdx.x] = pv[j0 + threadIdx.x];
+        if (threadIdx.x < jc) ps[threadIdx.x] = (int)(pv[j0 + threadIdx.x] - j0);
         __syncthreads();
-        for (int jj = 0; jj < jc; ++jj) {
-            const int64_t j = j0 + jj, sj = j % WL, p = ps[jj];
-            if (p != j && threadIdx.x < cw) {
-                const int64_t sp = p % WL;
-                T t = W[sj * cw + threadIdx.x];
-                W[sj * cw + threadIdx.x] = W[sp * cw + threadIdx.x];
-                W[sp * cw + threadIdx.x] = t;
-            }
-            __syncthreads();
-            for (int64_t e = threadIdx.x; e < kl * cw; e += GB_ST) {
-                const int64_t t = e / cw;
-                const int cc = (int)(e % cw);
-                const int64_t r = j + 1 + t;
-                if (r < n) {
-                    T &w = W[(r % WL) * cw + cc];
-                    T v = w;
-                    cfma(v, cneg(Ls[jj * kl + t]), W[sj * cw + cc]);
-                    w = v;
+        if (threadIdx.x < cw) {
+            // (1) the chunk's interchanges, in order, on this right-hand side
+            const int cc = threadIdx.x;
+            for (int jj = 0; jj < jc; ++jj) {
+                const int p = ps[jj];
+                if (p != jj) {
+                    int sa = s0 + jj, sb = s0 + p;
+                    if (sa >= WL) sa -= WL;
+                    if (sb >= WL) sb -= WL;
+                    const T t = W[sa * cw + cc];
+                    W[sa * cw + cc] = W[sb * cw + cc];
+                    W[sb * cw + cc] = t;
                 }
             }
-            __syncthreads();
-            if (threadIdx.x < ncol) Xb[j + (c0 + threadIdx.x) * ldx] = W[sj * cw + threadIdx.x];
+        } else if (threadIdx.x >= 32 && threadIdx.x < 32 + jc) {
+            // L'_jj: the later interchanges of the chunk on column jj
+            const int jj = threadIdx.x - 32;
+            T *col = Lb + jj * LR;
+            for (int jp = jj + 1; jp < jc; ++jp) {
+                const int p = ps[jp];
+                if (p != jp) {
+                    const T t = col[jp];
+                    col[jp] = col[p];
+                    col[p] = t;
+                }
+            }
+        }
+        __syncthreads();
+        // (2) unit lower triangular solve on the chunk's rows
+        if (wid < cw) {
+            int sl = s0 + lane;
+            if (sl >= WL) sl -= WL;
+            T x = (lane < jc) ? W[sl * cw + wid] : cx<T>(0, 0);
+            for (int jj = 0; jj + 1 < jc; ++jj) {
+                const T xj = shfl_cx(x, jj);
+                if (lane > jj && lane < jc) cfma(x, cneg(Lb[jj * LR + lane]), xj);
+            }
+            if (lane < jc) {
+                W[sl * cw + wid] = x;
+                if (wid < ncol) Xb[j0 + lane + (c0 + wid) * ldx] = x;
+            }
+        }
+        __syncthreads();
+        // (3) rows j0 + jc .. j0 + jc + kl - 1 -= L'(those rows, chunk) x(chunk)
+        for (int e = threadIdx.x; e < kl * cw; e += GB_ST) {
+            const int t = e % (int)kl, cc = e / (int)kl;
+            const int64_t r = j0 + jc + t;
+            if (r < n) {
+                int sr = s0 + jc + t;
+                while (sr >= WL) sr -= WL;
+                T acc = W[sr * cw + cc];
+                int sj = s0;
+                for (int jj = 0; jj < jc; ++jj) {
+                    cfma(acc, cneg(Lb[jj * LR + jc + t]), W[sj * cw + cc]);
+                    if (++sj == WL) sj = 0;
+                }
+                W[sr * cw + cc] = acc;
+            }
         }
         __syncthreads();
         // rows j0 .. j0+jc-1 are final; their slots take rows j0+WL .. (first
-        // touched at step j0 + jcm + 1 or later)
+        // touched by the chunk after next at the earliest)
         for (int e = threadIdx.x; e < jc * cw; e += GB_ST) {
             const int jj = e / cw, cc = e % cw;
             const int64_t r = j0 + jj + WL;
-            W[(r % WL) * cw + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+            int sl = s0 + jj;
+            if (sl >= WL) sl -= WL;
+            W[sl * cw + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
         }
     }
 }
 
-// Backward pass: for j = n-1..0: x_j /= U(j,j); rows j-kv .. j-1 -= U(:, j) x_j.
-// Same window / staging scheme: WL = kv + 1 + jcm rows, jcm columns of U
-// (diagonal included) staged per chunk.
+// Backward pass: for j = n-1..0: x_j /= U(j,j); rows j-kv .. j-1 -= U(:, j) x_j,
+// taken jc columns at a time: an upper triangular solve on the chunk's rows
+// (a warp per right-hand side), then one rank-jc update of the kv rows
+// above it.  Window of WL = kv + 1 + jcm rows; the chunk's columns of U
+// (diagonal included) staged column-major, Us[jj * (kv + 1) + t] =
+// U(j - t, j) with j = j1 - jj.
 template <typename T>
 __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF, T *X,
                                                   int64_t ldx, int64_t sX, int cw, int jcm)
 {
     extern __shared__ unsigned char sm_raw[];
-    const int64_t kv = kl + ku, WL = kv + 1 + jcm;
+    const int kv = (int)(kl + ku), WL = kv + 1 + jcm, UL = kv + 1;
     T *W = reinterpret_cast<T *>(sm_raw);      // WL x cw window, row r at slot r % WL
-    T *Us = W + WL * cw;                       // jcm x (kv + 1): U(j - t, j), t = 0..kv
-    __shared__ T s_x[GB_CW];
+    T *Us = W + (size_t)WL * cw;               // jcm x (kv + 1)
     const int b = blockIdx.y;
     const T *Fb = F + (int64_t)b * sF;
     T *Xb = X + (int64_t)b * sX;
     const int64_t c0 = (int64_t)blockIdx.x * cw;
     const int ncol = (int)((nrhs - c0) < cw ? (nrhs - c0) : cw);
-    for (int64_t e = threadIdx.x; e < WL * cw; e += GB_ST) {
-        const int64_t t = e % WL;
-        const int cc = (int)(e / WL);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < WL * cw; e += GB_ST) {
+        const int t = e % WL, cc = e / WL;
         const int64_t r = n - 1 - t;
-        if (r >= 0) W[(r % WL) * cw + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+        if (r >= 0) W[(int)(r % WL) * cw + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
     }
     for (int64_t j1 = n - 1; j1 >= 0; j1 -= jcm) {
         const int jc = (int)((j1 + 1) < jcm ? (j1 + 1) : jcm);
+        const int s1 = (int)(j1 % WL);        // slot of row j1; row j1 - d at s1 - d (mod WL)
         __syncthreads();
-        for (int64_t e = threadIdx.x; e < (int64_t)jc * (kv + 1); e += GB_ST) {
-            const int jj = (int)(e / (kv + 1));
-            const int64_t t = e % (kv + 1), c = j1 - jj, r = c - t;
-            Us[jj * (kv + 1) + t] = (r >= 0) ? Fb[bidx(kv, ldab, r, c)] : cx<T>(0, 0);
+        for (int e = threadIdx.x; e < jc * UL; e += GB_ST) {
+            const int jj = e / UL, t = e % UL;
+            const int64_t c = j1 - jj, r = c - t;
+            Us[jj * UL + t] = (r >= 0) ? Fb[bidx(kv, ldab, r, c)] : cx<T>(0, 0);
         }
         __syncthreads();
-        for (int jj = 0; jj < jc; ++jj) {
-            const int64_t j = j1 - jj, sj = j % WL;
-            const T *u = Us + jj * (kv + 1);
-            if (threadIdx.x < cw) {
-                const T v = cdiv(W[sj * cw + threadIdx.x], u[0]);
-                W[sj * cw + threadIdx.x] = v;
-                s_x[threadIdx.x] = v;
-                if (threadIdx.x < ncol) Xb[j + (c0 + threadIdx.x) * ldx] = v;
+        // upper triangular solve on rows j1 - jc + 1 .. j1 (lane d: row j1 - d)
+        if (wid < cw) {
+            int sl = s1 - lane;
+            if (sl < 0) sl += WL;
+            T x = (lane < jc) ? W[sl * cw + wid] : cx<T>(0, 0);
+            for (int jj = 0; jj < jc; ++jj) {
+                if (lane == jj) x = cdiv(x, Us[jj * UL]);
+                const T xj = shfl_cx(x, jj);
+                const int t = lane - jj;
+                if (t > 0 && t <= kv && lane < jc) cfma(x, cneg(Us[jj * UL + t]), xj);
             }
-            __syncthreads();
-            for (int64_t e = threadIdx.x; e < kv * cw; e += GB_ST) {
-                const int64_t t = e / cw;
-                const int cc = (int)(e % cw);
-                const int64_t r = j - 1 - t;
-                if (r >= 0) {
-                    T &w = W[(r % WL) * cw + cc];
-                    T v = w;
-                    cfma(v, cneg(u[t + 1]), s_x[cc]);
-                    w = v;
+            if (lane < jc) {
+                W[sl * cw + wid] = x;
+                if (wid < ncol) Xb[j1 - lane + (c0 + wid) * ldx] = x;
+            }
+        }
+        __syncthreads();
+        // rows above the chunk: r = j1 - jc - tt, tt = 0 .. kv-1
+        for (int e = threadIdx.x; e < kv * cw; e += GB_ST) {
+            const int tt = e % kv, cc = e / kv;
+            const int64_t r = j1 - jc - tt;
+            if (r >= 0) {
+                int sr = s1 - jc - tt;
+                while (sr < 0) sr += WL;
+                T acc = W[sr * cw + cc];
+                int sj = s1;
+                for (int jj = 0; jj < jc; ++jj) {
+                    const int t = jc - jj + tt;       // (j1 - jj) - r
+                    if (t <= kv) cfma(acc, cneg(Us[jj * UL + t]), W[sj * cw + cc]);
+                    if (--sj < 0) sj = WL - 1;
                 }
+                W[sr * cw + cc] = acc;
             }
-            __syncthreads();
         }
+        __syncthreads();
         // rows j1-jc+1 .. j1 are final; their slots take rows j - WL
         for (int e = threadIdx.x; e < jc * cw; e += GB_ST) {
             const int jj = e / cw, cc = e % cw;
             const int64_t r = j1 - jj - WL;
-            if (r >= 0) W[(r % WL) * cw + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+            int sl = s1 - jj;
+            if (sl < 0) sl += WL;
+            if (r >= 0) W[sl * cw + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
         }
     }
 }
@@ -546,7 +618,7 @@ int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int
 // of es bytes: the staged factor columns and right-hand-side chunks.
 static size_t gb_fwd_smem(int64_t kl, size_t es, int cw, int jcm)
 {
-    return ((size_t)(kl + 1 + jcm) * cw + (size_t)jcm * kl) * es + jcm * sizeof(int) + 16;
+    return ((size_t)(kl + 1 + jcm) * cw + (size_t)jcm * (jcm + kl)) * es + jcm * sizeof(int) + 16;
 }
 static size_t gb_bwd_smem(int64_t kl, int64_t ku, size_t es, int cw, int jcm)
 {

@@ -22,11 +22,17 @@
 //     F = V^{-1} C' V^,   lambda_i = F_ii,   G_ij = F_ij / (lambda_j - lambda_i),
 //     Y' = V^ (I + G),    Y = Zh Y'          (error O(|D|^2 / gap)).
 //
-// Every product is an FP64 GEMM (the triangular factors' zero halves
-// skipped); the triangular solves are products with explicit triangular
-// inverses.  (The digit-sliced tensor-core GEMM is 48-bit fixed point per
-// row and column: at m0 = 1280 it left the Newton residual near 3e-12
-// instead of 1e-13.)  The eigenpairs are accepted only if each
+// The products that define C and C' (B~^{-1} A~, the similarity with Z)
+// are FP64 GEMMs; the triangular solves are products with explicit
+// triangular inverses.  The Newton step itself runs in defect form: with
+// T^ V^ = V^ Lh (Lh = diag T^), W' = C' V^ - V^ Lh = D V^ is small, F =
+// Lh + V^{-1} W', and the residual C' Y' - Y' L = V^ S1 + W' (I + G) with
+// S1 small too.  Every one of these products has a small operand, so they
+// run on the digit-sliced tensor-core GEMM (48-bit fixed point per row and
+// column of its operands) at FP64 accuracy; computed as plain products of
+// O(1) matrices on it, the step's residual stalled near 3e-12 at m0 = 1280
+// instead of 1e-13.  (Without the digit-sliced scratch every product is an
+// FP64 GEMM.)  The eigenpairs are accepted only if each
 // ||C' y'_i - lambda_i y'_i|| / ((max|C_ij| + |lambda_i|) ||y'_i||) is at
 // most accept_tol; otherwise the caller runs the cold solve (Hessenberg
 // reduction and QR of the whole matrix).  The subspace of every pass is the
@@ -94,9 +100,10 @@ __global__ void k_newton_g(int m, zd *__restrict__ F, const zd *__restrict__ lam
 }
 
 // max_i ||W_i - lambda_i Y_i|| / ((cnorm + |lambda_i|) ||Y_i||) into *out
-// (non-negative doubles order like their bit patterns).  Warp per column.
+// (non-negative doubles order like their bit patterns); is_resid: W holds
+// the residual block itself.  Warp per column.
 __global__ void k_eig_resid(int m, const zd *__restrict__ W, const zd *__restrict__ Y, const zd *__restrict__ lam,
-                            double cnorm, unsigned long long *__restrict__ out)
+                            double cnorm, unsigned long long *__restrict__ out, int is_resid = 0)
 {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= m) return;
@@ -106,7 +113,7 @@ __global__ void k_eig_resid(int m, const zd *__restrict__ W, const zd *__restric
     double r = 0.0, yy = 0.0;
     for (int p = lane; p < m; p += 32) {
         const zd yv = y[p];
-        const zd d = zsub(w[p], zmul(l, yv));
+        const zd d = is_resid ? w[p] : zsub(w[p], zmul(l, yv));
         r += zabs2(d);
         yy += zabs2(yv);
     }
@@ -119,6 +126,46 @@ __global__ void k_eig_resid(int m, const zd *__restrict__ W, const zd *__restric
         double rel = (yy > 0.0) ? sqrt(r / yy) / (cnorm + zabs(l)) : 1e300;
         if (!(rel == rel)) rel = 1e300;
         atomicMax(out, (unsigned long long)__double_as_longlong(rel));
+    }
+}
+
+// D = C' - T^ (m x m; T^ upper triangular) and lamh = diag(T^).
+__global__ void k_defect_split(int m, const zd *__restrict__ Cq, const zd *__restrict__ Th, zd *__restrict__ D,
+                               zd *__restrict__ lamh)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        const zd t = Th[e];
+        D[e] = (i <= j) ? zsub(Cq[e], t) : Cq[e];
+        if (i == j) lamh[i] = t;
+    }
+}
+
+// F_ii += lamh_i, then lambda_i = F_ii (alpha), beta_i = 1.
+__global__ void k_add_diag_lambda(int m, zd *__restrict__ F, const zd *__restrict__ lamh, zd *__restrict__ alpha,
+                                  zd *__restrict__ beta)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const zd f = zadd(F[i + (int64_t)i * m], lamh[i]);
+    F[i + (int64_t)i * m] = f;
+    alpha[i] = f;
+    beta[i] = zmake(1.0, 0.0);
+}
+
+// S1 = (Lh - L) + Lh G - G L (Lh = diag(lamh), L = diag(lam)):
+// S1_ij = G_ij (lamh_i - lam_j) off the diagonal, lamh_i - lam_i on it
+// (G_ii = 0).
+__global__ void k_newton_s1(int m, const zd *__restrict__ G, const zd *__restrict__ lamh, const zd *__restrict__ lam,
+                            zd *__restrict__ S1)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        S1[e] = (i == j) ? zsub(lamh[i], lam[i]) : zmul(G[e], zsub(lamh[i], lam[j]));
     }
 }
 
@@ -222,10 +269,17 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
         if ((r = oz_prepare_cols(s, K, N, Bm, ldb, oz->cols))) return r;
         return oz_gemm(s, M, N, K, oz->rows, oz->cols, alpha, nullptr, 0, beta, Cm, ldc, oz->err);
     };
+    // the products that define C and C' themselves: FP64 unless the pass's
+    // pairs are needed only well above the digit-sliced GEMM's resolution
+    auto mulc = [&](int conj_a, int64_t M, int64_t N, int64_t K, zd alpha, const zd *Am, int64_t lda, const zd *Bm,
+                    int64_t ldb, zd beta, zd *Cm, int64_t ldc, int tri) -> int {
+        if (!prm.cold_fp32) return zgemm_batched(s, conj_a, M, N, K, alpha, Am, lda, 0, Bm, ldb, 0, beta, Cm, ldc, 0, 1, tri);
+        return mul(conj_a, M, N, K, alpha, Am, lda, Bm, ldb, beta, Cm, ldc, tri);
+    };
     // C = B~^{-1} A~ (B~ = R2 is upper triangular), into Cp
     if ((e = mark(0.0))) return e;
     if ((e = tri_inverse(s, m, Bt, m, w.W, w.Ts))) return e;
-    if ((e = mul(0, m, m, m, one, w.W, m, A, m, zero, w.Cp, m, 1))) return e;
+    if ((e = mulc(0, m, m, m, one, w.W, m, A, m, zero, w.Cp, m, 1))) return e;
     if ((e = mark(tri_inv + 4.0 * m3))) return e;
     const zd *C = w.Cp;
     k_col_stats<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, C, w.lower, w.cmax);
@@ -277,8 +331,8 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     zd *Cq = A;
     FEAST_CUDA_TRY(cudaMemcpyAsync(Cq, C, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
     if ((e = mark(0.0))) return e;
-    if ((e = mul(0, m, mb, mb, one, C + (int64_t)k * m, m, w.Z, mb, zero, Cq + (int64_t)k * m, m, 0))) return e;
-    if ((e = mul(1, mb, m, mb, one, w.Z, mb, Cq + k, m, zero, Bt + k, m, 0))) return e;
+    if ((e = mulc(0, m, mb, mb, one, C + (int64_t)k * m, m, w.Z, mb, zero, Cq + (int64_t)k * m, m, 0))) return e;
+    if ((e = mulc(1, mb, m, mb, one, w.Z, mb, Cq + k, m, zero, Bt + k, m, 0))) return e;
     if ((e = mark(16.0 * (double)m * mb * mb))) return e;
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(Cq + k, sizeof(zd) * m, Bt + k, sizeof(zd) * m, sizeof(zd) * mb, m,
                                      cudaMemcpyDeviceToDevice, s));
@@ -291,26 +345,59 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
                                          sizeof(zd) * mb, mb, cudaMemcpyDeviceToDevice, s));
     zd *Vh = Bt;  // V^, unit upper triangular
     if ((e = schur_vectors(s, m, w.Cp, Vh, hn, w.W))) return e;
-    // F = V^{-1} (C' V^)
-    if ((e = mark(0.0))) return e;
-    if ((e = mul(0, m, m, m, one, Cq, m, Vh, m, zero, w.W, m, 2))) return e;
-    if ((e = tri_inverse(s, m, Vh, m, w.Cp, w.Ts))) return e;
     zd *F = V;
-    if ((e = mul(0, m, m, m, one, w.Cp, m, w.W, m, zero, F, m, 1))) return e;
-    if ((e = mark(8.0 * m3 + tri_inv))) return e;
-    k_diag_lambda<<<cdiv(m, 128), 128, 0, s>>>(m, F, alpha, beta);
-    FEAST_LAUNCH_CHECK();
-    FEAST_CUDA_TRY(cudaMemsetAsync(w.res, 0, 16, s));
-    k_newton_g<<<grid_for(mm), 256, 0, s>>>(m, F, alpha, w.bad);
-    FEAST_LAUNCH_CHECK();
-    // Y' = V^ + V^ G, and its residual against C'
-    FEAST_CUDA_TRY(cudaMemcpyAsync(w.Yp, Vh, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
-    if ((e = mark(0.0))) return e;
-    if ((e = mul(0, m, m, m, one, Vh, m, F, m, one, w.Yp, m, 1))) return e;
-    if ((e = mul(0, m, m, m, one, Cq, m, w.Yp, m, zero, w.W, m, 0))) return e;
-    if ((e = mark(12.0 * m3))) return e;
-    k_eig_resid<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, w.W, w.Yp, alpha, hn, w.res);
-    FEAST_LAUNCH_CHECK();
+    if (!oz) {
+        // F = V^{-1} (C' V^)
+        if ((e = mark(0.0))) return e;
+        if ((e = mul(0, m, m, m, one, Cq, m, Vh, m, zero, w.W, m, 2))) return e;
+        if ((e = tri_inverse(s, m, Vh, m, w.Cp, w.Ts))) return e;
+        if ((e = mul(0, m, m, m, one, w.Cp, m, w.W, m, zero, F, m, 1))) return e;
+        if ((e = mark(8.0 * m3 + tri_inv))) return e;
+        k_diag_lambda<<<cdiv(m, 128), 128, 0, s>>>(m, F, alpha, beta);
+        FEAST_LAUNCH_CHECK();
+        FEAST_CUDA_TRY(cudaMemsetAsync(w.res, 0, 16, s));
+        k_newton_g<<<grid_for(mm), 256, 0, s>>>(m, F, alpha, w.bad);
+        FEAST_LAUNCH_CHECK();
+        // Y' = V^ + V^ G, and its residual against C'
+        FEAST_CUDA_TRY(cudaMemcpyAsync(w.Yp, Vh, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+        if ((e = mark(0.0))) return e;
+        if ((e = mul(0, m, m, m, one, Vh, m, F, m, one, w.Yp, m, 1))) return e;
+        if ((e = mul(0, m, m, m, one, Cq, m, w.Yp, m, zero, w.W, m, 0))) return e;
+        if ((e = mark(12.0 * m3))) return e;
+        k_eig_resid<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, w.W, w.Yp, alpha, hn, w.res);
+        FEAST_LAUNCH_CHECK();
+    } else {
+        // The same step in defect form, every product on the digit-sliced
+        // GEMM with one small operand (its error is relative to the
+        // operands' row / column maxima): with C' = T^ + D and T^ V^ = V^ Lh,
+        //   W' = C' V^ - V^ Lh = D V^,   F = Lh + V^{-1} W',
+        //   Y' = V^ + V^ G,   C' Y' - Y' L = V^ S1 + W' + W' G,
+        //   S1 = (Lh - L) + Lh G - G L   (L = diag(F), G as above).
+        zd *lamh = (zd *)w.lower;   // diag(T^) (the column statistics are spent)
+        k_defect_split<<<grid_for(mm), 256, 0, s>>>(m, Cq, w.Cp, w.W, lamh);
+        FEAST_LAUNCH_CHECK();
+        if ((e = mark(0.0))) return e;
+        if ((e = mul(0, m, m, m, one, w.W, m, Vh, m, zero, w.S, m, 2))) return e;       // W'
+        if ((e = tri_inverse(s, m, Vh, m, w.Cp, w.Ts))) return e;
+        if ((e = mul(0, m, m, m, one, w.Cp, m, w.S, m, zero, F, m, 1))) return e;       // V^{-1} W'
+        if ((e = mark(8.0 * m3 + tri_inv))) return e;   // (algorithmic: V^ triangular)
+        k_add_diag_lambda<<<cdiv(m, 128), 128, 0, s>>>(m, F, lamh, alpha, beta);
+        FEAST_LAUNCH_CHECK();
+        FEAST_CUDA_TRY(cudaMemsetAsync(w.res, 0, 16, s));
+        k_newton_g<<<grid_for(mm), 256, 0, s>>>(m, F, alpha, w.bad);
+        FEAST_LAUNCH_CHECK();
+        FEAST_CUDA_TRY(cudaMemcpyAsync(w.Yp, Vh, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+        k_newton_s1<<<grid_for(mm), 256, 0, s>>>(m, F, lamh, alpha, w.W);
+        FEAST_LAUNCH_CHECK();
+        FEAST_CUDA_TRY(cudaMemcpyAsync(Cq, w.S, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));   // R = W'
+        if ((e = mark(0.0))) return e;
+        if ((e = mul(0, m, m, m, one, Vh, m, F, m, one, w.Yp, m, 1))) return e;       // Y' = V^ + V^ G
+        if ((e = mul(0, m, m, m, one, Vh, m, w.W, m, one, Cq, m, 1))) return e;       // R += V^ S1
+        if ((e = mul(0, m, m, m, one, w.S, m, F, m, one, Cq, m, 0))) return e;        // R += W' G
+        if ((e = mark(16.0 * m3))) return e;
+        k_eig_resid<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, Cq, w.Yp, alpha, hn, w.res, 1);
+        FEAST_LAUNCH_CHECK();
+    }
     struct {
         unsigned long long r;
         int bad;
@@ -328,7 +415,7 @@ int zeig_warm(cudaStream_t s, int m, zd *A, zd *Bt, zd *alpha, zd *beta, zd *V, 
     // Y = Zh Y', unit columns
     FEAST_CUDA_TRY(cudaMemcpy2DAsync(V, sizeof(zd) * m, w.Yp, sizeof(zd) * m, sizeof(zd) * k, m,
                                      cudaMemcpyDeviceToDevice, s));
-    if ((e = mul(0, mb, m, mb, one, w.Z, mb, w.Yp + k, m, zero, V + k, m, 0))) return e;
+    if ((e = mulc(0, mb, m, mb, one, w.Z, mb, w.Yp + k, m, zero, V + k, m, 0))) return e;
     if ((e = normalise_cols(s, m, V))) return e;
     res->accepted = 1;
     return FEAST_OK;
