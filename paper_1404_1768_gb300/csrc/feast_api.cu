@@ -144,6 +144,7 @@ constexpr double kWarmAccMin = 1e-12;  // the cold double-single QR's own backwa
 // FP32 Schur form (~1e-6 remainder) one Newton step reaches ~1e-10.
 constexpr double kColdFp32AccMin = 1e-8;
 constexpr int kZeigMinM = 8;         // smallest projected problem on the standard-form QR
+constexpr double kZeigSmallEpsMin = 1e-11;   // ... when m0 <= 64: the strictest eps it serves
 
 struct Carver {
     char *base;
@@ -863,7 +864,10 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
     // the projected solve is held to 1e-3 of the accuracy already reached
     // (eta before any pair is accepted)
     const double eref = (c->c_prev > 0 && c->e_prev > 0.0) ? c->e_prev : c->eta;
-    const double acc = fmax(kWarmAccMin, 1e-3 * eref);
+    // (a pass at max_iter returns its pairs whatever the tests say: full
+    // accuracy, as at any pass that may stop)
+    const bool final_pass = c->k >= c->max_iter && !c->no_stop;
+    const double acc = final_pass ? kWarmAccMin : fmax(kWarmAccMin, 1e-3 * eref);
     if (c->warm_ready) {
         // the previous pass filtered its |rho|-ordered Ritz vectors: C is
         // block upper triangular up to a remainder of the size of its
@@ -900,18 +904,21 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
     }
     if (!c->last_warm.accepted) {
         // before any pair has been accepted the stop cannot fire at this
-        // pass (lines 13-14 need a fixed non-zero count), so its eigenpairs
-        // are needed only far beyond their residuals (>= eta): the QR
-        // deflates at 1e-8.  Any pass that may stop deflates at the
-        // double-single floor, so that its pairs reach eps.
-        const double defl = (c->c_prev > 0) ? 0.0 : 1e-8;
+        // pass (lines 13-14 need a fixed non-zero count), so unless it is
+        // the last pass (max_iter) its eigenpairs are needed only far
+        // beyond their residuals (>= eta): the QR deflates at 1e-8.  Any
+        // pass that may stop deflates at the double-single floor, so that
+        // its pairs reach eps.
+        const double defl = (c->c_prev > 0 || final_pass) ? 0.0 : 1e-8;
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->Q, c->P, sizeof(zd) * 2 * m * m, cudaMemcpyDeviceToDevice, s));
         if (rr && (e = triangularise_bt(c))) return e;
         // B~ is upper triangular here (R2, or made so for Rayleigh-Ritz):
         // the standard-form QR on the FP32 pipe (double-single) from m =
-        // kZeigMinM up; the FP64 QZ of the pencil only below (GB300's FP64
-        // pipe made it ~50 ms at m0 = 64)
-        if (m >= kZeigMinM)
+        // kZeigMinM up (GB300's FP64 pipe made the FP64 QZ ~50 ms at m0 =
+        // 64); a small problem keeps the FP64 QZ when eps is within ~100x
+        // of the double-single QR's backward error (2^-44 of ||C||), so
+        // that e(k) can still fall below eps
+        if (m > 64 || (m >= kZeigMinM && c->eps >= kZeigSmallEpsMin))
             e = zeig_large(s, (int)m, c->Q, c->Q + m * m, c->alpha, c->beta, c->Yv, c->qz_work, &c->st->qz_fail,
                            &c->st->timeout, &c->st->qz_sweeps, defl);
         else

@@ -217,6 +217,19 @@ __global__ void k_gb_writeback(int64_t n, int64_t kl, int64_t ku, int64_t k0, in
     }
 }
 
+// Asynchronous global -> shared copies of B bytes (B = 4, 8 or 16); an
+// invalid source writes zeros instead (nothing is read).  The staging of
+// the next chunk's factor columns runs under the current chunk's solves.
+template <int B>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(B), "r"(valid ? B : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Forward pass of the solve (unblocked convention: for j = 0..n-1, swap
 // rows j and piv[j], then rows j+1 .. j+kl -= l_j x_j), taken jc steps at a
 // time.  Within a chunk the interchanges commute to the front: the chunk is
@@ -228,17 +241,20 @@ __global__ void k_gb_writeback(int64_t n, int64_t kl, int64_t ku, int64_t k0, in
 // rank-jc update of the kl rows below it.  CTA = (chunk of cw <= GB_CW
 // right-hand sides, node); the right-hand sides live in a circular window
 // of WL = kl + 1 + jcm rows in shared memory, the chunk's multipliers
-// (jcm + kl rows x jcm columns, column-major) and pivots beside it.
+// (jcm + kl rows x jcm columns, column-major) and pivots beside it, in
+// nbuf = 2 buffers when they fit (the next chunk's copied in meanwhile).
 template <typename T>
 __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
-                                                  const T *F, int64_t ldab, int64_t sF,
-                                                  const int *piv, T *X, int64_t ldx, int64_t sX, int cw, int jcm)
+                                                  const T *F, int64_t ldab, int64_t sF, const int *piv, T *X,
+                                                  int64_t ldx, int64_t sX, int cw, int jcm, int nbuf)
 {
-    extern __shared__ unsigned char sm_raw[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
     const int WL = (int)(kl + 1 + jcm), LR = (int)(jcm + kl), kv = (int)(kl + ku);
     T *W = reinterpret_cast<T *>(sm_raw);      // WL x cw window, row r at slot r % WL
-    T *Lb = W + (size_t)WL * cw;               // LR x jcm: Lb[jj * LR + rho] = L'(j0 + rho, j0 + jj)
-    int *ps = reinterpret_cast<int *>(Lb + (size_t)LR * jcm);   // pivots of the chunk, minus j0
+    T *const Lb0 = W + (size_t)WL * cw;         // LR x jcm: Lb[jj * LR + rho] = L'(j0 + rho, j0 + jj)
+    T *const Lb1 = Lb0 + (size_t)(nbuf - 1) * LR * jcm;
+    int *const pb0 = reinterpret_cast<int *>(Lb0 + (size_t)nbuf * LR * jcm);   // the chunk's pivots (global rows)
+    int *const pb1 = pb0 + (nbuf - 1) * jcm;
     const int b = blockIdx.y;
     const T *Fb = F + (int64_t)b * sF;
     const int *pv = piv + (int64_t)b * n;
@@ -246,27 +262,37 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
     const int64_t c0 = (int64_t)blockIdx.x * cw;
     const int ncol = (int)((nrhs - c0) < cw ? (nrhs - c0) : cw);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto stage = [&](int64_t js, T *Lb, int *ps) {
+        const int jcs = (int)((n - js) < jcm ? (n - js) : jcm);
+        for (int e = threadIdx.x; e < LR * jcs; e += GB_ST) {
+            const int jj = e / LR, rho = e % LR;
+            const int64_t r = js + rho, c = js + jj;
+            const bool in = rho > jj && rho <= jj + kl && r < n;
+            cp_async<sizeof(T)>(Lb + jj * LR + rho, in ? (const void *)(Fb + bidx(kv, ldab, r, c)) : (const void *)Fb,
+                                in);
+        }
+        if (threadIdx.x < jcs) cp_async<4>(ps + threadIdx.x, pv + js + threadIdx.x, true);
+    };
     for (int e = threadIdx.x; e < WL * cw; e += GB_ST) {
         const int r = e % WL, cc = e / WL;
-        W[r * cw + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+        const bool in = r < n && cc < ncol;
+        cp_async<sizeof(T)>(W + r * cw + cc, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb, in);
     }
-    for (int64_t j0 = 0; j0 < n; j0 += jcm) {
+    stage(0, Lb0, pb0);
+    cp_async_commit();
+    int k = 0;
+    for (int64_t j0 = 0; j0 < n; j0 += jcm, ++k) {
         const int jc = (int)((n - j0) < jcm ? (n - j0) : jcm);
         const int s0 = (int)(j0 % WL);
-        __syncthreads();
-        // multipliers of the chunk's columns, rows j+1 .. j+kl of column j
-        for (int e = threadIdx.x; e < LR * jc; e += GB_ST) {
-            const int jj = e / LR, rho = e % LR;
-            const int64_t r = j0 + rho, c = j0 + jj;
-            Lb[jj * LR + rho] = (rho > jj && rho <= jj + kl && r < n) ? Fb[bidx(kv, ldab, r, c)] : cx<T>(0, 0);
-        }
-        if (threadIdx.x < jc) ps[threadIdx.x] = (int)(pv[j0 + threadIdx.x] - j0);
+        T *Lb = (k & 1) ? Lb1 : Lb0;
+        const int *ps = (k & 1) ? pb1 : pb0;
+        cp_async_wait_all();
         __syncthreads();
         if (threadIdx.x < cw) {
             // (1) the chunk's interchanges, in order, on this right-hand side
             const int cc = threadIdx.x;
             for (int jj = 0; jj < jc; ++jj) {
-                const int p = ps[jj];
+                const int p = (int)(ps[jj] - j0);
                 if (p != jj) {
                     int sa = s0 + jj, sb = s0 + p;
                     if (sa >= WL) sa -= WL;
@@ -281,7 +307,7 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
             const int jj = threadIdx.x - 32;
             T *col = Lb + jj * LR;
             for (int jp = jj + 1; jp < jc; ++jp) {
-                const int p = ps[jp];
+                const int p = (int)(ps[jp] - j0);
                 if (p != jp) {
                     const T t = col[jp];
                     col[jp] = col[p];
@@ -290,6 +316,11 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
             }
         }
         __syncthreads();
+        const bool more = j0 + jcm < n;
+        if (nbuf == 2 && more) {
+            stage(j0 + jcm, (k & 1) ? Lb0 : Lb1, (k & 1) ? pb0 : pb1);
+            cp_async_commit();
+        }
         // (2) unit lower triangular solve on the chunk's rows
         if (wid < cw) {
             int sl = s0 + lane;
@@ -322,16 +353,20 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
             }
         }
         __syncthreads();
-        // rows j0 .. j0+jc-1 are final; their slots take rows j0+WL .. (first
-        // touched by the chunk after next at the earliest)
+        // rows j0 .. j0+jc-1 are final; their slots take rows j0+WL ..
         for (int e = threadIdx.x; e < jc * cw; e += GB_ST) {
             const int jj = e / cw, cc = e % cw;
             const int64_t r = j0 + jj + WL;
             int sl = s0 + jj;
             if (sl >= WL) sl -= WL;
-            W[sl * cw + cc] = (r < n && cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+            const bool in = r < n && cc < ncol;
+            cp_async<sizeof(T)>(W + sl * cw + cc, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb,
+                                in);
         }
+        if (nbuf == 1 && more) stage(j0 + jcm, Lb0, pb0);   // (its buffer is free only now)
+        cp_async_commit();
     }
+    cp_async_wait_all();
 }
 
 // Backward pass: for j = n-1..0: x_j /= U(j,j); rows j-kv .. j-1 -= U(:, j) x_j,
@@ -339,37 +374,56 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
 // (a warp per right-hand side), then one rank-jc update of the kv rows
 // above it.  Window of WL = kv + 1 + jcm rows; the chunk's columns of U
 // (diagonal included) staged column-major, Us[jj * (kv + 1) + t] =
-// U(j - t, j) with j = j1 - jj.
+// U(j - t, j) with j = j1 - jj, in nbuf buffers as in the forward pass.
 template <typename T>
 __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF, T *X,
-                                                  int64_t ldx, int64_t sX, int cw, int jcm)
+                                                  int64_t ldx, int64_t sX, int cw, int jcm, int nbuf)
 {
-    extern __shared__ unsigned char sm_raw[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
     const int kv = (int)(kl + ku), WL = kv + 1 + jcm, UL = kv + 1;
     T *W = reinterpret_cast<T *>(sm_raw);      // WL x cw window, row r at slot r % WL
-    T *Us = W + (size_t)WL * cw;               // jcm x (kv + 1)
+    T *const Ub0 = W + (size_t)WL * cw;
+    T *const Ub1 = Ub0 + (size_t)(nbuf - 1) * jcm * UL;
     const int b = blockIdx.y;
     const T *Fb = F + (int64_t)b * sF;
     T *Xb = X + (int64_t)b * sX;
     const int64_t c0 = (int64_t)blockIdx.x * cw;
     const int ncol = (int)((nrhs - c0) < cw ? (nrhs - c0) : cw);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto stage = [&](int64_t js, T *Us) {
+        const int jcs = (int)((js + 1) < jcm ? (js + 1) : jcm);
+        for (int e = threadIdx.x; e < jcs * UL; e += GB_ST) {
+            const int jj = e / UL, t = e % UL;
+            const int64_t c = js - jj, r = c - t;
+            const bool in = r >= 0;
+            cp_async<sizeof(T)>(Us + jj * UL + t, in ? (const void *)(Fb + bidx(kv, ldab, r, c)) : (const void *)Fb,
+                                in);
+        }
+    };
     for (int e = threadIdx.x; e < WL * cw; e += GB_ST) {
         const int t = e % WL, cc = e / WL;
         const int64_t r = n - 1 - t;
-        if (r >= 0) W[(int)(r % WL) * cw + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+        if (r >= 0) {
+            const bool in = cc < ncol;
+            cp_async<sizeof(T)>(W + (int)(r % WL) * cw + cc, in ? (const void *)(Xb + r + (c0 + cc) * ldx)
+                                                                : (const void *)Xb, in);
+        }
     }
-    for (int64_t j1 = n - 1; j1 >= 0; j1 -= jcm) {
+    stage(n - 1, Ub0);
+    cp_async_commit();
+    int k = 0;
+    for (int64_t j1 = n - 1; j1 >= 0; j1 -= jcm, ++k) {
         const int jc = (int)((j1 + 1) < jcm ? (j1 + 1) : jcm);
         const int s1 = (int)(j1 % WL);        // slot of row j1; row j1 - d at s1 - d (mod WL)
+        const T *Us = (k & 1) ? Ub1 : Ub0;
+        const bool more = j1 - jcm >= 0;
+        cp_async_wait_all();
         __syncthreads();
-        for (int e = threadIdx.x; e < jc * UL; e += GB_ST) {
-            const int jj = e / UL, t = e % UL;
-            const int64_t c = j1 - jj, r = c - t;
-            Us[jj * UL + t] = (r >= 0) ? Fb[bidx(kv, ldab, r, c)] : cx<T>(0, 0);
+        if (nbuf == 2 && more) {
+            stage(j1 - jcm, (k & 1) ? Ub0 : Ub1);
+            cp_async_commit();
         }
-        __syncthreads();
         // upper triangular solve on rows j1 - jc + 1 .. j1 (lane d: row j1 - d)
         if (wid < cw) {
             int sl = s1 - lane;
@@ -411,9 +465,16 @@ __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t
             const int64_t r = j1 - jj - WL;
             int sl = s1 - jj;
             if (sl < 0) sl += WL;
-            if (r >= 0) W[sl * cw + cc] = (cc < ncol) ? Xb[r + (c0 + cc) * ldx] : cx<T>(0, 0);
+            if (r >= 0) {
+                const bool in = cc < ncol;
+                cp_async<sizeof(T)>(W + sl * cw + cc, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb,
+                                    in);
+            }
         }
+        if (nbuf == 1 && more) stage(j1 - jcm, Ub0);
+        cp_async_commit();
     }
+    cp_async_wait_all();
 }
 
 // Y = op X with op = A (which 0) or z_j B - A style combinations done by the
@@ -429,6 +490,183 @@ __global__ void k_gb_matmul(int64_t n, int64_t kl, int64_t ku, const zd *M, int6
         zd acc = zmake(0.0, 0.0);
         for (int64_t j = j0; j <= j1; ++j) zfma(acc, M[ku + i - j + j * ldin], X[j + c * ldx]);
         Y[i + c * ldy] = acc;
+    }
+}
+
+// The whole band LU of one node in one CTA (complex64; one launch for all
+// nodes): for each panel of nb columns, (1) the panel's nb + kl rows into
+// shared memory, (2) its partial-pivot LU there (pivot: largest |.|^2,
+// the first on ties), (3) the interchanges on the kv columns right of it
+// in the band, (4) U12 = L11^{-1} A12 (a thread per column, kept in shared
+// memory), (5) A22 -= L21 U12 on the band (a warp per 32 rows x 4
+// columns), (6) the panel back with its multipliers in the unblocked
+// convention.  The same factors as the multi-launch form; the nodes are
+// independent, so no CTA waits for another.
+constexpr int GL_T = 256;
+constexpr int GL_NB = 32;
+template <typename T>
+__global__ void __launch_bounds__(GL_T) k_gb_lu_fused(int64_t n, int kl, int ku, T *F, int64_t ldab, int64_t sF,
+                                                     int *piv, int nbp, int *info, int *row)
+{
+    typedef typename CxReal<T>::type R;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int kv = kl + ku, ldd = nbp + kl;
+    T *D = reinterpret_cast<T *>(sm_raw);      // ldd x nbp panel, column-major
+    const int ldu = kv + 1;
+    T *U = D + (size_t)ldd * nbp;               // nbp x kv, row-major: U[k * ldu + cc]
+    int *ps = reinterpret_cast<int *>(U + (size_t)nbp * ldu);  // local pivots of the panel
+    __shared__ R s_val[GL_T / 32];
+    __shared__ int s_idx[GL_T / 32];
+    __shared__ int s_p;
+    const int b = blockIdx.x;
+    T *Fb = F + (int64_t)b * sF;
+    int *pvb = piv + (int64_t)b * n;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const T zero = cx<T>(0, 0);
+    for (int64_t k0 = 0; k0 < n; k0 += nbp) {
+        const int nb = (int)((n - k0) < nbp ? (n - k0) : nbp);
+        const int rows = (int)((n - k0) < ldd ? (n - k0) : ldd);
+        // (1) gather
+        for (int e = tid; e < ldd * nb; e += GL_T) {
+            const int r = e % ldd, cc = e / ldd;
+            const int64_t i = k0 + r, c = k0 + cc;
+            D[cc * ldd + r] = (r < rows && i - c <= kl && c - i <= kv) ? Fb[bidx(kv, ldab, i, c)] : zero;
+        }
+        __syncthreads();
+        // (2) panel LU
+        for (int j = 0; j < nb; ++j) {
+            const T *dj = D + j * ldd;
+            R best = -1;
+            int bi = j;
+            for (int r = j + tid; r < rows; r += GL_T) {
+                const R v = cabs2(dj[r]);
+                if (v > best) { best = v; bi = r; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const R ov = __shfl_down_sync(0xffffffffu, best, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                R bv = s_val[0];
+                int bx = s_idx[0];
+                for (int w = 1; w < GL_T / 32; ++w)
+                    if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bx)) { bv = s_val[w]; bx = s_idx[w]; }
+                s_p = bx;
+                ps[j] = bx;
+                if (bv == 0 && info && atomicCAS(info, 0, b + 1) == 0 && row) *row = (int)(k0 + j) + 1;
+            }
+            __syncthreads();
+            const int p = s_p;
+            if (p != j && tid < nb) {
+                const T t = D[tid * ldd + j];
+                D[tid * ldd + j] = D[tid * ldd + p];
+                D[tid * ldd + p] = t;
+            }
+            __syncthreads();
+            const T d = D[j * ldd + j];
+            if (!cis_zero(d)) {
+                for (int r = j + 1 + tid; r < rows; r += GL_T) D[j * ldd + r] = cdiv(D[j * ldd + r], d);
+                __syncthreads();
+                const int rr = rows - j - 1, cn = nb - j - 1;
+                for (int e = tid; e < rr * cn; e += GL_T) {
+                    const int r = j + 1 + e % rr, cc = j + 1 + e / rr;
+                    T v = D[cc * ldd + r];
+                    cfma(v, cneg(D[j * ldd + r]), D[cc * ldd + j]);
+                    D[cc * ldd + r] = v;
+                }
+            }
+            __syncthreads();
+        }
+        if (tid < nb) pvb[k0 + tid] = (int)(k0 + ps[tid]);
+        // (3) the interchanges on the columns right of the panel
+        for (int cc = tid; cc < kv; cc += GL_T) {
+            const int64_t c = k0 + nb + cc;
+            if (c >= n) continue;
+            for (int j = 0; j < nb; ++j) {
+                const int64_t r = k0 + j, p = k0 + ps[j];
+                if (p != r && c - r <= kv) {
+                    T &x = Fb[bidx(kv, ldab, r, c)], &y = Fb[bidx(kv, ldab, p, c)];
+                    const T t = x;
+                    x = y;
+                    y = t;
+                }
+            }
+        }
+        __syncthreads();
+        // (4) U12 = L11^{-1} A12 in shared memory (rows padded to kv + 1),
+        // a thread per column for the triangular solve
+        for (int e = tid; e < nbp * kv; e += GL_T) {
+            const int r = e % nbp, cc = e / nbp;
+            const int64_t c = k0 + nb + cc;
+            U[r * ldu + cc] = (r < nb && c < n && c - (k0 + r) <= kv) ? Fb[bidx(kv, ldab, k0 + r, c)] : zero;
+        }
+        __syncthreads();
+        for (int cc = tid; cc < kv; cc += GL_T)
+            for (int i = 0; i + 1 < nb; ++i) {
+                const T xi = U[i * ldu + cc];
+                for (int r = i + 1; r < nb; ++r) {
+                    T v = U[r * ldu + cc];
+                    cfma(v, cneg(D[i * ldd + r]), xi);
+                    U[r * ldu + cc] = v;
+                }
+            }
+        __syncthreads();
+        for (int e = tid; e < nb * kv; e += GL_T) {
+            const int r = e % nb, cc = e / nb;
+            const int64_t c = k0 + nb + cc;
+            if (c < n && c - (k0 + r) <= kv) Fb[bidx(kv, ldab, k0 + r, c)] = U[r * ldu + cc];
+        }
+        // (5) A22 -= L21 U12: rows k0+nb+t (t < rows-nb <= kl), columns
+        // k0+nb+cc (cc < kv) -- all inside the band; a warp per 32 rows x 4
+        // columns, a lane per row
+        {
+            const int R2 = rows - nb;
+            const int rt = (R2 + 31) / 32, ct = (kv + 3) / 4;
+            for (int task = wid; task < rt * ct; task += GL_T / 32) {
+                const int t = (task % rt) * 32 + lane, c4 = (task / rt) * 4;
+                if (t >= R2) continue;
+                T acc[4] = {zero, zero, zero, zero};
+                for (int k = 0; k < nb; ++k) {
+                    const T l = D[k * ldd + nb + t];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (c4 + u < kv) cfma(acc[u], l, U[k * ldu + c4 + u]);
+                }
+                const int64_t i = k0 + nb + t;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t c = k0 + nb + c4 + u;
+                    if (c4 + u < kv && c < n) {
+                        T &dst = Fb[bidx(kv, ldab, i, c)];
+                        dst = cadd(dst, cneg(acc[u]));
+                    }
+                }
+            }
+        }
+        // (6) the panel back, multipliers in the unblocked convention (the
+        // panel's later interchanges undone on each column)
+        if (tid < nb) {
+            T *col = D + tid * ldd;
+            for (int t = nb - 1; t > tid; --t) {
+                const int p = ps[t];
+                if (p != t) {
+                    const T v = col[t];
+                    col[t] = col[p];
+                    col[p] = v;
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < rows * nb; e += GL_T) {
+            const int r = e % rows, cc = e / rows;
+            const int64_t i = k0 + r, c = k0 + cc;
+            if (i - c <= kl && c - i <= kv) Fb[bidx(kv, ldab, i, c)] = D[cc * ldd + r];
+        }
+        __syncthreads();
     }
 }
 
@@ -576,11 +814,32 @@ int gb_form(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *A, cons
     return FEAST_OK;
 }
 
+// Shared memory of the one-launch band LU for a panel width nbp.
+static size_t gb_lu_fused_smem(int64_t kl, int64_t ku, int nbp, size_t es)
+{
+    return ((size_t)(nbp + kl) * nbp + (size_t)nbp * (kl + ku + 1)) * es + (size_t)nbp * sizeof(int);
+}
+
 template <typename T>
 int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int *piv, void *scratch,
              int *pivl, int *info, int *row)
 {
     const int64_t ldab = 2 * kl + ku + 1, kv = kl + ku, sF = ldab * n;
+    if constexpr (sizeof(T) == sizeof(cf)) {
+        // complex64: the whole LU of each node in one CTA when its panel
+        // and U12 fit shared memory (the widest panel that does) and the
+        // band is narrow enough that one SM's share of the trailing
+        // updates (kl x kv x nb per panel) stays below the panel's own
+        // latency; wider bands spread their updates over the GPU below
+        for (int nbp = GL_NB; nbp >= 8 && kv <= 512; nbp /= 2) {
+            const size_t sm = gb_lu_fused_smem(kl, ku, nbp, sizeof(T));
+            if (sm + 1024 > kSmemOptinMax) continue;
+            FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_lu_fused<T>, sm));
+            k_gb_lu_fused<T><<<q, GL_T, sm, s>>>(n, (int)kl, (int)ku, F, ldab, sF, piv, nbp, info, row);
+            FEAST_LAUNCH_CHECK();
+            return FEAST_OK;
+        }
+    }
     const int ldd = (int)(GB_NB + kl);
     T *D = (T *)scratch;
     const int64_t sD = (int64_t)ldd * GB_NB;
@@ -616,35 +875,37 @@ int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int
 
 // Dynamic shared memory of the band solves (forward, backward) for elements
 // of es bytes: the staged factor columns and right-hand-side chunks.
-static size_t gb_fwd_smem(int64_t kl, size_t es, int cw, int jcm)
+static size_t gb_fwd_smem(int64_t kl, size_t es, int cw, int jcm, int nbuf)
 {
-    return ((size_t)(kl + 1 + jcm) * cw + (size_t)jcm * (jcm + kl)) * es + jcm * sizeof(int) + 16;
+    return ((size_t)(kl + 1 + jcm) * cw + (size_t)nbuf * jcm * (jcm + kl)) * es + (size_t)nbuf * jcm * sizeof(int) + 16;
 }
-static size_t gb_bwd_smem(int64_t kl, int64_t ku, size_t es, int cw, int jcm)
+static size_t gb_bwd_smem(int64_t kl, int64_t ku, size_t es, int cw, int jcm, int nbuf)
 {
     const int64_t kv = kl + ku;
-    return ((size_t)(kv + 1 + jcm) * cw + (size_t)jcm * (kv + 1)) * es;
+    return ((size_t)(kv + 1 + jcm) * cw + (size_t)nbuf * jcm * (kv + 1)) * es;
 }
 
-// Staging of the band solves: the most right-hand sides per CTA (cw) and
-// the deepest factor staging (jcm) whose shared memory fits, preferring
-// width (parallel work per step) over depth.  Wide bands trade both for
-// the band itself: cw = jcm = 1 holds just a window of kv + 2 rows and one
-// factor column.
+// Staging of the band solves: the most right-hand sides per CTA (cw), then
+// the deepest factor staging (jcm) whose shared memory fits, with the next
+// chunk's factor columns double-buffered (nbuf = 2) while a chunk of at
+// least 8 steps fits that way.  Wide bands trade all three for the band
+// itself: cw = jcm = nbuf = 1 holds a window of kv + 2 rows and one factor
+// column.
 struct GbPlan {
-    int cw, jcm;
+    int cw, jcm, nbuf;
     size_t smf, smb;
 };
 static GbPlan gb_plan(int64_t kl, int64_t ku, size_t es)
 {
     const size_t lim = kSmemOptinMax - 1024;
-    GbPlan p{1, 1, gb_fwd_smem(kl, es, 1, 1), gb_bwd_smem(kl, ku, es, 1, 1)};
-    for (int cw = GB_CW; cw >= 1; cw /= 2)
-        for (int jcm = GB_JC; jcm >= 1; jcm /= 2) {
-            const size_t f = gb_fwd_smem(kl, es, cw, jcm), b = gb_bwd_smem(kl, ku, es, cw, jcm);
-            if (f <= lim && b <= lim) return GbPlan{cw, jcm, f, b};
-        }
-    return p;   // (does not fit: the caller refuses the band)
+    for (int nbuf = 2; nbuf >= 1; --nbuf)
+        for (int cw = GB_CW; cw >= 1; cw /= 2)
+            for (int jcm = GB_JC; jcm >= (nbuf == 2 ? 8 : 1); jcm /= 2) {
+                const size_t f = gb_fwd_smem(kl, es, cw, jcm, nbuf), b = gb_bwd_smem(kl, ku, es, cw, jcm, nbuf);
+                if (f <= lim && b <= lim) return GbPlan{cw, jcm, nbuf, f, b};
+            }
+    // (does not fit: the caller refuses the band)
+    return GbPlan{1, 1, 1, gb_fwd_smem(kl, es, 1, 1, 1), gb_bwd_smem(kl, ku, es, 1, 1, 1)};
 }
 
 size_t gb_solve_smem_bytes(int64_t kl, int64_t ku, size_t es)
@@ -663,9 +924,9 @@ int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *
     dim3 g(cdiv(nrhs, pl.cw), q);
     FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_fwd<T>, pl.smf));
     FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_bwd<T>, pl.smb));
-    k_gb_fwd<T><<<g, GB_ST, pl.smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX, pl.cw, pl.jcm);
+    k_gb_fwd<T><<<g, GB_ST, pl.smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX, pl.cw, pl.jcm, pl.nbuf);
     FEAST_LAUNCH_CHECK();
-    k_gb_bwd<T><<<g, GB_ST, pl.smb, s>>>(n, kl, ku, nrhs, F, ldab, sF, X, ldx, sX, pl.cw, pl.jcm);
+    k_gb_bwd<T><<<g, GB_ST, pl.smb, s>>>(n, kl, ku, nrhs, F, ldab, sF, X, ldx, sX, pl.cw, pl.jcm, pl.nbuf);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }

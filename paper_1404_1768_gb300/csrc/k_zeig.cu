@@ -159,51 +159,63 @@ __global__ void k_rank1_right2(int m, int cols, zd *C, zd *Q, int ld, const zd *
 constexpr int HG_T = 256;        // threads per CTA
 constexpr int HG_R = 16;         // rows per slab of the right update
 constexpr int HG_U = 8;          // loads in flight per thread
-__global__ void __launch_bounds__(HG_T) k_hess_grid(int m, zd *C, zd *Q, int ld, GridSync g)
+template <typename T>
+__device__ __forceinline__ T hg_scale(T a, typename CxReal<T>::type s)
 {
-    extern __shared__ zd hv[];                   // v (m - 1 entries at most)
-    __shared__ double red[HG_T / 32];
-    __shared__ zd part[HG_T / HG_R][HG_R];
-    __shared__ zd uslab[HG_R];
+    return cx<T>(a.x * s, a.y * s);
+}
+// T = double2 (the double-single QR's input), or float2 in the FP32 build
+// (its Schur form is polished in FP64 afterwards, and GB300's FP32 pipe is
+// 64x its FP64 one)
+template <typename T>
+__global__ void __launch_bounds__(HG_T) k_hess_grid(int m, T *C, T *Q, int ld, GridSync g)
+{
+    typedef typename CxReal<T>::type R;
+    extern __shared__ __align__(16) unsigned char hv_raw[];
+    T *hv = reinterpret_cast<T *>(hv_raw);       // v (m - 1 entries at most)
+    __shared__ R red[HG_T / 32];
+    __shared__ T part[HG_T / HG_R][HG_R];
+    __shared__ T uslab[HG_R];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gwarp = blockIdx.x * (HG_T / 32) + wid, nwarps = gridDim.x * (HG_T / 32);
+    const T zero = cx<T>(0, 0);
     for (int j = 0; j + 2 < m; ++j) {
         const int len = m - j - 1;
-        const zd *x = C + (j + 1) + (int64_t)j * ld;
+        const T *x = C + (j + 1) + (int64_t)j * ld;
         // reflector (every CTA, same order)
-        double pn = 0.0;
-        for (int i = threadIdx.x; i < len; i += HG_T) pn += zabs2(__ldcg(x + i));
+        R pn = 0;
+        for (int i = threadIdx.x; i < len; i += HG_T) pn += cabs2(__ldcg(x + i));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) pn += __shfl_xor_sync(0xffffffffu, pn, off);
         if (lane == 0) red[wid] = pn;
         __syncthreads();
-        double ss = 0.0;
+        R ss = 0;
         for (int w = 0; w < HG_T / 32; ++w) ss += red[w];
-        const double nrm = sqrt(ss);
-        const zd x0 = __ldcg(x);
-        const double a0 = zabs(x0);
-        const zd ph = a0 > 0.0 ? zscale(x0, 1.0 / a0) : zmake(1.0, 0.0);
-        const zd beta = zscale(ph, -nrm);
-        const double vv = 2.0 * nrm * (nrm + a0);
-        const double tau = vv > 0.0 ? 2.0 / vv : 0.0;
-        for (int i = threadIdx.x; i < len; i += HG_T) hv[i] = (i == 0) ? zsub(x0, beta) : __ldcg(x + i);
+        const R nrm = sqrt(ss);
+        const T x0 = __ldcg(x);
+        const R a0 = sqrt(cabs2(x0));
+        const T ph = a0 > 0 ? hg_scale(x0, (R)1 / a0) : cx<T>(1, 0);
+        const T beta = hg_scale(ph, -nrm);
+        const R vv = (R)2 * nrm * (nrm + a0);
+        const R tau = vv > 0 ? (R)2 / vv : (R)0;
+        for (int i = threadIdx.x; i < len; i += HG_T) hv[i] = (i == 0) ? cadd(x0, cneg(beta)) : __ldcg(x + i);
         __syncthreads();
         // left update of the trailing block, one warp per column (HG_U
         // loads in flight per lane: the steps are latency-bound otherwise)
         for (int c = gwarp; c < len; c += nwarps) {
-            zd *col = C + (j + 1) + (int64_t)(j + 1 + c) * ld;
-            zd acc = zmake(0.0, 0.0);
+            T *col = C + (j + 1) + (int64_t)(j + 1 + c) * ld;
+            T acc = zero;
             for (int i0 = lane; i0 < len; i0 += 32 * HG_U) {
-                zd a[HG_U];
+                T a[HG_U];
 #pragma unroll
                 for (int u = 0; u < HG_U; ++u) {
                     const int i = i0 + 32 * u;
-                    a[u] = (i < len) ? __ldcg(col + i) : zmake(0.0, 0.0);
+                    a[u] = (i < len) ? __ldcg(col + i) : zero;
                 }
 #pragma unroll
                 for (int u = 0; u < HG_U; ++u) {
                     const int i = i0 + 32 * u;
-                    if (i < len) zfma_conj(acc, hv[i], a[u]);
+                    if (i < len) cfma(acc, cconj(hv[i]), a[u]);
                 }
             }
 #pragma unroll
@@ -211,19 +223,19 @@ __global__ void __launch_bounds__(HG_T) k_hess_grid(int m, zd *C, zd *Q, int ld,
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
             }
-            const zd f = zscale(acc, -tau);
+            const T f = hg_scale(acc, -tau);
             for (int i0 = lane; i0 < len; i0 += 32 * HG_U) {
-                zd a[HG_U];
+                T a[HG_U];
 #pragma unroll
                 for (int u = 0; u < HG_U; ++u) {
                     const int i = i0 + 32 * u;
-                    a[u] = (i < len) ? __ldcg(col + i) : zmake(0.0, 0.0);
+                    a[u] = (i < len) ? __ldcg(col + i) : zero;
                 }
 #pragma unroll
                 for (int u = 0; u < HG_U; ++u) {
                     const int i = i0 + 32 * u;
                     if (i < len) {
-                        zfma(a[u], hv[i], f);
+                        cfma(a[u], hv[i], f);
                         __stcg(col + i, a[u]);
                     }
                 }
@@ -234,46 +246,46 @@ __global__ void __launch_bounds__(HG_T) k_hess_grid(int m, zd *C, zd *Q, int ld,
         const int tr = threadIdx.x % HG_R, tg = threadIdx.x / HG_R;
         for (int slab = blockIdx.x; slab * HG_R < 2 * m; slab += gridDim.x) {
             const int r = slab * HG_R + tr;
-            zd *M = (r < m) ? C : Q;
+            T *M = (r < m) ? C : Q;
             const int rr = (r < m) ? r : r - m;
             constexpr int CG = HG_T / HG_R;          // column groups
-            zd acc = zmake(0.0, 0.0);
+            T acc = zero;
             if (r < 2 * m)
                 for (int c0 = tg; c0 < len; c0 += CG * HG_U) {
-                    zd a[HG_U];
+                    T a[HG_U];
 #pragma unroll
                     for (int u = 0; u < HG_U; ++u) {
                         const int c = c0 + CG * u;
-                        a[u] = (c < len) ? __ldcg(M + rr + (int64_t)(j + 1 + c) * ld) : zmake(0.0, 0.0);
+                        a[u] = (c < len) ? __ldcg(M + rr + (int64_t)(j + 1 + c) * ld) : zero;
                     }
 #pragma unroll
                     for (int u = 0; u < HG_U; ++u) {
                         const int c = c0 + CG * u;
-                        if (c < len) zfma(acc, a[u], hv[c]);
+                        if (c < len) cfma(acc, a[u], hv[c]);
                     }
                 }
             part[tg][tr] = acc;
             __syncthreads();
             if (tg == 0) {
-                zd s = part[0][tr];
-                for (int q = 1; q < HG_T / HG_R; ++q) s = zadd(s, part[q][tr]);
-                uslab[tr] = zscale(s, -tau);
+                T sum = part[0][tr];
+                for (int q = 1; q < HG_T / HG_R; ++q) sum = cadd(sum, part[q][tr]);
+                uslab[tr] = hg_scale(sum, -tau);
             }
             __syncthreads();
             if (r < 2 * m) {
-                const zd f = uslab[tr];
+                const T f = uslab[tr];
                 for (int c0 = tg; c0 < len; c0 += CG * HG_U) {
-                    zd a[HG_U];
+                    T a[HG_U];
 #pragma unroll
                     for (int u = 0; u < HG_U; ++u) {
                         const int c = c0 + CG * u;
-                        a[u] = (c < len) ? __ldcg(M + rr + (int64_t)(j + 1 + c) * ld) : zmake(0.0, 0.0);
+                        a[u] = (c < len) ? __ldcg(M + rr + (int64_t)(j + 1 + c) * ld) : zero;
                     }
 #pragma unroll
                     for (int u = 0; u < HG_U; ++u) {
                         const int c = c0 + CG * u;
                         if (c < len) {
-                            zfma(a[u], f, zconj(hv[c]));
+                            cfma(a[u], f, cconj(hv[c]));
                             __stcg(M + rr + (int64_t)(j + 1 + c) * ld, a[u]);
                         }
                     }
@@ -284,9 +296,27 @@ __global__ void __launch_bounds__(HG_T) k_hess_grid(int m, zd *C, zd *Q, int ld,
         // column j: (beta, 0, ..., 0) -- every CTA has read it
         if (blockIdx.x == 0)
             for (int i = threadIdx.x; i < len; i += HG_T)
-                __stcg(C + (j + 1 + i) + (int64_t)j * ld, (i == 0) ? beta : zmake(0.0, 0.0));
+                __stcg(C + (j + 1 + i) + (int64_t)j * ld, (i == 0) ? beta : zero);
         if (!grid_barrier(g)) return;
     }
+}
+
+// complex128 <-> complex64 copies of an m x m matrix, and the identity
+__global__ void k_z2c(int64_t count, const zd *__restrict__ x, cf *__restrict__ y)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = make_float2((float)x[e].x, (float)x[e].y);
+}
+__global__ void k_c2z(int64_t count, const cf *__restrict__ x, zd *__restrict__ y)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = zmake((double)x[e].x, (double)x[e].y);
+}
+__global__ void k_eye_c(int m, cf *Q)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        Q[e] = make_float2((e % m) == (e / m) ? 1.f : 0.f, 0.f);
 }
 
 __global__ void k_eye(int m, zd *Q, int ld)
@@ -1646,12 +1676,20 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
     unsigned *hbar = (unsigned *)(((uintptr_t)(wv + m) + 15) & ~(uintptr_t)15);   // (w is unused by it)
     int hgrid = 0;
     if (m >= 3) {
+        // the FP32 build reduces in FP32 too when its multishift QR follows
+        // (C and Q in complex64 in the double-single copies' space)
+        const bool hf = FEAST_QR_FP32 && m > SQ_MAX;
         int dev = 0, sms = 0, per = 0;
-        const size_t hsm = sizeof(zd) * (size_t)m;
+        const size_t hsm = (hf ? sizeof(cf) : sizeof(zd)) * (size_t)m;
         FEAST_CUDA_TRY(cudaGetDevice(&dev));
         FEAST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        FEAST_CUDA_TRY(ensure_dyn_smem(k_hess_grid, hsm));
-        FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hess_grid, HG_T, hsm));
+        if (hf) {
+            FEAST_CUDA_TRY(ensure_dyn_smem(k_hess_grid<cf>, hsm));
+            FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hess_grid<cf>, HG_T, hsm));
+        } else {
+            FEAST_CUDA_TRY(ensure_dyn_smem(k_hess_grid<zd>, hsm));
+            FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hess_grid<zd>, HG_T, hsm));
+        }
         hgrid = (per >= 1) ? sms : 0;
         const int need = (2 * m + HG_R - 1) / HG_R;     // right-update slabs
         if (hgrid > need) hgrid = need;
@@ -1659,9 +1697,27 @@ int schur_large(cudaStream_t s, int m, zd *C, zd *Q, void *work, int *fail, int 
             FEAST_CUDA_TRY(cudaMemsetAsync(hbar, 0, 2 * sizeof(unsigned), s));
             GridSync hg{hbar, hbar + 1, timeout, TO_HESS};
             int mm = m, ldq = m;
-            void *hargs[] = {&mm, &C, &Q, &ldq, &hg};
-            FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hess_grid, dim3(hgrid), dim3(HG_T), hargs, hsm, s));
-            FEAST_LAUNCH_CHECK();
+            const unsigned gc = cdiv((size_t)m * m, 256) > 4096 ? 4096 : cdiv((size_t)m * m, 256);
+            if (hf) {
+                cf *Cf = (cf *)Hds, *Qf = (cf *)Qds;
+                k_z2c<<<gc, 256, 0, s>>>((int64_t)m * m, C, Cf);
+                FEAST_LAUNCH_CHECK();
+                k_eye_c<<<gc, 256, 0, s>>>(m, Qf);
+                FEAST_LAUNCH_CHECK();
+                void *hargs[] = {&mm, &Cf, &Qf, &ldq, &hg};
+                FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hess_grid<cf>, dim3(hgrid), dim3(HG_T), hargs,
+                                                           hsm, s));
+                FEAST_LAUNCH_CHECK();
+                k_c2z<<<gc, 256, 0, s>>>((int64_t)m * m, Cf, C);
+                FEAST_LAUNCH_CHECK();
+                k_c2z<<<gc, 256, 0, s>>>((int64_t)m * m, Qf, Q);
+                FEAST_LAUNCH_CHECK();
+            } else {
+                void *hargs[] = {&mm, &C, &Q, &ldq, &hg};
+                FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_hess_grid<zd>, dim3(hgrid), dim3(HG_T), hargs,
+                                                           hsm, s));
+                FEAST_LAUNCH_CHECK();
+            }
         }
     }
     for (int j = 0; hgrid == 0 && j + 2 < m; ++j) {

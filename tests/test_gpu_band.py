@@ -158,3 +158,22 @@ def test_band_full_grid_n16384(prec):
     assert _match_rel(r["lam"], inside) < 1e-8
     assert np.all(r["res"] < 1e-10)
     g.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_band_non_regular_pencil_reports_singular(prec):
+    """Tridiagonal A and B sharing a zero row: det(z B - A) = 0 for every
+    z, so every shifted band matrix has an exact zero pivot -> FEAST_ESINGULAR
+    at set-up (the complex64 band LU of the precision form included)."""
+    fg = _fg()
+    n, kl, ku = 70, 1, 1
+    A = _random_band(n, kl, ku, 3)
+    B = _random_band(n, kl, ku, 4)
+    B[ku, :] += 5.0
+    for M in (A, B):
+        for j in range(max(0, 37 - ku), min(n, 37 + kl + 1)):
+            M[ku + 37 - j, j] = 0.0          # row 37 of both is zero
+    Y = inputs.complex_normal(np.random.default_rng(2), (n, 4))
+    with pytest.raises(fg.FeastError) as ei:
+        fg.Feast(A, B, Y, prec=prec, contour_kind=0, rule=1, q=8, center=0j, a=1.0, kind=1, kl=kl, ku=ku)
+    assert ei.value.status == -4
