@@ -611,15 +611,17 @@ def roofline_phases(prob, args, ph, infos):
     gms = sum(i.get("ms_warm_gemm", 0.0) for i in warm)
     gfl = sum(i.get("warm_gemm_flop", 0.0) for i in warm)
     if warm and t_warm >= t_cold and gms > 0.0 and gfl > 0.0:
-        # the library's own CUDA events around exactly the FP64 product
-        # launches of the warm Newton step (GEMMs, triangular inverses)
+        # the library's own CUDA events around exactly the product launches
+        # of the warm Newton step: FP64 GEMMs and triangular inverses for C
+        # and C', the defect-form products on the digit-sliced tensor-core
+        # GEMM; reported against the FP64 peak (what the arithmetic needs)
         ach = gfl / (gms / 1e3) / 1e12
         out["projected eigensolve"] = {
             "bound": "alu", "achieved": ach, "peak": FP64_MEASURED_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP64_MEASURED_TFLOPS, "traffic": None,
-            "kernel": "k_gemm<double2> + triangular inverses of the warm Newton step (C = B~^-1 A~, "
-                      "C' = Zh^H C Zh, V^-1 (C' V^), V^ G, C' Y') on the FP64 pipe; CUDA events around "
-                      "exactly those launches",
+            "kernel": "warm Newton step: k_gemm<double2> + triangular inverses (C = B~^-1 A~, C' = Zh^H C Zh) "
+                      "and k_oz_gemm for the defect-form products (D V^, V^-1 W', V^ G, V^ S1, W' G), "
+                      "FP64-equivalent flops; CUDA events around exactly those launches",
             "peak_source": FP64_SOURCE,
             "algorithmic_flops_per_pass": gfl / len(warm), "kernel_ms_per_pass": gms / len(warm),
             "warm_passes": len(warm), "cold_passes": len(cold),

@@ -144,6 +144,11 @@ constexpr double kWarmAccMin = 1e-12;  // the cold double-single QR's own backwa
 // FP32 Schur form (~1e-6 remainder) one Newton step reaches ~1e-10.
 constexpr double kColdFp32AccMin = 1e-8;
 constexpr int kZeigMinM = 8;         // smallest projected problem on the standard-form QR
+// banded precision form: the n x m0 products go to the digit-sliced
+// tensor-core GEMM from this width on (below it the FP64 GEMMs of the tall,
+// skinny blocks were faster: at n = 16384, m0 = 64 the orthonormalisation
+// took 9.8 ms per pass in FP64 and 16.8 ms on the digit slices)
+constexpr int kBandOzMinM = 256;
 constexpr double kZeigSmallEpsMin = 1e-11;   // ... when m0 <= 64: the strictest eps it serves
 
 struct Carver {
@@ -226,6 +231,14 @@ void carve(feast_ctx *c, Carver &cv)
             c->R64 = cv.take<zd>(q * n * m);
             c->nrm2 = cv.take<double>(q + 1);
             carve_defect(c, cv);
+            if (m >= kBandOzMinM) {
+                // digit planes for the n x m0 products (projection, Ritz
+                // vectors, Cholesky QR, warm Newton step) on the tensor cores
+                c->ozX = cv.take<char>(oz_cols_bytes((int64_t)n, (int64_t)(2 * m)));
+                const size_t r1 = oz_rows_bytes((int64_t)m, (int64_t)n), r2 = oz_rows_bytes((int64_t)n, (int64_t)m);
+                c->ozR = cv.take<char>(r1 > r2 ? r1 : r2);
+                c->chol_work = cv.take<char>(zorth_chol_work_bytes((int64_t)m));
+            }
         }
         c->gb_pivl = cv.take<int>(gb_piv_scratch(c->kl, (int)q));
     } else if (c->prec == FEAST_FP64) {
@@ -366,12 +379,15 @@ int collect_scalar(feast_ctx *c, int op, double *v)
 // Y = B X (copy when B = I).  X, Y: n x m, leading dim n.
 // Dense operands of the precision form: FP64-accurate products on the
 // tensor cores (digit planes of the left operand made beforehand).
+// products with the dense operators A, B on their digit planes
 bool use_oz(const feast_ctx *c) { return c->kind == FEAST_DENSE && c->prec != FEAST_FP64; }
+// the n x m0 and m0 x m0 products of the precision form (dense or band)
+bool use_oz_small(const feast_ctx *c) { return c->prec != FEAST_FP64 && c->ozR && c->ozX; }
 
 // Digit-plane scratch for the orthonormalisation's tall updates (precision form).
 const OzScratch *orth_oz(feast_ctx *c)
 {
-    if (!use_oz(c)) return nullptr;
+    if (!use_oz_small(c)) return nullptr;
     c->oz_orth = OzScratch{c->ozR, c->ozX, &c->st->timeout};
     return &c->oz_orth;
 }
@@ -847,7 +863,7 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
     const bool rr = c->projection == FEAST_RAYLEIGH_RITZ;
     const zd *Tb = rr ? c->U1 : c->U2;
     if ((e = apply_A(c, c->U1, c->W, m))) return e;
-    if (use_oz(c)) {
+    if (use_oz_small(c)) {
         if ((e = oz_prepare_rows(s, m, n, Tb, n, c->ozR, 1))) return e;
         if ((e = oz_mul(c, c->ozR, m, n, c->W, n, 2 * m, c->P, m))) return e;
     } else if ((e = zgemm_batched(s, 1, m, 2 * m, n, kOne, Tb, n, 0, c->W, n, 0, kZero, c->P, m, 0, 1))) {
@@ -927,7 +943,7 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         if (e) return e;
     }
     FEAST_CUDA_TRY(cudaEventRecord(c->ev[2], s));
-    if (use_oz(c)) {
+    if (use_oz_small(c)) {
         // x_i = U1 y_i, A x_i = (A U1) y_i, B x_i = (B U1) y_i with Y's digits made once
         if ((e = oz_prepare_cols(s, m, m, c->Yv, m, c->ozX))) return e;
         const zd *lhs[3] = {c->U1, c->W, c->W + n * m};

@@ -243,14 +243,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // of WL = kl + 1 + jcm rows in shared memory, the chunk's multipliers
 // (jcm + kl rows x jcm columns, column-major) and pivots beside it, in
 // nbuf = 2 buffers when they fit (the next chunk's copied in meanwhile).
-template <typename T>
+template <typename T, int CW>
 __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF, const int *piv, T *X,
-                                                  int64_t ldx, int64_t sX, int cw, int jcm, int nbuf)
+                                                  int64_t ldx, int64_t sX, int jcm, int nbuf)
 {
+    constexpr int cw = CW;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int WL = (int)(kl + 1 + jcm), LR = (int)(jcm + kl), kv = (int)(kl + ku);
-    T *W = reinterpret_cast<T *>(sm_raw);      // WL x cw window, row r at slot r % WL
+    T *W = reinterpret_cast<T *>(sm_raw);      // cw columns of WL slots: row r of column cc at W[cc * WL + r % WL]
     T *const Lb0 = W + (size_t)WL * cw;         // LR x jcm: Lb[jj * LR + rho] = L'(j0 + rho, j0 + jj)
     T *const Lb1 = Lb0 + (size_t)(nbuf - 1) * LR * jcm;
     int *const pb0 = reinterpret_cast<int *>(Lb0 + (size_t)nbuf * LR * jcm);   // the chunk's pivots (global rows)
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
     for (int e = threadIdx.x; e < WL * cw; e += GB_ST) {
         const int r = e % WL, cc = e / WL;
         const bool in = r < n && cc < ncol;
-        cp_async<sizeof(T)>(W + r * cw + cc, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb, in);
+        cp_async<sizeof(T)>(W + cc * WL + r, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb, in);
     }
     stage(0, Lb0, pb0);
     cp_async_commit();
@@ -297,9 +298,9 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
                     int sa = s0 + jj, sb = s0 + p;
                     if (sa >= WL) sa -= WL;
                     if (sb >= WL) sb -= WL;
-                    const T t = W[sa * cw + cc];
-                    W[sa * cw + cc] = W[sb * cw + cc];
-                    W[sb * cw + cc] = t;
+                    const T t = W[cc * WL + sa];
+                    W[cc * WL + sa] = W[cc * WL + sb];
+                    W[cc * WL + sb] = t;
                 }
             }
         } else if (threadIdx.x >= 32 && threadIdx.x < 32 + jc) {
@@ -325,32 +326,37 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
         if (wid < cw) {
             int sl = s0 + lane;
             if (sl >= WL) sl -= WL;
-            T x = (lane < jc) ? W[sl * cw + wid] : cx<T>(0, 0);
+            T x = (lane < jc) ? W[wid * WL + sl] : cx<T>(0, 0);
             for (int jj = 0; jj + 1 < jc; ++jj) {
                 const T xj = shfl_cx(x, jj);
                 if (lane > jj && lane < jc) cfma(x, cneg(Lb[jj * LR + lane]), xj);
             }
             if (lane < jc) {
-                W[sl * cw + wid] = x;
+                W[wid * WL + sl] = x;
                 if (wid < ncol) Xb[j0 + lane + (c0 + wid) * ldx] = x;
             }
         }
         __syncthreads();
-        // (3) rows j0 + jc .. j0 + jc + kl - 1 -= L'(those rows, chunk) x(chunk)
-        for (int e = threadIdx.x; e < kl * cw; e += GB_ST) {
-            const int t = e % (int)kl, cc = e / (int)kl;
+        // (3) rows j0 + jc .. j0 + jc + kl - 1 -= L'(those rows, chunk) x(chunk):
+        // a thread per row and all cw right-hand sides (one multiplier load
+        // per cw products; the x values are broadcast)
+        for (int t = threadIdx.x; t < kl; t += GB_ST) {
             const int64_t r = j0 + jc + t;
-            if (r < n) {
-                int sr = s0 + jc + t;
-                while (sr >= WL) sr -= WL;
-                T acc = W[sr * cw + cc];
-                int sj = s0;
-                for (int jj = 0; jj < jc; ++jj) {
-                    cfma(acc, cneg(Lb[jj * LR + jc + t]), W[sj * cw + cc]);
-                    if (++sj == WL) sj = 0;
-                }
-                W[sr * cw + cc] = acc;
+            if (r >= n) continue;
+            int sr = s0 + jc + t;
+            while (sr >= WL) sr -= WL;
+            T acc[CW];
+#pragma unroll
+            for (int cc = 0; cc < CW; ++cc) acc[cc] = W[cc * WL + sr];
+            int sj = s0;
+            for (int jj = 0; jj < jc; ++jj) {
+                const T l = cneg(Lb[jj * LR + jc + t]);
+#pragma unroll
+                for (int cc = 0; cc < CW; ++cc) cfma(acc[cc], l, W[cc * WL + sj]);
+                if (++sj == WL) sj = 0;
             }
+#pragma unroll
+            for (int cc = 0; cc < CW; ++cc) W[cc * WL + sr] = acc[cc];
         }
         __syncthreads();
         // rows j0 .. j0+jc-1 are final; their slots take rows j0+WL ..
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
             int sl = s0 + jj;
             if (sl >= WL) sl -= WL;
             const bool in = r < n && cc < ncol;
-            cp_async<sizeof(T)>(W + sl * cw + cc, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb,
+            cp_async<sizeof(T)>(W + cc * WL + sl, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb,
                                 in);
         }
         if (nbuf == 1 && more) stage(j0 + jcm, Lb0, pb0);   // (its buffer is free only now)
@@ -375,14 +381,15 @@ __global__ void __launch_bounds__(GB_ST) k_gb_fwd(int64_t n, int64_t kl, int64_t
 // above it.  Window of WL = kv + 1 + jcm rows; the chunk's columns of U
 // (diagonal included) staged column-major, Us[jj * (kv + 1) + t] =
 // U(j - t, j) with j = j1 - jj, in nbuf buffers as in the forward pass.
-template <typename T>
+template <typename T, int CW>
 __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t ku, int64_t nrhs,
                                                   const T *F, int64_t ldab, int64_t sF, T *X,
-                                                  int64_t ldx, int64_t sX, int cw, int jcm, int nbuf)
+                                                  int64_t ldx, int64_t sX, int jcm, int nbuf)
 {
+    constexpr int cw = CW;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int kv = (int)(kl + ku), WL = kv + 1 + jcm, UL = kv + 1;
-    T *W = reinterpret_cast<T *>(sm_raw);      // WL x cw window, row r at slot r % WL
+    T *W = reinterpret_cast<T *>(sm_raw);      // cw columns of WL slots: row r of column cc at W[cc * WL + r % WL]
     T *const Ub0 = W + (size_t)WL * cw;
     T *const Ub1 = Ub0 + (size_t)(nbuf - 1) * jcm * UL;
     const int b = blockIdx.y;
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t
         const int64_t r = n - 1 - t;
         if (r >= 0) {
             const bool in = cc < ncol;
-            cp_async<sizeof(T)>(W + (int)(r % WL) * cw + cc, in ? (const void *)(Xb + r + (c0 + cc) * ldx)
+            cp_async<sizeof(T)>(W + cc * WL + (int)(r % WL), in ? (const void *)(Xb + r + (c0 + cc) * ldx)
                                                                 : (const void *)Xb, in);
         }
     }
@@ -428,7 +435,7 @@ __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t
         if (wid < cw) {
             int sl = s1 - lane;
             if (sl < 0) sl += WL;
-            T x = (lane < jc) ? W[sl * cw + wid] : cx<T>(0, 0);
+            T x = (lane < jc) ? W[wid * WL + sl] : cx<T>(0, 0);
             for (int jj = 0; jj < jc; ++jj) {
                 if (lane == jj) x = cdiv(x, Us[jj * UL]);
                 const T xj = shfl_cx(x, jj);
@@ -436,27 +443,33 @@ __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t
                 if (t > 0 && t <= kv && lane < jc) cfma(x, cneg(Us[jj * UL + t]), xj);
             }
             if (lane < jc) {
-                W[sl * cw + wid] = x;
+                W[wid * WL + sl] = x;
                 if (wid < ncol) Xb[j1 - lane + (c0 + wid) * ldx] = x;
             }
         }
         __syncthreads();
-        // rows above the chunk: r = j1 - jc - tt, tt = 0 .. kv-1
-        for (int e = threadIdx.x; e < kv * cw; e += GB_ST) {
-            const int tt = e % kv, cc = e / kv;
+        // rows above the chunk: r = j1 - jc - tt, tt = 0 .. kv-1, a thread
+        // per row and all cw right-hand sides
+        for (int tt = threadIdx.x; tt < kv; tt += GB_ST) {
             const int64_t r = j1 - jc - tt;
-            if (r >= 0) {
-                int sr = s1 - jc - tt;
-                while (sr < 0) sr += WL;
-                T acc = W[sr * cw + cc];
-                int sj = s1;
-                for (int jj = 0; jj < jc; ++jj) {
-                    const int t = jc - jj + tt;       // (j1 - jj) - r
-                    if (t <= kv) cfma(acc, cneg(Us[jj * UL + t]), W[sj * cw + cc]);
-                    if (--sj < 0) sj = WL - 1;
+            if (r < 0) continue;
+            int sr = s1 - jc - tt;
+            while (sr < 0) sr += WL;
+            T acc[CW];
+#pragma unroll
+            for (int cc = 0; cc < CW; ++cc) acc[cc] = W[cc * WL + sr];
+            int sj = s1;
+            for (int jj = 0; jj < jc; ++jj) {
+                const int t = jc - jj + tt;       // (j1 - jj) - r
+                if (t <= kv) {
+                    const T u = cneg(Us[jj * UL + t]);
+#pragma unroll
+                    for (int cc = 0; cc < CW; ++cc) cfma(acc[cc], u, W[cc * WL + sj]);
                 }
-                W[sr * cw + cc] = acc;
+                if (--sj < 0) sj = WL - 1;
             }
+#pragma unroll
+            for (int cc = 0; cc < CW; ++cc) W[cc * WL + sr] = acc[cc];
         }
         __syncthreads();
         // rows j1-jc+1 .. j1 are final; their slots take rows j - WL
@@ -467,7 +480,7 @@ __global__ void __launch_bounds__(GB_ST) k_gb_bwd(int64_t n, int64_t kl, int64_t
             if (sl < 0) sl += WL;
             if (r >= 0) {
                 const bool in = cc < ncol;
-                cp_async<sizeof(T)>(W + sl * cw + cc, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb,
+                cp_async<sizeof(T)>(W + cc * WL + sl, in ? (const void *)(Xb + r + (c0 + cc) * ldx) : (const void *)Xb,
                                     in);
             }
         }
@@ -493,17 +506,32 @@ __global__ void k_gb_matmul(int64_t n, int64_t kl, int64_t ku, const zd *M, int6
     }
 }
 
-// The whole band LU of one node in one CTA (complex64; one launch for all
-// nodes): for each panel of nb columns, (1) the panel's nb + kl rows into
-// shared memory, (2) its partial-pivot LU there (pivot: largest |.|^2,
-// the first on ties), (3) the interchanges on the kv columns right of it
-// in the band, (4) U12 = L11^{-1} A12 (a thread per column, kept in shared
-// memory), (5) A22 -= L21 U12 on the band (a warp per 32 rows x 4
-// columns), (6) the panel back with its multipliers in the unblocked
-// convention.  The same factors as the multi-launch form; the nodes are
-// independent, so no CTA waits for another.
-constexpr int GL_T = 256;
+// The whole band LU of one node in one cluster of GL_C CTAs (complex64;
+// one launch for all nodes): for each panel of nb columns, every CTA of the
+// cluster (1) copies the panel's nb + kl rows into its shared memory and
+// (2) factors it there with partial pivoting (pivot: largest |.|^2, the
+// first on ties) -- the same arithmetic in the same order in every CTA, so
+// their panels agree bit for bit and nothing is exchanged; then each CTA
+// takes its own slice of the kv columns right of the panel: (3) the
+// panel's interchanges, (4) U12 = L11^{-1} A12 (a warp per column, in
+// shared memory), (5) A22 -= L21 U12 on the band (a warp per 32 rows x 4
+// columns); (6) CTA 0 writes the panel back with its multipliers in the
+// unblocked convention.  A cluster barrier closes each panel.  The same
+// factors as the multi-launch form; the clusters (nodes) never wait for
+// one another.
+constexpr int GL_T = 512;
+constexpr int GL_C = 8;          // CTAs per node (a portable cluster)
 constexpr int GL_NB = 32;
+__device__ __forceinline__ unsigned gl_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void gl_cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 template <typename T>
 __global__ void __launch_bounds__(GL_T) k_gb_lu_fused(int64_t n, int kl, int ku, T *F, int64_t ldab, int64_t sF,
                                                      int *piv, int nbp, int *info, int *row)
@@ -511,14 +539,16 @@ __global__ void __launch_bounds__(GL_T) k_gb_lu_fused(int64_t n, int kl, int ku,
     typedef typename CxReal<T>::type R;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int kv = kl + ku, ldd = nbp + kl;
+    const int rank = (int)gl_rank(), kvs = (kv + GL_C - 1) / GL_C;
+    const int cb = rank * kvs, ce = (cb + kvs < kv) ? cb + kvs : kv;   // this CTA's columns cc in [cb, ce)
+    const int nc = ce > cb ? ce - cb : 0, ldu = kvs + 1;
     T *D = reinterpret_cast<T *>(sm_raw);      // ldd x nbp panel, column-major
-    const int ldu = kv + 1;
-    T *U = D + (size_t)ldd * nbp;               // nbp x kv, row-major: U[k * ldu + cc]
+    T *U = D + (size_t)ldd * nbp;               // nbp x kvs slice of U12, row-major: U[k * ldu + cc - cb]
     int *ps = reinterpret_cast<int *>(U + (size_t)nbp * ldu);  // local pivots of the panel
     __shared__ R s_val[GL_T / 32];
     __shared__ int s_idx[GL_T / 32];
     __shared__ int s_p;
-    const int b = blockIdx.x;
+    const int b = blockIdx.x / GL_C;
     T *Fb = F + (int64_t)b * sF;
     int *pvb = piv + (int64_t)b * n;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -526,13 +556,18 @@ __global__ void __launch_bounds__(GL_T) k_gb_lu_fused(int64_t n, int kl, int ku,
     for (int64_t k0 = 0; k0 < n; k0 += nbp) {
         const int nb = (int)((n - k0) < nbp ? (n - k0) : nbp);
         const int rows = (int)((n - k0) < ldd ? (n - k0) : ldd);
-        // (1) gather
+        // (1) gather (asynchronous copies, all in flight at once)
         for (int e = tid; e < ldd * nb; e += GL_T) {
             const int r = e % ldd, cc = e / ldd;
             const int64_t i = k0 + r, c = k0 + cc;
-            D[cc * ldd + r] = (r < rows && i - c <= kl && c - i <= kv) ? Fb[bidx(kv, ldab, i, c)] : zero;
+            const bool in = r < rows && i - c <= kl && c - i <= kv;
+            cp_async<sizeof(T)>(D + cc * ldd + r, in ? (const void *)(Fb + bidx(kv, ldab, i, c)) : (const void *)Fb, in);
         }
+        cp_async_commit();
+        cp_async_wait_all();
         __syncthreads();
+        // every CTA holds the panel before CTA 0 can write it back (step 6)
+        gl_cluster_sync();
         // (2) panel LU
         for (int j = 0; j < nb; ++j) {
             const T *dj = D + j * ldd;
@@ -550,17 +585,15 @@ __global__ void __launch_bounds__(GL_T) k_gb_lu_fused(int64_t n, int kl, int ku,
             }
             if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
             __syncthreads();
+            // every thread reduces the warp partials itself (the same order)
+            R bv = s_val[0];
+            int p = s_idx[0];
+            for (int w = 1; w < GL_T / 32; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < p)) { bv = s_val[w]; p = s_idx[w]; }
             if (tid == 0) {
-                R bv = s_val[0];
-                int bx = s_idx[0];
-                for (int w = 1; w < GL_T / 32; ++w)
-                    if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bx)) { bv = s_val[w]; bx = s_idx[w]; }
-                s_p = bx;
-                ps[j] = bx;
-                if (bv == 0 && info && atomicCAS(info, 0, b + 1) == 0 && row) *row = (int)(k0 + j) + 1;
+                ps[j] = p;
+                if (bv == 0 && rank == 0 && info && atomicCAS(info, 0, b + 1) == 0 && row) *row = (int)(k0 + j) + 1;
             }
-            __syncthreads();
-            const int p = s_p;
             if (p != j && tid < nb) {
                 const T t = D[tid * ldd + j];
                 D[tid * ldd + j] = D[tid * ldd + p];
@@ -571,19 +604,21 @@ __global__ void __launch_bounds__(GL_T) k_gb_lu_fused(int64_t n, int kl, int ku,
             if (!cis_zero(d)) {
                 for (int r = j + 1 + tid; r < rows; r += GL_T) D[j * ldd + r] = cdiv(D[j * ldd + r], d);
                 __syncthreads();
-                const int rr = rows - j - 1, cn = nb - j - 1;
-                for (int e = tid; e < rr * cn; e += GL_T) {
-                    const int r = j + 1 + e % rr, cc = j + 1 + e / rr;
-                    T v = D[cc * ldd + r];
-                    cfma(v, cneg(D[j * ldd + r]), D[cc * ldd + j]);
-                    D[cc * ldd + r] = v;
+                // rows j+1 .. rows-1 by lane, columns j+1 .. nb-1 by warp
+                for (int r = j + 1 + lane; r < rows; r += 32) {
+                    const T l = cneg(D[j * ldd + r]);
+                    for (int cc = j + 1 + wid; cc < nb; cc += GL_T / 32) {
+                        T v = D[cc * ldd + r];
+                        cfma(v, l, D[cc * ldd + j]);
+                        D[cc * ldd + r] = v;
+                    }
                 }
             }
             __syncthreads();
         }
-        if (tid < nb) pvb[k0 + tid] = (int)(k0 + ps[tid]);
-        // (3) the interchanges on the columns right of the panel
-        for (int cc = tid; cc < kv; cc += GL_T) {
+        if (rank == 0 && tid < nb) pvb[k0 + tid] = (int)(k0 + ps[tid]);
+        // (3) the interchanges on this CTA's columns right of the panel
+        for (int cc = cb + tid; cc < ce; cc += GL_T) {
             const int64_t c = k0 + nb + cc;
             if (c >= n) continue;
             for (int j = 0; j < nb; ++j) {
@@ -597,76 +632,89 @@ __global__ void __launch_bounds__(GL_T) k_gb_lu_fused(int64_t n, int kl, int ku,
             }
         }
         __syncthreads();
-        // (4) U12 = L11^{-1} A12 in shared memory (rows padded to kv + 1),
-        // a thread per column for the triangular solve
-        for (int e = tid; e < nbp * kv; e += GL_T) {
-            const int r = e % nbp, cc = e / nbp;
-            const int64_t c = k0 + nb + cc;
-            U[r * ldu + cc] = (r < nb && c < n && c - (k0 + r) <= kv) ? Fb[bidx(kv, ldab, k0 + r, c)] : zero;
+        // (4) U12 = L11^{-1} A12 on this CTA's columns, in shared memory
+        // (rows padded to kvs + 1)
+        for (int e = tid; e < nbp * nc; e += GL_T) {
+            const int r = e % nbp, cl = e / nbp;
+            const int64_t c = k0 + nb + cb + cl;
+            const bool in = r < nb && c < n && c - (k0 + r) <= kv;
+            cp_async<sizeof(T)>(U + r * ldu + cl, in ? (const void *)(Fb + bidx(kv, ldab, k0 + r, c)) : (const void *)Fb,
+                                in);
         }
+        cp_async_commit();
+        cp_async_wait_all();
         __syncthreads();
-        for (int cc = tid; cc < kv; cc += GL_T)
+        // a warp per column, a lane per row, the solved value by shuffles
+        for (int cl = wid; cl < nc; cl += GL_T / 32) {
+            T x = (lane < nb) ? U[lane * ldu + cl] : zero;
             for (int i = 0; i + 1 < nb; ++i) {
-                const T xi = U[i * ldu + cc];
-                for (int r = i + 1; r < nb; ++r) {
-                    T v = U[r * ldu + cc];
-                    cfma(v, cneg(D[i * ldd + r]), xi);
-                    U[r * ldu + cc] = v;
-                }
+                const T xi = shfl_cx(x, i);
+                if (lane > i && lane < nb) cfma(x, cneg(D[i * ldd + lane]), xi);
             }
-        __syncthreads();
-        for (int e = tid; e < nb * kv; e += GL_T) {
-            const int r = e % nb, cc = e / nb;
-            const int64_t c = k0 + nb + cc;
-            if (c < n && c - (k0 + r) <= kv) Fb[bidx(kv, ldab, k0 + r, c)] = U[r * ldu + cc];
+            if (lane < nb) U[lane * ldu + cl] = x;
         }
-        // (5) A22 -= L21 U12: rows k0+nb+t (t < rows-nb <= kl), columns
-        // k0+nb+cc (cc < kv) -- all inside the band; a warp per 32 rows x 4
+        __syncthreads();
+        for (int e = tid; e < nb * nc; e += GL_T) {
+            const int r = e % nb, cl = e / nb;
+            const int64_t c = k0 + nb + cb + cl;
+            if (c < n && c - (k0 + r) <= kv) Fb[bidx(kv, ldab, k0 + r, c)] = U[r * ldu + cl];
+        }
+        // (5) A22 -= L21 U12: rows k0+nb+t (t < rows-nb <= kl), this CTA's
+        // columns k0+nb+cc -- all inside the band; a warp per 32 rows x 4
         // columns, a lane per row
         {
             const int R2 = rows - nb;
-            const int rt = (R2 + 31) / 32, ct = (kv + 3) / 4;
+            const int rt = (R2 + 31) / 32, ct = (nc + 3) / 4;
             for (int task = wid; task < rt * ct; task += GL_T / 32) {
                 const int t = (task % rt) * 32 + lane, c4 = (task / rt) * 4;
                 if (t >= R2) continue;
+                const int64_t i = k0 + nb + t;
+                // the destinations first: their loads run under the products
+                T old[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t c = k0 + nb + cb + c4 + u;
+                    old[u] = (c4 + u < nc && c < n) ? Fb[bidx(kv, ldab, i, c)] : zero;
+                }
                 T acc[4] = {zero, zero, zero, zero};
                 for (int k = 0; k < nb; ++k) {
                     const T l = D[k * ldd + nb + t];
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-                        if (c4 + u < kv) cfma(acc[u], l, U[k * ldu + c4 + u]);
+                        if (c4 + u < nc) cfma(acc[u], l, U[k * ldu + c4 + u]);
                 }
-                const int64_t i = k0 + nb + t;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int64_t c = k0 + nb + c4 + u;
-                    if (c4 + u < kv && c < n) {
-                        T &dst = Fb[bidx(kv, ldab, i, c)];
-                        dst = cadd(dst, cneg(acc[u]));
+                    const int64_t c = k0 + nb + cb + c4 + u;
+                    if (c4 + u < nc && c < n) Fb[bidx(kv, ldab, i, c)] = cadd(old[u], cneg(acc[u]));
+                }
+            }
+        }
+        __syncthreads();   // (step 5 reads L21 from the panel that step 6 rewrites)
+        // (6) the panel back (CTA 0), multipliers in the unblocked convention
+        // (the panel's later interchanges undone on each column)
+        if (rank == 0) {
+            if (tid < nb) {
+                T *col = D + tid * ldd;
+                for (int t = nb - 1; t > tid; --t) {
+                    const int p = ps[t];
+                    if (p != t) {
+                        const T v = col[t];
+                        col[t] = col[p];
+                        col[p] = v;
                     }
                 }
             }
-        }
-        // (6) the panel back, multipliers in the unblocked convention (the
-        // panel's later interchanges undone on each column)
-        if (tid < nb) {
-            T *col = D + tid * ldd;
-            for (int t = nb - 1; t > tid; --t) {
-                const int p = ps[t];
-                if (p != t) {
-                    const T v = col[t];
-                    col[t] = col[p];
-                    col[p] = v;
-                }
+            __syncthreads();
+            for (int e = tid; e < rows * nb; e += GL_T) {
+                const int r = e % rows, cc = e / rows;
+                const int64_t i = k0 + r, c = k0 + cc;
+                if (i - c <= kl && c - i <= kv) Fb[bidx(kv, ldab, i, c)] = D[cc * ldd + r];
             }
         }
-        __syncthreads();
-        for (int e = tid; e < rows * nb; e += GL_T) {
-            const int r = e % rows, cc = e / rows;
-            const int64_t i = k0 + r, c = k0 + cc;
-            if (i - c <= kl && c - i <= kv) Fb[bidx(kv, ldab, i, c)] = D[cc * ldd + r];
-        }
-        __syncthreads();
+        // every CTA's updates (and the panel) are in memory before any
+        // CTA gathers the next panel
+        gl_cluster_sync();
     }
 }
 
@@ -814,10 +862,11 @@ int gb_form(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *A, cons
     return FEAST_OK;
 }
 
-// Shared memory of the one-launch band LU for a panel width nbp.
+// Shared memory of the one-launch band LU (per CTA) for a panel width nbp.
 static size_t gb_lu_fused_smem(int64_t kl, int64_t ku, int nbp, size_t es)
 {
-    return ((size_t)(nbp + kl) * nbp + (size_t)nbp * (kl + ku + 1)) * es + (size_t)nbp * sizeof(int);
+    const int64_t kvs = (kl + ku + GL_C - 1) / GL_C;
+    return ((size_t)(nbp + kl) * nbp + (size_t)nbp * (kvs + 1)) * es + (size_t)nbp * sizeof(int);
 }
 
 template <typename T>
@@ -826,16 +875,30 @@ int gb_getrf(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, T *F, int
 {
     const int64_t ldab = 2 * kl + ku + 1, kv = kl + ku, sF = ldab * n;
     if constexpr (sizeof(T) == sizeof(cf)) {
-        // complex64: the whole LU of each node in one CTA when its panel
-        // and U12 fit shared memory (the widest panel that does) and the
-        // band is narrow enough that one SM's share of the trailing
-        // updates (kl x kv x nb per panel) stays below the panel's own
-        // latency; wider bands spread their updates over the GPU below
+        // complex64: the whole LU of each node in one cluster when its
+        // panel and its slice of U12 fit shared memory (the widest panel
+        // that does) and the band is narrow enough that the cluster's
+        // share of the trailing updates (kl x kv x nb per panel) stays
+        // near the panel's own latency; wider bands spread their updates
+        // over the whole GPU below
         for (int nbp = GL_NB; nbp >= 8 && kv <= 512; nbp /= 2) {
             const size_t sm = gb_lu_fused_smem(kl, ku, nbp, sizeof(T));
             if (sm + 1024 > kSmemOptinMax) continue;
             FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_lu_fused<T>, sm));
-            k_gb_lu_fused<T><<<q, GL_T, sm, s>>>(n, (int)kl, (int)ku, F, ldab, sF, piv, nbp, info, row);
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = GL_C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3((unsigned)(q * GL_C));
+            cfg.blockDim = dim3(GL_T);
+            cfg.dynamicSmemBytes = sm;
+            cfg.stream = s;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            FEAST_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gb_lu_fused<T>, n, (int)kl, (int)ku, F, ldab, sF, piv, nbp,
+                                              info, row));
             FEAST_LAUNCH_CHECK();
             return FEAST_OK;
         }
@@ -914,21 +977,33 @@ size_t gb_solve_smem_bytes(int64_t kl, int64_t ku, size_t es)
     return p.smf > p.smb ? p.smf : p.smb;
 }
 
+template <typename T, int CW>
+static int gb_solve_cw(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *F, const int *piv,
+                       int64_t nrhs, T *X, int64_t ldx, int64_t sX, const GbPlan &pl)
+{
+    const int64_t ldab = 2 * kl + ku + 1, sF = ldab * n;
+    dim3 g(cdiv(nrhs, CW), q);
+    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_fwd<T, CW>, pl.smf));
+    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_bwd<T, CW>, pl.smb));
+    k_gb_fwd<T, CW><<<g, GB_ST, pl.smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX, pl.jcm, pl.nbuf);
+    FEAST_LAUNCH_CHECK();
+    k_gb_bwd<T, CW><<<g, GB_ST, pl.smb, s>>>(n, kl, ku, nrhs, F, ldab, sF, X, ldx, sX, pl.jcm, pl.nbuf);
+    FEAST_LAUNCH_CHECK();
+    return FEAST_OK;
+}
+
 template <typename T>
 int gb_solve(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, int q, const T *F, const int *piv,
              int64_t nrhs, T *X, int64_t ldx, int64_t sX)
 {
-    const int64_t ldab = 2 * kl + ku + 1, sF = ldab * n;
     const GbPlan pl = gb_plan(kl, ku, sizeof(T));
     if (pl.smf > kSmemOptinMax - 1024 || pl.smb > kSmemOptinMax - 1024) return FEAST_EINVAL;
-    dim3 g(cdiv(nrhs, pl.cw), q);
-    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_fwd<T>, pl.smf));
-    FEAST_CUDA_TRY(ensure_dyn_smem(k_gb_bwd<T>, pl.smb));
-    k_gb_fwd<T><<<g, GB_ST, pl.smf, s>>>(n, kl, ku, nrhs, F, ldab, sF, piv, X, ldx, sX, pl.cw, pl.jcm, pl.nbuf);
-    FEAST_LAUNCH_CHECK();
-    k_gb_bwd<T><<<g, GB_ST, pl.smb, s>>>(n, kl, ku, nrhs, F, ldab, sF, X, ldx, sX, pl.cw, pl.jcm, pl.nbuf);
-    FEAST_LAUNCH_CHECK();
-    return FEAST_OK;
+    switch (pl.cw) {
+    case 8: return gb_solve_cw<T, 8>(s, n, kl, ku, q, F, piv, nrhs, X, ldx, sX, pl);
+    case 4: return gb_solve_cw<T, 4>(s, n, kl, ku, q, F, piv, nrhs, X, ldx, sX, pl);
+    case 2: return gb_solve_cw<T, 2>(s, n, kl, ku, q, F, piv, nrhs, X, ldx, sX, pl);
+    default: return gb_solve_cw<T, 1>(s, n, kl, ku, q, F, piv, nrhs, X, ldx, sX, pl);
+    }
 }
 
 int gb_matmul(cudaStream_t s, int64_t n, int64_t kl, int64_t ku, const zd *M, int64_t ldin, int64_t m,

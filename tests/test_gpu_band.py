@@ -177,3 +177,27 @@ def test_band_non_regular_pencil_reports_singular(prec):
     with pytest.raises(fg.FeastError) as ei:
         fg.Feast(A, B, Y, prec=prec, contour_kind=0, rule=1, q=8, center=0j, a=1.0, kind=1, kl=kl, ku=ku)
     assert ei.value.status == -4
+
+
+def test_band_lu_complex64_without_refinement():
+    """The complex64 band LU on its own (no refinement sweeps: every digit of
+    the filtered block comes from the factors and one solve each): n = 3000
+    with kl = 120, ku = 90 (94 panels of the one-launch factorisation, a
+    ragged last one), a diagonally dominant band, so the complex64 solve is
+    good to ~1e-6 of the oracle's FP64 one; a factor entry off by a race or a
+    misplaced interchange would show as O(1)."""
+    fg = _fg()
+    n, kl, ku, m0, q = 3000, 120, 90, 12, 4
+    A = _fast_band(n, kl, ku, 21)
+    A[ku, :] += 4.0 * (kl + ku)
+    B = _fast_band(n, kl, ku, 22)
+    B[ku, :] += 4.0 * (kl + ku)
+    Y = inputs.complex_normal(np.random.default_rng(9), (n, m0))
+    kw = dict(contour_kind=1, rule=1, q=q, center=0.5 + 0.2j, a=1.5, b=0.8, kind=1, kl=kl, ku=ku)
+    g = fg.Feast(A, B, Y, prec=1, refine_tol=1e-14, max_refine=0, **kw)
+    o = oracle.Feast(A, B, Y, **kw)
+    V = inputs.complex_normal(np.random.default_rng(10), (n, m0))
+    Ug, Uo = g.filter(V), o.filter(V)
+    err = np.abs(Ug - Uo).max() / np.abs(Uo).max()
+    assert err < 1e-4, err
+    g.close(); o.close()
