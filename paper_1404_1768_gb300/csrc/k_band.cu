@@ -519,7 +519,7 @@ __global__ void k_gb_matmul(int64_t n, int64_t kl, int64_t ku, const zd *M, int6
 // unblocked convention.  A cluster barrier closes each panel.  The same
 // factors as the multi-launch form; the clusters (nodes) never wait for
 // one another.
-constexpr int GL_T = 512;
+constexpr int GL_T = 256;
 constexpr int GL_C = 8;          // CTAs per node (a portable cluster)
 constexpr int GL_NB = 32;
 __device__ __forceinline__ unsigned gl_rank()
@@ -585,11 +585,16 @@ __global__ void __launch_bounds__(GL_T) k_gb_lu_fused(int64_t n, int kl, int ku,
             }
             if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
             __syncthreads();
-            // every thread reduces the warp partials itself (the same order)
-            R bv = s_val[0];
-            int p = s_idx[0];
-            for (int w = 1; w < GL_T / 32; ++w)
-                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < p)) { bv = s_val[w]; p = s_idx[w]; }
+            // every warp reduces the warp partials itself (a shuffle tree in
+            // the same order everywhere)
+            R bv = (lane < GL_T / 32) ? s_val[lane] : (R)-1;
+            int p = (lane < GL_T / 32) ? s_idx[lane] : j;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const R ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, p, off);
+                if (ov > bv || (ov == bv && oi < p)) { bv = ov; p = oi; }
+            }
             if (tid == 0) {
                 ps[j] = p;
                 if (bv == 0 && rank == 0 && info && atomicCAS(info, 0, b + 1) == 0 && row) *row = (int)(k0 + j) + 1;

@@ -634,7 +634,9 @@ __device__ __forceinline__ void far_right(float4 *row, int ld, int nrot, const R
 // next sweep's shifts; the rest of the window goes back to Hessenberg form
 // by Householder reflections and the whole window transform is applied to
 // the rest of H and to Z by the grid.
-constexpr int NW = 48;           // largest deflation window
+// largest deflation window (the FP32 build's window is solved by one warp,
+// and its rotation chain grows with the window: a smaller one there)
+constexpr int NW = FEAST_QR_FP32 ? 32 : 48;
 constexpr int NWP = NW + 1;
 
 __device__ __forceinline__ ds ds_sqrt(ds x) { return (x.h > 0.f) ? ds_mul(x, ds_rsqrt(x)) : ds_make(0.f, 0.f); }
@@ -722,7 +724,7 @@ __device__ bool win_schur(int w, cds (*T)[NWP], cds (*V)[NWP], float tol_rel, fl
 
 #if FEAST_QR_FP32
 // FP32 build: the same single-shift QR by one warp.  The window's rows and
-// columns (at most NW = 48) take one or two lanes each, and in FP32 a
+// columns (at most NW) take one or two lanes each, and in FP32 a
 // rotation is a few operations per lane -- less than the CTA barriers the
 // whole-CTA form spends on each one; lanes order their shared-memory
 // updates with __syncwarp.  The other warps of the CTA wait at the caller's
@@ -1282,8 +1284,18 @@ __global__ void k_schur_vectors(int m, const zd *St, int ld, zd *Y, double snorm
     __syncwarp();
     for (int i = k - 1; i >= 0; --i) {
         const zd *srow = St + (int64_t)i * ld;   // S[i, :]
-        zd acc = zmake(0.0, 0.0);
-        for (int p = i + 1 + lane; p <= k; p += 32) zfma(acc, srow[p], y[p]);
+        // four independent partial sums: four loads of each operand in
+        // flight per lane (the step is bound by their latency)
+        zd acc = zmake(0.0, 0.0), a1 = acc, a2 = acc, a3 = acc;
+        int p = i + 1 + lane;
+        for (; p + 96 <= k; p += 128) {
+            zfma(acc, srow[p], y[p]);
+            zfma(a1, srow[p + 32], y[p + 32]);
+            zfma(a2, srow[p + 64], y[p + 64]);
+            zfma(a3, srow[p + 96], y[p + 96]);
+        }
+        for (; p <= k; p += 32) zfma(acc, srow[p], y[p]);
+        acc = zadd(zadd(acc, a1), zadd(a2, a3));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
