@@ -149,7 +149,7 @@ constexpr int kZeigMinM = 8;         // smallest projected problem on the standa
 // skinny blocks were faster: at n = 16384, m0 = 64 the orthonormalisation
 // took 9.8 ms per pass in FP64 and 16.8 ms on the digit slices)
 constexpr int kBandOzMinM = 256;
-constexpr double kZeigSmallEpsMin = 1e-11;   // ... when m0 <= 64: the strictest eps it serves
+constexpr double kZeigSmallEpsMin = 1e-10;   // ... when m0 <= 64: the strictest eps it serves
 
 struct Carver {
     char *base;
@@ -931,7 +931,7 @@ static int iterate_impl(feast_ctx *c, feast_iter_info *info)
         // B~ is upper triangular here (R2, or made so for Rayleigh-Ritz):
         // the standard-form QR on the FP32 pipe (double-single) from m =
         // kZeigMinM up (GB300's FP64 pipe made the FP64 QZ ~50 ms at m0 =
-        // 64); a small problem keeps the FP64 QZ when eps is within ~100x
+        // 64); a small problem keeps the FP64 QZ when eps is within ~1000x
         // of the double-single QR's backward error (2^-44 of ||C||), so
         // that e(k) can still fall below eps
         if (m > 64 || (m >= kZeigMinM && c->eps >= kZeigSmallEpsMin))

@@ -17,6 +17,8 @@ namespace feast {
 namespace {
 constexpr int GB_M = 64, GB_N = 64, GB_K = 8, GB_T = 256;
 
+constexpr int GB_SMAX = 8;     // most K-slices of a tile summed in one (portable) cluster
+
 __device__ __forceinline__ void atomic_cadd(double2 *p, double2 v)
 {
     atomicAdd(&p->x, v.x);
@@ -28,9 +30,41 @@ __device__ __forceinline__ void atomic_cadd(float2 *p, float2 v)
     atomicAdd(&p->y, v.y);
 }
 
-// splits > 1: blockIdx.z = batch * splits + s covers the s-th slice of K and
-// adds alpha * partial into C atomically (C pre-scaled by beta on the host
-// side of the launch).
+__device__ __forceinline__ unsigned gb_cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void gb_cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Load 2 (float2) or 4 (double2) words of shared memory from CTA `rank`.
+__device__ __forceinline__ float2 gb_dsmem_load(const float2 *p, unsigned rank)
+{
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ double2 gb_dsmem_load(const double2 *p, unsigned rank)
+{
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    double2 v;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+    return v;
+}
+
+// splits > 1: blockIdx.z = batch * splits + s takes the s-th slice of K.
+// Up to GB_SMAX slices the launch groups a tile's slices into one cluster
+// (s = the CTA's rank in it) and CTA 0 sums the slices' tiles in rank order
+// through distributed shared memory before it writes C, so the result does
+// not depend on which slice finishes first; beyond that (long, skinny
+// products) the slices add alpha * partial into C atomically, C pre-scaled
+// by beta on the host side of the launch.
 template <typename T>
 __global__ void __launch_bounds__(GB_T) k_gemm(int conj_a, int64_t m, int64_t n, int64_t k,
                                                T alpha, const T *__restrict__ A, int64_t lda,
@@ -41,6 +75,7 @@ __global__ void __launch_bounds__(GB_T) k_gemm(int conj_a, int64_t m, int64_t n,
 {
     __shared__ T As[GB_K][GB_M + 1];
     __shared__ T Bs[GB_K][GB_N + 1];
+    extern __shared__ __align__(16) unsigned char gb_red_raw[];   // splits > 1: this slice's tile
     const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
     const int64_t i0 = (int64_t)blockIdx.x * GB_M, j0 = (int64_t)blockIdx.y * GB_N;
     if (tri == 3 && i0 >= j0 + GB_N) return;  // tile below the diagonal (uniform per CTA)
@@ -89,6 +124,37 @@ __global__ void __launch_bounds__(GB_T) k_gemm(int conj_a, int64_t m, int64_t n,
         }
         __syncthreads();
     }
+    if (splits > GB_SMAX) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                int64_t gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * c;
+                if (gi < m && gj < n) atomic_cadd(&C[gi + gj * ldc], cmul(alpha, acc[a][c]));
+            }
+        return;
+    }
+    if (splits > 1) {
+        // every slice's tile into its own shared memory; CTA 0 adds the
+        // others' in rank order (distributed shared memory), then all wait
+        // until it has read them
+        T *red = reinterpret_cast<T *>(gb_red_raw);
+        const unsigned rank = gb_cluster_rank();
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) red[(a * 4 + c) * GB_T + threadIdx.x] = acc[a][c];
+        gb_cluster_sync();
+        if (rank == 0)
+            for (int r = 1; r < splits; ++r)
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        acc[a][c] = cadd(acc[a][c], gb_dsmem_load(red + (a * 4 + c) * GB_T + threadIdx.x, r));
+        gb_cluster_sync();
+        if (rank != 0) return;
+    }
     const bool beta0 = cis_zero(beta);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -97,12 +163,8 @@ __global__ void __launch_bounds__(GB_T) k_gemm(int conj_a, int64_t m, int64_t n,
             int64_t gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * c;
             if (gi < m && gj < n) {
                 T v = cmul(alpha, acc[a][c]);
-                if (splits > 1) {
-                    atomic_cadd(&C[gi + gj * ldc], v);
-                } else {
-                    if (!beta0) v = cadd(v, cmul(beta, C[gi + gj * ldc]));
-                    C[gi + gj * ldc] = v;
-                }
+                if (!beta0) v = cadd(v, cmul(beta, C[gi + gj * ldc]));
+                C[gi + gj * ldc] = v;
             }
         }
 }
@@ -131,29 +193,61 @@ int gemm_batched(cudaStream_t s, int conj_a, int64_t m, int64_t n, int64_t k, T 
     if (tri < 0 || tri > 3 || (conj_a && (tri == 1 || tri == 2))) return FEAST_EINVAL;
     const unsigned tiles = cdiv(m, GB_M) * cdiv(n, GB_N) * (unsigned)batch;
     // split K when the output tiles cannot fill the GPU twice over (the
-    // FP64 pipe is the bound, so every SM counts)
+    // FP64 pipe is the bound, so every SM counts: a 64 x 64 tile with
+    // K = 256 is ~1 ms of one SM's FP64 pipe), in slices of at least 32
+    // (complex64: 128); up to GB_SMAX slices are summed in a fixed order
+    // (one cluster per tile), more of them atomically (products with a
+    // long K and only a tile or two of output)
+    const bool fp64 = sizeof(T) == sizeof(zd);
+    const int64_t kmin = fp64 ? 32 : 128;
     int splits = 1;
-    if (tiles < 2 * 152 && k >= 4 * 128) {
-        int64_t want = (2 * 152 + tiles - 1) / tiles;
-        int64_t maxs = k / 128;
-        splits = (int)(want < maxs ? want : maxs);
+    if (tiles < 2 * 152 && k >= (fp64 ? 2 * kmin : 4 * kmin)) {
+        const int64_t want = (2 * 152 + tiles - 1) / tiles;
+        const int64_t many = k >= 512 ? (want < k / 128 ? want : k / 128) : 0;   // slices of >= 128
+        int64_t few = want < k / kmin ? want : k / kmin;                         // slices of >= kmin
+        if (few > GB_SMAX) few = GB_SMAX;
+        splits = (int)(many > GB_SMAX ? many : few);
         if (splits * batch > 65535) splits = 65535 / batch;
         if (splits < 1) splits = 1;
     }
     int64_t kchunk = (k + splits - 1) / splits;
     kchunk = ((kchunk + GB_K - 1) / GB_K) * GB_K;
-    if (splits > 1) {
+    dim3 grid(cdiv(m, GB_M), cdiv(n, GB_N), batch * splits);
+    if (grid.y > 65535) return FEAST_EINVAL;
+    if (splits == 1) {
+        k_gemm<T><<<grid, GB_T, 0, s>>>(conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, 1, kchunk,
+                                        tri);
+        FEAST_LAUNCH_CHECK();
+        return FEAST_OK;
+    }
+    if (splits > GB_SMAX) {
         // C <- beta C first; the slices then add alpha * partial atomically
         if (!(beta.x == 1 && beta.y == 0)) {
             unsigned gx = cdiv((size_t)m * n, 256);
             k_scale<T><<<dim3(gx > 4096 ? 4096 : gx, batch), 256, 0, s>>>(m, n, beta, C, ldc, sC);
             FEAST_LAUNCH_CHECK();
         }
+        k_gemm<T><<<grid, GB_T, 0, s>>>(conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, splits,
+                                        kchunk, tri);
+        FEAST_LAUNCH_CHECK();
+        return FEAST_OK;
     }
-    dim3 grid(cdiv(m, GB_M), cdiv(n, GB_N), batch * splits);
-    if (grid.y > 65535) return FEAST_EINVAL;
-    k_gemm<T><<<grid, GB_T, 0, s>>>(conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
-                                    splits, kchunk, tri);
+    const size_t red = sizeof(T) * 16 * GB_T;
+    FEAST_CUDA_TRY(ensure_dyn_smem(k_gemm<T>, red));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = (unsigned)splits;
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(GB_T);
+    cfg.dynamicSmemBytes = red;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FEAST_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gemm<T>, conj_a, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                      sC, splits, kchunk, tri));
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }
