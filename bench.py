@@ -588,6 +588,13 @@ def solve_step(fg, *a, step="", **kw):
         return solve_once(fg, *a, **kw)
 
 
+# DRAM bytes per launch of the kernels that lead two workloads' roofline
+# entries, from ncu captures of exactly those workloads (the summaries under
+# profiles/ give the commands); valid for those sizes only
+HQR_FP32_DRAM_BYTES = 40165376 + 52448512                      # k_hqr, cold pass, n = 4096, m0 = 1280
+BAND_SOLVE_DRAM_BYTES = (434.031616 + 110.770432 + 700.294144 + 119.855616) * 1e6   # k_gb_fwd + k_gb_bwd
+
+
 def _bf16_peak():
     return _measured("bf16_tflops_sustained", 1753.1)
 
@@ -647,9 +654,12 @@ def roofline_phases(prob, args, ph, infos):
         # the whole cold projected-eigensolve phase time
         fp32 = [i for i in cold if i.get("qz_cold_fp32") == 1]
         ops = sum(i["qz_phases"] * 32 * 2 * m0 * (24.0 if i.get("qz_cold_fp32") == 1 else 172.0) for i in cold)
+        # DRAM bytes of one cold-pass k_hqr launch from the ncu capture of
+        # this workload (profiles/k_hqr_fp32_dense_n4096_m1280_q32.md)
+        meas = HQR_FP32_DRAM_BYTES if (n, m0, q) == (4096, 1280, 32) and fp32 else None
         out["projected eigensolve"] = {
             "bound": "alu", "achieved": ops / (t_cold / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ops / (t_cold / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": None,
+            "frac": ops / (t_cold / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": meas,
             "kernel": ("k_hqr multishift QR with early deflation (FP32 build on %d of %d cold passes, then the FP64 "
                        "Newton polish; double-single otherwise): a latency-bound rotation chain; phase time of the "
                        "cold passes (Hessenberg reduction, Newton step and eigenvectors included)" % (len(fp32), len(cold))),
@@ -716,8 +726,12 @@ def roofline(prob, args, ph):
         es = 16 if args.prec == "fp64" else 8
         traffic = q * (2 * kl + ku + 1) * n * es + 4 * q * n * m0 * es
         peak = FP64_PEAK_TFLOPS if args.prec == "fp64" else FP32_PEAK_TFLOPS
+        # DRAM bytes of one forward + backward solve from the ncu capture of
+        # this workload (profiles/k_gb_solve_band_n16384_m64_q16.md)
+        meas = (BAND_SOLVE_DRAM_BYTES if (args.prec != "fp64" and (n, kl, ku, q, m0) == (16384, 128, 128, 16, 64))
+                else None)
         return {"bound": "alu", "achieved": flops / t_solve / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / t_solve / 1e12 / peak, "traffic": None,
+                "frac": flops / t_solve / 1e12 / peak, "traffic": meas,
                 "kernel": "band solves k_gb_fwd + k_gb_bwd (subspace-build phase), "
                           + ("FP64 pipe" if args.prec == "fp64" else "FP32 pipe"),
                 "peak_source": "derived: 152 SMs x " + ("2 DFMA" if args.prec == "fp64" else "128 FFMA")
