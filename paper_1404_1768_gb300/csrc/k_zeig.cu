@@ -1273,7 +1273,12 @@ __global__ void __launch_bounds__(QT, 1) k_hqr(int m, float4 *H, float4 *Z, int 
 // row of S reads contiguous memory.  Y is m x m (upper triangular on output).
 __global__ void k_schur_vectors(int m, const zd *St, int ld, zd *Y, double snorm)
 {
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    // eigenvector k costs ~k^2 / 2 complex MACs on the FP64 pipe: the warps
+    // of a CTA take eigenvectors gridDim.x apart, so that every SM gets a
+    // mix of short and long ones (consecutive k put the longest ones of all
+    // on one SM)
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x + (int)gridDim.x * (threadIdx.x >> 5);
     if (k >= m) return;
     const double eps = 2.220446049250313e-16;
     const double small = eps * fmax(snorm, 1e-300);
