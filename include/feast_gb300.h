@@ -111,7 +111,7 @@ typedef struct {
  * a host collective and a copy back).  Every rank makes the same sequence
  * of calls.  Return 0, or non-zero on failure (the library then returns
  * FEAST_ECUDA).  Uses: the partial sums of line 16 and of the first
- * subspace (SUM, 2 n m0 doubles), the set-up's singular-pivot verdict
+ * subspace (SUM, 2 n m0 doubles), the set-up's singular-pivot outcome
  * (SUM, 1 double) and each pass's stopping flag (BCAST, 1 double: rank 0's
  * flag is every rank's, so that all ranks stop at the same pass). */
 enum { FEAST_COLL_SUM = 0, FEAST_COLL_BCAST = 1 };
