@@ -129,3 +129,46 @@ def test_batch_schedule_autotuner_picks_the_fastest_trial():
     assert t.best == 32 and t.next() == 32
     t.record(32, 50.0)            # a slower repeat keeps the best time
     assert t.times[32] == 30.0 and t.best == 32
+
+
+def test_solve_step_runs_a_solve_again_after_a_bounded_wait_gave_up():
+    """A solve that ends with ETIMEOUT (a bounded device wait gave up; the
+    kernels returned and the context is intact) is run once more and listed
+    in the JSON line's retried_solves; any other failure propagates."""
+    import types
+
+    class FeastError(RuntimeError):
+        def __init__(self, status):
+            super().__init__(f"status {status}")
+            self.status = status
+
+    fg = types.SimpleNamespace(FeastError=FeastError)
+    calls = []
+
+    def fake_solve_once(fg_, *a, **kw):
+        calls.append(1)
+        if len(calls) == 1:
+            raise FeastError(-6)
+        return {"ok": True}
+
+    saved = bench.solve_once
+    bench.RETRIES.clear()
+    try:
+        bench.solve_once = fake_solve_once
+        assert bench.solve_step(fg, step="timed 0") == {"ok": True}
+        assert len(calls) == 2
+        assert len(bench.RETRIES) == 1 and bench.RETRIES[0]["step"] == "timed 0"
+
+        def failing(fg_, *a, **kw):
+            raise FeastError(-4)
+
+        bench.solve_once = failing
+        try:
+            bench.solve_step(fg, step="timed 1")
+            raise AssertionError("a singular pencil must not be retried")
+        except FeastError as e:
+            assert e.status == -4
+        assert len(bench.RETRIES) == 1
+    finally:
+        bench.solve_once = saved
+        bench.RETRIES.clear()
