@@ -316,7 +316,8 @@ struct OzScratch {
 // <- upper triangular with real positive diagonal.  Gram matrices and the
 // products V R^{-1} on the tensor cores (oz.rows >= oz_rows_bytes(max(n, m),
 // max(n, m)), oz.cols >= oz_cols_bytes(n, m)); Cholesky and triangular
-// inverses FP64.  *ok = 0 (V untouched) when a pivot shows cond(V) beyond
+// inverses FP64 (oz.rows null: every product an FP64 GEMM, through tmp,
+// n x m).  *ok = 0 (V untouched) when a pivot shows cond(V) beyond
 // reach (checked on the first factorisation); the caller then runs
 // BCGS2.  work: zorth_chol_work_bytes(m).
 // Ri (m x m, ld m) = R^{-1}, R upper triangular (ld ldr); recursive
@@ -326,7 +327,7 @@ size_t tri_inverse_scratch_elems(int m);
 int tri_inverse(cudaStream_t s, int m, const zd *R, int64_t ldr, zd *Ri, zd *T);
 size_t zorth_chol_work_bytes(int64_t m);
 int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr, void *work,
-               const OzScratch &oz, int *ok);
+               const OzScratch &oz, int *ok, zd *tmp = nullptr);
 
 int zorth(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr,
           zd *work, int *timeout, const OzScratch *oz = nullptr);

@@ -237,8 +237,10 @@ void carve(feast_ctx *c, Carver &cv)
                 c->ozX = cv.take<char>(oz_cols_bytes((int64_t)n, (int64_t)(2 * m)));
                 const size_t r1 = oz_rows_bytes((int64_t)m, (int64_t)n), r2 = oz_rows_bytes((int64_t)n, (int64_t)m);
                 c->ozR = cv.take<char>(r1 > r2 ? r1 : r2);
-                c->chol_work = cv.take<char>(zorth_chol_work_bytes((int64_t)m));
             }
+            // Cholesky QR twice (FP64 GEMMs below that width; BCGS2 as the
+            // fallback when a pivot shows the block too ill-conditioned)
+            c->chol_work = cv.take<char>(zorth_chol_work_bytes((int64_t)m));
         }
         c->gb_pivl = cv.take<int>(gb_piv_scratch(c->kl, (int)q));
     } else if (c->prec == FEAST_FP64) {
@@ -604,7 +606,9 @@ int orth_block(feast_ctx *c, zd *V, zd *R)
     int e;
     if (c->chol_work) {
         int ok = 0;
-        if ((e = zorth_chol(c->s, n, m, V, n, R, m, c->chol_work, *orth_oz(c), &ok))) return e;
+        const OzScratch *oz = orth_oz(c);
+        const OzScratch none{nullptr, nullptr, &c->st->timeout};
+        if ((e = zorth_chol(c->s, n, m, V, n, R, m, c->chol_work, oz ? *oz : none, &ok, c->tmp))) return e;
         if (ok) return FEAST_OK;
     }
     return zorth(c->s, n, m, V, n, R, m, c->orth_work, &c->st->timeout, orth_oz(c));

@@ -250,6 +250,8 @@ unsigned grid_for(size_t count)
 int oz_mm(cudaStream_t s, const OzScratch &oz, int conj_a, int64_t M, int64_t N, int64_t K, zd alpha, const zd *A,
           int64_t lda, const zd *B, int64_t ldb, zd beta, zd *C, int64_t ldc)
 {
+    // (without digit-plane scratch: the FP64 GEMM; C must not overlap A, B)
+    if (!oz.rows) return zgemm_batched(s, conj_a, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1);
     int e;
     if ((e = oz_prepare_rows(s, M, K, A, lda, oz.rows, conj_a))) return e;
     if ((e = oz_prepare_cols(s, K, N, B, ldb, oz.cols))) return e;
@@ -336,9 +338,27 @@ size_t zorth_chol_work_bytes(int64_t m)
            sizeof(double) * (size_t)m + 64;
 }
 
-int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr, void *work,
-               const OzScratch &oz, int *ok)
+// V <- V X (beta = 0) or V <- V + V X (beta = 1), X m x m: on the digit
+// slices in place, or in FP64 through tmp (n x m, a copy of V).
+static int mul_right(cudaStream_t s, const OzScratch &oz, int64_t n, int64_t m, zd *V, int64_t ldv, const zd *X,
+                     zd beta, zd *tmp)
 {
+    const zd one = zmake(1.0, 0.0);
+    int e;
+    if (oz.rows) {
+        if ((e = oz_prepare_rows(s, n, m, V, ldv, oz.rows))) return e;
+        if ((e = oz_prepare_cols(s, m, m, X, m, oz.cols))) return e;
+        return oz_gemm(s, n, m, m, oz.rows, oz.cols, one, nullptr, 0, beta, V, ldv, oz.err);
+    }
+    FEAST_CUDA_TRY(cudaMemcpy2DAsync(tmp, sizeof(zd) * n, V, sizeof(zd) * ldv, sizeof(zd) * n, m,
+                                     cudaMemcpyDeviceToDevice, s));
+    return zgemm_batched(s, 0, n, m, m, one, tmp, n, 0, X, m, 0, beta, V, ldv, 0, 1);
+}
+
+int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr, void *work,
+               const OzScratch &oz, int *ok, zd *tmp)
+{
+    if (!oz.rows && !tmp) return FEAST_EINVAL;
     *ok = 0;
     if (m <= 0) {
         *ok = 1;
@@ -360,9 +380,7 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
     int e;
     FEAST_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), s));
     // pass 1: G = V^H V = R_a^H R_a, V <- V R_a^{-1}
-    if ((e = oz_prepare_rows(s, m, n, V, ldv, oz.rows, 1))) return e;
-    if ((e = oz_prepare_cols(s, n, m, V, ldv, oz.cols))) return e;
-    if ((e = oz_gemm(s, m, m, n, oz.rows, oz.cols, one, nullptr, 0, zero, F0, m, oz.err))) return e;
+    if ((e = oz_mm(s, oz, 1, m, m, n, one, V, ldv, V, ldv, zero, F0, m))) return e;
     if ((e = cholesky(s, (int)m, F0, d0, fail, bar, rinv, oz.err))) return e;
     {
         int hf = 0;
@@ -373,17 +391,13 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
     k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F0, m);
     FEAST_LAUNCH_CHECK();
     if ((e = tri_inverse(s, (int)m, F0, m, Ti, Ts))) return e;
-    if ((e = oz_prepare_rows(s, n, m, V, ldv, oz.rows))) return e;
-    if ((e = oz_prepare_cols(s, m, m, Ti, m, oz.cols))) return e;
-    if ((e = oz_gemm(s, n, m, m, oz.rows, oz.cols, one, nullptr, 0, zero, V, ldv, oz.err))) return e;
+    if ((e = mul_right(s, oz, n, m, V, ldv, Ti, zero, tmp))) return e;
     // pass 2: G = V^H V = I + E with E ~ eps cond(V)^2.  R_b = I + S with
     // S + S^H = E - S^H S; S_0 = phi(E), S = phi(E - S_0^H S_0) (error
     // O(|E|^3), phi = strict upper part + half the diagonal), R_b^{-1} =
     // I - S + S^2 (error O(|E|^3)): V <- V + V (S^2 - S).  Only when
     // max|E| <= 1e-4; otherwise a second Cholesky and inverse.
-    if ((e = oz_prepare_rows(s, m, n, V, ldv, oz.rows, 1))) return e;
-    if ((e = oz_prepare_cols(s, n, m, V, ldv, oz.cols))) return e;
-    if ((e = oz_gemm(s, m, m, n, oz.rows, oz.cols, one, nullptr, 0, zero, F1, m, oz.err))) return e;
+    if ((e = oz_mm(s, oz, 1, m, m, n, one, V, ldv, V, ldv, zero, F1, m))) return e;
     FEAST_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), s));
     k_offident_max<<<grid_for(mm), 256, 0, s>>>((int)m, F1, emax);
     FEAST_LAUNCH_CHECK();
@@ -406,7 +420,7 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
         // D = S^2 - S, then V <- V + V D
         FEAST_CUDA_TRY(cudaMemcpyAsync(D, S, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
         if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, S, m, zmake(-1.0, 0.0), D, m))) return e;
-        if ((e = oz_mm(s, oz, 0, n, m, m, one, V, ldv, D, m, one, V, ldv))) return e;
+        if ((e = mul_right(s, oz, n, m, V, ldv, D, one, tmp))) return e;
         // R = (I + S) R_a
         if (R) {
             FEAST_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(zd) * ldr, F0, sizeof(zd) * m, sizeof(zd) * m, m,
@@ -418,15 +432,9 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
         k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F1, m);
         FEAST_LAUNCH_CHECK();
         if ((e = tri_inverse(s, (int)m, F1, m, Ti, Ts))) return e;
-        if ((e = oz_prepare_rows(s, n, m, V, ldv, oz.rows))) return e;
-        if ((e = oz_prepare_cols(s, m, m, Ti, m, oz.cols))) return e;
-        if ((e = oz_gemm(s, n, m, m, oz.rows, oz.cols, one, nullptr, 0, zero, V, ldv, oz.err))) return e;
+        if ((e = mul_right(s, oz, n, m, V, ldv, Ti, zero, tmp))) return e;
         // R = R_b R_a
-        if (R) {
-            if ((e = oz_prepare_rows(s, m, m, F1, m, oz.rows))) return e;
-            if ((e = oz_prepare_cols(s, m, m, F0, m, oz.cols))) return e;
-            if ((e = oz_gemm(s, m, m, m, oz.rows, oz.cols, one, nullptr, 0, zero, R, ldr, oz.err))) return e;
-        }
+        if (R && (e = oz_mm(s, oz, 0, m, m, m, one, F1, m, F0, m, zero, R, ldr))) return e;
     }
     if (R) {
         k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, R, ldr);
