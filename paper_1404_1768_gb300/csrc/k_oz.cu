@@ -54,6 +54,43 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return a | (b << 16);
 }
 
+// x as a double, exactly, for |x| < 2^51: 1.5 2^52 + x has x in its low
+// significand bits
+__device__ __forceinline__ double exact_double(long long x)
+{
+    return __longlong_as_double(x + 0x4338000000000000LL) - 6755399441055744.0;
+}
+
+// A row or column with an Inf or NaN entry: its products are NaN (its
+// digits are zero, and the epilogue writes NaN).
+constexpr int OZ_NONFINITE = -0x40000000;
+
+// The larger of |Re v|, |Im v| as IEEE bits (non-negative doubles order like
+// their bits), folded into mx; bad is set for a non-finite entry.
+__device__ __forceinline__ void fold_mag(zd v, unsigned long long &mx, bool &bad)
+{
+    const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull;
+    const unsigned long long m = a > b ? a : b;
+    bad = bad || m >= 0x7ff0000000000000ull;
+    mx = m > mx ? m : mx;
+}
+
+// Warp-wide: the exponent e with max < 2^e (frexp's; 0 for zero), or
+// OZ_NONFINITE, in every lane.
+__device__ __forceinline__ int warp_exponent(unsigned long long mx, bool bad)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    if (__any_sync(0xffffffffu, bad)) return OZ_NONFINITE;
+    if (mx == 0) return 0;
+    const int bexp = (int)(mx >> 52);
+    return bexp ? bexp - 1022 : 64 - __clzll((long long)mx) - 1074;   // (subnormal max)
+}
+
 // e_i with max_k max(|Re a_ik|, |Im a_ik|) < 2^e_i (0 for a zero row); one
 // warp per row.  ct: the operand is the conjugate transpose of the stored
 // matrix, a_ik = conj(A[k + i lda]).
@@ -63,18 +100,11 @@ __global__ void k_oz_rowexp(int64_t M, int64_t K, const zd *__restrict__ A, int6
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= M) return;
-    double mx = 0.0;
-    for (int64_t k = lane; k < K; k += 32) {
-        const zd v = ct ? A[k + i * lda] : A[i + k * lda];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) {
-        int ex = 0;
-        if (mx > 0.0) frexp(mx, &ex);
-        e[i] = ex;
-    }
+    unsigned long long mx = 0;
+    bool bad = false;
+    for (int64_t k = lane; k < K; k += 32) fold_mag(ct ? A[k + i * lda] : A[i + k * lda], mx, bad);
+    const int ex = warp_exponent(mx, bad);
+    if (lane == 0) e[i] = ex;
 }
 
 // f_j for column j of B (one warp per column).
@@ -83,29 +113,45 @@ __global__ void k_oz_colexp(int64_t K, int64_t N, const zd *__restrict__ B, int6
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= N) return;
-    double mx = 0.0;
-    for (int64_t k = lane; k < K; k += 32) {
-        zd v = B[k + j * ldb];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) {
-        int ex = 0;
-        if (mx > 0.0) frexp(mx, &ex);
-        f[j] = ex;
-    }
+    unsigned long long mx = 0;
+    bool bad = false;
+    for (int64_t k = lane; k < K; k += 32) fold_mag(B[k + j * ldb], mx, bad);
+    const int ex = warp_exponent(mx, bad);
+    if (lane == 0) f[j] = ex;
 }
 
-// Digits of one real value already scaled into (-1, 1).
-__device__ __forceinline__ void digits(double r, float (&d)[OZ_S])
+// Digits of one real value v (IEEE bits b) scaled by 2^-e into (-1, 1):
+// with N_s = rint(64^s v 2^-e) (round half to even), digit s is
+// N_s - 64 N_(s-1) -- the same digits as the recursion t = 64 r, d = rint(t),
+// r = t - d, whose steps are all exact (a subtracted multiple of 64 is even,
+// so it commutes with the rounding).  Each N_s comes from the 53-bit
+// significand by an integer shift with round-half-even, so the slicing runs
+// on the integer pipe, not the FP64 one (1/64 of the FP32 rate on this part),
+// and is exact for subnormal rows too.  (v is finite: rows and columns with
+// an Inf or NaN are not sliced.)
+__device__ __forceinline__ void digits(unsigned long long b, int e, float (&d)[OZ_S])
 {
+    const int ex = (int)(b >> 52) & 0x7ff;
+    const unsigned long long mant = (b & 0xfffffffffffffull) | (ex ? (1ull << 52) : 0ull);
+    const int base = (ex ? ex : 1) - 1075 - e;   // |v| 2^-e = mant 2^base < 1
+    const bool neg = (b >> 63) != 0;
+    long long prev = 0;
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) {
-        const double t = r * 64.0;
-        const double q = rint(t);
-        d[s] = (float)q;
-        r = t - q;
+    for (int s = 1; s <= OZ_S; ++s) {
+        const int rs = -(base + 6 * s);
+        unsigned long long q;
+        if (rs <= 0) {
+            q = mant << (-rs);                       // (a subnormal row: no bits below the point)
+        } else if (rs >= 64) {
+            q = 0;                                   // below 2^-11
+        } else {
+            q = mant >> rs;
+            const unsigned long long rem = mant & ((1ull << rs) - 1), half = 1ull << (rs - 1);
+            q += (rem > half || (rem == half && (q & 1))) ? 1ull : 0ull;
+        }
+        const long long N = neg ? -(long long)q : (long long)q;
+        d[s - 1] = (float)(int)(N - 64 * prev);      // |digit| <= 64: exact
+        prev = N;
     }
 }
 
@@ -122,13 +168,14 @@ __global__ void k_oz_slice_rows(int64_t M, int64_t K, const zd *__restrict__ A, 
         const int64_t rr = x / half, kc = x % half;
         const int64_t i = rr >> 1;
         float d0[OZ_S], d1[OZ_S];
-        if (kc < K) {
-            zd v = ct ? A[kc + i * lda] : A[i + kc * lda];
-            if (ct) v.y = -v.y;
-            const double sc = ldexp(1.0, -e[i]);
-            const double a = v.x * sc, b = v.y * sc;
-            if ((rr & 1) == 0) { digits(a, d0); digits(-b, d1); }
-            else { digits(b, d0); digits(a, d1); }
+        const int ei = e[i];
+        if (kc < K && ei != OZ_NONFINITE) {
+            const zd v = ct ? A[kc + i * lda] : A[i + kc * lda];
+            const unsigned long long sgn = 1ull << 63;
+            const unsigned long long a = (unsigned long long)__double_as_longlong(v.x);
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) ^ (ct ? sgn : 0ull);
+            if ((rr & 1) == 0) { digits(a, ei, d0); digits(b ^ sgn, ei, d1); }
+            else { digits(b, ei, d0); digits(a, ei, d1); }
         } else {
 #pragma unroll
             for (int s = 0; s < OZ_S; ++s) { d0[s] = 0.f; d1[s] = 0.f; }
@@ -151,11 +198,11 @@ __global__ void k_oz_slice_cols(int64_t K, int64_t N, const zd *__restrict__ B, 
          x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = x / half, kc = x % half;
         float d0[OZ_S], d1[OZ_S];
-        if (kc < K) {
+        const int fj = f[j];
+        if (kc < K && fj != OZ_NONFINITE) {
             const zd v = B[kc + j * ldb];
-            const double sc = ldexp(1.0, -f[j]);
-            digits(v.x * sc, d0);
-            digits(v.y * sc, d1);
+            digits((unsigned long long)__double_as_longlong(v.x), fj, d0);
+            digits((unsigned long long)__double_as_longlong(v.y), fj, d1);
         } else {
 #pragma unroll
             for (int s = 0; s < OZ_S; ++s) { d0[s] = 0.f; d1[s] = 0.f; }
@@ -291,16 +338,30 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int c = 0; c < nchunk; ++c) {
             if (!mbar_wait(&chunk_full, (uint32_t)(c & 1)) || *(volatile int *)&s_fail) { good = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // acc += sum_g 64^-g S_g = 2^-18 (hi + 2^-24 lo) with the exact
+            // integers hi = sum_(g<4) 64^(3-g) S_g, lo = sum_(g>=4) 64^(7-g) S_g
+            // (|hi|, |lo| < 2^45): two roundings per chunk instead of eight,
+            // and the class sums combined on the integer pipe
+            static_assert(OZ_NG == 8, "the read-out pairs eight weight classes");
+            const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-            for (int g = 0; g < OZ_NG; ++g) {
-                const double w = ldexp(1.0, -6 * g);
+            for (int cg = 0; cg < OZ_BN / 8; ++cg) {
+                int p[4][8];   // p_q = 64 S_2q + S_(2q+1) (|p_q| < 2^31)
 #pragma unroll
-                for (int h = 0; h < OZ_BN / 32; ++h) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * OZ_BN + h * 32), v);
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t va[8], vb[8];
+                    tmem_ld8x2(tw + (uint32_t)(2 * q * OZ_BN + cg * 8), tw + (uint32_t)((2 * q + 1) * OZ_BN + cg * 8),
+                               va, vb);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        acc[h * 32 + j] = fma((double)__uint_as_float(v[j]), w, acc[h * 32 + j]);
+                    for (int j = 0; j < 8; ++j)
+                        p[q][j] = __float2int_rn(__uint_as_float(va[j])) * 64 + __float2int_rn(__uint_as_float(vb[j]));
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const long long hi = (long long)p[0][j] * 4096 + p[1][j];
+                    const long long lo = (long long)p[2][j] * 4096 + p[3][j];
+                    const double t = fma(exact_double(lo), 0x1p-24, exact_double(hi));
+                    acc[cg * 8 + j] = fma(t, 0x1p-18, acc[cg * 8 + j]);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -318,6 +379,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             // with the old values loaded first
             const int hsel = im_row ? 1 : 0;
             const bool rd = (out.beta.x != 0.0 || out.beta.y != 0.0);
+            // (a real alpha and a unit beta, the common cases, skip the complex products)
+            const bool real_alpha = out.zcol == nullptr && out.alpha.y == 0.0;
+            const bool unit_beta = out.beta.x == 1.0 && out.beta.y == 0.0;
 #pragma unroll
             for (int g8 = 0; g8 < OZ_BN / 2; g8 += 8) {
                 zd d[8], o[8];
@@ -337,12 +401,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int col = col0 + hsel * 32 + g8 + i;
-                    if (r < mr && col < n) {
-                        const double sc = ldexp(1.0, er + fb[col] - 12);
-                        zd al = out.alpha;
-                        if (out.zcol) al = zmul(al, out.zcol[col / out.cblk]);
-                        zd res = zmul(al, zscale(d[i], sc));
-                        if (rd) res = zadd(res, zmul(out.beta, o[i]));
+                    if (r < mr && col < n && (er == OZ_NONFINITE || fb[col] == OZ_NONFINITE)) {
+                        out.C[ci + (int64_t)col * out.ldc] = zmake(__longlong_as_double(0x7ff8000000000000LL),
+                                                                   __longlong_as_double(0x7ff8000000000000LL));
+                    } else if (r < mr && col < n) {
+                        // d 2^(e_i + f_j - 12): a power of two built from its bits, or
+                        // (a result near the ends of the range) ldexp, one rounding
+                        const int ex = er + fb[col] - 12;
+                        zd res = (ex >= -1022 && ex <= 1023)
+                                     ? zscale(d[i], __longlong_as_double((long long)(ex + 1023) << 52))
+                                     : zmake(ldexp(d[i].x, ex), ldexp(d[i].y, ex));
+                        if (real_alpha) {
+                            if (out.alpha.x != 1.0) res = zscale(res, out.alpha.x);
+                        } else {
+                            zd al = out.alpha;
+                            if (out.zcol) al = zmul(al, out.zcol[col / out.cblk]);
+                            res = zmul(al, res);
+                        }
+                        if (rd) res = zadd(res, unit_beta ? o[i] : zmul(out.beta, o[i]));
                         out.C[ci + (int64_t)col * out.ldc] = res;
                     }
                 }

@@ -55,3 +55,58 @@ def test_zgemm_oz_exact_on_small_integers():
     B = rng.integers(-40, 40, (300, 90)) + 1j * rng.integers(-40, 40, (300, 90))
     out = fg.zgemm_oz(A, B)
     np.testing.assert_array_equal(out, A @ B)
+
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-2.5, 1.0), (0.5, 0.0), (1.0, -1.0)])
+def test_zgemm_oz_real_alpha_unit_beta(alpha, beta):
+    """The epilogue's short forms (a real alpha, a unit beta) give the same
+    products as the complex-scalar form."""
+    import paper_1404_1768_gb300 as fg
+    rng = np.random.default_rng(17)
+    A = inputs.complex_normal(rng, (150, 700))
+    B = inputs.complex_normal(rng, (700, 90))
+    C0 = inputs.complex_normal(rng, (150, 90))
+    out = fg.zgemm_oz(A, B, C0, alpha=alpha, beta=beta)
+    _check(A, B, C0, alpha, beta, out)
+
+
+def test_zgemm_oz_subnormal_rows():
+    """A row whose entries are all subnormal (|a| ~ 1e-310) is sliced from
+    its own bits: the row keeps its relative accuracy."""
+    import paper_1404_1768_gb300 as fg
+    rng = np.random.default_rng(21)
+    A = inputs.complex_normal(rng, (40, 200))
+    A[7] *= 1e-310
+    A[8] *= 5e-322
+    B = inputs.complex_normal(rng, (200, 30))
+    out = fg.zgemm_oz(A, B)
+    assert np.all(np.isfinite(out))
+    ref = A @ B
+    for i in (7, 8):
+        ra = np.max(np.maximum(np.abs(A[i].real), np.abs(A[i].imag)))
+        cb = np.max(np.maximum(np.abs(B.real), np.abs(B.imag)), axis=0)
+        # subnormal entries carry fewer bits than the digits: the bound is
+        # the larger of the method's and the entries' own spacing
+        bound = 2.0 ** -45 * 200 * ra * cb + 200 * 5e-324 * cb
+        assert np.all(np.abs(out[i] - ref[i]) <= bound)
+    _check(np.delete(A, [7, 8], 0), B, np.zeros((38, 30)), 1.0, 0.0, np.delete(out, [7, 8], 0))
+
+
+def test_zgemm_oz_non_finite_rows_and_columns_are_nan():
+    """An Inf or NaN in row i of A or column j of B makes row i / column j of
+    the product non-finite (NaN), as in complex128; every other entry is
+    unaffected."""
+    import paper_1404_1768_gb300 as fg
+    rng = np.random.default_rng(23)
+    A = inputs.complex_normal(rng, (60, 120))
+    B = inputs.complex_normal(rng, (120, 50))
+    A[3, 10] = np.nan
+    A[11, 0] = complex(np.inf, 0.0)
+    B[5, 7] = complex(0.0, -np.inf)
+    out = fg.zgemm_oz(A, B)
+    bad_r, bad_c = [3, 11], [7]
+    assert np.all(np.isnan(out[bad_r, :]))
+    assert np.all(np.isnan(out[:, bad_c]))
+    keep_r = [i for i in range(60) if i not in bad_r]
+    keep_c = [j for j in range(50) if j not in bad_c]
+    _check(A[keep_r], B[:, keep_c], np.zeros((58, 49)), 1.0, 0.0, out[np.ix_(keep_r, keep_c)])
