@@ -599,8 +599,9 @@ int filter_defect(feast_ctx *c, zd *Uout)
 
 // V = Q R in place (n x m0).  Dense precision form: Cholesky QR twice on
 // the tensor-core products (k_chol.cu), BCGS2 if V is too ill-conditioned
-// for it; otherwise BCGS2 (k_zorth.cu).
-int orth_block(feast_ctx *c, zd *V, zd *R)
+// for it; otherwise BCGS2 (k_zorth.cu).  want_r false: only Q is needed (R
+// may be left unset; it is scratch for BCGS2).
+int orth_block(feast_ctx *c, zd *V, zd *R, bool want_r = true)
 {
     const int64_t n = c->n, m = c->m0;
     int e;
@@ -608,7 +609,9 @@ int orth_block(feast_ctx *c, zd *V, zd *R)
         int ok = 0;
         const OzScratch *oz = orth_oz(c);
         const OzScratch none{nullptr, nullptr, &c->st->timeout};
-        if ((e = zorth_chol(c->s, n, m, V, n, R, m, c->chol_work, oz ? *oz : none, &ok, c->tmp))) return e;
+        if ((e = zorth_chol(c->s, n, m, V, n, want_r ? R : nullptr, m, c->chol_work, oz ? *oz : none, &ok,
+                            c->tmp)))
+            return e;
         if (ok) return FEAST_OK;
     }
     return zorth(c->s, n, m, V, n, R, m, c->orth_work, &c->st->timeout, orth_oz(c));
@@ -622,7 +625,7 @@ int orthonormalise(feast_ctx *c, const zd *Usrc)
     int e;
     if (Usrc != c->U1)
         FEAST_CUDA_TRY(cudaMemcpyAsync(c->U1, Usrc, sizeof(zd) * n * m, cudaMemcpyDeviceToDevice, c->s));
-    if ((e = orth_block(c, c->U1, c->R1))) return e;
+    if ((e = orth_block(c, c->U1, c->R1, false))) return e;   // (only U1's span and order are used)
     zd *BU1 = c->W + n * m;
     if ((e = apply_B(c, c->U1, BU1, m))) return e;
     if (c->projection == FEAST_RAYLEIGH_RITZ) return FEAST_OK;

@@ -5,21 +5,25 @@
 //     Q = Q_1 R_b^{-1},  R = R_b R_a.
 //
 // The Gram matrices and the products V R^{-1} are FP64-accurate GEMMs on the
-// tensor cores (k_oz.cu); the Cholesky factorisations and the triangular
-// inverses are FP64 (the Cholesky one cooperative launch, the inverse by
-// recursive doubling).  The first pass leaves Q_1 orthonormal to ~eps
-// cond(V)^2, the second to ~eps, while cond(V) stays below ~1e6.  Every
-// pivot is checked against its column's original norm: a pivot below
-// 1e-12 of it (cond(V) out of reach) reports failure and the caller runs
-// the column-by-column BCGS2 instead.  R has a real positive diagonal, like
-// the Householder QR with that sign convention, so Q and R are the same
-// unique factors.
+// tensor cores (k_oz.cu); the triangular inverses are FP64 (recursive
+// doubling), the Cholesky factorisations one cooperative launch each: FP64,
+// or -- the first one, on the digit-sliced path from m = 256 -- FP32 on the
+// unit-diagonal Gram matrix, since the second pass corrects whatever the
+// first leaves.  The first pass leaves Q_1 orthonormal to ~eps cond(V)^2
+// (FP64) or ~2^-24 cond of the scaled Gram matrix (FP32), the second to
+// ~eps, while cond(V) stays below ~1e6.  Every FP64 pivot is checked
+// against its column's original norm: a pivot below 1e-12 of it (cond(V)
+// out of reach) reports failure and the caller runs the column-by-column
+// BCGS2 instead.  R has a real positive diagonal, like the Householder QR
+// with that sign convention, so Q and R are the same unique factors.
 #include "common.cuh"
 
 namespace feast {
 namespace {
 
 constexpr int CB = 32;  // Cholesky block
+constexpr int kChol32MinM = 256;      // the FP32 first factorisation from this block width up
+constexpr double kChol32Tol = 1e-4;   // its pivots against the unit diagonal
 
 __global__ void k_diag_copy(int m, const zd *__restrict__ G, double *__restrict__ d)
 {
@@ -73,16 +77,22 @@ __global__ void __launch_bounds__(CB) k_trinv_diag(int m, const zd *__restrict__
 // SM): per 32-column step, CTA 0 factors and inverts the diagonal block;
 // after a grid barrier every warp takes columns of the row panel
 // R12 = R11^{-H} G12; after another, the CTAs share the 32 x 32 tiles of the
-// trailing block's upper triangle (G22 -= R12^H R12).  FP64 throughout; the
-// launch sequence of the blocked form (three launches per step, each too
-// small to fill the GPU) becomes grid barriers.
+// trailing block's upper triangle (G22 -= R12^H R12).  The launch sequence
+// of the blocked form (three launches per step, each too small to fill the
+// GPU) becomes grid barriers.  T = double2 (FP64) or float2 (FP32: the
+// first factorisation of Cholesky QR, on a unit-diagonal Gram matrix).  A
+// pivot at or below tol times its reference (d0, or 1 without one) sets
+// *fail.
 constexpr int PT = 256;
-__global__ void __launch_bounds__(PT, 1) k_chol_grid(int m, zd *__restrict__ G, const double *__restrict__ d0,
-                                                     int *__restrict__ fail, zd *__restrict__ rinv, GridSync gs)
+template <typename T>
+__global__ void __launch_bounds__(PT, 1) k_chol_grid(int m, T *__restrict__ G, const double *__restrict__ d0,
+                                                     double tol, int *__restrict__ fail, T *__restrict__ rinv,
+                                                     GridSync gs)
 {
-    __shared__ zd T[CB][CB + 1];
-    __shared__ zd P2[CB][CB + 1];
-    __shared__ double rsh;
+    using R = typename CxReal<T>::type;
+    __shared__ T Tb[CB][CB + 1];
+    __shared__ T P2[CB][CB + 1];
+    __shared__ R rsh;
     const int tid = threadIdx.x, lane = tid & 31;
     const int gwarp = blockIdx.x * (PT / 32) + (tid >> 5), nwarp = gridDim.x * (PT / 32);
     for (int k0 = 0; k0 < m; k0 += CB) {
@@ -91,53 +101,55 @@ __global__ void __launch_bounds__(PT, 1) k_chol_grid(int m, zd *__restrict__ G, 
         if (blockIdx.x == 0) {
             for (int e = tid; e < CB * CB; e += PT) {
                 const int i = e % CB, k = e / CB;
-                T[i][k] = (i < nb && k < nb) ? G[(k0 + i) + (int64_t)(k0 + k) * m] : zmake(0.0, 0.0);
+                Tb[i][k] = (i < nb && k < nb) ? G[(k0 + i) + (int64_t)(k0 + k) * m] : cx<T>(0, 0);
             }
             __syncthreads();
             for (int j = 0; j < nb; ++j) {
                 if (tid == 0) {
-                    const double d = T[j][j].x, ref = d0[k0 + j];
-                    double r;
-                    if (!(d > 1e-12 * ref) || !(ref > 0.0)) {
+                    const double d = (double)Tb[j][j].x, ref = d0 ? d0[k0 + j] : 1.0;
+                    R r;
+                    if (!(d > tol * ref) || !(ref > 0.0)) {
                         *fail = 1;
-                        r = 1.0;
+                        r = (R)1;
                     } else {
-                        r = sqrt(d);
+                        r = sqrt((R)d);
                     }
-                    T[j][j] = zmake(r, 0.0);
-                    rsh = 1.0 / r;
+                    Tb[j][j] = cx<T>(r, 0);
+                    rsh = (R)1 / r;
                 }
                 __syncthreads();
-                for (int k = j + 1 + tid; k < nb; k += PT) T[j][k] = zscale(T[j][k], rsh);
+                for (int k = j + 1 + tid; k < nb; k += PT) Tb[j][k] = cx<T>(Tb[j][k].x * rsh, Tb[j][k].y * rsh);
                 __syncthreads();
                 for (int e = tid; e < CB * CB; e += PT) {
                     const int i = e % CB, k = e / CB;
                     if (i > j && k >= i && k < nb) {
-                        const zd rji = T[j][i], rjk = T[j][k];
-                        T[i][k] = zsub(T[i][k], zmake(rji.x * rjk.x + rji.y * rjk.y, rji.x * rjk.y - rji.y * rjk.x));
+                        const T rji = Tb[j][i], rjk = Tb[j][k];
+                        Tb[i][k] = cx<T>(Tb[i][k].x - (rji.x * rjk.x + rji.y * rjk.y),
+                                         Tb[i][k].y - (rji.x * rjk.y - rji.y * rjk.x));
                     }
                 }
                 __syncthreads();
             }
             for (int e = tid; e < CB * CB; e += PT) {
                 const int i = e % CB, k = e / CB;
-                if (i < nb && k < nb && k >= i) G[(k0 + i) + (int64_t)(k0 + k) * m] = T[i][k];
+                if (i < nb && k < nb && k >= i) G[(k0 + i) + (int64_t)(k0 + k) * m] = Tb[i][k];
             }
             // R11^{-1} (upper), column k by thread k: back-substitution
             if (tid < nb) {
                 const int k = tid;
-                zd x[CB];
+                T x[CB];
 #pragma unroll
-                for (int i = 0; i < CB; ++i) x[i] = zmake(0.0, 0.0);
-                x[k] = zmake(1.0 / T[k][k].x, 0.0);
+                for (int i = 0; i < CB; ++i) x[i] = cx<T>(0, 0);
+                x[k] = cx<T>((R)1 / Tb[k][k].x, 0);
 #pragma unroll
                 for (int i = CB - 1; i >= 0; --i) {
                     if (i >= k) continue;
-                    zd acc = zmake(0.0, 0.0);
+                    T acc = cx<T>(0, 0);
 #pragma unroll
                     for (int p = 0; p < CB; ++p)
-                        if (p > i && p <= k) zfma(acc, T[i][p], x[p]);
-                    x[i] = zscale(zmake(-acc.x, -acc.y), 1.0 / T[i][i].x);
+                        if (p > i && p <= k) cfma(acc, Tb[i][p], x[p]);
+                    const R di = (R)1 / Tb[i][i].x;
+                    x[i] = cx<T>(-acc.x * di, -acc.y * di);
                 }
 #pragma unroll
                 for (int i = 0; i < CB; ++i) rinv[i + k * CB] = x[i];
@@ -148,19 +160,19 @@ __global__ void __launch_bounds__(PT, 1) k_chol_grid(int m, zd *__restrict__ G, 
         // row panel: column c by one warp, lane i -> entry i
         for (int e = tid; e < CB * CB; e += PT) {
             const int i = e % CB, k = e / CB;
-            T[i][k] = (i < nb && k < nb) ? rinv[i + k * CB] : zmake(0.0, 0.0);
+            Tb[i][k] = (i < nb && k < nb) ? rinv[i + k * CB] : cx<T>(0, 0);
         }
         __syncthreads();
         for (int c = k1 + gwarp; c < m; c += nwarp) {
-            const zd g = (lane < nb) ? G[(k0 + lane) + (int64_t)c * m] : zmake(0.0, 0.0);
-            zd acc = zmake(0.0, 0.0);
+            const T g = (lane < nb) ? G[(k0 + lane) + (int64_t)c * m] : cx<T>(0, 0);
+            T acc = cx<T>(0, 0);
             for (int p = 0; p < nb; ++p) {
-                zd gp;
+                T gp;
                 gp.x = __shfl_sync(0xffffffffu, g.x, p);
                 gp.y = __shfl_sync(0xffffffffu, g.y, p);
                 if (p <= lane) {
-                    const zd rp = T[p][lane];  // (R11^{-H})_{lane, p} = conj(rinv_{p, lane})
-                    acc = zadd(acc, zmake(rp.x * gp.x + rp.y * gp.y, rp.x * gp.y - rp.y * gp.x));
+                    const T rp = Tb[p][lane];  // (R11^{-H})_{lane, p} = conj(rinv_{p, lane})
+                    acc = cadd(acc, cx<T>(rp.x * gp.x + rp.y * gp.y, rp.x * gp.y - rp.y * gp.x));
                 }
             }
             if (lane < nb) G[(k0 + lane) + (int64_t)c * m] = acc;
@@ -179,26 +191,60 @@ __global__ void __launch_bounds__(PT, 1) k_chol_grid(int m, zd *__restrict__ G, 
             for (int e = tid; e < CB * CB; e += PT) {
                 const int p = e % CB, a = e / CB;
                 const bool okp = p < nb;
-                T[p][a] = (okp && r0 + a < m) ? G[(k0 + p) + (int64_t)(r0 + a) * m] : zmake(0.0, 0.0);
-                P2[p][a] = (okp && c0 + a < m) ? G[(k0 + p) + (int64_t)(c0 + a) * m] : zmake(0.0, 0.0);
+                Tb[p][a] = (okp && r0 + a < m) ? G[(k0 + p) + (int64_t)(r0 + a) * m] : cx<T>(0, 0);
+                P2[p][a] = (okp && c0 + a < m) ? G[(k0 + p) + (int64_t)(c0 + a) * m] : cx<T>(0, 0);
             }
             __syncthreads();
             for (int e = tid; e < CB * CB; e += PT) {
                 const int a = e % CB, b = e / CB;
                 const int gi = r0 + a, gj = c0 + b;
                 if (gi >= m || gj >= m) continue;
-                zd acc = zmake(0.0, 0.0);
+                R ax = 0, ay = 0;
 #pragma unroll 8
                 for (int p = 0; p < CB; ++p) {
-                    const zd x = T[p][a], y = P2[p][b];  // conj(x) y
-                    acc.x += x.x * y.x + x.y * y.y;
-                    acc.y += x.x * y.y - x.y * y.x;
+                    const T x = Tb[p][a], y = P2[p][b];  // conj(x) y
+                    ax += x.x * y.x + x.y * y.y;
+                    ay += x.x * y.y - x.y * y.x;
                 }
-                zd &gv = G[gi + (int64_t)gj * m];
-                gv = zsub(gv, acc);
+                T &gv = G[gi + (int64_t)gj * m];
+                gv = cx<T>(gv.x - ax, gv.y - ay);
             }
         }
         if (!grid_barrier(gs)) return;
+    }
+}
+
+// Unit-diagonal scaling for the FP32 factorisation: dsq_j = sqrt(G_jj) and
+// its reciprocal (dsq[m + j]), then S = (D^-1 G D^-1) in complex64 (m x m).
+__global__ void k_chol_dsq(int m, const zd *__restrict__ G, double *__restrict__ dsq)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const double d = sqrt(G[j + (int64_t)j * m].x);
+    dsq[j] = d;
+    dsq[m + j] = 1.0 / d;
+}
+
+__global__ void k_chol_scale(int m, const zd *__restrict__ G, const double *__restrict__ dsq, cf *__restrict__ S)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        const double f = dsq[m + i] * dsq[m + j];
+        S[e] = cmakef((float)(G[e].x * f), (float)(G[e].y * f));
+    }
+}
+
+// R = R32 D in FP64 (upper triangle; zeros below): the factor of G = D S D.
+__global__ void k_chol_unscale(int m, const cf *__restrict__ R32, const double *__restrict__ dsq,
+                               zd *__restrict__ R)
+{
+    const int64_t total = (int64_t)m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), j = (int)(e / m);
+        R[e] = (i <= j) ? zmake((double)R32[e].x * dsq[j], (double)R32[e].y * dsq[j]) : zmake(0.0, 0.0);
     }
 }
 
@@ -260,20 +306,20 @@ int oz_mm(cudaStream_t s, const OzScratch &oz, int conj_a, int64_t M, int64_t N,
 
 // G (m x m, Hermitian positive definite) -> R upper triangular in place,
 // G = R^H R (upper triangle; the lower one is left as it was).  One
-// cooperative launch (k_chol_grid).  work: 2 barrier words + a 32 x 32
-// scratch.
-int cholesky(cudaStream_t s, int m, zd *G, double *d0, int *fail, unsigned *bar, zd *rinv, int *timeout)
+// cooperative launch (k_chol_grid<T>); pivots checked against tol d0 (d0
+// null: against tol).  work: 2 barrier words + a 32 x 32 scratch.
+template <typename T>
+int chol_launch(cudaStream_t s, int m, T *G, const double *d0, double tol, int *fail, unsigned *bar, T *rinv,
+                int *timeout)
 {
-    k_diag_copy<<<cdiv(m, 128), 128, 0, s>>>(m, G, d0);
-    FEAST_LAUNCH_CHECK();
     int dev = 0, sms = 0, per = 0;
     FEAST_CUDA_TRY(cudaGetDevice(&dev));
     FEAST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_grid, PT, 0));
+    FEAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_grid<T>, PT, 0));
     if (per < 1) return FEAST_ECUDA;
     FEAST_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
     GridSync gs{bar, bar + 1, timeout, TO_CHOL};
-    void *args[] = {&m, &G, &d0, &fail, &rinv, &gs};
+    void *args[] = {&m, &G, &d0, &tol, &fail, &rinv, &gs};
     // as many CTAs as the first trailing update has ~4 tiles for (at least
     // 8, at most one per SM): a small factorisation leaves the rest of the
     // GPU to other work (the pencils of a batch)
@@ -281,9 +327,17 @@ int cholesky(cudaStream_t s, int m, zd *G, double *d0, int *fail, unsigned *bar,
     int grid = nt * (nt + 1) / 8;
     if (grid < 8) grid = 8;
     if (grid > sms) grid = sms;
-    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_chol_grid, dim3(grid), dim3(PT), args, 0, s));
+    FEAST_CUDA_TRY(cudaLaunchCooperativeKernel((void *)k_chol_grid<T>, dim3(grid), dim3(PT), args, 0, s));
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
+}
+
+// The FP64 factorisation, pivots against 1e-12 of the original diagonal.
+int cholesky(cudaStream_t s, int m, zd *G, double *d0, int *fail, unsigned *bar, zd *rinv, int *timeout)
+{
+    k_diag_copy<<<cdiv(m, 128), 128, 0, s>>>(m, G, d0);
+    FEAST_LAUNCH_CHECK();
+    return chol_launch<zd>(s, m, G, d0, 1e-12, fail, bar, rinv, timeout);
 }
 
 }  // namespace
@@ -378,69 +432,103 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
     unsigned long long *emax = (unsigned long long *)(bar + 2);
     const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
     int e;
-    FEAST_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), s));
-    // pass 1: G = V^H V = R_a^H R_a, V <- V R_a^{-1}
-    if ((e = oz_mm(s, oz, 1, m, m, n, one, V, ldv, V, ldv, zero, F0, m))) return e;
-    if ((e = cholesky(s, (int)m, F0, d0, fail, bar, rinv, oz.err))) return e;
-    {
-        int hf = 0;
-        FEAST_CUDA_TRY(cudaMemcpyAsync(&hf, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
-        FEAST_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hf) return FEAST_OK;  // V too ill-conditioned: caller falls back
-    }
-    k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F0, m);
-    FEAST_LAUNCH_CHECK();
-    if ((e = tri_inverse(s, (int)m, F0, m, Ti, Ts))) return e;
-    if ((e = mul_right(s, oz, n, m, V, ldv, Ti, zero, tmp))) return e;
-    // pass 2: G = V^H V = I + E with E ~ eps cond(V)^2.  R_b = I + S with
-    // S + S^H = E - S^H S; S_0 = phi(E), S = phi(E - S_0^H S_0) (error
-    // O(|E|^3), phi = strict upper part + half the diagonal), R_b^{-1} =
-    // I - S + S^2 (error O(|E|^3)): V <- V + V (S^2 - S).  Only when
-    // max|E| <= 1e-4; otherwise a second Cholesky and inverse.
-    if ((e = oz_mm(s, oz, 1, m, m, n, one, V, ldv, V, ldv, zero, F1, m))) return e;
-    FEAST_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), s));
-    k_offident_max<<<grid_for(mm), 256, 0, s>>>((int)m, F1, emax);
-    FEAST_LAUNCH_CHECK();
-    unsigned long long hb = 0;
-    FEAST_CUDA_TRY(cudaMemcpyAsync(&hb, emax, sizeof(hb), cudaMemcpyDeviceToHost, s));
-    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
-    double hemax;
-    memcpy(&hemax, &hb, sizeof(double));
-    if (hemax <= 1e-4) {
-        // S_0 = phi(G - I) into Ti; S = phi(G - I - S_0^H S_0) into Ts (m x m)
-        // (the products of these small corrections on the tensor cores: the
-        // digit planes scale per row and column, so their error is relative
-        // to the corrections themselves)
-        zd *S = Ti, *D = rinv_big;
-        k_phi<<<grid_for(mm), 256, 0, s>>>((int)m, F1, nullptr, S);
-        FEAST_LAUNCH_CHECK();
-        if ((e = oz_mm(s, oz, 1, m, m, m, one, S, m, S, m, zero, D, m))) return e;   // S_0^H S_0
-        k_phi<<<grid_for(mm), 256, 0, s>>>((int)m, F1, D, S);
-        FEAST_LAUNCH_CHECK();
-        // D = S^2 - S, then V <- V + V D
-        FEAST_CUDA_TRY(cudaMemcpyAsync(D, S, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
-        if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, S, m, zmake(-1.0, 0.0), D, m))) return e;
-        if ((e = mul_right(s, oz, n, m, V, ldv, D, one, tmp))) return e;
-        // R = (I + S) R_a
-        if (R) {
-            FEAST_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(zd) * ldr, F0, sizeof(zd) * m, sizeof(zd) * m, m,
+    // The first factorisation only has to bring V R_a^{-1} close to
+    // orthonormal (the second pass corrects it; R stays exact because V is
+    // multiplied by the FP64 inverse of the R_a used): on the digit-sliced
+    // path it runs in FP32 on the unit-diagonal Gram matrix D^-1 G D^-1,
+    // with V kept in tmp.  A pivot at or below 1e-4 there, or a second-pass
+    // defect max|E| above 1/2, starts again from V in FP64.
+    const bool try32 = oz.rows != nullptr && tmp != nullptr && m >= kChol32MinM;
+    bool dirty = false;   // V holds the product of a discarded FP32 first pass
+    for (int attempt = try32 ? 0 : 1; attempt < 2; ++attempt) {
+        const bool use32 = attempt == 0;
+        if (use32)
+            FEAST_CUDA_TRY(cudaMemcpy2DAsync(tmp, sizeof(zd) * n, V, sizeof(zd) * ldv, sizeof(zd) * n, m,
                                              cudaMemcpyDeviceToDevice, s));
-            if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, F0, m, one, R, ldr))) return e;
+        else if (dirty)
+            FEAST_CUDA_TRY(cudaMemcpy2DAsync(V, sizeof(zd) * ldv, tmp, sizeof(zd) * n, sizeof(zd) * n, m,
+                                             cudaMemcpyDeviceToDevice, s));
+        FEAST_CUDA_TRY(cudaMemsetAsync(fail, 0, sizeof(int), s));
+        // pass 1: G = V^H V = R_a^H R_a, V <- V R_a^{-1}
+        if ((e = oz_mm(s, oz, 1, m, m, n, one, V, ldv, V, ldv, zero, F0, m))) return e;
+        int hf = 0;
+        if (use32) {
+            cf *S32 = (cf *)F1;          // (F1 is free until pass 2)
+            double *dsq = (double *)Ti;  // 2m: (Ti is written after the unscaling)
+            k_chol_dsq<<<cdiv(m, 128), 128, 0, s>>>((int)m, F0, dsq);
+            FEAST_LAUNCH_CHECK();
+            k_chol_scale<<<grid_for(mm), 256, 0, s>>>((int)m, F0, dsq, S32);
+            FEAST_LAUNCH_CHECK();
+            if ((e = chol_launch<cf>(s, (int)m, S32, nullptr, kChol32Tol, fail, bar, (cf *)rinv, oz.err))) return e;
+            FEAST_CUDA_TRY(cudaMemcpyAsync(&hf, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+            if (hf) continue;            // beyond FP32: the FP64 factorisation
+            k_chol_unscale<<<grid_for(mm), 256, 0, s>>>((int)m, S32, dsq, F0);
+            FEAST_LAUNCH_CHECK();
+        } else {
+            if ((e = cholesky(s, (int)m, F0, d0, fail, bar, rinv, oz.err))) return e;
+            FEAST_CUDA_TRY(cudaMemcpyAsync(&hf, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+            FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+            if (hf) return FEAST_OK;     // V too ill-conditioned: caller falls back
+            k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F0, m);
+            FEAST_LAUNCH_CHECK();
         }
-    } else {
-        if ((e = cholesky(s, (int)m, F1, d0, fail, bar, rinv, oz.err))) return e;
-        k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F1, m);
-        FEAST_LAUNCH_CHECK();
-        if ((e = tri_inverse(s, (int)m, F1, m, Ti, Ts))) return e;
+        if ((e = tri_inverse(s, (int)m, F0, m, Ti, Ts))) return e;
         if ((e = mul_right(s, oz, n, m, V, ldv, Ti, zero, tmp))) return e;
-        // R = R_b R_a
-        if (R && (e = oz_mm(s, oz, 0, m, m, m, one, F1, m, F0, m, zero, R, ldr))) return e;
-    }
-    if (R) {
-        k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, R, ldr);
+        dirty = use32;
+        // pass 2: G = V^H V = I + E with E ~ eps cond(V)^2 (FP64 first
+        // pass; ~2^-24 cond(D^-1 G D^-1) after the FP32 one).  R_b = I + S
+        // with S + S^H = E - S^H S; S_0 = phi(E), S = phi(E - S_0^H S_0)
+        // (error O(|E|^3), phi = strict upper part + half the diagonal),
+        // R_b^{-1} = I - S + S^2 (error O(|E|^3)): V <- V + V (S^2 - S).
+        // Only when max|E| <= 1e-4; otherwise a second Cholesky and inverse.
+        if ((e = oz_mm(s, oz, 1, m, m, n, one, V, ldv, V, ldv, zero, F1, m))) return e;
+        FEAST_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), s));
+        k_offident_max<<<grid_for(mm), 256, 0, s>>>((int)m, F1, emax);
         FEAST_LAUNCH_CHECK();
+        unsigned long long hb = 0;
+        FEAST_CUDA_TRY(cudaMemcpyAsync(&hb, emax, sizeof(hb), cudaMemcpyDeviceToHost, s));
+        FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+        double hemax;
+        memcpy(&hemax, &hb, sizeof(double));
+        if (use32 && !(hemax <= 0.5)) continue;
+        if (hemax <= 1e-4) {
+            // S_0 = phi(G - I) into Ti; S = phi(G - I - S_0^H S_0) into Ts (m x m)
+            // (the products of these small corrections on the tensor cores: the
+            // digit planes scale per row and column, so their error is relative
+            // to the corrections themselves)
+            zd *S = Ti, *D = rinv_big;
+            k_phi<<<grid_for(mm), 256, 0, s>>>((int)m, F1, nullptr, S);
+            FEAST_LAUNCH_CHECK();
+            if ((e = oz_mm(s, oz, 1, m, m, m, one, S, m, S, m, zero, D, m))) return e;   // S_0^H S_0
+            k_phi<<<grid_for(mm), 256, 0, s>>>((int)m, F1, D, S);
+            FEAST_LAUNCH_CHECK();
+            // D = S^2 - S, then V <- V + V D
+            FEAST_CUDA_TRY(cudaMemcpyAsync(D, S, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
+            if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, S, m, zmake(-1.0, 0.0), D, m))) return e;
+            if ((e = mul_right(s, oz, n, m, V, ldv, D, one, tmp))) return e;
+            // R = (I + S) R_a
+            if (R) {
+                FEAST_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(zd) * ldr, F0, sizeof(zd) * m, sizeof(zd) * m, m,
+                                                 cudaMemcpyDeviceToDevice, s));
+                if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, F0, m, one, R, ldr))) return e;
+            }
+        } else {
+            if ((e = cholesky(s, (int)m, F1, d0, fail, bar, rinv, oz.err))) return e;
+            k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F1, m);
+            FEAST_LAUNCH_CHECK();
+            if ((e = tri_inverse(s, (int)m, F1, m, Ti, Ts))) return e;
+            if ((e = mul_right(s, oz, n, m, V, ldv, Ti, zero, tmp))) return e;
+            // R = R_b R_a
+            if (R && (e = oz_mm(s, oz, 0, m, m, m, one, F1, m, F0, m, zero, R, ldr))) return e;
+        }
+        if (R) {
+            k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, R, ldr);
+            FEAST_LAUNCH_CHECK();
+        }
+        *ok = 1;
+        return FEAST_OK;
     }
-    *ok = 1;
     return FEAST_OK;
 }
 

@@ -1860,7 +1860,20 @@ int schur_vectors(cudaStream_t s, int m, const zd *T, zd *Y, double snorm, zd *s
 {
     k_transpose<<<dim3(cdiv(m, 32), cdiv(m, 32)), 256, 0, s>>>(m, T, m, scratch);
     FEAST_LAUNCH_CHECK();
-    k_schur_vectors<<<cdiv((size_t)m * 32, 256), 256, 0, s>>>(m, scratch, m, Y, snorm);
+    // one CTA per SM with ceil(m / SMs) warps: eigenvector k on CTA k mod
+    // G, so every SM gets the same mix of long and short back-substitutions
+    // (a grid of 8-warp CTAs a little larger than the SM count doubles the
+    // work of the SMs that take two)
+    int dev = 0, sms = 0;
+    FEAST_CUDA_TRY(cudaGetDevice(&dev));
+    FEAST_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int G = sms < m ? sms : m;
+    int wpc = (m + G - 1) / G;
+    if (wpc > 32) {
+        wpc = 32;
+        G = (m + 31) / 32;
+    }
+    k_schur_vectors<<<G, 32 * wpc, 0, s>>>(m, scratch, m, Y, snorm);
     FEAST_LAUNCH_CHECK();
     return FEAST_OK;
 }

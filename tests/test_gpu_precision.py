@@ -96,13 +96,17 @@ def test_gfeast_precision_form_n200():
     g.close(); o.close()
 
 
-@pytest.mark.parametrize("n,m0,cond", [(200, 64, 1e2), (700, 230, 1e4), (700, 230, 1e9)])
+@pytest.mark.parametrize("n,m0,cond", [(200, 64, 1e2), (700, 230, 1e4), (700, 230, 1e9), (1000, 300, 3.0),
+                                        (1000, 300, 1e2), (1000, 300, 1e5), (1000, 300, 1e9)])
 def test_cholesky_qr_of_b_u1(n, m0, cond):
     """U2 R2 = B U1 in the precision form (Cholesky QR twice on tensor-core
     Gram matrices; BCGS2 when the block is too ill-conditioned for it -- the
-    cond = 1e9 case): U2 orthonormal, R2 upper triangular with a real
+    cond = 1e9 cases): U2 orthonormal, R2 upper triangular with a real
     positive diagonal, U2 R2 = B U1, and both equal to the unique Householder
-    factors with that sign convention (numpy's QR, signs fixed)."""
+    factors with that sign convention (numpy's QR, signs fixed).  From
+    m0 = 256 the first factorisation is tried in FP32 on the unit-diagonal
+    Gram matrix; the m0 = 300 cases reach its series pass, a second FP64
+    Cholesky, its FP64 restart or BCGS2 as their conditioning requires."""
     fg = _fg()
     p = inputs.prescribed_pencil(n, m0, seed=n + 1)
     g = fg.Feast(p.A, p.B, p.Y, prec=fg.FEAST_C64_REFINE, q=8, center=0j, a=1.0)
