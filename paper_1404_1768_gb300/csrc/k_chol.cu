@@ -24,6 +24,7 @@ namespace {
 constexpr int CB = 32;  // Cholesky block
 constexpr int kChol32MinM = 256;      // the FP32 first factorisation from this block width up
 constexpr double kChol32Tol = 1e-4;   // its pivots against the unit diagonal
+constexpr double kSeriesMax = 1e-2;   // largest Gram defect repeated series rounds take on (no R)
 
 __global__ void k_diag_copy(int m, const zd *__restrict__ G, double *__restrict__ d)
 {
@@ -409,6 +410,23 @@ static int mul_right(cudaStream_t s, const OzScratch &oz, int64_t n, int64_t m, 
     return zgemm_batched(s, 0, n, m, m, one, tmp, n, 0, X, m, 0, beta, V, ldv, 0, 1);
 }
 
+// G = V^H V (m x m) and max |G - I| (read back).
+static int gram_defect(cudaStream_t s, const OzScratch &oz, int64_t n, int64_t m, const zd *V, int64_t ldv, zd *G,
+                       unsigned long long *emax, double *hemax)
+{
+    const zd one = zmake(1.0, 0.0), zero = zmake(0.0, 0.0);
+    int e;
+    if ((e = oz_mm(s, oz, 1, m, m, n, one, V, ldv, V, ldv, zero, G, m))) return e;
+    FEAST_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), s));
+    k_offident_max<<<grid_for((size_t)m * m), 256, 0, s>>>((int)m, G, emax);
+    FEAST_LAUNCH_CHECK();
+    unsigned long long hb = 0;
+    FEAST_CUDA_TRY(cudaMemcpyAsync(&hb, emax, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    FEAST_CUDA_TRY(cudaStreamSynchronize(s));
+    memcpy(hemax, &hb, sizeof(double));
+    return FEAST_OK;
+}
+
 int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, int64_t ldr, void *work,
                const OzScratch &oz, int *ok, zd *tmp)
 {
@@ -481,22 +499,25 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
         // with S + S^H = E - S^H S; S_0 = phi(E), S = phi(E - S_0^H S_0)
         // (error O(|E|^3), phi = strict upper part + half the diagonal),
         // R_b^{-1} = I - S + S^2 (error O(|E|^3)): V <- V + V (S^2 - S).
-        // Only when max|E| <= 1e-4; otherwise a second Cholesky and inverse.
-        if ((e = oz_mm(s, oz, 1, m, m, n, one, V, ldv, V, ldv, zero, F1, m))) return e;
-        FEAST_CUDA_TRY(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), s));
-        k_offident_max<<<grid_for(mm), 256, 0, s>>>((int)m, F1, emax);
-        FEAST_LAUNCH_CHECK();
-        unsigned long long hb = 0;
-        FEAST_CUDA_TRY(cudaMemcpyAsync(&hb, emax, sizeof(hb), cudaMemcpyDeviceToHost, s));
-        FEAST_CUDA_TRY(cudaStreamSynchronize(s));
-        double hemax;
-        memcpy(&hemax, &hb, sizeof(double));
+        double hemax = 0.0;
+        if ((e = gram_defect(s, oz, n, m, V, ldv, F1, emax, &hemax))) return e;
         if (use32 && !(hemax <= 0.5)) continue;
-        if (hemax <= 1e-4) {
-            // S_0 = phi(G - I) into Ti; S = phi(G - I - S_0^H S_0) into Ts (m x m)
-            // (the products of these small corrections on the tensor cores: the
-            // digit planes scale per row and column, so their error is relative
-            // to the corrections themselves)
+        // Series rounds, each taking a defect E to O(|E|^3): one when max|E|
+        // <= 1e-4 (R = (I + S) R_a then holds to O(|E|^3) as well).  Without
+        // R (only Q's span and orthonormality wanted, and every round is an
+        // upper triangular map with a positive diagonal, so Q is still the
+        // unique factor) up to three from max|E| <= kSeriesMax, the Gram
+        // matrix and its defect measured again after each round that started
+        // above 1e-4.  A defect out of their reach gets a second Cholesky and
+        // inverse instead.
+        const double series_max = R ? 1e-4 : kSeriesMax;
+        bool finished = false;
+        int rounds = 0;
+        while (hemax <= series_max && rounds < 3) {
+            // S_0 = phi(G - I) into Ti; S = phi(G - I - S_0^H S_0) into Ti
+            // (the products of these small corrections on the tensor cores:
+            // the digit planes scale per row and column, so their error is
+            // relative to the corrections themselves)
             zd *S = Ti, *D = rinv_big;
             k_phi<<<grid_for(mm), 256, 0, s>>>((int)m, F1, nullptr, S);
             FEAST_LAUNCH_CHECK();
@@ -507,19 +528,26 @@ int zorth_chol(cudaStream_t s, int64_t n, int64_t m, zd *V, int64_t ldv, zd *R, 
             FEAST_CUDA_TRY(cudaMemcpyAsync(D, S, sizeof(zd) * mm, cudaMemcpyDeviceToDevice, s));
             if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, S, m, zmake(-1.0, 0.0), D, m))) return e;
             if ((e = mul_right(s, oz, n, m, V, ldv, D, one, tmp))) return e;
-            // R = (I + S) R_a
+            // R = (I + S) R_a (R: a single round)
             if (R) {
                 FEAST_CUDA_TRY(cudaMemcpy2DAsync(R, sizeof(zd) * ldr, F0, sizeof(zd) * m, sizeof(zd) * m, m,
                                                  cudaMemcpyDeviceToDevice, s));
                 if ((e = oz_mm(s, oz, 0, m, m, m, one, S, m, F0, m, one, R, ldr))) return e;
             }
-        } else {
+            ++rounds;
+            if (hemax <= 1e-4) {
+                finished = true;
+                break;
+            }
+            if ((e = gram_defect(s, oz, n, m, V, ldv, F1, emax, &hemax))) return e;
+        }
+        if (!finished) {
             if ((e = cholesky(s, (int)m, F1, d0, fail, bar, rinv, oz.err))) return e;
             k_zero_lower<<<grid_for(mm), 256, 0, s>>>((int)m, F1, m);
             FEAST_LAUNCH_CHECK();
             if ((e = tri_inverse(s, (int)m, F1, m, Ti, Ts))) return e;
             if ((e = mul_right(s, oz, n, m, V, ldv, Ti, zero, tmp))) return e;
-            // R = R_b R_a
+            // R = R_b R_a (with R no series round has run)
             if (R && (e = oz_mm(s, oz, 0, m, m, m, one, F1, m, F0, m, zero, R, ldr))) return e;
         }
         if (R) {
