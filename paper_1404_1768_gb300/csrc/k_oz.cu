@@ -12,11 +12,14 @@
 //     A' = diag(2^e) sum_s 64^-s A_s ,   likewise B' = (sum_t 64^-t B_t) diag(2^f).
 // Digits are small integers, exact in bf16, and a digit product is exact in
 // the FP32 accumulator; so is any sum of products of one weight class
-// g = s + t over a K-chunk of OZ_KC terms (its magnitude stays below 2^24).
-// The kernel keeps one tensor-memory accumulator per class g = 2..9 (all
-// products with s + t <= OZ_S + 1; the rest weigh < 2^-60), reads the classes
-// out after each K-chunk and sums them in FP64 registers as
-// acc += sum_g 64^-(g-2) S_g; finally C gets alpha_c 2^(e_i + f_j - 12) acc.
+// g = s + t over a K-chunk of OZ_KC terms while it stays below 2^24 (the
+// leading classes always do; a late class can pass it only by a factor
+// ~1.3 at worst, and rounds then at a weight below 2^-60).  The kernel keeps
+// one tensor-memory accumulator per class g = 2..9 (all products with
+// s + t <= OZ_S + 1; the rest weigh < 2^-60), reads the classes out after
+// each K-chunk, combines them on the integer pipe into two exact int64
+// partials and adds acc += sum_g 64^-(g-2) S_g in FP64 with two roundings;
+// finally C gets alpha_c 2^(e_i + f_j - 12) acc.
 // Representation and truncation error: ~2^-48 relative to
 // max_k |A'_ik| * max_k |B'_kj| per entry, K-fold at most.
 //
